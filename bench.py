@@ -1,0 +1,358 @@
+"""Benchmark of the constrained-motion hot path on one GB300 (or N replicas).
+
+Prints one JSON line: whole-job constrained waypoints/s (projection + FK + CC) of the CUDA
+library on seeded synthetic workloads, with the dominant kernel's roofline, an end-to-end
+figure through the C ABI with host buffers, and the FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload validate|plan]
+  python bench.py --impl reference ...   # the oracle arm (CPU), same workload and metric
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_06791_gb300 import synth as S  # noqa: E402
+
+METRIC = "constrained waypoints/s (proj+FK+CC); p50 plan ms, learned vs plain @1e-4 resid"
+UNIT = "waypoints/s"
+
+# ---- algorithmic work per unit (FP32 operations of the method as the kernels state it;
+#      FMA = 2, add/mul/min/max/compare = 1, each sin/cos pair, atan2, sqrt, rsqrt and
+#      divide = 1) ----
+F_CHAIN_JOINT = 48          # one DH joint of the chain (u, v, p, y, z columns)
+F_TASK_RP_JOINT = 8         # roll/pitch task-Jacobian entries per joint
+F_TASK_RP_FIXED = 12        # Euler angles and the rate map (2 atan2, sqrt, rsqrt, div, ...)
+F_DAMPED_JOINT = 9          # J J^T accumulation (6) + g = J^T y (3) per joint
+F_DAMPED_FIXED = 10         # 2x2 solve
+F_UPDATE_JOINT = 10         # smoothing hinge, update, clamp per joint
+F_VALIDITY = 4
+F_SPHERE_FK = 18            # R c + p
+F_PAIR_SPHERE = 11
+F_PAIR_BOX = 34
+F_PAIR_CAPSULE = 25
+
+
+def flops_waypoint_iter(dof: int) -> int:
+    return (dof * (F_CHAIN_JOINT + F_TASK_RP_JOINT + F_DAMPED_JOINT + F_UPDATE_JOINT)
+            + dof + F_TASK_RP_FIXED + F_DAMPED_FIXED + F_VALIDITY)
+
+
+def flops_cc_waypoint(n_spheres: int, n_sph: int, n_box: int, n_cap: int) -> int:
+    return n_spheres * (F_SPHERE_FK + n_sph * F_PAIR_SPHERE + n_box * F_PAIR_BOX
+                        + n_cap * F_PAIR_CAPSULE)
+
+
+def algorithmic_flops(dof, W, S_, scene_counts, status, first_fail, iters):
+    """Work the method evaluates for these outcomes: Alg. 1 evaluates waypoints 1..W-1 in
+    each of its iterations; FK + CC walk waypoints 0..first colliding one (all W if valid,
+    none if the projection failed)."""
+    status = np.asarray(status).astype(np.int64)
+    ff = np.asarray(first_fail).astype(np.int64)
+    it = np.asarray(iters).astype(np.int64)
+    proj = (it * (W - 1)).sum() * flops_waypoint_iter(dof)
+    cc_wp = np.where(status == 0, W, np.where(status == 2, ff + 1, 0)).sum()
+    return float(proj + cc_wp * flops_cc_waypoint(S_, *scene_counts)), int(cc_wp)
+
+
+def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP32 FMA-pipe peak: SMs x 128 lanes x 2 FLOP x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# workloads
+
+def config1_workload(seed=1):
+    """7-DOF arm (59 spheres), 16 obstacle spheres in the 1.2 m cube, 256 motions x 32
+    waypoints between uniform configurations, roll/pitch constraint, <= 20 iterations."""
+    rb = S.make_arm7(seed)
+    sc = S.make_scene(1000 + seed, n_sph=16)
+    c = S.roll_pitch(20)
+    return rb, sc, c, 256, 32
+
+
+def manifold_starts_gpu(ctx, rb, n, seed):
+    """Uniform configurations projected onto the manifold by the library (inputs only)."""
+    import torch
+    out = []
+    k = 0
+    while sum(len(o) for o in out) < n:
+        q = torch.from_numpy(S.uniform_configs(rb, 2 * n, seed + k).astype(np.float32)).cuda()
+        r = ctx.project_configs(q, 60)
+        ok = r["ok"].bool()
+        out.append(r["q"][ok])
+        k += 1
+    return torch.cat(out)[:n].contiguous()
+
+
+def init_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("CPRRTC_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_validate(args, world, rank, local):
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    rb, sc, c, n, W = config1_workload()
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_obstacles(sc)
+    ctx.set_constraint(c)
+    with torch.cuda.stream(stream):
+        # each rank validates its own seeded batch (weak scaling, no collective)
+        q0 = manifold_starts_gpu(ctx, rb, n, 10_000 + 97 * rank)
+        q1 = torch.from_numpy(S.uniform_configs(rb, n, 20_000 + 97 * rank).astype(np.float32)).to(dev)
+        out = ctx.alloc_validate_outputs(n, W, q0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            ctx.validate(q0, q1, W, out=out)
+        stream.synchronize()
+        ctx.set_timing(True)
+        ctx.reset_timing()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        for k in range(args.steps):
+            flush.fill_(float(k))            # evict L2 between steps (write > L2 size)
+            starts[k].record(stream)
+            ctx.validate(q0, q1, W, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        kms, launches = ctx.kernel_time("validate")
+        ctx.set_timing(False)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    st = out["status"].cpu().numpy()
+    ff = out["first_fail"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    flops, cc_wp = algorithmic_flops(rb.dof, W, len(rb.spheres),
+                                     (len(sc.sph), len(sc.box), len(sc.cap)), st, ff, it)
+    waypoints = n * W * args.steps * world
+    value = waypoints / (total_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    h_q0 = q0.cpu().pin_memory()
+    h_q1 = q1.cpu().pin_memory()
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()}
+    for _ in range(2):
+        ctx.validate(h_q0, h_q1, W, out=h_out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.validate(h_q0, h_q1, W, out=h_out)
+    e2e_s = time.perf_counter() - t0
+    h2d = 2 * n * rb.dof * 4
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values())
+    e2e = {"value": n * W * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    avg_kernel_s = kms / 1e3 / max(launches, 1)
+    achieved = flops / avg_kernel_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "config 1: batched constrained motion validation",
+                   "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
+                   "obstacles": {"spheres": len(sc.sph)}, "constraint": "roll-pitch",
+                   "max_iters": c.max_iters, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "outcomes": {"valid": int((st == 0).sum()), "proj_fail": int((st == 1).sum()),
+                     "collision": int((st == 2).sum()), "mean_iters": float(it.mean()),
+                     "cc_waypoints": cc_wp},
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "validate_kernel", "flop_per_launch": flops,
+                     "avg_launch_ms": avg_kernel_s * 1e3,
+                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
+                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return line, (rb, sc, c, n, W, q0.cpu().numpy(), q1.cpu().numpy())
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+
+
+def cpu_baseline_validate(inputs, budget_s=10.0):
+    """The FP64 oracle, as it stands, on the host cores over the same motions."""
+    import oracle
+    rb, sc, c, n, W, q0, q1 = inputs
+    orc = oracle.Oracle(rb, sc, c)
+    cores = os.cpu_count() or 1
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        orc.validate(q0, q1, W, n_threads=cores)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 200:
+            break
+    return {"value": n * W * reps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} passes over the same {n} motions x {W} waypoints "
+                      f"({el:.1f} s, {cores} threads)"}
+
+
+def reference_arm(args, world, rank):
+    """The oracle arm: the FP64 CPU oracle as it stands, on the same workload and metric."""
+    if rank != 0:
+        return None
+    import oracle
+    rb, sc, c, n, W = config1_workload()
+    orc = oracle.Oracle(rb, sc, c)
+    starts = []
+    for q in S.uniform_configs(rb, 4 * n, 10_000):
+        ok, qp, _, _ = orc.project_config(q, max_iters=60)
+        if ok:
+            starts.append(qp)
+        if len(starts) == n:
+            break
+    q0 = S.f32(np.array(starts))
+    q1 = S.uniform_configs(rb, n, 20_000)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        orc.validate(q0, q1, W, n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.validate(q0, q1, W, n_threads=cores)
+    el = time.perf_counter() - t0
+    value = n * W * args.steps / el
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "config 1: batched constrained motion validation",
+                       "motions": n, "W": W, "dof": rb.dof, "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} passes over {n} motions x {W} waypoints"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="validate", choices=["validate"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    world, rank, local = init_dist()
+    if args.impl == "reference":
+        line = reference_arm(args, world, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    line, inputs = run_validate(args, world, rank, local)
+    if rank == 0:
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline_validate(inputs, args.cpu_budget)
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * cprrtc.h — C ABI of the GB300 (sm_103a) constrained-motion library.
+ *
+ * The library implements the data-parallel hot path of cpRRTC (Hu, Wang, Christensen,
+ * "cpRRTC: GPU-Parallel RRT-Connect for Constrained Motion Planning"): for each candidate
+ * motion, straight-line interpolation (Sec. III), parallel projection of the waypoints onto
+ * a task-constraint manifold (Sec. III-A, Algorithm 1), forward kinematics of the robot's
+ * collision spheres and sphere-vs-obstacle collision checks with early termination
+ * (Sec. IV), and RRT-Connect tree extension with greedy connect (Sec. III, Sec. II).
+ *
+ * Conventions shared by every call:
+ *  - Return value: CPRRTC_OK (0) or a negative CPRRTC_E_* code. On error nothing is written
+ *    to outputs except where stated, and cprrtc_last_error(ctx) describes the failure.
+ *    Per-motion and per-problem outcomes are reported in status arrays, never as errors.
+ *  - Arrays are C-contiguous. Configurations are FP32, [n][dof]. Robot and scene
+ *    parameters are passed as doubles and stored on the device as FP32.
+ *  - Array pointers may be host or device memory (detected per pointer). If every array of
+ *    a call is device memory the call is asynchronous on the context's stream; otherwise
+ *    the library copies through its own device buffers and returns after the results are in
+ *    host memory.
+ *  - The caller owns every buffer it passes. set_* calls copy their arguments into
+ *    library-owned device memory, replacing the previous copy.
+ *  - One context per host thread; contexts are independent.
+ */
+#ifndef CPRRTC_H
+#define CPRRTC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPRRTC_MAX_DOF 8
+#define CPRRTC_MAX_W 64
+#define CPRRTC_MAX_SPHERES 256
+
+/* ---- error codes ---- */
+#define CPRRTC_OK 0
+#define CPRRTC_E_INVALID_ARG (-1)
+#define CPRRTC_E_NOT_CONFIGURED (-2)
+#define CPRRTC_E_CUDA (-3)
+#define CPRRTC_E_OOM (-4)
+#define CPRRTC_E_CAPACITY (-5)
+#define CPRRTC_E_TIMEOUT (-6)
+#define CPRRTC_E_UNSUPPORTED (-7)
+
+/* ---- enums ---- */
+#define CPRRTC_JOINT_REVOLUTE 0
+#define CPRRTC_JOINT_PRISMATIC 1
+
+#define CPRRTC_CONSTRAINT_NONE 0       /* no projection; collision checks only */
+#define CPRRTC_CONSTRAINT_ROLL_PITCH 1 /* end-effector roll and pitch held at 0 */
+#define CPRRTC_CONSTRAINT_Z_PLANE 2    /* end-effector point on the plane z = target */
+
+#define CPRRTC_MOTION_VALID 0
+#define CPRRTC_MOTION_PROJ_FAIL 1 /* Alg. 1 returned None (not projected in max_iters) */
+#define CPRRTC_MOTION_COLLISION 2
+
+/* ---- robot and scene ---- */
+
+/* One joint in standard Denavit-Hartenberg form (Sec. III: FK per waypoint):
+ * revolute  T = Rz(theta0 + q) Tz(d) Tx(a) Rx(alpha);
+ * prismatic T = Rz(theta0) Tz(d + q) Tx(a) Rx(alpha). Limits [lo, hi] clamp projection. */
+typedef struct {
+  int type;
+  double d, a, alpha, theta0, lo, hi;
+} cprrtc_joint;
+
+/* A collision sphere rigidly attached to a frame: frame 0 is the base (world), frame k the
+ * frame after joint k; centre (x, y, z) in that frame, radius r > 0. */
+typedef struct {
+  int frame;
+  double x, y, z, r;
+} cprrtc_sphere;
+
+typedef struct {
+  double x, y, z, r;
+} cprrtc_obs_sphere;
+
+/* Oriented box: centre c, half-extents h, rotation R (row-major) with world = c + R local. */
+typedef struct {
+  double c[3];
+  double h[3];
+  double R[9];
+} cprrtc_obs_box;
+
+/* Capsule: segment p0-p1 swept by a ball of radius r. */
+typedef struct {
+  double p0[3];
+  double p1[3];
+  double r;
+} cprrtc_obs_capsule;
+
+/* Task constraint and the parameters of Algorithm 1 (Sec. III-A). A waypoint is valid when
+ * ||E_task||_inf < tol_task and max_k E_sm,k < tol_sm, with
+ * E_sm,k = max(0, |xi_k[i] - xi_k[i-1]| - tau) and
+ * tau = max(c_sm * ||q_end - q_start||_inf / (W - 1), tau_floor).
+ * Update: xi_new[i] = clamp(xi[i] - alpha (J^+ E_task + (xi[i] - xi[i-1]) * E_sm)), with
+ * the damped pseudoinverse J^+ = J^T (J J^T + lambda^2 I)^-1. */
+typedef struct {
+  int type;         /* CPRRTC_CONSTRAINT_* */
+  double target;    /* plane height for Z_PLANE */
+  double tol_task;  /* default 1e-4 */
+  double c_sm;      /* default 2 */
+  double tau_floor; /* default 1e-3 */
+  double tol_sm;    /* default 1e-4 */
+  double alpha;     /* default 1 */
+  double lambda;    /* default 1e-3 */
+  int max_iters;    /* 1..255, default 20 */
+} cprrtc_constraint;
+
+typedef struct cprrtc_ctx cprrtc_ctx;
+
+/* ---- lifecycle ---- */
+
+/* Creates a context on CUDA device `device`. `stream` is a cudaStream_t (NULL: the legacy
+ * default stream). *out receives the context; it is NULL on failure.
+ * Errors: E_INVALID_ARG (out NULL, bad device), E_CUDA, E_OOM. */
+int cprrtc_create(cprrtc_ctx** out, int device, void* stream);
+
+/* Frees the context and every device buffer it owns. Accepts NULL. */
+int cprrtc_destroy(cprrtc_ctx* ctx);
+
+/* Replaces the stream later calls run on. */
+int cprrtc_set_stream(cprrtc_ctx* ctx, void* stream);
+
+/* Message for the last error on this context ("" if none). Owned by the context. */
+const char* cprrtc_last_error(const cprrtc_ctx* ctx);
+
+/* Robot kinematic table and collision spheres (Sec. III: "each thread performs forward
+ * kinematics (FK) and collision checking (CC)"). 1 <= dof <= 8, 1 <= n_spheres <= 256,
+ * sphere frames in [0, dof], ee = end-effector point in frame dof (host pointers).
+ * Errors: E_INVALID_ARG, E_UNSUPPORTED (sizes beyond the maxima), E_CUDA, E_OOM. */
+int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
+                     const cprrtc_sphere* spheres, int n_spheres, const double ee[3]);
+
+/* Obstacle set (Sec. IV; cuboid obstacles in Sec. V). Host pointers; a pointer may be NULL
+ * when its count is 0. Counts >= 0; the total may be 0. Errors: E_INVALID_ARG, E_CUDA,
+ * E_OOM. */
+int cprrtc_set_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* spheres, int n_spheres,
+                         const cprrtc_obs_box* boxes, int n_boxes,
+                         const cprrtc_obs_capsule* capsules, int n_capsules);
+
+/* Task constraint and Algorithm 1 parameters (Sec. III-A). Errors: E_INVALID_ARG. */
+int cprrtc_set_constraint(cprrtc_ctx* ctx, const cprrtc_constraint* c);
+
+/* ---- motion validation (Sec. III, Alg. 1, Sec. IV) ---- */
+
+/* Validates n motions q_start[m] -> q_end[m], each as W >= 2 interpolated waypoints
+ * (W <= 64): interpolation, Alg. 1 projection (unless the constraint is NONE), then FK and
+ * CC of every waypoint of the projected segment, waypoint 0 included.
+ * Outputs (any may be NULL except status):
+ *   out_q      [n][W][dof] projected segment (for PROJ_FAIL: the segment after the last
+ *              iteration);
+ *   status     [n] CPRRTC_MOTION_*;
+ *   first_fail [n] first unaccepted waypoint (PROJ_FAIL), first colliding waypoint
+ *              (COLLISION) or -1 (VALID);
+ *   iters      [n] iteration at which Alg. 1 accepted the segment (0 for NONE;
+ *              max_iters on PROJ_FAIL);
+ *   resid      [n] max over waypoints 1..W-1 of the last evaluated ||E_task||_inf.
+ * Requires set_robot. Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_UNSUPPORTED, E_CUDA,
+ * E_OOM. n = 0 is a no-op. */
+int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, int n, int W,
+                    float* out_q, uint8_t* status, int32_t* first_fail, uint8_t* iters,
+                    float* resid);
+
+/* Projects n single configurations onto the constraint manifold by repeated damped steps
+ * q <- clamp(q - alpha J^+ E_task) until ||E_task||_inf < tol_task, at most max_iters
+ * steps (the per-waypoint update of Alg. 1 without the smoothing term; the projection
+ * operator of CBiRRT-style planners, Sec. II). q_out [n][dof]; ok [n] 1/0; resid [n]
+ * (may be NULL). Requires set_robot and a constraint other than NONE. */
+int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,
+                           float* q_out, uint8_t* ok, float* resid);
+
+/* ---- timing ---- */
+
+/* When enabled, the library records CUDA events around each launch of its kernels on the
+ * context's stream. cprrtc_kernel_time returns the summed device time (ms) and the launch
+ * count of the kernel named `name` ("validate", "project", "plan") since the last reset,
+ * synchronising on the events. */
+int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
+int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
+int cprrtc_reset_timing(cprrtc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPRRTC_H */

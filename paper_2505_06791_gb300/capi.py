@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libcprrtc.so (include/cprrtc.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name; `Context` wraps a context
+handle. Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory);
+all computation happens in the library's CUDA kernels. If the library is missing this
+module raises on first use: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcprrtc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cprrtc.h")
+
+OK = 0
+E_INVALID_ARG, E_NOT_CONFIGURED, E_CUDA, E_OOM, E_CAPACITY, E_TIMEOUT, E_UNSUPPORTED = \
+    -1, -2, -3, -4, -5, -6, -7
+MOTION_VALID, MOTION_PROJ_FAIL, MOTION_COLLISION = 0, 1, 2
+MAX_DOF, MAX_W, MAX_SPHERES = 8, 64, 256
+
+JOINT_DT = np.dtype([("type", "<i4"), ("d", "<f8"), ("a", "<f8"), ("alpha", "<f8"),
+                     ("theta0", "<f8"), ("lo", "<f8"), ("hi", "<f8")], align=True)
+SPHERE_DT = np.dtype([("frame", "<i4"), ("x", "<f8"), ("y", "<f8"), ("z", "<f8"),
+                      ("r", "<f8")], align=True)
+OBS_SPHERE_DT = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("r", "<f8")], align=True)
+OBS_BOX_DT = np.dtype([("c", "<f8", 3), ("h", "<f8", 3), ("R", "<f8", 9)], align=True)
+OBS_CAPSULE_DT = np.dtype([("p0", "<f8", 3), ("p1", "<f8", 3), ("r", "<f8")], align=True)
+
+
+class cprrtc_constraint(C.Structure):
+    _fields_ = [("type", C.c_int), ("target", C.c_double), ("tol_task", C.c_double),
+                ("c_sm", C.c_double), ("tau_floor", C.c_double), ("tol_sm", C.c_double),
+                ("alpha", C.c_double), ("lambda_", C.c_double), ("max_iters", C.c_int)]
+
+
+class CprrtcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cprrtc error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "cprrtc_create": [C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
+    "cprrtc_destroy": [C.c_void_p],
+    "cprrtc_set_stream": [C.c_void_p, C.c_void_p],
+    "cprrtc_last_error": [C.c_void_p],
+    "cprrtc_set_robot": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p],
+    "cprrtc_set_obstacles": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                             C.c_int],
+    "cprrtc_set_constraint": [C.c_void_p, C.POINTER(cprrtc_constraint)],
+    "cprrtc_validate": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_project_configs": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                               C.c_void_p, C.c_void_p],
+    "cprrtc_set_timing": [C.c_void_p, C.c_int],
+    "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
+                           C.POINTER(C.c_longlong)],
+    "cprrtc_reset_timing": [C.c_void_p],
+}
+
+
+def header_symbols() -> list:
+    """Function names declared in include/cprrtc.h."""
+    import re
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cprrtc_\w+)\s*\(", text, re.M)))
+
+
+def lib():
+    """Loads libcprrtc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "paper_2505_06791_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_char_p if name == "cprrtc_last_error" else C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def joints_array(robot) -> np.ndarray:
+    a = np.zeros(robot.dof, JOINT_DT)
+    j = np.asarray(robot.joints, np.float64)
+    a["type"] = j[:, 0].astype(np.int32)
+    for i, f in enumerate(["d", "a", "alpha", "theta0", "lo", "hi"]):
+        a[f] = j[:, i + 1]
+    return a
+
+
+def spheres_array(robot) -> np.ndarray:
+    s = np.asarray(robot.spheres, np.float64)
+    a = np.zeros(len(s), SPHERE_DT)
+    a["frame"] = s[:, 0].astype(np.int32)
+    a["x"], a["y"], a["z"], a["r"] = s[:, 1], s[:, 2], s[:, 3], s[:, 4]
+    return a
+
+
+def scene_arrays(scene):
+    sph = np.zeros(len(scene.sph), OBS_SPHERE_DT)
+    if len(scene.sph):
+        s = np.asarray(scene.sph, np.float64)
+        sph["x"], sph["y"], sph["z"], sph["r"] = s[:, 0], s[:, 1], s[:, 2], s[:, 3]
+    box = np.zeros(len(scene.box), OBS_BOX_DT)
+    if len(scene.box):
+        b = np.asarray(scene.box, np.float64)
+        box["c"], box["h"], box["R"] = b[:, 0:3], b[:, 3:6], b[:, 6:15]
+    cap = np.zeros(len(scene.cap), OBS_CAPSULE_DT)
+    if len(scene.cap):
+        c = np.asarray(scene.cap, np.float64)
+        cap["p0"], cap["p1"], cap["r"] = c[:, 0:3], c[:, 3:6], c[:, 6]
+    return sph, box, cap
+
+
+def constraint_struct(c) -> cprrtc_constraint:
+    return cprrtc_constraint(c.type, c.target, c.tol_task, c.c_sm, c.tau_floor, c.tol_sm,
+                             c.alpha, c.lam, c.max_iters)
+
+
+class Context:
+    """One library context (device, stream, robot, obstacles, constraint)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._L = lib()
+        h = C.c_void_p()
+        rc = self._L.cprrtc_create(C.byref(h), device, stream)
+        if rc != OK:
+            raise CprrtcError(rc, "cprrtc_create failed")
+        self.h = h
+        self.dof = None
+
+    def _check(self, rc):
+        if rc != OK:
+            raise CprrtcError(rc, self._L.cprrtc_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._L.cprrtc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.cprrtc_set_stream(self.h, raw))
+
+    def set_robot(self, robot):
+        j = joints_array(robot)
+        s = spheres_array(robot)
+        ee = np.ascontiguousarray(robot.ee, np.float64)
+        self._check(self._L.cprrtc_set_robot(self.h, j.ctypes.data, robot.dof, s.ctypes.data,
+                                             len(s), ee.ctypes.data))
+        self.dof = robot.dof
+
+    def set_obstacles(self, scene):
+        sph, box, cap = scene_arrays(scene)
+        self._check(self._L.cprrtc_set_obstacles(
+            self.h, sph.ctypes.data if len(sph) else None, len(sph),
+            box.ctypes.data if len(box) else None, len(box),
+            cap.ctypes.data if len(cap) else None, len(cap)))
+
+    def set_constraint(self, c):
+        cs = constraint_struct(c)
+        self._check(self._L.cprrtc_set_constraint(self.h, C.byref(cs)))
+
+    def set_timing(self, on: bool):
+        self._check(self._L.cprrtc_set_timing(self.h, int(on)))
+
+    def kernel_time(self, name: str):
+        ms, n = C.c_double(), C.c_longlong()
+        self._check(self._L.cprrtc_kernel_time(self.h, name.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def reset_timing(self):
+        self._check(self._L.cprrtc_reset_timing(self.h))
+
+    def alloc_validate_outputs(self, n, W, like):
+        """Output buffers matching `like` (CUDA tensor -> CUDA tensors, else numpy)."""
+        dof = self.dof or int(like.shape[1])
+        if _is_cuda(like):
+            import torch
+            dev = like.device
+            return dict(q=torch.empty((n, W, dof), dtype=torch.float32, device=dev),
+                        status=torch.empty(n, dtype=torch.uint8, device=dev),
+                        first_fail=torch.empty(n, dtype=torch.int32, device=dev),
+                        iters=torch.empty(n, dtype=torch.uint8, device=dev),
+                        resid=torch.empty(n, dtype=torch.float32, device=dev))
+        return dict(q=np.empty((n, W, dof), np.float32), status=np.empty(n, np.uint8),
+                    first_fail=np.empty(n, np.int32), iters=np.empty(n, np.uint8),
+                    resid=np.empty(n, np.float32))
+
+    def validate(self, q_start, q_end, W: int, out=None, with_q: bool = True):
+        """cprrtc_validate on n motions. Returns the output dict."""
+        n = int(q_start.shape[0])
+        if out is None:
+            out = self.alloc_validate_outputs(n, W, q_start)
+        self._check(cprrtc_validate(self.h, q_start, q_end, n, W,
+                                    out["q"] if with_q else None, out["status"],
+                                    out["first_fail"], out["iters"], out["resid"]))
+        return out
+
+    def project_configs(self, q_in, max_iters: int, out=None):
+        n = int(q_in.shape[0])
+        if out is None:
+            if _is_cuda(q_in):
+                import torch
+                out = dict(q=torch.empty_like(q_in),
+                           ok=torch.empty(n, dtype=torch.uint8, device=q_in.device),
+                           resid=torch.empty(n, dtype=torch.float32, device=q_in.device))
+            else:
+                out = dict(q=np.empty_like(np.asarray(q_in, np.float32)),
+                           ok=np.empty(n, np.uint8), resid=np.empty(n, np.float32))
+        self._check(cprrtc_project_configs(self.h, q_in, n, max_iters, out["q"], out["ok"],
+                                           out["resid"]))
+        return out
+
+
+# ---- functions under the C names (pointer marshalling only) ----
+
+def cprrtc_validate(h, q_start, q_end, n, W, out_q, status, first_fail, iters, resid):
+    return lib().cprrtc_validate(h, _ptr(q_start), _ptr(q_end), n, W, _ptr(out_q),
+                                 _ptr(status), _ptr(first_fail), _ptr(iters), _ptr(resid))
+
+
+def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
+    return lib().cprrtc_project_configs(h, _ptr(q_in), n, max_iters, _ptr(q_out), _ptr(ok),
+                                        _ptr(resid))
+
+
+__all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
+           "cprrtc_project_configs"]

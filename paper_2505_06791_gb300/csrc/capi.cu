@@ -1,0 +1,493 @@
+// C-ABI layer: context lifecycle, robot / scene / constraint upload, pointer staging and
+// the exported entry points declared in include/cprrtc.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cprrtc.h"
+#include "launch.h"
+
+using namespace cprrtc;
+
+namespace {
+
+struct TimingRec {
+  std::string name;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct cprrtc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  DeviceInfo dev{};
+  bool has_robot = false;
+  RobotDev rb{};
+  float4* d_spheres = nullptr;
+  int* d_sframe = nullptr;
+  SceneDev sc{};
+  float4* d_obs = nullptr;
+  size_t obs_cap = 0;  // float4 slots
+  ConsDev cs{};
+  char* d_stage = nullptr;
+  size_t stage_cap = 0;
+  bool timing = false;
+  std::vector<TimingRec> pending;
+  std::map<std::string, std::pair<double, long long>> acc;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+int fail(cprrtc_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(cprrtc_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(ctx, e == cudaErrorMemoryAllocation ? CPRRTC_E_OOM : CPRRTC_E_CUDA, m);
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t take_event(cprrtc_ctx* ctx) {
+  if (!ctx->events.empty()) {
+    cudaEvent_t e = ctx->events.back();
+    ctx->events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with events when timing is enabled.
+struct LaunchTimer {
+  cprrtc_ctx* ctx;
+  TimingRec rec{};
+  bool on;
+  LaunchTimer(cprrtc_ctx* c, const char* name) : ctx(c), on(c->timing) {
+    if (!on) return;
+    rec.name = name;
+    rec.a = take_event(ctx);
+    rec.b = take_event(ctx);
+    cudaEventRecord(rec.a, ctx->stream);
+  }
+  void done() {
+    if (!on) return;
+    cudaEventRecord(rec.b, ctx->stream);
+    ctx->pending.push_back(rec);
+    on = false;
+  }
+};
+
+// Host <-> device staging of the array arguments of one call. Device pointers are used as
+// they are; host arrays get a slot in the context's staging buffer.
+struct Staging {
+  struct Item {
+    const void* host_in;
+    void* host_out;
+    size_t bytes;
+    size_t off;
+    void** dev;
+  };
+  std::vector<Item> items;
+  size_t total = 0;
+  bool any_host = false;
+
+  template <class T>
+  void input(const T* p, size_t bytes, const T** dev) {
+    if (!p || bytes == 0 || is_device_ptr(p)) {
+      *dev = p;
+      return;
+    }
+    any_host = true;
+    items.push_back({p, nullptr, bytes, total, reinterpret_cast<void**>(const_cast<T**>(dev))});
+    total += (bytes + 255) & ~size_t(255);
+  }
+  template <class T>
+  void output(T* p, size_t bytes, T** dev) {
+    if (!p || bytes == 0 || is_device_ptr(p)) {
+      *dev = p;
+      return;
+    }
+    any_host = true;
+    items.push_back({nullptr, p, bytes, total, reinterpret_cast<void**>(dev)});
+    total += (bytes + 255) & ~size_t(255);
+  }
+  // Allocates, assigns device pointers and uploads inputs.
+  int begin(cprrtc_ctx* ctx) {
+    if (total > ctx->stage_cap) {
+      const size_t cap = std::max(total, ctx->stage_cap * 2);
+      if (ctx->d_stage) cudaFree(ctx->d_stage);
+      ctx->d_stage = nullptr;
+      ctx->stage_cap = 0;
+      cudaError_t e = cudaMalloc(&ctx->d_stage, cap);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "staging allocation");
+      ctx->stage_cap = cap;
+    }
+    for (auto& it : items) {
+      *it.dev = ctx->d_stage + it.off;
+      if (it.host_in) {
+        cudaError_t e = cudaMemcpyAsync(ctx->d_stage + it.off, it.host_in, it.bytes,
+                                        cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "host-to-device copy");
+      }
+    }
+    return CPRRTC_OK;
+  }
+  // Downloads outputs and waits for them when any argument was host memory.
+  int end(cprrtc_ctx* ctx) {
+    for (auto& it : items) {
+      if (it.host_out) {
+        cudaError_t e = cudaMemcpyAsync(it.host_out, ctx->d_stage + it.off, it.bytes,
+                                        cudaMemcpyDeviceToHost, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "device-to-host copy");
+      }
+    }
+    if (any_host) {
+      cudaError_t e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    }
+    return CPRRTC_OK;
+  }
+};
+
+template <class T>
+int upload(cprrtc_ctx* ctx, T** dst, size_t* cap, const std::vector<T>& src) {
+  if (src.size() > *cap || !*dst) {
+    if (*dst) cudaFree(*dst);
+    *dst = nullptr;
+    *cap = 0;
+    size_t n = std::max<size_t>(src.size(), 1);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "device allocation");
+    *cap = n;
+  }
+  if (!src.empty()) {
+    cudaError_t e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "upload");
+  }
+  return CPRRTC_OK;
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+}  // namespace
+
+extern "C" {
+
+int cprrtc_create(cprrtc_ctx** out, int device, void* stream) {
+  if (!out) return CPRRTC_E_INVALID_ARG;
+  *out = nullptr;
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CPRRTC_E_CUDA;
+  }
+  if (device < 0 || device >= n_dev) return CPRRTC_E_INVALID_ARG;
+  cprrtc_ctx* ctx = new (std::nothrow) cprrtc_ctx();
+  if (!ctx) return CPRRTC_E_OOM;
+  ctx->device = device;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  DeviceGuard g(device);
+  int smem = 0;
+  if (cudaDeviceGetAttribute(&ctx->dev.sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return CPRRTC_E_CUDA;
+  }
+  ctx->dev.smem_optin = (size_t)smem;
+  ctx->cs = ConsDev{kConsNone, 0.f, 1e-4f, 2.f, 1e-3f, 1e-4f, 1.f, 1e-6f, 20};
+  ctx->sc = SceneDev{nullptr, 0, 0, 0};
+  *out = ctx;
+  return CPRRTC_OK;
+}
+
+int cprrtc_destroy(cprrtc_ctx* ctx) {
+  if (!ctx) return CPRRTC_OK;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(ctx->d_spheres);
+  cudaFree(ctx->d_sframe);
+  cudaFree(ctx->d_obs);
+  cudaFree(ctx->d_stage);
+  for (auto& r : ctx->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ctx->events) cudaEventDestroy(e);
+  delete ctx;
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_stream(cprrtc_ctx* ctx, void* stream) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  return CPRRTC_OK;
+}
+
+const char* cprrtc_last_error(const cprrtc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
+                     const cprrtc_sphere* spheres, int n_spheres, const double ee[3]) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!joints || !spheres || !ee) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_robot: null pointer");
+  if (dof < 1 || dof > CPRRTC_MAX_DOF)
+    return fail(ctx, dof < 1 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED, "set_robot: dof must be in [1, 8]");
+  if (n_spheres < 1 || n_spheres > CPRRTC_MAX_SPHERES)
+    return fail(ctx, n_spheres < 1 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED,
+                "set_robot: n_spheres must be in [1, 256]");
+  RobotDev rb{};
+  rb.dof = dof;
+  rb.n_spheres = n_spheres;
+  for (int k = 0; k < dof; ++k) {
+    const cprrtc_joint& j = joints[k];
+    if ((j.type != CPRRTC_JOINT_REVOLUTE && j.type != CPRRTC_JOINT_PRISMATIC) || !is_finite(j.d) ||
+        !is_finite(j.a) || !is_finite(j.alpha) || !is_finite(j.theta0) || !is_finite(j.lo) || !is_finite(j.hi) || j.lo > j.hi)
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "set_robot: bad joint " + std::to_string(k));
+    JointDev& d = rb.j[k];
+    d.ca = (float)std::cos(j.alpha);
+    d.sa = (float)std::sin(j.alpha);
+    d.a = (float)j.a;
+    d.d = (float)j.d;
+    d.theta0 = (float)j.theta0;
+    d.ct0 = (float)std::cos(j.theta0);
+    d.st0 = (float)std::sin(j.theta0);
+    d.lo = (float)j.lo;
+    d.hi = (float)j.hi;
+    d.prismatic = j.type == CPRRTC_JOINT_PRISMATIC;
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (!is_finite(ee[i])) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_robot: bad ee");
+    rb.ee[i] = (float)ee[i];
+  }
+  // spheres sorted by frame (stable): lanes of one frame read the same transform
+  std::vector<int> order(n_spheres);
+  for (int i = 0; i < n_spheres; ++i) {
+    const cprrtc_sphere& s = spheres[i];
+    if (s.frame < 0 || s.frame > dof || !is_finite(s.x) || !is_finite(s.y) || !is_finite(s.z) || !(s.r > 0) || !is_finite(s.r))
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "set_robot: bad sphere " + std::to_string(i));
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return spheres[a].frame < spheres[b].frame; });
+  std::vector<float4> loc(n_spheres);
+  std::vector<int> frm(n_spheres);
+  for (int i = 0; i < n_spheres; ++i) {
+    const cprrtc_sphere& s = spheres[order[i]];
+    loc[i] = make_float4((float)s.x, (float)s.y, (float)s.z, (float)s.r);
+    frm[i] = s.frame;
+  }
+  DeviceGuard g(ctx->device);
+  size_t cap1 = 0, cap2 = 0;
+  if (ctx->d_spheres) { cudaFree(ctx->d_spheres); ctx->d_spheres = nullptr; }
+  if (ctx->d_sframe) { cudaFree(ctx->d_sframe); ctx->d_sframe = nullptr; }
+  int rc = upload(ctx, &ctx->d_spheres, &cap1, loc);
+  if (rc) return rc;
+  rc = upload(ctx, &ctx->d_sframe, &cap2, frm);
+  if (rc) return rc;
+  rb.spheres = ctx->d_spheres;
+  rb.sphere_frame = ctx->d_sframe;
+  ctx->rb = rb;
+  ctx->has_robot = true;
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
+                         const cprrtc_obs_box* box, int n_box, const cprrtc_obs_capsule* cap,
+                         int n_cap) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (n_sph < 0 || n_box < 0 || n_cap < 0 || (n_sph && !sph) || (n_box && !box) || (n_cap && !cap))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad counts or null pointer");
+  if ((long long)n_sph + 4LL * n_box + 2LL * n_cap > (1LL << 26))
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, "set_obstacles: too many obstacles");
+  std::vector<float4> v;
+  v.reserve((size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
+  for (int i = 0; i < n_sph; ++i) {
+    const cprrtc_obs_sphere& o = sph[i];
+    if (!is_finite(o.x) || !is_finite(o.y) || !is_finite(o.z) || !is_finite(o.r) || o.r < 0)
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad sphere " + std::to_string(i));
+    v.push_back(make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r));
+  }
+  for (int i = 0; i < n_box; ++i) {
+    const cprrtc_obs_box& b = box[i];
+    for (int k = 0; k < 3; ++k)
+      if (!is_finite(b.c[k]) || !is_finite(b.h[k]) || b.h[k] < 0)
+        return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad box " + std::to_string(i));
+    for (int k = 0; k < 9; ++k)
+      if (!is_finite(b.R[k])) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad box rotation");
+    // columns of R are the box axes in world coordinates
+    v.push_back(make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]));
+    v.push_back(make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]));
+    v.push_back(make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]));
+    v.push_back(make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f));
+  }
+  for (int i = 0; i < n_cap; ++i) {
+    const cprrtc_obs_capsule& c = cap[i];
+    for (int k = 0; k < 3; ++k)
+      if (!is_finite(c.p0[k]) || !is_finite(c.p1[k]))
+        return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad capsule " + std::to_string(i));
+    if (!is_finite(c.r) || c.r < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad capsule radius");
+    const double u[3] = {c.p1[0] - c.p0[0], c.p1[1] - c.p0[1], c.p1[2] - c.p0[2]};
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    v.push_back(make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r));
+    v.push_back(make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f));
+  }
+  DeviceGuard g(ctx->device);
+  int rc = upload(ctx, &ctx->d_obs, &ctx->obs_cap, v);
+  if (rc) return rc;
+  ctx->sc = SceneDev{ctx->d_obs, n_sph, n_box, n_cap};
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_constraint(cprrtc_ctx* ctx, const cprrtc_constraint* c) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!c) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: null pointer");
+  if (c->type < CPRRTC_CONSTRAINT_NONE || c->type > CPRRTC_CONSTRAINT_Z_PLANE)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: unknown type");
+  if (c->max_iters < 1 || c->max_iters > 255)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: max_iters must be in [1, 255]");
+  if (!is_finite(c->target) || !(c->tol_task > 0) || !(c->tol_sm > 0) || !(c->c_sm > 0) ||
+      !(c->tau_floor >= 0) || !is_finite(c->alpha) || !(c->lambda >= 0) || !is_finite(c->lambda) ||
+      !is_finite(c->tol_task) || !is_finite(c->tol_sm) || !is_finite(c->c_sm) || !is_finite(c->tau_floor))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: bad parameter");
+  ctx->cs = ConsDev{c->type,          (float)c->target, (float)c->tol_task,
+                    (float)c->c_sm,   (float)c->tau_floor, (float)c->tol_sm,
+                    (float)c->alpha,  (float)(c->lambda * c->lambda), c->max_iters};
+  return CPRRTC_OK;
+}
+
+int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, int n, int W,
+                    float* out_q, uint8_t* status, int32_t* first_fail, uint8_t* iters,
+                    float* resid) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "validate: set_robot first");
+  if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "validate: n < 0");
+  if (W < 2 || W > CPRRTC_MAX_W)
+    return fail(ctx, W < 2 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED, "validate: W must be in [2, 64]");
+  if (n == 0) return CPRRTC_OK;
+  if (!q_start || !q_end || !status) return fail(ctx, CPRRTC_E_INVALID_ARG, "validate: null pointer");
+  DeviceGuard g(ctx->device);
+  const size_t dof = ctx->rb.dof, N = (size_t)n;
+  ValidateArgs a{};
+  a.n = n;
+  a.W = W;
+  a.cc_skip_first = 0;
+  Staging st;
+  st.input(q_start, N * dof * sizeof(float), &a.q_start);
+  st.input(q_end, N * dof * sizeof(float), &a.q_end);
+  st.output(out_q, N * W * dof * sizeof(float), &a.out_q);
+  st.output(status, N, &a.status);
+  st.output(first_fail, N * sizeof(int32_t), &a.first_fail);
+  st.output(iters, N, &a.iters);
+  st.output(resid, N * sizeof(float), &a.resid);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  LaunchTimer tm(ctx, "validate");
+  cudaError_t e = launch_validate(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "validate launch");
+  return st.end(ctx);
+}
+
+int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,
+                           float* q_out, uint8_t* ok, float* resid) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "project_configs: set_robot first");
+  if (ctx->cs.type == kConsNone)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "project_configs: constraint is NONE");
+  if (n < 0 || max_iters < 0 || max_iters > 100000)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "project_configs: bad n or max_iters");
+  if (n == 0) return CPRRTC_OK;
+  if (!q_in || !q_out) return fail(ctx, CPRRTC_E_INVALID_ARG, "project_configs: null pointer");
+  DeviceGuard g(ctx->device);
+  const size_t dof = ctx->rb.dof, N = (size_t)n;
+  const float* d_in;
+  float *d_out, *d_res;
+  uint8_t* d_ok;
+  Staging st;
+  st.input(q_in, N * dof * sizeof(float), &d_in);
+  st.output(q_out, N * dof * sizeof(float), &d_out);
+  st.output(ok, N, &d_ok);
+  st.output(resid, N * sizeof(float), &d_res);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  LaunchTimer tm(ctx, "project");
+  cudaError_t e = launch_project_configs(ctx->rb, ctx->cs, d_in, n, max_iters, d_out, d_ok, d_res, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "project launch");
+  return st.end(ctx);
+}
+
+int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  ctx->timing = enabled != 0;
+  return CPRRTC_OK;
+}
+
+int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches) {
+  if (!ctx || !name || !ms || !launches) return CPRRTC_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  for (auto& r : ctx->pending) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event synchronize");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed");
+    auto& slot = ctx->acc[r.name];
+    slot.first += t;
+    slot.second += 1;
+    ctx->events.push_back(r.a);
+    ctx->events.push_back(r.b);
+  }
+  ctx->pending.clear();
+  auto it = ctx->acc.find(name);
+  *ms = it == ctx->acc.end() ? 0.0 : it->second.first;
+  *launches = it == ctx->acc.end() ? 0 : it->second.second;
+  return CPRRTC_OK;
+}
+
+int cprrtc_reset_timing(cprrtc_ctx* ctx) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  double ms;
+  long long l;
+  cprrtc_kernel_time(ctx, "", &ms, &l);
+  ctx->acc.clear();
+  return CPRRTC_OK;
+}
+
+}  // extern "C"

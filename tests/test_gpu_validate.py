@@ -1,0 +1,180 @@
+"""GPU parity of cprrtc_validate / cprrtc_project_configs (through the C ABI) with the
+FP64 oracle on identical seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2505_06791_gb300 import synth as S
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_06791_gb300 import build
+    build.build()
+    return torch
+
+
+def make_ctx(robot, scene, constraint):
+    from paper_2505_06791_gb300.capi import Context
+    ctx = Context(0)
+    ctx.set_robot(robot)
+    ctx.set_obstacles(scene)
+    ctx.set_constraint(constraint)
+    return ctx
+
+
+def manifold_starts(orc, robot, n, seed):
+    out = []
+    for q in S.uniform_configs(robot, 3 * n + 20, seed):
+        ok, qp, _, _ = orc.project_config(q, max_iters=60)
+        if ok:
+            out.append(qp)
+        if len(out) == n:
+            break
+    assert len(out) == n
+    return S.f32(np.array(out))
+
+
+def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.9):
+    ctx = make_ctx(robot, scene, c)
+    dq0 = torch.from_numpy(q0.astype(np.float32)).cuda()
+    dq1 = torch.from_numpy(q1.astype(np.float32)).cuda()
+    out = ctx.validate(dq0, dq1, W)
+    torch.cuda.synchronize()
+    runs = parity.oracle_runs(oracle_mod.Oracle(robot, scene, c), c, q0, q1, W)
+    stats, bad = parity.compare(out, runs)
+    ctx.close()
+    assert not bad, (stats, bad[:10])
+    assert stats["exact"] >= min_exact * stats["n"], stats
+    return stats, out, runs[0]
+
+
+def test_config1_full_size_roll_pitch(torch_cuda, oracle_mod):
+    """7-DOF arm, 59 spheres, 16 obstacle spheres, 256 motions x 32 waypoints, roll/pitch."""
+    rb = S.make_arm7(1)
+    sc = S.make_scene(1001, n_sph=16)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 256, 1002)
+    q1 = S.uniform_configs(rb, 256, 1003)
+    stats, out, o = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32)
+    st = parity.to_np(out["status"])
+    assert set(np.unique(st)) <= {0, 1, 2}
+    print(stats, np.bincount(st, minlength=3))
+
+
+def test_short_motions_mixed_obstacles(torch_cuda, oracle_mod):
+    """Planner-like 0.3 rad motions among 100 spheres, 60 boxes, 40 capsules."""
+    rb = S.make_arm7(1)
+    sc = S.make_mixed_scene(2001)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 200, 2002)
+    q1 = S.nearby_configs(rb, q0, 0.3, 2003)
+    stats, out, o = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32)
+    print(stats, np.bincount(parity.to_np(out["status"]), minlength=3))
+
+
+@pytest.mark.parametrize("W", [2, 7, 31, 32, 33, 64])
+def test_no_constraint_collision_parity(torch_cuda, oracle_mod, W):
+    """Projection bypassed: interpolation + FK + CC on all three primitive kinds, with
+    ragged waypoint counts around the warp width."""
+    rb = S.make_arm7(2)
+    sc = S.make_mixed_scene(3001, 20, 12, 8)
+    c = S.no_constraint()
+    q0 = S.uniform_configs(rb, 150, 3002)
+    q1 = np.concatenate([S.nearby_configs(rb, q0[:75], 0.4, 3003), S.uniform_configs(rb, 75, 3004)])
+    stats, out, o = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, W, min_exact=0.95)
+    gq = parity.to_np(out["q"]).astype(np.float64)
+    assert np.abs(gq - o["q"]).max() < 1e-6
+    assert (parity.to_np(out["iters"]) == 0).all()
+
+
+def test_z_plane_eight_dof_long_segments(torch_cuda, oracle_mod):
+    """8-DOF arm on a prismatic torso, 120 spheres, z-plane constraint, W = 64 (two
+    waypoints per lane)."""
+    rb = S.make_arm8(3)
+    sc = S.make_scene(4001, n_sph=64, sph_r=(0.02, 0.02))
+    c = S.z_plane(0.9)
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 96, 4002)
+    q1 = np.concatenate([S.nearby_configs(rb, q0[:48], 0.5, 4003), S.uniform_configs(rb, 48, 4004)])
+    stats, out, o = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 64)
+    print(stats)
+
+
+def test_six_dof_arm_and_tiny_robot(torch_cuda, oracle_mod):
+    rb = S.make_arm6(4)
+    sc = S.make_mixed_scene(5001, 10, 5, 5)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 64, 5002)
+    q1 = S.nearby_configs(rb, q0, 0.3, 5003)
+    run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 16, min_exact=0.6)
+    one = S.Robot(rb.joints, rb.ee, rb.spheres[:1].copy())
+    run_case(torch_cuda, oracle_mod, one, sc, S.no_constraint(), q0, q1, 5, min_exact=0.9)
+
+
+def test_host_and_device_pointers_agree(torch_cuda, oracle_mod):
+    rb = S.make_arm7(1)
+    sc = S.make_mixed_scene(6001, 30, 10, 10)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 40, 6002)
+    q1 = S.nearby_configs(rb, q0, 0.3, 6003)
+    ctx = make_ctx(rb, sc, c)
+    host = ctx.validate(q0.astype(np.float32), q1.astype(np.float32), 32)
+    dev = ctx.validate(torch_cuda.from_numpy(q0.astype(np.float32)).cuda(),
+                       torch_cuda.from_numpy(q1.astype(np.float32)).cuda(), 32)
+    for k in host:
+        assert np.array_equal(host[k], parity.to_np(dev[k])), k
+    ctx.close()
+
+
+def test_edge_cases_and_errors(torch_cuda, oracle_mod):
+    from paper_2505_06791_gb300 import capi
+    rb = S.make_arm7(1)
+    ctx = capi.Context(0)
+    q = np.zeros((3, 7), np.float32)
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.validate(q, q, 32)
+    assert e.value.code == capi.E_NOT_CONFIGURED
+    ctx.set_robot(rb)
+    ctx.set_constraint(S.no_constraint())
+    out = ctx.validate(q[:0], q[:0], 32)                    # n = 0: no-op
+    assert len(out["status"]) == 0
+    out = ctx.validate(q, q, 8)                             # no obstacles at all
+    assert (out["status"] == 0).all() and (out["first_fail"] == -1).all()
+    for W, code in ((1, capi.E_INVALID_ARG), (65, capi.E_UNSUPPORTED)):
+        with pytest.raises(capi.CprrtcError) as e:
+            ctx.validate(q, q, W)
+        assert e.value.code == code
+    bad = S.Constraint(max_iters=0)
+    with pytest.raises(capi.CprrtcError):
+        ctx.set_constraint(bad)
+    ctx.close()
+
+
+def test_project_configs_parity(torch_cuda, oracle_mod):
+    rb = S.make_arm7(1)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, constraint=c)
+    q = S.uniform_configs(rb, 300, 7001)
+    ctx = make_ctx(rb, S.Scene(), c)
+    out = ctx.project_configs(torch_cuda.from_numpy(q.astype(np.float32)).cuda(), 60)
+    gq, gok = parity.to_np(out["q"]), parity.to_np(out["ok"])
+    agree = 0
+    for i in range(len(q)):
+        ok, qp, it, res = orc.project_config(q[i], max_iters=60)
+        if ok and gok[i]:
+            if np.abs(gq[i] - qp).max() < 1e-4:
+                agree += 1
+        elif ok == bool(gok[i]):
+            agree += 1
+    assert agree >= 0.95 * len(q)
+    ctx.close()
