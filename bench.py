@@ -150,6 +150,208 @@ def manifold_starts_gpu(ctx, rb, n, seed):
     return torch.cat(out)[:n].contiguous()
 
 
+PLAN_N = 1000
+PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=200, workers=8, max_nodes=2048,
+                   max_connect=32, max_path=512)
+
+
+def config2_scenes(n, seed=2):
+    """Config 2: per-problem scenes of 200 mixed obstacles (100 spheres, 60 oriented boxes,
+    40 capsules) in a 3 x 3 x 1.8 m workspace around the arm, base keep-out 0.35 m."""
+    return [S.make_planning_scene(2_000_000 + 10_007 * seed + p) for p in range(n)]
+
+
+def gpu_start_goal(rb, c, scenes, seed, device):
+    """Start/goal per problem: uniform configurations projected by the library, kept when
+    collision-free with every robot sphere inflated by 1 mm (library collision check)."""
+    import torch
+    from paper_2505_06791_gb300.capi import Context
+    proj = Context(device)
+    proj.set_robot(rb)
+    proj.set_constraint(c)
+    inflated = S.Robot(rb.joints, rb.ee, rb.spheres.copy())
+    inflated.spheres[:, 4] += 1e-3
+    chk = Context(device)
+    chk.set_robot(inflated)
+    chk.set_constraint(S.no_constraint())
+    starts, goals = [], []
+    for p, sc in enumerate(scenes):
+        chk.set_obstacles(sc)
+        found = []
+        k = 0
+        while len(found) < 2:
+            cand = torch.from_numpy(S.uniform_configs(rb, 64, seed * 1_000_003 + 977 * p + k)
+                                    .astype(np.float32)).cuda()
+            r = proj.project_configs(cand, 60)
+            qp = r["q"][r["ok"].bool()].contiguous()
+            if len(qp):
+                v = chk.validate(qp, qp, 2, with_q=False)
+                free = qp[v["status"] == 0]
+                found += [free[i] for i in range(min(2 - len(found), len(free)))]
+            k += 1
+            if k > 200:
+                raise RuntimeError(f"no collision-free start/goal for problem {p}")
+        starts.append(found[0])
+        goals.append(found[1])
+    proj.close()
+    chk.close()
+    return torch.stack(starts).contiguous(), torch.stack(goals).contiguous()
+
+
+def plan_flops(dof, scenes, n_spheres, work):
+    work = np.asarray(work, dtype=np.float64)
+    f_iter = flops_waypoint_iter(dof)
+    f_cc = np.array([flops_cc_waypoint(n_spheres, len(sc.sph), len(sc.box), len(sc.cap))
+                     for sc in scenes])
+    return float((work[:, 0] * f_iter + work[:, 1] * f_cc).sum())
+
+
+def run_plan(args, world, rank, local):
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rb, c = S.make_arm7(1), S.roll_pitch(20)
+    n = args.problems
+    # each rank plans its own seeded problems (weak scaling, no collective)
+    seed = 2 + 1000 * rank
+    scenes = config2_scenes(n, seed)
+    start, goal = gpu_start_goal(rb, c, scenes, seed, local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_constraint(c)
+    ctx.set_scene_batch(scenes)
+    prm = ctx.plan_params(seed=seed, **PLAN_PARAMS)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        out = ctx.alloc_plan_outputs(n, prm, start, edges=False)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            ctx.plan(start, goal, prm, out=out)
+        stream.synchronize()
+        ctx.set_timing(True)
+        ctx.reset_timing()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        for k in range(args.steps):
+            flush.fill_(float(k))            # evict L2 between steps (write > L2 size)
+            starts[k].record(stream)
+            ctx.plan(start, goal, prm, out=out)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
+        kms, launches = ctx.kernel_time("plan")
+        ctx.set_timing(False)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    L = out["path_len"].cpu().numpy()
+    wp = out["waypoints"].cpu().numpy()
+    ms = out["plan_ms"].cpu().numpy()
+    work = out["work"].cpu().numpy()
+    rounds = out["rounds"].cpu().numpy()
+    waypoints_step = int(wp.sum())
+    value = waypoints_step * args.steps * world / (total_ms / 1e3)
+    flops = plan_flops(rb.dof, scenes, len(rb.spheres), work)
+
+    # end to end through the C ABI with pinned host buffers
+    h_start = start.cpu().pin_memory()
+    h_goal = goal.cpu().pin_memory()
+    h_out = {k: (torch.empty(v.shape, dtype=v.dtype).pin_memory() if v is not None else None)
+             for k, v in out.items()}
+    ctx.plan(h_start, h_goal, prm, out=h_out)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        ctx.plan(h_start, h_goal, prm, out=h_out)
+    e2e_s = time.perf_counter() - t0
+    h2d = 2 * n * rb.dof * 4
+    d2h = sum(v.numel() * v.element_size() for v in h_out.values() if v is not None)
+    e2e = {"value": waypoints_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    avg_kernel_s = kms / 1e3 / max(launches, 1)
+    achieved = flops / avg_kernel_s / 1e12
+    solved = L > 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "config 2: RRT-Connect planner, plain form", "problems": n,
+                   "dof": rb.dof, "robot_spheres": len(rb.spheres),
+                   "obstacles_per_problem": {"spheres": 100, "boxes": 60, "capsules": 40},
+                   "constraint": "roll-pitch", "range": PLAN_PARAMS["range_"],
+                   "W": PLAN_PARAMS["W"], "max_rounds": PLAN_PARAMS["max_rounds"],
+                   "workers_per_problem": PLAN_PARAMS["workers"],
+                   "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
+        "p95_plan_ms": float(np.percentile(ms[solved], 95)) if solved.any() else None,
+        "p50_plan_ms_all": float(np.percentile(ms, 50)),
+        "success_rate": float(solved.mean()),
+        "waypoints_per_step": waypoints_step,
+        "mean_rounds": float(rounds.mean()),
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "plan_kernel",
+                     "flop_per_launch": flops, "avg_launch_ms": avg_kernel_s * 1e3,
+                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
+                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    inputs = (rb, c, scenes, start.cpu().numpy(), goal.cpu().numpy(), seed)
+    return line, inputs
+
+
+def oracle_plan_sample(rb, c, scenes, start, goal, seed, budget_s, threads):
+    """Oracle planner over the first problems of the workload, one problem per host thread,
+    until the time budget is spent. Returns (waypoints/s, per-problem ms, #problems)."""
+    import concurrent.futures as cf
+    import oracle
+
+    def one(p):
+        orc = oracle.Oracle(rb, scenes[p], c)
+        t = time.perf_counter()
+        r = orc.plan(start[p:p + 1], goal[p:p + 1], range_=PLAN_PARAMS["range_"],
+                     W=PLAN_PARAMS["W"], max_rounds=PLAN_PARAMS["max_rounds"],
+                     n_workers=PLAN_PARAMS["workers"], max_nodes=PLAN_PARAMS["max_nodes"],
+                     max_connect=PLAN_PARAMS["max_connect"], seed=seed,
+                     max_path=PLAN_PARAMS["max_path"])
+        return (time.perf_counter() - t) * 1e3, int(r["waypoints"][0]), int(r["path_len"][0] > 0)
+
+    t0 = time.perf_counter()
+    res = []
+    p = 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        while p < len(scenes) and time.perf_counter() - t0 < budget_s:
+            batch = list(range(p, min(p + threads, len(scenes))))
+            res += list(ex.map(one, batch))
+            p += len(batch)
+    el = time.perf_counter() - t0
+    wp = sum(r[1] for r in res)
+    return wp / el, [r[0] for r in res], len(res), sum(r[2] for r in res), el
+
+
+def cpu_baseline_plan(inputs, budget_s):
+    rb, c, scenes, start, goal, seed = inputs
+    cores = os.cpu_count() or 1
+    v, ms, n, solved, el = oracle_plan_sample(rb, c, scenes, start, goal, seed, budget_s, cores)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of the {len(scenes)} problems, one per thread ({el:.1f} s); "
+                      f"solved {solved}, p50 plan {np.percentile(ms, 50):.0f} ms per problem"}
+
+
 def init_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,6 +498,56 @@ def cpu_baseline_validate(inputs, budget_s=10.0):
                       f"({el:.1f} s, {cores} threads)"}
 
 
+def reference_arm_plan(args, world, rank):
+    """The oracle arm on the planner workload: the FP64 oracle's RRT-Connect on the same
+    seeded problems (start/goal chosen by the oracle), a bounded sample per step."""
+    if rank != 0:
+        return None
+    import oracle
+    rb, c = S.make_arm7(1), S.roll_pitch(20)
+    seed = 2
+    cores = os.cpu_count() or 1
+    n = cores
+    scenes = config2_scenes(n, seed)
+    starts, goals = [], []
+    for p, sc in enumerate(scenes):
+        orc = oracle.Oracle(rb, sc, c)
+        found = []
+        k = 0
+        while len(found) < 2:
+            for q in S.uniform_configs(rb, 64, seed * 1_000_003 + 977 * p + k):
+                ok, qp, _, _ = orc.project_config(q, max_iters=60)
+                if ok and orc.config_clearance(qp) > 1e-3:
+                    found.append(qp)
+                if len(found) == 2:
+                    break
+            k += 1
+        starts.append(found[0])
+        goals.append(found[1])
+    start, goal = S.f32(np.array(starts)), S.f32(np.array(goals))
+    budget = max(2.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_plan_sample(rb, c, scenes, start, goal, seed, budget, cores)
+    tot_wp, tot_s, ms_all = 0.0, 0.0, []
+    for _ in range(args.steps):
+        v, ms, n_done, solved, el = oracle_plan_sample(rb, c, scenes, start, goal, seed, budget, cores)
+        tot_wp += v * el
+        tot_s += el
+        ms_all += ms
+    value = tot_wp / tot_s
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "config 2: RRT-Connect planner, plain form",
+                       "problems": n, "dof": rb.dof, "parallelism": "host threads"},
+            "p50_plan_ms": float(np.percentile(ms_all, 50)),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} problems per step, one per thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
 def reference_arm(args, world, rank):
     """The oracle arm: the FP64 CPU oracle as it stands, on the same workload and metric."""
     if rank != 0:
@@ -335,22 +587,29 @@ def reference_arm(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="validate", choices=["validate"])
-    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--workload", default="plan", choices=["plan", "validate"])
+    ap.add_argument("--problems", type=int, default=PLAN_N)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     world, rank, local = init_dist()
     if args.impl == "reference":
-        line = reference_arm(args, world, rank)
+        fn = reference_arm_plan if args.workload == "plan" else reference_arm
+        line = fn(args, world, rank)
         if line is not None:
             print(json.dumps(line), flush=True)
         return
-    line, inputs = run_validate(args, world, rank, local)
+    if args.workload == "plan":
+        line, inputs = run_plan(args, world, rank, local)
+        baseline = cpu_baseline_plan
+    else:
+        line, inputs = run_validate(args, world, rank, local)
+        baseline = cpu_baseline_validate
     if rank == 0:
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline_validate(inputs, args.cpu_budget)
+            line["cpu_baseline"] = baseline(inputs, args.cpu_budget)
         print(json.dumps(line), flush=True)
 
 

@@ -173,6 +173,66 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
 int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,
                            float* q_out, uint8_t* ok, float* resid);
 
+/* ---- planning (Sec. III: RRT-Connect tree extension with constrained motions) ---- */
+
+/* Per-problem obstacle sets for cprrtc_plan with use_scene_batch = 1: problem p uses
+ * scene p. Scene s owns spheres [sphere_offsets[s], sphere_offsets[s+1]) of `spheres`, and
+ * likewise boxes and capsules; each offsets array has n_scenes + 1 non-decreasing entries
+ * starting at 0 (host pointers). Errors: E_INVALID_ARG, E_CUDA, E_OOM. */
+int cprrtc_set_scene_batch(cprrtc_ctx* ctx, int n_scenes, const cprrtc_obs_sphere* spheres,
+                           const int32_t* sphere_offsets, const cprrtc_obs_box* boxes,
+                           const int32_t* box_offsets, const cprrtc_obs_capsule* capsules,
+                           const int32_t* capsule_offsets);
+
+/* RRT-Connect parameters. Each round, `workers` extensions run in parallel against the
+ * trees as they stood at the round's start; worker w extends tree (round + w) mod 2 toward
+ * a Philox4x32-10 sample (counter {problem, round, w, draw}, key {seed, 0}), then greedily
+ * extends the same tree toward the nearest node of the other tree while each projected
+ * motion is valid and ends strictly closer (Sec. III). The trees connect when the closing
+ * hop (within 10 * tau_floor in inf-norm) is valid without projection. New nodes are
+ * appended in worker order; the lowest worker that connects wins. Deterministic for a
+ * seed. */
+typedef struct {
+  double range;        /* steering step, L2 in joint space; default 0.3 */
+  int W;               /* waypoints per motion, 2..64; default 32 */
+  int max_rounds;      /* rounds per problem (>= 1); default 200 */
+  int workers;         /* extensions per round = warps per problem, 1..16; default 8 */
+  int max_nodes;       /* capacity of each tree (>= 2); default 2048 */
+  int max_connect;     /* greedy connect steps per extension (>= 0); default 32 */
+  int max_path;        /* capacity of the path outputs, in nodes (>= 2); default 512 */
+  uint32_t seed;
+  int use_scene_batch; /* 1: problem p uses scene p of cprrtc_set_scene_batch; 0: the
+                          cprrtc_set_obstacles scene for every problem */
+} cprrtc_plan_params;
+
+/* Plans n problems start[p] -> goal[p] ([n][dof], on the constraint manifold and
+ * collision-free for a meaningful result). Outputs (path_len required, the rest may be
+ * NULL):
+ *   path_len   [n] nodes in the path (0: not solved in max_rounds; -needed if the path
+ *              did not fit in max_path);
+ *   path       [n][max_path][dof] nodes from start to goal;
+ *   path_edges [n][max_path-1][W][dof] the validated (projected) motion between path
+ *              nodes j and j+1, waypoint 0 at node j;
+ *   rounds     [n] rounds run; waypoints [n] waypoints validated (W per motion checked);
+ *   plan_ms    [n] device time of the problem's CTA, ms;
+ *   work       [n][2] work evaluated: Alg. 1 waypoint updates (iterations x (W-1) summed
+ *              over motions) and waypoints collision-checked (early exit included).
+ * The library keeps the trees in its own device memory (about
+ * n * 2 * max_nodes * (W * dof + 9) * 4 bytes). Requires set_robot, and set_obstacles or
+ * set_scene_batch (n_scenes = n). Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_UNSUPPORTED,
+ * E_CUDA, E_OOM. */
+int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
+                const cprrtc_plan_params* params, int32_t* path_len, float* path,
+                float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
+                int64_t* work);
+
+/* ---- counter-based random numbers ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11) of n counters [n][4] under key {key0, key1}, on the
+ * device: out [n][4]. The generator the planner samples with. */
+int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t* counters,
+                  int n, uint32_t* out);
+
 /* ---- timing ---- */
 
 /* When enabled, the library records CUDA events around each launch of its kernels on the

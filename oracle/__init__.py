@@ -220,6 +220,14 @@ class Oracle:
         return dict(q=out_q, status=ints[0], first_fail=ints[1], iters=ints[2], resid=dbl[0],
                     proj_margin=dbl[1], cc_margin=dbl[2])
 
+    def check_segment(self, xi, tau):
+        """(max task error, max step excess over tau, min clearance) of a given segment."""
+        xi = _d(xi)
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        lib().orc_check_segment(C.byref(self.rb), C.byref(self.sc), C.byref(self.c), _p(xi),
+                                xi.shape[0], C.c_double(tau), C.byref(a), C.byref(b), C.byref(c))
+        return a.value, b.value, c.value
+
     # ---- planner ----
     def plan(self, start, goal, range_=0.3, W=32, max_rounds=200, n_workers=8,
              max_nodes=4096, max_connect=64, seed=1, max_path=512, n_threads=1):

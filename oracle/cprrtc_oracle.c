@@ -563,8 +563,8 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  *   - greedy connect: target = nearest node of tree b to q_end; repeat: if
  *     ||cur - target||_inf <= tau_floor * 10 (the connect radius), the closing hop
  *     cur -> target must be valid as it stands (Alg. 1 with one iteration, then CC) and the
- *     trees are connected; otherwise steer cur toward target, validate, and keep the new
- *     end only if it is valid and strictly closer (L2) to target.
+ *     trees are connected; otherwise, at most max_connect times, steer cur toward target,
+ *     validate, and keep the new end only if it is valid and strictly closer (L2).
  * ======================================================================================== */
 
 typedef struct {
@@ -685,7 +685,8 @@ static int plan_one(const plan_env* env, const double* start, const double* goal
       /* greedy connect toward the nearest node of the other tree */
       int target = nearest(&T[b], count0[b], q_e, n);
       const double* tq = T[b].nodes + target * n;
-      for (int step = 0; step < pp->max_connect; ++step) {
+      int steps = 0;
+      for (;;) {
         const double* cur = P + (pend_count[w] - 1) * n;
         double gap = 0.0;
         for (int k = 0; k < n; ++k) gap = fmax(gap, fabs(cur[k] - tq[k]));
@@ -696,6 +697,8 @@ static int plan_one(const plan_env* env, const double* start, const double* goal
           }
           break;
         }
+        if (steps >= pp->max_connect) break;
+        ++steps;
         steer(cur, tq, pp->range, n, q_s);
         if (!motion_ok(env, env->c, cur, q_s, q_e, xi, centres, &wp)) break;
         if (!(dist2(q_e, tq, n) < dist2(cur, tq, n))) break;
@@ -819,4 +822,30 @@ int orc_plan(const orc_robot* rb, const orc_scene* sc, const orc_constraint* c,
   int solved = 0;
   for (int p = 0; p < n_problems; ++p) solved += path_len[p] > 0;
   return solved;
+}
+
+/* ========================================================================================
+ * Checks of a given waypoint sequence (used to re-validate planner output): the largest
+ * ||E_task||_inf over waypoints 1..W-1, the largest per-joint step excess
+ * max_k |xi_k[i] - xi_k[i-1]| - tau, and the smallest clearance over waypoints.
+ * ======================================================================================== */
+void orc_check_segment(const orc_robot* rb, const orc_scene* sc, const orc_constraint* c,
+                       const double* xi, int W, double tau, double* max_task,
+                       double* max_step_excess, double* min_clearance) {
+  const int n = rb->dof;
+  double* centres = (double*)malloc(sizeof(double) * 3 * (rb->n_spheres + 1));
+  double mt = 0.0, ms = -INFINITY, mc = INFINITY;
+  for (int i = 0; i < W; ++i) {
+    if (i > 0) {
+      double e[6], Jt[6 * ORC_MAX_DOF];
+      int m = orc_task(rb, c, xi + i * n, e, Jt);
+      mt = fmax(mt, norm_inf(e, m));
+      for (int k = 0; k < n; ++k) ms = fmax(ms, fabs(xi[i * n + k] - xi[(i - 1) * n + k]) - tau);
+    }
+    mc = fmin(mc, config_clearance(rb, sc, xi + i * n, centres));
+  }
+  free(centres);
+  *max_task = mt;
+  *max_step_excess = ms;
+  *min_clearance = mc;
 }

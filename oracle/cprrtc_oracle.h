@@ -122,6 +122,12 @@ int orc_validate(const orc_robot* rb, const orc_scene* sc, const orc_constraint*
                  int n_threads, double* out_q, int* status, int* first_fail, int* iters,
                  double* resid, double* proj_margin, double* cc_margin);
 
+/* Re-validation of a given segment xi[W][dof]: largest task error (waypoints 1..W-1),
+ * largest step excess over tau, smallest clearance (all waypoints). */
+void orc_check_segment(const orc_robot* rb, const orc_scene* sc, const orc_constraint* c,
+                       const double* xi, int W, double tau, double* max_task,
+                       double* max_step_excess, double* min_clearance);
+
 /* ---- counter-based RNG ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -40,6 +40,12 @@ class cprrtc_constraint(C.Structure):
                 ("alpha", C.c_double), ("lambda_", C.c_double), ("max_iters", C.c_int)]
 
 
+class cprrtc_plan_params(C.Structure):
+    _fields_ = [("range", C.c_double), ("W", C.c_int), ("max_rounds", C.c_int),
+                ("workers", C.c_int), ("max_nodes", C.c_int), ("max_connect", C.c_int),
+                ("max_path", C.c_int), ("seed", C.c_uint32), ("use_scene_batch", C.c_int)]
+
+
 class CprrtcError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"cprrtc error {code}: {msg}")
@@ -62,6 +68,12 @@ _SIGS = {
                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_project_configs": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                C.c_void_p, C.c_void_p],
+    "cprrtc_set_scene_batch": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_plan": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                    C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
     "cprrtc_set_timing": [C.c_void_p, C.c_int],
     "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
                            C.POINTER(C.c_longlong)],
@@ -244,6 +256,61 @@ class Context:
                                     out["first_fail"], out["iters"], out["resid"]))
         return out
 
+    def set_scene_batch(self, scenes):
+        """One obstacle set per planning problem (problem p uses scenes[p])."""
+        parts = [scene_arrays(sc) for sc in scenes]
+        arrs, offs = [], []
+        for t, dt in enumerate((OBS_SPHERE_DT, OBS_BOX_DT, OBS_CAPSULE_DT)):
+            counts = [len(pt[t]) for pt in parts]
+            offs.append(np.concatenate([[0], np.cumsum(counts)]).astype(np.int32))
+            a = np.concatenate([pt[t] for pt in parts]) if sum(counts) else np.zeros(1, dt)
+            arrs.append(np.ascontiguousarray(a))
+        self._check(self._L.cprrtc_set_scene_batch(
+            self.h, len(scenes), arrs[0].ctypes.data, offs[0].ctypes.data, arrs[1].ctypes.data,
+            offs[1].ctypes.data, arrs[2].ctypes.data, offs[2].ctypes.data))
+
+    @staticmethod
+    def plan_params(range_=0.3, W=32, max_rounds=200, workers=8, max_nodes=2048,
+                    max_connect=32, max_path=512, seed=1, use_scene_batch=True):
+        return cprrtc_plan_params(range_, W, max_rounds, workers, max_nodes, max_connect,
+                                  max_path, seed, int(use_scene_batch))
+
+    def alloc_plan_outputs(self, n, params, like, edges=True):
+        dof, W, mp = self.dof, params.W, params.max_path
+        if _is_cuda(like):
+            import torch
+            d = like.device
+            out = dict(path_len=torch.empty(n, dtype=torch.int32, device=d),
+                       path=torch.empty((n, mp, dof), dtype=torch.float32, device=d),
+                       rounds=torch.empty(n, dtype=torch.int32, device=d),
+                       waypoints=torch.empty(n, dtype=torch.int64, device=d),
+                       plan_ms=torch.empty(n, dtype=torch.float32, device=d),
+                       work=torch.empty((n, 2), dtype=torch.int64, device=d))
+            out["path_edges"] = torch.empty((n, mp - 1, W, dof), dtype=torch.float32,
+                                            device=d) if edges else None
+            return out
+        out = dict(path_len=np.empty(n, np.int32), path=np.empty((n, mp, dof), np.float32),
+                   rounds=np.empty(n, np.int32), waypoints=np.empty(n, np.int64),
+                   plan_ms=np.empty(n, np.float32), work=np.empty((n, 2), np.int64))
+        out["path_edges"] = np.empty((n, mp - 1, W, dof), np.float32) if edges else None
+        return out
+
+    def plan(self, start, goal, params, out=None, edges=True):
+        """cprrtc_plan on n problems; returns the output dict."""
+        n = int(start.shape[0])
+        if out is None:
+            out = self.alloc_plan_outputs(n, params, start, edges)
+        self._check(cprrtc_plan(self.h, start, goal, n, params, out["path_len"], out["path"],
+                                out.get("path_edges"), out.get("rounds"), out.get("waypoints"),
+                                out.get("plan_ms"), out.get("work")))
+        return out
+
+    def philox(self, key0, key1, counters):
+        c = np.ascontiguousarray(counters, dtype=np.uint32)
+        out = np.empty_like(c)
+        self._check(cprrtc_philox(self.h, key0, key1, c, len(c), out))
+        return out
+
     def project_configs(self, q_in, max_iters: int, out=None):
         n = int(q_in.shape[0])
         if out is None:
@@ -262,6 +329,17 @@ class Context:
 
 # ---- functions under the C names (pointer marshalling only) ----
 
+def cprrtc_plan(h, start, goal, n, params, path_len, path, path_edges, rounds, waypoints,
+                plan_ms, work):
+    return lib().cprrtc_plan(h, _ptr(start), _ptr(goal), n, C.byref(params), _ptr(path_len),
+                             _ptr(path), _ptr(path_edges), _ptr(rounds), _ptr(waypoints),
+                             _ptr(plan_ms), _ptr(work))
+
+
+def cprrtc_philox(h, key0, key1, counters, n, out):
+    return lib().cprrtc_philox(h, key0, key1, _ptr(counters), n, _ptr(out))
+
+
 def cprrtc_validate(h, q_start, q_end, n, W, out_q, status, first_fail, iters, resid):
     return lib().cprrtc_validate(h, _ptr(q_start), _ptr(q_end), n, W, _ptr(out_q),
                                  _ptr(status), _ptr(first_fail), _ptr(iters), _ptr(resid))
@@ -273,4 +351,4 @@ def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
 
 
 __all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
-           "cprrtc_project_configs"]
+           "cprrtc_project_configs", "cprrtc_plan", "cprrtc_philox"]

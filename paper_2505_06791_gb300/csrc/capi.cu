@@ -37,6 +37,16 @@ struct cprrtc_ctx {
   ConsDev cs{};
   char* d_stage = nullptr;
   size_t stage_cap = 0;
+  // scene batch for planning
+  float4* d_batch_obs = nullptr;
+  size_t batch_obs_cap = 0;
+  int4* d_batch_tab = nullptr;
+  size_t batch_tab_cap = 0;
+  int n_scenes = 0;
+  int max_scene_f4 = 0;
+  // planner trees and per-worker pending buffers
+  char* d_plan = nullptr;
+  size_t plan_cap = 0;
   bool timing = false;
   std::vector<TimingRec> pending;
   std::map<std::string, std::pair<double, long long>> acc;
@@ -203,6 +213,44 @@ int upload(cprrtc_ctx* ctx, T** dst, size_t* cap, const std::vector<T>& src) {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
+// Packs obstacles into the float4 stream the kernels read: spheres {x,y,z,r}; boxes
+// {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0}; capsules {p0, r} {p1 - p0, 1/|p1-p0|^2}.
+int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
+                   const cprrtc_obs_box* box, int n_box, const cprrtc_obs_capsule* cap, int n_cap,
+                   std::vector<float4>& v) {
+  v.reserve(v.size() + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
+  for (int i = 0; i < n_sph; ++i) {
+    const cprrtc_obs_sphere& o = sph[i];
+    if (!is_finite(o.x) || !is_finite(o.y) || !is_finite(o.z) || !is_finite(o.r) || o.r < 0)
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad sphere " + std::to_string(i));
+    v.push_back(make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r));
+  }
+  for (int i = 0; i < n_box; ++i) {
+    const cprrtc_obs_box& b = box[i];
+    for (int k = 0; k < 3; ++k)
+      if (!is_finite(b.c[k]) || !is_finite(b.h[k]) || b.h[k] < 0)
+        return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box " + std::to_string(i));
+    for (int k = 0; k < 9; ++k)
+      if (!is_finite(b.R[k])) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box rotation");
+    v.push_back(make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]));
+    v.push_back(make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]));
+    v.push_back(make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]));
+    v.push_back(make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f));
+  }
+  for (int i = 0; i < n_cap; ++i) {
+    const cprrtc_obs_capsule& c = cap[i];
+    for (int k = 0; k < 3; ++k)
+      if (!is_finite(c.p0[k]) || !is_finite(c.p1[k]))
+        return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad capsule " + std::to_string(i));
+    if (!is_finite(c.r) || c.r < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad capsule radius");
+    const double u[3] = {c.p1[0] - c.p0[0], c.p1[1] - c.p0[1], c.p1[2] - c.p0[2]};
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    v.push_back(make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r));
+    v.push_back(make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f));
+  }
+  return CPRRTC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -245,6 +293,9 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_sframe);
   cudaFree(ctx->d_obs);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_batch_obs);
+  cudaFree(ctx->d_batch_tab);
+  cudaFree(ctx->d_plan);
   for (auto& r : ctx->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -336,41 +387,53 @@ int cprrtc_set_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sp
   if ((long long)n_sph + 4LL * n_box + 2LL * n_cap > (1LL << 26))
     return fail(ctx, CPRRTC_E_UNSUPPORTED, "set_obstacles: too many obstacles");
   std::vector<float4> v;
-  v.reserve((size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
-  for (int i = 0; i < n_sph; ++i) {
-    const cprrtc_obs_sphere& o = sph[i];
-    if (!is_finite(o.x) || !is_finite(o.y) || !is_finite(o.z) || !is_finite(o.r) || o.r < 0)
-      return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad sphere " + std::to_string(i));
-    v.push_back(make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r));
-  }
-  for (int i = 0; i < n_box; ++i) {
-    const cprrtc_obs_box& b = box[i];
-    for (int k = 0; k < 3; ++k)
-      if (!is_finite(b.c[k]) || !is_finite(b.h[k]) || b.h[k] < 0)
-        return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad box " + std::to_string(i));
-    for (int k = 0; k < 9; ++k)
-      if (!is_finite(b.R[k])) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad box rotation");
-    // columns of R are the box axes in world coordinates
-    v.push_back(make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]));
-    v.push_back(make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]));
-    v.push_back(make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]));
-    v.push_back(make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f));
-  }
-  for (int i = 0; i < n_cap; ++i) {
-    const cprrtc_obs_capsule& c = cap[i];
-    for (int k = 0; k < 3; ++k)
-      if (!is_finite(c.p0[k]) || !is_finite(c.p1[k]))
-        return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad capsule " + std::to_string(i));
-    if (!is_finite(c.r) || c.r < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad capsule radius");
-    const double u[3] = {c.p1[0] - c.p0[0], c.p1[1] - c.p0[1], c.p1[2] - c.p0[2]};
-    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    v.push_back(make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r));
-    v.push_back(make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f));
-  }
+  int rc = pack_obstacles(ctx, sph, n_sph, box, n_box, cap, n_cap, v);
+  if (rc) return rc;
   DeviceGuard g(ctx->device);
-  int rc = upload(ctx, &ctx->d_obs, &ctx->obs_cap, v);
+  rc = upload(ctx, &ctx->d_obs, &ctx->obs_cap, v);
   if (rc) return rc;
   ctx->sc = SceneDev{ctx->d_obs, n_sph, n_box, n_cap};
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_scene_batch(cprrtc_ctx* ctx, int n_scenes, const cprrtc_obs_sphere* sph,
+                           const int32_t* sph_off, const cprrtc_obs_box* box,
+                           const int32_t* box_off, const cprrtc_obs_capsule* cap,
+                           const int32_t* cap_off) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (n_scenes < 1 || !sph_off || !box_off || !cap_off)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_scene_batch: n_scenes < 1 or null offsets");
+  const int32_t* offs[3] = {sph_off, box_off, cap_off};
+  for (int t = 0; t < 3; ++t) {
+    if (offs[t][0] != 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_scene_batch: offsets must start at 0");
+    for (int i = 0; i < n_scenes; ++i)
+      if (offs[t][i + 1] < offs[t][i])
+        return fail(ctx, CPRRTC_E_INVALID_ARG, "set_scene_batch: offsets must not decrease");
+  }
+  if ((sph_off[n_scenes] && !sph) || (box_off[n_scenes] && !box) || (cap_off[n_scenes] && !cap))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_scene_batch: null obstacle array");
+  if ((long long)sph_off[n_scenes] + 4LL * box_off[n_scenes] + 2LL * cap_off[n_scenes] > (1LL << 28))
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, "set_scene_batch: too many obstacles");
+  std::vector<float4> all;
+  std::vector<int4> tab(n_scenes);
+  int max_f4 = 0;
+  for (int s_ = 0; s_ < n_scenes; ++s_) {
+    const int ns = sph_off[s_ + 1] - sph_off[s_], nb = box_off[s_ + 1] - box_off[s_],
+              nc = cap_off[s_ + 1] - cap_off[s_];
+    std::vector<float4> v;
+    int rc = pack_obstacles(ctx, sph + sph_off[s_], ns, box + box_off[s_], nb, cap + cap_off[s_], nc, v);
+    if (rc) return rc;
+    tab[s_] = make_int4((int)all.size(), ns, nb, nc);
+    max_f4 = std::max(max_f4, (int)v.size());
+    all.insert(all.end(), v.begin(), v.end());
+  }
+  DeviceGuard g(ctx->device);
+  int rc = upload(ctx, &ctx->d_batch_obs, &ctx->batch_obs_cap, all);
+  if (rc) return rc;
+  rc = upload(ctx, &ctx->d_batch_tab, &ctx->batch_tab_cap, tab);
+  if (rc) return rc;
+  ctx->n_scenes = n_scenes;
+  ctx->max_scene_f4 = max_f4;
   return CPRRTC_OK;
 }
 
@@ -450,6 +513,102 @@ int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_it
   cudaError_t e = launch_project_configs(ctx->rb, ctx->cs, d_in, n, max_iters, d_out, d_ok, d_res, ctx->stream);
   tm.done();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project launch");
+  return st.end(ctx);
+}
+
+int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
+                const cprrtc_plan_params* pp, int32_t* path_len, float* path, float* path_edges,
+                int32_t* rounds, int64_t* waypoints, float* plan_ms, int64_t* work) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan: set_robot first");
+  if (!pp) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: null params");
+  if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: n < 0");
+  if (pp->W < 2 || pp->W > CPRRTC_MAX_W || !(pp->range > 0) || !is_finite(pp->range) ||
+      pp->max_rounds < 1 || pp->workers < 1 || pp->workers > kMaxWorkers || pp->max_nodes < 2 ||
+      pp->max_connect < 0 || pp->max_path < 2)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: bad parameters");
+  if (pp->use_scene_batch && ctx->n_scenes != n)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan: scene batch must hold one scene per problem");
+  if (n == 0) return CPRRTC_OK;
+  if (!start || !goal || !path_len || !path) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: null pointer");
+  DeviceGuard g(ctx->device);
+  const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
+  const size_t B = (size_t)pp->workers, PC = (size_t)pp->max_connect + 2, MN = (size_t)pp->max_nodes;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_nodes = al(N * 2 * MN * 8 * sizeof(float));
+  const size_t b_parent = al(N * 2 * MN * sizeof(int));
+  const size_t b_edges = al(N * 2 * MN * W * dof * sizeof(float));
+  const size_t b_pend = al(N * B * PC * 8 * sizeof(float));
+  const size_t b_pedge = al(N * B * PC * W * dof * sizeof(float));
+  const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
+  if (need > ctx->plan_cap) {
+    if (ctx->d_plan) cudaFree(ctx->d_plan);
+    ctx->d_plan = nullptr;
+    ctx->plan_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_plan, need);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan: tree allocation");
+    ctx->plan_cap = need;
+  }
+  PlanArgs a{};
+  a.n = n;
+  a.range = (float)pp->range;
+  a.W = pp->W;
+  a.max_rounds = pp->max_rounds;
+  a.workers = pp->workers;
+  a.max_nodes = pp->max_nodes;
+  a.max_connect = pp->max_connect;
+  a.max_path = pp->max_path;
+  a.seed = pp->seed;
+  if (pp->use_scene_batch) {
+    a.scene_obs = ctx->d_batch_obs;
+    a.scenes = ctx->d_batch_tab;
+    a.max_scene_f4 = ctx->max_scene_f4;
+  } else {
+    a.scene_obs = nullptr;
+    a.scenes = nullptr;
+    a.max_scene_f4 = ctx->sc.n_float4();
+  }
+  char* base = ctx->d_plan;
+  a.nodes = reinterpret_cast<float*>(base);
+  a.parent = reinterpret_cast<int*>(base + b_nodes);
+  a.edges = reinterpret_cast<float*>(base + b_nodes + b_parent);
+  a.pend = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges);
+  a.pend_edges = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges + b_pend);
+  Staging st;
+  st.input(start, N * dof * sizeof(float), &a.start);
+  st.input(goal, N * dof * sizeof(float), &a.goal);
+  st.output(path_len, N * sizeof(int32_t), &a.path_len);
+  st.output(path, N * (size_t)pp->max_path * dof * sizeof(float), &a.path);
+  st.output(path_edges, N * (size_t)(pp->max_path - 1) * W * dof * sizeof(float), &a.path_edges);
+  st.output(rounds, N * sizeof(int32_t), &a.rounds);
+  st.output(reinterpret_cast<long long*>(waypoints), N * sizeof(int64_t), &a.waypoints);
+  st.output(plan_ms, N * sizeof(float), &a.plan_ms);
+  st.output(reinterpret_cast<long long*>(work), N * 2 * sizeof(int64_t), &a.work);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  LaunchTimer tm(ctx, "plan");
+  cudaError_t e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
+  return st.end(ctx);
+}
+
+int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t* counters, int n,
+                  uint32_t* out) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "philox: n < 0");
+  if (n == 0) return CPRRTC_OK;
+  if (!counters || !out) return fail(ctx, CPRRTC_E_INVALID_ARG, "philox: null pointer");
+  DeviceGuard g(ctx->device);
+  const uint32_t* d_in;
+  uint32_t* d_out;
+  Staging st;
+  st.input(counters, (size_t)n * 4 * sizeof(uint32_t), &d_in);
+  st.output(out, (size_t)n * 4 * sizeof(uint32_t), &d_out);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  cudaError_t e = launch_philox(key0, key1, d_in, n, d_out, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "philox launch");
   return st.end(ctx);
 }
 

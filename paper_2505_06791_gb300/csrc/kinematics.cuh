@@ -5,7 +5,11 @@
 // with the previous frame's axes x, y, z and origin p,
 //   u = x cos(theta) + y sin(theta),  v = y cos(theta) - x sin(theta),
 //   p' = p + a u + d z,  x' = u,  y' = v cos(alpha) + z sin(alpha),  z' = z cos(alpha) - v sin(alpha)
-// (about 24 FMA-class operations and one sincos per joint).
+// (48 FLOP and one sincos per joint).
+//
+// The constraint type is a template parameter: per-joint quantities the task Jacobian does
+// not read are dead code and take no registers. The Jacobian is not stored: its entries
+// are linear in the stored joint axes and are recomputed where the damped step needs them.
 #pragma once
 #include "device_types.cuh"
 
@@ -14,28 +18,28 @@ namespace cprrtc {
 // Floats stored per frame: axes x, y, z then origin p (columns of the 3x4 transform).
 constexpr int kFrameFloats = 12;
 
-struct TaskEval {
-  int m;              // task rows (0, 1 or 2)
-  float e0, e1;       // task error
-  float J0[kMaxDof];  // task Jacobian rows
-  float J1[kMaxDof];
+// 1/pi in FP32: joint angles are reduced exactly by sincospif(angle / pi).
+constexpr float kInvPi = 0.318309886183790671538f;
+
+// What one chain evaluation leaves for the task error and Jacobian.
+struct ChainState {
+  float x0, x1, x2, y0, y1, y2, z0, z1, z2, p0, p1, p2;  // last frame (dof)
+  float zx[kMaxDof], zy[kMaxDof], zz[kMaxDof];           // axis of joint k (z of frame k)
+  float px[kMaxDof], py[kMaxDof];                        // origin of frame k
 };
 
 // Runs the DH chain for configuration q. If `fr` is non-null, frames 1..dof are written to
-// fr[(k-1)*12 .. ] as {x, y, z, p}. If `task`, fills t with the task error and Jacobian of
-// constraint c.
-template <bool task>
-__device__ __forceinline__ void chain(const RobotDev& rb, const ConsDev& c, const float* q,
-                                      float* fr, TaskEval& t) {
+// fr[(k-1)*12 ..] as {x, y, z, p}.
+__device__ __forceinline__ void chain(const RobotDev& rb, const float* q, float* fr,
+                                      ChainState& s) {
   float x0 = 1.f, x1 = 0.f, x2 = 0.f;
   float y0 = 0.f, y1 = 1.f, y2 = 0.f;
   float z0 = 0.f, z1 = 0.f, z2 = 1.f;
   float p0 = 0.f, p1 = 0.f, p2 = 0.f;
-  float zx[kMaxDof], zy[kMaxDof], zz[kMaxDof], px[kMaxDof], py[kMaxDof];
 #pragma unroll
   for (int k = 0; k < kMaxDof; ++k) {
     if (k < rb.dof) {
-      zx[k] = z0; zy[k] = z1; zz[k] = z2; px[k] = p0; py[k] = p1;
+      s.zx[k] = z0; s.zy[k] = z1; s.zz[k] = z2; s.px[k] = p0; s.py[k] = p1;
       const JointDev& J = rb.j[k];
       float ct, st, d = J.d;
       if (J.prismatic) {
@@ -43,7 +47,7 @@ __device__ __forceinline__ void chain(const RobotDev& rb, const ConsDev& c, cons
         st = J.st0;
         d += q[k];
       } else {
-        sincosf(J.theta0 + q[k], &st, &ct);
+        sincospif((J.theta0 + q[k]) * kInvPi, &st, &ct);
       }
       const float u0 = fmaf(x0, ct, y0 * st), u1 = fmaf(x1, ct, y1 * st), u2 = fmaf(x2, ct, y2 * st);
       const float v0 = fmaf(y0, ct, -x0 * st), v1 = fmaf(y1, ct, -x1 * st), v2 = fmaf(y2, ct, -x2 * st);
@@ -64,81 +68,92 @@ __device__ __forceinline__ void chain(const RobotDev& rb, const ConsDev& c, cons
       }
     }
   }
-  if (!task) return;
-  if (c.type == kConsRollPitch) {
+  s.x0 = x0; s.x1 = x1; s.x2 = x2; s.y0 = y0; s.y1 = y1; s.y2 = y2;
+  s.z0 = z0; s.z1 = z1; s.z2 = z2; s.p0 = p0; s.p1 = p1; s.p2 = p2;
+}
+
+// Task error, the scalars its Jacobian needs, and the damped step of one configuration.
+template <int CT>
+struct Task {
+  float e0, e1;
+  // roll/pitch: J0_k = (x0 zx_k + x1 zy_k) * c0,  J1_k = (x0 zy_k - x1 zx_k) * c1
+  // z-plane:    J0_k = zx_k (pe1 - py_k) - zy_k (pe0 - px_k)   (zz_k for prismatic joints)
+  float c0, c1, pe0, pe1;
+};
+
+template <int CT>
+__device__ __forceinline__ Task<CT> task_error(const RobotDev& rb, const ConsDev& c,
+                                               const ChainState& s) {
+  Task<CT> t{};
+  if (CT == kConsRollPitch) {
     // ZYX Euler angles of R = [x y z]: R11 = x0, R21 = x1, R31 = x2, R32 = y2, R33 = z2.
-    t.m = 2;
-    t.e0 = atan2f(y2, z2);                                  // roll
-    t.e1 = atan2f(-x2, sqrtf(fmaf(y2, y2, z2 * z2)));       // pitch
-    // Euler-rate map: cos(yaw)/cos(pitch) = R11 / c2, sin(yaw)/cos(pitch) = R21 / c2 with
-    // c2 = R11^2 + R21^2 = cos(pitch)^2; second row uses cos(yaw), sin(yaw) = R11, R21 / c.
-    const float c2 = fmaf(x0, x0, x1 * x1);
-    const float inv_c2 = 1.0f / c2;
-    const float inv_c = rsqrtf(c2);
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) {
-      if (k < rb.dof) {
-        const bool rev = !rb.j[k].prismatic;
-        t.J0[k] = rev ? fmaf(x0, zx[k], x1 * zy[k]) * inv_c2 : 0.f;
-        t.J1[k] = rev ? fmaf(x0, zy[k], -x1 * zx[k]) * inv_c : 0.f;
-      }
-    }
-  } else if (c.type == kConsZPlane) {
-    t.m = 1;
-    const float e0 = fmaf(x0, rb.ee[0], fmaf(y0, rb.ee[1], fmaf(z0, rb.ee[2], p0)));
-    const float e1 = fmaf(x1, rb.ee[0], fmaf(y1, rb.ee[1], fmaf(z1, rb.ee[2], p1)));
-    const float e2 = fmaf(x2, rb.ee[0], fmaf(y2, rb.ee[1], fmaf(z2, rb.ee[2], p2)));
-    t.e0 = e2 - c.target;
+    t.e0 = atan2f(s.y2, s.z2);                                   // roll
+    t.e1 = atan2f(-s.x2, sqrtf(fmaf(s.y2, s.y2, s.z2 * s.z2)));  // pitch
+    // Euler-rate map rows: (cos(yaw), sin(yaw)) / cos(pitch) = (R11, R21) / c2 and
+    // (-sin(yaw), cos(yaw)) = (-R21, R11) / c, with c2 = R11^2 + R21^2 = cos(pitch)^2.
+    const float c2 = fmaf(s.x0, s.x0, s.x1 * s.x1);
+    t.c0 = 1.0f / c2;
+    t.c1 = rsqrtf(c2);
+  } else if (CT == kConsZPlane) {
+    t.pe0 = fmaf(s.x0, rb.ee[0], fmaf(s.y0, rb.ee[1], fmaf(s.z0, rb.ee[2], s.p0)));
+    t.pe1 = fmaf(s.x1, rb.ee[0], fmaf(s.y1, rb.ee[1], fmaf(s.z1, rb.ee[2], s.p1)));
+    const float pe2 = fmaf(s.x2, rb.ee[0], fmaf(s.y2, rb.ee[1], fmaf(s.z2, rb.ee[2], s.p2)));
+    t.e0 = pe2 - c.target;
     t.e1 = 0.f;
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) {
-      if (k < rb.dof) {
-        // z component of z_k x (p_e - p_k) (revolute) or z_k (prismatic)
-        t.J0[k] = rb.j[k].prismatic ? zz[k] : fmaf(zx[k], e1 - py[k], -zy[k] * (e0 - px[k]));
-        t.J1[k] = 0.f;
-      }
-    }
   } else {
-    t.m = 0;
     t.e0 = t.e1 = 0.f;
   }
+  return t;
 }
 
-// g = J^T (J J^T + lambda^2 I)^-1 e for m <= 2 (Cramer's rule on the 2x2 system).
-__device__ __forceinline__ void damped_step(const RobotDev& rb, const ConsDev& c,
-                                            const TaskEval& t, float* g) {
-  if (t.m == 2) {
-    float a = c.lam2, b = 0.f, d = c.lam2;
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k)
-      if (k < rb.dof) {
-        a = fmaf(t.J0[k], t.J0[k], a);
-        b = fmaf(t.J0[k], t.J1[k], b);
-        d = fmaf(t.J1[k], t.J1[k], d);
-      }
-    const float inv_det = 1.0f / fmaf(a, d, -b * b);
-    const float y0 = fmaf(d, t.e0, -b * t.e1) * inv_det;
-    const float y1 = fmaf(a, t.e1, -b * t.e0) * inv_det;
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k)
-      if (k < rb.dof) g[k] = fmaf(t.J0[k], y0, t.J1[k] * y1);
-  } else if (t.m == 1) {
-    float a = c.lam2;
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k)
-      if (k < rb.dof) a = fmaf(t.J0[k], t.J0[k], a);
-    const float y0 = t.e0 / a;
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k)
-      if (k < rb.dof) g[k] = t.J0[k] * y0;
+template <int CT>
+__device__ __forceinline__ void jac_entry(const RobotDev& rb, const ChainState& s,
+                                          const Task<CT>& t, int k, float& j0, float& j1) {
+  if (CT == kConsRollPitch) {
+    const bool rev = !rb.j[k].prismatic;
+    j0 = rev ? fmaf(s.x0, s.zx[k], s.x1 * s.zy[k]) * t.c0 : 0.f;
+    j1 = rev ? fmaf(s.x0, s.zy[k], -s.x1 * s.zx[k]) * t.c1 : 0.f;
+  } else if (CT == kConsZPlane) {
+    j0 = rb.j[k].prismatic ? s.zz[k]
+                           : fmaf(s.zx[k], t.pe1 - s.py[k], -s.zy[k] * (t.pe0 - s.px[k]));
+    j1 = 0.f;
   } else {
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) g[k] = 0.f;
+    j0 = j1 = 0.f;
   }
 }
 
-__device__ __forceinline__ float task_err_inf(const TaskEval& t) {
-  return t.m == 2 ? fmaxf(fabsf(t.e0), fabsf(t.e1)) : (t.m == 1 ? fabsf(t.e0) : 0.f);
+// Solves (J J^T + lambda^2 I) y = e for m <= 2 (Cramer's rule); the step is g_k = J_k . y.
+template <int CT>
+__device__ __forceinline__ void damped_solve(const RobotDev& rb, const ConsDev& c,
+                                             const ChainState& s, const Task<CT>& t,
+                                             float& y0, float& y1) {
+  float a = c.lam2, b = 0.f, d = c.lam2;
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) {
+    if (k < rb.dof) {
+      float j0, j1;
+      jac_entry<CT>(rb, s, t, k, j0, j1);
+      a = fmaf(j0, j0, a);
+      b = fmaf(j0, j1, b);
+      d = fmaf(j1, j1, d);
+    }
+  }
+  if (CT == kConsRollPitch) {
+    const float inv_det = 1.0f / fmaf(a, d, -b * b);
+    y0 = fmaf(d, t.e0, -b * t.e1) * inv_det;
+    y1 = fmaf(a, t.e1, -b * t.e0) * inv_det;
+  } else if (CT == kConsZPlane) {
+    y0 = t.e0 / a;
+    y1 = 0.f;
+  } else {
+    y0 = y1 = 0.f;
+  }
+}
+
+template <int CT>
+__device__ __forceinline__ float task_err_inf(const Task<CT>& t) {
+  return CT == kConsRollPitch ? fmaxf(fabsf(t.e0), fabsf(t.e1))
+                              : (CT == kConsZPlane ? fabsf(t.e0) : 0.f);
 }
 
 }  // namespace cprrtc

@@ -29,6 +29,39 @@ struct ValidateArgs {
   int stage_obs;  // set by the launcher
 };
 
+constexpr int kMaxWorkers = 16;  // warps per planning problem
+
+struct PlanArgs {
+  const float* start;
+  const float* goal;
+  int n;
+  float range;
+  int W, max_rounds, workers, max_nodes, max_connect, max_path;
+  uint32_t seed;
+  const float4* scene_obs;  // scene batch: obstacle stream
+  const int4* scenes;       // [n] {float4 offset, n_sph, n_box, n_cap}; null: shared scene
+  int max_scene_f4;         // largest scene, float4 slots
+  float* nodes;             // [n][2][max_nodes][8]
+  int* parent;              // [n][2][max_nodes]
+  float* edges;             // [n][2][max_nodes][W][dof]
+  float* pend;              // [n][workers][max_connect + 2][8]
+  float* pend_edges;        // [n][workers][max_connect + 2][W][dof]
+  int32_t* path_len;
+  float* path;
+  float* path_edges;
+  int32_t* rounds;
+  long long* waypoints;
+  float* plan_ms;
+  long long* work;          // [n][2] Alg. 1 waypoint evaluations, collision-checked waypoints
+  int stage_obs;            // set by the launcher
+};
+
+size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
+cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
+                        const DeviceInfo& dev, cudaStream_t stream);
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
+                          cudaStream_t stream);
+
 size_t validate_smem_bytes(const RobotDev& rb, const SceneDev& sc, int W, bool stage_obs);
 cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs,
                             ValidateArgs a, const DeviceInfo& dev, cudaStream_t stream);

@@ -48,24 +48,25 @@ struct ProjResult {
   float resid;     // max over waypoints 1..W-1 of the last evaluated ||E_task||_inf
 };
 
-// Alg. 1 on the warp's motion. q[WPL][kMaxDof] holds this lane's waypoints (the
-// interpolated segment on entry, the segment after the last iteration on exit). Frames of
-// every waypoint's evaluation are written to fr (stride frame_stride(dof)); on success they
-// describe the returned segment. With the NONE constraint only the frames are computed.
-template <int WPL>
+// Alg. 1 on the warp's motion, constraint type CT, at most max_iters iterations.
+// q[WPL][kMaxDof] holds this lane's waypoints (the interpolated segment on entry, the
+// segment after the last iteration on exit). Frames of every waypoint's evaluation are
+// written to fr (stride frame_stride(dof)); on success they describe the returned segment.
+// With CT = kConsNone only the frames are computed.
+template <int CT, int WPL>
 __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const ConsDev& c,
-                                                   float (&q)[WPL][kMaxDof], int W, float tau,
-                                                   float* fr) {
+                                                   int max_iters, float (&q)[WPL][kMaxDof],
+                                                   int W, float tau, float* fr) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int fs = frame_stride(dof);
   ProjResult res{kValid, 0, -1, 0.f};
-  TaskEval t;
-  if (c.type == kConsNone) {
+  ChainState cs;
+  if (CT == kConsNone) {
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {
       const int i = lane + 32 * s;
-      if (i < W) chain<false>(rb, c, q[s], fr + i * fs, t);
+      if (i < W) chain(rb, q[s], fr + i * fs, cs);
     }
     return res;
   }
@@ -75,48 +76,41 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
 #pragma unroll
   for (int s = 0; s < WPL; ++s) last_err[s] = 0.f;
   int prog = 0;
-  for (int it = 1; it <= c.max_iters; ++it) {
-    // predecessor waypoint i-1 of each slot (lane 0 of slot 1 takes lane 31 of slot 0)
-    float prev[WPL][kMaxDof];
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) {
-      if (k < dof) {
-#pragma unroll
-        for (int s = 0; s < WPL; ++s) {
-          float up = __shfl_up_sync(kFull, q[s][k], 1);
-          if (s > 0) {
-            const float wrap = __shfl_sync(kFull, q[s - 1][k], 31);
-            if (lane == 0) up = wrap;
-          }
-          prev[s][k] = up;
-        }
-      }
-    }
+  for (int it = 1; it <= max_iters; ++it) {
     float qn[WPL][kMaxDof];
     unsigned long long valid_mask = 0ull;
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {
       const int i = lane + 32 * s;
-      bool valid = true;
-      if (i < W) {
-        chain<true>(rb, c, q[s], fr + i * fs, t);
-        float g[kMaxDof];
-        damped_step(rb, c, t, g);
-        float esm_max = 0.f;
+      // every lane evaluates (lanes past W on a clamped copy) so that the shuffles below
+      // run converged; only in-range lanes write frames
+      chain(rb, q[s], i < W ? fr + i * fs : nullptr, cs);
+      const Task<CT> t = task_error<CT>(rb, c, cs);
+      float y0, y1;
+      damped_solve<CT>(rb, c, cs, t, y0, y1);
+      float esm_max = 0.f;
 #pragma unroll
-        for (int k = 0; k < kMaxDof; ++k) {
-          if (k < dof) {
-            const float dk = q[s][k] - prev[s][k];
-            const float esm = fmaxf(0.f, fabsf(dk) - tau);
-            const float v = fmaf(-c.alpha, fmaf(dk, esm, g[k]), q[s][k]);
-            qn[s][k] = fminf(fmaxf(v, rb.j[k].lo), rb.j[k].hi);
-            esm_max = fmaxf(esm_max, esm);
+      for (int k = 0; k < kMaxDof; ++k) {
+        if (k < dof) {
+          // predecessor waypoint i-1 (lane 0 of slot s > 0 takes lane 31 of slot s-1)
+          float prev = __shfl_up_sync(kFull, q[s][k], 1);
+          if (s > 0) {
+            const float wrap = __shfl_sync(kFull, q[s > 0 ? s - 1 : 0][k], 31);
+            if (lane == 0) prev = wrap;
           }
+          float j0, j1;
+          jac_entry<CT>(rb, cs, t, k, j0, j1);
+          const float g = fmaf(j0, y0, j1 * y1);
+          const float dk = q[s][k] - prev;
+          const float esm = fmaxf(0.f, fabsf(dk) - tau);
+          const float v = fmaf(-c.alpha, fmaf(dk, esm, g), q[s][k]);
+          qn[s][k] = fminf(fmaxf(v, rb.j[k].lo), rb.j[k].hi);
+          esm_max = fmaxf(esm_max, esm);
         }
-        const float et = task_err_inf(t);
-        valid = (esm_max < c.tol_sm) && (et < c.tol_task);
-        if (i > prog) last_err[s] = et;
       }
+      const float et = task_err_inf<CT>(t);
+      const bool valid = (i >= W) || ((esm_max < c.tol_sm) && (et < c.tol_task));
+      if (i > prog && i < W) last_err[s] = et;
       valid_mask |= (unsigned long long)__ballot_sync(kFull, valid) << (32 * s);
     }
     // acceptance: advance prog over the contiguous valid run after it
@@ -147,7 +141,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
   res.resid = m;
   if (prog != W - 1) {
     res.status = kProjFail;
-    res.iters = c.max_iters;
+    res.iters = max_iters;
     res.first_fail = prog + 1;
   }
   return res;
@@ -193,12 +187,14 @@ __device__ __forceinline__ int collide_warp(const RobotDev& rb, const SceneDev& 
       }
       for (int o0 = 0; o0 < sc.n_sph; o0 += kVoteEvery) {
         const int o1 = min(o0 + kVoteEvery, sc.n_sph);
+#pragma unroll 4
         for (int o = o0; o < o1; ++o) hit |= act && hit_sphere(cx, cy, cz, r, obs[o]);
         if (__any_sync(kFull, hit)) break;
       }
       if (__any_sync(kFull, hit)) break;
       for (int o0 = 0; o0 < sc.n_box; o0 += kVoteEvery) {
         const int o1 = min(o0 + kVoteEvery, sc.n_box);
+#pragma unroll 2
         for (int o = o0; o < o1; ++o)
           hit |= act && hit_box(cx, cy, cz, r, box[4 * o], box[4 * o + 1], box[4 * o + 2],
                                 box[4 * o + 3]);
@@ -207,6 +203,7 @@ __device__ __forceinline__ int collide_warp(const RobotDev& rb, const SceneDev& 
       if (__any_sync(kFull, hit)) break;
       for (int o0 = 0; o0 < sc.n_cap; o0 += kVoteEvery) {
         const int o1 = min(o0 + kVoteEvery, sc.n_cap);
+#pragma unroll 2
         for (int o = o0; o < o1; ++o)
           hit |= act && hit_capsule(cx, cy, cz, r, cap[2 * o], cap[2 * o + 1]);
         if (__any_sync(kFull, hit)) break;

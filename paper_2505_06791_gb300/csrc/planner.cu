@@ -1,0 +1,470 @@
+// RRT-Connect with constrained motions (Sec. III, Sec. II): one CTA per planning problem,
+// one warp per tree extension.
+//
+// Each round, every warp w extends tree a = (round + w) mod 2 toward a Philox sample
+// (counter {problem, round, w, draw}, key {seed, 0}): nearest node, steer by at most
+// `range`, validate the motion (Alg. 1 + FK + CC, waypoint 0 skipped), then greedily
+// extends the same tree from the new node toward its nearest node in the other tree while
+// each projected motion is valid and ends strictly closer. Within 10 * tau_floor (inf-norm)
+// of that node, the closing hop must be valid as it stands (one Alg. 1 iteration + CC) and
+// the trees are connected. Warps work against the trees as they stood when the round
+// began; their new nodes are appended in warp order after a barrier, and the lowest warp
+// that connected returns the path. The search is therefore deterministic for a seed.
+//
+// Trees live in global memory (nodes padded to 8 floats, parent indices, and each node's
+// projected incoming motion, so that returned paths are dense). The problem's obstacles
+// are staged into shared memory when they fit.
+#include "launch.h"
+#include "motion.cuh"
+#include "philox.cuh"
+
+namespace cprrtc {
+
+struct PlanShared {
+  int count0[2];               // tree sizes when the round began
+  int pcount[kMaxWorkers];     // nodes each warp added this round
+  int ptree[kMaxWorkers];
+  int pnear[kMaxWorkers];      // tree index of the first added node's parent
+  int ptarget[kMaxWorkers];    // nearest node of the other tree (connect target)
+  int pconn[kMaxWorkers];      // 1 if the warp connected the trees
+  long long wp[kMaxWorkers];   // waypoints validated by each warp
+  long long wproj[kMaxWorkers];
+  long long wcc[kMaxWorkers];
+};
+
+__device__ __forceinline__ void load_cfg(const float* src, int dof, float* q) {
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) q[k] = k < dof ? src[k] : 0.f;
+}
+
+// Nearest of nodes[0, count) (stride 8 floats) to q in L2; lowest index on ties.
+__device__ __forceinline__ int nearest_warp(const float* __restrict__ nodes, int count,
+                                            const float* q, int dof) {
+  const int lane = threadIdx.x & 31;
+  float best = INFINITY;
+  int bi = 0x7fffffff;
+  for (int j = lane; j < count; j += 32) {
+    const float4* n4 = reinterpret_cast<const float4*>(nodes + (size_t)j * 8);
+    const float4 a = n4[0], b = n4[1];
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k)
+      if (k < dof) {
+        const float t = v[k] - q[k];
+        d = fmaf(t, t, d);
+      }
+    if (d < best) {
+      best = d;
+      bi = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(kFull, best, o);
+    const int oi = __shfl_xor_sync(kFull, bi, o);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  return bi;
+}
+
+__device__ __forceinline__ float dist2(const float* a, const float* b, int dof) {
+  float d = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k)
+    if (k < dof) {
+      const float t = a[k] - b[k];
+      d = fmaf(t, t, d);
+    }
+  return d;
+}
+
+// q_s = from + min(1, range / |to - from|) (to - from)
+__device__ __forceinline__ void steer(const float* from, const float* to, float range, int dof,
+                                      float* out) {
+  const float d = sqrtf(dist2(from, to, dof));
+  const float f = d > range ? range / d : 1.f;
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k)
+    if (k < dof) out[k] = fmaf(f, to[k] - from[k], from[k]);
+}
+
+// The warp's segment waypoint W-1 broadcast to every lane.
+template <int WPL>
+__device__ __forceinline__ void last_waypoint(const float (&q)[WPL][kMaxDof], int W, int dof,
+                                              float* out) {
+  const int src = (W - 1) & 31;
+  const bool hi = (W - 1) >= 32;
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) {
+    if (k < dof) {
+      const float v = (WPL > 1 && hi) ? q[WPL > 1 ? 1 : 0][k] : q[0][k];
+      out[k] = __shfl_sync(kFull, v, src);
+    }
+  }
+}
+
+template <int WPL>
+__device__ __forceinline__ void store_edge(float* dst, const float (&q)[WPL][kMaxDof], int W,
+                                           int dof) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < WPL; ++s) {
+    const int i = lane + 32 * s;
+    if (i < W) {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) dst[i * dof + k] = q[s][k];
+    }
+  }
+}
+
+__device__ __forceinline__ void store_cfg(float* dst, const float* q, int dof) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 8) {
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k)
+      if (k == lane) v = k < dof ? q[k] : 0.f;
+    dst[lane] = v;
+  }
+}
+
+// Copies `count` floats (lanes in parallel).
+__device__ __forceinline__ void copy_warp(float* dst, const float* src, int count) {
+  for (int i = threadIdx.x & 31; i < count; i += 32) dst[i] = src[i];
+}
+
+// Copies a W x dof edge, reversing the waypoint order when `rev`.
+__device__ __forceinline__ void copy_edge(float* dst, const float* src, int W, int dof, bool rev) {
+  for (int i = threadIdx.x & 31; i < W * dof; i += 32) {
+    const int w = i / dof, k = i - w * dof;
+    dst[i] = src[(rev ? (W - 1 - w) : w) * dof + k];
+  }
+}
+
+struct MotionWork {
+  long long proj;  // waypoint evaluations of Alg. 1: iterations x (W - 1)
+  long long cc;    // waypoints collision-checked
+};
+
+// Interpolate q0 -> q1, project (at most cs.max_iters iterations), FK + CC from waypoint 1.
+template <int CT, int WPL>
+__device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDev& sc,
+                                               const ConsDev& cs, MotionWork& work,
+                                               const float4* obs, const float4* sph,
+                                               const int* sfr, const float* q0,
+                                               const float* q1, int W, float* fr,
+                                               float (&q)[WPL][kMaxDof]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
+  const float tau = step_threshold(cs, q0, q1, W, rb.dof);
+  const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau, fr);
+  __syncwarp();
+  work.proj += (long long)pr.iters * (W - 1);
+  if (pr.status != kValid) return kProjFail;
+  const int ff = collide_warp(rb, sc, obs, sph, sfr, W, 1, fr);
+  __syncwarp();
+  work.cc += ff >= 0 ? ff : W - 1;
+  return ff >= 0 ? kCollision : kValid;
+}
+
+template <int CT, int WPL>
+__global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, PlanArgs a) {
+  const int p = blockIdx.x;
+  if (p >= a.n) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int B = a.workers, dof = rb.dof, W = a.W;
+  long long t_start = 0;
+  if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+
+  SceneDev sc = shared_scene;
+  if (a.scenes) {
+    const int4 d = a.scenes[p];
+    sc.obs = a.scene_obs + d.x;
+    sc.n_sph = d.y;
+    sc.n_box = d.z;
+    sc.n_cap = d.w;
+  }
+  extern __shared__ float4 smem[];
+  const int n4 = sc.n_float4();
+  float4* s_obs = smem;
+  float4* s_sph = smem + (a.stage_obs ? a.max_scene_f4 : 0);
+  int* s_sfr = reinterpret_cast<int*>(s_sph + rb.n_spheres);
+  float* s_fr = reinterpret_cast<float*>(s_sfr + ((rb.n_spheres + 3) & ~3));
+  // PlanShared holds 64-bit counters: place it on a 16-byte boundary (as sized on the host)
+  PlanShared* sh = reinterpret_cast<PlanShared*>(
+      (reinterpret_cast<uintptr_t>(s_fr + (size_t)B * W * frame_stride(dof)) + 15) & ~uintptr_t(15));
+  if (a.stage_obs)
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
+  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) {
+    s_sph[i] = rb.spheres[i];
+    s_sfr[i] = rb.sphere_frame[i];
+  }
+  const float4* obs = a.stage_obs ? s_obs : sc.obs;
+  float* fr = s_fr + (size_t)warp * W * frame_stride(dof);
+
+  const size_t tree_stride = (size_t)a.max_nodes;
+  float* nodes[2];
+  int* parent[2];
+  float* edges[2];
+  for (int t = 0; t < 2; ++t) {
+    nodes[t] = a.nodes + ((size_t)p * 2 + t) * tree_stride * 8;
+    parent[t] = a.parent + ((size_t)p * 2 + t) * tree_stride;
+    edges[t] = a.edges + ((size_t)p * 2 + t) * tree_stride * W * dof;
+  }
+  const int PC = a.max_connect + 2;  // pending slots: extension + connect nodes + hop edge
+  float* pnode = a.pend + ((size_t)p * B + warp) * PC * 8;
+  float* pedge = a.pend_edges + ((size_t)p * B + warp) * PC * W * dof;
+
+  if (warp == 0) {
+    float q[kMaxDof];
+    load_cfg(a.start + (size_t)p * dof, dof, q);
+    store_cfg(nodes[0], q, dof);
+    load_cfg(a.goal + (size_t)p * dof, dof, q);
+    store_cfg(nodes[1], q, dof);
+    if (lane == 0) {
+      parent[0][0] = -1;
+      parent[1][0] = -1;
+      sh->count0[0] = 1;
+      sh->count0[1] = 1;
+    }
+  }
+  if (lane == 0) sh->wp[warp] = 0;
+  __syncthreads();
+
+  ConsDev hop = cs;
+  hop.max_iters = 1;
+  const float connect_radius = 10.f * cs.tau_floor;
+  long long wp = 0;
+  MotionWork work{0, 0};
+  int rounds_used = 0, win = -1;
+  for (int r = 0; r < a.max_rounds; ++r) {
+    const int ta = (r + warp) & 1, tb = ta ^ 1;
+    const int ca = sh->count0[ta], cb = sh->count0[tb];
+    // sample
+    float qr[kMaxDof];
+    {
+      const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 0u}, a.seed, 0u);
+      const U32x4 u1 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 1u}, a.seed, 0u);
+      const uint32_t w8[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) qr[k] = fmaf(u24(w8[k]), rb.j[k].hi - rb.j[k].lo, rb.j[k].lo);
+    }
+    const int near = nearest_warp(nodes[ta], ca, qr, dof);
+    float cur[kMaxDof], q1[kMaxDof], qt[kMaxDof];
+    load_cfg(nodes[ta] + (size_t)near * 8, dof, cur);
+    steer(cur, qr, a.range, dof, q1);
+    // One validation call site: mode 0 = extension toward the sample, 1 = greedy connect
+    // step toward qt, 2 = closing hop onto qt (one Alg. 1 iteration, i.e. as it stands).
+    int mode = 0, k = 0, conn = 0, target = -1, steps = 0;
+    while (true) {
+      float q[WPL][kMaxDof];
+      const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, obs, s_sph, s_sfr,
+                                              cur, q1, W, fr, q);
+      wp += W;
+      if (st != kValid) break;
+      if (mode == 2) {
+        conn = 1;
+        store_edge<WPL>(pedge + (size_t)k * W * dof, q, W, dof);
+        break;
+      }
+      float qe[kMaxDof];
+      last_waypoint<WPL>(q, W, dof, qe);
+      if (mode == 0) {
+        target = nearest_warp(nodes[tb], cb, qe, dof);
+        load_cfg(nodes[tb] + (size_t)target * 8, dof, qt);
+      } else if (!(dist2(qe, qt, dof) < dist2(cur, qt, dof))) {
+        break;
+      }
+      store_cfg(pnode + (size_t)k * 8, qe, dof);
+      store_edge<WPL>(pedge + (size_t)k * W * dof, q, W, dof);
+      ++k;
+#pragma unroll
+      for (int j = 0; j < kMaxDof; ++j) cur[j] = qe[j];
+      // next motion: the closing hop when within reach, else one more connect step
+      float gap = 0.f;
+#pragma unroll
+      for (int j = 0; j < kMaxDof; ++j)
+        if (j < dof) gap = fmaxf(gap, fabsf(cur[j] - qt[j]));
+      if (gap <= connect_radius) {
+        mode = 2;
+#pragma unroll
+        for (int j = 0; j < kMaxDof; ++j) q1[j] = qt[j];
+      } else {
+        if (steps >= a.max_connect) break;
+        ++steps;
+        mode = 1;
+        steer(cur, qt, a.range, dof, q1);
+      }
+    }
+    if (lane == 0) {
+      sh->pcount[warp] = k;
+      sh->ptree[warp] = ta;
+      sh->pnear[warp] = near;
+      sh->ptarget[warp] = target;
+      sh->pconn[warp] = conn;
+    }
+    __syncthreads();
+    rounds_used = r + 1;
+    win = -1;
+    for (int w = 0; w < B; ++w)
+      if (sh->pconn[w]) {
+        win = w;
+        break;
+      }
+    if (win >= 0) break;
+    // append this round's nodes in warp order
+    {
+      const int base = sh->count0[ta];
+      int off = 0;
+      for (int w = 0; w < warp; ++w)
+        if (sh->ptree[w] == ta) off += sh->pcount[w];
+      for (int j = 0; j < k; ++j) {
+        const int dst = base + off + j;
+        if (dst >= a.max_nodes) break;
+        copy_warp(nodes[ta] + (size_t)dst * 8, pnode + (size_t)j * 8, 8);
+        copy_warp(edges[ta] + (size_t)dst * W * dof, pedge + (size_t)j * W * dof, W * dof);
+        if (lane == 0) parent[ta][dst] = j == 0 ? near : dst - 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < 2; ++t) {
+        int add = 0;
+        for (int w = 0; w < B; ++w)
+          if (sh->ptree[w] == t) add += sh->pcount[w];
+        sh->count0[t] = min(sh->count0[t] + add, a.max_nodes);
+      }
+    }
+    __syncthreads();
+  }
+  if (lane == 0) {
+    sh->wp[warp] = wp;
+    sh->wproj[warp] = work.proj;
+    sh->wcc[warp] = work.cc;
+  }
+
+  if (win >= 0 && warp == win) {
+    // path: root_a .. near, added nodes, target .. root_b; reversed when tree a is the goal tree
+    const int ta = sh->ptree[win], tb = ta ^ 1;
+    const int near = sh->pnear[win], k = sh->pcount[win], target = sh->ptarget[win];
+    int len_a = 0, len_b = 0;
+    for (int v = near; v >= 0; v = parent[ta][v]) ++len_a;
+    for (int v = target; v >= 0; v = parent[tb][v]) ++len_b;
+    const int total = len_a + k + len_b;
+    const bool flip = ta == 1;
+    float* path = a.path + (size_t)p * a.max_path * dof;
+    float* pe = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * W * dof : nullptr;
+    auto npos = [&](int pos) { return flip ? total - 1 - pos : pos; };
+    auto epos = [&](int e) { return flip ? total - 2 - e : e; };
+    if (total <= a.max_path) {
+      int pos = len_a - 1;
+      for (int v = near; v >= 0; v = parent[ta][v], --pos) {
+        copy_warp(path + (size_t)npos(pos) * dof, nodes[ta] + (size_t)v * 8, dof);
+        if (pe && parent[ta][v] >= 0)  // edge pos-1 -> pos is v's incoming motion
+          copy_edge(pe + (size_t)epos(pos - 1) * W * dof, edges[ta] + (size_t)v * W * dof, W, dof, flip);
+      }
+      for (int j = 0; j < k; ++j) {
+        copy_warp(path + (size_t)npos(len_a + j) * dof, pnode + (size_t)j * 8, dof);
+        if (pe) copy_edge(pe + (size_t)epos(len_a - 1 + j) * W * dof, pedge + (size_t)j * W * dof, W, dof, flip);
+      }
+      if (pe)  // closing hop: last added node -> target
+        copy_edge(pe + (size_t)epos(len_a + k - 1) * W * dof, pedge + (size_t)k * W * dof, W, dof, flip);
+      pos = len_a + k;
+      for (int v = target; v >= 0; v = parent[tb][v], ++pos) {
+        copy_warp(path + (size_t)npos(pos) * dof, nodes[tb] + (size_t)v * 8, dof);
+        if (pe && parent[tb][v] >= 0)  // edge pos -> pos+1 is v's incoming motion reversed
+          copy_edge(pe + (size_t)epos(pos) * W * dof, edges[tb] + (size_t)v * W * dof, W, dof, !flip);
+      }
+    }
+    if (lane == 0) a.path_len[p] = total <= a.max_path ? total : -total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (win < 0) a.path_len[p] = 0;
+    long long total_wp = 0, tp = 0, tc = 0;
+    for (int w = 0; w < B; ++w) {
+      total_wp += sh->wp[w];
+      tp += sh->wproj[w];
+      tc += sh->wcc[w];
+    }
+    if (a.rounds) a.rounds[p] = rounds_used;
+    if (a.waypoints) a.waypoints[p] = total_wp;
+    if (a.work) {
+      a.work[2 * p] = tp;
+      a.work[2 * p + 1] = tc;
+    }
+    long long t_end;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - t_start) * 1e-6);
+  }
+}
+
+static const void* plan_fn(int ct, int W) {
+  const bool two = W > 32;
+  switch (ct) {
+    case kConsRollPitch:
+      return two ? (const void*)plan_kernel<kConsRollPitch, 2> : (const void*)plan_kernel<kConsRollPitch, 1>;
+    case kConsZPlane:
+      return two ? (const void*)plan_kernel<kConsZPlane, 2> : (const void*)plan_kernel<kConsZPlane, 1>;
+    default:
+      return two ? (const void*)plan_kernel<kConsNone, 2> : (const void*)plan_kernel<kConsNone, 1>;
+  }
+}
+
+size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage) {
+  size_t b = 0;
+  if (stage) b += (size_t)max_scene_f4 * sizeof(float4);
+  b += (size_t)rb.n_spheres * sizeof(float4);
+  b += (size_t)((rb.n_spheres + 3) & ~3) * sizeof(int);
+  b += (size_t)workers * W * frame_stride(rb.dof) * sizeof(float);
+  b = (b + 15) & ~size_t(15);
+  b += sizeof(PlanShared);
+  return b;
+}
+
+cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
+                        const DeviceInfo& dev, cudaStream_t stream) {
+  if (a.n <= 0) return cudaSuccess;
+  size_t smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, true);
+  a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
+  if (!a.stage_obs) smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, false);
+  if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
+  const void* fn = plan_fn(cs.type, a.W);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<RobotDev*>(&rb), const_cast<SceneDev*>(&sc),
+                  const_cast<ConsDev*>(&cs), &a};
+  e = cudaLaunchKernel(fn, dim3(a.n), dim3(32 * a.workers), args, smem, stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace cprrtc
+
+namespace cprrtc {
+
+__global__ void philox_kernel(uint32_t k0, uint32_t k1, const uint4* __restrict__ ctr, int n,
+                              uint4* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = ctr[i];
+  const U32x4 r = philox4x32_10(U32x4{c.x, c.y, c.z, c.w}, k0, k1);
+  out[i] = make_uint4(r.x, r.y, r.z, r.w);
+}
+
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
+                          cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  philox_kernel<<<(n + 255) / 256, 256, 0, stream>>>(k0, k1, reinterpret_cast<const uint4*>(ctr),
+                                                     n, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace cprrtc

@@ -8,9 +8,9 @@ namespace cprrtc {
 // Robot spheres, their frames and each warp's frame cache live in shared memory; the
 // obstacle stream is staged there too when it fits (coalesced float4 copies), else read
 // from global memory through L1 (every lane reads the same obstacle: one broadcast).
-template <int WPL>
-__global__ void __launch_bounds__(kValidateWarps * 32)
-    validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
+// (No __launch_bounds__: with it, ptxas caps registers low enough to spill here.)
+template <int CT, int WPL>
+__global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
   extern __shared__ float4 smem[];
   const int n4 = sc.n_float4();
   float4* s_obs = smem;
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kValidateWarps * 32)
 #pragma unroll
     for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, dof, q[s]);
     const float tau = step_threshold(cs, q0, q1, W, dof);
-    const ProjResult pr = project_warp<WPL>(rb, cs, q, W, tau, fr);
+    const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau, fr);
     __syncwarp();
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid) {
@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kValidateWarps * 32)
 }
 
 // One thread per configuration: damped steps until ||E_task||_inf < tol_task.
+template <int CT>
 __global__ void project_configs_kernel(RobotDev rb, ConsDev cs, const float* __restrict__ q_in,
                                        int n, int max_iters, float* q_out, uint8_t* ok,
                                        float* resid) {
@@ -81,28 +82,47 @@ __global__ void project_configs_kernel(RobotDev rb, ConsDev cs, const float* __r
   float q[kMaxDof];
 #pragma unroll
   for (int k = 0; k < kMaxDof; ++k) q[k] = k < dof ? q_in[(size_t)m * dof + k] : 0.f;
-  TaskEval t;
+  ChainState s;
   int success = 0;
   float err = 0.f;
   for (int it = 0; it <= max_iters; ++it) {
-    chain<true>(rb, cs, q, nullptr, t);
-    err = task_err_inf(t);
+    chain(rb, q, nullptr, s);
+    const Task<CT> t = task_error<CT>(rb, cs, s);
+    err = task_err_inf<CT>(t);
     if (err < cs.tol_task) {
       success = 1;
       break;
     }
     if (it == max_iters) break;
-    float g[kMaxDof];
-    damped_step(rb, cs, t, g);
+    float y0, y1;
+    damped_solve<CT>(rb, cs, s, t, y0, y1);
 #pragma unroll
-    for (int k = 0; k < kMaxDof; ++k)
-      if (k < dof) q[k] = fminf(fmaxf(fmaf(-cs.alpha, g[k], q[k]), rb.j[k].lo), rb.j[k].hi);
+    for (int k = 0; k < kMaxDof; ++k) {
+      if (k < dof) {
+        float j0, j1;
+        jac_entry<CT>(rb, s, t, k, j0, j1);
+        const float g = fmaf(j0, y0, j1 * y1);
+        q[k] = fminf(fmaxf(fmaf(-cs.alpha, g, q[k]), rb.j[k].lo), rb.j[k].hi);
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < kMaxDof; ++k)
     if (k < dof) q_out[(size_t)m * dof + k] = q[k];
   if (ok) ok[m] = (uint8_t)success;
   if (resid) resid[m] = err;
+}
+
+static const void* validate_fn(int ct, int W) {
+  const bool two = W > 32;
+  switch (ct) {
+    case kConsRollPitch:
+      return two ? (const void*)validate_kernel<kConsRollPitch, 2> : (const void*)validate_kernel<kConsRollPitch, 1>;
+    case kConsZPlane:
+      return two ? (const void*)validate_kernel<kConsZPlane, 2> : (const void*)validate_kernel<kConsZPlane, 1>;
+    default:
+      return two ? (const void*)validate_kernel<kConsNone, 2> : (const void*)validate_kernel<kConsNone, 1>;
+  }
 }
 
 size_t validate_smem_bytes(const RobotDev& rb, const SceneDev& sc, int W, bool stage_obs) {
@@ -121,7 +141,7 @@ cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDe
   a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
   if (!a.stage_obs) smem = validate_smem_bytes(rb, sc, a.W, false);
   if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-  const void* fn = a.W <= 32 ? (const void*)validate_kernel<1> : (const void*)validate_kernel<2>;
+  const void* fn = validate_fn(cs.type, a.W);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -131,10 +151,10 @@ cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDe
   const long long need = (a.n + kValidateWarps - 1) / kValidateWarps;
   const long long cap = (long long)per_sm * dev.sm_count;
   const int grid = (int)(need < cap ? need : cap);
-  if (a.W <= 32)
-    validate_kernel<1><<<grid, kValidateWarps * 32, smem, stream>>>(rb, sc, cs, a);
-  else
-    validate_kernel<2><<<grid, kValidateWarps * 32, smem, stream>>>(rb, sc, cs, a);
+  void* args[] = {const_cast<RobotDev*>(&rb), const_cast<SceneDev*>(&sc),
+                  const_cast<ConsDev*>(&cs), &a};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(kValidateWarps * 32), args, smem, stream);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -143,8 +163,11 @@ cudaError_t launch_project_configs(const RobotDev& rb, const ConsDev& cs, const 
                                    float* resid, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   const int block = 128;
-  project_configs_kernel<<<(n + block - 1) / block, block, 0, stream>>>(rb, cs, q_in, n, max_iters,
-                                                                       q_out, ok, resid);
+  const int grid = (n + block - 1) / block;
+  if (cs.type == kConsZPlane)
+    project_configs_kernel<kConsZPlane><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
+  else
+    project_configs_kernel<kConsRollPitch><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
   return cudaGetLastError();
 }
 

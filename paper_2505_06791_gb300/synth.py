@@ -169,6 +169,45 @@ def make_scene(seed: int, n_sph: int = 16, n_box: int = 0, n_cap: int = 0,
     return Scene(f32(sph), f32(box), f32(cap))
 
 
+# Planning workspace around the arm, and the keep-out cylinder around its base (robot
+# mount): obstacle centres are drawn outside it.
+WORK_LO = np.array([-1.5, -1.5, 0.0])
+WORK_HI = np.array([1.5, 1.5, 1.8])
+BASE_KEEPOUT = 0.35
+
+
+def make_planning_scene(seed: int, n_sph: int = 100, n_box: int = 60, n_cap: int = 40,
+                        lo=WORK_LO, hi=WORK_HI, keepout: float = BASE_KEEPOUT) -> Scene:
+    """Mixed obstacles for one planning problem: centres uniform in the workspace box,
+    redrawn while within `keepout` (m, horizontal) of the base axis."""
+    rng = np.random.default_rng(seed)
+    sc = make_scene(int(rng.integers(1 << 31)), n_sph, n_box, n_cap, lo=lo, hi=hi)
+
+    def centre_ok(c):
+        return math.hypot(c[0], c[1]) >= keepout
+
+    def redraw(arr, centre_fn, move):
+        for i in range(len(arr)):
+            while not centre_ok(centre_fn(arr[i])):
+                move(arr, i, rng.uniform(lo, hi) - centre_fn(arr[i]))
+
+    def mv_sph(a, i, d):
+        a[i, :3] += d
+
+    def mv_box(a, i, d):
+        a[i, :3] += d
+
+    def mv_cap(a, i, d):
+        a[i, :3] += d
+        a[i, 3:6] += d
+
+    sph, box, cap = sc.sph.copy(), sc.box.copy(), sc.cap.copy()
+    redraw(sph, lambda r: r[:3], mv_sph)
+    redraw(box, lambda r: r[:3], mv_box)
+    redraw(cap, lambda r: (r[:3] + r[3:6]) / 2, mv_cap)
+    return Scene(f32(sph), f32(box), f32(cap))
+
+
 def make_mixed_scene(seed: int, n_sph: int = 100, n_box: int = 60, n_cap: int = 40) -> Scene:
     """Mixed primitives: spheres r U[0.05,0.15], oriented boxes with sides U[0.05,0.3],
     capsules with length U[0.1,0.4] and radius U[0.02,0.08]."""

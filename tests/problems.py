@@ -1,0 +1,68 @@
+"""Seeded planning problems for tests: per-problem mixed scenes (synth) and start/goal pairs
+drawn uniformly, projected onto the manifold and kept when collision-free, both decided by
+the oracle. Inputs only: the same arrays go to the CUDA path and to the oracle."""
+import numpy as np
+
+from paper_2505_06791_gb300 import synth as S
+
+
+def planning_problems(oracle_mod, robot, constraint, n, seed, counts=(100, 60, 40),
+                      clearance=1e-3):
+    scenes, starts, goals = [], [], []
+    p = 0
+    attempt = 0
+    while p < n:
+        sc = S.make_planning_scene(seed + 7919 * attempt + p, *counts)
+        orc = oracle_mod.Oracle(robot, sc, constraint)
+        found = []
+        for q in S.uniform_configs(robot, 60, seed + 104729 * attempt + p):
+            if constraint.type != 0:
+                ok, q, _, _ = orc.project_config(q, max_iters=60)
+                if not ok:
+                    continue
+            if orc.config_clearance(q) > clearance:
+                found.append(q)
+            if len(found) == 2:
+                break
+        if len(found) < 2:
+            attempt += 1
+            continue
+        scenes.append(sc)
+        starts.append(found[0])
+        goals.append(found[1])
+        p += 1
+    return scenes, S.f32(np.array(starts)), S.f32(np.array(goals))
+
+
+def check_paths(oracle_mod, robot, constraint, scenes, start, goal, out, W, range_,
+                problems=None, slack=2e-6, contact=1e-5):
+    """Re-validates every returned path with the oracle; returns (#checked, list of issues)."""
+    to_np = lambda x: x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)  # noqa
+    L = to_np(out["path_len"])
+    path = to_np(out["path"])
+    edges = to_np(out["path_edges"])
+    issues, checked = [], 0
+    tau = max(constraint.c_sm * range_ / (W - 1), constraint.tau_floor)
+    for p in (range(len(L)) if problems is None else problems):
+        n = int(L[p])
+        if n <= 0:
+            continue
+        checked += 1
+        orc = oracle_mod.Oracle(robot, scenes[p], constraint)
+        P = path[p, :n].astype(np.float64)
+        if not (np.array_equal(path[p, 0], start[p].astype(np.float32)) and
+                np.array_equal(path[p, n - 1], goal[p].astype(np.float32))):
+            issues.append((p, "endpoints"))
+        for j in range(n - 1):
+            E = edges[p, j].astype(np.float64)
+            if np.abs(E[0] - P[j]).max() > 1e-6 or np.abs(E[-1] - P[j + 1]).max() > 1e-6:
+                issues.append((p, j, "edge does not join its nodes"))
+                continue
+            t, s_, c = orc.check_segment(E, tau)
+            if constraint.type != 0 and t >= constraint.tol_task + slack:
+                issues.append((p, j, "off manifold", t))
+            if s_ >= constraint.tol_sm + slack:
+                issues.append((p, j, "discontinuous", s_))
+            if c <= -contact:
+                issues.append((p, j, "collision", c))
+    return checked, issues

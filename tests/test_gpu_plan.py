@@ -1,0 +1,135 @@
+"""GPU RRT-Connect (cprrtc_plan) through the C ABI: every returned path is re-validated by
+the FP64 oracle, runs are deterministic for a seed, and the device Philox4x32-10 matches the
+oracle's bit for bit."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2505_06791_gb300 import synth as S
+from tests import problems as PB
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_06791_gb300 import build
+    build.build()
+    return torch
+
+
+def ctx_for(robot, constraint):
+    from paper_2505_06791_gb300.capi import Context
+    ctx = Context(0)
+    ctx.set_robot(robot)
+    ctx.set_constraint(constraint)
+    return ctx
+
+
+def test_philox_matches_oracle(torch_cuda, oracle_mod):
+    ctx = ctx_for(S.make_arm7(1), S.roll_pitch())
+    gold = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    for line in open(gold):
+        f = line.split()
+        ctr = np.array([[int(x, 16) for x in f[2:6]]], np.uint32)
+        key = [int(x, 16) for x in f[6:8]]
+        assert ctx.philox(key[0], key[1], ctr)[0].tolist() == [int(x, 16) for x in f[8:12]]
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(100_000, 4), dtype=np.uint64).astype(np.uint32)
+    out = ctx.philox(12345, 678, ctr)
+    for i in range(0, 100_000, 997):
+        assert out[i].tolist() == oracle_mod.philox4x32_10(ctr[i].tolist(), [12345, 678])
+    ctx.close()
+
+
+def run_plan(torch, ctx, scenes, start, goal, params):
+    if scenes is not None:
+        ctx.set_scene_batch(scenes)
+    s = torch.from_numpy(start.astype(np.float32)).cuda()
+    g = torch.from_numpy(goal.astype(np.float32)).cuda()
+    out = ctx.plan(s, g, params)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def test_plan_roll_pitch_paths_are_valid_and_deterministic(torch_cuda, oracle_mod):
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 12, 900)
+    ctx = ctx_for(rb, c)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=300, workers=8, seed=7)
+    out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
+    again = run_plan(torch_cuda, ctx, None, start, goal, prm)
+    for k in ("path_len", "path", "rounds", "waypoints"):
+        assert np.array_equal(out[k], again[k]), k
+    L = out["path_len"]
+    assert (L >= 0).all()
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
+    assert not issues, issues[:10]
+    # the oracle's planner, same problems and seed (trees differ with FP32 vs FP64 decisions)
+    ref = oracle_mod.Oracle(rb, scenes[0], c)
+    solved_ref = 0
+    for p in range(len(scenes)):
+        ref.set_scene(scenes[p])
+        r = ref.plan(start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=300,
+                     n_workers=8, max_connect=32, seed=7)
+        solved_ref += int(r["path_len"][0] > 0)
+    print("gpu solved", int((L > 0).sum()), "oracle solved", solved_ref, "checked", checked)
+    assert checked == int((L > 0).sum())
+    assert (L > 0).sum() >= max(1, solved_ref // 2)
+    assert (out["waypoints"] % 32 == 0).all() and (out["waypoints"] > 0).all()
+    assert (out["plan_ms"] > 0).all()
+    ctx.close()
+
+
+def test_plan_unconstrained_shared_scene(torch_cuda, oracle_mod):
+    rb, c = S.make_arm7(2), S.no_constraint()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 1, 950, counts=(40, 20, 10))
+    n = 6
+    start = np.repeat(start, n, 0)
+    goal = np.repeat(goal, n, 0)
+    ctx = ctx_for(rb, c)
+    ctx.set_obstacles(scenes[0])
+    prm = ctx.plan_params(range_=0.4, W=16, max_rounds=200, workers=4, seed=3,
+                          use_scene_batch=False)
+    out = run_plan(torch_cuda, ctx, None, start, goal, prm)
+    assert (out["path_len"] > 0).sum() >= 1
+    checked, issues = PB.check_paths(oracle_mod, rb, c, [scenes[0]] * n, start, goal, out, 16, 0.4)
+    assert not issues, issues[:10]
+    ctx.close()
+
+
+def test_plan_z_plane_eight_dof_w64(torch_cuda, oracle_mod):
+    rb, c = S.make_arm8(3), S.z_plane(0.9)
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 4, 970, counts=(30, 15, 10))
+    ctx = ctx_for(rb, c)
+    prm = ctx.plan_params(range_=0.3, W=64, max_rounds=150, workers=4, seed=11, max_path=600)
+    out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 64, 0.3)
+    assert not issues, issues[:10]
+    print("z-plane solved", checked)
+    ctx.close()
+
+
+def test_plan_argument_errors(torch_cuda, oracle_mod):
+    from paper_2505_06791_gb300 import capi
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    ctx = ctx_for(rb, c)
+    q = np.zeros((2, 7), np.float32)
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.plan(q, q, ctx.plan_params(use_scene_batch=True))   # no scene batch set
+    assert e.value.code == capi.E_NOT_CONFIGURED
+    ctx.set_scene_batch([S.Scene(), S.Scene()])
+    for bad in (dict(W=1), dict(W=65), dict(workers=0), dict(workers=17), dict(max_path=1),
+                dict(max_nodes=1), dict(range_=0.0)):
+        with pytest.raises(capi.CprrtcError) as e:
+            ctx.plan(q, q, ctx.plan_params(**bad))
+        assert e.value.code == capi.E_INVALID_ARG, bad
+    # start == goal in an empty scene, unconstrained: connects in the first round
+    ctx.set_constraint(S.no_constraint())
+    out = ctx.plan(q, q, ctx.plan_params(W=8, workers=2))
+    assert (out["path_len"] >= 2).all()
+    ctx.close()

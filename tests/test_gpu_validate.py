@@ -40,7 +40,7 @@ def manifold_starts(orc, robot, n, seed):
     return S.f32(np.array(out))
 
 
-def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.9):
+def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.8):
     ctx = make_ctx(robot, scene, c)
     dq0 = torch.from_numpy(q0.astype(np.float32)).cuda()
     dq1 = torch.from_numpy(q1.astype(np.float32)).cuda()
