@@ -151,7 +151,7 @@ def manifold_starts_gpu(ctx, rb, n, seed):
 
 
 PLAN_N = 1000
-PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=200, workers=8, max_nodes=2048,
+PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=1000, workers=8, max_nodes=2048,
                    max_connect=32, max_path=512)
 
 
@@ -592,8 +592,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="plan", choices=["plan", "validate"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
+    ap.add_argument("--max-rounds", type=int, default=None,
+                    help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
+    if args.max_rounds is not None:
+        PLAN_PARAMS["max_rounds"] = args.max_rounds
     world, rank, local = init_dist()
     if args.impl == "reference":
         fn = reference_arm_plan if args.workload == "plan" else reference_arm

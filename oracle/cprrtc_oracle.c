@@ -550,21 +550,24 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * extend the same tree from the new node toward its nearest node in the other tree.
  *
  * Round structure (reading; the paper runs many extensions at once, one per thread block):
- * in each round, n_workers extensions are attempted, each against the trees as they stood
- * when the round began; the nodes each worker adds are appended at the end of the round in
- * worker order, and the lowest-numbered worker that connects the trees ends the problem.
- *   - worker w in round r extends tree a = (r + w) mod 2 toward a sample drawn from
- *     Philox4x32-10 with counter {problem, r, w, draw} and key {seed, 0}; each 32-bit output
- *     x gives u = (x >> 8) * 2^-24 and q_k = lo_k + u_k (hi_k - lo_k);
- *   - q_near = nearest node (L2, lowest index on ties); q_steer = q_near moved toward the
- *     sample by at most `range` (L2);
- *   - the motion q_near -> q_steer is validated with waypoint 0 skipped; if valid, its end
- *     q_end (the end is free under projection) joins tree a with parent q_near;
- *   - greedy connect: target = nearest node of tree b to q_end; repeat: if
- *     ||cur - target||_inf <= tau_floor * 10 (the connect radius), the closing hop
- *     cur -> target must be valid as it stands (Alg. 1 with one iteration, then CC) and the
- *     trees are connected; otherwise, at most max_connect times, steer cur toward target,
- *     validate, and keep the new end only if it is valid and strictly closer (L2).
+ * n_workers workers each validate one motion per round, against the trees as they stood
+ * when the round began. Each worker carries a chain across rounds:
+ *   - EXTEND: tree a = (round + w) mod 2; a sample from Philox4x32-10 with counter
+ *     {problem, round, w, draw} and key {seed, 0} (each 32-bit output x gives
+ *     u = (x >> 8) * 2^-24, q_k = lo_k + u_k (hi_k - lo_k)); q_near = nearest node (L2, lowest
+ *     index on ties); q_steer = q_near moved toward the sample by at most `range` (L2); the
+ *     motion q_near -> q_steer is validated with waypoint 0 skipped. A valid end q_end (the
+ *     end is free under projection) becomes a node with parent q_near, and the chain's
+ *     target becomes the nearest node of the other tree.
+ *   - CONNECT: steer from the chain's last node toward the target; the projected end becomes
+ *     a node only if the motion is valid and the end is strictly closer (L2) to the target.
+ *   - HOP: once the last node is within 10 * tau_floor (inf-norm) of the target, the closing
+ *     motion must be valid as it stands (Alg. 1 with one iteration, then CC); then the trees
+ *     are connected.
+ *   After a new node the chain continues with HOP if in reach, else CONNECT (at most
+ *   max_connect CONNECT motions per chain); a rejected motion returns the worker to EXTEND.
+ * The nodes of a round are appended in worker order (dropped beyond max_nodes, which ends
+ * that chain), and the lowest worker that connected ends the problem.
  * ======================================================================================== */
 
 typedef struct {
@@ -636,6 +639,15 @@ static int motion_ok(const plan_env* env, const orc_constraint* c, const double*
   return 1;
 }
 
+typedef struct {
+  int mode;          /* 0 EXTEND, 1 CONNECT, 2 HOP */
+  int tree, last, target, steps;
+  double cur[ORC_MAX_DOF], qt[ORC_MAX_DOF];
+  /* this round */
+  int add, conn;
+  double qe[ORC_MAX_DOF];
+} worker_state;
+
 static int plan_one(const plan_env* env, const double* start, const double* goal,
                     uint32_t problem, int max_path, double* path, int* rounds_used,
                     long long* waypoints) {
@@ -651,12 +663,7 @@ static int plan_one(const plan_env* env, const double* start, const double* goal
   }
   memcpy(T[0].nodes, start, sizeof(double) * n);
   memcpy(T[1].nodes, goal, sizeof(double) * n);
-  /* per-worker pending nodes: config, tree, parent (>= 0 tree index, < 0 pending -(j+1)) */
-  const int pend_cap = 1 + pp->max_connect;
-  double* pend = (double*)malloc(sizeof(double) * pp->n_workers * pend_cap * n);
-  int* pend_parent = (int*)malloc(sizeof(int) * pp->n_workers * pend_cap);
-  int* pend_count = (int*)calloc(pp->n_workers, sizeof(int));
-  int* pend_tree = (int*)calloc(pp->n_workers, sizeof(int));
+  worker_state* ws = (worker_state*)calloc(pp->n_workers, sizeof(worker_state));
   double xi[ORC_MAX_W * ORC_MAX_DOF];
   double* centres = (double*)malloc(sizeof(double) * 3 * (env->rb->n_spheres + 1));
   orc_constraint hop = *env->c;
@@ -665,91 +672,105 @@ static int plan_one(const plan_env* env, const double* start, const double* goal
   long long wp = 0;
   int path_len = 0;
 
-  for (int r = 0; r < pp->max_rounds && path_len == 0; ++r) {
-    int count0[2] = {T[0].count, T[1].count};
-    int win_w = -1, win_target = -1;
+  for (int r = 0; r < pp->max_rounds; ++r) {
+    const int count0[2] = {T[0].count, T[1].count};
+    int win = -1;
     for (int w = 0; w < pp->n_workers; ++w) {
-      int a = (r + w) & 1, b = 1 - a;
-      double* P = pend + (size_t)w * pend_cap * n;
-      int* PP = pend_parent + w * pend_cap;
-      pend_count[w] = 0;
-      pend_tree[w] = a;
-      double q_rand[ORC_MAX_DOF], q_s[ORC_MAX_DOF], q_e[ORC_MAX_DOF];
-      sample_config(env->rb, problem, (uint32_t)r, (uint32_t)w, pp->seed, q_rand);
-      int near = nearest(&T[a], count0[a], q_rand, n);
-      steer(T[a].nodes + near * n, q_rand, pp->range, n, q_s);
-      if (!motion_ok(env, env->c, T[a].nodes + near * n, q_s, q_e, xi, centres, &wp)) continue;
-      memcpy(P, q_e, sizeof(double) * n);
-      PP[0] = near;
-      pend_count[w] = 1;
-      /* greedy connect toward the nearest node of the other tree */
-      int target = nearest(&T[b], count0[b], q_e, n);
-      const double* tq = T[b].nodes + target * n;
-      int steps = 0;
-      for (;;) {
-        const double* cur = P + (pend_count[w] - 1) * n;
-        double gap = 0.0;
-        for (int k = 0; k < n; ++k) gap = fmax(gap, fabs(cur[k] - tq[k]));
-        if (gap <= connect_radius) {
-          if (motion_ok(env, &hop, cur, tq, q_e, xi, centres, &wp)) {
-            win_w = w;
-            win_target = target;
-          }
-          break;
-        }
-        if (steps >= pp->max_connect) break;
-        ++steps;
-        steer(cur, tq, pp->range, n, q_s);
-        if (!motion_ok(env, env->c, cur, q_s, q_e, xi, centres, &wp)) break;
-        if (!(dist2(q_e, tq, n) < dist2(cur, tq, n))) break;
-        if (pend_count[w] >= pend_cap) break;
-        memcpy(P + pend_count[w] * n, q_e, sizeof(double) * n);
-        PP[pend_count[w]] = -pend_count[w]; /* parent = pending entry pend_count-1 */
-        pend_count[w]++;
+      worker_state* s = &ws[w];
+      double q1[ORC_MAX_DOF];
+      s->add = 0;
+      s->conn = 0;
+      if (s->mode == 0) {
+        double q_rand[ORC_MAX_DOF];
+        s->tree = (r + w) & 1;
+        sample_config(env->rb, problem, (uint32_t)r, (uint32_t)w, pp->seed, q_rand);
+        s->last = nearest(&T[s->tree], count0[s->tree], q_rand, n);
+        memcpy(s->cur, T[s->tree].nodes + s->last * n, sizeof(double) * n);
+        steer(s->cur, q_rand, pp->range, n, q1);
+      } else if (s->mode == 1) {
+        steer(s->cur, s->qt, pp->range, n, q1);
+      } else {
+        memcpy(q1, s->qt, sizeof(double) * n);
       }
-      if (win_w >= 0) break;
+      double q_end[ORC_MAX_DOF];
+      if (!motion_ok(env, s->mode == 2 ? &hop : env->c, s->cur, q1, q_end, xi, centres, &wp))
+        continue;
+      if (s->mode == 2) {
+        s->conn = 1;
+        if (win < 0) win = w;
+        continue;
+      }
+      int accept = 1;
+      if (s->mode == 0) {
+        const orc_tree* tb = &T[s->tree ^ 1];
+        s->target = nearest(tb, count0[s->tree ^ 1], q_end, n);
+        memcpy(s->qt, tb->nodes + s->target * n, sizeof(double) * n);
+      } else {
+        accept = dist2(q_end, s->qt, n) < dist2(s->cur, s->qt, n);
+      }
+      if (accept) {
+        s->add = 1;
+        memcpy(s->qe, q_end, sizeof(double) * n);
+      }
     }
     *rounds_used = r + 1;
-    if (win_w >= 0) {
-      /* chain: root_a .. near, pending..., target .. root_b */
-      int a = pend_tree[win_w], b = 1 - a;
-      int near = pend_parent[win_w * pend_cap];
-      int len_a = 0;
-      for (int v = near; v >= 0; v = T[a].parent[v]) ++len_a;
-      int len_b = 0;
-      for (int v = win_target; v >= 0; v = T[b].parent[v]) ++len_b;
-      int total = len_a + pend_count[win_w] + len_b;
+    if (win >= 0) {
+      /* root_a .. last, target .. root_b; reversed when tree a is the goal tree */
+      const worker_state* s = &ws[win];
+      const int a = s->tree, b = a ^ 1;
+      int len_a = 0, len_b = 0;
+      for (int v = s->last; v >= 0; v = T[a].parent[v]) ++len_a;
+      for (int v = s->target; v >= 0; v = T[b].parent[v]) ++len_b;
+      const int total = len_a + len_b;
       if (total > max_path) {
         path_len = -total;
         break;
       }
       double* seq = (double*)malloc(sizeof(double) * total * n);
       int pos = len_a - 1;
-      for (int v = near; v >= 0; v = T[a].parent[v], --pos)
+      for (int v = s->last; v >= 0; v = T[a].parent[v], --pos)
         memcpy(seq + pos * n, T[a].nodes + v * n, sizeof(double) * n);
       pos = len_a;
-      for (int j = 0; j < pend_count[win_w]; ++j, ++pos)
-        memcpy(seq + pos * n, pend + ((size_t)win_w * pend_cap + j) * n, sizeof(double) * n);
-      for (int v = win_target; v >= 0; v = T[b].parent[v], ++pos)
+      for (int v = s->target; v >= 0; v = T[b].parent[v], ++pos)
         memcpy(seq + pos * n, T[b].nodes + v * n, sizeof(double) * n);
       for (int j = 0; j < total; ++j) {
-        int src = (a == 0) ? j : total - 1 - j;
+        const int src = (a == 0) ? j : total - 1 - j;
         memcpy(path + j * n, seq + src * n, sizeof(double) * n);
       }
       free(seq);
       path_len = total;
       break;
     }
-    /* append pending nodes in worker order */
+    /* append this round's nodes in worker order; advance each chain */
     for (int w = 0; w < pp->n_workers; ++w) {
-      orc_tree* t = &T[pend_tree[w]];
-      int base = t->count;
-      for (int j = 0; j < pend_count[w]; ++j) {
-        if (t->count >= cap) break;
-        int pp_ = pend_parent[w * pend_cap + j];
-        memcpy(t->nodes + t->count * n, pend + ((size_t)w * pend_cap + j) * n, sizeof(double) * n);
-        t->parent[t->count] = pp_ >= 0 ? pp_ : base + (-pp_ - 1);
-        t->count++;
+      worker_state* s = &ws[w];
+      int stored = -1;
+      if (s->add) {
+        orc_tree* t = &T[s->tree];
+        if (t->count < cap) {
+          stored = t->count;
+          memcpy(t->nodes + stored * n, s->qe, sizeof(double) * n);
+          t->parent[stored] = s->last;
+          t->count++;
+        }
+      }
+      if (stored >= 0) {
+        s->last = stored;
+        memcpy(s->cur, s->qe, sizeof(double) * n);
+        double gap = 0.0;
+        for (int k = 0; k < n; ++k) gap = fmax(gap, fabs(s->cur[k] - s->qt[k]));
+        if (gap <= connect_radius) {
+          s->mode = 2;
+        } else if (s->steps < pp->max_connect) {
+          s->mode = 1;
+          s->steps++;
+        } else {
+          s->mode = 0;
+          s->steps = 0;
+        }
+      } else {
+        s->mode = 0;
+        s->steps = 0;
       }
     }
   }
@@ -758,10 +779,7 @@ static int plan_one(const plan_env* env, const double* start, const double* goal
     free(T[t].nodes);
     free(T[t].parent);
   }
-  free(pend);
-  free(pend_parent);
-  free(pend_count);
-  free(pend_tree);
+  free(ws);
   free(centres);
   return path_len;
 }

@@ -363,6 +363,33 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
     loc[i] = make_float4((float)s.x, (float)s.y, (float)s.z, (float)s.r);
     frm[i] = s.frame;
   }
+  // Bounding sphere of each frame's spheres, from the FP32 values the kernels use: centre at
+  // the middle of their bounding box, radius max(|c - b| + r) padded by 1e-5 m and rounded
+  // up, so a miss of the bound proves a miss of every sphere under FP32 evaluation.
+  for (int f = 0; f <= CPRRTC_MAX_DOF; ++f) rb.bound[f] = make_float4(0.f, 0.f, 0.f, -1.f);
+  for (int f = 0; f <= dof; ++f) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    bool any = false;
+    for (int i = 0; i < n_spheres; ++i) {
+      if (frm[i] != f) continue;
+      any = true;
+      const double c[3] = {loc[i].x, loc[i].y, loc[i].z};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], c[k]);
+        hi[k] = std::max(hi[k], c[k]);
+      }
+    }
+    if (!any) continue;
+    const float b[3] = {(float)(0.5 * (lo[0] + hi[0])), (float)(0.5 * (lo[1] + hi[1])),
+                        (float)(0.5 * (lo[2] + hi[2]))};
+    double R = 0.0;
+    for (int i = 0; i < n_spheres; ++i) {
+      if (frm[i] != f) continue;
+      const double dx = (double)loc[i].x - b[0], dy = (double)loc[i].y - b[1], dz = (double)loc[i].z - b[2];
+      R = std::max(R, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)loc[i].w);
+    }
+    rb.bound[f] = make_float4(b[0], b[1], b[2], std::nextafter((float)(R + 1e-5), 1e30f));
+  }
   DeviceGuard g(ctx->device);
   size_t cap1 = 0, cap2 = 0;
   if (ctx->d_spheres) { cudaFree(ctx->d_spheres); ctx->d_spheres = nullptr; }
@@ -533,13 +560,13 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   if (!start || !goal || !path_len || !path) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: null pointer");
   DeviceGuard g(ctx->device);
   const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
-  const size_t B = (size_t)pp->workers, PC = (size_t)pp->max_connect + 2, MN = (size_t)pp->max_nodes;
+  const size_t B = (size_t)pp->workers, MN = (size_t)pp->max_nodes;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t b_nodes = al(N * 2 * MN * 8 * sizeof(float));
   const size_t b_parent = al(N * 2 * MN * sizeof(int));
   const size_t b_edges = al(N * 2 * MN * W * dof * sizeof(float));
-  const size_t b_pend = al(N * B * PC * 8 * sizeof(float));
-  const size_t b_pedge = al(N * B * PC * W * dof * sizeof(float));
+  const size_t b_pend = al(N * B * 8 * sizeof(float));
+  const size_t b_pedge = al(N * B * 2 * W * dof * sizeof(float));
   const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
   if (need > ctx->plan_cap) {
     if (ctx->d_plan) cudaFree(ctx->d_plan);

@@ -29,6 +29,9 @@ struct RobotDev {
   int n_spheres;
   JointDev j[kMaxDof];
   float ee[3];
+  // bounding sphere of each frame's robot spheres {centre in that frame, radius + 1e-5 m};
+  // radius -1 for a frame without spheres
+  float4 bound[kMaxDof + 1];
   const float4* spheres;     // [n_spheres] {x, y, z, r} in the sphere's frame, sorted by frame
   const int* sphere_frame;   // [n_spheres] frame index, 0 = base
 };

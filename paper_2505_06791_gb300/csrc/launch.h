@@ -44,8 +44,8 @@ struct PlanArgs {
   float* nodes;             // [n][2][max_nodes][8]
   int* parent;              // [n][2][max_nodes]
   float* edges;             // [n][2][max_nodes][W][dof]
-  float* pend;              // [n][workers][max_connect + 2][8]
-  float* pend_edges;        // [n][workers][max_connect + 2][W][dof]
+  float* pend;              // [n][workers][8] node a warp produced this round
+  float* pend_edges;        // [n][workers][2][W][dof] its motion, and the closing hop
   int32_t* path_len;
   float* path;
   float* path_edges;

@@ -8,10 +8,10 @@
 // Every lane evaluates its waypoints in every iteration (a frozen waypoint reproduces the
 // same values), so the loop has no divergence; only waypoints after `prog` commit.
 //
-// Collision checking walks the waypoints in order with the lanes spread over the robot's
-// spheres. The first waypoint with any penetrating pair ends the walk: the warp-wide vote
-// plays the role of the paper's shared collision flag, checked every few primitives, and
-// the index it reports is the smallest colliding waypoint whatever the lane timing.
+// Collision checking walks the waypoints in order (see collide_warp). The first waypoint
+// with any penetrating pair ends the walk: the warp-wide vote plays the role of the paper's
+// shared collision flag, and the index it reports is the smallest colliding waypoint
+// whatever the lane timing.
 #pragma once
 #include "collide.cuh"
 #include "kinematics.cuh"
@@ -147,70 +147,140 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
   return res;
 }
 
-// World centre of robot sphere `s` at the waypoint whose frames start at `fw`.
-__device__ __forceinline__ void sphere_world(const float4 loc, int frame, const float* fw,
-                                             float& cx, float& cy, float& cz) {
-  if (frame == 0) {
-    cx = loc.x; cy = loc.y; cz = loc.z;
+// World position of a point given in the frame whose 12 floats {x, y, z, p} start at f
+// (frame 0, the base, is the identity: f == nullptr).
+__device__ __forceinline__ void to_world(const float* f, float lx, float ly, float lz,
+                                         float& cx, float& cy, float& cz) {
+  if (!f) {
+    cx = lx; cy = ly; cz = lz;
     return;
   }
-  const float* f = fw + (frame - 1) * kFrameFloats;
-  cx = fmaf(f[0], loc.x, fmaf(f[3], loc.y, fmaf(f[6], loc.z, f[9])));
-  cy = fmaf(f[1], loc.x, fmaf(f[4], loc.y, fmaf(f[7], loc.z, f[10])));
-  cz = fmaf(f[2], loc.x, fmaf(f[5], loc.y, fmaf(f[8], loc.z, f[11])));
+  cx = fmaf(f[0], lx, fmaf(f[3], ly, fmaf(f[6], lz, f[9])));
+  cy = fmaf(f[1], lx, fmaf(f[4], ly, fmaf(f[7], lz, f[10])));
+  cz = fmaf(f[2], lx, fmaf(f[5], ly, fmaf(f[8], lz, f[11])));
 }
 
-// Primitives tested between two votes on the warp's collision flag.
-constexpr int kVoteEvery = 8;
+// Per-warp shared-memory scratch of the collision walk.
+struct CcScratch {
+  const float4* bnd;  // [dof + 1] frame bounding spheres, local coordinates (shared by the CTA)
+  float4* wsph;       // [S] world centre + radius of each robot sphere at the current waypoint
+  float4* wbnd;       // [dof + 1] world centre + padded radius of each frame's bounding sphere
+};
+
+// Shared-memory layout of the motion kernels, in bytes from the dynamic shared base:
+//   obstacles (staged only when they fit) | robot spheres | frame bounds | sphere frames |
+//   per warp: world spheres, world bounds, frame cache | extra (kernel-specific, 16-aligned)
+struct SmemLayout {
+  size_t obs, sph, bnd, sfr, warp0, warp_bytes, wsph, wbnd, frames, extra, total;
+  __host__ __device__ SmemLayout(int stage_f4, int S, int dof, int W, int warps,
+                                 size_t extra_bytes) {
+    auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+    obs = 0;
+    sph = al(obs + (size_t)stage_f4 * 16);
+    bnd = al(sph + (size_t)S * 16);
+    sfr = al(bnd + (size_t)(kMaxDof + 1) * 16);
+    warp0 = al(sfr + (size_t)S * 4);
+    wsph = 0;
+    wbnd = al(wsph + (size_t)S * 16);
+    frames = al(wbnd + (size_t)(kMaxDof + 1) * 16);
+    warp_bytes = al(frames + (size_t)W * (kFrameFloats * dof + 1) * 4);
+    extra = al(warp0 + (size_t)warps * warp_bytes);
+    total = extra + extra_bytes;
+  }
+};
+
+// Stages robot spheres, their frames and the frame bounds into shared memory.
+__device__ __forceinline__ void stage_robot(const RobotDev& rb, char* base, const SmemLayout& L) {
+  float4* sph = reinterpret_cast<float4*>(base + L.sph);
+  float4* bnd = reinterpret_cast<float4*>(base + L.bnd);
+  int* sfr = reinterpret_cast<int*>(base + L.sfr);
+  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) {
+    sph[i] = rb.spheres[i];
+    sfr[i] = rb.sphere_frame[i];
+  }
+#pragma unroll
+  for (int f = 0; f <= kMaxDof; ++f)
+    if (threadIdx.x == f) bnd[f] = rb.bound[f];
+}
+
+// Tests obstacle o (index into the sphere / box / capsule ranges) against ball (c, r).
+__device__ __forceinline__ bool hit_obstacle(const SceneDev& sc, const float4* __restrict__ obs,
+                                             int o, float cx, float cy, float cz, float r) {
+  if (o < sc.n_sph) return hit_sphere(cx, cy, cz, r, obs[o]);
+  o -= sc.n_sph;
+  if (o < sc.n_box) {
+    const float4* b = obs + sc.n_sph + 4 * o;
+    return hit_box(cx, cy, cz, r, b[0], b[1], b[2], b[3]);
+  }
+  o -= sc.n_box;
+  const float4* k = obs + sc.n_sph + 4 * sc.n_box + 2 * o;
+  return hit_capsule(cx, cy, cz, r, k[0], k[1]);
+}
 
 // FK + CC of waypoints [i0, W) in order; returns the first colliding waypoint or -1.
-// sph/sfr: robot spheres (shared memory), obs: obstacle stream (shared or global).
+//
+// Two levels per waypoint, exact: each lane takes one obstacle of a 32-obstacle chunk and
+// tests it against the bounding sphere of every frame's robot spheres (radius padded by
+// 1e-5 m, far above the FP32 error of either test, so a miss there proves every sphere of
+// that frame misses). Only the (obstacle, frame) pairs that survive are tested sphere by
+// sphere, lanes over the robot's spheres. The warp-wide vote after each such obstacle
+// plays the role of the paper's shared collision flag (Sec. IV).
 __device__ __forceinline__ int collide_warp(const RobotDev& rb, const SceneDev& sc,
                                             const float4* __restrict__ obs,
                                             const float4* sph, const int* sfr, int W, int i0,
-                                            const float* fr) {
+                                            const float* fr, CcScratch cc) {
   const int lane = threadIdx.x & 31;
-  const int fs = frame_stride(rb.dof);
+  const int dof = rb.dof;
+  const int fs = frame_stride(dof);
   const int S = rb.n_spheres;
-  const float4* box = obs + sc.n_sph;
-  const float4* cap = box + 4 * sc.n_box;
+  const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
   for (int i = i0; i < W; ++i) {
     const float* fw = fr + i * fs;
-    bool hit = false;
-    for (int s = lane; s - lane < S; s += 32) {
-      const bool act = s < S;
-      float cx = 0.f, cy = 0.f, cz = 0.f, r = 0.f;
-      if (act) {
-        const float4 loc = sph[s];
-        sphere_world(loc, sfr[s], fw, cx, cy, cz);
-        r = loc.w;
-      }
-      for (int o0 = 0; o0 < sc.n_sph; o0 += kVoteEvery) {
-        const int o1 = min(o0 + kVoteEvery, sc.n_sph);
-#pragma unroll 4
-        for (int o = o0; o < o1; ++o) hit |= act && hit_sphere(cx, cy, cz, r, obs[o]);
-        if (__any_sync(kFull, hit)) break;
-      }
-      if (__any_sync(kFull, hit)) break;
-      for (int o0 = 0; o0 < sc.n_box; o0 += kVoteEvery) {
-        const int o1 = min(o0 + kVoteEvery, sc.n_box);
-#pragma unroll 2
-        for (int o = o0; o < o1; ++o)
-          hit |= act && hit_box(cx, cy, cz, r, box[4 * o], box[4 * o + 1], box[4 * o + 2],
-                                box[4 * o + 3]);
-        if (__any_sync(kFull, hit)) break;
-      }
-      if (__any_sync(kFull, hit)) break;
-      for (int o0 = 0; o0 < sc.n_cap; o0 += kVoteEvery) {
-        const int o1 = min(o0 + kVoteEvery, sc.n_cap);
-#pragma unroll 2
-        for (int o = o0; o < o1; ++o)
-          hit |= act && hit_capsule(cx, cy, cz, r, cap[2 * o], cap[2 * o + 1]);
-        if (__any_sync(kFull, hit)) break;
-      }
-      if (__any_sync(kFull, hit)) break;
+    if (lane <= dof) {
+      const float4 b = cc.bnd[lane];
+      float x, y, z;
+      to_world(lane == 0 ? nullptr : fw + (lane - 1) * kFrameFloats, b.x, b.y, b.z, x, y, z);
+      cc.wbnd[lane] = make_float4(x, y, z, b.w);
     }
-    if (__any_sync(kFull, hit)) return i;
+    for (int s = lane; s < S; s += 32) {
+      const float4 l = sph[s];
+      const int f = sfr[s];
+      float x, y, z;
+      to_world(f == 0 ? nullptr : fw + (f - 1) * kFrameFloats, l.x, l.y, l.z, x, y, z);
+      cc.wsph[s] = make_float4(x, y, z, l.w);
+    }
+    __syncwarp();
+    bool hit = false;
+    for (int base = 0; base < n_obs && !hit; base += 32) {
+      const int o = base + lane;
+      unsigned mask = 0u;
+      if (o < n_obs) {
+        for (int f = 0; f <= dof; ++f) {
+          const float4 b = cc.wbnd[f];
+          if (b.w >= 0.f && hit_obstacle(sc, obs, o, b.x, b.y, b.z, b.w)) mask |= 1u << f;
+        }
+      }
+      unsigned cand = __ballot_sync(kFull, mask != 0u);
+      while (cand) {
+        const int src = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int oo = base + src;
+        const unsigned m = __shfl_sync(kFull, mask, src);
+        bool h = false;
+        for (int s = lane; s < S; s += 32) {
+          if ((m >> sfr[s]) & 1u) {
+            const float4 c = cc.wsph[s];
+            h |= hit_obstacle(sc, obs, oo, c.x, c.y, c.z, c.w);
+          }
+        }
+        if (__any_sync(kFull, h)) {
+          hit = true;
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if (hit) return i;
   }
   return -1;
 }

@@ -1,15 +1,17 @@
 // RRT-Connect with constrained motions (Sec. III, Sec. II): one CTA per planning problem,
-// one warp per tree extension.
+// one warp per tree extension, one motion per warp per round.
 //
-// Each round, every warp w extends tree a = (round + w) mod 2 toward a Philox sample
-// (counter {problem, round, w, draw}, key {seed, 0}): nearest node, steer by at most
-// `range`, validate the motion (Alg. 1 + FK + CC, waypoint 0 skipped), then greedily
-// extends the same tree from the new node toward its nearest node in the other tree while
-// each projected motion is valid and ends strictly closer. Within 10 * tau_floor (inf-norm)
-// of that node, the closing hop must be valid as it stands (one Alg. 1 iteration + CC) and
-// the trees are connected. Warps work against the trees as they stood when the round
-// began; their new nodes are appended in warp order after a barrier, and the lowest warp
-// that connected returns the path. The search is therefore deterministic for a seed.
+// Each warp carries an extension chain across rounds: mode EXTEND picks tree
+// a = (round + w) mod 2, draws a Philox sample (counter {problem, round, w, draw}, key
+// {seed, 0}), steers from its nearest node by at most `range` and validates the motion
+// (Alg. 1 + FK + CC, waypoint 0 skipped); a valid end becomes a node and the chain turns to
+// the nearest node of the other tree (the target). Mode CONNECT steers toward the target
+// and keeps the projected end only if it is strictly closer; within 10 * tau_floor
+// (inf-norm) of the target, mode HOP checks the closing motion as it stands (one Alg. 1
+// iteration + CC) and a valid hop connects the trees. Warps read the trees as they stood at
+// the start of the round; the nodes of a round are appended in warp order after a barrier,
+// and the lowest warp that connected returns the path. One motion per round keeps the
+// barrier wait short; the search is deterministic for a seed.
 //
 // Trees live in global memory (nodes padded to 8 floats, parent indices, and each node's
 // projected incoming motion, so that returned paths are dense). The problem's obstacles
@@ -22,10 +24,10 @@ namespace cprrtc {
 
 struct PlanShared {
   int count0[2];               // tree sizes when the round began
-  int pcount[kMaxWorkers];     // nodes each warp added this round
-  int ptree[kMaxWorkers];
-  int pnear[kMaxWorkers];      // tree index of the first added node's parent
-  int ptarget[kMaxWorkers];    // nearest node of the other tree (connect target)
+  int padd[kMaxWorkers];       // 1 if the warp produced a node this round
+  int ptree[kMaxWorkers];      // the warp's chain tree
+  int pparent[kMaxWorkers];    // parent of the produced node (the chain's last node)
+  int ptarget[kMaxWorkers];    // the chain's target in the other tree
   int pconn[kMaxWorkers];      // 1 if the warp connected the trees
   long long wp[kMaxWorkers];   // waypoints validated by each warp
   long long wproj[kMaxWorkers];
@@ -158,7 +160,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
                                                const float4* obs, const float4* sph,
                                                const int* sfr, const float* q0,
                                                const float* q1, int W, float* fr,
-                                               float (&q)[WPL][kMaxDof]) {
+                                               const CcScratch& cc, float (&q)[WPL][kMaxDof]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
@@ -167,7 +169,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
   __syncwarp();
   work.proj += (long long)pr.iters * (W - 1);
   if (pr.status != kValid) return kProjFail;
-  const int ff = collide_warp(rb, sc, obs, sph, sfr, W, 1, fr);
+  const int ff = collide_warp(rb, sc, obs, sph, sfr, W, 1, fr, cc);
   __syncwarp();
   work.cc += ff >= 0 ? ff : W - 1;
   return ff >= 0 ? kCollision : kValid;
@@ -190,51 +192,46 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
     sc.n_box = d.z;
     sc.n_cap = d.w;
   }
-  extern __shared__ float4 smem[];
+  extern __shared__ __align__(16) char smem[];
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, dof, W, B,
+                     sizeof(PlanShared));
   const int n4 = sc.n_float4();
-  float4* s_obs = smem;
-  float4* s_sph = smem + (a.stage_obs ? a.max_scene_f4 : 0);
-  int* s_sfr = reinterpret_cast<int*>(s_sph + rb.n_spheres);
-  float* s_fr = reinterpret_cast<float*>(s_sfr + ((rb.n_spheres + 3) & ~3));
-  // PlanShared holds 64-bit counters: place it on a 16-byte boundary (as sized on the host)
-  PlanShared* sh = reinterpret_cast<PlanShared*>(
-      (reinterpret_cast<uintptr_t>(s_fr + (size_t)B * W * frame_stride(dof)) + 15) & ~uintptr_t(15));
+  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
   if (a.stage_obs)
     for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
-  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) {
-    s_sph[i] = rb.spheres[i];
-    s_sfr[i] = rb.sphere_frame[i];
-  }
+  stage_robot(rb, smem, L);
+  const float4* s_sph = reinterpret_cast<const float4*>(smem + L.sph);
+  const int* s_sfr = reinterpret_cast<const int*>(smem + L.sfr);
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
-  float* fr = s_fr + (size_t)warp * W * frame_stride(dof);
+  char* wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+  float* fr = reinterpret_cast<float*>(wbase + L.frames);
+  const CcScratch cc{reinterpret_cast<const float4*>(smem + L.bnd),
+                     reinterpret_cast<float4*>(wbase + L.wsph),
+                     reinterpret_cast<float4*>(wbase + L.wbnd)};
+  PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
 
-  const size_t tree_stride = (size_t)a.max_nodes;
-  float* nodes[2];
-  int* parent[2];
-  float* edges[2];
-  for (int t = 0; t < 2; ++t) {
-    nodes[t] = a.nodes + ((size_t)p * 2 + t) * tree_stride * 8;
-    parent[t] = a.parent + ((size_t)p * 2 + t) * tree_stride;
-    edges[t] = a.edges + ((size_t)p * 2 + t) * tree_stride * W * dof;
-  }
-  const int PC = a.max_connect + 2;  // pending slots: extension + connect nodes + hop edge
-  float* pnode = a.pend + ((size_t)p * B + warp) * PC * 8;
-  float* pedge = a.pend_edges + ((size_t)p * B + warp) * PC * W * dof;
+  const size_t wd = (size_t)W * dof;
+  const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
+  // tree t of this problem (computed, not tabulated: a table indexed by t lives in local memory)
+  auto nodes = [&](int t) { return a.nodes + (tree0 + (size_t)t * a.max_nodes) * 8; };
+  auto parent = [&](int t) { return a.parent + tree0 + (size_t)t * a.max_nodes; };
+  auto edges = [&](int t) { return a.edges + (tree0 + (size_t)t * a.max_nodes) * wd; };
+  float* wnode = a.pend + ((size_t)p * B + warp) * 8;              // node produced this round
+  float* wedge = a.pend_edges + ((size_t)p * B + warp) * 2 * wd;   // its motion, then the hop
 
   if (warp == 0) {
     float q[kMaxDof];
     load_cfg(a.start + (size_t)p * dof, dof, q);
-    store_cfg(nodes[0], q, dof);
+    store_cfg(nodes(0), q, dof);
     load_cfg(a.goal + (size_t)p * dof, dof, q);
-    store_cfg(nodes[1], q, dof);
+    store_cfg(nodes(1), q, dof);
     if (lane == 0) {
-      parent[0][0] = -1;
-      parent[1][0] = -1;
+      parent(0)[0] = -1;
+      parent(1)[0] = -1;
       sh->count0[0] = 1;
       sh->count0[1] = 1;
     }
   }
-  if (lane == 0) sh->wp[warp] = 0;
   __syncthreads();
 
   ConsDev hop = cs;
@@ -243,70 +240,63 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
   long long wp = 0;
   MotionWork work{0, 0};
   int rounds_used = 0, win = -1;
+  // chain state (warp-uniform): 0 extend, 1 connect, 2 closing hop
+  int mode = 0, ta = 0, last = 0, target = -1, steps = 0;
+  float cur[kMaxDof], qt[kMaxDof];
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) cur[k] = qt[k] = 0.f;
   for (int r = 0; r < a.max_rounds; ++r) {
-    const int ta = (r + warp) & 1, tb = ta ^ 1;
-    const int ca = sh->count0[ta], cb = sh->count0[tb];
-    // sample
-    float qr[kMaxDof];
-    {
+    float q1[kMaxDof];
+    if (mode == 0) {
+      ta = (r + warp) & 1;
       const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 0u}, a.seed, 0u);
       const U32x4 u1 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 1u}, a.seed, 0u);
       const uint32_t w8[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      float qr[kMaxDof];
 #pragma unroll
       for (int k = 0; k < kMaxDof; ++k)
-        if (k < dof) qr[k] = fmaf(u24(w8[k]), rb.j[k].hi - rb.j[k].lo, rb.j[k].lo);
+        qr[k] = k < dof ? fmaf(u24(w8[k]), rb.j[k].hi - rb.j[k].lo, rb.j[k].lo) : 0.f;
+      last = nearest_warp(nodes(ta), sh->count0[ta], qr, dof);
+      load_cfg(nodes(ta) + (size_t)last * 8, dof, cur);
+      steer(cur, qr, a.range, dof, q1);
+    } else if (mode == 1) {
+      steer(cur, qt, a.range, dof, q1);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k) q1[k] = qt[k];
     }
-    const int near = nearest_warp(nodes[ta], ca, qr, dof);
-    float cur[kMaxDof], q1[kMaxDof], qt[kMaxDof];
-    load_cfg(nodes[ta] + (size_t)near * 8, dof, cur);
-    steer(cur, qr, a.range, dof, q1);
-    // One validation call site: mode 0 = extension toward the sample, 1 = greedy connect
-    // step toward qt, 2 = closing hop onto qt (one Alg. 1 iteration, i.e. as it stands).
-    int mode = 0, k = 0, conn = 0, target = -1, steps = 0;
-    while (true) {
-      float q[WPL][kMaxDof];
-      const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, obs, s_sph, s_sfr,
-                                              cur, q1, W, fr, q);
-      wp += W;
-      if (st != kValid) break;
+    float q[WPL][kMaxDof];
+    const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, obs, s_sph,
+                                            s_sfr, cur, q1, W, fr, cc, q);
+    wp += W;
+    int add = 0, conn = 0;
+    float qe[kMaxDof];
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) qe[k] = cur[k];
+    if (st == kValid) {
       if (mode == 2) {
         conn = 1;
-        store_edge<WPL>(pedge + (size_t)k * W * dof, q, W, dof);
-        break;
-      }
-      float qe[kMaxDof];
-      last_waypoint<WPL>(q, W, dof, qe);
-      if (mode == 0) {
-        target = nearest_warp(nodes[tb], cb, qe, dof);
-        load_cfg(nodes[tb] + (size_t)target * 8, dof, qt);
-      } else if (!(dist2(qe, qt, dof) < dist2(cur, qt, dof))) {
-        break;
-      }
-      store_cfg(pnode + (size_t)k * 8, qe, dof);
-      store_edge<WPL>(pedge + (size_t)k * W * dof, q, W, dof);
-      ++k;
-#pragma unroll
-      for (int j = 0; j < kMaxDof; ++j) cur[j] = qe[j];
-      // next motion: the closing hop when within reach, else one more connect step
-      float gap = 0.f;
-#pragma unroll
-      for (int j = 0; j < kMaxDof; ++j)
-        if (j < dof) gap = fmaxf(gap, fabsf(cur[j] - qt[j]));
-      if (gap <= connect_radius) {
-        mode = 2;
-#pragma unroll
-        for (int j = 0; j < kMaxDof; ++j) q1[j] = qt[j];
+        store_edge<WPL>(wedge + wd, q, W, dof);
       } else {
-        if (steps >= a.max_connect) break;
-        ++steps;
-        mode = 1;
-        steer(cur, qt, a.range, dof, q1);
+        last_waypoint<WPL>(q, W, dof, qe);
+        bool accept = true;
+        if (mode == 0) {
+          target = nearest_warp(nodes(ta ^ 1), sh->count0[ta ^ 1], qe, dof);
+          load_cfg(nodes(ta ^ 1) + (size_t)target * 8, dof, qt);
+        } else {
+          accept = dist2(qe, qt, dof) < dist2(cur, qt, dof);
+        }
+        if (accept) {
+          add = 1;
+          store_cfg(wnode, qe, dof);
+          store_edge<WPL>(wedge, q, W, dof);
+        }
       }
     }
     if (lane == 0) {
-      sh->pcount[warp] = k;
+      sh->padd[warp] = add;
       sh->ptree[warp] = ta;
-      sh->pnear[warp] = near;
+      sh->pparent[warp] = last;
       sh->ptarget[warp] = target;
       sh->pconn[warp] = conn;
     }
@@ -320,29 +310,51 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
       }
     if (win >= 0) break;
     // append this round's nodes in warp order
-    {
-      const int base = sh->count0[ta];
+    int dst = -1;
+    if (add) {
       int off = 0;
       for (int w = 0; w < warp; ++w)
-        if (sh->ptree[w] == ta) off += sh->pcount[w];
-      for (int j = 0; j < k; ++j) {
-        const int dst = base + off + j;
-        if (dst >= a.max_nodes) break;
-        copy_warp(nodes[ta] + (size_t)dst * 8, pnode + (size_t)j * 8, 8);
-        copy_warp(edges[ta] + (size_t)dst * W * dof, pedge + (size_t)j * W * dof, W * dof);
-        if (lane == 0) parent[ta][dst] = j == 0 ? near : dst - 1;
+        if (sh->padd[w] && sh->ptree[w] == ta) ++off;
+      dst = sh->count0[ta] + off;
+      if (dst < a.max_nodes) {
+        copy_warp(nodes(ta) + (size_t)dst * 8, wnode, 8);
+        copy_warp(edges(ta) + (size_t)dst * wd, wedge, (int)wd);
+        if (lane == 0) parent(ta)[dst] = last;
+      } else {
+        dst = -1;
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int t = 0; t < 2; ++t) {
-        int add = 0;
-        for (int w = 0; w < B; ++w)
-          if (sh->ptree[w] == t) add += sh->pcount[w];
-        sh->count0[t] = min(sh->count0[t] + add, a.max_nodes);
+        int n_add = 0;
+        for (int w = 0; w < B; ++w) n_add += sh->padd[w] && sh->ptree[w] == t;
+        sh->count0[t] = min(sh->count0[t] + n_add, a.max_nodes);
       }
     }
     __syncthreads();
+    // next motion of the chain
+    if (dst >= 0) {
+      last = dst;
+      float gap = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k) {
+        cur[k] = qe[k];
+        if (k < dof) gap = fmaxf(gap, fabsf(cur[k] - qt[k]));
+      }
+      if (gap <= connect_radius) {
+        mode = 2;
+      } else if (steps < a.max_connect) {
+        mode = 1;
+        ++steps;
+      } else {
+        mode = 0;
+        steps = 0;
+      }
+    } else {
+      mode = 0;
+      steps = 0;
+    }
   }
   if (lane == 0) {
     sh->wp[warp] = wp;
@@ -351,36 +363,38 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
   }
 
   if (win >= 0 && warp == win) {
-    // path: root_a .. near, added nodes, target .. root_b; reversed when tree a is the goal tree
-    const int ta = sh->ptree[win], tb = ta ^ 1;
-    const int near = sh->pnear[win], k = sh->pcount[win], target = sh->ptarget[win];
+    // path: root_a .. last, closing hop, target .. root_b; reversed when tree a is the
+    // goal tree
+    const int tb = ta ^ 1;
     int len_a = 0, len_b = 0;
-    for (int v = near; v >= 0; v = parent[ta][v]) ++len_a;
-    for (int v = target; v >= 0; v = parent[tb][v]) ++len_b;
-    const int total = len_a + k + len_b;
+    for (int v = last; v >= 0; v = parent(ta)[v]) ++len_a;
+    for (int v = target; v >= 0; v = parent(tb)[v]) ++len_b;
+    const int total = len_a + len_b;
     const bool flip = ta == 1;
     float* path = a.path + (size_t)p * a.max_path * dof;
-    float* pe = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * W * dof : nullptr;
-    auto npos = [&](int pos) { return flip ? total - 1 - pos : pos; };
-    auto epos = [&](int e) { return flip ? total - 2 - e : e; };
+    float* pe = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
     if (total <= a.max_path) {
       int pos = len_a - 1;
-      for (int v = near; v >= 0; v = parent[ta][v], --pos) {
-        copy_warp(path + (size_t)npos(pos) * dof, nodes[ta] + (size_t)v * 8, dof);
-        if (pe && parent[ta][v] >= 0)  // edge pos-1 -> pos is v's incoming motion
-          copy_edge(pe + (size_t)epos(pos - 1) * W * dof, edges[ta] + (size_t)v * W * dof, W, dof, flip);
+      for (int v = last; v >= 0; v = parent(ta)[v], --pos) {
+        const int np = flip ? total - 1 - pos : pos;
+        copy_warp(path + (size_t)np * dof, nodes(ta) + (size_t)v * 8, dof);
+        if (pe && parent(ta)[v] >= 0) {  // edge pos-1 -> pos is v's incoming motion
+          const int e = flip ? total - 1 - pos : pos - 1;
+          copy_edge(pe + (size_t)e * wd, edges(ta) + (size_t)v * wd, W, dof, flip);
+        }
       }
-      for (int j = 0; j < k; ++j) {
-        copy_warp(path + (size_t)npos(len_a + j) * dof, pnode + (size_t)j * 8, dof);
-        if (pe) copy_edge(pe + (size_t)epos(len_a - 1 + j) * W * dof, pedge + (size_t)j * W * dof, W, dof, flip);
+      if (pe) {  // closing hop: last -> target
+        const int e = flip ? total - 1 - len_a : len_a - 1;
+        copy_edge(pe + (size_t)e * wd, wedge + wd, W, dof, flip);
       }
-      if (pe)  // closing hop: last added node -> target
-        copy_edge(pe + (size_t)epos(len_a + k - 1) * W * dof, pedge + (size_t)k * W * dof, W, dof, flip);
-      pos = len_a + k;
-      for (int v = target; v >= 0; v = parent[tb][v], ++pos) {
-        copy_warp(path + (size_t)npos(pos) * dof, nodes[tb] + (size_t)v * 8, dof);
-        if (pe && parent[tb][v] >= 0)  // edge pos -> pos+1 is v's incoming motion reversed
-          copy_edge(pe + (size_t)epos(pos) * W * dof, edges[tb] + (size_t)v * W * dof, W, dof, !flip);
+      pos = len_a;
+      for (int v = target; v >= 0; v = parent(tb)[v], ++pos) {
+        const int np = flip ? total - 1 - pos : pos;
+        copy_warp(path + (size_t)np * dof, nodes(tb) + (size_t)v * 8, dof);
+        if (pe && parent(tb)[v] >= 0) {  // edge pos -> pos+1 is v's incoming motion reversed
+          const int e = flip ? total - 2 - pos : pos;
+          copy_edge(pe + (size_t)e * wd, edges(tb) + (size_t)v * wd, W, dof, !flip);
+        }
       }
     }
     if (lane == 0) a.path_len[p] = total <= a.max_path ? total : -total;
@@ -419,14 +433,8 @@ static const void* plan_fn(int ct, int W) {
 }
 
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage) {
-  size_t b = 0;
-  if (stage) b += (size_t)max_scene_f4 * sizeof(float4);
-  b += (size_t)rb.n_spheres * sizeof(float4);
-  b += (size_t)((rb.n_spheres + 3) & ~3) * sizeof(int);
-  b += (size_t)workers * W * frame_stride(rb.dof) * sizeof(float);
-  b = (b + 15) & ~size_t(15);
-  b += sizeof(PlanShared);
-  return b;
+  return SmemLayout(stage ? max_scene_f4 : 0, rb.n_spheres, rb.dof, W, workers,
+                    sizeof(PlanShared)).total;
 }
 
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,

@@ -11,23 +11,24 @@ namespace cprrtc {
 // (No __launch_bounds__: with it, ptxas caps registers low enough to spill here.)
 template <int CT, int WPL>
 __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
-  extern __shared__ float4 smem[];
+  extern __shared__ __align__(16) char smem[];
   const int n4 = sc.n_float4();
-  float4* s_obs = smem;
-  float4* s_sph = smem + (a.stage_obs ? n4 : 0);
-  int* s_sfr = reinterpret_cast<int*>(s_sph + rb.n_spheres);
-  float* s_fr = reinterpret_cast<float*>(s_sfr + ((rb.n_spheres + 3) & ~3));
+  const SmemLayout L(a.stage_obs ? n4 : 0, rb.n_spheres, rb.dof, a.W, kValidateWarps, 0);
+  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
   if (a.stage_obs)
     for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
-  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) {
-    s_sph[i] = rb.spheres[i];
-    s_sfr[i] = rb.sphere_frame[i];
-  }
+  stage_robot(rb, smem, L);
   __syncthreads();
+  const float4* s_sph = reinterpret_cast<const float4*>(smem + L.sph);
+  const int* s_sfr = reinterpret_cast<const int*>(smem + L.sfr);
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dof = rb.dof, W = a.W;
-  float* fr = s_fr + warp * W * frame_stride(dof);
+  char* wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+  float* fr = reinterpret_cast<float*>(wbase + L.frames);
+  const CcScratch cc{reinterpret_cast<const float4*>(smem + L.bnd),
+                     reinterpret_cast<float4*>(wbase + L.wsph),
+                     reinterpret_cast<float4*>(wbase + L.wbnd)};
 
   for (int m = blockIdx.x * kValidateWarps + warp; m < a.n; m += gridDim.x * kValidateWarps) {
     float q0[kMaxDof], q1[kMaxDof];
@@ -46,7 +47,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     __syncwarp();
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid) {
-      ff = collide_warp(rb, sc, obs, s_sph, s_sfr, W, a.cc_skip_first, fr);
+      ff = collide_warp(rb, sc, obs, s_sph, s_sfr, W, a.cc_skip_first, fr, cc);
       if (ff >= 0) st = kCollision;
     }
     if (a.out_q) {
@@ -126,12 +127,7 @@ static const void* validate_fn(int ct, int W) {
 }
 
 size_t validate_smem_bytes(const RobotDev& rb, const SceneDev& sc, int W, bool stage_obs) {
-  size_t b = 0;
-  if (stage_obs) b += (size_t)sc.n_float4() * sizeof(float4);
-  b += (size_t)rb.n_spheres * sizeof(float4);
-  b += (size_t)((rb.n_spheres + 3) & ~3) * sizeof(int);
-  b += (size_t)kValidateWarps * W * frame_stride(rb.dof) * sizeof(float);
-  return b;
+  return SmemLayout(stage_obs ? sc.n_float4() : 0, rb.n_spheres, rb.dof, W, kValidateWarps, 0).total;
 }
 
 cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs,

@@ -60,7 +60,7 @@ def test_plan_roll_pitch_paths_are_valid_and_deterministic(torch_cuda, oracle_mo
     rb, c = S.make_arm7(1), S.roll_pitch()
     scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 12, 900)
     ctx = ctx_for(rb, c)
-    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=300, workers=8, seed=7)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=600, workers=8, seed=7)
     out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
     again = run_plan(torch_cuda, ctx, None, start, goal, prm)
     for k in ("path_len", "path", "rounds", "waypoints"):
@@ -70,13 +70,16 @@ def test_plan_roll_pitch_paths_are_valid_and_deterministic(torch_cuda, oracle_mo
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
     assert not issues, issues[:10]
     # the oracle's planner, same problems and seed (trees differ with FP32 vs FP64 decisions)
-    ref = oracle_mod.Oracle(rb, scenes[0], c)
-    solved_ref = 0
-    for p in range(len(scenes)):
-        ref.set_scene(scenes[p])
-        r = ref.plan(start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=300,
-                     n_workers=8, max_connect=32, seed=7)
-        solved_ref += int(r["path_len"][0] > 0)
+    import concurrent.futures as cf
+
+    def oracle_solves(p):
+        r = oracle_mod.Oracle(rb, scenes[p], c).plan(
+            start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=600, n_workers=8,
+            max_connect=32, seed=7)
+        return int(r["path_len"][0] > 0)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        solved_ref = sum(ex.map(oracle_solves, range(len(scenes))))
     print("gpu solved", int((L > 0).sum()), "oracle solved", solved_ref, "checked", checked)
     assert checked == int((L > 0).sum())
     assert (L > 0).sum() >= max(1, solved_ref // 2)
@@ -93,7 +96,7 @@ def test_plan_unconstrained_shared_scene(torch_cuda, oracle_mod):
     goal = np.repeat(goal, n, 0)
     ctx = ctx_for(rb, c)
     ctx.set_obstacles(scenes[0])
-    prm = ctx.plan_params(range_=0.4, W=16, max_rounds=200, workers=4, seed=3,
+    prm = ctx.plan_params(range_=0.4, W=16, max_rounds=600, workers=4, seed=3,
                           use_scene_batch=False)
     out = run_plan(torch_cuda, ctx, None, start, goal, prm)
     assert (out["path_len"] > 0).sum() >= 1
@@ -106,7 +109,7 @@ def test_plan_z_plane_eight_dof_w64(torch_cuda, oracle_mod):
     rb, c = S.make_arm8(3), S.z_plane(0.9)
     scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 4, 970, counts=(30, 15, 10))
     ctx = ctx_for(rb, c)
-    prm = ctx.plan_params(range_=0.3, W=64, max_rounds=150, workers=4, seed=11, max_path=600)
+    prm = ctx.plan_params(range_=0.3, W=64, max_rounds=400, workers=4, seed=11, max_path=600)
     out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 64, 0.3)
     assert not issues, issues[:10]
