@@ -226,6 +226,34 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
                 int64_t* work);
 
+/* ---- planning without allocation ---- */
+
+/* Size of the library's fixed device scratch for cprrtc_plan_static: 16 MiB, held by every
+ * GPU that loads the library until the process exits. */
+#define CPRRTC_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* cprrtc_plan for callers that must not allocate device memory while they run: a control
+ * loop that cannot absorb the latency and implicit device synchronisation of cudaMalloc,
+ * or a process whose device memory is all held by another allocator (a framework's caching
+ * pool). The paper has no counterpart; results are those of cprrtc_plan on the same
+ * arguments.
+ *  - It allocates nothing: the trees live in a file-scope device array of
+ *    CPRRTC_STATIC_SCRATCH_BYTES instead of library-allocated memory. Inputs and outputs
+ *    are the caller's and must all be device memory (host pointers: E_INVALID_ARG).
+ *  - Sizes beyond the array (n * 2 * max_nodes * (W * dof + 9) * 4 bytes plus
+ *    n * workers * (2 * W * dof + 8) * 4 bytes, each part rounded up to 256 bytes) are
+ *    rejected with E_CAPACITY.
+ *  - The first call on a device looks up the array's device address (once per device);
+ *    make that first call before any stream capture.
+ *  - Every call on a device shares the one array, whose contents persist between calls;
+ *    calls that overlap on the GPU (other streams, other host threads) race on it.
+ *  - Kernel timing (cprrtc_set_timing) does not cover this call.
+ * Errors: as cprrtc_plan, plus E_CAPACITY. */
+int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
+                       const cprrtc_plan_params* params, int32_t* path_len, float* path,
+                       float* path_edges, int32_t* rounds, int64_t* waypoints,
+                       float* plan_ms, int64_t* work);
+
 /* ---- counter-based random numbers ---- */
 
 /* Philox4x32-10 (Salmon et al., SC'11) of n counters [n][4] under key {key0, key1}, on the

@@ -73,6 +73,9 @@ _SIGS = {
     "cprrtc_plan": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                     C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_plan_static": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                           C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
     "cprrtc_set_timing": [C.c_void_p, C.c_int],
     "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
@@ -336,6 +339,13 @@ def cprrtc_plan(h, start, goal, n, params, path_len, path, path_edges, rounds, w
                              _ptr(plan_ms), _ptr(work))
 
 
+def cprrtc_plan_static(h, start, goal, n, params, path_len, path, path_edges, rounds,
+                       waypoints, plan_ms, work):
+    return lib().cprrtc_plan_static(h, _ptr(start), _ptr(goal), n, C.byref(params),
+                                    _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
+                                    _ptr(waypoints), _ptr(plan_ms), _ptr(work))
+
+
 def cprrtc_philox(h, key0, key1, counters, n, out):
     return lib().cprrtc_philox(h, key0, key1, _ptr(counters), n, _ptr(out))
 
@@ -351,4 +361,4 @@ def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
 
 
 __all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
-           "cprrtc_project_configs", "cprrtc_plan", "cprrtc_philox"]
+           "cprrtc_project_configs", "cprrtc_plan", "cprrtc_plan_static", "cprrtc_philox"]

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -677,3 +678,112 @@ int cprrtc_reset_timing(cprrtc_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---- planning from a fixed device array (no allocation) ----------------------------------
+//
+// The trees of cprrtc_plan_static live here, one array per device that loads the library.
+// Host code must not use the symbol as an address: the kernel receives the device address
+// looked up with cudaGetSymbolAddress, once per device.
+namespace {
+
+static __device__ __align__(256) unsigned char g_plan_scratch[CPRRTC_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of g_plan_scratch on `device` (which must be current); nullptr on error.
+void* static_scratch(int device, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (device < 0 || device >= kStaticMaxDevices) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[device]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_plan_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    g_static_ptr[device] = p;
+  }
+  return g_static_ptr[device];
+}
+
+}  // namespace
+
+extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
+                                  const cprrtc_plan_params* pp, int32_t* path_len, float* path,
+                                  float* path_edges, int32_t* rounds, int64_t* waypoints,
+                                  float* plan_ms, int64_t* work) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan_static: set_robot first");
+  if (!pp) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: null params");
+  if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: n < 0");
+  if (pp->W < 2 || pp->W > CPRRTC_MAX_W || !(pp->range > 0) || !is_finite(pp->range) ||
+      pp->max_rounds < 1 || pp->workers < 1 || pp->workers > kMaxWorkers || pp->max_nodes < 2 ||
+      pp->max_connect < 0 || pp->max_path < 2)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: bad parameters");
+  if (pp->use_scene_batch && ctx->n_scenes != n)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan_static: scene batch must hold one scene per problem");
+  if (n == 0) return CPRRTC_OK;
+  if (!start || !goal || !path_len || !path)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: null pointer");
+  DeviceGuard g(ctx->device);
+  const void* arrays[] = {start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work};
+  for (const void* a : arrays)
+    if (a && !is_device_ptr(a))
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: every array must be device memory");
+  const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
+  const size_t B = (size_t)pp->workers, MN = (size_t)pp->max_nodes;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t b_nodes = al(N * 2 * MN * 8 * sizeof(float));
+  const size_t b_parent = al(N * 2 * MN * sizeof(int));
+  const size_t b_edges = al(N * 2 * MN * W * dof * sizeof(float));
+  const size_t b_pend = al(N * B * 8 * sizeof(float));
+  const size_t b_pedge = al(N * B * 2 * W * dof * sizeof(float));
+  const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
+  if (need > (size_t)CPRRTC_STATIC_SCRATCH_BYTES)
+    return fail(ctx, CPRRTC_E_CAPACITY,
+                "plan_static: needs " + std::to_string(need) + " bytes of scratch, the fixed array holds " +
+                    std::to_string((size_t)CPRRTC_STATIC_SCRATCH_BYTES) +
+                    " (reduce n, max_nodes, W or workers)");
+  cudaError_t e;
+  char* base = static_cast<char*>(static_scratch(ctx->device, &e));
+  if (!base) return cuda_fail(ctx, e, "plan_static: cudaGetSymbolAddress");
+  PlanArgs a{};
+  a.start = start;
+  a.goal = goal;
+  a.n = n;
+  a.range = (float)pp->range;
+  a.W = pp->W;
+  a.max_rounds = pp->max_rounds;
+  a.workers = pp->workers;
+  a.max_nodes = pp->max_nodes;
+  a.max_connect = pp->max_connect;
+  a.max_path = pp->max_path;
+  a.seed = pp->seed;
+  if (pp->use_scene_batch) {
+    a.scene_obs = ctx->d_batch_obs;
+    a.scenes = ctx->d_batch_tab;
+    a.max_scene_f4 = ctx->max_scene_f4;
+  } else {
+    a.scene_obs = nullptr;
+    a.scenes = nullptr;
+    a.max_scene_f4 = ctx->sc.n_float4();
+  }
+  a.nodes = reinterpret_cast<float*>(base);
+  a.parent = reinterpret_cast<int*>(base + b_nodes);
+  a.edges = reinterpret_cast<float*>(base + b_nodes + b_parent);
+  a.pend = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges);
+  a.pend_edges = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges + b_pend);
+  a.path_len = path_len;
+  a.path = path;
+  a.path_edges = path_edges;
+  a.rounds = rounds;
+  a.waypoints = reinterpret_cast<long long*>(waypoints);
+  a.plan_ms = plan_ms;
+  a.work = reinterpret_cast<long long*>(work);
+  e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan_static launch");
+  return CPRRTC_OK;
+}
