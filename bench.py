@@ -66,6 +66,15 @@ def algorithmic_flops(dof, W, S_, scene_counts, status, first_fail, iters):
     return float(proj + cc_wp * flops_cc_waypoint(S_, *scene_counts)), int(cc_wp)
 
 
+def executed_flops(dof: int, counters) -> float:
+    """FLOPs of the work the kernels evaluated (cprrtc_work_counters): Alg. 1 waypoint
+    updates, DH chains of the collision check, points moved to world coordinates, and
+    ball-vs-primitive tests by primitive."""
+    upd, chains, tf, ps, pb, pc = [float(x) for x in counters]
+    return (upd * flops_waypoint_iter(dof) + chains * dof * F_CHAIN_JOINT + tf * F_SPHERE_FK
+            + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
+
+
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     """FP32 FMA-pipe peak: SMs x 128 lanes x 2 FLOP x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -234,6 +243,7 @@ def run_plan(args, world, rank, local):
         stream.synchronize()
         ctx.set_timing(True)
         ctx.reset_timing()
+        ctx.work_counters(reset=True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         clocks = ClockSampler(local)
@@ -250,6 +260,7 @@ def run_plan(args, world, rank, local):
         clk = clocks.stop()
         step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
         kms, launches = ctx.kernel_time("plan")
+        counters = ctx.work_counters() / max(args.steps, 1)
         ctx.set_timing(False)
     total_ms = max_over_ranks(sum(step_ms), world)
     L = out["path_len"].cpu().numpy()
@@ -259,7 +270,8 @@ def run_plan(args, world, rank, local):
     rounds = out["rounds"].cpu().numpy()
     waypoints_step = int(wp.sum())
     value = waypoints_step * args.steps * world / (total_ms / 1e3)
-    flops = plan_flops(rb.dof, scenes, len(rb.spheres), work)
+    nominal = plan_flops(rb.dof, scenes, len(rb.spheres), work)
+    flops = executed_flops(rb.dof, counters)
 
     # end to end through the C ABI with pinned host buffers
     h_start = start.cpu().pin_memory()
@@ -305,8 +317,17 @@ def run_plan(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "kernel": "plan_kernel",
                      "flop_per_launch": flops, "avg_launch_ms": avg_kernel_s * 1e3,
+                     "work_per_launch": {"alg1_updates": float(counters[0]),
+                                         "cc_chains": float(counters[1]),
+                                         "transforms": float(counters[2]),
+                                         "tests_sph_box_cap": [float(x) for x in counters[3:6]]},
                      "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"},
+                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
+                                  "counts; no measured FP32 peak)"},
+        "all_pairs_equivalent": {"flop_per_launch": nominal,
+                                 "tflops": nominal / avg_kernel_s / 1e12,
+                                 "note": "FLOPs a check of every robot sphere against every "
+                                         "obstacle would take for the same waypoints"},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -402,6 +423,7 @@ def run_validate(args, world, rank, local):
         stream.synchronize()
         ctx.set_timing(True)
         ctx.reset_timing()
+        ctx.work_counters(reset=True)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         clocks = ClockSampler(local)
@@ -418,13 +440,15 @@ def run_validate(args, world, rank, local):
         clk = clocks.stop()
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         kms, launches = ctx.kernel_time("validate")
+        counters = ctx.work_counters() / max(args.steps, 1)
         ctx.set_timing(False)
     total_ms = max_over_ranks(sum(step_ms), world)
     st = out["status"].cpu().numpy()
     ff = out["first_fail"].cpu().numpy()
     it = out["iters"].cpu().numpy()
-    flops, cc_wp = algorithmic_flops(rb.dof, W, len(rb.spheres),
-                                     (len(sc.sph), len(sc.box), len(sc.cap)), st, ff, it)
+    nominal, cc_wp = algorithmic_flops(rb.dof, W, len(rb.spheres),
+                                       (len(sc.sph), len(sc.box), len(sc.cap)), st, ff, it)
+    flops = executed_flops(rb.dof, counters)
     waypoints = n * W * args.steps * world
     value = waypoints / (total_ms / 1e3)
 
@@ -466,7 +490,10 @@ def run_validate(args, world, rank, local):
                      "kernel": "validate_kernel", "flop_per_launch": flops,
                      "avg_launch_ms": avg_kernel_s * 1e3,
                      "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"},
+                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
+                                  "counts; no measured FP32 peak)"},
+        "all_pairs_equivalent": {"flop_per_launch": nominal,
+                                 "tflops": nominal / avg_kernel_s / 1e12},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

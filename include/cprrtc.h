@@ -268,6 +268,15 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
  * count of the kernel named `name` ("validate", "project", "plan") since the last reset,
  * synchronising on the events. */
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
+
+/* Work the validate and plan kernels of this context evaluated since creation or the last
+ * reset, for throughput accounting (out has 6 entries): out[0] Alg. 1 waypoint updates (per
+ * iteration, the waypoints after prog), out[1] DH chains evaluated by collision checking
+ * (per checked waypoint and pass), out[2] points moved to world coordinates (frame bounding
+ * spheres and robot spheres), out[3..5] ball-vs-primitive tests against spheres, boxes and
+ * capsules (swept bounds, frame bounds and robot spheres together). Synchronises the
+ * context's stream; reset = 1 zeroes them. */
+int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);
 

@@ -78,6 +78,7 @@ _SIGS = {
                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
     "cprrtc_set_timing": [C.c_void_p, C.c_int],
+    "cprrtc_work_counters": [C.c_void_p, C.c_void_p, C.c_int],
     "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
                            C.POINTER(C.c_longlong)],
     "cprrtc_reset_timing": [C.c_void_p],
@@ -230,6 +231,13 @@ class Context:
         ms, n = C.c_double(), C.c_longlong()
         self._check(self._L.cprrtc_kernel_time(self.h, name.encode(), C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def work_counters(self, reset: bool = False) -> np.ndarray:
+        """[Alg. 1 updates, collision-check chains, world transforms, sphere tests, box tests,
+        capsule tests] since the last reset."""
+        out = np.zeros(6, np.int64)
+        self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
+        return out
 
     def reset_timing(self):
         self._check(self._L.cprrtc_reset_timing(self.h))

@@ -48,6 +48,8 @@ struct cprrtc_ctx {
   // planner trees and per-worker pending buffers
   char* d_plan = nullptr;
   size_t plan_cap = 0;
+  // executed-work totals (validate and plan kernels)
+  unsigned long long* d_work = nullptr;
   bool timing = false;
   std::vector<TimingRec> pending;
   std::map<std::string, std::pair<double, long long>> acc;
@@ -214,18 +216,22 @@ int upload(cprrtc_ctx* ctx, T** dst, size_t* cap, const std::vector<T>& src) {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
-// Packs obstacles into the float4 stream the kernels read: spheres {x,y,z,r}; boxes
-// {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0}; capsules {p0, r} {p1 - p0, 1/|p1-p0|^2}.
+// Packs obstacles into the float4 stream the kernels read, component arrays per primitive:
+// spheres [n] {x,y,z,r}; boxes 4 x [n]: {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0};
+// capsules 2 x [n]: {p0, r} {p1 - p0, 1/|p1-p0|^2}.
 int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
                    const cprrtc_obs_box* box, int n_box, const cprrtc_obs_capsule* cap, int n_cap,
                    std::vector<float4>& v) {
-  v.reserve(v.size() + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
+  const size_t s0 = v.size();
+  v.resize(s0 + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
+  float4* out = v.data() + s0;
   for (int i = 0; i < n_sph; ++i) {
     const cprrtc_obs_sphere& o = sph[i];
     if (!is_finite(o.x) || !is_finite(o.y) || !is_finite(o.z) || !is_finite(o.r) || o.r < 0)
       return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad sphere " + std::to_string(i));
-    v.push_back(make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r));
+    out[i] = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r);
   }
+  float4* bx = out + n_sph;
   for (int i = 0; i < n_box; ++i) {
     const cprrtc_obs_box& b = box[i];
     for (int k = 0; k < 3; ++k)
@@ -233,11 +239,12 @@ int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
         return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box " + std::to_string(i));
     for (int k = 0; k < 9; ++k)
       if (!is_finite(b.R[k])) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box rotation");
-    v.push_back(make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]));
-    v.push_back(make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]));
-    v.push_back(make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]));
-    v.push_back(make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f));
+    bx[i] = make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]);
+    bx[n_box + i] = make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]);
+    bx[2 * n_box + i] = make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]);
+    bx[3 * n_box + i] = make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f);
   }
+  float4* cp = bx + 4 * n_box;
   for (int i = 0; i < n_cap; ++i) {
     const cprrtc_obs_capsule& c = cap[i];
     for (int k = 0; k < 3; ++k)
@@ -246,8 +253,8 @@ int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
     if (!is_finite(c.r) || c.r < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad capsule radius");
     const double u[3] = {c.p1[0] - c.p0[0], c.p1[1] - c.p0[1], c.p1[2] - c.p0[2]};
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    v.push_back(make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r));
-    v.push_back(make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f));
+    cp[i] = make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r);
+    cp[n_cap + i] = make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f);
   }
   return CPRRTC_OK;
 }
@@ -279,6 +286,13 @@ int cprrtc_create(cprrtc_ctx** out, int device, void* stream) {
     return CPRRTC_E_CUDA;
   }
   ctx->dev.smem_optin = (size_t)smem;
+  if (cudaMalloc(&ctx->d_work, kWorkCounters * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->d_work, 0, kWorkCounters * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ctx->d_work);
+    delete ctx;
+    return CPRRTC_E_OOM;
+  }
   ctx->cs = ConsDev{kConsNone, 0.f, 1e-4f, 2.f, 1e-3f, 1e-4f, 1.f, 1e-6f, 20};
   ctx->sc = SceneDev{nullptr, 0, 0, 0};
   *out = ctx;
@@ -297,6 +311,7 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_batch_obs);
   cudaFree(ctx->d_batch_tab);
   cudaFree(ctx->d_plan);
+  cudaFree(ctx->d_work);
   for (auto& r : ctx->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -367,7 +382,13 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
   // Bounding sphere of each frame's spheres, from the FP32 values the kernels use: centre at
   // the middle of their bounding box, radius max(|c - b| + r) padded by 1e-5 m and rounded
   // up, so a miss of the bound proves a miss of every sphere under FP32 evaluation.
-  for (int f = 0; f <= CPRRTC_MAX_DOF; ++f) rb.bound[f] = make_float4(0.f, 0.f, 0.f, -1.f);
+  for (int f = 0; f <= CPRRTC_MAX_DOF; ++f) {
+    rb.bound[f] = make_float4(0.f, 0.f, 0.f, -1.f);
+    rb.n_per_frame[f] = 0;
+  }
+  for (int i = 0; i < n_spheres; ++i) rb.n_per_frame[frm[i]]++;
+  rb.bound_count = 0;
+  for (int f = 0; f <= dof; ++f) rb.bound_count += rb.n_per_frame[f] > 0;
   for (int f = 0; f <= dof; ++f) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     bool any = false;
@@ -498,6 +519,7 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
   a.n = n;
   a.W = W;
   a.cc_skip_first = 0;
+  a.work_counters = ctx->d_work;
   Staging st;
   st.input(q_start, N * dof * sizeof(float), &a.q_start);
   st.input(q_end, N * dof * sizeof(float), &a.q_end);
@@ -587,6 +609,7 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   a.max_connect = pp->max_connect;
   a.max_path = pp->max_path;
   a.seed = pp->seed;
+  a.work_counters = ctx->d_work;
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;
@@ -638,6 +661,18 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
   cudaError_t e = launch_philox(key0, key1, d_in, n, d_out, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "philox launch");
   return st.end(ctx);
+}
+
+int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset) {
+  if (!ctx || !out) return CPRRTC_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  unsigned long long h[kWorkCounters];
+  cudaError_t e = cudaMemcpyAsync(h, ctx->d_work, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(ctx->d_work, 0, sizeof(h), ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "work counters");
+  for (int i = 0; i < kWorkCounters; ++i) out[i] = (int64_t)h[i];
+  return CPRRTC_OK;
 }
 
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled) {

@@ -32,13 +32,16 @@ struct RobotDev {
   // bounding sphere of each frame's robot spheres {centre in that frame, radius + 1e-5 m};
   // radius -1 for a frame without spheres
   float4 bound[kMaxDof + 1];
+  int n_per_frame[kMaxDof + 1];  // robot spheres on each frame
+  int bound_count;               // frames with spheres
   const float4* spheres;     // [n_spheres] {x, y, z, r} in the sphere's frame, sorted by frame
   const int* sphere_frame;   // [n_spheres] frame index, 0 = base
 };
 
-// Obstacles as one float4 stream: spheres {x,y,z,rho}; boxes 4 x float4
-// {cx,cy,cz,hx} {col0, hy} {col1, hz} {col2, 0} where col_k is column k of R (box axis k);
-// capsules 2 x float4 {p0, rc} {u = p1 - p0, 1/|u|^2}.
+// Obstacles as one float4 stream, component arrays per primitive so that lanes reading
+// consecutive obstacles read consecutive float4s: spheres [n_sph] {x,y,z,rho}; boxes
+// 4 arrays of [n_box]: {cx,cy,cz,hx} {col0, hy} {col1, hz} {col2, 0} where col_k is column
+// k of R (box axis k); capsules 2 arrays of [n_cap]: {p0, rc} {u = p1 - p0, 1/|u|^2}.
 struct SceneDev {
   const float4* obs;
   int n_sph, n_box, n_cap;

@@ -9,6 +9,7 @@
 namespace cprrtc {
 
 constexpr int kValidateWarps = 4;  // warps (motions in flight) per CTA
+constexpr int kWorkCounters = 6;   // updates, chains, transforms, sphere / box / capsule tests
 
 struct DeviceInfo {
   int sm_count;
@@ -26,6 +27,7 @@ struct ValidateArgs {
   int32_t* first_fail;
   uint8_t* iters;
   float* resid;
+  unsigned long long* work_counters;  // [6] executed-work totals (may be null)
   int stage_obs;  // set by the launcher
 };
 
@@ -52,7 +54,8 @@ struct PlanArgs {
   int32_t* rounds;
   long long* waypoints;
   float* plan_ms;
-  long long* work;          // [n][2] Alg. 1 waypoint evaluations, collision-checked waypoints
+  long long* work;          // [n][2] Alg. 1 waypoint updates, collision-checked waypoints
+  unsigned long long* work_counters;  // [6] executed-work totals (may be null)
   int stage_obs;            // set by the launcher
 };
 

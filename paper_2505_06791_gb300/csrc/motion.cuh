@@ -18,10 +18,6 @@
 
 namespace cprrtc {
 
-// Floats per waypoint in the per-warp frame cache: 12 per frame 1..dof, plus one pad so
-// that consecutive waypoints fall in different shared-memory banks.
-__host__ __device__ inline int frame_stride(int dof) { return kFrameFloats * dof + 1; }
-
 // Interpolated waypoint i of q0 -> q1 (W waypoints): q0 + (i / (W-1)) (q1 - q0).
 __device__ __forceinline__ void interp(const float* q0, const float* q1, int i, int W, int dof,
                                        float* q) {
@@ -46,30 +42,59 @@ struct ProjResult {
   int iters;
   int first_fail;  // first unaccepted waypoint on failure
   float resid;     // max over waypoints 1..W-1 of the last evaluated ||E_task||_inf
+  int updates;     // waypoint updates Alg. 1 needed: sum over iterations of (W - 1 - prog)
+};
+
+// Work a warp evaluated, for roofline accounting (warp-uniform counts, per waypoint).
+struct WorkCount {
+  long long updates;     // Alg. 1 waypoint updates
+  long long chains;      // DH chains evaluated for collision checking
+  long long transforms;  // points moved to world coordinates (frame bounds, robot spheres)
+  long long p_sph, p_box, p_cap;  // ball-vs-primitive tests by primitive
+  __device__ __forceinline__ void add_type(const SceneDev& sc, int o, long long n) {
+    if (o < sc.n_sph)
+      p_sph += n;
+    else if (o < sc.n_sph + sc.n_box)
+      p_box += n;
+    else
+      p_cap += n;
+  }
+  // swept-bound tests of obstacles [lo, hi) against nb frame bounds
+  __device__ __forceinline__ void add_tests(const SceneDev& sc, int lo, int hi, int nb) {
+    const int c_s = max(0, min(hi, sc.n_sph) - lo);
+    const int c_b = max(0, min(hi, sc.n_sph + sc.n_box) - max(lo, sc.n_sph));
+    p_sph += (long long)nb * c_s;
+    p_box += (long long)nb * c_b;
+    p_cap += (long long)nb * (hi - lo - c_s - c_b);
+  }
+  __device__ __forceinline__ void count_test(const SceneDev& sc, int o, int n) { add_type(sc, o, n); }
+  __device__ __forceinline__ void count_fine(const SceneDev& sc, int o, int n) {
+    add_type(sc, o, n);
+    transforms += n;
+  }
+  __device__ void flush(unsigned long long* dst) const {
+    if (!dst || (threadIdx.x & 31) != 0) return;
+    atomicAdd(dst + 0, (unsigned long long)updates);
+    atomicAdd(dst + 1, (unsigned long long)chains);
+    atomicAdd(dst + 2, (unsigned long long)transforms);
+    atomicAdd(dst + 3, (unsigned long long)p_sph);
+    atomicAdd(dst + 4, (unsigned long long)p_box);
+    atomicAdd(dst + 5, (unsigned long long)p_cap);
+  }
 };
 
 // Alg. 1 on the warp's motion, constraint type CT, at most max_iters iterations.
 // q[WPL][kMaxDof] holds this lane's waypoints (the interpolated segment on entry, the
-// segment after the last iteration on exit). Frames of every waypoint's evaluation are
-// written to fr (stride frame_stride(dof)); on success they describe the returned segment.
-// With CT = kConsNone only the frames are computed.
+// segment after the last iteration on exit). With CT = kConsNone nothing is done.
 template <int CT, int WPL>
 __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const ConsDev& c,
                                                    int max_iters, float (&q)[WPL][kMaxDof],
-                                                   int W, float tau, float* fr) {
+                                                   int W, float tau) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
-  const int fs = frame_stride(dof);
-  ProjResult res{kValid, 0, -1, 0.f};
+  ProjResult res{kValid, 0, -1, 0.f, 0};
   ChainState cs;
-  if (CT == kConsNone) {
-#pragma unroll
-    for (int s = 0; s < WPL; ++s) {
-      const int i = lane + 32 * s;
-      if (i < W) chain(rb, q[s], fr + i * fs, cs);
-    }
-    return res;
-  }
+  if (CT == kConsNone) return res;
   // waypoints [0, W) as a 64-bit mask
   const unsigned long long in_range = (W >= 64) ? ~0ull : ((1ull << W) - 1ull);
   float last_err[WPL];
@@ -83,8 +108,8 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
     for (int s = 0; s < WPL; ++s) {
       const int i = lane + 32 * s;
       // every lane evaluates (lanes past W on a clamped copy) so that the shuffles below
-      // run converged; only in-range lanes write frames
-      chain(rb, q[s], i < W ? fr + i * fs : nullptr, cs);
+      // run converged
+      chain(rb, q[s], nullptr, cs);
       const Task<CT> t = task_error<CT>(rb, c, cs);
       float y0, y1;
       damped_solve<CT>(rb, c, cs, t, y0, y1);
@@ -113,6 +138,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
       if (i > prog && i < W) last_err[s] = et;
       valid_mask |= (unsigned long long)__ballot_sync(kFull, valid) << (32 * s);
     }
+    res.updates += W - 1 - prog;
     // acceptance: advance prog over the contiguous valid run after it
     const unsigned long long after = in_range & ~((2ull << prog) - 1ull);  // (prog, W)
     const unsigned long long invalid = after & ~valid_mask;
@@ -147,60 +173,77 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
   return res;
 }
 
-// World position of a point given in the frame whose 12 floats {x, y, z, p} start at f
-// (frame 0, the base, is the identity: f == nullptr).
-__device__ __forceinline__ void to_world(const float* f, float lx, float ly, float lz,
-                                         float& cx, float& cy, float& cz) {
-  if (!f) {
-    cx = lx; cy = ly; cz = lz;
-    return;
-  }
-  cx = fmaf(f[0], lx, fmaf(f[3], ly, fmaf(f[6], lz, f[9])));
-  cy = fmaf(f[1], lx, fmaf(f[4], ly, fmaf(f[7], lz, f[10])));
-  cz = fmaf(f[2], lx, fmaf(f[5], ly, fmaf(f[8], lz, f[11])));
-}
-
-// Per-warp shared-memory scratch of the collision walk.
-struct CcScratch {
-  const float4* bnd;  // [dof + 1] frame bounding spheres, local coordinates (shared by the CTA)
-  float4* wsph;       // [S] world centre + radius of each robot sphere at the current waypoint
-  float4* wbnd;       // [dof + 1] world centre + padded radius of each frame's bounding sphere
-};
-
 // Shared-memory layout of the motion kernels, in bytes from the dynamic shared base:
-//   obstacles (staged only when they fit) | robot spheres | frame bounds | sphere frames |
-//   per warp: world spheres, world bounds, frame cache | extra (kernel-specific, 16-aligned)
+//   obstacles (staged only when they fit) | robot spheres (sorted by frame) | frame bounds |
+//   spheres per frame | first sphere of each frame | joints |
+//   per warp: waypoints [W][9] floats, swept bounds [dof + 1], candidate list |
+//   extra (kernel-specific, 16-aligned)
+constexpr int kCandMax = 128;  // candidate obstacles listed per pass of the collision check
+
 struct SmemLayout {
-  size_t obs, sph, bnd, sfr, warp0, warp_bytes, wsph, wbnd, frames, extra, total;
-  __host__ __device__ SmemLayout(int stage_f4, int S, int dof, int W, int warps,
-                                 size_t extra_bytes) {
+  size_t obs, sph, bnd, nsf, foff, jnt, warp0, warp_bytes, wq, sbnd, cand, extra, total;
+  __host__ __device__ SmemLayout(int stage_f4, int S, int W, int warps, size_t extra_bytes) {
     auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
     obs = 0;
     sph = al(obs + (size_t)stage_f4 * 16);
     bnd = al(sph + (size_t)S * 16);
-    sfr = al(bnd + (size_t)(kMaxDof + 1) * 16);
-    warp0 = al(sfr + (size_t)S * 4);
-    wsph = 0;
-    wbnd = al(wsph + (size_t)S * 16);
-    frames = al(wbnd + (size_t)(kMaxDof + 1) * 16);
-    warp_bytes = al(frames + (size_t)W * (kFrameFloats * dof + 1) * 4);
+    nsf = al(bnd + (size_t)(kMaxDof + 1) * 16);
+    foff = al(nsf + (size_t)(kMaxDof + 1) * 4);
+    jnt = al(foff + (size_t)(kMaxDof + 2) * 4);
+    warp0 = al(jnt + sizeof(JointDev) * kMaxDof);
+    wq = 0;
+    sbnd = al(wq + (size_t)W * 9 * 4);
+    cand = al(sbnd + (size_t)(kMaxDof + 1) * 16);
+    warp_bytes = al(cand + (size_t)kCandMax * 4);
     extra = al(warp0 + (size_t)warps * warp_bytes);
     total = extra + extra_bytes;
   }
 };
 
-// Stages robot spheres, their frames and the frame bounds into shared memory.
+// What the collision check reads from shared memory.
+struct CcShared {
+  const float4* sph;    // [S] robot spheres {x, y, z, r} in their frames, sorted by frame
+  const float4* bnd;    // [dof + 1] frame bounding spheres (local centre, padded radius)
+  const int* nsf;       // [dof + 1] spheres per frame
+  const int* foff;      // [dof + 2] first sphere of each frame
+  const JointDev* jnt;  // [dof]
+  float* wq;            // this warp: waypoints [W][9]
+  float4* sbnd;         // this warp: swept frame bounds [dof + 1]
+  unsigned* cand;       // this warp: candidate list, obstacle | frame mask << 20
+};
+
+__device__ __forceinline__ CcShared cc_shared(char* base, const SmemLayout& L, int warp) {
+  char* w = base + L.warp0 + (size_t)warp * L.warp_bytes;
+  return CcShared{reinterpret_cast<const float4*>(base + L.sph),
+                  reinterpret_cast<const float4*>(base + L.bnd),
+                  reinterpret_cast<const int*>(base + L.nsf),
+                  reinterpret_cast<const int*>(base + L.foff),
+                  reinterpret_cast<const JointDev*>(base + L.jnt),
+                  reinterpret_cast<float*>(w + L.wq), reinterpret_cast<float4*>(w + L.sbnd),
+                  reinterpret_cast<unsigned*>(w + L.cand)};
+}
+
+// Stages robot spheres, frame bounds, per-frame counts and offsets and the joint table.
 __device__ __forceinline__ void stage_robot(const RobotDev& rb, char* base, const SmemLayout& L) {
   float4* sph = reinterpret_cast<float4*>(base + L.sph);
   float4* bnd = reinterpret_cast<float4*>(base + L.bnd);
-  int* sfr = reinterpret_cast<int*>(base + L.sfr);
-  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) {
-    sph[i] = rb.spheres[i];
-    sfr[i] = rb.sphere_frame[i];
-  }
+  int* nsf = reinterpret_cast<int*>(base + L.nsf);
+  int* foff = reinterpret_cast<int*>(base + L.foff);
+  JointDev* jnt = reinterpret_cast<JointDev*>(base + L.jnt);
+  for (int i = threadIdx.x; i < rb.n_spheres; i += blockDim.x) sph[i] = rb.spheres[i];
+  if (threadIdx.x == 0) {  // small tables, constant indices into the parameter block
+    int o = 0;
 #pragma unroll
-  for (int f = 0; f <= kMaxDof; ++f)
-    if (threadIdx.x == f) bnd[f] = rb.bound[f];
+    for (int f = 0; f <= kMaxDof; ++f) {
+      bnd[f] = rb.bound[f];
+      nsf[f] = rb.n_per_frame[f];
+      foff[f] = o;
+      o += rb.n_per_frame[f];
+    }
+    foff[kMaxDof + 1] = o;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) jnt[k] = rb.j[k];
+  }
 }
 
 // Tests obstacle o (index into the sphere / box / capsule ranges) against ball (c, r).
@@ -209,80 +252,236 @@ __device__ __forceinline__ bool hit_obstacle(const SceneDev& sc, const float4* _
   if (o < sc.n_sph) return hit_sphere(cx, cy, cz, r, obs[o]);
   o -= sc.n_sph;
   if (o < sc.n_box) {
-    const float4* b = obs + sc.n_sph + 4 * o;
-    return hit_box(cx, cy, cz, r, b[0], b[1], b[2], b[3]);
+    const float4* b = obs + sc.n_sph + o;  // component j at b[j * n_box]
+    return hit_box(cx, cy, cz, r, b[0], b[sc.n_box], b[2 * sc.n_box], b[3 * sc.n_box]);
   }
   o -= sc.n_box;
-  const float4* k = obs + sc.n_sph + 4 * sc.n_box + 2 * o;
-  return hit_capsule(cx, cy, cz, r, k[0], k[1]);
+  const float4* k = obs + sc.n_sph + 4 * sc.n_box + o;  // component j at k[j * n_cap]
+  return hit_capsule(cx, cy, cz, r, k[0], k[sc.n_cap]);
 }
 
-// FK + CC of waypoints [i0, W) in order; returns the first colliding waypoint or -1.
+// One DH frame of a lane's waypoint: axes x, y, z and origin p (world).
+struct Frame {
+  float x0, x1, x2, y0, y1, y2, z0, z1, z2, p0, p1, p2;
+  __device__ __forceinline__ void identity() {
+    x0 = 1.f; x1 = 0.f; x2 = 0.f; y0 = 0.f; y1 = 1.f; y2 = 0.f;
+    z0 = 0.f; z1 = 0.f; z2 = 1.f; p0 = 0.f; p1 = 0.f; p2 = 0.f;
+  }
+  // Advances by joint J at joint value q (same arithmetic as `chain`).
+  __device__ __forceinline__ void advance(const JointDev& J, float q) {
+    float ct, st, d = J.d;
+    if (J.prismatic) {
+      ct = J.ct0;
+      st = J.st0;
+      d += q;
+    } else {
+      sincospif((J.theta0 + q) * kInvPi, &st, &ct);
+    }
+    const float u0 = fmaf(x0, ct, y0 * st), u1 = fmaf(x1, ct, y1 * st), u2 = fmaf(x2, ct, y2 * st);
+    const float v0 = fmaf(y0, ct, -x0 * st), v1 = fmaf(y1, ct, -x1 * st), v2 = fmaf(y2, ct, -x2 * st);
+    p0 = fmaf(J.a, u0, fmaf(d, z0, p0));
+    p1 = fmaf(J.a, u1, fmaf(d, z1, p1));
+    p2 = fmaf(J.a, u2, fmaf(d, z2, p2));
+    x0 = u0; x1 = u1; x2 = u2;
+    y0 = fmaf(v0, J.ca, z0 * J.sa); y1 = fmaf(v1, J.ca, z1 * J.sa); y2 = fmaf(v2, J.ca, z2 * J.sa);
+    const float nz0 = fmaf(z0, J.ca, -v0 * J.sa), nz1 = fmaf(z1, J.ca, -v1 * J.sa),
+                nz2 = fmaf(z2, J.ca, -v2 * J.sa);
+    z0 = nz0; z1 = nz1; z2 = nz2;
+  }
+  __device__ __forceinline__ void world(float lx, float ly, float lz, float& cx, float& cy,
+                                        float& cz) const {
+    cx = fmaf(x0, lx, fmaf(y0, ly, fmaf(z0, lz, p0)));
+    cy = fmaf(x1, lx, fmaf(y1, ly, fmaf(z1, lz, p1)));
+    cz = fmaf(x2, lx, fmaf(y2, ly, fmaf(z2, lz, p2)));
+  }
+};
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// FK + CC of waypoints [i0, W) of the warp's segment (lane l holds waypoints l + 32 s in
+// q). Returns the smallest colliding waypoint, or -1. With `any_hit`, returns as soon as
+// some waypoint is known to collide (the index is then a colliding waypoint, not
+// necessarily the smallest): the paper's shared flag (Sec. IV), for callers that only need
+// the verdict.
 //
-// Two levels per waypoint, exact: each lane takes one obstacle of a 32-obstacle chunk and
-// tests it against the bounding sphere of every frame's robot spheres (radius padded by
-// 1e-5 m, far above the FP32 error of either test, so a miss there proves every sphere of
-// that frame misses). Only the (obstacle, frame) pairs that survive are tested sphere by
-// sphere, lanes over the robot's spheres. The warp-wide vote after each such obstacle
-// plays the role of the paper's shared collision flag (Sec. IV).
-__device__ __forceinline__ int collide_warp(const RobotDev& rb, const SceneDev& sc,
-                                            const float4* __restrict__ obs,
-                                            const float4* sph, const int* sfr, int W, int i0,
-                                            const float* fr, CcScratch cc) {
+// Exact culling in three levels (a miss at a level proves a miss of everything under it,
+// every radius padded by at least 1e-5 m, far above the FP32 error of the tests):
+//  1. per motion: each frame's bounding sphere is swept over the waypoints (a ball around
+//     the box of its centres); each obstacle is tested once against every swept bound and
+//     the obstacles that touch one are listed with the frames they touch;
+//  2. per waypoint (lane), frame by frame along the chain: the frame's bounding sphere
+//     against each listed obstacle of that frame;
+//  3. the frame's robot spheres, for lanes whose bound touched the obstacle.
+template <int WPL>
+__device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev& sc,
+                                              const float4* __restrict__ obs, const CcShared& S,
+                                              const float (&q)[WPL][kMaxDof], int W, int i0,
+                                              bool any_hit, WorkCount& work) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
-  const int fs = frame_stride(dof);
-  const int S = rb.n_spheres;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
-  for (int i = i0; i < W; ++i) {
-    const float* fw = fr + i * fs;
-    if (lane <= dof) {
-      const float4 b = cc.bnd[lane];
-      float x, y, z;
-      to_world(lane == 0 ? nullptr : fw + (lane - 1) * kFrameFloats, b.x, b.y, b.z, x, y, z);
-      cc.wbnd[lane] = make_float4(x, y, z, b.w);
+  // waypoints to shared memory: the chain below walks frames in a runtime loop
+#pragma unroll
+  for (int s = 0; s < WPL; ++s) {
+    const int i = lane + 32 * s;
+    if (i < W) {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) S.wq[i * 9 + k] = q[s][k];
     }
-    for (int s = lane; s < S; s += 32) {
-      const float4 l = sph[s];
-      const int f = sfr[s];
-      float x, y, z;
-      to_world(f == 0 ? nullptr : fw + (f - 1) * kFrameFloats, l.x, l.y, l.z, x, y, z);
-      cc.wsph[s] = make_float4(x, y, z, l.w);
+  }
+  __syncwarp();
+  bool act[WPL];
+  int n_act = 0;
+#pragma unroll
+  for (int s = 0; s < WPL; ++s) {
+    const int i = lane + 32 * s;
+    act[s] = i >= i0 && i < W;
+  }
+  n_act = max(0, W - i0);
+  if (n_act == 0 || n_obs == 0) return -1;
+
+  // ---- level 1: swept frame bounds over the segment ----
+  {
+    Frame F[WPL];
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) F[s].identity();
+    for (int f = 0; f <= dof; ++f) {
+      if (f > 0) {
+        const JointDev J = S.jnt[f - 1];
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) F[s].advance(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+      }
+      const float4 b = S.bnd[f];
+      if (b.w < 0.f) continue;  // no spheres on this frame (warp-uniform)
+      float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+      float hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
+      float c[WPL][3];
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) {
+        F[s].world(b.x, b.y, b.z, c[s][0], c[s][1], c[s][2]);
+        if (act[s]) {
+          lo0 = fminf(lo0, c[s][0]); lo1 = fminf(lo1, c[s][1]); lo2 = fminf(lo2, c[s][2]);
+          hi0 = fmaxf(hi0, c[s][0]); hi1 = fmaxf(hi1, c[s][1]); hi2 = fmaxf(hi2, c[s][2]);
+        }
+      }
+      const float m0 = 0.5f * (warp_min(lo0) + warp_max(hi0));
+      const float m1 = 0.5f * (warp_min(lo1) + warp_max(hi1));
+      const float m2 = 0.5f * (warp_min(lo2) + warp_max(hi2));
+      float r2 = 0.f;
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) {
+        if (act[s]) {
+          const float d0 = c[s][0] - m0, d1 = c[s][1] - m1, d2 = c[s][2] - m2;
+          r2 = fmaxf(r2, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+        }
+      }
+      const float rad = sqrtf(warp_max(r2)) * 1.000001f + b.w + 1e-5f;
+      if (lane == 0) S.sbnd[f] = make_float4(m0, m1, m2, rad);
     }
+    work.chains += n_act;
+    work.transforms += (long long)n_act * (dof + 1);
     __syncwarp();
-    bool hit = false;
-    for (int base = 0; base < n_obs && !hit; base += 32) {
-      const int o = base + lane;
+  }
+
+  int best = 0x7fffffff;  // smallest colliding waypoint found so far
+  for (int o0 = 0; o0 < n_obs;) {
+    // ---- candidate list: obstacles touching a swept bound, with the frames they touch ----
+    int n_cand = 0;
+    while (o0 < n_obs && n_cand + 32 <= kCandMax) {
+      const int o = o0 + lane;
       unsigned mask = 0u;
       if (o < n_obs) {
         for (int f = 0; f <= dof; ++f) {
-          const float4 b = cc.wbnd[f];
-          if (b.w >= 0.f && hit_obstacle(sc, obs, o, b.x, b.y, b.z, b.w)) mask |= 1u << f;
+          const float4 b = S.sbnd[f];
+          if (S.bnd[f].w >= 0.f && hit_obstacle(sc, obs, o, b.x, b.y, b.z, b.w)) mask |= 1u << f;
         }
       }
-      unsigned cand = __ballot_sync(kFull, mask != 0u);
-      while (cand) {
-        const int src = __ffs(cand) - 1;
-        cand &= cand - 1;
-        const int oo = base + src;
-        const unsigned m = __shfl_sync(kFull, mask, src);
-        bool h = false;
-        for (int s = lane; s < S; s += 32) {
-          if ((m >> sfr[s]) & 1u) {
-            const float4 c = cc.wsph[s];
-            h |= hit_obstacle(sc, obs, oo, c.x, c.y, c.z, c.w);
-          }
-        }
-        if (__any_sync(kFull, h)) {
-          hit = true;
-          break;
-        }
-      }
+      const unsigned bal = __ballot_sync(kFull, mask != 0u);
+      if (mask) S.cand[n_cand + __popc(bal & ((1u << lane) - 1u))] = (unsigned)o | (mask << 20);
+      n_cand += __popc(bal);
+      const int hi = min(o0 + 32, n_obs);
+      work.add_tests(sc, o0, hi, rb.bound_count);
+      o0 = hi;
     }
     __syncwarp();
-    if (hit) return i;
+    if (n_cand == 0) continue;
+    // ---- levels 2 and 3: lanes walk their waypoints' chains frame by frame ----
+    Frame F[WPL];
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) F[s].identity();
+    bool hit[WPL];
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) hit[s] = false;
+    for (int f = 0; f <= dof; ++f) {
+      if (f > 0) {
+        const JointDev J = S.jnt[f - 1];
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) F[s].advance(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+      }
+      const float4 b = S.bnd[f];
+      if (b.w < 0.f) continue;
+      float bc[WPL][3];
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) F[s].world(b.x, b.y, b.z, bc[s][0], bc[s][1], bc[s][2]);
+      const int s_lo = S.foff[f], s_hi = S.foff[f + 1];
+      for (int j = 0; j < n_cand; ++j) {
+        const unsigned e = S.cand[j];
+        if (!((e >> (20 + f)) & 1u)) continue;
+        const int o = (int)(e & 0xFFFFFu);
+        bool near[WPL];
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) {
+          near[s] = act[s] && !hit[s] && hit_obstacle(sc, obs, o, bc[s][0], bc[s][1], bc[s][2], b.w);
+          any |= near[s];
+        }
+        work.count_test(sc, o, n_act);
+        const unsigned nb = __ballot_sync(kFull, any);
+        if (!nb) continue;
+        for (int si = s_lo; si < s_hi; ++si) {
+          const float4 l = S.sph[si];
+#pragma unroll
+          for (int s = 0; s < WPL; ++s) {
+            if (near[s]) {
+              float cx, cy, cz;
+              F[s].world(l.x, l.y, l.z, cx, cy, cz);
+              hit[s] |= hit_obstacle(sc, obs, o, cx, cy, cz, l.w);
+            }
+          }
+        }
+        int near_cnt = 0;
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) near_cnt += __popc(__ballot_sync(kFull, near[s]));
+        work.count_fine(sc, o, near_cnt * (s_hi - s_lo));
+      }
+      if (any_hit) {
+        bool h = false;
+#pragma unroll
+        for (int s = 0; s < WPL; ++s) h |= hit[s];
+        if (__any_sync(kFull, h)) break;
+      }
+    }
+    work.chains += n_act;
+    work.transforms += (long long)n_act * (dof + 1);
+    // smallest colliding waypoint of this pass
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+      const unsigned hb = __ballot_sync(kFull, hit[s]);
+      if (hb) best = min(best, 32 * s + __ffs(hb) - 1);
+    }
+    if (best != 0x7fffffff && (any_hit || best == i0)) break;
   }
-  return -1;
+  return best == 0x7fffffff ? -1 : best;
 }
 
 }  // namespace cprrtc

@@ -32,6 +32,9 @@ struct PlanShared {
   long long wp[kMaxWorkers];   // waypoints validated by each warp
   long long wproj[kMaxWorkers];
   long long wcc[kMaxWorkers];
+  // each warp's configurations, identical across its lanes: kept here instead of in every
+  // lane's registers: [0] current chain node, [1] target, [2] motion end, [3] scratch
+  float cfg[kMaxWorkers][4][8];
 };
 
 __device__ __forceinline__ void load_cfg(const float* src, int dof, float* q) {
@@ -73,6 +76,14 @@ __device__ __forceinline__ int nearest_warp(const float* __restrict__ nodes, int
   return bi;
 }
 
+// dst[0..7] = src[0..dof) padded with zeros (lanes 0..7), then the warp synchronises.
+__device__ __forceinline__ void copy_cfg(float* dst, const float* src, int dof) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (lane < 8) dst[lane] = lane < dof ? src[lane] : 0.f;
+  __syncwarp();
+}
+
 __device__ __forceinline__ float dist2(const float* a, const float* b, int dof) {
   float d = 0.f;
 #pragma unroll
@@ -84,29 +95,30 @@ __device__ __forceinline__ float dist2(const float* a, const float* b, int dof) 
   return d;
 }
 
-// q_s = from + min(1, range / |to - from|) (to - from)
+// out = from + min(1, range / |to - from|) (to - from); from, to, out in shared memory.
 __device__ __forceinline__ void steer(const float* from, const float* to, float range, int dof,
                                       float* out) {
+  const int lane = threadIdx.x & 31;
   const float d = sqrtf(dist2(from, to, dof));
   const float f = d > range ? range / d : 1.f;
-#pragma unroll
-  for (int k = 0; k < kMaxDof; ++k)
-    if (k < dof) out[k] = fmaf(f, to[k] - from[k], from[k]);
+  __syncwarp();
+  if (lane < 8) out[lane] = lane < dof ? fmaf(f, to[lane] - from[lane], from[lane]) : 0.f;
+  __syncwarp();
 }
 
-// The warp's segment waypoint W-1 broadcast to every lane.
+// The warp's segment waypoint W-1 written to out (shared memory) by the lane holding it.
 template <int WPL>
 __device__ __forceinline__ void last_waypoint(const float (&q)[WPL][kMaxDof], int W, int dof,
                                               float* out) {
-  const int src = (W - 1) & 31;
-  const bool hi = (W - 1) >= 32;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (lane == ((W - 1) & 31)) {
+    const bool hi = (W - 1) >= 32;
 #pragma unroll
-  for (int k = 0; k < kMaxDof; ++k) {
-    if (k < dof) {
-      const float v = (WPL > 1 && hi) ? q[WPL > 1 ? 1 : 0][k] : q[0][k];
-      out[k] = __shfl_sync(kFull, v, src);
-    }
+    for (int k = 0; k < kMaxDof; ++k)
+      out[k] = k < dof ? ((WPL > 1 && hi) ? q[WPL > 1 ? 1 : 0][k] : q[0][k]) : 0.f;
   }
+  __syncwarp();
 }
 
 template <int WPL>
@@ -149,27 +161,29 @@ __device__ __forceinline__ void copy_edge(float* dst, const float* src, int W, i
 }
 
 struct MotionWork {
-  long long proj;  // waypoint evaluations of Alg. 1: iterations x (W - 1)
+  long long proj;  // waypoint updates Alg. 1 needed
   long long cc;    // waypoints collision-checked
 };
 
-// Interpolate q0 -> q1, project (at most cs.max_iters iterations), FK + CC from waypoint 1.
+// Interpolate q0 -> q1, project (at most cs.max_iters iterations), FK + CC from waypoint 1
+// stopping at the first collision found.
 template <int CT, int WPL>
 __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDev& sc,
                                                const ConsDev& cs, MotionWork& work,
-                                               const float4* obs, const float4* sph,
-                                               const int* sfr, const float* q0,
-                                               const float* q1, int W, float* fr,
-                                               const CcScratch& cc, float (&q)[WPL][kMaxDof]) {
+                                               WorkCount& wc, const float4* obs,
+                                               const CcShared& S, const float* q0,
+                                               const float* q1, int W,
+                                               float (&q)[WPL][kMaxDof]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
   const float tau = step_threshold(cs, q0, q1, W, rb.dof);
-  const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau, fr);
+  const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
   __syncwarp();
-  work.proj += (long long)pr.iters * (W - 1);
+  work.proj += pr.updates;
+  wc.updates += pr.updates;
   if (pr.status != kValid) return kProjFail;
-  const int ff = collide_warp(rb, sc, obs, sph, sfr, W, 1, fr, cc);
+  const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc);
   __syncwarp();
   work.cc += ff >= 0 ? ff : W - 1;
   return ff >= 0 ? kCollision : kValid;
@@ -193,21 +207,15 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
     sc.n_cap = d.w;
   }
   extern __shared__ __align__(16) char smem[];
-  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, dof, W, B,
-                     sizeof(PlanShared));
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, W, B, sizeof(PlanShared));
   const int n4 = sc.n_float4();
   float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
   if (a.stage_obs)
     for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
   stage_robot(rb, smem, L);
-  const float4* s_sph = reinterpret_cast<const float4*>(smem + L.sph);
-  const int* s_sfr = reinterpret_cast<const int*>(smem + L.sfr);
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
-  char* wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
-  float* fr = reinterpret_cast<float*>(wbase + L.frames);
-  const CcScratch cc{reinterpret_cast<const float4*>(smem + L.bnd),
-                     reinterpret_cast<float4*>(wbase + L.wsph),
-                     reinterpret_cast<float4*>(wbase + L.wbnd)};
+  const CcShared S = cc_shared(smem, L, warp);
+  WorkCount wc{0, 0, 0, 0, 0, 0};
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
 
   const size_t wd = (size_t)W * dof;
@@ -242,37 +250,36 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
   int rounds_used = 0, win = -1;
   // chain state (warp-uniform): 0 extend, 1 connect, 2 closing hop
   int mode = 0, ta = 0, last = 0, target = -1, steps = 0;
-  float cur[kMaxDof], qt[kMaxDof];
-#pragma unroll
-  for (int k = 0; k < kMaxDof; ++k) cur[k] = qt[k] = 0.f;
+  float* cur = sh->cfg[warp][0];
+  float* qt = sh->cfg[warp][1];
+  float* q1 = sh->cfg[warp][2];
+  float* qe = sh->cfg[warp][3];
   for (int r = 0; r < a.max_rounds; ++r) {
-    float q1[kMaxDof];
     if (mode == 0) {
       ta = (r + warp) & 1;
       const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 0u}, a.seed, 0u);
       const U32x4 u1 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 1u}, a.seed, 0u);
       const uint32_t w8[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-      float qr[kMaxDof];
+      float v = 0.f;
 #pragma unroll
-      for (int k = 0; k < kMaxDof; ++k)
-        qr[k] = k < dof ? fmaf(u24(w8[k]), rb.j[k].hi - rb.j[k].lo, rb.j[k].lo) : 0.f;
-      last = nearest_warp(nodes(ta), sh->count0[ta], qr, dof);
-      load_cfg(nodes(ta) + (size_t)last * 8, dof, cur);
-      steer(cur, qr, a.range, dof, q1);
+      for (int k = 0; k < kMaxDof; ++k)  // lane k takes word k (no dynamic register index)
+        if (k == lane && k < dof) v = fmaf(u24(w8[k]), rb.j[k].hi - rb.j[k].lo, rb.j[k].lo);
+      __syncwarp();
+      if (lane < 8) qe[lane] = v;  // the sample, in the scratch slot
+      __syncwarp();
+      last = nearest_warp(nodes(ta), sh->count0[ta], qe, dof);
+      copy_cfg(cur, nodes(ta) + (size_t)last * 8, dof);
+      steer(cur, qe, a.range, dof, q1);
     } else if (mode == 1) {
       steer(cur, qt, a.range, dof, q1);
     } else {
-#pragma unroll
-      for (int k = 0; k < kMaxDof; ++k) q1[k] = qt[k];
+      copy_cfg(q1, qt, dof);
     }
     float q[WPL][kMaxDof];
-    const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, obs, s_sph,
-                                            s_sfr, cur, q1, W, fr, cc, q);
+    const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, wc, obs, S,
+                                            cur, q1, W, q);
     wp += W;
     int add = 0, conn = 0;
-    float qe[kMaxDof];
-#pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) qe[k] = cur[k];
     if (st == kValid) {
       if (mode == 2) {
         conn = 1;
@@ -282,7 +289,7 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
         bool accept = true;
         if (mode == 0) {
           target = nearest_warp(nodes(ta ^ 1), sh->count0[ta ^ 1], qe, dof);
-          load_cfg(nodes(ta ^ 1) + (size_t)target * 8, dof, qt);
+          copy_cfg(qt, nodes(ta ^ 1) + (size_t)target * 8, dof);
         } else {
           accept = dist2(qe, qt, dof) < dist2(cur, qt, dof);
         }
@@ -336,12 +343,11 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
     // next motion of the chain
     if (dst >= 0) {
       last = dst;
+      copy_cfg(cur, qe, dof);
       float gap = 0.f;
 #pragma unroll
-      for (int k = 0; k < kMaxDof; ++k) {
-        cur[k] = qe[k];
+      for (int k = 0; k < kMaxDof; ++k)
         if (k < dof) gap = fmaxf(gap, fabsf(cur[k] - qt[k]));
-      }
       if (gap <= connect_radius) {
         mode = 2;
       } else if (steps < a.max_connect) {
@@ -361,6 +367,7 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
     sh->wproj[warp] = work.proj;
     sh->wcc[warp] = work.cc;
   }
+  wc.flush(a.work_counters);
 
   if (win >= 0 && warp == win) {
     // path: root_a .. last, closing hop, target .. root_b; reversed when tree a is the
@@ -433,8 +440,7 @@ static const void* plan_fn(int ct, int W) {
 }
 
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage) {
-  return SmemLayout(stage ? max_scene_f4 : 0, rb.n_spheres, rb.dof, W, workers,
-                    sizeof(PlanShared)).total;
+  return SmemLayout(stage ? max_scene_f4 : 0, rb.n_spheres, W, workers, sizeof(PlanShared)).total;
 }
 
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,

@@ -5,30 +5,25 @@
 
 namespace cprrtc {
 
-// Robot spheres, their frames and each warp's frame cache live in shared memory; the
-// obstacle stream is staged there too when it fits (coalesced float4 copies), else read
-// from global memory through L1 (every lane reads the same obstacle: one broadcast).
+// Robot tables and each warp's collision scratch live in shared memory; the obstacle
+// stream is staged there too when it fits (coalesced float4 copies), else read from
+// global memory through L1. The first colliding waypoint is exact (no early exit).
 // (No __launch_bounds__: with it, ptxas caps registers low enough to spill here.)
 template <int CT, int WPL>
 __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int n4 = sc.n_float4();
-  const SmemLayout L(a.stage_obs ? n4 : 0, rb.n_spheres, rb.dof, a.W, kValidateWarps, 0);
+  const SmemLayout L(a.stage_obs ? n4 : 0, rb.n_spheres, a.W, kValidateWarps, 0);
   float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
   if (a.stage_obs)
     for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
   stage_robot(rb, smem, L);
   __syncthreads();
-  const float4* s_sph = reinterpret_cast<const float4*>(smem + L.sph);
-  const int* s_sfr = reinterpret_cast<const int*>(smem + L.sfr);
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dof = rb.dof, W = a.W;
-  char* wbase = smem + L.warp0 + (size_t)warp * L.warp_bytes;
-  float* fr = reinterpret_cast<float*>(wbase + L.frames);
-  const CcScratch cc{reinterpret_cast<const float4*>(smem + L.bnd),
-                     reinterpret_cast<float4*>(wbase + L.wsph),
-                     reinterpret_cast<float4*>(wbase + L.wbnd)};
+  const CcShared S = cc_shared(smem, L, warp);
+  WorkCount work{0, 0, 0, 0, 0, 0};
 
   for (int m = blockIdx.x * kValidateWarps + warp; m < a.n; m += gridDim.x * kValidateWarps) {
     float q0[kMaxDof], q1[kMaxDof];
@@ -43,11 +38,11 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
 #pragma unroll
     for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, dof, q[s]);
     const float tau = step_threshold(cs, q0, q1, W, dof);
-    const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau, fr);
-    __syncwarp();
+    const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
+    work.updates += pr.updates;
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid) {
-      ff = collide_warp(rb, sc, obs, s_sph, s_sfr, W, a.cc_skip_first, fr, cc);
+      ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work);
       if (ff >= 0) st = kCollision;
     }
     if (a.out_q) {
@@ -70,6 +65,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     }
     __syncwarp();
   }
+  work.flush(a.work_counters);
 }
 
 // One thread per configuration: damped steps until ||E_task||_inf < tol_task.
@@ -127,7 +123,7 @@ static const void* validate_fn(int ct, int W) {
 }
 
 size_t validate_smem_bytes(const RobotDev& rb, const SceneDev& sc, int W, bool stage_obs) {
-  return SmemLayout(stage_obs ? sc.n_float4() : 0, rb.n_spheres, rb.dof, W, kValidateWarps, 0).total;
+  return SmemLayout(stage_obs ? sc.n_float4() : 0, rb.n_spheres, W, kValidateWarps, 0).total;
 }
 
 cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs,

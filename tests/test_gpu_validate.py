@@ -178,3 +178,31 @@ def test_project_configs_parity(torch_cuda, oracle_mod):
             agree += 1
     assert agree >= 0.95 * len(q)
     ctx.close()
+
+
+def test_work_counters_match_outputs(torch_cuda, oracle_mod):
+    """The executed-work counters agree with what the outputs imply: every motion that
+    reaches collision checking costs one swept-bound chain per waypoint plus at most one
+    more in the fused pass (50 obstacles fit one candidate list), tests every obstacle
+    against every swept frame bound, and Alg. 1 needs no more than iterations x (W - 1)
+    updates."""
+    rb = S.make_arm7(1)
+    sc = S.make_mixed_scene(8001, 30, 10, 10)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 64, 8002)
+    q1 = S.nearby_configs(rb, q0, 0.3, 8003)
+    ctx = make_ctx(rb, sc, c)
+    ctx.work_counters(reset=True)
+    out = ctx.validate(torch_cuda.from_numpy(q0.astype(np.float32)).cuda(),
+                       torch_cuda.from_numpy(q1.astype(np.float32)).cuda(), 32)
+    cnt = ctx.work_counters()
+    st, it = (parity.to_np(out[k]).astype(np.int64) for k in ("status", "iters"))
+    reached = int((st != 1).sum())
+    nb = len(np.unique(rb.spheres[:, 0]))
+    n_obs = len(sc.sph) + len(sc.box) + len(sc.cap)
+    assert 0 < cnt[0] <= (it * 31).sum()
+    assert 32 * reached <= cnt[1] <= 2 * 32 * reached
+    assert cnt[3:].sum() >= reached * nb * n_obs
+    assert cnt[2] >= 32 * reached * nb
+    ctx.close()
