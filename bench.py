@@ -75,6 +75,26 @@ def executed_flops(dof: int, counters) -> float:
             + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
 
 
+def profiled_traffic_per_unit(name: str, key: str):
+    """DRAM bytes per unit recorded in profiles/<name> from an ncu capture, or None when the
+    kernel sources changed since (the file records their hash)."""
+    import glob
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256_16: ([0-9a-f]{16})", text)
+    m_val = re.search(key + r": ([0-9.eE+]+)", text)
+    if not (m_hash and m_val):
+        return None
+    src = sorted(glob.glob(os.path.join(ROOT, "paper_2505_06791_gb300", "csrc", "*")))
+    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    return float(m_val.group(1)) if h == m_hash.group(1) else None
+
+
 def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     """FP32 FMA-pipe peak: SMs x 128 lanes x 2 FLOP x clock."""
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
@@ -295,6 +315,9 @@ def run_plan(args, world, rank, local):
     avg_kernel_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_kernel_s / 1e12
     solved = L > 0
+    per_round = profiled_traffic_per_unit("plan_kernel_config2.md",
+                                          "traffic_per_problem_round_bytes")
+    traffic = None if per_round is None else per_round * float(rounds.sum())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -315,7 +338,9 @@ def run_plan(args, world, rank, local):
         "mean_rounds": float(rounds.mean()),
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "plan_kernel",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "plan_kernel",
+                     "traffic_note": "ncu DRAM bytes per problem-round of a 304-problem capture "
+                                     "(profiles/plan_kernel_config2.md) x problem-rounds",
                      "flop_per_launch": flops, "avg_launch_ms": avg_kernel_s * 1e3,
                      "work_per_launch": {"alg1_updates": float(counters[0]),
                                          "cc_chains": float(counters[1]),
