@@ -45,13 +45,14 @@ struct ProjResult {
   int updates;     // waypoint updates Alg. 1 needed: sum over iterations of (W - 1 - prog)
 };
 
-// Work a warp evaluated, for roofline accounting (warp-uniform counts, per waypoint).
+// Work a warp evaluated, for roofline accounting (warp-uniform counts). 32-bit per warp:
+// one warp's launch stays far below 2^32 of each (the totals are summed in 64 bits).
 struct WorkCount {
-  long long updates;     // Alg. 1 waypoint updates
-  long long chains;      // DH chains evaluated for collision checking
-  long long transforms;  // points moved to world coordinates (frame bounds, robot spheres)
-  long long p_sph, p_box, p_cap;  // ball-vs-primitive tests by primitive
-  __device__ __forceinline__ void add_type(const SceneDev& sc, int o, long long n) {
+  unsigned updates;     // Alg. 1 waypoint updates
+  unsigned chains;      // DH chains evaluated for collision checking
+  unsigned transforms;  // points moved to world coordinates (frame bounds, robot spheres)
+  unsigned p_sph, p_box, p_cap;  // ball-vs-primitive tests by primitive
+  __device__ __forceinline__ void add_type(const SceneDev& sc, int o, unsigned n) {
     if (o < sc.n_sph)
       p_sph += n;
     else if (o < sc.n_sph + sc.n_box)
@@ -63,9 +64,9 @@ struct WorkCount {
   __device__ __forceinline__ void add_tests(const SceneDev& sc, int lo, int hi, int nb) {
     const int c_s = max(0, min(hi, sc.n_sph) - lo);
     const int c_b = max(0, min(hi, sc.n_sph + sc.n_box) - max(lo, sc.n_sph));
-    p_sph += (long long)nb * c_s;
-    p_box += (long long)nb * c_b;
-    p_cap += (long long)nb * (hi - lo - c_s - c_b);
+    p_sph += (unsigned)(nb * c_s);
+    p_box += (unsigned)(nb * c_b);
+    p_cap += (unsigned)(nb * (hi - lo - c_s - c_b));
   }
   __device__ __forceinline__ void count_test(const SceneDev& sc, int o, int n) { add_type(sc, o, n); }
   __device__ __forceinline__ void count_fine(const SceneDev& sc, int o, int n) {
@@ -389,7 +390,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       if (lane == 0) S.sbnd[f] = make_float4(m0, m1, m2, rad);
     }
     work.chains += n_act;
-    work.transforms += (long long)n_act * (dof + 1);
+    work.transforms += (unsigned)(n_act * (dof + 1));
     __syncwarp();
   }
 
@@ -472,7 +473,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       }
     }
     work.chains += n_act;
-    work.transforms += (long long)n_act * (dof + 1);
+    work.transforms += (unsigned)(n_act * (dof + 1));
     // smallest colliding waypoint of this pass
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {

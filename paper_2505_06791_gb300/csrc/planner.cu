@@ -32,6 +32,7 @@ struct PlanShared {
   long long wp[kMaxWorkers];   // waypoints validated by each warp
   long long wproj[kMaxWorkers];
   long long wcc[kMaxWorkers];
+  long long t_start;           // globaltimer at the CTA's start
   // each warp's configurations, identical across its lanes: kept here instead of in every
   // lane's registers: [0] current chain node, [1] target, [2] motion end, [3] scratch
   float cfg[kMaxWorkers][4][8];
@@ -160,9 +161,9 @@ __device__ __forceinline__ void copy_edge(float* dst, const float* src, int W, i
   }
 }
 
-struct MotionWork {
-  long long proj;  // waypoint updates Alg. 1 needed
-  long long cc;    // waypoints collision-checked
+struct MotionWork {  // per warp (32-bit suffices for one launch)
+  unsigned proj;  // waypoint updates Alg. 1 needed
+  unsigned cc;    // waypoints collision-checked
 };
 
 // Interpolate q0 -> q1, project (at most cs.max_iters iterations), FK + CC from waypoint 1
@@ -180,23 +181,33 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
   const float tau = step_threshold(cs, q0, q1, W, rb.dof);
   const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
   __syncwarp();
-  work.proj += pr.updates;
-  wc.updates += pr.updates;
+  work.proj += (unsigned)pr.updates;
+  wc.updates += (unsigned)pr.updates;
   if (pr.status != kValid) return kProjFail;
   const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc);
   __syncwarp();
-  work.cc += ff >= 0 ? ff : W - 1;
+  work.cc += (unsigned)(ff >= 0 ? ff : W - 1);
   return ff >= 0 ? kCollision : kValid;
 }
 
+// Register cap of the planner kernel (0: the compiler's choice). Fewer registers let more
+// 8-warp CTAs share an SM at the price of some spills.
+#ifndef CPRRTC_PLAN_MAXNREG
+#define CPRRTC_PLAN_MAXNREG 0
+#endif
+#if CPRRTC_PLAN_MAXNREG > 0
+#define CPRRTC_PLAN_REGS __maxnreg__(CPRRTC_PLAN_MAXNREG)
+#else
+#define CPRRTC_PLAN_REGS
+#endif
+
 template <int CT, int WPL>
-__global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, PlanArgs a) {
+__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
+                                             PlanArgs a) {
   const int p = blockIdx.x;
   if (p >= a.n) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int B = a.workers, dof = rb.dof, W = a.W;
-  long long t_start = 0;
-  if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
 
   SceneDev sc = shared_scene;
   if (a.scenes) {
@@ -215,8 +226,13 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
   stage_robot(rb, smem, L);
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
   const CcShared S = cc_shared(smem, L, warp);
-  WorkCount wc{0, 0, 0, 0, 0, 0};
+  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+  if (threadIdx.x == 0) {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    sh->t_start = t;
+  }
 
   const size_t wd = (size_t)W * dof;
   const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
@@ -245,8 +261,8 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
   ConsDev hop = cs;
   hop.max_iters = 1;
   const float connect_radius = 10.f * cs.tau_floor;
-  long long wp = 0;
-  MotionWork work{0, 0};
+  unsigned wp = 0;
+  MotionWork work{0u, 0u};
   int rounds_used = 0, win = -1;
   // chain state (warp-uniform): 0 extend, 1 connect, 2 closing hop
   int mode = 0, ta = 0, last = 0, target = -1, steps = 0;
@@ -423,7 +439,7 @@ __global__ void plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs, Plan
     }
     long long t_end;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - t_start) * 1e-6);
+    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sh->t_start) * 1e-6);
   }
 }
 

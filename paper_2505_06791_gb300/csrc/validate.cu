@@ -23,7 +23,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dof = rb.dof, W = a.W;
   const CcShared S = cc_shared(smem, L, warp);
-  WorkCount work{0, 0, 0, 0, 0, 0};
+  WorkCount work{0u, 0u, 0u, 0u, 0u, 0u};
 
   for (int m = blockIdx.x * kValidateWarps + warp; m < a.n; m += gridDim.x * kValidateWarps) {
     float q0[kMaxDof], q1[kMaxDof];
@@ -39,7 +39,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, dof, q[s]);
     const float tau = step_threshold(cs, q0, q1, W, dof);
     const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
-    work.updates += pr.updates;
+    work.updates += (unsigned)pr.updates;
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid) {
       ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work);
