@@ -398,6 +398,172 @@ def cpu_baseline_plan(inputs, budget_s):
                       f"solved {solved}, p50 plan {np.percentile(ms, 50):.0f} ms per problem"}
 
 
+BATCH_N = 512
+BATCH_PARAMS = dict(range_=0.3, max_rounds=1000, workers=8, max_nodes=2048, max_connect=32,
+                    max_path=512)
+
+
+def gpu_batch_start_goal(robots, cons, problems, scenes, seed, device):
+    """Start/goal [n][8] per problem with the library: uniform configurations of the
+    problem's robot, projected under its constraint, kept when collision-free with every
+    robot sphere inflated by 1 mm."""
+    import torch
+    from paper_2505_06791_gb300.capi import Context
+    proj, chk = Context(device), Context(device)
+    start = torch.zeros((len(problems), 8), device="cuda")
+    goal = torch.zeros((len(problems), 8), device="cuda")
+    cur_r = None
+    for p, (r, c, sc, W) in enumerate(problems):
+        rb = robots[r]
+        if r != cur_r:
+            proj.set_robot(rb)
+            inflated = S.Robot(rb.joints, rb.ee, rb.spheres.copy())
+            inflated.spheres[:, 4] += 1e-3
+            chk.set_robot(inflated)
+            chk.set_constraint(S.no_constraint())
+            cur_r = r
+        chk.set_obstacles(scenes[sc])
+        found, k = [], 0
+        while len(found) < 2:
+            cand = torch.from_numpy(S.uniform_configs(rb, 64, seed * 1_000_003 + 977 * p + k)
+                                    .astype(np.float32)).cuda()
+            if cons[c].type != 0:
+                proj.set_constraint(cons[c])
+                res = proj.project_configs(cand, 60)
+                cand = res["q"][res["ok"].bool()].contiguous()
+            if len(cand):
+                v = chk.validate(cand, cand, 2, with_q=False)
+                free = cand[v["status"] == 0]
+                found += [free[i] for i in range(min(2 - len(found), len(free)))]
+            k += 1
+            if k > 400:
+                raise RuntimeError(f"no collision-free start/goal for problem {p}")
+        start[p, :rb.dof] = found[0]
+        goal[p, :rb.dof] = found[1]
+    proj.close()
+    chk.close()
+    return start, goal
+
+
+def run_batch(args, world, rank, local):
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = 5 + 1000 * rank
+    robots, cons, probs, scenes = S.make_batch_mix(args.problems, seed)
+    start, goal = gpu_batch_start_goal(robots, cons, probs, scenes, seed, local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot_table(robots)
+    ctx.set_constraint_table(cons)
+    ctx.set_scene_batch(scenes)
+    prm = ctx.plan_params(seed=seed, use_scene_batch=True, **BATCH_PARAMS)
+    max_W = max(p[3] for p in probs)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        tuning = ctx.autotune_batch(probs, start, goal, prm, trial_rounds=20)
+        tune_s = time.perf_counter() - t0
+        out = ctx.alloc_batch_outputs(len(probs), prm, max_W, start)
+        ctx.batch_capture(probs, start, goal, prm, out, tuning=tuning)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            ctx.batch_replay()
+        stream.synchronize()
+        ctx.set_timing(True)
+        ctx.reset_timing()
+        ctx.work_counters(reset=True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            ctx.batch_replay()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
+        kms, launches = ctx.kernel_time("plan_batch")
+        counters = ctx.work_counters() / max(args.steps, 1)
+        ctx.set_timing(False)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    L = out["path_len"].cpu().numpy()
+    wp = out["waypoints"].cpu().numpy()
+    ms = out["plan_ms"].cpu().numpy()
+    waypoints_step = int(wp.sum())
+    value = waypoints_step * args.steps * world / (total_ms / 1e3)
+    # executed FLOPs: dof differs per problem; weight Alg. 1 updates by the mean dof
+    mean_dof = float(np.mean([robots[r].dof for r, _, _, _ in probs]))
+    upd, chains, tf, ps, pb, pc = [float(x) for x in counters]
+    flops = (upd * flops_waypoint_iter(round(mean_dof)) + chains * mean_dof * F_CHAIN_JOINT
+             + tf * F_SPHERE_FK + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
+    # end to end through the C ABI with pinned host buffers
+    h_start = start.cpu().pin_memory()
+    h_goal = goal.cpu().pin_memory()
+    h_out = {k: (torch.empty(v.shape, dtype=v.dtype).pin_memory() if v is not None else None)
+             for k, v in out.items()}
+    ctx.plan_batch(probs, h_start, h_goal, prm, tuning=tuning, out=h_out)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        ctx.plan_batch(probs, h_start, h_goal, prm, tuning=tuning, out=h_out)
+    e2e_s = time.perf_counter() - t0
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    avg_s = kms / 1e3 / max(launches, 1)
+    achieved = flops / avg_s / 1e12
+    solved = L > 0
+    classes = {}
+    for (r, c, sc, W) in probs:
+        key = f"{['none', 'roll-pitch', 'z-plane'][c]}/W{W}"
+        classes[key] = classes.get(key, 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "config 5: batched uneven serving mix, one CUDA-graph launch",
+                   "problems": len(probs), "dof": [6, 7, 8],
+                   "obstacles_per_problem": "log-uniform [10, 5000], 50/30/20 spheres/boxes/"
+                                            "capsules, sizes x min(1, (200/n)^(1/3))",
+                   "constraints": ["none", "roll-pitch", "z-plane"], "W": [16, 32, 64],
+                   "max_rounds": BATCH_PARAMS["max_rounds"],
+                   "workers_per_problem": BATCH_PARAMS["workers"],
+                   "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
+        "p99_plan_ms": float(np.percentile(ms[solved], 99)) if solved.any() else None,
+        "p50_plan_ms_all": float(np.percentile(ms, 50)),
+        "p99_plan_ms_all": float(np.percentile(ms, 99)),
+        "success_rate": float(solved.mean()),
+        "waypoints_per_step": waypoints_step,
+        "classes": classes,
+        "tuning": tuning.as_dict(), "autotune_s": tune_s,
+        "e2e": {"value": waypoints_step * e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 2 * len(probs) * 8 * 4,
+                "d2h_bytes_per_step": sum(v.numel() * v.element_size()
+                                          for v in h_out.values() if v is not None)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "plan_batch_kernel (6 classes, one graph)",
+                     "flop_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
+                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
+                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
+                                  "counts; no measured FP32 peak)"},
+        "gpu_launches": int(launches) * sum(1 for v in classes.values() if v),
+        "clocks": clk,
+    }
+    return line, None
+
+
 def init_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -642,7 +808,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="plan", choices=["plan", "validate"])
+    ap.add_argument("--workload", default="plan", choices=["plan", "validate", "batch"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
@@ -660,11 +826,16 @@ def main():
     if args.workload == "plan":
         line, inputs = run_plan(args, world, rank, local)
         baseline = cpu_baseline_plan
+    elif args.workload == "batch":
+        if args.problems == PLAN_N:
+            args.problems = BATCH_N
+        line, inputs = run_batch(args, world, rank, local)
+        baseline = None
     else:
         line, inputs = run_validate(args, world, rank, local)
         baseline = cpu_baseline_validate
     if rank == 0:
-        if world == 1:
+        if world == 1 and baseline is not None:
             line["cpu_baseline"] = baseline(inputs, args.cpu_budget)
         print(json.dumps(line), flush=True)
 

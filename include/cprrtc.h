@@ -226,6 +226,82 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
                 int64_t* work);
 
+/* ---- batches of uneven planning problems ---- */
+
+/* One robot of a robot table (arguments of cprrtc_set_robot). */
+typedef struct {
+  const cprrtc_joint* joints;
+  int dof;
+  const cprrtc_sphere* spheres;
+  int n_spheres;
+  double ee[3];
+} cprrtc_robot_desc;
+
+#define CPRRTC_BATCH_MAX_ROBOTS 8
+#define CPRRTC_BATCH_MAX_CONSTRAINTS 8
+/* Problem classes of a batch: 2 * constraint type + (W > 32). */
+#define CPRRTC_BATCH_CLASSES 6
+
+/* Robot table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_ROBOTS; host pointers).
+ * Errors: as cprrtc_set_robot, E_UNSUPPORTED for n beyond the maximum. */
+int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n);
+
+/* Constraint table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_CONSTRAINTS). */
+int cprrtc_set_constraint_table(cprrtc_ctx* ctx, const cprrtc_constraint* constraints, int n);
+
+/* One problem of a batch: indices into the robot table, the constraint table and the scene
+ * batch (cprrtc_set_scene_batch), and its waypoints per motion (2..64). */
+typedef struct {
+  int robot;
+  int constraint;
+  int scene;
+  int W;
+} cprrtc_problem;
+
+/* Launch shape of each problem class: CTAs per SM (0: as many as fit) and whether the class
+ * stages its obstacles into shared memory (else they are read through L1). Neither changes
+ * any result: a problem's search depends only on its own inputs and the plan parameters. */
+typedef struct {
+  int ctas_per_sm[CPRRTC_BATCH_CLASSES];
+  int stage_obstacles[CPRRTC_BATCH_CLASSES];
+} cprrtc_tuning;
+
+/* Plans n problems of mixed robots, constraints, scenes and W in one go: every problem class
+ * runs one persistent kernel (grid of SMs x CTAs per SM) that takes problems from an atomic
+ * queue, longest expected first; the classes run concurrently. Each problem is planned
+ * exactly as cprrtc_plan would plan it with its own robot, constraint, scene and W (problem
+ * index p in the Philox counter). problems: host array. start, goal: [n][8] (first dof
+ * entries used). params: range, max_rounds, workers, max_nodes, max_connect, max_path and
+ * seed are used; W and use_scene_batch are ignored. tuning: NULL uses the last
+ * cprrtc_autotune_batch result (as many CTAs as fit, staging when it fits, if none). Outputs as cprrtc_plan with configurations padded to 8 floats: path
+ * [n][max_path][8], path_edges [n][max_path-1][Wmax][8] (Wmax = largest W of the batch; NULL
+ * allowed). Errors: E_NOT_CONFIGURED (tables or scene batch missing), E_INVALID_ARG (bad
+ * index, W, parameter), E_CUDA, E_OOM. */
+int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, const float* start,
+                      const float* goal, const cprrtc_plan_params* params,
+                      const cprrtc_tuning* tuning, int32_t* path_len, float* path,
+                      float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
+                      int64_t* work);
+
+/* Autotuner: for every class present in the batch, times short runs (trial_rounds rounds)
+ * of each launch shape (obstacles staged or read through L1; 1 up to the fitting number of
+ * CTAs per SM) and keeps the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
+ * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. */
+int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
+                          const float* start, const float* goal, const cprrtc_plan_params* params,
+                          int trial_rounds, cprrtc_tuning* out);
+
+/* Records one cprrtc_plan_batch into a CUDA graph held by the context (replacing any
+ * previous one); cprrtc_batch_replay launches it on the context's stream. Every array must
+ * be device memory; a replay reads the current contents of start and goal and overwrites
+ * the outputs. The problems, tables and scene batch are the ones at capture time. */
+int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
+                         const float* start, const float* goal, const cprrtc_plan_params* params,
+                         const cprrtc_tuning* tuning, int32_t* path_len, float* path,
+                         float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
+                         int64_t* work);
+int cprrtc_batch_replay(cprrtc_ctx* ctx);
+
 /* ---- planning without allocation ---- */
 
 /* Size of the library's fixed device scratch for cprrtc_plan_static: 16 MiB, held by every

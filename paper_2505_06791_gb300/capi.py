@@ -46,6 +46,27 @@ class cprrtc_plan_params(C.Structure):
                 ("max_path", C.c_int), ("seed", C.c_uint32), ("use_scene_batch", C.c_int)]
 
 
+class cprrtc_robot_desc(C.Structure):
+    _fields_ = [("joints", C.c_void_p), ("dof", C.c_int), ("spheres", C.c_void_p),
+                ("n_spheres", C.c_int), ("ee", C.c_double * 3)]
+
+
+class cprrtc_problem(C.Structure):
+    _fields_ = [("robot", C.c_int), ("constraint", C.c_int), ("scene", C.c_int), ("W", C.c_int)]
+
+
+BATCH_CLASSES = 6
+
+
+class cprrtc_tuning(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int * BATCH_CLASSES),
+                ("stage_obstacles", C.c_int * BATCH_CLASSES)]
+
+    def as_dict(self):
+        return {"ctas_per_sm": list(self.ctas_per_sm),
+                "stage_obstacles": list(self.stage_obstacles)}
+
+
 class CprrtcError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"cprrtc error {code}: {msg}")
@@ -76,6 +97,17 @@ _SIGS = {
     "cprrtc_plan_static": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                            C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_set_robot_table": [C.c_void_p, C.c_void_p, C.c_int],
+    "cprrtc_set_constraint_table": [C.c_void_p, C.c_void_p, C.c_int],
+    "cprrtc_plan_batch": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                          C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_autotune_batch": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                              C.POINTER(cprrtc_plan_params), C.c_int, C.c_void_p],
+    "cprrtc_batch_capture": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                             C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "cprrtc_batch_replay": [C.c_void_p],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
     "cprrtc_set_timing": [C.c_void_p, C.c_int],
     "cprrtc_work_counters": [C.c_void_p, C.c_void_p, C.c_int],
@@ -316,6 +348,87 @@ class Context:
                                 out.get("plan_ms"), out.get("work")))
         return out
 
+    # ---- batches of uneven problems ----
+    def set_robot_table(self, robots):
+        descs = (cprrtc_robot_desc * len(robots))()
+        keep = []
+        for i, rb in enumerate(robots):
+            j, sp = joints_array(rb), spheres_array(rb)
+            keep += [j, sp]
+            descs[i].joints = j.ctypes.data
+            descs[i].dof = rb.dof
+            descs[i].spheres = sp.ctypes.data
+            descs[i].n_spheres = len(sp)
+            for k in range(3):
+                descs[i].ee[k] = float(rb.ee[k])
+        self._check(self._L.cprrtc_set_robot_table(self.h, C.addressof(descs), len(robots)))
+        self.batch_dofs = [rb.dof for rb in robots]
+
+    def set_constraint_table(self, constraints):
+        arr = (cprrtc_constraint * len(constraints))(*[constraint_struct(c) for c in constraints])
+        self._check(self._L.cprrtc_set_constraint_table(self.h, C.addressof(arr),
+                                                        len(constraints)))
+
+    @staticmethod
+    def problems_array(problems):
+        """problems: iterable of (robot, constraint, scene, W)."""
+        problems = list(problems)
+        arr = (cprrtc_problem * max(1, len(problems)))()
+        for i, (r, c, sc, W) in enumerate(problems):
+            arr[i].robot, arr[i].constraint, arr[i].scene, arr[i].W = r, c, sc, W
+        return arr
+
+    def alloc_batch_outputs(self, n, params, max_W, like, edges=False):
+        mp = params.max_path
+        if _is_cuda(like):
+            import torch
+            d = like.device
+            out = dict(path_len=torch.empty(n, dtype=torch.int32, device=d),
+                       path=torch.empty((n, mp, 8), dtype=torch.float32, device=d),
+                       rounds=torch.empty(n, dtype=torch.int32, device=d),
+                       waypoints=torch.empty(n, dtype=torch.int64, device=d),
+                       plan_ms=torch.empty(n, dtype=torch.float32, device=d),
+                       work=torch.empty((n, 2), dtype=torch.int64, device=d))
+            out["path_edges"] = torch.empty((n, mp - 1, max_W, 8), dtype=torch.float32,
+                                            device=d) if edges else None
+            return out
+        out = dict(path_len=np.empty(n, np.int32), path=np.empty((n, mp, 8), np.float32),
+                   rounds=np.empty(n, np.int32), waypoints=np.empty(n, np.int64),
+                   plan_ms=np.empty(n, np.float32), work=np.empty((n, 2), np.int64))
+        out["path_edges"] = np.empty((n, mp - 1, max_W, 8), np.float32) if edges else None
+        return out
+
+    def plan_batch(self, problems, start, goal, params, tuning=None, out=None, edges=False):
+        """problems: list of (robot, constraint, scene, W); start, goal: [n][8]."""
+        probs = self.problems_array(problems)
+        n = len(list(problems))
+        max_W = max(p[3] for p in problems)
+        if out is None:
+            out = self.alloc_batch_outputs(n, params, max_W, start, edges)
+        self._check(cprrtc_plan_batch(self.h, probs, n, start, goal, params, tuning,
+                                      out["path_len"], out["path"], out.get("path_edges"),
+                                      out.get("rounds"), out.get("waypoints"),
+                                      out.get("plan_ms"), out.get("work")))
+        return out
+
+    def autotune_batch(self, problems, start, goal, params, trial_rounds=20):
+        probs = self.problems_array(problems)
+        t = cprrtc_tuning()
+        self._check(cprrtc_autotune_batch(self.h, probs, len(list(problems)), start, goal, params,
+                                          trial_rounds, t))
+        return t
+
+    def batch_capture(self, problems, start, goal, params, out, tuning=None):
+        probs = self.problems_array(problems)
+        self._check(cprrtc_batch_capture(self.h, probs, len(list(problems)), start, goal, params,
+                                         tuning, out["path_len"], out["path"],
+                                         out.get("path_edges"), out.get("rounds"),
+                                         out.get("waypoints"), out.get("plan_ms"),
+                                         out.get("work")))
+
+    def batch_replay(self):
+        self._check(cprrtc_batch_replay(self.h))
+
     def philox(self, key0, key1, counters):
         c = np.ascontiguousarray(counters, dtype=np.uint32)
         out = np.empty_like(c)
@@ -354,6 +467,32 @@ def cprrtc_plan_static(h, start, goal, n, params, path_len, path, path_edges, ro
                                     _ptr(waypoints), _ptr(plan_ms), _ptr(work))
 
 
+def cprrtc_plan_batch(h, problems, n, start, goal, params, tuning, path_len, path, path_edges,
+                      rounds, waypoints, plan_ms, work):
+    return lib().cprrtc_plan_batch(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
+                                   C.byref(params), C.addressof(tuning) if tuning else None,
+                                   _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
+                                   _ptr(waypoints), _ptr(plan_ms), _ptr(work))
+
+
+def cprrtc_autotune_batch(h, problems, n, start, goal, params, trial_rounds, out):
+    return lib().cprrtc_autotune_batch(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
+                                       C.byref(params), trial_rounds,
+                                       C.addressof(out) if out is not None else None)
+
+
+def cprrtc_batch_capture(h, problems, n, start, goal, params, tuning, path_len, path, path_edges,
+                         rounds, waypoints, plan_ms, work):
+    return lib().cprrtc_batch_capture(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
+                                      C.byref(params), C.addressof(tuning) if tuning else None,
+                                      _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
+                                      _ptr(waypoints), _ptr(plan_ms), _ptr(work))
+
+
+def cprrtc_batch_replay(h):
+    return lib().cprrtc_batch_replay(h)
+
+
 def cprrtc_philox(h, key0, key1, counters, n, out):
     return lib().cprrtc_philox(h, key0, key1, _ptr(counters), n, _ptr(out))
 
@@ -369,4 +508,6 @@ def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
 
 
 __all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
-           "cprrtc_project_configs", "cprrtc_plan", "cprrtc_plan_static", "cprrtc_philox"]
+           "cprrtc_project_configs", "cprrtc_plan", "cprrtc_plan_static", "cprrtc_philox",
+           "cprrtc_plan_batch", "cprrtc_autotune_batch", "cprrtc_batch_capture",
+           "cprrtc_batch_replay"]

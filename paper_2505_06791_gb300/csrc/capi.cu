@@ -1,6 +1,7 @@
 // C-ABI layer: context lifecycle, robot / scene / constraint upload, pointer staging and
 // the exported entry points declared in include/cprrtc.h.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,17 @@
 using namespace cprrtc;
 
 namespace {
+
+// Device buffers one batch launch references (kept alive while a captured graph exists).
+struct BatchRes {
+  int4* d_probs = nullptr;
+  size_t probs_cap = 0;
+  int* d_order = nullptr;
+  size_t order_cap = 0;
+  unsigned* d_counters = nullptr;
+  char* d_scratch = nullptr;
+  size_t scratch_cap = 0;
+};
 
 struct TimingRec {
   std::string name;
@@ -50,6 +62,20 @@ struct cprrtc_ctx {
   size_t plan_cap = 0;
   // executed-work totals (validate and plan kernels)
   unsigned long long* d_work = nullptr;
+  // batch tables
+  std::vector<RobotDev> tab_robots;
+  float4* d_tab_sph = nullptr;
+  size_t tab_sph_cap = 0;
+  int* d_tab_frm = nullptr;
+  size_t tab_frm_cap = 0;
+  std::vector<ConsDev> tab_cons;
+  cprrtc_tuning tuned{};
+  bool has_tuned = false;
+  BatchRes batch_res, graph_res;
+  cudaStream_t side[kBatchClasses] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kBatchClasses] = {};
+  cudaGraphExec_t graph_exec = nullptr;
   bool timing = false;
   std::vector<TimingRec> pending;
   std::map<std::string, std::pair<double, long long>> acc;
@@ -216,22 +242,81 @@ int upload(cprrtc_ctx* ctx, T** dst, size_t* cap, const std::vector<T>& src) {
 
 bool is_finite(double x) { return std::isfinite(x); }
 
-// Packs obstacles into the float4 stream the kernels read, component arrays per primitive:
-// spheres [n] {x,y,z,r}; boxes 4 x [n]: {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0};
-// capsules 2 x [n]: {p0, r} {p1 - p0, 1/|p1-p0|^2}.
+// 3-bit interleave helper of a 30-bit Morton code.
+uint32_t spread10(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Order of `centres` along a Morton curve over their bounding box (ties keep input order).
+std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres) {
+  const size_t n = centres.size();
+  std::vector<int> idx(n);
+  for (size_t i = 0; i < n; ++i) idx[i] = (int)i;
+  if (n < 2) return idx;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (auto& c : centres)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], c[k]);
+      hi[k] = std::max(hi[k], c[k]);
+    }
+  std::vector<uint32_t> code(n);
+  for (size_t i = 0; i < n; ++i) {
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+      const double span = hi[k] - lo[k];
+      const double t = span > 0 ? (centres[i][k] - lo[k]) / span : 0.0;
+      q[k] = (uint32_t)std::min(1023.0, std::max(0.0, std::floor(t * 1024.0)));
+    }
+    code[i] = spread10(q[0]) | (spread10(q[1]) << 1) | (spread10(q[2]) << 2);
+  }
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return code[a] < code[b]; });
+  return idx;
+}
+
+float round_down(double x) {
+  float f = (float)x;
+  return (double)f > x ? std::nextafter(f, -INFINITY) : f;
+}
+float round_up(double x) {
+  float f = (float)x;
+  return (double)f < x ? std::nextafter(f, INFINITY) : f;
+}
+
+// Packs obstacles into the float4 stream the kernels read. Each primitive kind is sorted
+// along a Morton curve (neighbours in the stream are neighbours in space; collision results
+// do not depend on the order) and stored as component arrays: spheres [n] {x,y,z,r}; boxes
+// 4 x [n]: {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0}; capsules 2 x [n]:
+// {p0, r} {p1 - p0, 1/|p1-p0|^2}. Then, per chunk of 32 consecutive obstacles, an
+// axis-aligned box containing every obstacle of the chunk (rounded outward to FP32).
 int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
                    const cprrtc_obs_box* box, int n_box, const cprrtc_obs_capsule* cap, int n_cap,
                    std::vector<float4>& v) {
+  const int n_obs = n_sph + n_box + n_cap;
+  const int n_chunks = (n_obs + kChunk - 1) / kChunk;
   const size_t s0 = v.size();
-  v.resize(s0 + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap);
+  v.resize(s0 + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap + 2 * (size_t)n_chunks);
   float4* out = v.data() + s0;
+  std::vector<std::array<double, 6>> aabb(n_obs);  // per obstacle, in stream order
+  std::vector<std::array<double, 3>> cen;
+  cen.resize(n_sph);
   for (int i = 0; i < n_sph; ++i) {
     const cprrtc_obs_sphere& o = sph[i];
     if (!is_finite(o.x) || !is_finite(o.y) || !is_finite(o.z) || !is_finite(o.r) || o.r < 0)
       return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad sphere " + std::to_string(i));
-    out[i] = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r);
+    cen[i] = {o.x, o.y, o.z};
   }
-  float4* bx = out + n_sph;
+  std::vector<int> ord = morton_order(cen);
+  for (int j = 0; j < n_sph; ++j) {
+    const cprrtc_obs_sphere& o = sph[ord[j]];
+    out[j] = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.r);
+    aabb[j] = {o.x - o.r, o.y - o.r, o.z - o.r, o.x + o.r, o.y + o.r, o.z + o.r};
+  }
+  cen.resize(n_box);
   for (int i = 0; i < n_box; ++i) {
     const cprrtc_obs_box& b = box[i];
     for (int k = 0; k < 3; ++k)
@@ -239,22 +324,60 @@ int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
         return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box " + std::to_string(i));
     for (int k = 0; k < 9; ++k)
       if (!is_finite(b.R[k])) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad box rotation");
-    bx[i] = make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]);
-    bx[n_box + i] = make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]);
-    bx[2 * n_box + i] = make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]);
-    bx[3 * n_box + i] = make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f);
+    cen[i] = {b.c[0], b.c[1], b.c[2]};
   }
-  float4* cp = bx + 4 * n_box;
+  ord = morton_order(cen);
+  float4* bx = out + n_sph;
+  for (int j = 0; j < n_box; ++j) {
+    const cprrtc_obs_box& b = box[ord[j]];
+    bx[j] = make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]);
+    bx[n_box + j] = make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]);
+    bx[2 * n_box + j] = make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]);
+    bx[3 * n_box + j] = make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f);
+    std::array<double, 6> a;
+    for (int r = 0; r < 3; ++r) {  // world half-extent along axis r: sum_k |R[r][k]| h_k
+      const double ext = std::fabs(b.R[3 * r]) * b.h[0] + std::fabs(b.R[3 * r + 1]) * b.h[1] +
+                         std::fabs(b.R[3 * r + 2]) * b.h[2];
+      a[r] = b.c[r] - ext;
+      a[3 + r] = b.c[r] + ext;
+    }
+    aabb[n_sph + j] = a;
+  }
+  cen.resize(n_cap);
   for (int i = 0; i < n_cap; ++i) {
     const cprrtc_obs_capsule& c = cap[i];
     for (int k = 0; k < 3; ++k)
       if (!is_finite(c.p0[k]) || !is_finite(c.p1[k]))
         return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad capsule " + std::to_string(i));
     if (!is_finite(c.r) || c.r < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "obstacles: bad capsule radius");
+    cen[i] = {0.5 * (c.p0[0] + c.p1[0]), 0.5 * (c.p0[1] + c.p1[1]), 0.5 * (c.p0[2] + c.p1[2])};
+  }
+  ord = morton_order(cen);
+  float4* cp = bx + 4 * n_box;
+  for (int j = 0; j < n_cap; ++j) {
+    const cprrtc_obs_capsule& c = cap[ord[j]];
     const double u[3] = {c.p1[0] - c.p0[0], c.p1[1] - c.p0[1], c.p1[2] - c.p0[2]};
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    cp[i] = make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r);
-    cp[n_cap + i] = make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f);
+    cp[j] = make_float4((float)c.p0[0], (float)c.p0[1], (float)c.p0[2], (float)c.r);
+    cp[n_cap + j] = make_float4((float)u[0], (float)u[1], (float)u[2], uu > 0 ? (float)(1.0 / uu) : 0.f);
+    std::array<double, 6> a;
+    for (int k = 0; k < 3; ++k) {
+      a[k] = std::min(c.p0[k], c.p1[k]) - c.r;
+      a[3 + k] = std::max(c.p0[k], c.p1[k]) + c.r;
+    }
+    aabb[n_sph + n_box + j] = a;
+  }
+  // chunk boxes, padded by 1e-5 m beyond the FP32 values the kernels test against
+  float4* cb = cp + 2 * n_cap;
+  for (int ch = 0; ch < n_chunks; ++ch) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int o = ch * kChunk; o < std::min(n_obs, (ch + 1) * kChunk); ++o)
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], aabb[o][k]);
+        hi[k] = std::max(hi[k], aabb[o][3 + k]);
+      }
+    cb[2 * ch] = make_float4(round_down(lo[0] - 1e-5), round_down(lo[1] - 1e-5), round_down(lo[2] - 1e-5), 0.f);
+    cb[2 * ch + 1] = make_float4(round_up(hi[0] + 1e-5), round_up(hi[1] + 1e-5), round_up(hi[2] + 1e-5), 0.f);
   }
   return CPRRTC_OK;
 }
@@ -312,6 +435,20 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_batch_tab);
   cudaFree(ctx->d_plan);
   cudaFree(ctx->d_work);
+  cudaFree(ctx->d_tab_sph);
+  cudaFree(ctx->d_tab_frm);
+  for (BatchRes* r : {&ctx->batch_res, &ctx->graph_res}) {
+    cudaFree(r->d_probs);
+    cudaFree(r->d_order);
+    cudaFree(r->d_counters);
+    cudaFree(r->d_scratch);
+  }
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  for (int c = 0; c < kBatchClasses; ++c) {
+    if (ctx->side[c]) cudaStreamDestroy(ctx->side[c]);
+    if (ctx->ev_join[c]) cudaEventDestroy(ctx->ev_join[c]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   for (auto& r : ctx->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -329,16 +466,22 @@ int cprrtc_set_stream(cprrtc_ctx* ctx, void* stream) {
 
 const char* cprrtc_last_error(const cprrtc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
-                     const cprrtc_sphere* spheres, int n_spheres, const double ee[3]) {
-  if (!ctx) return CPRRTC_E_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Validates one robot and converts it to the kernels' form: FP32 joint table, spheres sorted
+// by frame (loc, frm) and per-frame bounding spheres. Device pointers are left unset.
+int build_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof, const cprrtc_sphere* spheres,
+                int n_spheres, const double ee[3], RobotDev& rb, std::vector<float4>& loc,
+                std::vector<int>& frm) {
   if (!joints || !spheres || !ee) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_robot: null pointer");
   if (dof < 1 || dof > CPRRTC_MAX_DOF)
     return fail(ctx, dof < 1 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED, "set_robot: dof must be in [1, 8]");
   if (n_spheres < 1 || n_spheres > CPRRTC_MAX_SPHERES)
     return fail(ctx, n_spheres < 1 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED,
                 "set_robot: n_spheres must be in [1, 256]");
-  RobotDev rb{};
+  rb = RobotDev{};
   rb.dof = dof;
   rb.n_spheres = n_spheres;
   for (int k = 0; k < dof; ++k) {
@@ -372,8 +515,8 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
   }
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return spheres[a].frame < spheres[b].frame; });
-  std::vector<float4> loc(n_spheres);
-  std::vector<int> frm(n_spheres);
+  loc.assign(n_spheres, make_float4(0.f, 0.f, 0.f, 0.f));
+  frm.assign(n_spheres, 0);
   for (int i = 0; i < n_spheres; ++i) {
     const cprrtc_sphere& s = spheres[order[i]];
     loc[i] = make_float4((float)s.x, (float)s.y, (float)s.z, (float)s.r);
@@ -412,6 +555,21 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
     }
     rb.bound[f] = make_float4(b[0], b[1], b[2], std::nextafter((float)(R + 1e-5), 1e30f));
   }
+  return CPRRTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
+                     const cprrtc_sphere* spheres, int n_spheres, const double ee[3]) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  RobotDev rb;
+  std::vector<float4> loc;
+  std::vector<int> frm;
+  int rc0 = build_robot(ctx, joints, dof, spheres, n_spheres, ee, rb, loc, frm);
+  if (rc0) return rc0;
   DeviceGuard g(ctx->device);
   size_t cap1 = 0, cap2 = 0;
   if (ctx->d_spheres) { cudaFree(ctx->d_spheres); ctx->d_spheres = nullptr; }
@@ -433,7 +591,7 @@ int cprrtc_set_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sp
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (n_sph < 0 || n_box < 0 || n_cap < 0 || (n_sph && !sph) || (n_box && !box) || (n_cap && !cap))
     return fail(ctx, CPRRTC_E_INVALID_ARG, "set_obstacles: bad counts or null pointer");
-  if ((long long)n_sph + 4LL * n_box + 2LL * n_cap > (1LL << 26))
+  if ((long long)n_sph + 4LL * n_box + 2LL * n_cap > (1LL << 26) || (long long)n_sph + n_box + n_cap > (1LL << 20))
     return fail(ctx, CPRRTC_E_UNSUPPORTED, "set_obstacles: too many obstacles");
   std::vector<float4> v;
   int rc = pack_obstacles(ctx, sph, n_sph, box, n_box, cap, n_cap, v);
@@ -822,3 +980,488 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   if (e != cudaSuccess) return cuda_fail(ctx, e, "plan_static launch");
   return CPRRTC_OK;
 }
+
+
+// ---- batches of uneven problems ------------------------------------------------------------
+
+namespace {
+
+// Host-side preparation of a batch: problem descriptors, classes and dequeue orders.
+struct BatchPlan {
+  int n = 0;
+  std::vector<int4> probs;
+  std::vector<int> order;            // per class, concatenated
+  int off[kBatchClasses + 1] = {};   // class c: order[off[c] .. off[c + 1])
+  int max_W[kBatchClasses] = {}, max_S[kBatchClasses] = {}, max_f4[kBatchClasses] = {};
+  int max_W_all = 0;
+};
+
+int prepare_batch(cprrtc_ctx* ctx, const cprrtc_problem* probs, int n, BatchPlan& bp) {
+  if (ctx->tab_robots.empty() || ctx->tab_cons.empty())
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "batch: set the robot and constraint tables first");
+  if (ctx->n_scenes < 1) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "batch: set a scene batch first");
+  if (!probs || n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: bad problems");
+  if (is_device_ptr(probs)) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: problems must be host memory");
+  std::vector<int4> scene_tab(ctx->n_scenes);
+  if (cudaMemcpy(scene_tab.data(), ctx->d_batch_tab, sizeof(int4) * ctx->n_scenes,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(ctx, cudaGetLastError(), "batch: scene table");
+  bp = BatchPlan{};
+  bp.n = n;
+  bp.probs.resize(n);
+  std::vector<std::pair<double, int>> cls[kBatchClasses];
+  for (int p = 0; p < n; ++p) {
+    const cprrtc_problem& q = probs[p];
+    if (q.robot < 0 || q.robot >= (int)ctx->tab_robots.size() || q.constraint < 0 ||
+        q.constraint >= (int)ctx->tab_cons.size() || q.scene < 0 || q.scene >= ctx->n_scenes ||
+        q.W < 2 || q.W > CPRRTC_MAX_W)
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: bad problem " + std::to_string(p));
+    bp.probs[p] = make_int4(q.robot, q.constraint, q.scene, q.W);
+    const RobotDev& r = ctx->tab_robots[q.robot];
+    const int ct = ctx->tab_cons[q.constraint].type;
+    const int c = 2 * ct + (q.W > 32 ? 1 : 0);
+    const int4 sd = scene_tab[q.scene];
+    const int n_obs = sd.y + sd.z + sd.w;
+    const int f4 = SceneDev{nullptr, sd.y, sd.z, sd.w}.n_float4();
+    // expected cost for longest-first ordering: waypoints x (obstacles + robot spheres)
+    const double cost = (double)q.W * (n_obs + r.n_spheres) * (ct != kConsNone ? 2.0 : 1.0);
+    cls[c].push_back({cost, p});
+    bp.max_W[c] = std::max(bp.max_W[c], q.W);
+    bp.max_S[c] = std::max(bp.max_S[c], r.n_spheres);
+    bp.max_f4[c] = std::max(bp.max_f4[c], f4);
+    bp.max_W_all = std::max(bp.max_W_all, q.W);
+  }
+  for (int c = 0; c < kBatchClasses; ++c) {
+    std::stable_sort(cls[c].begin(), cls[c].end(),
+                     [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+                       return a.first > b.first;
+                     });
+    bp.off[c] = (int)bp.order.size();
+    for (auto& e : cls[c]) bp.order.push_back(e.second);
+  }
+  bp.off[kBatchClasses] = (int)bp.order.size();
+  return CPRRTC_OK;
+}
+
+cprrtc_tuning default_tuning() {
+  cprrtc_tuning t{};
+  for (int c = 0; c < kBatchClasses; ++c) {
+    t.ctas_per_sm[c] = 0;
+    t.stage_obstacles[c] = 1;
+  }
+  return t;
+}
+
+// Shared memory and grid of class c under tuning t (stage falls back to L1 if it does not fit).
+struct ClassLaunch {
+  bool on = false;
+  int workers = 8, grid = 0, stage = 0;
+  size_t smem = 0;
+};
+
+ClassLaunch class_launch(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuning& t, int workers,
+                         int c) {
+  ClassLaunch L;
+  const int nc = bp.off[c + 1] - bp.off[c];
+  if (nc == 0) return L;
+  L.workers = workers;
+  L.stage = t.stage_obstacles[c] ? 1 : 0;
+  L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, L.stage);
+  if (L.smem > ctx->dev.smem_optin) {
+    L.stage = 0;
+    L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, false);
+  }
+  if (L.smem > ctx->dev.smem_optin) return L;
+  const int occ = plan_batch_occupancy(c, L.workers, L.smem);
+  if (occ < 1) return L;
+  const int per_sm = t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
+  L.grid = std::min(nc, per_sm * ctx->dev.sm_count);
+  L.on = L.grid > 0;
+  return L;
+}
+
+template <class T>
+int ensure(cprrtc_ctx* ctx, T** p, size_t* cap, size_t count) {
+  if (count <= *cap && *p) return CPRRTC_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch allocation");
+  *cap = std::max<size_t>(count, 1);
+  return CPRRTC_OK;
+}
+
+// Uploads the problems and orders, sizes the per-CTA scratch and launches the classes in
+// cls_mask concurrently on side streams joined back into the context's stream.
+int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base,
+              const cprrtc_tuning& t, unsigned cls_mask, bool capturing) {
+  ClassLaunch L[kBatchClasses];
+  size_t scratch_off[kBatchClasses + 1] = {};
+  const size_t MN = (size_t)base.max_nodes;
+  for (int c = 0; c < kBatchClasses; ++c) {
+    scratch_off[c + 1] = scratch_off[c];
+    if (!((cls_mask >> c) & 1u)) continue;
+    L[c] = class_launch(ctx, bp, t, base.workers, c);
+    if (bp.off[c + 1] > bp.off[c] && !L[c].on)
+      return fail(ctx, CPRRTC_E_UNSUPPORTED, "batch: class " + std::to_string(c) + " does not fit an SM");
+    if (!L[c].on) continue;
+    const size_t ew = (size_t)bp.max_W[c] * 8;
+    const size_t slot = 2 * MN * 8 * 4 + 2 * MN * 4 + 2 * MN * ew * 4 +
+                        (size_t)L[c].workers * 8 * 4 + (size_t)L[c].workers * 2 * ew * 4;
+    scratch_off[c + 1] = scratch_off[c] + ((slot * L[c].grid + 255) & ~size_t(255));
+  }
+  if (!capturing) {
+    int rc = ensure(ctx, &res.d_probs, &res.probs_cap, bp.probs.size());
+    if (!rc) rc = ensure(ctx, &res.d_order, &res.order_cap, bp.order.size());
+    if (!rc && !res.d_counters) {
+      cudaError_t e = cudaMalloc(&res.d_counters, kBatchClasses * sizeof(unsigned));
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "batch counters");
+    }
+    if (!rc) rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, scratch_off[kBatchClasses]);
+    if (rc) return rc;
+    if (!bp.probs.empty()) {
+      cudaError_t e = cudaMemcpyAsync(res.d_probs, bp.probs.data(), bp.probs.size() * sizeof(int4),
+                                      cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.d_order, bp.order.data(), bp.order.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload");
+    }
+  }
+  BatchTables T{};
+  for (size_t i = 0; i < ctx->tab_robots.size(); ++i) T.robots[i] = ctx->tab_robots[i];
+  for (size_t i = 0; i < ctx->tab_cons.size(); ++i) T.cons[i] = ctx->tab_cons[i];
+  if (!ctx->ev_fork) {
+    if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "batch events");
+    for (int c = 0; c < kBatchClasses; ++c)
+      if (cudaStreamCreateWithFlags(&ctx->side[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(ctx, cudaGetLastError(), "batch streams");
+  }
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch fork");
+  for (int c = 0; c < kBatchClasses; ++c) {
+    if (!L[c].on) continue;
+    BatchArgs b{};
+    b.a = base;
+    b.a.stage_obs = L[c].stage;
+    b.a.max_scene_f4 = bp.max_f4[c];
+    b.problems = res.d_probs;
+    b.order = res.d_order + bp.off[c];
+    b.n_class = bp.off[c + 1] - bp.off[c];
+    b.counter = res.d_counters + c;
+    b.max_S = bp.max_S[c];
+    b.max_W = bp.max_W[c];
+    b.out_max_W = bp.max_W_all;
+    const size_t ew = (size_t)bp.max_W[c] * 8, B = (size_t)L[c].workers, G = (size_t)L[c].grid;
+    char* base_p = res.d_scratch + scratch_off[c];
+    b.nodes = reinterpret_cast<float*>(base_p);
+    b.parent = reinterpret_cast<int*>(b.nodes + G * 2 * MN * 8);
+    b.edges = reinterpret_cast<float*>(b.parent + G * 2 * MN);
+    b.pend = b.edges + G * 2 * MN * ew;
+    b.pend_edges = b.pend + G * B * 8;
+    if ((e = cudaStreamWaitEvent(ctx->side[c], ctx->ev_fork, 0)) != cudaSuccess ||
+        (e = launch_plan_batch(c, b, T, L[c].grid, L[c].smem, ctx->side[c])) != cudaSuccess ||
+        (e = cudaEventRecord(ctx->ev_join[c], ctx->side[c])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join[c], 0)) != cudaSuccess)
+      return cuda_fail(ctx, e, "batch launch");
+  }
+  return CPRRTC_OK;
+}
+
+PlanArgs batch_base(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, int n) {
+  PlanArgs a{};
+  a.n = n;
+  a.range = (float)pp->range;
+  a.W = 0;
+  a.max_rounds = pp->max_rounds;
+  a.workers = pp->workers;
+  a.max_nodes = pp->max_nodes;
+  a.max_connect = pp->max_connect;
+  a.max_path = pp->max_path;
+  a.seed = pp->seed;
+  a.scene_obs = ctx->d_batch_obs;
+  a.scenes = ctx->d_batch_tab;
+  a.work_counters = ctx->d_work;
+  return a;
+}
+
+int check_batch_params(cprrtc_ctx* ctx, const cprrtc_plan_params* pp) {
+  if (!pp || !(pp->range > 0) || !is_finite(pp->range) || pp->max_rounds < 1 || pp->max_nodes < 2 ||
+      pp->max_connect < 0 || pp->max_path < 2 || pp->workers < 1 || pp->workers > kMaxWorkers)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: bad parameters");
+  return CPRRTC_OK;
+}
+
+// Stages the batch's arrays (host or device) and fills base's pointers.
+void stage_batch_io(Staging& st, PlanArgs& a, size_t N, int max_path, int max_W, const float* start,
+                    const float* goal, int32_t* path_len, float* path, float* path_edges,
+                    int32_t* rounds, int64_t* waypoints, float* plan_ms, int64_t* work) {
+  st.input(start, N * 8 * sizeof(float), &a.start);
+  st.input(goal, N * 8 * sizeof(float), &a.goal);
+  st.output(path_len, N * sizeof(int32_t), &a.path_len);
+  st.output(path, N * (size_t)max_path * 8 * sizeof(float), &a.path);
+  st.output(path_edges, N * (size_t)(max_path - 1) * max_W * 8 * sizeof(float), &a.path_edges);
+  st.output(rounds, N * sizeof(int32_t), &a.rounds);
+  st.output(reinterpret_cast<long long*>(waypoints), N * sizeof(int64_t), &a.waypoints);
+  st.output(plan_ms, N * sizeof(float), &a.plan_ms);
+  st.output(reinterpret_cast<long long*>(work), N * 2 * sizeof(int64_t), &a.work);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!robots || n < 1) return fail(ctx, CPRRTC_E_INVALID_ARG, "robot table: empty");
+  if (n > CPRRTC_BATCH_MAX_ROBOTS) return fail(ctx, CPRRTC_E_UNSUPPORTED, "robot table: too many robots");
+  std::vector<RobotDev> tab(n);
+  std::vector<float4> all_loc;
+  std::vector<int> all_frm;
+  std::vector<size_t> off(n);
+  for (int i = 0; i < n; ++i) {
+    std::vector<float4> loc;
+    std::vector<int> frm;
+    int rc = build_robot(ctx, robots[i].joints, robots[i].dof, robots[i].spheres, robots[i].n_spheres,
+                         robots[i].ee, tab[i], loc, frm);
+    if (rc) return rc;
+    off[i] = all_loc.size();
+    all_loc.insert(all_loc.end(), loc.begin(), loc.end());
+    all_frm.insert(all_frm.end(), frm.begin(), frm.end());
+  }
+  DeviceGuard g(ctx->device);
+  int rc = upload(ctx, &ctx->d_tab_sph, &ctx->tab_sph_cap, all_loc);
+  if (!rc) rc = upload(ctx, &ctx->d_tab_frm, &ctx->tab_frm_cap, all_frm);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    tab[i].spheres = ctx->d_tab_sph + off[i];
+    tab[i].sphere_frame = ctx->d_tab_frm + off[i];
+  }
+  ctx->tab_robots = tab;
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_constraint_table(cprrtc_ctx* ctx, const cprrtc_constraint* cons, int n) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!cons || n < 1) return fail(ctx, CPRRTC_E_INVALID_ARG, "constraint table: empty");
+  if (n > CPRRTC_BATCH_MAX_CONSTRAINTS)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, "constraint table: too many constraints");
+  const ConsDev saved = ctx->cs;
+  std::vector<ConsDev> tab(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = cprrtc_set_constraint(ctx, &cons[i]);  // validates and converts
+    if (rc) {
+      ctx->cs = saved;
+      return rc;
+    }
+    tab[i] = ctx->cs;
+  }
+  ctx->cs = saved;
+  ctx->tab_cons = tab;
+  return CPRRTC_OK;
+}
+
+int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, const float* start,
+                      const float* goal, const cprrtc_plan_params* pp, const cprrtc_tuning* tuning,
+                      int32_t* path_len, float* path, float* path_edges, int32_t* rounds,
+                      int64_t* waypoints, float* plan_ms, int64_t* work) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  int rc = check_batch_params(ctx, pp);
+  if (rc) return rc;
+  if (n == 0) return CPRRTC_OK;
+  if (!start || !goal || !path_len || !path) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: null pointer");
+  DeviceGuard g(ctx->device);
+  BatchPlan bp;
+  rc = prepare_batch(ctx, problems, n, bp);
+  if (rc) return rc;
+  PlanArgs a = batch_base(ctx, pp, n);
+  Staging st;
+  stage_batch_io(st, a, (size_t)n, pp->max_path, bp.max_W_all, start, goal, path_len, path,
+                 path_edges, rounds, waypoints, plan_ms, work);
+  rc = st.begin(ctx);
+  if (rc) return rc;
+  const cprrtc_tuning t = tuning ? *tuning : (ctx->has_tuned ? ctx->tuned : default_tuning());
+  LaunchTimer tm(ctx, "plan_batch");
+  rc = run_batch(ctx, bp, ctx->batch_res, a, t, (1u << kBatchClasses) - 1u, false);
+  tm.done();
+  if (rc) return rc;
+  return st.end(ctx);
+}
+
+int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, const float* start,
+                          const float* goal, const cprrtc_plan_params* pp, int trial_rounds,
+                          cprrtc_tuning* out) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  int rc = check_batch_params(ctx, pp);
+  if (rc) return rc;
+  if (trial_rounds < 1) return fail(ctx, CPRRTC_E_INVALID_ARG, "autotune: trial_rounds < 1");
+  if (n < 1 || !start || !goal) return fail(ctx, CPRRTC_E_INVALID_ARG, "autotune: no problems");
+  DeviceGuard g(ctx->device);
+  BatchPlan bp;
+  rc = prepare_batch(ctx, problems, n, bp);
+  if (rc) return rc;
+  cprrtc_plan_params trial = *pp;
+  trial.max_rounds = trial_rounds;
+  PlanArgs a = batch_base(ctx, &trial, n);
+  a.work_counters = nullptr;
+  // device outputs of the trials (the tuner allocates; plan calls do not need to)
+  const size_t N = (size_t)n;
+  float *d_path = nullptr, *d_ms = nullptr;
+  int32_t *d_len = nullptr, *d_rounds = nullptr;
+  long long* d_wp = nullptr;
+  cudaError_t e = cudaMalloc(&d_path, N * trial.max_path * 8 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_len, N * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rounds, N * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_wp, N * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&d_ms, N * sizeof(float));
+  auto release = [&]() {
+    cudaFree(d_path);
+    cudaFree(d_len);
+    cudaFree(d_rounds);
+    cudaFree(d_wp);
+    cudaFree(d_ms);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(ctx, e, "autotune allocation");
+  }
+  a.path = d_path;
+  a.path_len = d_len;
+  a.rounds = d_rounds;
+  a.waypoints = d_wp;
+  a.plan_ms = d_ms;
+  Staging st;
+  st.input(start, N * 8 * sizeof(float), &a.start);
+  st.input(goal, N * 8 * sizeof(float), &a.goal);
+  rc = st.begin(ctx);
+  if (rc) {
+    release();
+    return rc;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cprrtc_tuning best = ctx->has_tuned ? ctx->tuned : default_tuning();
+  std::vector<long long> wp(N);
+  for (int c = 0; c < kBatchClasses && !rc; ++c) {
+    if (bp.off[c + 1] == bp.off[c]) continue;
+    double best_rate = -1.0;
+    for (int stage = 1; stage >= 0 && !rc; --stage) {
+      cprrtc_tuning t = best;
+      t.stage_obstacles[c] = stage;
+      t.ctas_per_sm[c] = 0;
+      const ClassLaunch full = class_launch(ctx, bp, t, pp->workers, c);
+      if (!full.on || full.stage != stage) continue;  // staging did not fit: tried as L1
+      const int occ = plan_batch_occupancy(c, full.workers, full.smem);
+      for (int ctas = 1; ctas <= std::min(occ, 4) && !rc; ++ctas) {
+        t.ctas_per_sm[c] = ctas;
+        cudaEventRecord(e0, ctx->stream);
+        rc = run_batch(ctx, bp, ctx->batch_res, a, t, 1u << c, false);
+        if (rc) break;
+        cudaEventRecord(e1, ctx->stream);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          rc = cuda_fail(ctx, e, "autotune trial");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaMemcpy(wp.data(), d_wp, N * sizeof(long long), cudaMemcpyDeviceToHost);
+        double total = 0.0;
+        for (int i = bp.off[c]; i < bp.off[c + 1]; ++i) total += (double)wp[bp.order[i]];
+        const double rate = ms > 0.f ? total / ms : 0.0;
+        if (rate > best_rate) {
+          best_rate = rate;
+          best.stage_obstacles[c] = stage;
+          best.ctas_per_sm[c] = ctas;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  release();
+  if (rc) return rc;
+  ctx->tuned = best;
+  ctx->has_tuned = true;
+  if (out) *out = best;
+  return CPRRTC_OK;
+}
+
+int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, const float* start,
+                         const float* goal, const cprrtc_plan_params* pp, const cprrtc_tuning* tuning,
+                         int32_t* path_len, float* path, float* path_edges, int32_t* rounds,
+                         int64_t* waypoints, float* plan_ms, int64_t* work) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  int rc = check_batch_params(ctx, pp);
+  if (rc) return rc;
+  if (n < 1 || !start || !goal || !path_len || !path)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "batch capture: null pointer or no problems");
+  DeviceGuard g(ctx->device);
+  const void* arrays[] = {start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work};
+  for (const void* ptr : arrays)
+    if (ptr && !is_device_ptr(ptr))
+      return fail(ctx, CPRRTC_E_INVALID_ARG, "batch capture: every array must be device memory");
+  BatchPlan bp;
+  rc = prepare_batch(ctx, problems, n, bp);
+  if (rc) return rc;
+  PlanArgs a = batch_base(ctx, pp, n);
+  Staging st;  // device pointers only: no copies
+  stage_batch_io(st, a, (size_t)n, pp->max_path, bp.max_W_all, start, goal, path_len, path,
+                 path_edges, rounds, waypoints, plan_ms, work);
+  const cprrtc_tuning t = tuning ? *tuning : (ctx->has_tuned ? ctx->tuned : default_tuning());
+  // buffers and attributes first (no allocation while capturing), then record the launches
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  rc = run_batch(ctx, bp, ctx->graph_res, a, t, 0u, false);  // uploads, no launch
+  if (rc) return rc;
+  BatchRes& res = ctx->graph_res;
+  {
+    // scratch for every class (run_batch with an empty mask sized nothing)
+    size_t need = 0;
+    const size_t MN = (size_t)pp->max_nodes;
+    for (int c = 0; c < kBatchClasses; ++c) {
+      const ClassLaunch L = class_launch(ctx, bp, t, pp->workers, c);
+      if (!L.on) continue;
+      const size_t ew = (size_t)bp.max_W[c] * 8;
+      const size_t slot = 2 * MN * 8 * 4 + 2 * MN * 4 + 2 * MN * ew * 4 +
+                          (size_t)L.workers * 8 * 4 + (size_t)L.workers * 2 * ew * 4;
+      need += (slot * L.grid + 255) & ~size_t(255);
+    }
+    rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, need);
+    if (rc) return rc;
+  }
+  if (!ctx->stream) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch capture: needs a non-default stream");
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture begin");
+  rc = run_batch(ctx, bp, res, a, t, (1u << kBatchClasses) - 1u, true);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(ctx->stream, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture end");
+  e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph instantiate");
+  return CPRRTC_OK;
+}
+
+int cprrtc_batch_replay(cprrtc_ctx* ctx) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->graph_exec) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "batch replay: nothing captured");
+  DeviceGuard g(ctx->device);
+  LaunchTimer tm(ctx, "plan_batch");
+  cudaError_t e = cudaGraphLaunch(ctx->graph_exec, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch replay");
+  return CPRRTC_OK;
+}
+
+}  // extern "C"

@@ -42,10 +42,16 @@ struct RobotDev {
 // consecutive obstacles read consecutive float4s: spheres [n_sph] {x,y,z,rho}; boxes
 // 4 arrays of [n_box]: {cx,cy,cz,hx} {col0, hy} {col1, hz} {col2, 0} where col_k is column
 // k of R (box axis k); capsules 2 arrays of [n_cap]: {p0, rc} {u = p1 - p0, 1/|u|^2}.
+// After the obstacle arrays, every chunk of 32 consecutive obstacles (in the order spheres,
+// boxes, capsules) has an axis-aligned box containing all of them: 2 float4 {min, -} {max, -}.
+constexpr int kChunk = 32;
 struct SceneDev {
   const float4* obs;
   int n_sph, n_box, n_cap;
-  __host__ __device__ int n_float4() const { return n_sph + 4 * n_box + 2 * n_cap; }
+  __host__ __device__ int n_obs() const { return n_sph + n_box + n_cap; }
+  __host__ __device__ int n_chunks() const { return (n_obs() + kChunk - 1) / kChunk; }
+  __host__ __device__ int chunk_off() const { return n_sph + 4 * n_box + 2 * n_cap; }
+  __host__ __device__ int n_float4() const { return chunk_off() + 2 * n_chunks(); }
 };
 
 // Task constraint and Algorithm 1 parameters in FP32.

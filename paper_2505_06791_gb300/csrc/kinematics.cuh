@@ -24,8 +24,10 @@ constexpr float kInvPi = 0.318309886183790671538f;
 // What one chain evaluation leaves for the task error and Jacobian.
 struct ChainState {
   float x0, x1, x2, y0, y1, y2, z0, z1, z2, p0, p1, p2;  // last frame (dof)
-  float zx[kMaxDof], zy[kMaxDof], zz[kMaxDof];           // axis of joint k (z of frame k)
-  float px[kMaxDof], py[kMaxDof];                        // origin of frame k
+  float zx[kMaxDof], zy[kMaxDof];  // x, y of the axis of joint k (z of frame k)
+  // z-plane Jacobian term of joint k: (z_k x p_k)_z for revolute joints (so that
+  // J_k = zx_k pe_y - zy_k pe_x - zm_k), -z_k,z for prismatic ones (zx = zy = 0 there)
+  float zm[kMaxDof];
 };
 
 // Runs the DH chain for configuration q. If `fr` is non-null, frames 1..dof are written to
@@ -39,8 +41,12 @@ __device__ __forceinline__ void chain(const RobotDev& rb, const float* q, float*
 #pragma unroll
   for (int k = 0; k < kMaxDof; ++k) {
     if (k < rb.dof) {
-      s.zx[k] = z0; s.zy[k] = z1; s.zz[k] = z2; s.px[k] = p0; s.py[k] = p1;
       const JointDev& J = rb.j[k];
+      if (J.prismatic) {
+        s.zx[k] = 0.f; s.zy[k] = 0.f; s.zm[k] = -z2;
+      } else {
+        s.zx[k] = z0; s.zy[k] = z1; s.zm[k] = fmaf(z0, p1, -z1 * p0);
+      }
       float ct, st, d = J.d;
       if (J.prismatic) {
         ct = J.ct0;
@@ -77,7 +83,7 @@ template <int CT>
 struct Task {
   float e0, e1;
   // roll/pitch: J0_k = (x0 zx_k + x1 zy_k) * c0,  J1_k = (x0 zy_k - x1 zx_k) * c1
-  // z-plane:    J0_k = zx_k (pe1 - py_k) - zy_k (pe0 - px_k)   (zz_k for prismatic joints)
+  // z-plane:    J0_k = zx_k pe1 - zy_k pe0 - zm_k  (= (z_k x (p_e - p_k))_z, or z_k,z)
   float c0, c1, pe0, pe1;
 };
 
@@ -114,8 +120,7 @@ __device__ __forceinline__ void jac_entry(const RobotDev& rb, const ChainState& 
     j0 = rev ? fmaf(s.x0, s.zx[k], s.x1 * s.zy[k]) * t.c0 : 0.f;
     j1 = rev ? fmaf(s.x0, s.zy[k], -s.x1 * s.zx[k]) * t.c1 : 0.f;
   } else if (CT == kConsZPlane) {
-    j0 = rb.j[k].prismatic ? s.zz[k]
-                           : fmaf(s.zx[k], t.pe1 - s.py[k], -s.zy[k] * (t.pe0 - s.px[k]));
+    j0 = fmaf(s.zx[k], t.pe1, fmaf(-s.zy[k], t.pe0, -s.zm[k]));
     j1 = 0.f;
   } else {
     j0 = j1 = 0.f;

@@ -59,6 +59,37 @@ struct PlanArgs {
   int stage_obs;            // set by the launcher
 };
 
+// Persistent batch of uneven planning problems (one launch).
+// Robot and constraint tables of a batch, passed by value (kernel parameter space).
+constexpr int kBatchMaxRobots = 8;
+constexpr int kBatchMaxCons = 8;
+struct BatchTables {
+  RobotDev robots[kBatchMaxRobots];
+  ConsDev cons[kBatchMaxCons];
+};
+
+struct BatchArgs {
+  PlanArgs a;                // shared parameters, scene batch, outputs ([n][8] configurations)
+  const int4* problems;      // [n] {robot, constraint, scene, W}
+  const int* order;          // [n_class] this class's problems in dequeue order
+  int n_class;
+  unsigned* counter;         // this class's dequeue counter (zeroed by the launcher)
+  int max_S, max_W;          // largest robot sphere count and W of this class
+  int out_max_W;             // largest W of the whole batch (path_edges row stride)
+  float* nodes;              // per CTA slot: [2][max_nodes][8]
+  int* parent;               // per CTA slot: [2][max_nodes]
+  float* edges;              // per CTA slot: [2][max_nodes][max_W * 8]
+  float* pend;               // per CTA slot: [workers][8]
+  float* pend_edges;         // per CTA slot: [workers][2][max_W * 8]
+};
+
+// Problem classes: 2 * constraint type + (W > 32).
+constexpr int kBatchClasses = 6;
+size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage);
+int plan_batch_occupancy(int cls, int workers, size_t smem);
+cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
+                              cudaStream_t stream);
+
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
                         const DeviceInfo& dev, cudaStream_t stream);

@@ -317,8 +317,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // Exact culling in three levels (a miss at a level proves a miss of everything under it,
 // every radius padded by at least 1e-5 m, far above the FP32 error of the tests):
 //  1. per motion: each frame's bounding sphere is swept over the waypoints (a ball around
-//     the box of its centres); each obstacle is tested once against every swept bound and
-//     the obstacles that touch one are listed with the frames they touch;
+//     the box of its centres); each chunk of 32 obstacles is tested through its bounding
+//     box, then each obstacle of a touched chunk against every swept bound, and the
+//     obstacles that touch one are listed with the frames they touch;
 //  2. per waypoint (lane), frame by frame along the chain: the frame's bounding sphere
 //     against each listed obstacle of that frame;
 //  3. the frame's robot spheres, for lanes whose bound touched the obstacle.
@@ -395,10 +396,42 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
   }
 
   int best = 0x7fffffff;  // smallest colliding waypoint found so far
-  for (int o0 = 0; o0 < n_obs;) {
+  const int n_chunks = sc.n_chunks();
+  int cb = 0;          // next group of 32 chunks to screen
+  unsigned near = 0u;  // chunks of the current group (base cb - 32) still to list
+  bool listed_all = false;
+  while (!listed_all) {
     // ---- candidate list: obstacles touching a swept bound, with the frames they touch ----
     int n_cand = 0;
-    while (o0 < n_obs && n_cand + 32 <= kCandMax) {
+    while (n_cand + 32 <= kCandMax) {
+      if (!near) {
+        if (cb >= n_chunks) {
+          listed_all = true;
+          break;
+        }
+        // lanes screen 32 chunks at once: chunk box against every swept frame bound
+        const int ch = cb + lane;
+        bool hit_chunk = false;
+        if (ch < n_chunks) {
+          const float4* cbx = obs + sc.chunk_off() + 2 * ch;
+          const float4 lo = cbx[0], hi = cbx[1];
+          for (int f = 0; f <= dof && !hit_chunk; ++f) {
+            if (S.bnd[f].w < 0.f) continue;
+            const float4 b = S.sbnd[f];
+            const float e0 = fmaxf(fmaxf(lo.x - b.x, b.x - hi.x), 0.f);
+            const float e1 = fmaxf(fmaxf(lo.y - b.y, b.y - hi.y), 0.f);
+            const float e2 = fmaxf(fmaxf(lo.z - b.z, b.z - hi.z), 0.f);
+            const float rr = b.w + 1e-5f;
+            hit_chunk = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < rr * rr;
+          }
+        }
+        near = __ballot_sync(kFull, hit_chunk);
+        work.p_box += (unsigned)(rb.bound_count * min(32, n_chunks - cb));
+        cb += 32;
+        continue;
+      }
+      const int o0 = (cb - 32 + __ffs(near) - 1) * kChunk;
+      near &= near - 1u;
       const int o = o0 + lane;
       unsigned mask = 0u;
       if (o < n_obs) {
@@ -410,9 +443,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       const unsigned bal = __ballot_sync(kFull, mask != 0u);
       if (mask) S.cand[n_cand + __popc(bal & ((1u << lane) - 1u))] = (unsigned)o | (mask << 20);
       n_cand += __popc(bal);
-      const int hi = min(o0 + 32, n_obs);
-      work.add_tests(sc, o0, hi, rb.bound_count);
-      o0 = hi;
+      work.add_tests(sc, o0, min(o0 + kChunk, n_obs), rb.bound_count);
     }
     __syncwarp();
     if (n_cand == 0) continue;

@@ -22,7 +22,25 @@
 
 namespace cprrtc {
 
+// One planning problem's inputs, scratch and outputs.
+struct ProblemView {
+  int p;                  // problem index: Philox counter and output slot
+  const float* start;     // dof floats
+  const float* goal;
+  int W;
+  float* nodes;           // [2][max_nodes][8]
+  int* parent;            // [2][max_nodes]
+  float* edges;           // [2][max_nodes][W * dof]
+  float* pend;            // [workers][8]
+  float* pend_edges;      // [workers][2][W * dof]
+  float* path;            // [max_path][ostride]
+  float* path_edges;      // [max_path - 1][estride] or null
+  int ostride;            // floats per configuration in the path outputs
+  int estride;            // floats per edge in path_edges (>= W * ostride)
+};
+
 struct PlanShared {
+  ProblemView pv;              // the problem being planned (uniform over the CTA)
   int count0[2];               // tree sizes when the round began
   int padd[kMaxWorkers];       // 1 if the warp produced a node this round
   int ptree[kMaxWorkers];      // the warp's chain tree
@@ -153,11 +171,13 @@ __device__ __forceinline__ void copy_warp(float* dst, const float* src, int coun
   for (int i = threadIdx.x & 31; i < count; i += 32) dst[i] = src[i];
 }
 
-// Copies a W x dof edge, reversing the waypoint order when `rev`.
-__device__ __forceinline__ void copy_edge(float* dst, const float* src, int W, int dof, bool rev) {
-  for (int i = threadIdx.x & 31; i < W * dof; i += 32) {
-    const int w = i / dof, k = i - w * dof;
-    dst[i] = src[(rev ? (W - 1 - w) : w) * dof + k];
+// Copies a W x dof edge (packed) to rows of `ostride` floats, reversing the waypoint order
+// when `rev`; row entries past dof are zeroed.
+__device__ __forceinline__ void copy_edge(float* dst, const float* src, int W, int dof,
+                                          int ostride, bool rev) {
+  for (int i = threadIdx.x & 31; i < W * ostride; i += 32) {
+    const int w = i / ostride, k = i - w * ostride;
+    dst[i] = k < dof ? src[(rev ? (W - 1 - w) : w) * dof + k] : 0.f;
   }
 }
 
@@ -166,11 +186,11 @@ struct MotionWork {  // per warp (32-bit suffices for one launch)
   unsigned cc;    // waypoints collision-checked
 };
 
-// Interpolate q0 -> q1, project (at most cs.max_iters iterations), FK + CC from waypoint 1
+// Interpolate q0 -> q1, project (at most max_iters iterations), FK + CC from waypoint 1
 // stopping at the first collision found.
 template <int CT, int WPL>
 __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDev& sc,
-                                               const ConsDev& cs, MotionWork& work,
+                                               const ConsDev& cs, int max_iters, MotionWork& work,
                                                WorkCount& wc, const float4* obs,
                                                const CcShared& S, const float* q0,
                                                const float* q1, int W,
@@ -179,7 +199,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 #pragma unroll
   for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
   const float tau = step_threshold(cs, q0, q1, W, rb.dof);
-  const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
+  const ProjResult pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau);
   __syncwarp();
   work.proj += (unsigned)pr.updates;
   wc.updates += (unsigned)pr.updates;
@@ -201,33 +221,18 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 #define CPRRTC_PLAN_REGS
 #endif
 
-template <int CT, int WPL>
-__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
-                                             PlanArgs a) {
-  const int p = blockIdx.x;
-  if (p >= a.n) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int B = a.workers, dof = rb.dof, W = a.W;
 
-  SceneDev sc = shared_scene;
-  if (a.scenes) {
-    const int4 d = a.scenes[p];
-    sc.obs = a.scene_obs + d.x;
-    sc.n_sph = d.y;
-    sc.n_box = d.z;
-    sc.n_cap = d.w;
-  }
-  extern __shared__ __align__(16) char smem[];
-  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, W, B, sizeof(PlanShared));
-  const int n4 = sc.n_float4();
-  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
-  if (a.stage_obs)
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
-  stage_robot(rb, smem, L);
-  const float4* obs = a.stage_obs ? s_obs : sc.obs;
-  const CcShared S = cc_shared(smem, L, warp);
-  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
-  PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+// The planner for one problem, run by the whole CTA (one warp per worker). Shared memory
+// (robot tables, obstacles, per-warp scratch) is staged by the caller.
+template <int CT, int WPL>
+__device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
+                                             const float4* obs, const ConsDev& cs,
+                                             const PlanArgs& a, const ProblemView& P,
+                                             const CcShared& S, PlanShared* sh,
+                                             WorkCount& wc) {
+  const int p = P.p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int B = blockDim.x >> 5, dof = rb.dof, W = P.W;
   if (threadIdx.x == 0) {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -235,19 +240,19 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
   }
 
   const size_t wd = (size_t)W * dof;
-  const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
+  const int MN = a.max_nodes;
   // tree t of this problem (computed, not tabulated: a table indexed by t lives in local memory)
-  auto nodes = [&](int t) { return a.nodes + (tree0 + (size_t)t * a.max_nodes) * 8; };
-  auto parent = [&](int t) { return a.parent + tree0 + (size_t)t * a.max_nodes; };
-  auto edges = [&](int t) { return a.edges + (tree0 + (size_t)t * a.max_nodes) * wd; };
-  float* wnode = a.pend + ((size_t)p * B + warp) * 8;              // node produced this round
-  float* wedge = a.pend_edges + ((size_t)p * B + warp) * 2 * wd;   // its motion, then the hop
+  auto nodes = [&](int t) { return P.nodes + (size_t)t * MN * 8; };
+  auto parent = [&](int t) { return P.parent + (size_t)t * MN; };
+  auto edges = [&](int t) { return P.edges + (size_t)t * MN * wd; };
+  float* wnode = P.pend + (size_t)warp * 8;              // node produced this round
+  float* wedge = P.pend_edges + (size_t)warp * 2 * wd;   // its motion, then the hop
 
   if (warp == 0) {
     float q[kMaxDof];
-    load_cfg(a.start + (size_t)p * dof, dof, q);
+    load_cfg(P.start, dof, q);
     store_cfg(nodes(0), q, dof);
-    load_cfg(a.goal + (size_t)p * dof, dof, q);
+    load_cfg(P.goal, dof, q);
     store_cfg(nodes(1), q, dof);
     if (lane == 0) {
       parent(0)[0] = -1;
@@ -257,9 +262,6 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     }
   }
   __syncthreads();
-
-  ConsDev hop = cs;
-  hop.max_iters = 1;
   const float connect_radius = 10.f * cs.tau_floor;
   unsigned wp = 0;
   MotionWork work{0u, 0u};
@@ -292,7 +294,8 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
       copy_cfg(q1, qt, dof);
     }
     float q[WPL][kMaxDof];
-    const int st = validate_motion<CT, WPL>(rb, sc, mode == 2 ? hop : cs, work, wc, obs, S,
+    // the closing hop is checked as it stands: one Alg. 1 iteration
+    const int st = validate_motion<CT, WPL>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
                                             cur, q1, W, q);
     wp += W;
     int add = 0, conn = 0;
@@ -383,7 +386,6 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     sh->wproj[warp] = work.proj;
     sh->wcc[warp] = work.cc;
   }
-  wc.flush(a.work_counters);
 
   if (win >= 0 && warp == win) {
     // path: root_a .. last, closing hop, target .. root_b; reversed when tree a is the
@@ -394,29 +396,31 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     for (int v = target; v >= 0; v = parent(tb)[v]) ++len_b;
     const int total = len_a + len_b;
     const bool flip = ta == 1;
-    float* path = a.path + (size_t)p * a.max_path * dof;
-    float* pe = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
+    const int os = P.ostride;
+    const size_t we = (size_t)P.estride;  // floats per output edge
+    float* path = P.path;
+    float* pe = P.path_edges;
     if (total <= a.max_path) {
       int pos = len_a - 1;
       for (int v = last; v >= 0; v = parent(ta)[v], --pos) {
         const int np = flip ? total - 1 - pos : pos;
-        copy_warp(path + (size_t)np * dof, nodes(ta) + (size_t)v * 8, dof);
+        copy_warp(path + (size_t)np * os, nodes(ta) + (size_t)v * 8, os);
         if (pe && parent(ta)[v] >= 0) {  // edge pos-1 -> pos is v's incoming motion
           const int e = flip ? total - 1 - pos : pos - 1;
-          copy_edge(pe + (size_t)e * wd, edges(ta) + (size_t)v * wd, W, dof, flip);
+          copy_edge(pe + (size_t)e * we, edges(ta) + (size_t)v * wd, W, dof, os, flip);
         }
       }
       if (pe) {  // closing hop: last -> target
         const int e = flip ? total - 1 - len_a : len_a - 1;
-        copy_edge(pe + (size_t)e * wd, wedge + wd, W, dof, flip);
+        copy_edge(pe + (size_t)e * we, wedge + wd, W, dof, os, flip);
       }
       pos = len_a;
       for (int v = target; v >= 0; v = parent(tb)[v], ++pos) {
         const int np = flip ? total - 1 - pos : pos;
-        copy_warp(path + (size_t)np * dof, nodes(tb) + (size_t)v * 8, dof);
+        copy_warp(path + (size_t)np * os, nodes(tb) + (size_t)v * 8, os);
         if (pe && parent(tb)[v] >= 0) {  // edge pos -> pos+1 is v's incoming motion reversed
           const int e = flip ? total - 2 - pos : pos;
-          copy_edge(pe + (size_t)e * wd, edges(tb) + (size_t)v * wd, W, dof, !flip);
+          copy_edge(pe + (size_t)e * we, edges(tb) + (size_t)v * wd, W, dof, os, !flip);
         }
       }
     }
@@ -441,6 +445,160 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
     if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sh->t_start) * 1e-6);
   }
+}
+
+template <int CT, int WPL>
+__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
+                                             PlanArgs a) {
+  const int p = blockIdx.x;
+  if (p >= a.n) return;
+  const int warp = threadIdx.x >> 5;
+  const int B = a.workers, dof = rb.dof, W = a.W;
+  SceneDev sc = shared_scene;
+  if (a.scenes) {
+    const int4 d = a.scenes[p];
+    sc.obs = a.scene_obs + d.x;
+    sc.n_sph = d.y;
+    sc.n_box = d.z;
+    sc.n_cap = d.w;
+  }
+  extern __shared__ __align__(16) char smem[];
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, W, B, sizeof(PlanShared));
+  const int n4 = sc.n_float4();
+  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
+  if (a.stage_obs)
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
+  stage_robot(rb, smem, L);
+  const float4* obs = a.stage_obs ? s_obs : sc.obs;
+  const CcShared S = cc_shared(smem, L, warp);
+  PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
+  const size_t wd = (size_t)W * dof;
+  const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
+  if (threadIdx.x == 0) {
+    ProblemView& P = sh->pv;
+    P.p = p;
+    P.start = a.start + (size_t)p * dof;
+    P.goal = a.goal + (size_t)p * dof;
+    P.W = W;
+    P.nodes = a.nodes + tree0 * 8;
+    P.parent = a.parent + tree0;
+    P.edges = a.edges + tree0 * wd;
+    P.pend = a.pend + (size_t)p * B * 8;
+    P.pend_edges = a.pend_edges + (size_t)p * B * 2 * wd;
+    P.path = a.path + (size_t)p * a.max_path * dof;
+    P.path_edges = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
+    P.ostride = dof;
+    P.estride = (int)wd;
+  }
+  __syncthreads();
+  plan_problem<CT, WPL>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
+  wc.flush(a.work_counters);
+}
+
+// ---- persistent batch of uneven problems --------------------------------------------------
+//
+// One persistent kernel per (constraint type, waypoints per lane) class, each specialised and
+// register-allocated for its class; the host launches the classes concurrently. A class's
+// grid of (SMs x CTAs per SM) CTAs dequeues its problems from an atomic counter in a given
+// order (longest expected first). Each problem names its robot, constraint, scene and W; the
+// CTA stages that robot and scene into shared memory and runs plan_problem. Trees live in a
+// per-CTA scratch slot reused across problems.
+template <int CT, int WPL>
+__global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTables T) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ SceneDev s_sc;
+  __shared__ int s_t, s_robot, s_cons;
+  const PlanArgs& a = b.a;
+  const int B = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, b.max_S, b.max_W, B, sizeof(PlanShared));
+  PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+  const CcShared S = cc_shared(smem, L, warp);
+  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
+  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
+  const size_t MN = (size_t)a.max_nodes, ew = (size_t)b.max_W * 8;  // edge floats (max)
+  const size_t slot = blockIdx.x;
+  for (;;) {
+    __syncthreads();  // the previous problem is done with shared memory
+    if (threadIdx.x == 0) s_t = (int)atomicAdd(b.counter, 1u);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= b.n_class) break;
+    const int p = b.order[t];
+    if (threadIdx.x == 0) {
+      const int4 d = b.problems[p];
+      s_robot = d.x;
+      s_cons = d.y;
+      const int4 sd = a.scenes[d.z];
+      s_sc = SceneDev{a.scene_obs + sd.x, sd.y, sd.z, sd.w};
+      ProblemView& P = sh->pv;
+      P.p = p;
+      P.start = a.start + (size_t)p * 8;
+      P.goal = a.goal + (size_t)p * 8;
+      P.W = d.w;
+      P.nodes = b.nodes + slot * 2 * MN * 8;
+      P.parent = b.parent + slot * 2 * MN;
+      P.edges = b.edges + slot * 2 * MN * ew;
+      P.pend = b.pend + slot * B * 8;
+      P.pend_edges = b.pend_edges + slot * B * 2 * ew;
+      const size_t oew = (size_t)b.out_max_W * 8;  // output edge floats: the batch's largest W
+      P.path = a.path + (size_t)p * a.max_path * 8;
+      P.path_edges = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * oew : nullptr;
+      P.ostride = 8;
+      P.estride = (int)oew;
+    }
+    __syncthreads();
+    // robot and constraint tables are read from the constant bank (kernel parameter)
+    const RobotDev& rb = T.robots[s_robot];
+    const ConsDev& cs = T.cons[s_cons];
+    const int n4 = s_sc.n_float4();
+    if (a.stage_obs)
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = s_sc.obs[i];
+    stage_robot(rb, smem, L);
+    __syncthreads();
+    plan_problem<CT, WPL>(rb, s_sc, a.stage_obs ? s_obs : s_sc.obs, cs, a, sh->pv, S, sh, wc);
+  }
+  wc.flush(a.work_counters);
+}
+
+static const void* plan_batch_fn(int cls) {
+  switch (cls) {
+    case 0: return (const void*)plan_batch_kernel<kConsNone, 1>;
+    case 1: return (const void*)plan_batch_kernel<kConsNone, 2>;
+    case 2: return (const void*)plan_batch_kernel<kConsRollPitch, 1>;
+    case 3: return (const void*)plan_batch_kernel<kConsRollPitch, 2>;
+    case 4: return (const void*)plan_batch_kernel<kConsZPlane, 1>;
+    default: return (const void*)plan_batch_kernel<kConsZPlane, 2>;
+  }
+}
+
+size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage) {
+  return SmemLayout(stage ? max_scene_f4 : 0, max_S, max_W, workers, sizeof(PlanShared)).total;
+}
+
+int plan_batch_occupancy(int cls, int workers, size_t smem) {
+  const void* fn = plan_batch_fn(cls);
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * workers, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
+}
+
+cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
+                              cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+  const void* fn = plan_batch_fn(cls);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&b, const_cast<BatchTables*>(&T)};
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * b.a.workers), args, smem, stream);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 static const void* plan_fn(int ct, int W) {

@@ -177,11 +177,15 @@ BASE_KEEPOUT = 0.35
 
 
 def make_planning_scene(seed: int, n_sph: int = 100, n_box: int = 60, n_cap: int = 40,
-                        lo=WORK_LO, hi=WORK_HI, keepout: float = BASE_KEEPOUT) -> Scene:
+                        lo=WORK_LO, hi=WORK_HI, keepout: float = BASE_KEEPOUT,
+                        scale: float = 1.0) -> Scene:
     """Mixed obstacles for one planning problem: centres uniform in the workspace box,
-    redrawn while within `keepout` (m, horizontal) of the base axis."""
+    redrawn while within `keepout` (m, horizontal) of the base axis. `scale` multiplies every
+    obstacle size (sphere radius, box sides, capsule length and radius)."""
     rng = np.random.default_rng(seed)
-    sc = make_scene(int(rng.integers(1 << 31)), n_sph, n_box, n_cap, lo=lo, hi=hi)
+    sc = make_scene(int(rng.integers(1 << 31)), n_sph, n_box, n_cap, lo=lo, hi=hi,
+                    sph_r=(0.05 * scale, 0.15 * scale), box_side=(0.05 * scale, 0.3 * scale),
+                    cap_len=(0.1 * scale, 0.4 * scale), cap_r=(0.02 * scale, 0.08 * scale))
 
     def centre_ok(c):
         return math.hypot(c[0], c[1]) >= keepout
@@ -287,3 +291,27 @@ def z_plane(z0: float = 0.9, max_iters: int = 20) -> Constraint:
 
 def no_constraint() -> Constraint:
     return Constraint(type=C_NONE)
+
+
+def make_batch_mix(n: int, seed: int, max_obstacles: int = 5000):
+    """Uneven batch: each problem draws a robot (6-, 7- or 8-DOF arm), a constraint (none,
+    roll-pitch, z-plane at 0.9 m), W in {16, 32, 64} and an obstacle count log-uniform in
+    [10, max_obstacles], split 50/30/20 into spheres, boxes and capsules. Above 200
+    obstacles every obstacle is shrunk by (200 / count)^(1/3), keeping the occupied volume
+    (like splitting each primitive into smaller ones). Returns robots, constraints, problems
+    [(robot, constraint, scene, W)] and scenes (scene p belongs to problem p)."""
+    rng = np.random.default_rng(seed)
+    robots = [make_arm6(1), make_arm7(1), make_arm8(1)]
+    constraints = [no_constraint(), roll_pitch(), z_plane(0.9)]
+    problems, scenes = [], []
+    for p in range(n):
+        r = int(rng.integers(3))
+        c = int(rng.integers(3))
+        W = (16, 32, 64)[int(rng.integers(3))]
+        count = int(round(math.exp(rng.uniform(math.log(10), math.log(max_obstacles)))))
+        ns, nb = int(round(0.5 * count)), int(round(0.3 * count))
+        nc = max(0, count - ns - nb)
+        scale = min(1.0, (200.0 / count) ** (1.0 / 3.0))
+        scenes.append(make_planning_scene(seed * 100_003 + p, ns, nb, nc, scale=scale))
+        problems.append((r, c, p, W))
+    return robots, constraints, problems, scenes

@@ -66,3 +66,70 @@ def check_paths(oracle_mod, robot, constraint, scenes, start, goal, out, W, rang
             if c <= -contact:
                 issues.append((p, j, "collision", c))
     return checked, issues
+
+
+def batch_start_goal(oracle_mod, robots, constraints, problems, scenes, seed, clearance=1e-3):
+    """Start and goal [n][8] for a batch: per problem, uniform configurations of its robot,
+    projected under its constraint and kept when collision-free in its scene (oracle)."""
+    n = len(problems)
+    start = np.zeros((n, 8))
+    goal = np.zeros((n, 8))
+    for p, (r, c, sc, W) in enumerate(problems):
+        rb, cons = robots[r], constraints[c]
+        orc = oracle_mod.Oracle(rb, scenes[sc], cons)
+        found, k = [], 0
+        while len(found) < 2:
+            for q in S.uniform_configs(rb, 40, seed + 7919 * p + 104729 * k):
+                if cons.type != 0:
+                    ok, q, _, _ = orc.project_config(q, max_iters=60)
+                    if not ok:
+                        continue
+                if orc.config_clearance(q) > clearance:
+                    found.append(q)
+                if len(found) == 2:
+                    break
+            k += 1
+            if k > 50:
+                raise RuntimeError(f"no free start/goal for problem {p}")
+        start[p, :rb.dof] = found[0]
+        goal[p, :rb.dof] = found[1]
+    return S.f32(start), S.f32(goal)
+
+
+def check_batch_paths(oracle_mod, robots, constraints, problems, scenes, start, goal, out,
+                      range_, slack=2e-6, contact=1e-5):
+    """Oracle re-validation of batch paths ([n][max_path][8] nodes, [n][max_path-1][Wmax][8]
+    edges)."""
+    to_np = lambda x: x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)  # noqa
+    L = to_np(out["path_len"])
+    path = to_np(out["path"])
+    edges = to_np(out["path_edges"]) if out.get("path_edges") is not None else None
+    issues, checked = [], 0
+    for p, (r, c, sc, W) in enumerate(problems):
+        n = int(L[p])
+        if n <= 0:
+            continue
+        checked += 1
+        rb, cons = robots[r], constraints[c]
+        dof = rb.dof
+        tau = max(cons.c_sm * range_ / (W - 1), cons.tau_floor)
+        orc = oracle_mod.Oracle(rb, scenes[sc], cons)
+        P = path[p, :n, :dof].astype(np.float64)
+        if not (np.array_equal(path[p, 0, :dof], start[p, :dof].astype(np.float32)) and
+                np.array_equal(path[p, n - 1, :dof], goal[p, :dof].astype(np.float32))):
+            issues.append((p, "endpoints"))
+        if edges is None:
+            continue
+        for j in range(n - 1):
+            E = edges[p, j, :W, :dof].astype(np.float64)
+            if np.abs(E[0] - P[j]).max() > 1e-6 or np.abs(E[-1] - P[j + 1]).max() > 1e-6:
+                issues.append((p, j, "edge does not join its nodes"))
+                continue
+            t, s_, cl = orc.check_segment(E, tau)
+            if cons.type != 0 and t >= cons.tol_task + slack:
+                issues.append((p, j, "off manifold", t))
+            if s_ >= cons.tol_sm + slack:
+                issues.append((p, j, "discontinuous", s_))
+            if cl <= -contact:
+                issues.append((p, j, "collision", cl))
+    return checked, issues

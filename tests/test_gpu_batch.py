@@ -1,0 +1,124 @@
+"""Persistent batches of uneven planning problems (cprrtc_plan_batch), their CUDA-graph
+capture and the autotuner, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2505_06791_gb300 import synth as S
+from tests import problems as PB
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_06791_gb300 import build
+    build.build()
+    return torch
+
+
+def to_np(out):
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def test_homogeneous_batch_equals_plan(torch_cuda, oracle_mod):
+    """A batch whose problems share robot, constraint and W plans exactly as cprrtc_plan."""
+    from paper_2505_06791_gb300.capi import Context
+    torch = torch_cuda
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 10, 1900)
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_constraint(c)
+    ctx.set_scene_batch(scenes)
+    ctx.set_robot_table([rb])
+    ctx.set_constraint_table([c])
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=300, workers=8, seed=9)
+    with torch.cuda.stream(stream):
+        s = torch.from_numpy(start.astype(np.float32)).cuda()
+        g = torch.from_numpy(goal.astype(np.float32)).cuda()
+        ref = to_np(ctx.plan(s, g, prm))
+        s8 = torch.zeros((10, 8), device="cuda")
+        g8 = torch.zeros((10, 8), device="cuda")
+        s8[:, :7] = s
+        g8[:, :7] = g
+        probs = [(0, 0, p, 32) for p in range(10)]
+        out = to_np(ctx.plan_batch(probs, s8, g8, prm, edges=True))
+    stream.synchronize()
+    for k in ("path_len", "rounds", "waypoints", "work"):
+        assert np.array_equal(out[k], ref[k]), k
+    for p in range(10):
+        n = int(ref["path_len"][p])
+        if n > 0:
+            assert np.array_equal(out["path"][p, :n, :7], ref["path"][p, :n])
+            assert np.array_equal(out["path_edges"][p, :n - 1, :32, :7],
+                                  ref["path_edges"][p, :n - 1])
+    ctx.close()
+
+
+def test_mixed_batch_paths_graph_and_tuning(torch_cuda, oracle_mod):
+    """Mixed robots, constraints, W and obstacle counts: every path is re-validated by the
+    oracle; repeated runs, a CUDA-graph replay and an autotuned launch shape all give the
+    same results."""
+    from paper_2505_06791_gb300.capi import Context
+    torch = torch_cuda
+    robots, cons, probs, scenes = S.make_batch_mix(18, 77, max_obstacles=400)
+    start, goal = PB.batch_start_goal(oracle_mod, robots, cons, probs, scenes, 31)
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream.cuda_stream)
+    ctx.set_robot_table(robots)
+    ctx.set_constraint_table(cons)
+    ctx.set_scene_batch(scenes)
+    prm = ctx.plan_params(range_=0.3, max_rounds=400, workers=8, seed=3, max_path=400)
+    max_W = max(p[3] for p in probs)
+    with torch.cuda.stream(stream):
+        s = torch.from_numpy(start.astype(np.float32)).cuda()
+        g = torch.from_numpy(goal.astype(np.float32)).cuda()
+        first = to_np(ctx.plan_batch(probs, s, g, prm, edges=True))
+        second = to_np(ctx.plan_batch(probs, s, g, prm, edges=True))
+        out = ctx.alloc_batch_outputs(len(probs), prm, max_W, s, edges=True)
+        ctx.batch_capture(probs, s, g, prm, out)
+        ctx.batch_replay()
+        ctx.batch_replay()
+    stream.synchronize()
+    replay = to_np(out)
+    for k in ("path_len", "path", "rounds", "waypoints", "work"):
+        assert np.array_equal(first[k], second[k]), k
+        assert np.array_equal(first[k], replay[k]), k
+    checked, issues = PB.check_batch_paths(oracle_mod, robots, cons, probs, scenes, start, goal,
+                                           first, 0.3)
+    assert not issues, issues[:10]
+    assert checked >= 3, checked
+    with torch.cuda.stream(stream):
+        tuned = ctx.autotune_batch(probs, s, g, prm, trial_rounds=5)
+        again = to_np(ctx.plan_batch(probs, s, g, prm, tuning=tuned, edges=True))
+    stream.synchronize()
+    for k in ("path_len", "path", "rounds", "waypoints", "work"):
+        assert np.array_equal(first[k], again[k]), k
+    ctx.close()
+
+
+def test_batch_argument_errors(torch_cuda):
+    from paper_2505_06791_gb300 import capi
+    ctx = capi.Context(0)
+    prm = ctx.plan_params()
+    q = np.zeros((1, 8), np.float32)
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.plan_batch([(0, 0, 0, 32)], q, q, prm)
+    assert e.value.code == capi.E_NOT_CONFIGURED
+    ctx.set_robot_table([S.make_arm7(1)])
+    ctx.set_constraint_table([S.no_constraint()])
+    ctx.set_scene_batch([S.Scene()])
+    for bad in ([(1, 0, 0, 32)], [(0, 1, 0, 32)], [(0, 0, 1, 32)], [(0, 0, 0, 1)],
+                [(0, 0, 0, 65)]):
+        with pytest.raises(capi.CprrtcError) as e:
+            ctx.plan_batch(bad, q, q, prm)
+        assert e.value.code == capi.E_INVALID_ARG, bad
+    with pytest.raises(capi.CprrtcError):
+        ctx.batch_replay()
+    out = ctx.plan_batch([(0, 0, 0, 16)], q, q, prm)
+    assert out["path_len"][0] >= 2      # start == goal, empty scene, no constraint
+    ctx.close()
