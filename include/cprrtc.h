@@ -173,6 +173,71 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
 int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,
                            float* q_out, uint8_t* ok, float* resid);
 
+/* ---- learned projection warm start ---- */
+
+/* A multilayer perceptron that predicts, for a configuration q, the correction
+ * proj(q) - q that the projection (cprrtc_project_configs) would apply, so that Alg. 1 can
+ * start closer to the manifold. The paper has no learned component: this is an addition,
+ * and the plain Alg. 1 stays both the fallback and the judge of every warm-started segment
+ * (cprrtc_validate_ws).
+ * Network (one per context, for the dof of the robot set when it is created):
+ *   x = q / pi; h1 = gelu(W1 x + b1); h2 = gelu(W2 h1 + b2); h3 = gelu(W3 h2 + b3);
+ *   correction = W4 h3 + b4, widths dof -> 256 -> 256 -> 256 -> dof,
+ *   gelu(z) = z Phi(z) with Phi the standard normal CDF (the exact form, through erf).
+ * Weights and activations are BF16 and products accumulate in FP32 on the tensor cores;
+ * biases, the FP32 master weights and the Adam state stay FP32.
+ * Parameter layout (compact, FP32, cprrtc_mlp_param_count(dof) entries): for l = 1..4,
+ * W_l [out_l][in_l] row-major then b_l [out_l]. */
+int64_t cprrtc_mlp_param_count(int dof);
+
+/* Creates (or re-creates) the network for the current robot, He-normal weights (the last
+ * layer scaled by 0.1) and zero biases from `seed`; resets the optimiser.
+ * Requires set_robot. Errors: E_NOT_CONFIGURED, E_CUDA, E_OOM. */
+int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed);
+
+/* Sets / reads the parameters (host arrays of `count` = cprrtc_mlp_param_count(dof)
+ * floats). Setting resets the Adam state. Errors: E_NOT_CONFIGURED (no network),
+ * E_INVALID_ARG (count mismatch, null), E_CUDA. */
+int cprrtc_mlp_set_params(cprrtc_ctx* ctx, const float* params, int64_t count);
+int cprrtc_mlp_get_params(cprrtc_ctx* ctx, float* params, int64_t count);
+
+/* Loss L = (1 / rows) sum_r 0.5 |f(q_r) - (t_r - q_r)|^2 over rows pairs (q [rows][dof],
+ * t [rows][dof]: q's projection) and its gradient with respect to every parameter
+ * (grads: host array of cprrtc_mlp_param_count(dof) floats, compact layout; loss: host,
+ * 1 float; either may be NULL). Does not change the parameters. Synchronous.
+ * Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_CUDA, E_OOM. */
+int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, float* grads,
+                    float* loss);
+
+/* Trains on n pairs (q, t) as above: `epochs` passes of minibatch Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8, learning rate lr) over floor(n / batch) batches in an order drawn per
+ * epoch from `seed`. loss_per_epoch [epochs] (host, may be NULL) receives each epoch's mean
+ * batch loss. Synchronous. Errors: E_NOT_CONFIGURED, E_INVALID_ARG (n < batch, batch < 1,
+ * epochs < 0, lr not finite), E_CUDA, E_OOM. */
+int cprrtc_mlp_train(cprrtc_ctx* ctx, const float* q, const float* t, int n, int batch,
+                     int epochs, float lr, uint64_t seed, float* loss_per_epoch);
+
+/* q_out [rows][dof] = q + correction(q) for rows configurations (no clamping).
+ * Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_CUDA, E_OOM. */
+int cprrtc_mlp_infer(cprrtc_ctx* ctx, const float* q, int rows, float* q_out);
+
+/* cprrtc_validate with the learned warm start: waypoint i = 1..W-1 of each motion's
+ * interpolation xi gets the correction f(xi_i) - (1 - i / (W - 1)) f(xi_0), clamped to the
+ * joint limits (xi_0 = q_start is taken to lie on the manifold, so f(xi_0) is the network's
+ * local error and is removed where the segment leaves its fixed start). If the largest
+ * ||E_task||_inf over those waypoints is then below that of the plain interpolation, Alg. 1
+ * runs from the corrected segment for at most refine_iters (1..20) iterations with the
+ * same thresholds. If the corrected start is not closer, or its run does not accept the
+ * whole segment, Alg. 1 runs from the plain interpolation with max_iters iterations,
+ * exactly as in cprrtc_validate. Collision checking then proceeds on the accepted segment.
+ * iters [n] counts the iterations of both runs; warm_used [n] (may be NULL) is 1 when the
+ * warm-started segment was the one accepted. Other arguments
+ * and outputs as cprrtc_validate. Requires set_robot, a constraint other than NONE and a
+ * network for the robot's dof. Errors: as cprrtc_validate. */
+int cprrtc_validate_ws(cprrtc_ctx* ctx, const float* q_start, const float* q_end, int n, int W,
+                       int refine_iters, float* out_q, uint8_t* status, int32_t* first_fail,
+                       uint8_t* iters, float* resid, uint8_t* warm_used);
+
 /* ---- planning (Sec. III: RRT-Connect tree extension with constrained motions) ---- */
 
 /* Per-problem obstacle sets for cprrtc_plan with use_scene_batch = 1: problem p uses
@@ -341,7 +406,8 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
 
 /* When enabled, the library records CUDA events around each launch of its kernels on the
  * context's stream. cprrtc_kernel_time returns the summed device time (ms) and the launch
- * count of the kernel named `name` ("validate", "project", "plan") since the last reset,
+ * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer") since the
+ * last reset,
  * synchronising on the events. */
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
 

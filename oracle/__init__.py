@@ -70,6 +70,8 @@ def lib():
             _lib.orc_task.restype = C.c_int
             _lib.orc_validate.restype = C.c_int
             _lib.orc_plan.restype = C.c_int
+            _lib.orc_mlp_param_count.restype = C.c_long
+            _lib.orc_mlp_loss_grad.restype = C.c_double
             for f in ("orc_clear_sphere", "orc_clear_box", "orc_clear_capsule",
                       "orc_config_clearance"):
                 getattr(_lib, f).restype = C.c_double
@@ -175,6 +177,19 @@ class Oracle:
                                       C.byref(it), C.byref(res))
         return bool(ok), out, it.value, res.value
 
+    def project_configs(self, q, max_iters=None, n_threads=1):
+        """orc_project_config over a batch [n][dof] (FP32 inputs), threaded."""
+        qs = np.ascontiguousarray(q, dtype=np.float32)
+        n = qs.shape[0]
+        out = np.zeros((n, self.dof))
+        ok = np.zeros(n, dtype=np.int32)
+        res = np.zeros(n)
+        mi = self.c.max_iters if max_iters is None else max_iters
+        lib().orc_project_configs(C.byref(self.rb), C.byref(self.c),
+                                  qs.ctypes.data_as(C.POINTER(C.c_float)), n, mi, n_threads,
+                                  _p(out), ok.ctypes.data_as(C.POINTER(C.c_int)), _p(res))
+        return ok.astype(bool), out, res
+
     def project_motion_sequential(self, xi_init, tau):
         xi_init = _d(xi_init)
         out = np.zeros_like(xi_init)
@@ -246,6 +261,27 @@ class Oracle:
                        rounds.ctypes.data_as(C.POINTER(C.c_int)),
                        wp.ctypes.data_as(C.POINTER(C.c_longlong)))
         return dict(path_len=path_len, path=path, rounds=rounds, waypoints=wp)
+
+
+def mlp_param_count(dof: int, H: int = 256) -> int:
+    return int(lib().orc_mlp_param_count(dof, H))
+
+
+def mlp_forward(params, q, dof: int, H: int = 256):
+    """FP64 corrections f(q) [rows][dof] of the warm-start network (compact layout)."""
+    p, q = _d(params), _d(q)
+    out = np.zeros((q.shape[0], dof))
+    lib().orc_mlp_forward(dof, H, _p(p), _p(q), q.shape[0], _p(out))
+    return out
+
+
+def mlp_loss_grad(params, q, t, dof: int, H: int = 256, n_threads: int = 1, grad=True):
+    """(loss, gradient) of (1/rows) sum 0.5 |f(q) - (t - q)|^2, FP64."""
+    p, q, t = _d(params), _d(q), _d(t)
+    g = np.zeros(p.size) if grad else None
+    loss = lib().orc_mlp_loss_grad(dof, H, _p(p), _p(q), _p(t), q.shape[0], n_threads,
+                                   _p(g) if grad else None)
+    return float(loss), g
 
 
 def philox4x32_10(ctr, key):

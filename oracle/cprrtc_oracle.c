@@ -517,6 +517,205 @@ int orc_validate(const orc_robot* rb, const orc_scene* sc, const orc_constraint*
 }
 
 /* ========================================================================================
+ * Batch single-configuration projection (orc_project_config over threads).
+ * ======================================================================================== */
+
+typedef struct {
+  const orc_robot* rb;
+  const orc_constraint* c;
+  const float* q_in;
+  int lo, hi, max_iters;
+  double* q_out;
+  int* ok;
+  double* resid;
+} proj_job;
+
+static void* project_worker(void* arg) {
+  proj_job* j = (proj_job*)arg;
+  const int n = j->rb->dof;
+  for (int m = j->lo; m < j->hi; ++m) {
+    double q[ORC_MAX_DOF];
+    for (int k = 0; k < n; ++k) q[k] = (double)j->q_in[(size_t)m * n + k];
+    int it = 0;
+    double res = 0.0;
+    int ok = orc_project_config(j->rb, j->c, q, j->max_iters, j->q_out + (size_t)m * n, &it, &res);
+    if (j->ok) j->ok[m] = ok;
+    if (j->resid) j->resid[m] = res;
+  }
+  return NULL;
+}
+
+void orc_project_configs(const orc_robot* rb, const orc_constraint* c, const float* q_in, int n,
+                         int max_iters, int n_threads, double* q_out, int* ok, double* resid) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  proj_job jobs[256];
+  for (int t = 0; t < n_threads; ++t) {
+    jobs[t] = (proj_job){rb, c, q_in, (int)((long)n * t / n_threads),
+                         (int)((long)n * (t + 1) / n_threads), max_iters, q_out, ok, resid};
+    pthread_create(&th[t], NULL, project_worker, &jobs[t]);
+  }
+  for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ========================================================================================
+ * Learned warm start network: a plain FP64 multilayer perceptron, forward pass and
+ * reverse-mode gradient of the mean squared correction error, one row at a time.
+ * ======================================================================================== */
+
+static void mlp_dims(int dof, int H, int l, int* out, int* in) {
+  *in = l == 0 ? dof : H;
+  *out = l == 3 ? dof : H;
+}
+
+long orc_mlp_param_count(int dof, int H) {
+  long n = 0;
+  for (int l = 0; l < 4; ++l) {
+    int o, i;
+    mlp_dims(dof, H, l, &o, &i);
+    n += (long)o * i + o;
+  }
+  return n;
+}
+
+static long mlp_layer_off(int dof, int H, int l) {
+  long off = 0;
+  for (int k = 0; k < l; ++k) {
+    int o, i;
+    mlp_dims(dof, H, k, &o, &i);
+    off += (long)o * i + o;
+  }
+  return off;
+}
+
+static const double kPi = 3.14159265358979323846;
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+/* d/dz of z Phi(z): Phi(z) + z phi(z) */
+static double gelu_d(double z) {
+  return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * kPi);
+}
+
+/* One row: a[l] = input of layer l (l = 0..3, stride H), z[l] = pre-activation of hidden
+ * layer l (l = 0..2, stride H), y = output. */
+static void mlp_row(int dof, int H, const double* params, const double* q, double* a, double* z,
+                    double* y) {
+  for (int k = 0; k < dof; ++k) a[k] = q[k] / kPi;
+  for (int l = 0; l < 4; ++l) {
+    int o, in;
+    mlp_dims(dof, H, l, &o, &in);
+    const double* Wl = params + mlp_layer_off(dof, H, l);
+    const double* bl = Wl + (long)o * in;
+    const double* x = a + (long)l * H;
+    for (int r = 0; r < o; ++r) {
+      double s = bl[r];
+      for (int c = 0; c < in; ++c) s += Wl[(long)r * in + c] * x[c];
+      if (l < 3) {
+        z[(long)l * H + r] = s;
+        a[(long)(l + 1) * H + r] = gelu(s);
+      } else {
+        y[r] = s;
+      }
+    }
+  }
+}
+
+void orc_mlp_forward(int dof, int H, const double* params, const double* q, int rows,
+                     double* corr) {
+  double* a = (double*)malloc(sizeof(double) * 4 * (size_t)H);
+  double* z = (double*)malloc(sizeof(double) * 3 * (size_t)H);
+  for (int r = 0; r < rows; ++r)
+    mlp_row(dof, H, params, q + (size_t)r * dof, a, z, corr + (size_t)r * dof);
+  free(a);
+  free(z);
+}
+
+typedef struct {
+  int dof, H, lo, hi, rows;
+  const double *params, *q, *t;
+  double* grads; /* this thread's accumulator (compact layout) or NULL */
+  double loss;
+} mlp_job;
+
+static void* mlp_worker(void* arg) {
+  mlp_job* j = (mlp_job*)arg;
+  const int dof = j->dof, H = j->H;
+  const int wide = H > dof ? H : dof;
+  double* a = (double*)malloc(sizeof(double) * 4 * (size_t)H);
+  double* z = (double*)malloc(sizeof(double) * 3 * (size_t)H);
+  double* d = (double*)malloc(sizeof(double) * (size_t)wide);  /* dL/d(output of layer l) */
+  double* dn = (double*)malloc(sizeof(double) * (size_t)wide);
+  double y[ORC_MAX_DOF];
+  j->loss = 0.0;
+  for (int r = j->lo; r < j->hi; ++r) {
+    const double* q = j->q + (size_t)r * dof;
+    const double* t = j->t + (size_t)r * dof;
+    mlp_row(dof, H, j->params, q, a, z, y);
+    /* error of the predicted correction; dL/dy = error / rows */
+    for (int k = 0; k < dof; ++k) {
+      const double res = y[k] - (t[k] - q[k]);
+      j->loss += 0.5 * res * res / j->rows;
+      d[k] = res / j->rows;
+    }
+    if (!j->grads) continue;
+    for (int l = 3; l >= 0; --l) {
+      int o, in;
+      mlp_dims(dof, H, l, &o, &in);
+      const long off = mlp_layer_off(dof, H, l);
+      const double* Wl = j->params + off;
+      double* gW = j->grads + off;
+      double* gb = gW + (long)o * in;
+      const double* x = a + (long)l * H;
+      for (int rr = 0; rr < o; ++rr) {
+        gb[rr] += d[rr];
+        for (int c = 0; c < in; ++c) gW[(long)rr * in + c] += d[rr] * x[c];
+      }
+      if (l == 0) break;
+      /* back through W_l, then through the GELU of hidden layer l-1 */
+      for (int c = 0; c < in; ++c) {
+        double s = 0.0;
+        for (int rr = 0; rr < o; ++rr) s += Wl[(long)rr * in + c] * d[rr];
+        dn[c] = s * gelu_d(z[(long)(l - 1) * H + c]);
+      }
+      memcpy(d, dn, sizeof(double) * (size_t)in);
+    }
+  }
+  free(a);
+  free(z);
+  free(d);
+  free(dn);
+  return NULL;
+}
+
+double orc_mlp_loss_grad(int dof, int H, const double* params, const double* q,
+                         const double* t, int rows, int n_threads, double* grads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 64) n_threads = 64;
+  if (n_threads > rows) n_threads = rows > 0 ? rows : 1;
+  const long np = orc_mlp_param_count(dof, H);
+  pthread_t th[64];
+  mlp_job jobs[64];
+  for (int k = 0; k < n_threads; ++k) {
+    jobs[k] = (mlp_job){dof, H, (int)((long)rows * k / n_threads),
+                        (int)((long)rows * (k + 1) / n_threads), rows, params, q, t,
+                        grads ? (double*)calloc((size_t)np, sizeof(double)) : NULL, 0.0};
+    pthread_create(&th[k], NULL, mlp_worker, &jobs[k]);
+  }
+  double loss = 0.0;
+  if (grads) memset(grads, 0, sizeof(double) * (size_t)np);
+  for (int k = 0; k < n_threads; ++k) {
+    pthread_join(th[k], NULL);
+    loss += jobs[k].loss;
+    if (grads) {
+      for (long i = 0; i < np; ++i) grads[i] += jobs[k].grads[i];
+      free(jobs[k].grads);
+    }
+  }
+  return loss;
+}
+
+/* ========================================================================================
  * Philox4x32-10, from the definition in Salmon et al., "Parallel random numbers: as easy
  * as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplications with the key added by
  * XOR and bumped by two Weyl constants between rounds.

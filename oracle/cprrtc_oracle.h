@@ -128,6 +128,24 @@ void orc_check_segment(const orc_robot* rb, const orc_scene* sc, const orc_const
                        const double* xi, int W, double tau, double* max_task,
                        double* max_step_excess, double* min_clearance);
 
+/* Batch of orc_project_config calls over n_threads threads: q_in, q_out [n][dof] (FP32 in,
+ * FP64 out), ok [n], resid [n] (either may be NULL). */
+void orc_project_configs(const orc_robot* rb, const orc_constraint* c, const float* q_in, int n,
+                         int max_iters, int n_threads, double* q_out, int* ok, double* resid);
+
+/* ---- learned warm start network (no counterpart in the paper) --------------------------
+ * f(q) = W4 g(W3 g(W2 g(W1 (q / pi) + b1) + b2) + b3) + b4, g(z) = z Phi(z) (exact GELU,
+ * Phi the standard normal CDF), widths dof -> H -> H -> H -> dof. Parameters in the
+ * compact layout: for l = 1..4, W_l [out_l][in_l] row-major then b_l [out_l]. */
+long orc_mlp_param_count(int dof, int H);
+/* corr [rows][dof] = f(q) for q [rows][dof]. */
+void orc_mlp_forward(int dof, int H, const double* params, const double* q, int rows,
+                     double* corr);
+/* Loss (1/rows) sum_r 0.5 |f(q_r) - (t_r - q_r)|^2; grads (compact layout, may be NULL)
+ * receives its gradient by reverse-mode differentiation written out layer by layer. */
+double orc_mlp_loss_grad(int dof, int H, const double* params, const double* q,
+                         const double* t, int rows, int n_threads, double* grads);
+
 /* ---- counter-based RNG ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -109,6 +109,17 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_batch_replay": [C.c_void_p],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
+    "cprrtc_mlp_param_count": [C.c_int],
+    "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
+    "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "cprrtc_mlp_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "cprrtc_mlp_train": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                         C.c_float, C.c_uint64, C.c_void_p],
+    "cprrtc_mlp_infer": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "cprrtc_validate_ws": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p],
     "cprrtc_set_timing": [C.c_void_p, C.c_int],
     "cprrtc_work_counters": [C.c_void_p, C.c_void_p, C.c_int],
     "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
@@ -121,7 +132,8 @@ def header_symbols() -> list:
     """Function names declared in include/cprrtc.h."""
     import re
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cprrtc_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(cprrtc_\w+)\s*\(", text,
+                                 re.M)))
 
 
 def lib():
@@ -136,7 +148,8 @@ def lib():
             for name, args in _SIGS.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
-                fn.restype = C.c_char_p if name == "cprrtc_last_error" else C.c_int
+                fn.restype = {"cprrtc_last_error": C.c_char_p,
+                              "cprrtc_mlp_param_count": C.c_int64}.get(name, C.c_int)
             _lib = L
     return _lib
 
@@ -297,6 +310,64 @@ class Context:
         self._check(cprrtc_validate(self.h, q_start, q_end, n, W,
                                     out["q"] if with_q else None, out["status"],
                                     out["first_fail"], out["iters"], out["resid"]))
+        return out
+
+    def validate_ws(self, q_start, q_end, W: int, refine_iters: int = 5, out=None,
+                    with_q: bool = True):
+        """cprrtc_validate_ws: validation with the learned warm start (adds out["warm"])."""
+        n = int(q_start.shape[0])
+        if out is None:
+            out = self.alloc_validate_outputs(n, W, q_start)
+        if "warm" not in out:
+            if _is_cuda(q_start):
+                import torch
+                out["warm"] = torch.empty(n, dtype=torch.uint8, device=q_start.device)
+            else:
+                out["warm"] = np.empty(n, np.uint8)
+        self._check(cprrtc_validate_ws(self.h, q_start, q_end, n, W, refine_iters,
+                                       out["q"] if with_q else None, out["status"],
+                                       out["first_fail"], out["iters"], out["resid"],
+                                       out["warm"]))
+        return out
+
+    # -- learned warm start --
+    def mlp_param_count(self, dof=None) -> int:
+        return int(self._L.cprrtc_mlp_param_count(int(dof or self.dof)))
+
+    def mlp_init(self, seed: int = 0):
+        self._check(self._L.cprrtc_mlp_init(self.h, int(seed)))
+
+    def mlp_set_params(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(self._L.cprrtc_mlp_set_params(self.h, p.ctypes.data, p.size))
+
+    def mlp_get_params(self) -> np.ndarray:
+        p = np.empty(self.mlp_param_count(), np.float32)
+        self._check(self._L.cprrtc_mlp_get_params(self.h, p.ctypes.data, p.size))
+        return p
+
+    def mlp_grad(self, q, t):
+        """(loss, gradient in the compact parameter layout) for pairs (q, t)."""
+        g = np.empty(self.mlp_param_count(), np.float32)
+        loss = np.zeros(1, np.float32)
+        self._check(cprrtc_mlp_grad(self.h, q, t, int(q.shape[0]), g, loss))
+        return float(loss[0]), g
+
+    def mlp_train(self, q, t, batch: int, epochs: int, lr: float, seed: int = 0):
+        """Minibatch Adam; returns the mean batch loss of each epoch."""
+        losses = np.zeros(max(epochs, 1), np.float32)
+        self._check(cprrtc_mlp_train(self.h, q, t, int(q.shape[0]), batch, epochs, lr, seed,
+                                     losses))
+        return losses[:epochs]
+
+    def mlp_infer(self, q, out=None):
+        if out is None:
+            if _is_cuda(q):
+                import torch
+                out = torch.empty_like(q)
+            else:
+                out = np.empty_like(np.asarray(q, np.float32))
+        self._check(cprrtc_mlp_infer(self.h, q, int(q.shape[0]), out))
         return out
 
     def set_scene_batch(self, scenes):
@@ -502,6 +573,26 @@ def cprrtc_validate(h, q_start, q_end, n, W, out_q, status, first_fail, iters, r
                                  _ptr(status), _ptr(first_fail), _ptr(iters), _ptr(resid))
 
 
+def cprrtc_validate_ws(h, q_start, q_end, n, W, refine_iters, out_q, status, first_fail, iters,
+                       resid, warm_used):
+    return lib().cprrtc_validate_ws(h, _ptr(q_start), _ptr(q_end), n, W, refine_iters,
+                                    _ptr(out_q), _ptr(status), _ptr(first_fail), _ptr(iters),
+                                    _ptr(resid), _ptr(warm_used))
+
+
+def cprrtc_mlp_grad(h, q, t, rows, grads, loss):
+    return lib().cprrtc_mlp_grad(h, _ptr(q), _ptr(t), rows, _ptr(grads), _ptr(loss))
+
+
+def cprrtc_mlp_train(h, q, t, n, batch, epochs, lr, seed, loss_per_epoch):
+    return lib().cprrtc_mlp_train(h, _ptr(q), _ptr(t), n, batch, epochs, lr, seed,
+                                  _ptr(loss_per_epoch))
+
+
+def cprrtc_mlp_infer(h, q, rows, q_out):
+    return lib().cprrtc_mlp_infer(h, _ptr(q), rows, _ptr(q_out))
+
+
 def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
     return lib().cprrtc_project_configs(h, _ptr(q_in), n, max_iters, _ptr(q_out), _ptr(ok),
                                         _ptr(resid))
@@ -510,4 +601,5 @@ def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
 __all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
            "cprrtc_project_configs", "cprrtc_plan", "cprrtc_plan_static", "cprrtc_philox",
            "cprrtc_plan_batch", "cprrtc_autotune_batch", "cprrtc_batch_capture",
-           "cprrtc_batch_replay"]
+           "cprrtc_batch_replay", "cprrtc_validate_ws", "cprrtc_mlp_grad", "cprrtc_mlp_train",
+           "cprrtc_mlp_infer"]

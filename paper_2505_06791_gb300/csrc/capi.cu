@@ -76,6 +76,10 @@ struct cprrtc_ctx {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kBatchClasses] = {};
   cudaGraphExec_t graph_exec = nullptr;
+  // learned warm start
+  MlpDev* mlp = nullptr;
+  float* d_warm = nullptr;  // corrections [n*W][16]
+  size_t warm_cap = 0;      // bytes
   bool timing = false;
   std::vector<TimingRec> pending;
   std::map<std::string, std::pair<double, long long>> acc;
@@ -437,6 +441,8 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_work);
   cudaFree(ctx->d_tab_sph);
   cudaFree(ctx->d_tab_frm);
+  mlp_destroy(ctx->mlp);
+  cudaFree(ctx->d_warm);
   for (BatchRes* r : {&ctx->batch_res, &ctx->graph_res}) {
     cudaFree(r->d_probs);
     cudaFree(r->d_order);
@@ -721,6 +727,207 @@ int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_it
   cudaError_t e = launch_project_configs(ctx->rb, ctx->cs, d_in, n, max_iters, d_out, d_ok, d_res, ctx->stream);
   tm.done();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "project launch");
+  return st.end(ctx);
+}
+
+// ---- learned warm start ----
+
+int64_t cprrtc_mlp_param_count(int dof) {
+  if (dof < 1 || dof > CPRRTC_MAX_DOF) return 0;
+  return (int64_t)mlp_compact_count(dof);
+}
+
+int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "mlp_init: set_robot first");
+  DeviceGuard g(ctx->device);
+  if (ctx->mlp) {
+    cudaStreamSynchronize(ctx->stream);
+    mlp_destroy(ctx->mlp);
+    ctx->mlp = nullptr;
+  }
+  cudaError_t e = mlp_create(&ctx->mlp, ctx->rb.dof);
+  if (e == cudaSuccess) e = mlp_init(ctx->mlp, seed, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_init");
+  return CPRRTC_OK;
+}
+
+static int mlp_ready(cprrtc_ctx* ctx, const char* who) {
+  if (!ctx->mlp) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, std::string(who) + ": call mlp_init first");
+  if (!ctx->has_robot || mlp_dof(ctx->mlp) != ctx->rb.dof)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, std::string(who) + ": network dof differs from the robot's");
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_set_params(cprrtc_ctx* ctx, const float* params, int64_t count) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->mlp) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "mlp_set_params: call mlp_init first");
+  if (!params || count != (int64_t)mlp_compact_count(mlp_dof(ctx->mlp)) || is_device_ptr(params))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_set_params: host array of mlp_param_count(dof) floats");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mlp_set_params(ctx->mlp, params, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_set_params");
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_get_params(cprrtc_ctx* ctx, float* params, int64_t count) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->mlp) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "mlp_get_params: call mlp_init first");
+  if (!params || count != (int64_t)mlp_compact_count(mlp_dof(ctx->mlp)) || is_device_ptr(params))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_get_params: host array of mlp_param_count(dof) floats");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mlp_get_params(ctx->mlp, params, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_get_params");
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, float* grads,
+                    float* loss) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (int rc = mlp_ready(ctx, "mlp_grad")) return rc;
+  if (rows < 1 || !q || !t) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_grad: rows >= 1 and data required");
+  if ((grads && is_device_ptr(grads)) || (loss && is_device_ptr(loss)))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_grad: grads and loss are host arrays");
+  DeviceGuard g(ctx->device);
+  const size_t bytes = (size_t)rows * ctx->rb.dof * sizeof(float);
+  const float *dq, *dt;
+  Staging st;
+  st.input(q, bytes, &dq);
+  st.input(t, bytes, &dt);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  cudaError_t e = mlp_grad(ctx->mlp, dq, dt, rows, grads, loss, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_grad");
+  return st.end(ctx);
+}
+
+int cprrtc_mlp_train(cprrtc_ctx* ctx, const float* q, const float* t, int n, int batch,
+                     int epochs, float lr, uint64_t seed, float* loss_per_epoch) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (int rc = mlp_ready(ctx, "mlp_train")) return rc;
+  if (batch < 1 || n < batch || epochs < 0 || !is_finite(lr) || !q || !t)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_train: need 1 <= batch <= n, epochs >= 0, finite lr");
+  if (loss_per_epoch && is_device_ptr(loss_per_epoch))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_train: loss_per_epoch is a host array");
+  if (epochs == 0) return CPRRTC_OK;
+  DeviceGuard g(ctx->device);
+  const size_t bytes = (size_t)n * ctx->rb.dof * sizeof(float);
+  const float *dq, *dt;
+  Staging st;
+  st.input(q, bytes, &dq);
+  st.input(t, bytes, &dt);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  LaunchTimer tm(ctx, "mlp_train");
+  cudaError_t e = mlp_train(ctx->mlp, dq, dt, n, batch, epochs, lr, seed, loss_per_epoch, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_train");
+  return st.end(ctx);
+}
+
+// q_out = q + correction, rows of [rows][dof]
+__global__ void add_correction_kernel(const float* __restrict__ q, const float* __restrict__ y, int rows,
+                                      int dof, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * dof) return;
+  const int r = i / dof, k = i - r * dof;
+  out[i] = q[i] + y[(size_t)r * 16 + k];
+}
+
+static int ensure_warm(cprrtc_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->warm_cap) return CPRRTC_OK;
+  if (ctx->d_warm) cudaFree(ctx->d_warm);
+  ctx->d_warm = nullptr;
+  ctx->warm_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->d_warm, bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "warm-start buffer");
+  ctx->warm_cap = bytes;
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_infer(cprrtc_ctx* ctx, const float* q, int rows, float* q_out) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (int rc = mlp_ready(ctx, "mlp_infer")) return rc;
+  if (rows < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_infer: rows < 0");
+  if (rows == 0) return CPRRTC_OK;
+  if (!q || !q_out) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_infer: null pointer");
+  DeviceGuard g(ctx->device);
+  const int dof = ctx->rb.dof;
+  const size_t bytes = (size_t)rows * dof * sizeof(float);
+  if (int rc = ensure_warm(ctx, (size_t)rows * 16 * sizeof(float))) return rc;
+  const float* dq;
+  float* dout;
+  Staging st;
+  st.input(q, bytes, &dq);
+  st.output(q_out, bytes, &dout);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  LaunchTimer tm(ctx, "mlp_infer");
+  cudaError_t e = mlp_infer(ctx->mlp, dq, dof, rows, ctx->d_warm, ctx->stream);
+  if (e == cudaSuccess) {
+    const int tot = rows * dof;
+    add_correction_kernel<<<(tot + 255) / 256, 256, 0, ctx->stream>>>(dq, ctx->d_warm, rows, dof, dout);
+    e = cudaGetLastError();
+  }
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_infer");
+  rc = st.end(ctx);
+  if (rc == CPRRTC_OK && st.any_host) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, mlp_error_flag(ctx->mlp), sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_infer status");
+    if (flag) return fail(ctx, CPRRTC_E_TIMEOUT, "mlp_infer: a wait of the inference kernel timed out");
+  }
+  return rc;
+}
+
+int cprrtc_validate_ws(cprrtc_ctx* ctx, const float* q_start, const float* q_end, int n, int W,
+                       int refine_iters, float* out_q, uint8_t* status, int32_t* first_fail,
+                       uint8_t* iters, float* resid, uint8_t* warm_used) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "validate_ws: set_robot first");
+  if (ctx->cs.type == kConsNone)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "validate_ws: constraint is NONE");
+  if (int rc = mlp_ready(ctx, "validate_ws")) return rc;
+  if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "validate_ws: n < 0");
+  if (refine_iters < 1 || refine_iters > 20)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "validate_ws: refine_iters must be in [1, 20]");
+  if (W < 2 || W > CPRRTC_MAX_W)
+    return fail(ctx, W < 2 ? CPRRTC_E_INVALID_ARG : CPRRTC_E_UNSUPPORTED, "validate_ws: W must be in [2, 64]");
+  if (n == 0) return CPRRTC_OK;
+  if (!q_start || !q_end || !status) return fail(ctx, CPRRTC_E_INVALID_ARG, "validate_ws: null pointer");
+  DeviceGuard g(ctx->device);
+  const size_t dof = ctx->rb.dof, N = (size_t)n;
+  if (int rc = ensure_warm(ctx, N * W * 16 * sizeof(float))) return rc;
+  ValidateArgs a{};
+  a.n = n;
+  a.W = W;
+  a.cc_skip_first = 0;
+  a.work_counters = ctx->d_work;
+  a.warm = ctx->d_warm;
+  a.warm_error = mlp_error_flag(ctx->mlp);
+  a.refine_iters = refine_iters;
+  Staging st;
+  st.input(q_start, N * dof * sizeof(float), &a.q_start);
+  st.input(q_end, N * dof * sizeof(float), &a.q_end);
+  st.output(out_q, N * W * dof * sizeof(float), &a.out_q);
+  st.output(status, N, &a.status);
+  st.output(first_fail, N * sizeof(int32_t), &a.first_fail);
+  st.output(iters, N, &a.iters);
+  st.output(resid, N * sizeof(float), &a.resid);
+  st.output(warm_used, N, &a.warm_used);
+  int rc = st.begin(ctx);
+  if (rc) return rc;
+  {
+    LaunchTimer tm(ctx, "mlp_infer");
+    cudaError_t e = mlp_infer_motions(ctx->mlp, a.q_start, a.q_end, n, W, ctx->d_warm, ctx->stream);
+    tm.done();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate_ws inference");
+  }
+  LaunchTimer tm(ctx, "validate");
+  cudaError_t e = launch_validate(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "validate_ws launch");
   return st.end(ctx);
 }
 

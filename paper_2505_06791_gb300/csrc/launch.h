@@ -28,6 +28,13 @@ struct ValidateArgs {
   uint8_t* iters;
   float* resid;
   unsigned long long* work_counters;  // [6] executed-work totals (may be null)
+  // learned warm start: corrections [n*W][16] (row m*W+i, dof used) added to waypoints
+  // i >= 1 before refine_iters Alg. 1 iterations; plain Alg. 1 from the interpolation when
+  // that does not project. Null: plain Alg. 1 only.
+  const float* warm;
+  int refine_iters;
+  uint8_t* warm_used;  // [n] 1 when the warm-started segment was accepted (may be null)
+  const int* warm_error;  // nonzero: the corrections are not valid; plain Alg. 1 only
   int stage_obs;  // set by the launcher
 };
 
@@ -95,6 +102,56 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
                           cudaStream_t stream);
+
+// ---- learned warm start (mlp.cu) ----
+constexpr int kMlpLayers = 4;
+constexpr int kMlpHidden = 256;
+constexpr int kMlpIO = 16;  // input / output width (dof used, zero padding)
+struct MlpDev;
+size_t mlp_param_count();
+size_t mlp_compact_count(int dof);
+cudaError_t mlp_create(MlpDev** out, int dof);
+void mlp_destroy(MlpDev* d);
+int mlp_dof(const MlpDev* d);
+int mlp_step(const MlpDev* d);
+cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s);
+cudaError_t mlp_get_params(MlpDev* d, float* host, cudaStream_t s);
+cudaError_t mlp_init(MlpDev* d, uint64_t seed, cudaStream_t s);
+cudaError_t mlp_infer(MlpDev* d, const float* q, int ldq, int rows, float* Y, cudaStream_t s);
+cudaError_t mlp_infer_motions(MlpDev* d, const float* q0, const float* q1, int n, int W, float* Y,
+                              cudaStream_t s);
+cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float* grads_host,
+                     float* loss_host, cudaStream_t s);
+cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, float lr,
+                           float* loss_dev, cudaStream_t s);
+cudaError_t mlp_train(MlpDev* d, const float* q, const float* t, int n, int batch, int epochs,
+                      float lr, uint64_t seed, float* loss_host, cudaStream_t s);
+// Fused tensor-core inference (mlp_fused.cu). Rows are configurations q [rows][ldq] when q
+// is set, else waypoints of motions (row m * W + i of the interpolation q0[m] -> q1[m]).
+struct FusedMlpArgs {
+  const float* q;
+  int ldq;
+  const float* q0;
+  const float* q1;
+  int W;
+  int dof;
+  int rows;
+  const uint8_t* wpack;  // packed weight image (launch_mlp_pack)
+  const float* bias;     // [3][256] + [16] FP32
+  float* out;            // [rows][16] corrections
+  int* error;            // set to 1 when a wait timed out
+};
+size_t mlp_fused_image_bytes();
+int mlp_fused_bias_floats();
+size_t mlp_fused_smem_bytes();
+// w0..w3: BF16 weights, padded [out][in] per layer ([256][16], [256][256] x 2, [16][256])
+cudaError_t launch_mlp_pack(const void* w0, const void* w1, const void* w2, const void* w3,
+                            uint8_t* image, cudaStream_t s);
+cudaError_t launch_mlp_fused(const FusedMlpArgs& a, int sm_count, cudaStream_t s);
+const int* mlp_error_flag(const MlpDev* d);
+cudaError_t launch_residual_target(const float* q, const float* t, int rows, int dof, float* T,
+                                   cudaStream_t s);
+cudaError_t launch_accumulate(float* dst, const float* src, cudaStream_t s);
 
 size_t validate_smem_bytes(const RobotDev& rb, const SceneDev& sc, int W, bool stage_obs);
 cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs,

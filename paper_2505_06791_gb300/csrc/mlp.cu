@@ -1,0 +1,818 @@
+// Learned projection warm start: a 4-layer MLP (dof -> 256 -> 256 -> 256 -> dof, GELU),
+// BF16 weights and activations, FP32 accumulation on the tensor cores, trained with Adam
+// by the kernels below (forward, backward, optimiser), and evaluated in batches to give
+// Alg. 1 a starting segment closer to the manifold.
+//
+// GEMM: C[M,N] = A'[M,K] B'[K,N] in BF16 x BF16 -> FP32 with mma.sync m16n8k16. A' is A
+// ([M][K], or [K][M] when transposed) and B' is B ([K][N], or [N][K] when transposed), all
+// row-major with given leading dimensions. Tiles of 64 x 64 x 32 per CTA (4 warps, each
+// 32 x 32), staged in shared memory as [row][k] with a padded pitch (conflict-free
+// fragment loads), transposed on the way in when needed. Epilogues fuse the bias, GELU,
+// GELU's derivative and split-K accumulation.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "launch.h"
+#include "mlp_common.cuh"
+
+namespace cprrtc {
+
+namespace {
+
+constexpr int kTM = 64, kTN = 64, kTK = 32;
+constexpr int kPitch = kTK + 8;  // bf16 per staged row (20 words: conflict-free fragments)
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+}  // namespace
+
+// Epilogue kinds.
+enum : int {
+  kEpiStore = 0,     // C (FP32) = acc
+  kEpiBiasGelu = 1,  // Z (FP32) = acc + bias; H (BF16) = gelu(Z)
+  kEpiBias = 2,      // C (FP32) = acc + bias
+  kEpiGeluBwd = 3,   // H (BF16) = acc * gelu'(Z)   (Z read, FP32)
+  kEpiAtomic = 4,    // C (FP32) += acc  (split-K)
+};
+
+struct GemmArgs {
+  int M, N, K;
+  const __nv_bfloat16* A;
+  int lda, transA;
+  const __nv_bfloat16* B;
+  int ldb, transB;
+  float* C;  // FP32 output / Z (ldc)
+  int ldc;
+  __nv_bfloat16* H;  // BF16 output (ldh)
+  int ldh;
+  const float* bias;
+  const float* Z;  // pre-activation for the GELU backward (ldc)
+  int k_split;     // K range per blockIdx.z
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
+  __shared__ __align__(16) __nv_bfloat16 As[kTM][kPitch];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kPitch];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
+  const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = kb; k0 < ke; k0 += kTK) {
+    // stage A' rows m0.. and B' columns n0.. as [row][k]; 64 x 32 each, 16 per thread
+    for (int e = tid; e < kTM * kTK; e += 128) {
+      int r, k;
+      if (g.transA) {  // source [K][M]: consecutive threads walk m
+        r = e % kTM;
+        k = e / kTM;
+      } else {         // source [M][K]: consecutive threads walk k
+        r = e / kTK;
+        k = e % kTK;
+      }
+      const int gm = m0 + r, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gm < g.M && gk < ke)
+        v = g.transA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+      As[r][k] = v;
+    }
+    for (int e = tid; e < kTN * kTK; e += 128) {
+      int c, k;
+      if (g.transB) {  // source [N][K]
+        c = e / kTK;
+        k = e % kTK;
+      } else {         // source [K][N]
+        c = e % kTN;
+        k = e / kTN;
+      }
+      const int gn = n0 + c, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gn < g.N && gk < ke)
+        v = g.transB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
+      Bs[c][k] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kTK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + gid;
+        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tig]);
+        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tig]);
+        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 8 + 2 * tig]);
+        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 8 + 2 * tig]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + 8 * j + gid;
+        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * tig]);
+        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 8 + 2 * tig]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  // epilogue: acc[i][j] holds rows wm+16i+gid (+8), columns wn+8j+2tig (+1)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + wm + 16 * i + gid + (r >> 1) * 8;
+        const int gn = n0 + wn + 8 * j + 2 * tig + (r & 1);
+        if (gm >= g.M || gn >= g.N) continue;
+        const float v = acc[i][j][r];
+        const size_t ci = (size_t)gm * g.ldc + gn;
+        if (EPI == kEpiStore) {
+          g.C[ci] = v;
+        } else if (EPI == kEpiAtomic) {
+          atomicAdd(&g.C[ci], v);
+        } else if (EPI == kEpiBias) {
+          g.C[ci] = v + g.bias[gn];
+        } else if (EPI == kEpiBiasGelu) {
+          const float z = v + g.bias[gn];
+          if (g.C) g.C[ci] = z;
+          g.H[(size_t)gm * g.ldh + gn] = __float2bfloat16(mlp_gelu(z));
+        } else {  // kEpiGeluBwd
+          g.H[(size_t)gm * g.ldh + gn] = __float2bfloat16(v * mlp_gelu_grad(g.Z[ci]));
+        }
+      }
+}
+
+cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
+  GemmArgs g = g0;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  int splits = 1;
+  if (epi == kEpiAtomic) {
+    // split the reduction so that the grid covers the GPU
+    const int tiles = ((g.M + kTM - 1) / kTM) * ((g.N + kTN - 1) / kTN);
+    splits = std::max(1, std::min((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
+  }
+  g.k_split = ((g.K + splits - 1) / splits + kTK - 1) / kTK * kTK;
+  splits = (g.K + g.k_split - 1) / g.k_split;
+  dim3 grid((g.M + kTM - 1) / kTM, (g.N + kTN - 1) / kTN, splits);
+  switch (epi) {
+    case kEpiStore: gemm_bf16_kernel<kEpiStore><<<grid, 128, 0, stream>>>(g); break;
+    case kEpiBiasGelu: gemm_bf16_kernel<kEpiBiasGelu><<<grid, 128, 0, stream>>>(g); break;
+    case kEpiBias: gemm_bf16_kernel<kEpiBias><<<grid, 128, 0, stream>>>(g); break;
+    case kEpiGeluBwd: gemm_bf16_kernel<kEpiGeluBwd><<<grid, 128, 0, stream>>>(g); break;
+    default: gemm_bf16_kernel<kEpiAtomic><<<grid, 128, 0, stream>>>(g); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---- elementwise kernels ---------------------------------------------------------------
+
+// X[r][0..in) = q[r][k] / pi (k < dof), zero padding; rows of the input to layer 1.
+__global__ void mlp_input_kernel(const float* __restrict__ q, int ldq, int rows, int dof, int in,
+                                 __nv_bfloat16* X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * in) return;
+  const int r = i / in, k = i - r * in;
+  X[i] = __float2bfloat16(k < dof ? q[(size_t)r * ldq + k] * kMlpInvPi : 0.f);
+}
+
+// Interpolated waypoints of each motion as MLP input rows (row m * W + i).
+__global__ void mlp_interp_input_kernel(const float* __restrict__ q0, const float* __restrict__ q1,
+                                        int n, int W, int dof, int in, __nv_bfloat16* X) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * W * in) return;
+  const int r = i / in, k = i - r * in;
+  const int m = r / W, w = r - m * W;
+  float v = 0.f;
+  if (k < dof) {
+    const float a = q0[(size_t)m * dof + k], b = q1[(size_t)m * dof + k];
+    v = fmaf((float)w / (float)(W - 1), b - a, a) * kMlpInvPi;
+  }
+  X[i] = __float2bfloat16(v);
+}
+
+// dY = (Y - T) / rows on the dof used outputs (zero on padding), and the loss 0.5 |Y-T|^2 / rows.
+__global__ void mse_grad_kernel(const float* __restrict__ Y, int ldy, const float* __restrict__ T,
+                                int ldt, int rows, int dof, int out, __nv_bfloat16* dY,
+                                float* loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < rows * out) {
+    const int r = i / out, k = i - r * out;
+    float d = 0.f;
+    if (k < dof) {
+      d = Y[(size_t)r * ldy + k] - T[(size_t)r * ldt + k];
+      l = 0.5f * d * d / (float)rows;
+    }
+    dY[i] = __float2bfloat16(d / (float)rows);
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l);
+}
+
+// db[n] = sum_r D[r][n]  (D in BF16, [rows][ld])
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ D, int ld, int rows, int N, float* db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) s += __bfloat162float(D[(size_t)r * ld + n]);
+  atomicAdd(&db[n], s);
+}
+
+// Adam on one tensor (FP32 master p, moments m v, gradient g), then its BF16 copies:
+// wt [rows][cols] (the tensor itself) and, if w_t is set, its transpose [cols][rows].
+// Entries outside [rows_used, cols_used) (padding) stay zero.
+__global__ void adam_kernel(float* p, float* m, float* v, const float* g, int rows, int cols,
+                            int rows_used, int cols_used, float lr, float b1, float b2, float eps,
+                            float c1, float c2, __nv_bfloat16* wt, __nv_bfloat16* w_t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i / cols, c = i - r * cols;
+  float x = 0.f;
+  if (r < rows_used && c < cols_used) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    x = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = x;
+  }
+  if (wt) wt[i] = __float2bfloat16(x);
+  if (w_t) w_t[(size_t)c * rows + r] = __float2bfloat16(x);
+}
+
+// BF16 copies of an FP32 tensor [rows][cols] (and of its transpose).
+__global__ void to_bf16_kernel(const float* p, int rows, int cols, __nv_bfloat16* wt,
+                               __nv_bfloat16* w_t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i / cols, c = i - r * cols;
+  if (wt) wt[i] = __float2bfloat16(p[i]);
+  if (w_t) w_t[(size_t)c * rows + r] = __float2bfloat16(p[i]);
+}
+
+// T[r][k] = t[r][k] - q[r][k] (k < dof), zero padding to 16.
+__global__ void residual_target_kernel(const float* __restrict__ q, const float* __restrict__ t, int rows,
+                                       int dof, float* T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * kMlpIO) return;
+  const int r = i / kMlpIO, k = i - r * kMlpIO;
+  T[i] = k < dof ? t[(size_t)r * dof + k] - q[(size_t)r * dof + k] : 0.f;
+}
+
+__global__ void accumulate_kernel(float* dst, const float* src) { *dst += *src; }
+
+cudaError_t launch_residual_target(const float* q, const float* t, int rows, int dof, float* T,
+                                   cudaStream_t s) {
+  const int n = rows * kMlpIO;
+  if (n <= 0) return cudaSuccess;
+  residual_target_kernel<<<(n + 255) / 256, 256, 0, s>>>(q, t, rows, dof, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(float* dst, const float* src, cudaStream_t s) {
+  accumulate_kernel<<<1, 1, 0, s>>>(dst, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_input(const float* q, int ldq, int rows, int dof, int in, __nv_bfloat16* X,
+                             cudaStream_t s) {
+  const int n = rows * in;
+  if (n <= 0) return cudaSuccess;
+  mlp_input_kernel<<<(n + 255) / 256, 256, 0, s>>>(q, ldq, rows, dof, in, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_interp_input(const float* q0, const float* q1, int n, int W, int dof, int in,
+                                    __nv_bfloat16* X, cudaStream_t s) {
+  const long long tot = (long long)n * W * in;
+  if (tot <= 0) return cudaSuccess;
+  mlp_interp_input_kernel<<<(int)((tot + 255) / 256), 256, 0, s>>>(q0, q1, n, W, dof, in, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mse_grad(const float* Y, int ldy, const float* T, int ldt, int rows, int dof, int out,
+                            __nv_bfloat16* dY, float* loss, cudaStream_t s) {
+  const int n = rows * out;
+  if (n <= 0) return cudaSuccess;
+  mse_grad_kernel<<<(n + 255) / 256, 256, 0, s>>>(Y, ldy, T, ldt, rows, dof, out, dY, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bias_grad(const __nv_bfloat16* D, int ld, int rows, int N, float* db, cudaStream_t s) {
+  if (rows <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + 127) / 128, std::min(rows, 256));
+  bias_grad_kernel<<<grid, 128, 0, s>>>(D, ld, rows, N, db);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, float* m, float* v, const float* g, int rows, int cols, int rows_used,
+                        int cols_used, float lr, float b1, float b2, float eps, int step,
+                        __nv_bfloat16* wt, __nv_bfloat16* w_t, cudaStream_t s) {
+  const int n = rows * cols;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, m, v, g, rows, cols, rows_used, cols_used, lr, b1, b2,
+                                              eps, c1, c2, wt, w_t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* p, int rows, int cols, __nv_bfloat16* wt, __nv_bfloat16* w_t,
+                           cudaStream_t s) {
+  const int n = rows * cols;
+  to_bf16_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, rows, cols, wt, w_t);
+  return cudaGetLastError();
+}
+
+// ---- the network and its training -----------------------------------------------------
+//
+// Layers l = 0..3: in_l -> out_l with in = (16, 256, 256, 256), out = (256, 256, 256, 16);
+// dof inputs and outputs are used, the rest is zero padding. Parameters (FP32 master copy)
+// are laid out flat as, per layer, the weight [out][in] then the bias [out].
+
+namespace {
+
+constexpr int kIn[kMlpLayers] = {kMlpIO, kMlpHidden, kMlpHidden, kMlpHidden};
+constexpr int kOut[kMlpLayers] = {kMlpHidden, kMlpHidden, kMlpHidden, kMlpIO};
+
+size_t w_off(int l) {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)kOut[i] * kIn[i] + kOut[i];
+  return o;
+}
+
+}  // namespace
+
+size_t mlp_param_count() { return w_off(kMlpLayers); }
+
+struct MlpDev {
+  int dof = 0;
+  int step = 0;
+  float* p = nullptr;   // FP32 master parameters
+  float* m = nullptr;   // Adam moments
+  float* v = nullptr;
+  float* g = nullptr;   // gradients
+  __nv_bfloat16* wb = nullptr;  // BF16 weights [out][in] per layer (biases stay FP32)
+  // fused inference: packed weight image, padded biases, timeout flag
+  uint8_t* wpack = nullptr;
+  float* bias_pad = nullptr;
+  int* err = nullptr;
+  bool packed = false;
+  int sm_count = 0;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+static cudaError_t ensure_ws(MlpDev* d, size_t bytes) {
+  if (bytes <= d->ws_bytes) return cudaSuccess;
+  if (d->ws) cudaFree(d->ws);
+  d->ws = nullptr;
+  d->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&d->ws, bytes);
+  if (e == cudaSuccess) d->ws_bytes = bytes;
+  return e;
+}
+
+cudaError_t mlp_create(MlpDev** out, int dof) {
+  *out = nullptr;
+  MlpDev* d = new MlpDev();
+  d->dof = dof;
+  const size_t n = mlp_param_count();
+  size_t nw = 0;
+  for (int l = 0; l < kMlpLayers; ++l) nw += (size_t)kOut[l] * kIn[l];
+  cudaError_t e = cudaMalloc(&d->p, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d->m, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d->v, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d->g, n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d->wb, nw * 2);
+  if (e == cudaSuccess) e = cudaMemset(d->p, 0, n * 4);
+  if (e == cudaSuccess) e = cudaMemset(d->m, 0, n * 4);
+  if (e == cudaSuccess) e = cudaMemset(d->v, 0, n * 4);
+  if (e == cudaSuccess) e = cudaMemset(d->wb, 0, nw * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->wpack, mlp_fused_image_bytes());
+  if (e == cudaSuccess) e = cudaMalloc(&d->bias_pad, (size_t)mlp_fused_bias_floats() * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d->err, 0, sizeof(int));
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    mlp_destroy(d);
+    return e;
+  }
+  *out = d;
+  return cudaSuccess;
+}
+
+void mlp_destroy(MlpDev* d) {
+  if (!d) return;
+  cudaFree(d->p);
+  cudaFree(d->m);
+  cudaFree(d->v);
+  cudaFree(d->g);
+  cudaFree(d->wb);
+  cudaFree(d->ws);
+  cudaFree(d->wpack);
+  cudaFree(d->bias_pad);
+  cudaFree(d->err);
+  delete d;
+}
+
+int mlp_dof(const MlpDev* d) { return d->dof; }
+const int* mlp_error_flag(const MlpDev* d) { return d->err; }
+int mlp_step(const MlpDev* d) { return d->step; }
+
+static __nv_bfloat16* wb_of(MlpDev* d, int l) {
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)kOut[i] * kIn[i];
+  return d->wb + o;
+}
+
+// Refreshes the BF16 weight copies from the FP32 master parameters.
+static cudaError_t refresh_bf16(MlpDev* d, cudaStream_t s) {
+  d->packed = false;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    cudaError_t e = launch_to_bf16(d->p + w_off(l), kOut[l], kIn[l], wb_of(d, l), nullptr, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Public (compact) layout for a robot with dof joints: per layer l, W_l [out_l][in_l] then
+// b_l [out_l], with in = (dof, 256, 256, 256) and out = (256, 256, 256, dof).
+size_t mlp_compact_count(int dof) {
+  return (size_t)kMlpHidden * dof + kMlpHidden + 2 * ((size_t)kMlpHidden * kMlpHidden + kMlpHidden) +
+         (size_t)dof * kMlpHidden + dof;
+}
+
+static void compact_dims(int dof, int l, int& rows, int& cols) {
+  rows = l == kMlpLayers - 1 ? dof : kOut[l];
+  cols = l == 0 ? dof : kIn[l];
+}
+
+// Sets the parameters from a host array in the compact layout (padding stays zero) and
+// resets the optimiser state.
+cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s) {
+  std::vector<float> p(mlp_param_count(), 0.f);
+  const float* src = host;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    int rows, cols;
+    compact_dims(d->dof, l, rows, cols);
+    float* w = p.data() + w_off(l);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) w[(size_t)r * kIn[l] + c] = *src++;
+    float* b = w + (size_t)kOut[l] * kIn[l];
+    for (int r = 0; r < rows; ++r) b[r] = *src++;
+  }
+  const size_t n = mlp_param_count();
+  cudaError_t e = cudaMemcpyAsync(d->p, p.data(), n * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->m, 0, n * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->v, 0, n * 4, s);
+  if (e == cudaSuccess) e = refresh_bf16(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  d->step = 0;
+  return e;
+}
+
+// Copies a padded device parameter-shaped array (parameters or gradients) to a host array
+// in the compact layout.
+static cudaError_t to_compact(MlpDev* d, const float* dev, float* host, cudaStream_t s) {
+  std::vector<float> p(mlp_param_count());
+  cudaError_t e = cudaMemcpyAsync(p.data(), dev, p.size() * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  float* dst = host;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    int rows, cols;
+    compact_dims(d->dof, l, rows, cols);
+    const float* w = p.data() + w_off(l);
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c) *dst++ = w[(size_t)r * kIn[l] + c];
+    const float* b = w + (size_t)kOut[l] * kIn[l];
+    for (int r = 0; r < rows; ++r) *dst++ = b[r];
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mlp_get_params(MlpDev* d, float* host, cudaStream_t s) { return to_compact(d, d->p, host, s); }
+
+// He-normal weights (the last layer scaled by 0.1: the corrections it predicts are small),
+// zero biases; Gaussian draws from a splitmix64 stream with the Box-Muller transform.
+cudaError_t mlp_init(MlpDev* d, uint64_t seed, cudaStream_t s) {
+  std::vector<float> p(mlp_compact_count(d->dof), 0.f);
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  auto next = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto normal = [&]() {
+    const double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  float* w = p.data();
+  for (int l = 0; l < kMlpLayers; ++l) {
+    int rows, cols;
+    compact_dims(d->dof, l, rows, cols);
+    const double sd = std::sqrt(2.0 / cols) * (l == kMlpLayers - 1 ? 0.1 : 1.0);
+    for (size_t i = 0; i < (size_t)rows * cols; ++i) *w++ = (float)(sd * normal());
+    w += rows;  // zero biases
+  }
+  return mlp_set_params(d, p.data(), s);
+}
+
+// Workspace layout for `rows` rows: X (bf16 16) | H ping-pong (bf16 256 x 2) | Z x 3 (f32
+// 256, training only) | Y (f32 16) | dY (bf16 16) | dZ ping-pong (bf16 256 x 2) | loss (f32).
+struct MlpWs {
+  __nv_bfloat16 *X, *H[2], *dY, *dZ[2];
+  float *Z[3], *Y, *loss;
+};
+
+static size_t ws_layout(char* base, int rows, bool train, MlpWs* w) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + o : nullptr;
+    o += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  const size_t R = (size_t)rows;
+  w->X = (__nv_bfloat16*)take(R * kMlpIO * 2);
+  w->H[0] = (__nv_bfloat16*)take(R * kMlpHidden * 2);
+  w->H[1] = (__nv_bfloat16*)take(R * kMlpHidden * 2);
+  for (int i = 0; i < 3; ++i) w->Z[i] = train ? (float*)take(R * kMlpHidden * 4) : nullptr;
+  w->Y = (float*)take(R * kMlpIO * 4);
+  w->dY = train ? (__nv_bfloat16*)take(R * kMlpIO * 2) : nullptr;
+  w->dZ[0] = train ? (__nv_bfloat16*)take(R * kMlpHidden * 2) : nullptr;
+  w->dZ[1] = train ? (__nv_bfloat16*)take(R * kMlpHidden * 2) : nullptr;
+  w->loss = (float*)take(4);
+  return o;
+}
+
+// Forward pass of rows of X already in w.X; Y (FP32 [rows][16]) = corrections. In training
+// mode the activations H_l (kept in a 3-deep set for the backward) and Z_l are stored.
+static cudaError_t forward(MlpDev* d, const MlpWs& w, int rows, __nv_bfloat16* Hkeep[3],
+                           cudaStream_t s) {
+  const __nv_bfloat16* in = w.X;
+  int ld_in = kMlpIO;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    GemmArgs g{};
+    g.M = rows;
+    g.N = kOut[l];
+    g.K = kIn[l];
+    g.A = in;
+    g.lda = ld_in;
+    g.transA = 0;
+    g.B = wb_of(d, l);  // [out][in] = [N][K]
+    g.ldb = kIn[l];
+    g.transB = 1;
+    g.bias = d->p + w_off(l) + (size_t)kOut[l] * kIn[l];
+    cudaError_t e;
+    if (l < kMlpLayers - 1) {
+      __nv_bfloat16* out = Hkeep ? Hkeep[l] : w.H[l & 1];
+      g.C = w.Z[0] && Hkeep ? w.Z[l] : nullptr;
+      g.ldc = kMlpHidden;
+      g.H = out;
+      g.ldh = kMlpHidden;
+      e = launch_gemm(kEpiBiasGelu, g, s);
+      in = out;
+      ld_in = kMlpHidden;
+    } else {
+      g.C = w.Y;
+      g.ldc = kMlpIO;
+      e = launch_gemm(kEpiBias, g, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Packs the current weights for the fused kernel when they changed since the last pack.
+static cudaError_t ensure_packed(MlpDev* d, cudaStream_t s) {
+  if (d->packed) return cudaSuccess;
+  cudaError_t e = launch_mlp_pack(wb_of(d, 0), wb_of(d, 1), wb_of(d, 2), wb_of(d, 3), d->wpack, s);
+  for (int l = 0; l < kMlpLayers && e == cudaSuccess; ++l)
+    e = cudaMemcpyAsync(d->bias_pad + 256 * l, d->p + w_off(l) + (size_t)kOut[l] * kIn[l],
+                        (size_t)kOut[l] * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) d->packed = true;
+  return e;
+}
+
+static cudaError_t run_fused(MlpDev* d, FusedMlpArgs a, cudaStream_t s) {
+  cudaError_t e = ensure_packed(d, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->err, 0, sizeof(int), s);
+  a.dof = d->dof;
+  a.wpack = d->wpack;
+  a.bias = d->bias_pad;
+  a.error = d->err;
+  if (e == cudaSuccess) e = launch_mlp_fused(a, d->sm_count, s);
+  return e;
+}
+
+// Inference: corrections Y [rows][16] for rows of q ([rows][ldq], first dof used).
+cudaError_t mlp_infer(MlpDev* d, const float* q, int ldq, int rows, float* Y, cudaStream_t s) {
+  FusedMlpArgs a{};
+  a.q = q;
+  a.ldq = ldq;
+  a.rows = rows;
+  a.out = Y;
+  return run_fused(d, a, s);
+}
+
+// Inference on the interpolated waypoints of n motions (row m * W + i) into Y [n*W][16].
+cudaError_t mlp_infer_motions(MlpDev* d, const float* q0, const float* q1, int n, int W, float* Y,
+                              cudaStream_t s) {
+  FusedMlpArgs a{};
+  a.q0 = q0;
+  a.q1 = q1;
+  a.W = W;
+  a.rows = n * W;
+  a.out = Y;
+  return run_fused(d, a, s);
+}
+
+// Loss 0.5 |MLP(q) - (t - q)|^2 averaged over rows and its gradient into d->g.
+// q, t: [rows][dof] device arrays. *loss_dev (device float) receives the loss.
+static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int rows, cudaStream_t s,
+                                 MlpWs& w) {
+  const size_t need = ws_layout(nullptr, rows, true, &w) + (size_t)rows * kMlpIO * 4;
+  cudaError_t e = ensure_ws(d, need);
+  if (e != cudaSuccess) return e;
+  const size_t used = ws_layout(d->ws, rows, true, &w);
+  float* target = reinterpret_cast<float*>(d->ws + used);  // t - q, [rows][16]
+  e = launch_mlp_input(q, d->dof, rows, d->dof, kMlpIO, w.X, s);
+  if (e != cudaSuccess) return e;
+  e = launch_residual_target(q, t, rows, d->dof, target, s);
+  if (e != cudaSuccess) return e;
+  __nv_bfloat16* H[3] = {w.H[0], w.H[1], w.dZ[1]};  // three stored activations
+  // a third activation buffer: reuse dZ[1] for H3 during the forward; the backward below
+  // writes dZ only into buffers whose activation is no longer needed
+  e = forward(d, w, rows, H, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(w.loss, 0, 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->g, 0, mlp_param_count() * 4, s);
+  if (e == cudaSuccess)
+    e = launch_mse_grad(w.Y, kMlpIO, target, kMlpIO, rows, d->dof, kMlpIO, w.dY, w.loss, s);
+  if (e != cudaSuccess) return e;
+  // backward, layer 3 .. 0: D_l = dL/dZ_l (BF16), previous activation A_{l} = H[l-1] or X
+  const __nv_bfloat16* D = w.dY;
+  int ldD = kMlpIO;
+  __nv_bfloat16* dz_out[3] = {w.dZ[0], w.H[1], w.dZ[0]};  // dZ_2 -> dZ[0], dZ_1 -> H[1], dZ_0 -> dZ[0]
+  for (int l = kMlpLayers - 1; l >= 0; --l) {
+    const __nv_bfloat16* Aprev = l == 0 ? w.X : H[l - 1];
+    const int ldA = l == 0 ? kMlpIO : kMlpHidden;
+    // weight gradient dW_l [out][in] = D^T Aprev  (split-K over rows, atomics)
+    GemmArgs gw{};
+    gw.M = kOut[l];
+    gw.N = kIn[l];
+    gw.K = rows;
+    gw.A = D;
+    gw.lda = ldD;
+    gw.transA = 1;  // D is [rows][out] = [K][M]
+    gw.B = Aprev;
+    gw.ldb = ldA;
+    gw.transB = 0;  // Aprev is [rows][in] = [K][N]
+    gw.C = d->g + w_off(l);
+    gw.ldc = kIn[l];
+    e = launch_gemm(kEpiAtomic, gw, s);
+    if (e == cudaSuccess) e = launch_bias_grad(D, ldD, rows, kOut[l], d->g + w_off(l) + (size_t)kOut[l] * kIn[l], s);
+    if (e != cudaSuccess) return e;
+    if (l == 0) break;
+    // dZ_{l-1} = (D W_l) * gelu'(Z_{l-1})
+    GemmArgs gd{};
+    gd.M = rows;
+    gd.N = kIn[l];
+    gd.K = kOut[l];
+    gd.A = D;
+    gd.lda = ldD;
+    gd.transA = 0;
+    gd.B = wb_of(d, l);  // [out][in] = [K][N]
+    gd.ldb = kIn[l];
+    gd.transB = 0;
+    gd.Z = w.Z[l - 1];
+    gd.ldc = kMlpHidden;
+    gd.H = dz_out[l - 1];
+    gd.ldh = kMlpHidden;
+    e = launch_gemm(kEpiGeluBwd, gd, s);
+    if (e != cudaSuccess) return e;
+    D = dz_out[l - 1];
+    ldD = kMlpHidden;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float* grads_host,
+                     float* loss_host, cudaStream_t s) {
+  MlpWs w;
+  cudaError_t e = loss_and_grad(d, q, t, rows, s, w);
+  if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, w.loss, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && grads_host) e = to_compact(d, d->g, grads_host, s);
+  return e;
+}
+
+// One Adam step on the batch; the batch loss is added to *loss_dev (device) if given.
+cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, float lr,
+                           float* loss_dev, cudaStream_t s) {
+  MlpWs w;
+  cudaError_t e = loss_and_grad(d, q, t, rows, s, w);
+  if (e != cudaSuccess) return e;
+  d->step++;
+  for (int l = 0; l < kMlpLayers; ++l) {
+    const int rows_used = l == kMlpLayers - 1 ? d->dof : kOut[l];
+    const int cols_used = l == 0 ? d->dof : kIn[l];
+    const size_t o = w_off(l);
+    e = launch_adam(d->p + o, d->m + o, d->v + o, d->g + o, kOut[l], kIn[l], rows_used, cols_used, lr,
+                    0.9f, 0.999f, 1e-8f, d->step, wb_of(d, l), nullptr, s);
+    if (e == cudaSuccess) {
+      const size_t ob = o + (size_t)kOut[l] * kIn[l];
+      e = launch_adam(d->p + ob, d->m + ob, d->v + ob, d->g + ob, 1, kOut[l], 1, rows_used, lr, 0.9f,
+                      0.999f, 1e-8f, d->step, nullptr, nullptr, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (loss_dev) e = launch_accumulate(loss_dev, w.loss, s);
+  return e;
+}
+
+// rows of q and t picked by idx into contiguous batch arrays
+__global__ void gather_rows_kernel(const float* __restrict__ q, const float* __restrict__ t,
+                                   const int* __restrict__ idx, int rows, int dof, float* qb, float* tb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * dof) return;
+  const int r = i / dof, k = i - r * dof;
+  const size_t src = (size_t)idx[r] * dof + k;
+  qb[i] = q[src];
+  tb[i] = t[src];
+}
+
+// Epochs of minibatch Adam over n pairs (q, t) in device memory, in an order drawn per epoch
+// (Fisher-Yates over a splitmix64 stream). loss_host[epoch] (optional) = mean batch loss.
+cudaError_t mlp_train(MlpDev* d, const float* q, const float* t, int n, int batch, int epochs,
+                      float lr, uint64_t seed, float* loss_host, cudaStream_t s) {
+  const int dof = d->dof;
+  const int nb = n / batch;  // full batches only
+  if (nb < 1) return cudaErrorInvalidValue;
+  int* idx = nullptr;
+  float *qb = nullptr, *tb = nullptr, *loss = nullptr;
+  cudaError_t e = cudaMalloc(&idx, (size_t)n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&qb, (size_t)batch * dof * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&tb, (size_t)batch * dof * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&loss, (size_t)std::max(epochs, 1) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, (size_t)std::max(epochs, 1) * 4, s);
+  std::vector<int> perm(n);
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  uint64_t st = seed ^ 0xD1B54A32D192ED03ull;
+  auto next = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    for (int i = n - 1; i > 0; --i) std::swap(perm[i], perm[(int)(next() % (uint64_t)(i + 1))]);
+    e = cudaMemcpyAsync(idx, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
+    // the host order must not change while the copy is in flight
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+      const int tot = batch * dof;
+      gather_rows_kernel<<<(tot + 255) / 256, 256, 0, s>>>(q, t, idx + (size_t)b * batch, batch, dof, qb, tb);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = mlp_train_step(d, qb, tb, batch, lr, loss + ep, s);
+    }
+  }
+  if (e == cudaSuccess && loss_host) {
+    std::vector<float> l(std::max(epochs, 1));
+    e = cudaMemcpyAsync(l.data(), loss, l.size() * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int ep = 0; ep < epochs; ++ep) loss_host[ep] = l[ep] / nb;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(idx);
+  cudaFree(qb);
+  cudaFree(tb);
+  cudaFree(loss);
+  return e;
+}
+
+}  // namespace cprrtc

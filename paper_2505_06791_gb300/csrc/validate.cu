@@ -35,11 +35,64 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
       }
     }
     float q[WPL][kMaxDof];
-#pragma unroll
-    for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, dof, q[s]);
     const float tau = step_threshold(cs, q0, q1, W, dof);
-    const ProjResult pr = project_warp<CT, WPL>(rb, cs, cs.max_iters, q, W, tau);
-    work.updates += (unsigned)pr.updates;
+    // pass 0 (warm start only): interpolation + learned correction, refine_iters
+    // iterations. The correction of waypoint i is f(xi_i) - (1 - i/(W-1)) f(xi_0): waypoint 0
+    // lies on the manifold, so f(xi_0) is the network's local error, removed where the
+    // segment joins its fixed start; pass 1: Alg. 1 from the interpolation. The plain pass runs when the warm
+    // one did not project the whole segment. The warm start is tried only when its largest
+    // task residual over waypoints 1..W-1 is below the interpolation's.
+    ProjResult pr;
+    int spent = 0, warm_ok = 0, first_pass = 1;
+    if (a.warm && !(a.warm_error && *a.warm_error)) {
+      float e_warm = 0.f, e_plain = 0.f;
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) {
+        const int i = lane + 32 * s;
+        if (i >= 1 && i < W) {
+          float qp[kMaxDof], qw[kMaxDof];
+          interp(q0, q1, i, W, dof, qp);
+          const float* y = a.warm + ((size_t)m * W + i) * 16;
+          const float* y0 = a.warm + (size_t)m * W * 16;
+          const float taper = 1.f - (float)i / (float)(W - 1);
+#pragma unroll
+          for (int k = 0; k < kMaxDof; ++k)
+            qw[k] = k < dof ? fminf(fmaxf(qp[k] + fmaf(-taper, y0[k], y[k]), rb.j[k].lo), rb.j[k].hi)
+                            : 0.f;
+          ChainState ch;
+          chain(rb, qp, nullptr, ch);
+          e_plain = fmaxf(e_plain, task_err_inf<CT>(task_error<CT>(rb, cs, ch)));
+          chain(rb, qw, nullptr, ch);
+          e_warm = fmaxf(e_warm, task_err_inf<CT>(task_error<CT>(rb, cs, ch)));
+          work.updates += 2u;
+        }
+      }
+      first_pass = warp_max(e_warm) < warp_max(e_plain) ? 0 : 1;
+    }
+    for (int pass = first_pass; pass < 2; ++pass) {
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) {
+        const int i = min(lane + 32 * s, W - 1);
+        interp(q0, q1, i, W, dof, q[s]);
+        if (pass == 0 && i > 0) {
+          const float* y = a.warm + ((size_t)m * W + i) * 16;
+          const float* y0 = a.warm + (size_t)m * W * 16;
+          const float taper = 1.f - (float)i / (float)(W - 1);
+#pragma unroll
+          for (int k = 0; k < kMaxDof; ++k)
+            if (k < dof)
+              q[s][k] = fminf(fmaxf(q[s][k] + fmaf(-taper, y0[k], y[k]), rb.j[k].lo), rb.j[k].hi);
+        }
+      }
+      pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? a.refine_iters : cs.max_iters, q, W, tau);
+      work.updates += (unsigned)pr.updates;
+      if (pass == 0 && pr.status == kValid) {
+        warm_ok = 1;
+        break;
+      }
+      if (pass == 0) spent = pr.iters;
+    }
+    pr.iters += spent;
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid) {
       ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work);
@@ -62,6 +115,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
       if (a.first_fail) a.first_fail[m] = ff;
       if (a.iters) a.iters[m] = (uint8_t)pr.iters;
       if (a.resid) a.resid[m] = pr.resid;
+      if (a.warm_used) a.warm_used[m] = (uint8_t)warm_ok;
     }
     __syncwarp();
   }

@@ -1,0 +1,234 @@
+"""GPU checks of the learned warm start: the network's forward pass and gradient (BF16
+tensor-core kernels) against the FP64 oracle on weights and data the test draws itself,
+training on oracle-projected pairs, and cprrtc_validate_ws, whose answers are judged by
+the plain projection's acceptance tests and the oracle's collision check."""
+import numpy as np
+import pytest
+
+from paper_2505_06791_gb300 import synth as S
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+DOF, H = 7, 256
+# BF16 rounds inputs, activations and back-propagated signals (relative 2^-9 each, about
+# eight roundings on any path); FP32 accumulation. Norm-relative error bound:
+REL_FWD = 2e-2
+REL_GRAD = 3e-2
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_06791_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def setup():
+    rb = S.make_arm7(1)
+    sc = S.make_scene(1001, n_sph=16)
+    c = S.roll_pitch(20)
+    return rb, sc, c
+
+
+def make_ctx(rb, sc, c):
+    from paper_2505_06791_gb300.capi import Context
+    ctx = Context(0)
+    ctx.set_robot(rb)
+    ctx.set_obstacles(sc)
+    ctx.set_constraint(c)
+    return ctx
+
+
+def bf16(x):
+    """Round FP32 values to the nearest BF16 (ties to even), returned as float64."""
+    a = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def random_params(oracle_mod, seed, out_scale=1.0):
+    """He-scaled FP32 weights and small biases in the compact layout."""
+    rng = np.random.default_rng(seed)
+    dims = [(H, DOF), (H, H), (H, H), (DOF, H)]
+    parts, weight_mask = [], []
+    for l, (o, i) in enumerate(dims):
+        s = np.sqrt(2.0 / i) * (out_scale if l == 3 else 1.0)
+        parts += [rng.normal(0, s, o * i), rng.normal(0, 0.05, o)]
+        weight_mask += [np.ones(o * i, bool), np.zeros(o, bool)]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == oracle_mod.mlp_param_count(DOF, H)
+    return p, np.concatenate(weight_mask)
+
+
+def oracle_view(p32, wmask):
+    """What the GPU computes with: BF16 weights, FP32 biases."""
+    p = p32.astype(np.float64)
+    p[wmask] = bf16(p32[wmask])
+    return p
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_param_roundtrip_and_init(torch_cuda, oracle_mod, setup):
+    ctx = make_ctx(*setup)
+    ctx.mlp_init(7)
+    a = ctx.mlp_get_params()
+    ctx.mlp_init(7)
+    np.testing.assert_array_equal(ctx.mlp_get_params(), a)
+    ctx.mlp_init(8)
+    assert not np.array_equal(ctx.mlp_get_params(), a)
+    assert a.size == oracle_mod.mlp_param_count(DOF, H) == ctx.mlp_param_count()
+    w2 = a[H * DOF + H: H * DOF + H + H * H]
+    assert abs(w2.std() - np.sqrt(2.0 / H)) < 0.05 * np.sqrt(2.0 / H)
+    p, _ = random_params(oracle_mod, 1)
+    ctx.mlp_set_params(p)
+    np.testing.assert_array_equal(ctx.mlp_get_params(), p)
+    ctx.close()
+
+
+@pytest.mark.parametrize("rows", [1, 65, 1000])
+def test_forward_matches_oracle(torch_cuda, oracle_mod, setup, rows):
+    ctx = make_ctx(*setup)
+    ctx.mlp_init(0)
+    p, wmask = random_params(oracle_mod, 10 + rows, out_scale=0.3)
+    ctx.mlp_set_params(p)
+    rb = setup[0]
+    q = S.uniform_configs(rb, rows, 500 + rows).astype(np.float32)
+    got = ctx.mlp_infer(torch_cuda.from_numpy(q).cuda()).cpu().numpy().astype(np.float64)
+    want = q + oracle_mod.mlp_forward(oracle_view(p, wmask), q.astype(np.float64), DOF, H)
+    corr_err = rel_err(got - q, want - q)
+    assert corr_err < REL_FWD, corr_err
+    ctx.close()
+
+
+def test_gradient_matches_oracle(torch_cuda, oracle_mod, setup):
+    rb = setup[0]
+    ctx = make_ctx(*setup)
+    ctx.mlp_init(0)
+    p, wmask = random_params(oracle_mod, 3, out_scale=0.3)
+    ctx.mlp_set_params(p)
+    rows = 777   # ragged against the 64-row tiles
+    rng = np.random.default_rng(4)
+    q = S.uniform_configs(rb, rows, 41).astype(np.float32)
+    t = (q + rng.normal(0, 0.3, q.shape)).astype(np.float32)
+    loss, g = ctx.mlp_grad(torch_cuda.from_numpy(q).cuda(), torch_cuda.from_numpy(t).cuda())
+    l_ref, g_ref = oracle_mod.mlp_loss_grad(oracle_view(p, wmask), q, t, DOF, H, n_threads=8)
+    assert abs(loss - l_ref) < REL_FWD * l_ref, (loss, l_ref)
+    off = 0
+    for o, i in [(H, DOF), (H, H), (H, H), (DOF, H)]:
+        for name, size in (("W", o * i), ("b", o)):
+            e = rel_err(g[off:off + size].astype(np.float64), g_ref[off:off + size])
+            assert e < REL_GRAD, (name, o, i, e)
+            off += size
+    ctx.close()
+
+
+def oracle_pairs(oracle_mod, rb, sc, c, n, seed):
+    """Uniform configurations and their oracle projections (successful ones)."""
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q = S.uniform_configs(rb, n, seed).astype(np.float32)
+    ok, qp, _ = orc.project_configs(q, 60, n_threads=16)
+    return q[ok], qp[ok].astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def trained(torch_cuda, oracle_mod, setup):
+    rb, sc, c = setup
+    q, t = oracle_pairs(oracle_mod, rb, sc, c, 60000, 11)
+    qh, th = oracle_pairs(oracle_mod, rb, sc, c, 4000, 12)
+    ctx = make_ctx(rb, sc, c)
+    ctx.mlp_init(3)
+    p0 = ctx.mlp_get_params()
+    dq, dt = torch_cuda.from_numpy(q).cuda(), torch_cuda.from_numpy(t).cuda()
+    losses = ctx.mlp_train(dq, dt, batch=512, epochs=30, lr=1e-3, seed=5)
+    return dict(ctx=ctx, p0=p0, losses=losses, held=(qh, th), n_train=len(q))
+
+
+def test_training_reduces_loss(oracle_mod, trained):
+    ctx, losses = trained["ctx"], trained["losses"]
+    assert np.all(np.isfinite(losses))
+    # uniform configurations -> projections is a hard, partly discontinuous map (the
+    # projection can land on either side of a branch): the loss falls by about half
+    assert losses[-1] < 0.7 * losses[0], losses
+    # held-out loss of the trained parameters, evaluated by the oracle in FP64
+    qh, th = trained["held"]
+    l0, _ = oracle_mod.mlp_loss_grad(trained["p0"], qh, th, DOF, H, n_threads=8, grad=False)
+    l1, _ = oracle_mod.mlp_loss_grad(ctx.mlp_get_params(), qh, th, DOF, H, n_threads=8,
+                                     grad=False)
+    zero = 0.5 * np.mean(np.sum((th.astype(np.float64) - qh) ** 2, axis=1))
+    assert l1 < 0.7 * zero and l1 < 0.7 * l0, (l0, l1, zero)
+
+
+def first_colliding(orc, seg):
+    """(first colliding waypoint or -1, deciding clearance) of a segment, FP64."""
+    cl = np.array([orc.config_clearance(x) for x in seg])
+    hit = np.nonzero(cl < 0)[0]
+    if len(hit):
+        return int(hit[0]), float(min(abs(cl[hit[0]]), np.abs(cl[: hit[0]]).min()
+                                      if hit[0] else np.inf))
+    return -1, float(np.abs(cl).min())
+
+
+def test_validate_ws_judged_by_plain_projection(torch_cuda, oracle_mod, setup, trained):
+    """Warm-started segments satisfy Alg. 1's acceptance tests (oracle re-check) and their
+    collision verdicts match the oracle; fallen-back motions are the plain method's
+    results; and the network pays: fewer iterations, no lost successes."""
+    torch = torch_cuda
+    rb, sc, c = setup
+    ctx = trained["ctx"]
+    orc = oracle_mod.Oracle(rb, sc, c)
+    n, W = 256, 32
+    q0 = np.stack([orc.project_config(q, 60)[1]
+                   for q in S.uniform_configs(rb, 3 * n, 71)
+                   if orc.project_config(q, 60)[0]][:n])
+    q0 = S.f32(q0).astype(np.float32)
+    q1 = S.uniform_configs(rb, n, 72).astype(np.float32)
+    # planner-like short motions too: q1 near q0 on the manifold side
+    rng = np.random.default_rng(73)
+    q1[n // 2:] = np.clip(q0[n // 2:] + rng.uniform(-0.3, 0.3, (n - n // 2, DOF)),
+                          rb.lo, rb.hi).astype(np.float32)
+    d0, d1 = torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()
+    plain = {k: parity.to_np(v) for k, v in ctx.validate(d0, d1, W).items()}
+    ws = {k: parity.to_np(v) for k, v in ctx.validate_ws(d0, d1, W, refine_iters=5).items()}
+    used = ws["warm"].astype(bool)
+    fb = ~used
+    # fallback: the plain method's answer, plus the refine iterations spent first
+    np.testing.assert_array_equal(ws["status"][fb], plain["status"][fb])
+    np.testing.assert_array_equal(ws["first_fail"][fb], plain["first_fail"][fb])
+    np.testing.assert_array_equal(ws["q"][fb], plain["q"][fb])
+    extra = ws["iters"][fb].astype(int) - plain["iters"][fb].astype(int)
+    assert set(np.unique(extra)) <= {0, 5}, np.unique(extra)
+    # warm-started and accepted: judge with the oracle
+    checked = 0
+    for m in np.nonzero(used)[0]:
+        assert ws["status"][m] != 1 and ws["iters"][m] <= 5
+        seg = ws["q"][m].astype(np.float64)
+        assert np.array_equal(seg[0], q0[m].astype(np.float64))
+        tau = oracle_mod.tau_step(c, q0[m], q1[m], W)
+        max_task, step_excess, _ = orc.check_segment(seg, tau)
+        assert max_task < c.tol_task + parity.DELTA, (m, max_task)
+        assert step_excess < c.tol_sm + parity.DELTA, (m, step_excess)
+        ff, margin = first_colliding(orc, seg)
+        if margin > parity.CONTACT_MARGIN:
+            assert ff == ws["first_fail"][m], (m, ff, ws["first_fail"][m], margin)
+            assert (ws["status"][m] == 2) == (ff >= 0)
+            checked += 1
+    assert used.sum() >= n // 10, used.sum()
+    assert checked >= 0.9 * used.sum()
+    # gain: no motion the plain method projects is lost, and iterations drop
+    plain_ok = plain["status"] != 1
+    ws_ok = ws["status"] != 1
+    assert np.all(ws_ok[plain_ok])
+    assert ws_ok.sum() >= plain_ok.sum()
+    it_plain = plain["iters"].astype(float)[plain_ok].mean()
+    it_ws = ws["iters"].astype(float)[plain_ok].mean()
+    print(f"warm used {used.mean():.2f}; projected plain {plain_ok.sum()} warm {ws_ok.sum()}; "
+          f"mean iters (plain-projected motions) plain {it_plain:.2f} warm {it_ws:.2f}")
+    assert ws_ok.sum() > plain_ok.sum() or it_ws < it_plain
