@@ -691,6 +691,181 @@ def run_validate(args, world, rank, local):
     return line, (rb, sc, c, n, W, q0.cpu().numpy(), q1.cpu().numpy())
 
 
+# ---- config 4: learned warm start -------------------------------------------------------
+
+WS_MOTIONS = 16384
+WS_W = 32
+WS_TRAIN = 1 << 20
+WS_EPOCHS = 10
+WS_REFINE = 5
+
+
+def mlp_flops_per_row(dof: int, hidden: int = 256) -> int:
+    """Multiply-adds of the warm-start network per row, x 2."""
+    return 2 * (dof * hidden + 2 * hidden * hidden + hidden * dof)
+
+
+def config4_workload(seed=4):
+    """7-DOF arm (59 spheres), roll/pitch constraint, one config-2 scene (100 spheres, 60
+    boxes, 40 capsules)."""
+    rb = S.make_arm7(1)
+    c = S.roll_pitch(20)
+    sc = S.make_planning_scene(4_000_000 + seed)
+    return rb, sc, c
+
+
+def run_warmstart(args, world, rank, local):
+    """Plain Alg. 1 validation against the learned warm start on the same motions: the
+    network is trained first (untimed) on 2^20 (uniform configuration -> its projection)
+    pairs, the projection done by the library's cprrtc_project_configs."""
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    rb, sc, c = config4_workload()
+    n, W = WS_MOTIONS, WS_W
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_obstacles(sc)
+    ctx.set_constraint(c)
+    seed = 40 + 1000 * rank
+    with torch.cuda.stream(stream):
+        # training pairs
+        t0 = time.perf_counter()
+        qs, ts, k = [], [], 0
+        while sum(len(x) for x in qs) < WS_TRAIN + 16384:
+            q = torch.from_numpy(S.uniform_configs(rb, 1 << 19, seed * 7919 + k)
+                                 .astype(np.float32)).to(dev)
+            r = ctx.project_configs(q, 60)
+            ok = r["ok"].bool()
+            qs.append(q[ok])
+            ts.append(r["q"][ok])
+            k += 1
+        q_all, t_all = torch.cat(qs), torch.cat(ts)
+        q_tr, t_tr = q_all[:WS_TRAIN].contiguous(), t_all[:WS_TRAIN].contiguous()
+        q_ho, t_ho = q_all[WS_TRAIN:WS_TRAIN + 16384].contiguous(), t_all[WS_TRAIN:WS_TRAIN + 16384].contiguous()
+        stream.synchronize()
+        pairs_s = time.perf_counter() - t0
+        ctx.mlp_init(seed)
+        held0, _ = ctx.mlp_grad(q_ho, t_ho)
+        t0 = time.perf_counter()
+        losses = ctx.mlp_train(q_tr, t_tr, batch=1024, epochs=WS_EPOCHS, lr=1e-3, seed=seed)
+        train_s = time.perf_counter() - t0
+        held1, _ = ctx.mlp_grad(q_ho, t_ho)
+        zero_loss = float(0.5 * ((t_ho - q_ho) ** 2).sum(1).mean())
+
+        q0 = manifold_starts_gpu(ctx, rb, n, 50_000 + 97 * rank)
+        q1 = torch.from_numpy(S.uniform_configs(rb, n, 60_000 + 97 * rank).astype(np.float32)).to(dev)
+        out_p = ctx.alloc_validate_outputs(n, W, q0)
+        out_w = ctx.alloc_validate_outputs(n, W, q0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            ctx.validate(q0, q1, W, out=out_p)
+            ctx.validate_ws(q0, q1, W, WS_REFINE, out=out_w)
+        stream.synchronize()
+
+        def timed(fn):
+            ctx.set_timing(True)
+            ctx.reset_timing()
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k_ in range(args.steps):
+                flush.fill_(float(k_))        # evict L2 between steps (write > L2 size)
+                starts[k_].record(stream)
+                fn()
+                ends[k_].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)), world)
+            kt = {name: ctx.kernel_time(name) for name in ("validate", "mlp_infer")}
+            ctx.set_timing(False)
+            return ms, kt
+
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms_plain, kt_plain = timed(lambda: ctx.validate(q0, q1, W, out=out_p))
+        ms_ws, kt_ws = timed(lambda: ctx.validate_ws(q0, q1, W, WS_REFINE, out=out_w))
+        clk = clocks.stop()
+
+    P = {k: v.cpu().numpy() for k, v in out_p.items()}
+    Wr = {k: v.cpu().numpy() for k, v in out_w.items()}
+    used = Wr["warm"].astype(bool)
+    extra = Wr["iters"].astype(int) - P["iters"].astype(int)
+    tried = used | ((~used) & (extra == WS_REFINE))
+    p_ok, w_ok = P["status"] != 1, Wr["status"] != 1
+    wps = n * W * args.steps * world
+    value_ws, value_plain = wps / (ms_ws / 1e3), wps / (ms_plain / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    h_q0, h_q1 = q0.cpu().pin_memory(), q1.cpu().pin_memory()
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out_w.items()}
+    ctx.validate_ws(h_q0, h_q1, W, WS_REFINE, out=h_out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.validate_ws(h_q0, h_q1, W, WS_REFINE, out=h_out)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": n * W * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * rb.dof * 4,
+           "d2h_bytes_per_step": sum(v.numel() * v.element_size() for v in h_out.values())}
+
+    peaks = load_peaks()
+    infer_ms, infer_launches = kt_ws["mlp_infer"]
+    infer_avg_s = infer_ms / 1e3 / max(infer_launches, 1)
+    flops_infer = mlp_flops_per_row(rb.dof) * n * W
+    tensor_peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = flops_infer / infer_avg_s / 1e12
+    vk_ms, vk_launches = kt_ws["validate"]
+    line = {
+        "metric": METRIC, "value": value_ws, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_ws / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 projection",
+        "data": "synthetic",
+        "config": {"workload": "config 4: learned warm start vs plain projection",
+                   "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
+                   "obstacles": {"spheres": len(sc.sph), "boxes": len(sc.box),
+                                 "capsules": len(sc.cap)},
+                   "constraint": "roll-pitch", "refine_iters": WS_REFINE,
+                   "max_iters": c.max_iters, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps,
+                  "projected": int(p_ok.sum()), "success_rate": float(p_ok.mean()),
+                  "valid": int((P["status"] == 0).sum()),
+                  "mean_iters": float(P["iters"].astype(float).mean())},
+        "warm_start": {"value": value_ws, "ms_per_step": ms_ws / args.steps,
+                       "projected": int(w_ok.sum()), "success_rate": float(w_ok.mean()),
+                       "valid": int((Wr["status"] == 0).sum()),
+                       "mean_iters": float(Wr["iters"].astype(float).mean()),
+                       "mean_iters_on_plain_projected": float(Wr["iters"][p_ok].astype(float).mean())
+                       if p_ok.any() else None,
+                       "plain_mean_iters_on_plain_projected": float(P["iters"][p_ok].astype(float).mean())
+                       if p_ok.any() else None,
+                       "warm_used": float(used.mean()), "tried": float(tried.mean()),
+                       "fallback_rate": float((tried & ~used).sum() / max(tried.sum(), 1)),
+                       "lost": int((p_ok & ~w_ok).sum()),
+                       "infer_ms_per_step": infer_avg_s * 1e3,
+                       "validate_ms_per_step": vk_ms / max(vk_launches, 1)},
+        "training": {"pairs": int(q_tr.shape[0]), "pair_generation_s": pairs_s,
+                     "epochs": WS_EPOCHS, "batch": 1024, "lr": 1e-3, "train_s": train_s,
+                     "samples_per_s": WS_EPOCHS * q_tr.shape[0] / train_s,
+                     "loss_first_last_epoch": [float(losses[0]), float(losses[-1])],
+                     "heldout_loss_init_trained": [held0, held1],
+                     "heldout_zero_prediction_loss": zero_loss,
+                     "pairs_source": "uniform configurations projected by cprrtc_project_configs"},
+        "e2e": e2e,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
+                     "frac": achieved / tensor_peak, "traffic": None, "kernel": "mlp_fused_kernel",
+                     "flop_per_launch": flops_infer, "avg_launch_ms": infer_avg_s * 1e3,
+                     "peak_note": "measured dense BF16 (MEASURED_PEAKS.json bf16_tflops, burst)"},
+        "gpu_launches": int(kt_ws["validate"][1] + kt_ws["mlp_infer"][1]),
+        "clocks": clk,
+    }
+    return line, (rb, sc, c, min(n, 2048), W, q0[:2048].cpu().numpy(), q1[:2048].cpu().numpy())
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -808,7 +983,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="plan", choices=["plan", "validate", "batch"])
+    ap.add_argument("--workload", default="plan",
+                    choices=["plan", "validate", "batch", "warmstart"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
@@ -831,6 +1007,9 @@ def main():
             args.problems = BATCH_N
         line, inputs = run_batch(args, world, rank, local)
         baseline = None
+    elif args.workload == "warmstart":
+        line, inputs = run_warmstart(args, world, rank, local)
+        baseline = cpu_baseline_validate
     else:
         line, inputs = run_validate(args, world, rank, local)
         baseline = cpu_baseline_validate

@@ -183,7 +183,8 @@ int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_it
  * Network (one per context, for the dof of the robot set when it is created):
  *   x = q / pi; h1 = gelu(W1 x + b1); h2 = gelu(W2 h1 + b2); h3 = gelu(W3 h2 + b3);
  *   correction = W4 h3 + b4, widths dof -> 256 -> 256 -> 256 -> dof,
- *   gelu(z) = z Phi(z) with Phi the standard normal CDF (the exact form, through erf).
+ *   gelu(z) = z Phi(z) with Phi the standard normal CDF (the erf form; on the GPU erf is
+ *   evaluated with Abramowitz and Stegun 7.1.28, |error| <= 3e-7, below BF16 resolution).
  * Weights and activations are BF16 and products accumulate in FP32 on the tensor cores;
  * biases, the FP32 master weights and the Adam state stay FP32.
  * Parameter layout (compact, FP32, cprrtc_mlp_param_count(dof) entries): for l = 1..4,

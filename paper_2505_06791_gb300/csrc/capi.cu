@@ -870,7 +870,7 @@ int cprrtc_mlp_infer(cprrtc_ctx* ctx, const float* q, int rows, float* q_out) {
     e = cudaGetLastError();
   }
   tm.done();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_infer");
+  if (e != cudaSuccess) return cuda_fail(ctx, e, (std::string("mlp_infer ") + mlp_fused_diag()).c_str());
   rc = st.end(ctx);
   if (rc == CPRRTC_OK && st.any_host) {
     int flag = 0;

@@ -148,6 +148,7 @@ size_t mlp_fused_smem_bytes();
 cudaError_t launch_mlp_pack(const void* w0, const void* w1, const void* w2, const void* w3,
                             uint8_t* image, cudaStream_t s);
 cudaError_t launch_mlp_fused(const FusedMlpArgs& a, int sm_count, cudaStream_t s);
+const char* mlp_fused_diag();  // why the last fused launch was refused, if it was
 const int* mlp_error_flag(const MlpDev* d);
 cudaError_t launch_residual_target(const float* q, const float* t, int rows, int dof, float* T,
                                    cudaStream_t s);
