@@ -691,6 +691,122 @@ def run_validate(args, world, rank, local):
     return line, (rb, sc, c, n, W, q0.cpu().numpy(), q1.cpu().numpy())
 
 
+# ---- config 3: collision checking in GEMM form ---------------------------------------------
+
+CC_N, CC_W = 4096, 64
+
+
+def config3_workload(seed=3):
+    """8-DOF arm (7-DOF arm on a 0..0.4 m prismatic torso, 120 spheres), 4096 obstacle
+    spheres of radius 0.02 m on the surfaces of 12 random boxes, end effector on z = 0.9 m."""
+    return S.make_arm8(1), S.make_box_surface_cloud(seed), S.z_plane(0.9)
+
+
+def run_gemmcc(args, world, rank, local):
+    """Validation of 4096 motions x 64 waypoints with the exact collision check and with the
+    GEMM form (TF32 and BF16 contraction + exact recheck); outputs compared across modes."""
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    rb, sc, c = config3_workload()
+    n, W = CC_N, CC_W
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_obstacles(sc)
+    ctx.set_constraint(c)
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    modes = {}
+    with torch.cuda.stream(stream):
+        q0 = manifold_starts_gpu(ctx, rb, n, 70_000 + 97 * rank)
+        q1 = torch.from_numpy(S.uniform_configs(rb, n, 80_000 + 97 * rank).astype(np.float32)).to(dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        for name, mode in (("exact", 0), ("gemm_tf32", 1), ("gemm_bf16", 2)):
+            ctx.set_cc_mode(mode, 0.005)
+            out = ctx.alloc_validate_outputs(n, W, q0)
+            for _ in range(args.warmup):
+                ctx.validate(q0, q1, W, out=out)
+            stream.synchronize()
+            ctx.cc_stats(reset=True)
+            ctx.set_timing(True)
+            ctx.reset_timing()
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))            # evict L2 between steps (write > L2 size)
+                starts[k].record(stream)
+                ctx.validate(q0, q1, W, out=out)
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)), world)
+            kv = ctx.kernel_time("validate")
+            kg = ctx.kernel_time("gemm_cc")
+            ctx.set_timing(False)
+            bound, rechecks = ctx.cc_stats(reset=True)
+            modes[name] = dict(ms=ms, kv=kv, kg=kg, bound=bound, rechecks=rechecks / max(args.steps, 1),
+                               out={k: v.cpu().numpy() for k, v in out.items()})
+        clk = clocks.stop()
+        ctx.set_cc_mode(0)
+    ex = modes["exact"]["out"]
+    st, ff = ex["status"], ex["first_fail"]
+    # waypoint tiles the GEMM form evaluates: every waypoint of a collision-free projected
+    # motion, and up to the first colliding waypoint + 1 of a colliding one
+    tiles = int(np.where(st == 0, W, np.where(st == 2, np.minimum(ff + 2, W), 0)).sum())
+    n_tiles = (len(sc.sph) + 255) // 256
+    tensor_flop = tiles * 128 * n_tiles * 256 * 2 * 16
+    wps = n * W * args.steps * world
+    summary = {}
+    for name, m in modes.items():
+        o = m["out"]
+        same = bool(np.array_equal(o["status"], st) and np.array_equal(o["first_fail"], ff)
+                    and np.array_equal(o["q"], ex["q"]))
+        entry = {"value": wps / (m["ms"] / 1e3), "ms_per_step": m["ms"] / args.steps,
+                 "validate_kernel_ms": m["kv"][0] / max(m["kv"][1], 1), "identical_to_exact": same}
+        if name != "exact":
+            g_ms = m["kg"][0] / max(m["kg"][1], 1)
+            peak = bf16_peak if name == "gemm_bf16" else bf16_peak / 2.0
+            entry.update({"gemm_cc_kernel_ms": g_ms, "error_bound_m2": m["bound"],
+                          "exact_rechecks_per_step": m["rechecks"],
+                          "tensor_tflops": tensor_flop / (g_ms / 1e3) / 1e12,
+                          "tensor_peak_tflops": peak,
+                          "peak_note": "BF16 measured (MEASURED_PEAKS.json bf16_tflops); TF32 = "
+                                       "BF16 x 0.5 (nominal dense ratio)" if name == "gemm_tf32"
+                                       else "BF16 measured (MEASURED_PEAKS.json bf16_tflops)"})
+        summary[name] = entry
+    best = max(("gemm_tf32", "gemm_bf16"), key=lambda k: summary[k]["value"])
+    b = summary[best]
+    line = {
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": f"{best[5:]} contraction, f32 recheck",
+        "data": "synthetic",
+        "config": {"workload": "config 3: obstacle-rich scene, collision check in GEMM form",
+                   "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
+                   "obstacles": {"spheres": len(sc.sph), "radius": 0.02},
+                   "constraint": "z-plane 0.9 m", "guard_m": 0.005,
+                   "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas x{world}"},
+        "modes": summary,
+        "outcomes": {"valid": int((st == 0).sum()), "proj_fail": int((st == 1).sum()),
+                     "collision": int((st == 2).sum()), "gemm_waypoint_tiles": tiles},
+        "roofline": {"bound": "tensor", "achieved": b["tensor_tflops"], "peak": b["tensor_peak_tflops"],
+                     "unit": "TFLOP/s", "frac": b["tensor_tflops"] / b["tensor_peak_tflops"],
+                     "traffic": None, "kernel": "gemm_cc_kernel",
+                     "flop_per_launch": tensor_flop, "avg_launch_ms": b["gemm_cc_kernel_ms"]},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    return line, (rb, sc, c, 64, W, q0[:64].cpu().numpy(), q1[:64].cpu().numpy())
+
+
 # ---- config 4: learned warm start -------------------------------------------------------
 
 WS_MOTIONS = 16384
@@ -984,7 +1100,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="plan",
-                    choices=["plan", "validate", "batch", "warmstart"])
+                    choices=["plan", "validate", "batch", "warmstart", "gemmcc"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
@@ -1007,6 +1123,9 @@ def main():
             args.problems = BATCH_N
         line, inputs = run_batch(args, world, rank, local)
         baseline = None
+    elif args.workload == "gemmcc":
+        line, inputs = run_gemmcc(args, world, rank, local)
+        baseline = cpu_baseline_validate
     elif args.workload == "warmstart":
         line, inputs = run_warmstart(args, world, rank, local)
         baseline = cpu_baseline_validate

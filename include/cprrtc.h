@@ -173,6 +173,30 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
 int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,
                            float* q_out, uint8_t* ok, float* resid);
 
+/* ---- collision checking in GEMM form ---- */
+
+#define CPRRTC_CC_EXACT 0     /* per-pair FP32 tests with culling (default) */
+#define CPRRTC_CC_GEMM_TF32 1 /* dense distance contraction on the tensor cores, TF32 */
+#define CPRRTC_CC_GEMM_BF16 2 /* the same in BF16 */
+
+/* Selects how cprrtc_validate checks collisions (Sec. IV's check, computed differently; the
+ * paper has no GEMM form). In the GEMM modes the squared distances of all robot-sphere x
+ * obstacle pairs of a waypoint, less the squared contact distance inflated by `guard_m`
+ * (metres, in [0, 0.1]; 0.005 is a 5 mm band), are one dense contraction of hi/lo-split
+ * operands with FP32 accumulation; the library bounds its error (cprrtc_cc_stats), and every
+ * pair it cannot clear is rechecked with the exact FP32 test. The outputs (status,
+ * first_fail, waypoints) are identical to CPRRTC_CC_EXACT's. GEMM modes take sphere
+ * obstacles only and at most 128 robot spheres (else cprrtc_validate returns
+ * E_UNSUPPORTED); they apply to cprrtc_validate (not to the planner or the warm-start call).
+ * Requires set_robot for the GEMM modes. Errors: E_INVALID_ARG, E_NOT_CONFIGURED, E_CUDA,
+ * E_OOM. */
+int cprrtc_set_cc_mode(cprrtc_ctx* ctx, int mode, double guard_m);
+
+/* The GEMM-form check's error bound E (m^2; 0 in EXACT mode) and its counters since the
+ * last reset: counters[0] = pairs rechecked exactly, counters[1] = reserved (0). Synchronises
+ * the context's stream; reset = 1 zeroes the counters. */
+int cprrtc_cc_stats(cprrtc_ctx* ctx, double* bound_m2, int64_t* counters, int reset);
+
 /* ---- learned projection warm start ---- */
 
 /* A multilayer perceptron that predicts, for a configuration q, the correction
@@ -407,8 +431,8 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
 
 /* When enabled, the library records CUDA events around each launch of its kernels on the
  * context's stream. cprrtc_kernel_time returns the summed device time (ms) and the launch
- * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer") since the
- * last reset,
+ * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer", "gemm_cc")
+ * since the last reset,
  * synchronising on the events. */
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
 

@@ -109,6 +109,8 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_batch_replay": [C.c_void_p],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
+    "cprrtc_set_cc_mode": [C.c_void_p, C.c_int, C.c_double],
+    "cprrtc_cc_stats": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_int],
     "cprrtc_mlp_param_count": [C.c_int],
     "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
@@ -329,6 +331,19 @@ class Context:
                                        out["first_fail"], out["iters"], out["resid"],
                                        out["warm"]))
         return out
+
+    # -- collision checking in GEMM form --
+    CC_EXACT, CC_GEMM_TF32, CC_GEMM_BF16 = 0, 1, 2
+
+    def set_cc_mode(self, mode: int, guard: float = 0.005):
+        self._check(self._L.cprrtc_set_cc_mode(self.h, int(mode), float(guard)))
+
+    def cc_stats(self, reset: bool = False):
+        """(error bound E in m^2, pairs rechecked exactly) of the GEMM-form check."""
+        b = C.c_double()
+        cnt = np.zeros(2, np.int64)
+        self._check(self._L.cprrtc_cc_stats(self.h, C.byref(b), cnt.ctypes.data, int(reset)))
+        return b.value, int(cnt[0])
 
     # -- learned warm start --
     def mlp_param_count(self, dof=None) -> int:

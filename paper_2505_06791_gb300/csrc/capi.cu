@@ -76,6 +76,22 @@ struct cprrtc_ctx {
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kBatchClasses] = {};
   cudaGraphExec_t graph_exec = nullptr;
+  // collision checking in GEMM form
+  int cc_mode = CPRRTC_CC_EXACT;
+  double cc_guard = 0.005;
+  std::vector<float4> host_sph;  // sphere obstacles as staged (FP32), image row order
+  std::vector<float4> host_robot_sph;  // robot spheres {x, y, z, r} in their frames
+  uint8_t* d_bimage = nullptr;
+  size_t bimage_cap = 0;
+  int cc_tiles = 0;
+  float4 cc_origin{};
+  double cc_bound = 0.0;
+  unsigned long long* d_cc_counters = nullptr;  // [2]
+  int* d_cc_error = nullptr;
+  float* d_cc_q = nullptr;  // projected waypoints when the caller does not ask for them
+  size_t cc_q_cap = 0;
+  int32_t* d_cc_ff = nullptr;
+  size_t cc_ff_cap = 0;
   // learned warm start
   MlpDev* mlp = nullptr;
   float* d_warm = nullptr;  // corrections [n*W][16]
@@ -443,6 +459,11 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_tab_frm);
   mlp_destroy(ctx->mlp);
   cudaFree(ctx->d_warm);
+  cudaFree(ctx->d_bimage);
+  cudaFree(ctx->d_cc_counters);
+  cudaFree(ctx->d_cc_error);
+  cudaFree(ctx->d_cc_q);
+  cudaFree(ctx->d_cc_ff);
   for (BatchRes* r : {&ctx->batch_res, &ctx->graph_res}) {
     cudaFree(r->d_probs);
     cudaFree(r->d_order);
@@ -568,6 +589,8 @@ int build_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof, const cprr
 
 extern "C" {
 
+static int build_cc_image(cprrtc_ctx* ctx);
+
 int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
                      const cprrtc_sphere* spheres, int n_spheres, const double ee[3]) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
@@ -588,6 +611,175 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
   rb.sphere_frame = ctx->d_sframe;
   ctx->rb = rb;
   ctx->has_robot = true;
+  ctx->host_robot_sph = loc;
+  if (ctx->cc_mode != CPRRTC_CC_EXACT) return build_cc_image(ctx);  // the bound depends on the robot
+  return CPRRTC_OK;
+}
+
+// ---- collision checking in GEMM form: the obstacle operand and its error bound ----
+
+namespace {
+
+// Round-to-nearest-even of an FP32 value to `bits` significant bits (BF16 8, TF32 11).
+float round_bits(float x, int bits) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  const int drop = 24 - bits;
+  const uint32_t half = (1u << (drop - 1)) - 1u + ((u >> drop) & 1u);
+  u = (u + half) & ~((1u << drop) - 1u);
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+// Byte offset of byte `kb` (< 128) of row r in the 128-byte-swizzle layout.
+size_t sw128_host(int r, int kb) {
+  return (size_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((kb >> 4) & 7) ^ (r & 7)) << 4) + (kb & 15));
+}
+
+}  // namespace
+
+// Builds the obstacle operand B' of the GEMM-form check for the current mode (layout and
+// columns as described in gemm_cc.cu) and the bound E on the contraction's error.
+static int build_cc_image(cprrtc_ctx* ctx) {
+  const bool tf32 = ctx->cc_mode == CPRRTC_CC_GEMM_TF32;
+  const int bits = tf32 ? 11 : 8, elem = tf32 ? 4 : 2, slice = 16 * elem, tpr = 128 / slice;
+  const int n = (int)ctx->host_sph.size();
+  const int tiles = std::max(1, (n + 255) / 256);
+  const int chunks = (tiles + tpr - 1) / tpr;
+  // origin: centre of the obstacles' bounding box
+  double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
+  double rho_max = 0.0;
+  for (const float4& o : ctx->host_sph) {
+    const double c[3] = {o.x, o.y, o.z};
+    for (int k = 0; k < 3; ++k) lo[k] = std::min(lo[k], c[k]), hi[k] = std::max(hi[k], c[k]);
+    rho_max = std::max(rho_max, (double)o.w);
+  }
+  float4 ori = make_float4(0.f, 0.f, 0.f, (float)(0.5 * ctx->cc_guard));
+  if (n > 0) ori = make_float4((float)(0.5 * (lo[0] + hi[0])), (float)(0.5 * (lo[1] + hi[1])),
+                               (float)(0.5 * (lo[2] + hi[2])), (float)(0.5 * ctx->cc_guard));
+  const double g2 = ori.w;
+  std::vector<uint8_t> img((size_t)chunks * 32768, 0);
+  auto put = [&](int j, int col, double v) {
+    const int t = j / 256, r = j % 256;
+    const size_t off = (size_t)(t / tpr) * 32768 + sw128_host(r, (t % tpr) * slice + col * elem);
+    const float f = round_bits((float)v, bits);
+    if (tf32) {
+      memcpy(&img[off], &f, 4);
+    } else {
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      const uint16_t h = (uint16_t)(u >> 16);  // exact: f has 8 significant bits
+      memcpy(&img[off], &h, 2);
+    }
+  };
+  auto split = [&](double v, double& h, double& l) {
+    h = round_bits((float)v, bits);
+    l = (double)round_bits((float)(v - h), bits);
+  };
+  double lb = 0.0;
+  for (int j = 0; j < tiles * 256; ++j) {
+    if (j >= n) {  // padding obstacle: s = 1e4
+      put(j, 12, 1e4);
+      continue;
+    }
+    const float4 o = ctx->host_sph[j];
+    const double b[3] = {(double)o.x - ori.x, (double)o.y - ori.y, (double)o.z - ori.z};
+    const double rp = (double)o.w + g2;
+    double h, l;
+    for (int k = 0; k < 3; ++k) {
+      split(b[k], h, l);
+      put(j, 3 * k, h);
+      put(j, 3 * k + 1, l);
+      put(j, 3 * k + 2, h);
+    }
+    put(j, 9, 1.0);
+    put(j, 10, 1.0);
+    put(j, 11, rp);
+    const double beta = b[0] * b[0] + b[1] * b[1] + b[2] * b[2] - rp * rp;
+    split(beta, h, l);
+    put(j, 12, h);
+    put(j, 13, l);
+    lb = std::max(lb, std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]));
+  }
+  // reach of the robot spheres from the origin: |base - origin| + sum of link lengths,
+  // offsets and prismatic travel + largest sphere offset in its frame
+  double reach = std::sqrt((double)ori.x * ori.x + (double)ori.y * ori.y + (double)ori.z * ori.z);
+  for (int k = 0; k < ctx->rb.dof; ++k) {
+    const JointDev& J = ctx->rb.j[k];
+    reach += std::fabs(J.a) + std::fabs(J.d) +
+             (J.prismatic ? std::max(std::fabs(J.lo), std::fabs(J.hi)) : 0.0);
+  }
+  double off_max = 0.0, r_max = 0.0;
+  for (const float4& sp : ctx->host_robot_sph) {
+    off_max = std::max(off_max, std::sqrt((double)sp.x * sp.x + (double)sp.y * sp.y + (double)sp.z * sp.z));
+    r_max = std::max(r_max, (double)sp.w);
+  }
+  const double la = reach + off_max, u = std::ldexp(1.0, -bits);
+  const double rpm = r_max + g2, rhom = rho_max + g2;
+  const double cross = 2.0 * la * lb, amax = la * la + rpm * rpm, bmax = lb * lb + rhom * rhom, rr = 2.0 * rpm * rhom;
+  // dropped lo*lo terms and the rounding of every split part (lo parts of TF32 operands may
+  // be truncated by the hardware), -2r' and rho' rounded once each, alpha evaluated in FP32,
+  // and the FP32 accumulation of 16 products (allowing 8x the textbook summation bound)
+  const double e_split = 5.0 * u * u * cross + 2.0 * u * u * (amax + bmax) + 2.01 * u * rr;
+  const double e_fp32 = std::ldexp(1.0, -21) * amax;
+  const double e_acc = 16.0 * std::ldexp(1.0, -21) * (3.0 * cross + amax + bmax + rr);
+  ctx->cc_bound = 1.5 * (e_split + e_fp32 + e_acc);
+  ctx->cc_origin = ori;
+  ctx->cc_tiles = tiles;
+  DeviceGuard gd(ctx->device);
+  if (img.size() > ctx->bimage_cap) {
+    cudaFree(ctx->d_bimage);
+    ctx->d_bimage = nullptr;
+    ctx->bimage_cap = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_bimage, img.size());
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "GEMM-form obstacle image");
+    ctx->bimage_cap = img.size();
+  }
+  cudaError_t e = cudaMemcpy(ctx->d_bimage, img.data(), img.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "GEMM-form obstacle image upload");
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_cc_mode(cprrtc_ctx* ctx, int mode, double guard_m) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (mode != CPRRTC_CC_EXACT && mode != CPRRTC_CC_GEMM_TF32 && mode != CPRRTC_CC_GEMM_BF16)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_cc_mode: unknown mode");
+  if (!(guard_m >= 0.0) || !(guard_m <= 0.1))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_cc_mode: guard must be in [0, 0.1] m");
+  if (mode != CPRRTC_CC_EXACT && !ctx->has_robot)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "set_cc_mode: set_robot first");
+  ctx->cc_mode = mode;
+  ctx->cc_guard = guard_m;
+  if (mode == CPRRTC_CC_EXACT) return CPRRTC_OK;
+  DeviceGuard g(ctx->device);
+  if (!ctx->d_cc_counters) {
+    cudaError_t e = cudaMalloc(&ctx->d_cc_counters, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_cc_counters, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cc_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_cc_error, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_cc_mode");
+  }
+  return build_cc_image(ctx);
+}
+
+int cprrtc_cc_stats(cprrtc_ctx* ctx, double* bound_m2, int64_t* counters, int reset) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (bound_m2) *bound_m2 = ctx->cc_mode == CPRRTC_CC_EXACT ? 0.0 : ctx->cc_bound;
+  if (!ctx->d_cc_counters) {
+    if (counters) counters[0] = counters[1] = 0;
+    return CPRRTC_OK;
+  }
+  DeviceGuard g(ctx->device);
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_cc_counters, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(ctx->d_cc_counters, 0, sizeof(h));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cc_stats");
+  if (counters) {
+    counters[0] = (int64_t)h[0];
+    counters[1] = (int64_t)h[1];
+  }
   return CPRRTC_OK;
 }
 
@@ -606,6 +798,8 @@ int cprrtc_set_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sp
   rc = upload(ctx, &ctx->d_obs, &ctx->obs_cap, v);
   if (rc) return rc;
   ctx->sc = SceneDev{ctx->d_obs, n_sph, n_box, n_cap};
+  ctx->host_sph.assign(v.begin(), v.begin() + n_sph);
+  if (ctx->cc_mode != CPRRTC_CC_EXACT) return build_cc_image(ctx);
   return CPRRTC_OK;
 }
 
@@ -694,11 +888,72 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
   st.output(resid, N * sizeof(float), &a.resid);
   int rc = st.begin(ctx);
   if (rc) return rc;
+  const bool gemm = ctx->cc_mode != CPRRTC_CC_EXACT;
+  if (gemm) {
+    // projection only here; the GEMM-form check needs the projected waypoints and a
+    // first-failure array even when the caller does not ask for them
+    if (ctx->sc.n_box || ctx->sc.n_cap)
+      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes sphere obstacles only");
+    if (ctx->rb.n_spheres > 128)
+      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes at most 128 robot spheres");
+    a.skip_cc = 1;
+    if (!a.out_q) {
+      const size_t need = N * W * dof * sizeof(float);
+      if (need > ctx->cc_q_cap) {
+        cudaFree(ctx->d_cc_q);
+        ctx->d_cc_q = nullptr;
+        ctx->cc_q_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_cc_q, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form waypoint buffer");
+        ctx->cc_q_cap = need;
+      }
+      a.out_q = ctx->d_cc_q;
+    }
+    if (!a.first_fail) {
+      const size_t need = N * sizeof(int32_t);
+      if (need > ctx->cc_ff_cap) {
+        cudaFree(ctx->d_cc_ff);
+        ctx->d_cc_ff = nullptr;
+        ctx->cc_ff_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_cc_ff, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form buffer");
+        ctx->cc_ff_cap = need;
+      }
+      a.first_fail = ctx->d_cc_ff;
+    }
+  }
   LaunchTimer tm(ctx, "validate");
   cudaError_t e = launch_validate(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
   tm.done();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "validate launch");
-  return st.end(ctx);
+  if (gemm) {
+    GemmCcArgs g{};
+    g.q = a.out_q;
+    g.n = n;
+    g.W = W;
+    g.status = a.status;
+    g.first_fail = a.first_fail;
+    g.bimage = ctx->d_bimage;
+    g.n_tiles = ctx->cc_tiles;
+    g.obs = ctx->sc.obs;
+    g.n_obs = ctx->sc.n_sph;
+    g.origin = ctx->cc_origin;
+    g.bound = (float)ctx->cc_bound;
+    g.counters = ctx->d_cc_counters;
+    g.error = ctx->d_cc_error;
+    LaunchTimer tg(ctx, "gemm_cc");
+    e = launch_gemm_cc(ctx->cc_mode == CPRRTC_CC_GEMM_TF32, ctx->rb, g, ctx->dev.sm_count, ctx->stream);
+    tg.done();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form check launch");
+  }
+  rc = st.end(ctx);
+  if (rc == CPRRTC_OK && gemm && st.any_host) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->d_cc_error, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form status");
+    if (flag) return fail(ctx, CPRRTC_E_TIMEOUT, "validate: a wait of the GEMM-form check timed out");
+  }
+  return rc;
 }
 
 int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_iters,

@@ -35,6 +35,7 @@ struct ValidateArgs {
   int refine_iters;
   uint8_t* warm_used;  // [n] 1 when the warm-started segment was accepted (may be null)
   const int* warm_error;  // nonzero: the corrections are not valid; plain Alg. 1 only
+  int skip_cc;            // 1: projection only (collision checking is done elsewhere)
   int stage_obs;  // set by the launcher
 };
 
@@ -126,6 +127,26 @@ cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, 
                            float* loss_dev, cudaStream_t s);
 cudaError_t mlp_train(MlpDev* d, const float* q, const float* t, int n, int batch, int epochs,
                       float lr, uint64_t seed, float* loss_host, cudaStream_t s);
+// Collision checking in GEMM form (gemm_cc.cu): motions with status kValid get their
+// waypoints (q, [n][W][dof]) checked against the sphere obstacles; colliding motions get
+// status kCollision and their first colliding waypoint.
+struct GemmCcArgs {
+  const float* q;
+  int n, W;
+  uint8_t* status;
+  int32_t* first_fail;
+  const uint8_t* bimage;  // packed B' (32 KB chunks)
+  int n_tiles;            // N tiles of 256 obstacles
+  const float4* obs;      // obstacle spheres {x, y, z, rho}, the image's row order
+  int n_obs;
+  float4 origin;          // {o, guard / 2}
+  float bound;            // E: pairs with s >= E cannot collide
+  unsigned long long* counters;  // [1] exact rechecks (may be null)
+  int* error;
+};
+size_t gemm_cc_smem_bytes();
+cudaError_t launch_gemm_cc(int tf32, const RobotDev& rb, const GemmCcArgs& a, int sm_count, cudaStream_t s);
+
 // Fused tensor-core inference (mlp_fused.cu). Rows are configurations q [rows][ldq] when q
 // is set, else waypoints of motions (row m * W + i of the interpolation q0[m] -> q1[m]).
 struct FusedMlpArgs {
