@@ -193,7 +193,7 @@ int cprrtc_project_configs(cprrtc_ctx* ctx, const float* q_in, int n, int max_it
 int cprrtc_set_cc_mode(cprrtc_ctx* ctx, int mode, double guard_m);
 
 /* The GEMM-form check's error bound E (m^2; 0 in EXACT mode) and its counters since the
- * last reset: counters[0] = pairs rechecked exactly, counters[1] = reserved (0). Synchronises
+ * last reset: counters[0] = pairs rechecked exactly, counters[1] = unused (0). Synchronises
  * the context's stream; reset = 1 zeroes the counters. */
 int cprrtc_cc_stats(cprrtc_ctx* ctx, double* bound_m2, int64_t* counters, int reset);
 

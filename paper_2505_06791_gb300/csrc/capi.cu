@@ -754,8 +754,9 @@ int cprrtc_set_cc_mode(cprrtc_ctx* ctx, int mode, double guard_m) {
   if (mode == CPRRTC_CC_EXACT) return CPRRTC_OK;
   DeviceGuard g(ctx->device);
   if (!ctx->d_cc_counters) {
-    cudaError_t e = cudaMalloc(&ctx->d_cc_counters, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_cc_counters, 0, 2 * sizeof(unsigned long long));
+    // word 0: rechecks, word 1: unused, word 2: the kernel's motion counter
+    cudaError_t e = cudaMalloc(&ctx->d_cc_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_cc_counters, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_cc_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_cc_error, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set_cc_mode");
@@ -941,6 +942,9 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
     g.bound = (float)ctx->cc_bound;
     g.counters = ctx->d_cc_counters;
     g.error = ctx->d_cc_error;
+    g.next = reinterpret_cast<int*>(ctx->d_cc_counters + 2);
+    e = cudaMemsetAsync(g.next, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form scheduling counter");
     LaunchTimer tg(ctx, "gemm_cc");
     e = launch_gemm_cc(ctx->cc_mode == CPRRTC_CC_GEMM_TF32, ctx->rb, g, ctx->dev.sm_count, ctx->stream);
     tg.done();

@@ -17,7 +17,9 @@
 // exact collision kernel, on sphere centres computed by the same FK arithmetic, so the
 // verdicts, and each motion's first colliding waypoint, are those of the exact kernel.
 //
-// One persistent CTA per SM takes motions in a fixed order and their waypoints in order.
+// One persistent CTA per SM takes motions from a global counter (the FK group fetches them,
+// skipping motions that did not project, into a small ring every role reads in the same
+// order) and their waypoints in order.
 // A waypoint is one M = 128 tile (robot spheres, padding rows never collide); the obstacles
 // are N tiles of 256, and every N tile is one (BF16) or two (TF32) tcgen05.mma into an FP32
 // accumulator in tensor memory (two accumulators, so the epilogue of one tile overlaps the
@@ -71,7 +73,9 @@ constexpr int kOffHit = kOffBarCc + kNumBarsCc * 8;  // int [2]
 constexpr int kOffTmemCc = kOffHit + 8;
 constexpr int kOffAbortCc = kOffTmemCc + 4;
 constexpr int kOffRechk = kOffAbortCc + 4;  // unsigned long long
-constexpr int kSmemCc = kOffRechk + 8;
+constexpr int kOffRing8 = kOffRechk + 8;    // int [8] motion ring, int fetched, int done
+constexpr int kRingM = 8;
+constexpr int kSmemCc = kOffRing8 + (kRingM + 2) * 4;
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint64_t kDrainNs = 20000000ull;
 static_assert(kOffBarCc % 8 == 0 && kOffRechk % 8 == 0, "alignment");
@@ -150,8 +154,8 @@ __device__ __forceinline__ void mma_cc(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void commit_to(uint32_t b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
 }
-__device__ __forceinline__ void tld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+__device__ __forceinline__ void tld32_issue(uint32_t taddr, float (&v)[32]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -161,10 +165,8 @@ __device__ __forceinline__ void tld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Round-to-nearest-even to the MMA precision (BF16: 8 significant bits, TF32: 11).
 template <int TF32>
@@ -219,6 +221,8 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     }
     *s_abort = 0;
     *s_rechk = 0ull;
+    *reinterpret_cast<volatile int*>(sm + kOffRing8 + kRingM * 4) = 0;
+    *reinterpret_cast<volatile int*>(sm + kOffRing8 + kRingM * 4 + 4) = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarpCc) {
@@ -230,6 +234,27 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
   tca();
   const uint32_t tmem = *s_tmem;
 
+  int* s_mring = reinterpret_cast<int*>(sm + kOffRing8);
+  volatile int* s_fetched = reinterpret_cast<volatile int*>(sm + kOffRing8 + kRingM * 4);
+  volatile int* s_done = s_fetched + 1;
+  // bounded wait on a shared counter written by another role
+  auto wait_count = [&](volatile int* cnt, int need) -> bool {  // until *cnt >= need
+    const uint64_t t0 = gtime();
+    while (*cnt < need) {
+      if (*s_abort) return false;
+      if (gtime() - t0 > kWaitNs) {
+        *s_abort = 1;
+        return false;
+      }
+      __nanosleep(64);
+    }
+    return true;
+  };
+  // the k-th motion of this CTA (-1: none left; -2: aborted)
+  auto motion = [&](int k) -> int {
+    if (!wait_count(s_fetched, k + 1)) return -2;
+    return *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]);
+  };
   // verdict of global waypoint g: the epilogue stores g + 1 into s_hit[g % 2] when it collided
   auto verdict_hit = [&](uint32_t g) { return s_hit[g & 1] == (int)(g + 1); };
   // per motion: issue(w) = w < W and (w < 2 or the motion is still active after verdict(w - 2))
@@ -248,8 +273,10 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         for (int c = 0; c < n_chunks; ++c) mb_drain(bar(kBFull + c), 0);
       } else {
         uint32_t fill = 0, g = 0;
-        for (int m = blockIdx.x; ok && m < a.n; m += gridDim.x) {
-          if (a.status[m] != kValid) continue;
+        for (int k = 0; ok; ++k) {
+          const int m = motion(k);
+          if (m == -2) ok = false;
+          if (m < 0) break;
           bool active = true;
           for (int w = 0; ok && w < W; ++w, ++g) {
             if (g >= 2) {
@@ -281,8 +308,10 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     if (lane == 0) {
       bool ok = true, loaded = false;
       uint32_t g = 0, tcount = 0, use = 0;
-      for (int m = blockIdx.x; ok && m < a.n; m += gridDim.x) {
-        if (a.status[m] != kValid) continue;
+      for (int k = 0; ok; ++k) {
+        const int m = motion(k);
+        if (m == -2) ok = false;
+        if (m < 0) break;
         bool active = true;
         for (int w = 0; ok && w < W; ++w, ++g) {
           if (g >= 2) {
@@ -336,8 +365,25 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     volatile int* s_ctl = reinterpret_cast<volatile int*>(s_frames + 2 * 9 * 12);  // control word
     uint32_t g = 0;
     bool ok = true;
-    for (int m = blockIdx.x; ok && m < a.n; m += gridDim.x) {
-      if (a.status[m] != kValid) continue;
+    for (int k = 0; ok; ++k) {
+      if (threadIdx.x == 0) {  // fetch the next projected motion into the ring
+        int m = -1;
+        if (wait_count(s_done, k - kRingM + 1)) {  // slot k % 8 no longer read
+          do {
+            m = atomicAdd(a.next, 1);
+          } while (m < a.n && a.status[m] != kValid);
+          if (m >= a.n) m = -1;
+        } else {
+          m = -2;
+        }
+        *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]) = m;
+        __threadfence_block();
+        *s_fetched = k + 1;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(kFkWarps * 32) : "memory");
+      const int m = *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]);
+      if (m == -2) ok = false;
+      if (m < 0) break;
       bool active = true;
       for (int w = 0; ok && w < W; ++w, ++g) {
         const int buf = g & 1;
@@ -417,8 +463,10 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     bool ok = true;
     uint32_t g = 0, tcount = 0;
     unsigned long long rechecks = 0;
-    for (int m = blockIdx.x; ok && m < a.n; m += gridDim.x) {
-      if (a.status[m] != kValid) continue;
+    for (int k = 0; ok; ++k) {
+      const int m = motion(k);
+      if (m == -2) ok = false;
+      if (m < 0) break;
       int first_hit = -1;
       for (int w = 0; ok && w < W; ++w, ++g) {
         const int buf = g & 1;
@@ -427,40 +475,55 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         if (!__all_sync(0xffffffffu, mb_wait(bar(kAFull + buf), (g >> 1) & 1, s_abort))) { ok = false; break; }
         const float4 cen = s_centre[buf * 128 + row];
         bool hit = false;
-        for (int t = 0; t < n_tiles; ++t, ++tcount) {
-          const uint32_t slot = tcount & 1;
-          if (!__all_sync(0xffffffffu, mb_wait(bar(kAccF + slot), (tcount >> 1) & 1, s_abort))) { ok = false; break; }
+        // per N tile: four 32-column quarters, the next quarter's tensor-memory load in
+        // flight while the current one is reduced
+        for (int t = 0; ok && t < n_tiles; ++t) {
+          const uint32_t tc = tcount + (uint32_t)t, slot = tc & 1;
+          if (!__all_sync(0xffffffffu, mb_wait(bar(kAccF + slot), (tc >> 1) & 1, s_abort))) {
+            ok = false;
+            break;
+          }
           tca();
           const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)half * 128;
-#pragma unroll 1
+          float v[32], nv[32];
+          tld32_issue(base, v);
+          tld_wait();
+#pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
-            float v[32];
-            tld32(base + q4 * 32, v);
-            if (q4 == 3) {  // the accumulator is free once read
+            if (q4 < 3) {
+              tld32_issue(base + (uint32_t)(q4 + 1) * 32, nv);
+            } else {  // every load of this tile has completed: release its accumulator
               tcb();
               __syncwarp();
               if (lane == 0) mb_arrive(bar(kAccE + slot));
             }
-            if (drain || cen.w < 0.f) continue;
-            float mn = v[0];
+            if (!drain && cen.w >= 0.f) {
+              float mn = v[0];
 #pragma unroll
-            for (int i = 1; i < 32; ++i) mn = fminf(mn, v[i]);
-            if (mn < E && !hit) {  // rare: candidates for the exact test
-              unsigned cm = 0u;
+              for (int i = 1; i < 32; ++i) mn = fminf(mn, v[i]);
+              if (mn < E && !hit) {  // rare: candidates for the exact test
+                unsigned cm = 0u;
 #pragma unroll
-              for (int i = 0; i < 32; ++i) cm |= (v[i] < E ? 1u : 0u) << i;
-              const int j0 = t * 256 + half * 128 + q4 * 32;
-              while (cm && !hit) {
-                const int i = __ffs(cm) - 1;
-                cm &= cm - 1u;
-                if (j0 + i < a.n_obs) {
-                  ++rechecks;
-                  hit = hit_sphere(cen.x, cen.y, cen.z, cen.w, a.obs[j0 + i]);
+                for (int i = 0; i < 32; ++i) cm |= (v[i] < E ? 1u : 0u) << i;
+                const int j0 = t * 256 + half * 128 + q4 * 32;
+                while (cm && !hit) {
+                  const int i = __ffs(cm) - 1;
+                  cm &= cm - 1u;
+                  if (j0 + i < a.n_obs) {
+                    ++rechecks;
+                    hit = hit_sphere(cen.x, cen.y, cen.z, cen.w, a.obs[j0 + i]);
+                  }
                 }
               }
             }
+            if (q4 < 3) {
+              tld_wait();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] = nv[i];
+            }
           }
         }
+        tcount += (uint32_t)n_tiles;
         if (!ok) break;
         // verdict of waypoint g: s_hit[g % 2] = g + 1 when any row collided
         const bool any = __any_sync(0xffffffffu, hit);
@@ -484,6 +547,8 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
           }
         }
       }
+      // every epilogue warp has passed this motion's last verdict: its ring slot is free
+      if (ok && e == 0 && lane == 0) *s_done = k + 1;
     }
     if (rechecks) atomicAdd(s_rechk, rechecks);
   }

@@ -143,6 +143,7 @@ struct GemmCcArgs {
   float bound;            // E: pairs with s >= E cannot collide
   unsigned long long* counters;  // [1] exact rechecks (may be null)
   int* error;
+  int* next;  // motion counter for the CTAs' dynamic scheduling, zeroed before the launch
 };
 size_t gemm_cc_smem_bytes();
 cudaError_t launch_gemm_cc(int tf32, const RobotDev& rb, const GemmCcArgs& a, int sm_count, cudaStream_t s);
