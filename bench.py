@@ -77,8 +77,8 @@ def executed_flops(dof: int, counters) -> float:
 
 def profiled_traffic_per_unit(name: str, key: str):
     """DRAM bytes per unit recorded in profiles/<name> from an ncu capture, or None when the
-    kernel sources changed since (the file records their hash)."""
-    import glob
+    kernel's sources (the files the profile lists) changed since (the file records their
+    hash)."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", name)
@@ -87,11 +87,16 @@ def profiled_traffic_per_unit(name: str, key: str):
     except OSError:
         return None
     m_hash = re.search(r"source_sha256_16: ([0-9a-f]{16})", text)
+    m_files = re.search(r"source_files: ([\w. ]+)", text)
     m_val = re.search(key + r": ([0-9.eE+]+)", text)
-    if not (m_hash and m_val):
+    if not (m_hash and m_val and m_files):
         return None
-    src = sorted(glob.glob(os.path.join(ROOT, "paper_2505_06791_gb300", "csrc", "*")))
-    h = hashlib.sha256(b"".join(open(f, "rb").read() for f in src)).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2505_06791_gb300", "csrc")
+    try:
+        blob = b"".join(open(os.path.join(csrc, f), "rb").read() for f in sorted(m_files.group(1).split()))
+    except OSError:
+        return None
+    h = hashlib.sha256(blob).hexdigest()[:16]
     return float(m_val.group(1)) if h == m_hash.group(1) else None
 
 
@@ -713,7 +718,7 @@ def run_gemmcc(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     rb, sc, c = config3_workload()
-    n, W = CC_N, CC_W
+    n, W = (CC_N if args.problems == PLAN_N else args.problems), CC_W
     ctx = Context(local, stream.cuda_stream)
     ctx.set_robot(rb)
     ctx.set_obstacles(sc)
@@ -783,6 +788,7 @@ def run_gemmcc(args, world, rank, local):
                                        else "BF16 measured (MEASURED_PEAKS.json bf16_tflops)"})
         summary[name] = entry
     best = max(("gemm_tf32", "gemm_bf16"), key=lambda k: summary[k]["value"])
+    gcc_tile_bytes = profiled_traffic_per_unit("gemm_cc_kernel_config3.md", "traffic_per_waypoint_tile_bytes")
     b = summary[best]
     line = {
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -799,7 +805,11 @@ def run_gemmcc(args, world, rank, local):
                      "collision": int((st == 2).sum()), "gemm_waypoint_tiles": tiles},
         "roofline": {"bound": "tensor", "achieved": b["tensor_tflops"], "peak": b["tensor_peak_tflops"],
                      "unit": "TFLOP/s", "frac": b["tensor_tflops"] / b["tensor_peak_tflops"],
-                     "traffic": None, "kernel": "gemm_cc_kernel",
+                     "traffic": (None if gcc_tile_bytes is None or best != "gemm_bf16"
+                                 else gcc_tile_bytes * tiles),
+                     "traffic_note": "ncu DRAM bytes per waypoint tile of a 512-motion BF16 capture "
+                                     "(profiles/gemm_cc_kernel_config3.md) x waypoint tiles",
+                     "kernel": "gemm_cc_kernel",
                      "flop_per_launch": tensor_flop, "avg_launch_ms": b["gemm_cc_kernel_ms"]},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
@@ -842,7 +852,7 @@ def run_warmstart(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     rb, sc, c = config4_workload()
-    n, W = WS_MOTIONS, WS_W
+    n, W = (WS_MOTIONS if args.problems == PLAN_N else args.problems), WS_W
     ctx = Context(local, stream.cuda_stream)
     ctx.set_robot(rb)
     ctx.set_obstacles(sc)
@@ -868,7 +878,7 @@ def run_warmstart(args, world, rank, local):
         ctx.mlp_init(seed)
         held0, _ = ctx.mlp_grad(q_ho, t_ho)
         t0 = time.perf_counter()
-        losses = ctx.mlp_train(q_tr, t_tr, batch=1024, epochs=WS_EPOCHS, lr=1e-3, seed=seed)
+        losses = ctx.mlp_train(q_tr, t_tr, batch=1024, epochs=args.train_epochs, lr=1e-3, seed=seed)
         train_s = time.perf_counter() - t0
         held1, _ = ctx.mlp_grad(q_ho, t_ho)
         zero_loss = float(0.5 * ((t_ho - q_ho) ** 2).sum(1).mean())
@@ -932,6 +942,7 @@ def run_warmstart(args, world, rank, local):
     infer_ms, infer_launches = kt_ws["mlp_infer"]
     infer_avg_s = infer_ms / 1e3 / max(infer_launches, 1)
     flops_infer = mlp_flops_per_row(rb.dof) * n * W
+    mlp_row_bytes = profiled_traffic_per_unit("mlp_fused_kernel_config4.md", "traffic_per_row_bytes")
     tensor_peak = float(peaks.get("bf16_tflops", 1900.0))
     achieved = flops_infer / infer_avg_s / 1e12
     vk_ms, vk_launches = kt_ws["validate"]
@@ -965,15 +976,19 @@ def run_warmstart(args, world, rank, local):
                        "infer_ms_per_step": infer_avg_s * 1e3,
                        "validate_ms_per_step": vk_ms / max(vk_launches, 1)},
         "training": {"pairs": int(q_tr.shape[0]), "pair_generation_s": pairs_s,
-                     "epochs": WS_EPOCHS, "batch": 1024, "lr": 1e-3, "train_s": train_s,
-                     "samples_per_s": WS_EPOCHS * q_tr.shape[0] / train_s,
+                     "epochs": args.train_epochs, "batch": 1024, "lr": 1e-3, "train_s": train_s,
+                     "samples_per_s": args.train_epochs * q_tr.shape[0] / train_s,
                      "loss_first_last_epoch": [float(losses[0]), float(losses[-1])],
                      "heldout_loss_init_trained": [held0, held1],
                      "heldout_zero_prediction_loss": zero_loss,
                      "pairs_source": "uniform configurations projected by cprrtc_project_configs"},
         "e2e": e2e,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": tensor_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tensor_peak, "traffic": None, "kernel": "mlp_fused_kernel",
+                     "frac": achieved / tensor_peak,
+                     "traffic": (None if mlp_row_bytes is None else mlp_row_bytes * n * W),
+                     "traffic_note": "ncu DRAM bytes per row of a 131072-row capture "
+                                     "(profiles/mlp_fused_kernel_config4.md) x rows",
+                     "kernel": "mlp_fused_kernel",
                      "flop_per_launch": flops_infer, "avg_launch_ms": infer_avg_s * 1e3,
                      "peak_note": "measured dense BF16 (MEASURED_PEAKS.json bf16_tflops, burst)"},
         "gpu_launches": int(kt_ws["validate"][1] + kt_ws["mlp_infer"][1]),
@@ -1093,6 +1108,23 @@ def reference_arm(args, world, rank):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_legs(args):
+    """The other configurations, each in a child process with the same steps and warm-up,
+    its own JSON line kept whole (a failing leg records its error instead)."""
+    legs = {}
+    for leg in [x for x in args.legs.split(",") if x]:
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", leg, "--steps", str(args.steps),
+               "--warmup", str(args.warmup), "--cpu-budget", "3", "--legs", "none"]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            legs[leg] = json.loads(lines[-1]) if r.returncode == 0 and lines else \
+                {"error": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"}
+        except (subprocess.TimeoutExpired, ValueError) as e:
+            legs[leg] = {"error": str(e)[:300]}
+    return legs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1105,6 +1137,11 @@ def main():
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
+                    help="warm-start training epochs (fewer for profiling runs)")
+    ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch",
+                    help="with the default planner workload on one GPU: the other configurations, "
+                         "each run as its own process and reported under 'legs' ('none' to skip)")
     args = ap.parse_args()
     if args.max_rounds is not None:
         PLAN_PARAMS["max_rounds"] = args.max_rounds
@@ -1135,6 +1172,8 @@ def main():
     if rank == 0:
         if world == 1 and baseline is not None:
             line["cpu_baseline"] = baseline(inputs, args.cpu_budget)
+        if args.workload == "plan" and world == 1 and args.legs != "none":
+            line["legs"] = run_legs(args)
         print(json.dumps(line), flush=True)
 
 
