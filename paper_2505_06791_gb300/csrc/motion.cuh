@@ -179,7 +179,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
 //   spheres per frame | first sphere of each frame | joints |
 //   per warp: waypoints [W][9] floats, swept bounds [dof + 1], candidate list |
 //   extra (kernel-specific, 16-aligned)
-constexpr int kCandMax = 128;  // candidate obstacles listed per pass of the collision check
+constexpr int kCandMax = 512;  // candidate obstacles listed per pass of the collision check
 
 struct SmemLayout {
   size_t obs, sph, bnd, nsf, foff, jnt, warp0, warp_bytes, wq, sbnd, cand, extra, total;
@@ -193,7 +193,7 @@ struct SmemLayout {
     jnt = al(foff + (size_t)(kMaxDof + 2) * 4);
     warp0 = al(jnt + sizeof(JointDev) * kMaxDof);
     wq = 0;
-    sbnd = al(wq + (size_t)W * 9 * 4);
+    sbnd = al(wq + (size_t)W * 9 * 8);
     cand = al(sbnd + (size_t)(kMaxDof + 1) * 16);
     warp_bytes = al(cand + (size_t)kCandMax * 4);
     extra = al(warp0 + (size_t)warps * warp_bytes);
@@ -208,7 +208,8 @@ struct CcShared {
   const int* nsf;       // [dof + 1] spheres per frame
   const int* foff;      // [dof + 2] first sphere of each frame
   const JointDev* jnt;  // [dof]
-  float* wq;            // this warp: waypoints [W][9]
+  float2* wq;           // this warp: per waypoint and joint {sin, cos} of the joint angle
+                        // (revolute) or {q, 0} (prismatic), [W][9]
   float4* sbnd;         // this warp: swept frame bounds [dof + 1]
   unsigned* cand;       // this warp: candidate list, obstacle | frame mask << 20
 };
@@ -220,7 +221,7 @@ __device__ __forceinline__ CcShared cc_shared(char* base, const SmemLayout& L, i
                   reinterpret_cast<const int*>(base + L.nsf),
                   reinterpret_cast<const int*>(base + L.foff),
                   reinterpret_cast<const JointDev*>(base + L.jnt),
-                  reinterpret_cast<float*>(w + L.wq), reinterpret_cast<float4*>(w + L.sbnd),
+                  reinterpret_cast<float2*>(w + L.wq), reinterpret_cast<float4*>(w + L.sbnd),
                   reinterpret_cast<unsigned*>(w + L.cand)};
 }
 
@@ -289,6 +290,29 @@ struct Frame {
                 nz2 = fmaf(z2, J.ca, -v2 * J.sa);
     z0 = nz0; z1 = nz1; z2 = nz2;
   }
+  // The same step from a cached {sin, cos} (revolute) or {q, 0} (prismatic): the values are
+  // those `advance` computes, so the frames are identical.
+  __device__ __forceinline__ void advance_cached(const JointDev& J, float2 v) {
+    float ct, st, d = J.d;
+    if (J.prismatic) {
+      ct = J.ct0;
+      st = J.st0;
+      d += v.x;
+    } else {
+      st = v.x;
+      ct = v.y;
+    }
+    const float u0 = fmaf(x0, ct, y0 * st), u1 = fmaf(x1, ct, y1 * st), u2 = fmaf(x2, ct, y2 * st);
+    const float v0 = fmaf(y0, ct, -x0 * st), v1 = fmaf(y1, ct, -x1 * st), v2 = fmaf(y2, ct, -x2 * st);
+    p0 = fmaf(J.a, u0, fmaf(d, z0, p0));
+    p1 = fmaf(J.a, u1, fmaf(d, z1, p1));
+    p2 = fmaf(J.a, u2, fmaf(d, z2, p2));
+    x0 = u0; x1 = u1; x2 = u2;
+    y0 = fmaf(v0, J.ca, z0 * J.sa); y1 = fmaf(v1, J.ca, z1 * J.sa); y2 = fmaf(v2, J.ca, z2 * J.sa);
+    const float nz0 = fmaf(z0, J.ca, -v0 * J.sa), nz1 = fmaf(z1, J.ca, -v1 * J.sa),
+                nz2 = fmaf(z2, J.ca, -v2 * J.sa);
+    z0 = nz0; z1 = nz1; z2 = nz2;
+  }
   __device__ __forceinline__ void world(float lx, float ly, float lz, float& cx, float& cy,
                                         float& cz) const {
     cx = fmaf(x0, lx, fmaf(y0, ly, fmaf(z0, lz, p0)));
@@ -331,14 +355,21 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
-  // waypoints to shared memory: the chain below walks frames in a runtime loop
+  // each waypoint's joint terms to shared memory once (the chains below walk frames in a
+  // runtime loop, once for the swept bounds and once per pass)
 #pragma unroll
   for (int s = 0; s < WPL; ++s) {
     const int i = lane + 32 * s;
     if (i < W) {
 #pragma unroll
-      for (int k = 0; k < kMaxDof; ++k)
-        if (k < dof) S.wq[i * 9 + k] = q[s][k];
+      for (int k = 0; k < kMaxDof; ++k) {
+        if (k < dof) {
+          const JointDev& J = S.jnt[k];
+          float2 v = make_float2(q[s][k], 0.f);
+          if (!J.prismatic) sincospif((J.theta0 + q[s][k]) * kInvPi, &v.x, &v.y);
+          S.wq[i * 9 + k] = v;
+        }
+      }
     }
   }
   __syncwarp();
@@ -361,7 +392,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       if (f > 0) {
         const JointDev J = S.jnt[f - 1];
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) F[s].advance(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
       }
       const float4 b = S.bnd[f];
       if (b.w < 0.f) continue;  // no spheres on this frame (warp-uniform)
@@ -447,6 +478,14 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
     }
     __syncwarp();
     if (n_cand == 0) continue;
+    // waypoints at or after the smallest colliding one found so far cannot change the answer
+    bool any_act = false;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+      act[s] = act[s] && lane + 32 * s < best;
+      any_act |= act[s];
+    }
+    if (!__any_sync(kFull, any_act)) break;
     // ---- levels 2 and 3: lanes walk their waypoints' chains frame by frame ----
     Frame F[WPL];
 #pragma unroll
@@ -458,7 +497,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       if (f > 0) {
         const JointDev J = S.jnt[f - 1];
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) F[s].advance(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
       }
       const float4 b = S.bnd[f];
       if (b.w < 0.f) continue;
