@@ -33,7 +33,7 @@ def to_np(x):
     return np.asarray(x)
 
 
-def oracle_runs(orc, constraint, q_start, q_end, W, cc_skip_first=False):
+def oracle_runs(orc, constraint, q_start, q_end, W, cc_skip_first=False, n_threads=1):
     """The base oracle run followed by the four threshold-shifted runs."""
     runs = []
     shifts = [(0, 0)]
@@ -44,7 +44,8 @@ def oracle_runs(orc, constraint, q_start, q_end, W, cc_skip_first=False):
         c.tol_task += dt
         c.tol_sm += ds
         orc.set_constraint(c)
-        runs.append(orc.validate(q_start, q_end, W, cc_skip_first=cc_skip_first))
+        runs.append(orc.validate(q_start, q_end, W, cc_skip_first=cc_skip_first,
+                                 n_threads=n_threads))
     orc.set_constraint(constraint)
     return runs
 

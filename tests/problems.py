@@ -97,15 +97,17 @@ def batch_start_goal(oracle_mod, robots, constraints, problems, scenes, seed, cl
 
 
 def check_batch_paths(oracle_mod, robots, constraints, problems, scenes, start, goal, out,
-                      range_, slack=2e-6, contact=1e-5):
+                      range_, slack=2e-6, contact=1e-5, sample=None):
     """Oracle re-validation of batch paths ([n][max_path][8] nodes, [n][max_path-1][Wmax][8]
-    edges)."""
+    edges); `sample` restricts it to those problem indices."""
     to_np = lambda x: x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)  # noqa
     L = to_np(out["path_len"])
     path = to_np(out["path"])
     edges = to_np(out["path_edges"]) if out.get("path_edges") is not None else None
     issues, checked = [], 0
     for p, (r, c, sc, W) in enumerate(problems):
+        if sample is not None and p not in sample:
+            continue
         n = int(L[p])
         if n <= 0:
             continue

@@ -2,6 +2,8 @@
 tensor-core kernels) against the FP64 oracle on weights and data the test draws itself,
 training on oracle-projected pairs, and cprrtc_validate_ws, whose answers are judged by
 the plain projection's acceptance tests and the oracle's collision check."""
+import os
+
 import numpy as np
 import pytest
 
@@ -232,3 +234,43 @@ def test_validate_ws_judged_by_plain_projection(torch_cuda, oracle_mod, setup, t
     print(f"warm used {used.mean():.2f}; projected plain {plain_ok.sum()} warm {ws_ok.sum()}; "
           f"mean iters (plain-projected motions) plain {it_plain:.2f} warm {it_ws:.2f}")
     assert ws_ok.sum() > plain_ok.sum() or it_ws < it_plain
+
+
+def test_validate_ws_full_size(torch_cuda, oracle_mod, setup, trained):
+    """16384 motions x 32 waypoints (the configuration-4 launch, roll-pitch): fallen-back
+    motions equal the plain method's results; 200 sampled warm-started motions are judged by
+    the oracle; no motion the plain method projects is lost."""
+    torch = torch_cuda
+    rb, sc, c = setup
+    ctx = trained["ctx"]
+    orc = oracle_mod.Oracle(rb, sc, c)
+    n, W = 16384, 32
+    threads = os.cpu_count() or 4
+    q0, k = [], 0
+    while len(q0) < n:
+        q = S.uniform_configs(rb, 2 * n, 90_000 + k).astype(np.float32)
+        ok, qp, _ = orc.project_configs(q, 60, n_threads=threads)
+        q0.extend(qp[ok])
+        k += 1
+    q0 = S.f32(np.array(q0[:n])).astype(np.float32)
+    q1 = S.uniform_configs(rb, n, 91_000).astype(np.float32)
+    d0, d1 = torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()
+    plain = {k_: parity.to_np(v) for k_, v in ctx.validate(d0, d1, W).items()}
+    ws = {k_: parity.to_np(v) for k_, v in ctx.validate_ws(d0, d1, W, refine_iters=5).items()}
+    used = ws["warm"].astype(bool)
+    fb = ~used
+    for key in ("status", "first_fail", "q"):
+        np.testing.assert_array_equal(ws[key][fb], plain[key][fb], err_msg=key)
+    plain_ok, ws_ok = plain["status"] != 1, ws["status"] != 1
+    assert np.all(ws_ok[plain_ok]) and ws_ok.sum() > plain_ok.sum()
+    rng = np.random.default_rng(17)
+    for m in rng.choice(np.nonzero(used)[0], min(200, int(used.sum())), replace=False):
+        seg = ws["q"][m].astype(np.float64)
+        tau = oracle_mod.tau_step(c, q0[m], q1[m], W)
+        max_task, step_excess, _ = orc.check_segment(seg, tau)
+        assert max_task < c.tol_task + parity.DELTA and step_excess < c.tol_sm + parity.DELTA, m
+        ff, margin = first_colliding(orc, seg)
+        if margin > parity.CONTACT_MARGIN:
+            assert ff == ws["first_fail"][m], (m, ff, ws["first_fail"][m])
+    print("full size: plain projected", int(plain_ok.sum()), "warm", int(ws_ok.sum()),
+          "warm used", int(used.sum()))
