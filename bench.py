@@ -294,7 +294,7 @@ def run_plan(args, world, rank, local):
     work = out["work"].cpu().numpy()
     rounds = out["rounds"].cpu().numpy()
     waypoints_step = int(wp.sum())
-    value = waypoints_step * args.steps * world / (total_ms / 1e3)
+    value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     nominal = plan_flops(rb.dof, scenes, len(rb.spheres), work)
     flops = executed_flops(rb.dof, counters)
 
@@ -504,7 +504,7 @@ def run_batch(args, world, rank, local):
     wp = out["waypoints"].cpu().numpy()
     ms = out["plan_ms"].cpu().numpy()
     waypoints_step = int(wp.sum())
-    value = waypoints_step * args.steps * world / (total_ms / 1e3)
+    value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     # executed FLOPs: dof differs per problem; weight Alg. 1 updates by the mean dof
     mean_dof = float(np.mean([robots[r].dof for r, _, _, _ in probs]))
     upd, chains, tf, ps, pb, pc = [float(x) for x in counters]
@@ -585,14 +585,27 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    """The slowest rank's time (the job's time)."""
+    import torch.distributed as dist
+    return x if world == 1 else _reduce(x, world, dist.ReduceOp.MAX)
+
+
+def sum_over_ranks(x, world):
+    """Units processed by all ranks (each rank draws its own seeded inputs)."""
+    import torch.distributed as dist
+    return x if world == 1 else _reduce(x, world, dist.ReduceOp.SUM)
 
 
 def run_validate(args, world, rank, local):
