@@ -403,8 +403,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(FusedMlpArg
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int i = c2 * 8 + 2 * e;
-                w[e] = pack_bf16x2(mlp_gelu(__uint_as_float(v[i]) + bb[2 * e]),
-                                   mlp_gelu(__uint_as_float(v[i + 1]) + bb[2 * e + 1]));
+                float g0, g1;
+                mlp_gelu2(__uint_as_float(v[i]) + bb[2 * e], __uint_as_float(v[i + 1]) + bb[2 * e + 1], g0, g1);
+                w[e] = pack_bf16x2(g0, g1);
               }
               // in place: all of this layer's MMAs have completed
               *reinterpret_cast<uint4*>(act + sw128(r, col0 + c2 * 8, kTileRows)) = make_uint4(w[0], w[1], w[2], w[3]);
