@@ -10,10 +10,13 @@
 // each coordinate product is kept to hi*hi + hi*lo + lo*hi:
 //   A' = [(-2a_k)hi, (-2a_k)hi, (-2a_k)lo]_k=0..2, alpha_hi, alpha_lo, -2r', 1, 1, 0, 0
 //   B' = [ b_k hi,    b_k lo,    b_k hi  ]_k=0..2, 1,        1,        rho', beta_hi, beta_lo, 0, 0
-// with alpha = |a|^2 - r'^2 and beta = |b|^2 - rho'^2. The host derives a bound E on
-// |s_tensor - s| from the unit roundoff of the precision and the coordinate ranges. A pair
-// with s_tensor >= E has s >= 0, i.e. clearance >= g > 0: no collision, and no FP32 rounding
-// can turn it into one. Pairs with s_tensor < E are rechecked with the same FP32 test as the
+// with alpha = |a|^2 - r'^2 - E and beta = |b|^2 - rho'^2. The host derives a bound E on
+// |s_tensor - s| from the unit roundoff of the precision and the coordinate ranges; folding
+// -E into alpha makes the contraction s - E. A pair with s_tensor - E >= 0 has s >= 0, i.e.
+// clearance >= g > 0: no collision, and no FP32 rounding can turn it into one. An epilogue
+// warp ORs the raw bits of its 64 accumulator columns: a clear sign bit clears all 64 pairs;
+// otherwise (rarely) the row is rechecked against those 64 obstacles with the same FP32
+// test as the
 // exact collision kernel, on sphere centres computed by the same FK arithmetic, so the
 // verdicts, and each motion's first colliding waypoint, are those of the exact kernel.
 //
@@ -29,14 +32,15 @@
 // chunks stay resident in shared memory (4096 obstacles in BF16); larger images stream
 // through a four-stage ring filled by bulk (TMA) copies.
 //
-// Warp roles (448 threads):
+// Warp roles (704 threads):
 //   warps 0-3   FK: the chain of the waypoint (one thread, Frame::advance from the base),
 //               then one thread per robot sphere: FP32 centre (Frame::world), the A' row in
 //               the operand layout, and the centre kept for the recheck.
-//   warps 4-11  epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and the
-//               128-column half (w - 4) / 4 of each N tile, takes the minimum per row, and
-//               rechecks the rare entries below E exactly.
-//   warp 12     producer of B' chunks; warp 13 allocates tensor memory and issues the MMAs.
+//   warps 4-19  epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and the
+//               64-column quarter (w - 4) / 4 of each N tile (both loads at once, so the
+//               accumulator is released before the tests), ORs the values' bits, and in the
+//               rare case of a set sign bit rechecks those 64 pairs exactly.
+//   warp 20     producer of B' chunks; warp 21 allocates tensor memory and issues the MMAs.
 // Early termination: after each waypoint the epilogue publishes a verdict. Waypoint w of a
 // motion is issued only while waypoint w - 2 was collision-free, so after the first
 // colliding waypoint h exactly one more (h + 1, if it exists) is in flight and is drained.
@@ -53,10 +57,10 @@ namespace cprrtc {
 
 namespace {
 
-constexpr int kCcThreads = 448;
+constexpr int kCcThreads = 704;
 constexpr int kFkWarps = 4;
-constexpr int kEpiFirst = 4, kEpiWarpsCc = 8;
-constexpr int kProdWarp = 12, kMmaWarpCc = 13;
+constexpr int kEpiFirst = 4, kEpiWarpsCc = 16;
+constexpr int kProdWarp = 20, kMmaWarpCc = 21;
 constexpr int kCcStages = 4;
 constexpr int kChunkBytes = 32768;
 constexpr int kATile = 128 * 128;  // one waypoint's A' (SW128, 128 rows x 128 B)
@@ -154,8 +158,7 @@ __device__ __forceinline__ void mma_cc(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void commit_to(uint32_t b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
 }
-__device__ __forceinline__ void tld32_issue(uint32_t taddr, float (&v)[32]) {
-  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+__device__ __forceinline__ void tld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -426,7 +429,8 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
           s_centre[buf * 128 + row] = make_float4(cx, cy, cz, l.w);
           const float ax = cx - ori.x, ay = cy - ori.y, az = cz - ori.z;
           const float rp = l.w + ori.w;
-          const float al = fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, -rp * rp)));
+          // alpha less the bound: a candidate pair is then simply s - E < 0 (a sign bit)
+          const float al = fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, -rp * rp))) - a.bound;
           const float m2[3] = {-2.f * ax, -2.f * ay, -2.f * az};
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
@@ -457,12 +461,11 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     }
   } else if (warp >= kEpiFirst && warp < kEpiFirst + kEpiWarpsCc) {
     const int e = warp - kEpiFirst;
-    const int lq = warp & 3, half = e >> 2;
+    const int lq = warp & 3, qc = e >> 2;  // lane quarter, 64-column quarter of each tile
     const int row = lq * 32 + lane;
-    const float E = a.bound;
     bool ok = true;
     uint32_t g = 0, tcount = 0;
-    unsigned long long rechecks = 0;
+    unsigned rechecks = 0;
     for (int k = 0; ok; ++k) {
       const int m = motion(k);
       if (m == -2) ok = false;
@@ -473,10 +476,11 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         const bool drain = first_hit >= 0;  // the one waypoint issued after the first hit
         // the FK warps' centres for this waypoint (a_full cannot move on before this verdict)
         if (!__all_sync(0xffffffffu, mb_wait(bar(kAFull + buf), (g >> 1) & 1, s_abort))) { ok = false; break; }
-        const float4 cen = s_centre[buf * 128 + row];
+        // the FK warps' centre of this row is read only when a recheck needs it
+        const float4* cen_p = s_centre + buf * 128 + row;
         bool hit = false;
-        // per N tile: four 32-column quarters, the next quarter's tensor-memory load in
-        // flight while the current one is reduced
+        // per N tile: this warp's 64 columns in two loads issued together; the accumulator
+        // is released as soon as they land, so the next tile's MMA overlaps the tests
         for (int t = 0; ok && t < n_tiles; ++t) {
           const uint32_t tc = tcount + (uint32_t)t, slot = tc & 1;
           if (!__all_sync(0xffffffffu, mb_wait(bar(kAccF + slot), (tc >> 1) & 1, s_abort))) {
@@ -484,42 +488,26 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
             break;
           }
           tca();
-          const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)half * 128;
-          float v[32], nv[32];
-          tld32_issue(base, v);
+          const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)qc * 64;
+          uint32_t va[32], vb[32];
+          tld32_issue(base, va);
+          tld32_issue(base + 32, vb);
           tld_wait();
+          uint32_t any = 0u;  // sign bit set iff some s - E < 0 among this warp's 64 columns
 #pragma unroll
-          for (int q4 = 0; q4 < 4; ++q4) {
-            if (q4 < 3) {
-              tld32_issue(base + (uint32_t)(q4 + 1) * 32, nv);
-            } else {  // every load of this tile has completed: release its accumulator
-              tcb();
-              __syncwarp();
-              if (lane == 0) mb_arrive(bar(kAccE + slot));
-            }
-            if (!drain && cen.w >= 0.f) {
-              float mn = v[0];
-#pragma unroll
-              for (int i = 1; i < 32; ++i) mn = fminf(mn, v[i]);
-              if (mn < E && !hit) {  // rare: candidates for the exact test
-                unsigned cm = 0u;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) cm |= (v[i] < E ? 1u : 0u) << i;
-                const int j0 = t * 256 + half * 128 + q4 * 32;
-                while (cm && !hit) {
-                  const int i = __ffs(cm) - 1;
-                  cm &= cm - 1u;
-                  if (j0 + i < a.n_obs) {
-                    ++rechecks;
-                    hit = hit_sphere(cen.x, cen.y, cen.z, cen.w, a.obs[j0 + i]);
-                  }
-                }
+          for (int i = 0; i < 32; ++i) any |= va[i] | vb[i];
+          tcb();
+          __syncwarp();
+          if (lane == 0) mb_arrive(bar(kAccE + slot));
+          if ((any >> 31) && !drain && cen_p->w >= 0.f) {
+            // rare: recheck this row against the 64 obstacles exactly
+            const float4 cen = *cen_p;
+            const int j0 = t * 256 + qc * 64;
+            for (int i = 0; i < 64 && !hit; ++i) {
+              if (j0 + i < a.n_obs) {
+                ++rechecks;
+                hit = hit_sphere(cen.x, cen.y, cen.z, cen.w, a.obs[j0 + i]);
               }
-            }
-            if (q4 < 3) {
-              tld_wait();
-#pragma unroll
-              for (int i = 0; i < 32; ++i) v[i] = nv[i];
             }
           }
         }
@@ -550,7 +538,7 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
       // every epilogue warp has passed this motion's last verdict: its ring slot is free
       if (ok && e == 0 && lane == 0) *s_done = k + 1;
     }
-    if (rechecks) atomicAdd(s_rechk, rechecks);
+    if (rechecks) atomicAdd(s_rechk, (unsigned long long)rechecks);
   }
   tcb();
   __syncthreads();
