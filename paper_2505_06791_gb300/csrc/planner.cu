@@ -262,6 +262,10 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     }
   }
   __syncthreads();
+  // tree sizes when the round began: every warp keeps its own copy, advanced from the
+  // round's shared flags (identically in every warp)
+  int cnt0 = sh->count0[0], cnt1 = sh->count0[1];
+  auto count_of = [&](int t) { return t ? cnt1 : cnt0; };
   const float connect_radius = 10.f * cs.tau_floor;
   unsigned wp = 0;
   MotionWork work{0u, 0u};
@@ -285,7 +289,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       __syncwarp();
       if (lane < 8) qe[lane] = v;  // the sample, in the scratch slot
       __syncwarp();
-      last = nearest_warp(nodes(ta), sh->count0[ta], qe, dof);
+      last = nearest_warp(nodes(ta), count_of(ta), qe, dof);
       copy_cfg(cur, nodes(ta) + (size_t)last * 8, dof);
       steer(cur, qe, a.range, dof, q1);
     } else if (mode == 1) {
@@ -307,7 +311,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         last_waypoint<WPL>(q, W, dof, qe);
         bool accept = true;
         if (mode == 0) {
-          target = nearest_warp(nodes(ta ^ 1), sh->count0[ta ^ 1], qe, dof);
+          target = nearest_warp(nodes(ta ^ 1), count_of(ta ^ 1), qe, dof);
           copy_cfg(qt, nodes(ta ^ 1) + (size_t)target * 8, dof);
         } else {
           accept = dist2(qe, qt, dof) < dist2(cur, qt, dof);
@@ -341,7 +345,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       int off = 0;
       for (int w = 0; w < warp; ++w)
         if (sh->padd[w] && sh->ptree[w] == ta) ++off;
-      dst = sh->count0[ta] + off;
+      dst = count_of(ta) + off;
       if (dst < a.max_nodes) {
         copy_warp(nodes(ta) + (size_t)dst * 8, wnode, 8);
         copy_warp(edges(ta) + (size_t)dst * wd, wedge, (int)wd);
@@ -350,14 +354,15 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         dst = -1;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int t = 0; t < 2; ++t) {
-        int n_add = 0;
-        for (int w = 0; w < B; ++w) n_add += sh->padd[w] && sh->ptree[w] == t;
-        sh->count0[t] = min(sh->count0[t] + n_add, a.max_nodes);
-      }
+    {
+      int n_add0 = 0, n_add1 = 0;
+      for (int w = 0; w < B; ++w)
+        if (sh->padd[w]) (sh->ptree[w] ? n_add1 : n_add0) += 1;
+      cnt0 = min(cnt0 + n_add0, a.max_nodes);
+      cnt1 = min(cnt1 + n_add1, a.max_nodes);
     }
+    // the appended nodes are visible to every warp's next nearest-neighbour scan, and the
+    // flags may be overwritten
     __syncthreads();
     // next motion of the chain
     if (dst >= 0) {
