@@ -226,6 +226,16 @@ int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed);
 int cprrtc_mlp_set_params(cprrtc_ctx* ctx, const float* params, int64_t count);
 int cprrtc_mlp_get_params(cprrtc_ctx* ctx, float* params, int64_t count);
 
+/* Checkpoints of the network: parameters, Adam moments and step count in a versioned
+ * binary file (little-endian): magic "CPRMLP01", uint32 version (1), dof, hidden (256),
+ * layers (4), int32 step, uint32 0, uint64 count, then count floats each of parameters,
+ * first and second moments (compact layout), then the CRC-32 (IEEE) of all preceding
+ * bytes. Load requires set_robot with the file's dof (creating the network if needed) and
+ * rejects a wrong magic, version, shape, size or checksum. Synchronous. Errors:
+ * E_NOT_CONFIGURED, E_INVALID_ARG (I/O or format), E_CUDA, E_OOM. */
+int cprrtc_mlp_save(cprrtc_ctx* ctx, const char* path);
+int cprrtc_mlp_load(cprrtc_ctx* ctx, const char* path);
+
 /* Loss L = (1 / rows) sum_r 0.5 |f(q_r) - (t_r - q_r)|^2 over rows pairs (q [rows][dof],
  * t [rows][dof]: q's projection) and its gradient with respect to every parameter
  * (grads: host array of cprrtc_mlp_param_count(dof) floats, compact layout; loss: host,
@@ -293,6 +303,9 @@ typedef struct {
   uint32_t seed;
   int use_scene_batch; /* 1: problem p uses scene p of cprrtc_set_scene_batch; 0: the
                           cprrtc_set_obstacles scene for every problem */
+  double time_budget_ms; /* device time per problem (>= 0; 0: none): a problem whose budget
+                            is spent stops at the end of its round with path_len 0 unless
+                            it connected; results then depend on timing */
 } cprrtc_plan_params;
 
 /* Plans n problems start[p] -> goal[p] ([n][dof], on the constraint manifold and

@@ -43,7 +43,8 @@ class cprrtc_constraint(C.Structure):
 class cprrtc_plan_params(C.Structure):
     _fields_ = [("range", C.c_double), ("W", C.c_int), ("max_rounds", C.c_int),
                 ("workers", C.c_int), ("max_nodes", C.c_int), ("max_connect", C.c_int),
-                ("max_path", C.c_int), ("seed", C.c_uint32), ("use_scene_batch", C.c_int)]
+                ("max_path", C.c_int), ("seed", C.c_uint32), ("use_scene_batch", C.c_int),
+                ("time_budget_ms", C.c_double)]
 
 
 class cprrtc_robot_desc(C.Structure):
@@ -115,6 +116,8 @@ _SIGS = {
     "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
+    "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
+    "cprrtc_mlp_load": [C.c_void_p, C.c_char_p],
     "cprrtc_mlp_grad": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "cprrtc_mlp_train": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                          C.c_float, C.c_uint64, C.c_void_p],
@@ -361,6 +364,12 @@ class Context:
         self._check(self._L.cprrtc_mlp_get_params(self.h, p.ctypes.data, p.size))
         return p
 
+    def mlp_save(self, path: str):
+        self._check(self._L.cprrtc_mlp_save(self.h, os.fsencode(path)))
+
+    def mlp_load(self, path: str):
+        self._check(self._L.cprrtc_mlp_load(self.h, os.fsencode(path)))
+
     def mlp_grad(self, q, t):
         """(loss, gradient in the compact parameter layout) for pairs (q, t)."""
         g = np.empty(self.mlp_param_count(), np.float32)
@@ -400,9 +409,9 @@ class Context:
 
     @staticmethod
     def plan_params(range_=0.3, W=32, max_rounds=200, workers=8, max_nodes=2048,
-                    max_connect=32, max_path=512, seed=1, use_scene_batch=True):
+                    max_connect=32, max_path=512, seed=1, use_scene_batch=True, time_budget_ms=0.0):
         return cprrtc_plan_params(range_, W, max_rounds, workers, max_nodes, max_connect,
-                                  max_path, seed, int(use_scene_batch))
+                                  max_path, seed, int(use_scene_batch), float(time_budget_ms))
 
     def alloc_plan_outputs(self, n, params, like, edges=True):
         dof, W, mp = self.dof, params.W, params.max_path

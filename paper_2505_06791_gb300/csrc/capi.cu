@@ -111,7 +111,13 @@ int fail(cprrtc_ctx* ctx, int code, const std::string& msg) {
 
 int cuda_fail(cprrtc_ctx* ctx, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-  return fail(ctx, e == cudaErrorMemoryAllocation ? CPRRTC_E_OOM : CPRRTC_E_CUDA, m);
+  if (e == cudaErrorMemoryAllocation) {
+    // A failed allocation is not sticky; clear it so that the next launch check of this
+    // thread does not report it again.
+    cudaGetLastError();
+    return fail(ctx, CPRRTC_E_OOM, m);
+  }
+  return fail(ctx, CPRRTC_E_CUDA, m);
 }
 
 // Makes the context's device current for the duration of a call.
@@ -1040,6 +1046,112 @@ int cprrtc_mlp_get_params(cprrtc_ctx* ctx, float* params, int64_t count) {
   return CPRRTC_OK;
 }
 
+// ---- warm-start network checkpoints ----
+
+namespace {
+
+// CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise.
+uint32_t crc32_update(uint32_t crc, const uint8_t* p, size_t n) {
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+const char kCkptMagic[8] = {'C', 'P', 'R', 'M', 'L', 'P', '0', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, dof, hidden, layers;
+  int32_t step;
+  uint32_t reserved;
+  uint64_t count;
+};
+
+}  // namespace
+
+int cprrtc_mlp_save(cprrtc_ctx* ctx, const char* path) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->mlp) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "mlp_save: call mlp_init first");
+  if (!path) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_save: null path");
+  DeviceGuard g(ctx->device);
+  const int dof = mlp_dof(ctx->mlp);
+  const size_t n = mlp_compact_count(dof);
+  std::vector<float> p(n), m(n), v(n);
+  CkptHeader h{};
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = kCkptVersion;
+  h.dof = (uint32_t)dof;
+  h.hidden = (uint32_t)kMlpHidden;
+  h.layers = (uint32_t)kMlpLayers;
+  h.count = n;
+  int step = 0;
+  cudaError_t e = mlp_get_state(ctx->mlp, p.data(), m.data(), v.data(), &step, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_save");
+  h.step = step;
+  std::vector<uint8_t> buf(sizeof(h) + 3 * n * 4 + 4);
+  uint8_t* o = buf.data();
+  memcpy(o, &h, sizeof(h));
+  memcpy(o + sizeof(h), p.data(), n * 4);
+  memcpy(o + sizeof(h) + n * 4, m.data(), n * 4);
+  memcpy(o + sizeof(h) + 2 * n * 4, v.data(), n * 4);
+  const uint32_t crc = crc32_update(0u, o, buf.size() - 4);
+  memcpy(o + buf.size() - 4, &crc, 4);
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, CPRRTC_E_INVALID_ARG, std::string("mlp_save: cannot open ") + path);
+  const size_t w = fwrite(buf.data(), 1, buf.size(), f);
+  const int closed = fclose(f);
+  if (w != buf.size() || closed != 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_save: write failed");
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_load(cprrtc_ctx* ctx, const char* path) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "mlp_load: set_robot first");
+  if (!path) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: null path");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, CPRRTC_E_INVALID_ARG, std::string("mlp_load: cannot open ") + path);
+  std::vector<uint8_t> buf;
+  uint8_t chunk[65536];
+  size_t r;
+  while ((r = fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + r);
+  fclose(f);
+  CkptHeader h{};
+  if (buf.size() < sizeof(h) + 4) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: truncated file");
+  memcpy(&h, buf.data(), sizeof(h));
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: not a warm-start checkpoint of this version");
+  if (h.dof != (uint32_t)ctx->rb.dof || h.hidden != (uint32_t)kMlpHidden || h.layers != (uint32_t)kMlpLayers ||
+      h.count != mlp_compact_count(ctx->rb.dof))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: network shape differs from the robot's");
+  const size_t n = (size_t)h.count;
+  if (buf.size() != sizeof(h) + 3 * n * 4 + 4) return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: bad size");
+  uint32_t crc;
+  memcpy(&crc, buf.data() + buf.size() - 4, 4);
+  if (crc != crc32_update(0u, buf.data(), buf.size() - 4))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_load: checksum mismatch");
+  DeviceGuard g(ctx->device);
+  if (!ctx->mlp || mlp_dof(ctx->mlp) != ctx->rb.dof) {
+    if (ctx->mlp) {
+      cudaStreamSynchronize(ctx->stream);
+      mlp_destroy(ctx->mlp);
+      ctx->mlp = nullptr;
+    }
+    cudaError_t e = mlp_create(&ctx->mlp, ctx->rb.dof);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_load");
+  }
+  std::vector<float> p(n), m(n), v(n);
+  memcpy(p.data(), buf.data() + sizeof(h), n * 4);
+  memcpy(m.data(), buf.data() + sizeof(h) + n * 4, n * 4);
+  memcpy(v.data(), buf.data() + sizeof(h) + 2 * n * 4, n * 4);
+  cudaError_t e = mlp_set_state(ctx->mlp, p.data(), m.data(), v.data(), h.step, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_load");
+  return CPRRTC_OK;
+}
+
 int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, float* grads,
                     float* loss) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
@@ -1199,7 +1311,7 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: n < 0");
   if (pp->W < 2 || pp->W > CPRRTC_MAX_W || !(pp->range > 0) || !is_finite(pp->range) ||
       pp->max_rounds < 1 || pp->workers < 1 || pp->workers > kMaxWorkers || pp->max_nodes < 2 ||
-      pp->max_connect < 0 || pp->max_path < 2)
+      pp->max_connect < 0 || pp->max_path < 2 || !(pp->time_budget_ms >= 0.0) || !is_finite(pp->time_budget_ms))
     return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: bad parameters");
   if (pp->use_scene_batch && ctx->n_scenes != n)
     return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan: scene batch must hold one scene per problem");
@@ -1233,6 +1345,7 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   a.max_connect = pp->max_connect;
   a.max_path = pp->max_path;
   a.seed = pp->seed;
+  a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
   a.work_counters = ctx->d_work;
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
@@ -1380,7 +1493,7 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   if (n < 0) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: n < 0");
   if (pp->W < 2 || pp->W > CPRRTC_MAX_W || !(pp->range > 0) || !is_finite(pp->range) ||
       pp->max_rounds < 1 || pp->workers < 1 || pp->workers > kMaxWorkers || pp->max_nodes < 2 ||
-      pp->max_connect < 0 || pp->max_path < 2)
+      pp->max_connect < 0 || pp->max_path < 2 || !(pp->time_budget_ms >= 0.0) || !is_finite(pp->time_budget_ms))
     return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: bad parameters");
   if (pp->use_scene_batch && ctx->n_scenes != n)
     return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "plan_static: scene batch must hold one scene per problem");
@@ -1421,6 +1534,7 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   a.max_connect = pp->max_connect;
   a.max_path = pp->max_path;
   a.seed = pp->seed;
+  a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;
@@ -1649,6 +1763,7 @@ PlanArgs batch_base(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, int n) {
   a.max_connect = pp->max_connect;
   a.max_path = pp->max_path;
   a.seed = pp->seed;
+  a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
   a.scene_obs = ctx->d_batch_obs;
   a.scenes = ctx->d_batch_tab;
   a.work_counters = ctx->d_work;
@@ -1657,7 +1772,8 @@ PlanArgs batch_base(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, int n) {
 
 int check_batch_params(cprrtc_ctx* ctx, const cprrtc_plan_params* pp) {
   if (!pp || !(pp->range > 0) || !is_finite(pp->range) || pp->max_rounds < 1 || pp->max_nodes < 2 ||
-      pp->max_connect < 0 || pp->max_path < 2 || pp->workers < 1 || pp->workers > kMaxWorkers)
+      pp->max_connect < 0 || pp->max_path < 2 || pp->workers < 1 || pp->workers > kMaxWorkers ||
+      !(pp->time_budget_ms >= 0.0) || !is_finite(pp->time_budget_ms))
     return fail(ctx, CPRRTC_E_INVALID_ARG, "batch: bad parameters");
   return CPRRTC_OK;
 }

@@ -48,6 +48,7 @@ struct PlanArgs {
   float range;
   int W, max_rounds, workers, max_nodes, max_connect, max_path;
   uint32_t seed;
+  unsigned long long budget_ns;  // per-problem device-time budget (0: none)
   const float4* scene_obs;  // scene batch: obstacle stream
   const int4* scenes;       // [n] {float4 offset, n_sph, n_box, n_cap}; null: shared scene
   int max_scene_f4;         // largest scene, float4 slots
@@ -117,6 +118,10 @@ int mlp_dof(const MlpDev* d);
 int mlp_step(const MlpDev* d);
 cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s);
 cudaError_t mlp_get_params(MlpDev* d, float* host, cudaStream_t s);
+// full optimiser state in the compact layout (checkpoints)
+cudaError_t mlp_get_state(MlpDev* d, float* params, float* m, float* v, int* step, cudaStream_t s);
+cudaError_t mlp_set_state(MlpDev* d, const float* params, const float* m, const float* v, int step,
+                          cudaStream_t s);
 cudaError_t mlp_init(MlpDev* d, uint64_t seed, cudaStream_t s);
 cudaError_t mlp_infer(MlpDev* d, const float* q, int ldq, int rows, float* Y, cudaStream_t s);
 cudaError_t mlp_infer_motions(MlpDev* d, const float* q0, const float* q1, int n, int W, float* Y,

@@ -469,9 +469,8 @@ static void compact_dims(int dof, int l, int& rows, int& cols) {
   cols = l == 0 ? dof : kIn[l];
 }
 
-// Sets the parameters from a host array in the compact layout (padding stays zero) and
-// resets the optimiser state.
-cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s) {
+// The padded device layout of a host array in the compact layout (padding zero).
+static std::vector<float> from_compact(const MlpDev* d, const float* host) {
   std::vector<float> p(mlp_param_count(), 0.f);
   const float* src = host;
   for (int l = 0; l < kMlpLayers; ++l) {
@@ -483,14 +482,47 @@ cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s) {
     float* b = w + (size_t)kOut[l] * kIn[l];
     for (int r = 0; r < rows; ++r) b[r] = *src++;
   }
+  return p;
+}
+
+// Sets parameters, Adam moments (null: zero) and step from host arrays in the compact layout.
+static cudaError_t set_state(MlpDev* d, const float* params, const float* m, const float* v, int step,
+                             cudaStream_t s) {
   const size_t n = mlp_param_count();
+  const std::vector<float> p = from_compact(d, params);
   cudaError_t e = cudaMemcpyAsync(d->p, p.data(), n * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d->m, 0, n * 4, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d->v, 0, n * 4, s);
+  std::vector<float> mm, vv;
+  if (e == cudaSuccess) {
+    if (m) {
+      mm = from_compact(d, m);
+      e = cudaMemcpyAsync(d->m, mm.data(), n * 4, cudaMemcpyHostToDevice, s);
+    } else {
+      e = cudaMemsetAsync(d->m, 0, n * 4, s);
+    }
+  }
+  if (e == cudaSuccess) {
+    if (v) {
+      vv = from_compact(d, v);
+      e = cudaMemcpyAsync(d->v, vv.data(), n * 4, cudaMemcpyHostToDevice, s);
+    } else {
+      e = cudaMemsetAsync(d->v, 0, n * 4, s);
+    }
+  }
   if (e == cudaSuccess) e = refresh_bf16(d, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  d->step = 0;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host vectors must outlive the copies
+  d->step = step;
   return e;
+}
+
+// Sets the parameters from a host array in the compact layout (padding stays zero) and
+// resets the optimiser state.
+cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s) {
+  return set_state(d, host, nullptr, nullptr, 0, s);
+}
+
+cudaError_t mlp_set_state(MlpDev* d, const float* params, const float* m, const float* v, int step,
+                          cudaStream_t s) {
+  return set_state(d, params, m, v, step, s);
 }
 
 // Copies a padded device parameter-shaped array (parameters or gradients) to a host array
@@ -514,6 +546,14 @@ static cudaError_t to_compact(MlpDev* d, const float* dev, float* host, cudaStre
 }
 
 cudaError_t mlp_get_params(MlpDev* d, float* host, cudaStream_t s) { return to_compact(d, d->p, host, s); }
+
+cudaError_t mlp_get_state(MlpDev* d, float* params, float* m, float* v, int* step, cudaStream_t s) {
+  cudaError_t e = to_compact(d, d->p, params, s);
+  if (e == cudaSuccess) e = to_compact(d, d->m, m, s);
+  if (e == cudaSuccess) e = to_compact(d, d->v, v, s);
+  *step = d->step;
+  return e;
+}
 
 // He-normal weights (the last layer scaled by 0.1: the corrections it predicts are small),
 // zero biases; Gaussian draws from a splitmix64 stream with the Box-Muller transform.

@@ -50,7 +50,8 @@ struct PlanShared {
   long long wp[kMaxWorkers];   // waypoints validated by each warp
   long long wproj[kMaxWorkers];
   long long wcc[kMaxWorkers];
-  long long t_start;           // globaltimer at the CTA's start
+  long long t_start;           // globaltimer at the problem's start
+  int stop;                    // 1 once the problem's time budget is spent
   // each warp's configurations, identical across its lanes: kept here instead of in every
   // lane's registers: [0] current chain node, [1] target, [2] motion end, [3] scratch
   float cfg[kMaxWorkers][4][8];
@@ -237,6 +238,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     sh->t_start = t;
+    sh->stop = 0;
   }
 
   const size_t wd = (size_t)W * dof;
@@ -361,9 +363,16 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       cnt0 = min(cnt0 + n_add0, a.max_nodes);
       cnt1 = min(cnt1 + n_add1, a.max_nodes);
     }
+    // optional time budget: decided by one thread, seen by all after the barrier
+    if (a.budget_ns && threadIdx.x == 0) {
+      long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if ((unsigned long long)(t - sh->t_start) > a.budget_ns) sh->stop = 1;
+    }
     // the appended nodes are visible to every warp's next nearest-neighbour scan, and the
     // flags may be overwritten
     __syncthreads();
+    if (sh->stop) break;
     // next motion of the chain
     if (dst >= 0) {
       last = dst;

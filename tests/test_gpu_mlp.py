@@ -274,3 +274,49 @@ def test_validate_ws_full_size(torch_cuda, oracle_mod, setup, trained):
             assert ff == ws["first_fail"][m], (m, ff, ws["first_fail"][m])
     print("full size: plain projected", int(plain_ok.sum()), "warm", int(ws_ok.sum()),
           "warm used", int(used.sum()))
+
+
+def test_checkpoint_roundtrip_and_corruption(torch_cuda, oracle_mod, setup, tmp_path):
+    """Save / load restores parameters, Adam moments and step exactly (continued training
+    from the loaded state equals continued training from the saved one); the file's CRC-32
+    agrees with zlib's; a flipped byte, a wrong robot and a truncated file are rejected."""
+    import zlib
+    from paper_2505_06791_gb300.capi import Context, CprrtcError
+    torch = torch_cuda
+    rb, sc, c = setup
+    ctx = make_ctx(rb, sc, c)
+    ctx.mlp_init(4)
+    rng = np.random.default_rng(8)
+    q = S.uniform_configs(rb, 2048, 44).astype(np.float32)
+    t = (q + rng.normal(0, 0.2, q.shape)).astype(np.float32)
+    dq, dt = torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda()
+    ctx.mlp_train(dq, dt, batch=256, epochs=2, lr=1e-3, seed=1)
+    path = str(tmp_path / "net.ckpt")
+    ctx.mlp_save(path)
+    blob = open(path, "rb").read()
+    assert blob[:8] == b"CPRMLP01"
+    assert int.from_bytes(blob[-4:], "little") == zlib.crc32(blob[:-4])
+    saved = ctx.mlp_get_params()
+    # a single-batch epoch is deterministic (one gradient, no split across batches)
+    ref = ctx.mlp_train(dq[:256], dt[:256], batch=256, epochs=1, lr=1e-3, seed=2)
+    after_ref = ctx.mlp_get_params()
+    other = make_ctx(rb, sc, c)
+    other.mlp_load(path)
+    np.testing.assert_array_equal(other.mlp_get_params(), saved)
+    got = other.mlp_train(dq[:256], dt[:256], batch=256, epochs=1, lr=1e-3, seed=2)
+    np.testing.assert_allclose(got, ref, rtol=1e-5)
+    np.testing.assert_allclose(other.mlp_get_params(), after_ref, rtol=1e-4, atol=1e-6)
+    bad = bytearray(blob)
+    bad[100] ^= 0x40
+    open(path, "wb").write(bytes(bad))
+    with pytest.raises(CprrtcError):
+        other.mlp_load(path)
+    open(path, "wb").write(blob[:-10])
+    with pytest.raises(CprrtcError):
+        other.mlp_load(path)
+    open(path, "wb").write(blob)
+    six = make_ctx(S.make_arm6(1), sc, S.roll_pitch(20))
+    with pytest.raises(CprrtcError):
+        six.mlp_load(path)
+    for x in (ctx, other, six):
+        x.close()

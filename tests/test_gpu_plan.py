@@ -136,3 +136,39 @@ def test_plan_argument_errors(torch_cuda, oracle_mod):
     out = ctx.plan(q, q, ctx.plan_params(W=8, workers=2))
     assert (out["path_len"] >= 2).all()
     ctx.close()
+
+
+def test_plan_time_budget_and_allocation_failure(torch_cuda, oracle_mod):
+    """A per-problem time budget stops problems early (fewer rounds, no path unless they
+    connected); a tree allocation beyond device memory is reported as E_OOM, not a fault."""
+    from paper_2505_06791_gb300.capi import CprrtcError
+    torch = torch_cuda
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 8, 950)
+    ctx = ctx_for(rb, c)
+    free = ctx.plan_params(range_=0.05, W=32, max_rounds=4000, workers=8, seed=3)
+    capped = ctx.plan_params(range_=0.05, W=32, max_rounds=4000, workers=8, seed=3,
+                             time_budget_ms=0.5)
+    a = run_plan(torch, ctx, scenes, start, goal, free)
+    b = run_plan(torch, ctx, None, start, goal, capped)
+    assert (b["rounds"] <= a["rounds"]).all()
+    assert (b["rounds"] < a["rounds"]).any()
+    stopped = b["rounds"] < a["rounds"]
+    assert (b["path_len"][stopped] == 0).all()
+    same = ~stopped
+    assert np.array_equal(a["path_len"][same], b["path_len"][same])
+    # 2 trees x 2^27 nodes x 64 waypoints x 7 joints x 4 bytes of edges: 481 GB
+    huge = ctx.plan_params(range_=0.3, W=64, max_rounds=10, workers=8, max_nodes=1 << 27,
+                           seed=1, use_scene_batch=False)
+    with pytest.raises(CprrtcError) as err:
+        run_plan(torch, ctx, None, start[:1], goal[:1], huge)
+    assert err.value.code == -4  # CPRRTC_E_OOM
+    # the context stays usable after the failed allocation
+    again = run_plan(torch, ctx, scenes, start, goal, free)
+    for k in ("path_len", "rounds", "waypoints"):
+        assert np.array_equal(again[k], a[k]), k
+    bad = ctx.plan_params(range_=0.3, time_budget_ms=-1.0, use_scene_batch=False)
+    with pytest.raises(CprrtcError) as err:
+        run_plan(torch, ctx, None, start[:1], goal[:1], bad)
+    assert err.value.code == -1  # CPRRTC_E_INVALID_ARG
+    ctx.close()
