@@ -262,6 +262,47 @@ __device__ __forceinline__ bool hit_obstacle(const SceneDev& sc, const float4* _
   return hit_capsule(cx, cy, cz, r, k[0], k[sc.n_cap]);
 }
 
+// One obstacle's rows, read once from shared memory for the repeated tests of the chain
+// walk (kind: 0 sphere, 1 box, 2 capsule; the same predicates as `hit_obstacle`).
+struct ObsView {
+  int kind;
+  float4 a, b, c, d;
+};
+
+__device__ __forceinline__ ObsView load_obstacle(const SceneDev& sc,
+                                                 const float4* __restrict__ obs, int o) {
+  ObsView v;
+  v.b = v.c = v.d = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (o < sc.n_sph) {
+    v.kind = 0;
+    v.a = obs[o];
+    return v;
+  }
+  o -= sc.n_sph;
+  if (o < sc.n_box) {
+    const float4* b = obs + sc.n_sph + o;
+    v.kind = 1;
+    v.a = b[0];
+    v.b = b[sc.n_box];
+    v.c = b[2 * sc.n_box];
+    v.d = b[3 * sc.n_box];
+    return v;
+  }
+  o -= sc.n_box;
+  const float4* k = obs + sc.n_sph + 4 * sc.n_box + o;
+  v.kind = 2;
+  v.a = k[0];
+  v.b = k[sc.n_cap];
+  return v;
+}
+
+__device__ __forceinline__ bool hit_view(const ObsView& v, float cx, float cy, float cz,
+                                         float r) {
+  if (v.kind == 0) return hit_sphere(cx, cy, cz, r, v.a);
+  if (v.kind == 1) return hit_box(cx, cy, cz, r, v.a, v.b, v.c, v.d);
+  return hit_capsule(cx, cy, cz, r, v.a, v.b);
+}
+
 // One DH frame of a lane's waypoint: axes x, y, z and origin p (world).
 struct Frame {
   float x0, x1, x2, y0, y1, y2, z0, z1, z2, p0, p1, p2;
@@ -505,35 +546,42 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
 #pragma unroll
       for (int s = 0; s < WPL; ++s) F[s].world(b.x, b.y, b.z, bc[s][0], bc[s][1], bc[s][2]);
       const int s_lo = S.foff[f], s_hi = S.foff[f + 1];
-      for (int j = 0; j < n_cand; ++j) {
-        const unsigned e = S.cand[j];
-        if (!((e >> (20 + f)) & 1u)) continue;
-        const int o = (int)(e & 0xFFFFFu);
-        bool near[WPL];
-        bool any = false;
-#pragma unroll
-        for (int s = 0; s < WPL; ++s) {
-          near[s] = act[s] && !hit[s] && hit_obstacle(sc, obs, o, bc[s][0], bc[s][1], bc[s][2], b.w);
-          any |= near[s];
-        }
-        work.count_test(sc, o, n_act);
-        const unsigned nb = __ballot_sync(kFull, any);
-        if (!nb) continue;
-        for (int si = s_lo; si < s_hi; ++si) {
-          const float4 l = S.sph[si];
+      // candidates of this frame, 32 at a time: one ballot finds them, the entries travel
+      // by shuffle, in increasing list order
+      for (int g = 0; g < n_cand; g += 32) {
+        const unsigned eg = g + lane < n_cand ? S.cand[g + lane] : 0u;
+        unsigned fm = __ballot_sync(kFull, (eg >> (20 + f)) & 1u);
+        while (fm) {
+          const unsigned e = __shfl_sync(kFull, eg, __ffs(fm) - 1);
+          fm &= fm - 1u;
+          const int o = (int)(e & 0xFFFFFu);
+          const ObsView ov = load_obstacle(sc, obs, o);
+          bool near[WPL];
+          bool any = false;
 #pragma unroll
           for (int s = 0; s < WPL; ++s) {
-            if (near[s]) {
-              float cx, cy, cz;
-              F[s].world(l.x, l.y, l.z, cx, cy, cz);
-              hit[s] |= hit_obstacle(sc, obs, o, cx, cy, cz, l.w);
+            near[s] = act[s] && !hit[s] && hit_view(ov, bc[s][0], bc[s][1], bc[s][2], b.w);
+            any |= near[s];
+          }
+          work.count_test(sc, o, n_act);
+          const unsigned nb = __ballot_sync(kFull, any);
+          if (!nb) continue;
+          for (int si = s_lo; si < s_hi; ++si) {
+            const float4 l = S.sph[si];
+#pragma unroll
+            for (int s = 0; s < WPL; ++s) {
+              if (near[s]) {
+                float cx, cy, cz;
+                F[s].world(l.x, l.y, l.z, cx, cy, cz);
+                hit[s] |= hit_view(ov, cx, cy, cz, l.w);
+              }
             }
           }
-        }
-        int near_cnt = 0;
+          int near_cnt = 0;
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) near_cnt += __popc(__ballot_sync(kFull, near[s]));
-        work.count_fine(sc, o, near_cnt * (s_hi - s_lo));
+          for (int s = 0; s < WPL; ++s) near_cnt += __popc(__ballot_sync(kFull, near[s]));
+          work.count_fine(sc, o, near_cnt * (s_hi - s_lo));
+        }
       }
       if (any_hit) {
         bool h = false;
