@@ -315,7 +315,8 @@ typedef struct {
  *              did not fit in max_path);
  *   path       [n][max_path][dof] nodes from start to goal;
  *   path_edges [n][max_path-1][W][dof] the validated (projected) motion between path
- *              nodes j and j+1, waypoint 0 at node j;
+ *              nodes j and j+1, waypoint 0 at node j (rows of path and path_edges
+ *              beyond path_len are not written);
  *   rounds     [n] rounds run; waypoints [n] waypoints validated (W per motion checked);
  *   plan_ms    [n] device time of the problem's CTA, ms;
  *   work       [n][2] work evaluated: Alg. 1 waypoint updates (iterations x (W-1) summed

@@ -316,14 +316,16 @@ float round_up(double x) {
 // Packs obstacles into the float4 stream the kernels read. Each primitive kind is sorted
 // along a Morton curve (neighbours in the stream are neighbours in space; collision results
 // do not depend on the order) and stored as component arrays: spheres [n] {x,y,z,r}; boxes
-// 4 x [n]: {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, 0}; capsules 2 x [n]:
-// {p0, r} {p1 - p0, 1/|p1-p0|^2}. Then, per chunk of 32 consecutive obstacles, an
-// axis-aligned box containing every obstacle of the chunk (rounded outward to FP32).
+// 4 x [n]: {c, hx} {R col 0, hy} {R col 1, hz} {R col 2, bounding radius}; capsules 2 x [n]:
+// {p0, r} {p1 - p0, 1/|p1-p0|^2}. Then, per chunk (kChunk consecutive obstacles of one
+// kind), an axis-aligned box containing every obstacle of the chunk (rounded outward to
+// FP32).
 int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
                    const cprrtc_obs_box* box, int n_box, const cprrtc_obs_capsule* cap, int n_cap,
                    std::vector<float4>& v) {
   const int n_obs = n_sph + n_box + n_cap;
-  const int n_chunks = (n_obs + kChunk - 1) / kChunk;
+  const SceneDev layout{nullptr, n_sph, n_box, n_cap};
+  const int n_chunks = layout.n_chunks();
   const size_t s0 = v.size();
   v.resize(s0 + (size_t)n_sph + 4 * (size_t)n_box + 2 * (size_t)n_cap + 2 * (size_t)n_chunks);
   float4* out = v.data() + s0;
@@ -359,7 +361,10 @@ int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
     bx[j] = make_float4((float)b.c[0], (float)b.c[1], (float)b.c[2], (float)b.h[0]);
     bx[n_box + j] = make_float4((float)b.R[0], (float)b.R[3], (float)b.R[6], (float)b.h[1]);
     bx[2 * n_box + j] = make_float4((float)b.R[1], (float)b.R[4], (float)b.R[7], (float)b.h[2]);
-    bx[3 * n_box + j] = make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8], 0.f);
+    // w: radius of a ball about the centre containing the box (padded beyond FP32 error)
+    const double rbox = std::sqrt(b.h[0] * b.h[0] + b.h[1] * b.h[1] + b.h[2] * b.h[2]);
+    bx[3 * n_box + j] = make_float4((float)b.R[2], (float)b.R[5], (float)b.R[8],
+                                    round_up(rbox * (1.0 + 1e-6) + 1e-6));
     std::array<double, 6> a;
     for (int r = 0; r < 3; ++r) {  // world half-extent along axis r: sum_k |R[r][k]| h_k
       const double ext = std::fabs(b.R[3 * r]) * b.h[0] + std::fabs(b.R[3 * r + 1]) * b.h[1] +
@@ -397,7 +402,7 @@ int pack_obstacles(cprrtc_ctx* ctx, const cprrtc_obs_sphere* sph, int n_sph,
   float4* cb = cp + 2 * n_cap;
   for (int ch = 0; ch < n_chunks; ++ch) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int o = ch * kChunk; o < std::min(n_obs, (ch + 1) * kChunk); ++o)
+    for (int o = layout.chunk_first(ch); o < layout.chunk_end(ch); ++o)
       for (int k = 0; k < 3; ++k) {
         lo[k] = std::min(lo[k], aabb[o][k]);
         hi[k] = std::max(hi[k], aabb[o][3 + k]);

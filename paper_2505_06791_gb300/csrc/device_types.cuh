@@ -40,16 +40,40 @@ struct RobotDev {
 
 // Obstacles as one float4 stream, component arrays per primitive so that lanes reading
 // consecutive obstacles read consecutive float4s: spheres [n_sph] {x,y,z,rho}; boxes
-// 4 arrays of [n_box]: {cx,cy,cz,hx} {col0, hy} {col1, hz} {col2, 0} where col_k is column
-// k of R (box axis k); capsules 2 arrays of [n_cap]: {p0, rc} {u = p1 - p0, 1/|u|^2}.
-// After the obstacle arrays, every chunk of 32 consecutive obstacles (in the order spheres,
-// boxes, capsules) has an axis-aligned box containing all of them: 2 float4 {min, -} {max, -}.
-constexpr int kChunk = 32;
+// 4 arrays of [n_box]: {cx,cy,cz,hx} {col0, hy} {col1, hz} {col2, rb} where col_k is column
+// k of R (box axis k) and rb the radius of a ball about the centre that contains the box;
+// capsules 2 arrays of [n_cap]: {p0, rc} {u = p1 - p0, 1/|u|^2}.
+// After the obstacle arrays come chunk boxes: the obstacles of each kind, in stream order,
+// are cut into chunks of kChunk (a kind's last chunk may be shorter; no chunk mixes kinds),
+// sphere chunks first, then box and capsule chunks; each chunk has an axis-aligned box
+// containing its obstacles: 2 float4 {min, -} {max, -}.
+constexpr int kChunk = 8;
 struct SceneDev {
   const float4* obs;
   int n_sph, n_box, n_cap;
   __host__ __device__ int n_obs() const { return n_sph + n_box + n_cap; }
-  __host__ __device__ int n_chunks() const { return (n_obs() + kChunk - 1) / kChunk; }
+  __host__ __device__ int chunks_sph() const { return (n_sph + kChunk - 1) / kChunk; }
+  __host__ __device__ int chunks_box() const { return (n_box + kChunk - 1) / kChunk; }
+  __host__ __device__ int n_chunks() const {
+    return chunks_sph() + chunks_box() + (n_cap + kChunk - 1) / kChunk;
+  }
+  // kind of chunk c: 0 spheres, 1 boxes, 2 capsules
+  __host__ __device__ int chunk_kind(int c) const {
+    return c < chunks_sph() ? 0 : c < chunks_sph() + chunks_box() ? 1 : 2;
+  }
+  // obstacles [chunk_first(c), chunk_end(c)) of chunk c
+  __host__ __device__ int chunk_first(int c) const {
+    const int k = chunk_kind(c);
+    return k == 0 ? c * kChunk
+                  : k == 1 ? n_sph + (c - chunks_sph()) * kChunk
+                           : n_sph + n_box + (c - chunks_sph() - chunks_box()) * kChunk;
+  }
+  __host__ __device__ int chunk_end(int c) const {
+    const int k = chunk_kind(c);
+    const int end = k == 0 ? n_sph : k == 1 ? n_sph + n_box : n_obs();
+    const int f = chunk_first(c) + kChunk;
+    return f < end ? f : end;
+  }
   __host__ __device__ int chunk_off() const { return n_sph + 4 * n_box + 2 * n_cap; }
   __host__ __device__ int n_float4() const { return chunk_off() + 2 * n_chunks(); }
 };

@@ -373,6 +373,62 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Order-preserving map of non-NaN floats to signed integers (negative floats have their
+// magnitude bits flipped), so that one integer warp reduction finds a float minimum or
+// maximum.
+__device__ __forceinline__ int float_key(float x) {
+  const int i = __float_as_int(x);
+  return i < 0 ? i ^ 0x7fffffff : i;
+}
+__device__ __forceinline__ float key_float(int k) {
+  return __int_as_float(k < 0 ? k ^ 0x7fffffff : k);
+}
+__device__ __forceinline__ float warp_min_exact(float v) {
+  return key_float(__reduce_min_sync(kFull, float_key(v)));
+}
+__device__ __forceinline__ float warp_max_exact(float v) {
+  return key_float(__reduce_max_sync(kFull, float_key(v)));
+}
+
+// Frames (bits of fmask) whose swept bound sbnd[f] = {centre, radius} the ball test `hit`
+// accepts; the tests are independent, unrolled over the frames.
+template <class Hit>
+__device__ __forceinline__ unsigned frames_touched(const float4* sbnd, unsigned fmask, Hit hit) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int f = 0; f <= kMaxDof; ++f)
+    if ((fmask >> f) & 1u) {
+      if (hit(sbnd[f])) m |= 1u << f;
+    }
+  return m;
+}
+
+// The same predicates as `hit_view` with the swept bounds as balls, one obstacle per lane;
+// `box_tests` counts the exact box tests made after the containing-ball test.
+__device__ __forceinline__ unsigned swept_mask(const ObsView& v, const float4* sbnd,
+                                               unsigned fmask, int& box_tests) {
+  if (v.kind == 0)
+    return frames_touched(sbnd, fmask,
+                          [&](float4 b) { return hit_sphere(b.x, b.y, b.z, b.w, v.a); });
+  if (v.kind == 1) {
+    // the ball containing the box first; the box test only for the frames that ball touches
+    const float4 ball = make_float4(v.a.x, v.a.y, v.a.z, v.d.w);
+    unsigned m = frames_touched(sbnd, fmask,
+                                [&](float4 b) { return hit_sphere(b.x, b.y, b.z, b.w, ball); });
+    unsigned out = 0u;
+    while (m) {
+      const int f = __ffs(m) - 1;
+      m &= m - 1u;
+      const float4 b = sbnd[f];
+      if (hit_box(b.x, b.y, b.z, b.w, v.a, v.b, v.c, v.d)) out |= 1u << f;
+      ++box_tests;
+    }
+    return out;
+  }
+  return frames_touched(sbnd, fmask,
+                        [&](float4 b) { return hit_capsule(b.x, b.y, b.z, b.w, v.a, v.b); });
+}
+
 // FK + CC of waypoints [i0, W) of the warp's segment (lane l holds waypoints l + 32 s in
 // q). Returns the smallest colliding waypoint, or -1. With `any_hit`, returns as soon as
 // some waypoint is known to collide (the index is then a colliding waypoint, not
@@ -425,6 +481,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
   if (n_act == 0 || n_obs == 0) return -1;
 
   // ---- level 1: swept frame bounds over the segment ----
+  unsigned fmask = 0u;  // frames that carry spheres (warp-uniform)
   {
     Frame F[WPL];
 #pragma unroll
@@ -437,6 +494,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       }
       const float4 b = S.bnd[f];
       if (b.w < 0.f) continue;  // no spheres on this frame (warp-uniform)
+      fmask |= 1u << f;
       float lo0 = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
       float hi0 = -INFINITY, hi1 = -INFINITY, hi2 = -INFINITY;
       float c[WPL][3];
@@ -448,9 +506,9 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
           hi0 = fmaxf(hi0, c[s][0]); hi1 = fmaxf(hi1, c[s][1]); hi2 = fmaxf(hi2, c[s][2]);
         }
       }
-      const float m0 = 0.5f * (warp_min(lo0) + warp_max(hi0));
-      const float m1 = 0.5f * (warp_min(lo1) + warp_max(hi1));
-      const float m2 = 0.5f * (warp_min(lo2) + warp_max(hi2));
+      const float m0 = 0.5f * (warp_min_exact(lo0) + warp_max_exact(hi0));
+      const float m1 = 0.5f * (warp_min_exact(lo1) + warp_max_exact(hi1));
+      const float m2 = 0.5f * (warp_min_exact(lo2) + warp_max_exact(hi2));
       float r2 = 0.f;
 #pragma unroll
       for (int s = 0; s < WPL; ++s) {
@@ -459,7 +517,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
           r2 = fmaxf(r2, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
         }
       }
-      const float rad = sqrtf(warp_max(r2)) * 1.000001f + b.w + 1e-5f;
+      const float rad = sqrtf(warp_max_exact(r2)) * 1.000001f + b.w + 1e-5f;
       if (lane == 0) S.sbnd[f] = make_float4(m0, m1, m2, rad);
     }
     work.chains += n_act;
@@ -487,35 +545,56 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
         if (ch < n_chunks) {
           const float4* cbx = obs + sc.chunk_off() + 2 * ch;
           const float4 lo = cbx[0], hi = cbx[1];
-          for (int f = 0; f <= dof && !hit_chunk; ++f) {
-            if (S.bnd[f].w < 0.f) continue;
-            const float4 b = S.sbnd[f];
-            const float e0 = fmaxf(fmaxf(lo.x - b.x, b.x - hi.x), 0.f);
-            const float e1 = fmaxf(fmaxf(lo.y - b.y, b.y - hi.y), 0.f);
-            const float e2 = fmaxf(fmaxf(lo.z - b.z, b.z - hi.z), 0.f);
-            const float rr = b.w + 1e-5f;
-            hit_chunk = fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < rr * rr;
-          }
+          hit_chunk = frames_touched(S.sbnd, fmask, [&](float4 b) {
+                        const float e0 = fmaxf(fmaxf(lo.x - b.x, b.x - hi.x), 0.f);
+                        const float e1 = fmaxf(fmaxf(lo.y - b.y, b.y - hi.y), 0.f);
+                        const float e2 = fmaxf(fmaxf(lo.z - b.z, b.z - hi.z), 0.f);
+                        const float rr = b.w + 1e-5f;
+                        return fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < rr * rr;
+                      }) != 0u;
         }
         near = __ballot_sync(kFull, hit_chunk);
         work.p_box += (unsigned)(rb.bound_count * min(32, n_chunks - cb));
         cb += 32;
         continue;
       }
-      const int o0 = (cb - 32 + __ffs(near) - 1) * kChunk;
-      near &= near - 1u;
-      const int o = o0 + lane;
+      // up to 32 / kChunk touched chunks of one kind, kChunk lanes each (one code path)
+      const int base = cb - 32;  // chunk of bit 0 of `near`
+      const int kind = sc.chunk_kind(base + __ffs(near) - 1);
+      const int cs = sc.chunks_sph(), cbx = sc.chunks_box();
+      const int k_c1 = kind == 0 ? cs : kind == 1 ? cs + cbx : n_chunks;  // kind's chunk end
+      const int k_o0 = kind == 0 ? 0 : kind == 1 ? sc.n_sph : sc.n_sph + sc.n_box;
+      const int k_o1 = kind == 0 ? sc.n_sph : kind == 1 ? sc.n_sph + sc.n_box : n_obs;
+      const int k_c0 = kind == 0 ? 0 : kind == 1 ? cs : cs + cbx;
+      // bits of `near` for chunks of this kind (chunk end relative to base, at most 32)
+      const int rel_end = k_c1 - base;
+      const unsigned kmask = near & (rel_end >= 32 ? kFull : (1u << rel_end) - 1u);
+      unsigned m = kmask;
+      int my_c = -1;
+#pragma unroll
+      for (int t = 0; t < 32 / kChunk; ++t) {
+        const int c = base + __ffs(m) - 1;
+        if (m && t == lane / kChunk) my_c = c;
+        m &= m - 1u;
+      }
+      near &= ~(kmask ^ m);  // the chunks taken
+      int o = -1;
       unsigned mask = 0u;
-      if (o < n_obs) {
-        for (int f = 0; f <= dof; ++f) {
-          const float4 b = S.sbnd[f];
-          if (S.bnd[f].w >= 0.f && hit_obstacle(sc, obs, o, b.x, b.y, b.z, b.w)) mask |= 1u << f;
-        }
+      if (my_c >= 0) o = k_o0 + (my_c - k_c0) * kChunk + lane % kChunk;
+      const bool valid = o >= 0 && o < k_o1;
+      int box_tests = 0;
+      if (valid) mask = swept_mask(load_obstacle(sc, obs, o), S.sbnd, fmask, box_tests);
+      {  // balls (spheres, and the balls containing boxes) or capsules against every bound
+        const unsigned tested = (unsigned)(__popc(__ballot_sync(kFull, valid)) * rb.bound_count);
+        if (kind == 2)
+          work.p_cap += tested;
+        else
+          work.p_sph += tested;
+        if (kind == 1) work.p_box += __reduce_add_sync(kFull, (unsigned)box_tests);
       }
       const unsigned bal = __ballot_sync(kFull, mask != 0u);
       if (mask) S.cand[n_cand + __popc(bal & ((1u << lane) - 1u))] = (unsigned)o | (mask << 20);
       n_cand += __popc(bal);
-      work.add_tests(sc, o0, min(o0 + kChunk, n_obs), rb.bound_count);
     }
     __syncwarp();
     if (n_cand == 0) continue;

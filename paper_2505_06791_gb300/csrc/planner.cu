@@ -84,16 +84,10 @@ __device__ __forceinline__ int nearest_warp(const float* __restrict__ nodes, int
       bi = j;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(kFull, best, o);
-    const int oi = __shfl_xor_sync(kFull, bi, o);
-    if (ob < best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
-    }
-  }
-  return bi;
+  // smallest distance, then the smallest index holding it (distances are >= 0, so their
+  // bit patterns order like the values)
+  const int kb = __reduce_min_sync(kFull, __float_as_int(best));
+  return __reduce_min_sync(kFull, __float_as_int(best) == kb ? bi : 0x7fffffff);
 }
 
 // dst[0..7] = src[0..dof) padded with zeros (lanes 0..7), then the warp synchronises.

@@ -135,3 +135,27 @@ def check_batch_paths(oracle_mod, robots, constraints, problems, scenes, start, 
             if cl <= -contact:
                 issues.append((p, j, "collision", cl))
     return checked, issues
+
+
+def assert_same_plans(a, b, keys=("path_len", "path", "rounds", "waypoints"), dofs=None,
+                      Ws=None):
+    """Two planner outputs (dicts of numpy arrays) agree: per-problem fields exactly, and
+    the path rows (and path_edges motions) that path_len says were written, over problem
+    p's dofs[p] joints and Ws[p] waypoints when given; rows beyond path_len and padding are
+    not part of the result."""
+    L = np.asarray(a["path_len"])
+    for k in keys:
+        if k in ("path", "path_edges"):
+            if a.get(k) is None:
+                continue
+            for p in range(len(L)):
+                n = int(L[p]) if L[p] > 0 else 0
+                d = a[k].shape[-1] if dofs is None else int(dofs[p])
+                if k == "path":
+                    x, y = a[k][p, :n, :d], b[k][p, :n, :d]
+                else:
+                    w = a[k].shape[2] if Ws is None else int(Ws[p])
+                    x, y = a[k][p, :max(n - 1, 0), :w, :d], b[k][p, :max(n - 1, 0), :w, :d]
+                assert np.array_equal(x, y), (k, p)
+        else:
+            assert np.array_equal(a[k], b[k]), k

@@ -85,9 +85,11 @@ def test_mixed_batch_paths_graph_and_tuning(torch_cuda, oracle_mod):
         ctx.batch_replay()
     stream.synchronize()
     replay = to_np(out)
-    for k in ("path_len", "path", "rounds", "waypoints", "work"):
-        assert np.array_equal(first[k], second[k]), k
-        assert np.array_equal(first[k], replay[k]), k
+    keys = ("path_len", "path", "path_edges", "rounds", "waypoints", "work")
+    dofs = [robots[pr[0]].dof for pr in probs]
+    Ws = [pr[3] for pr in probs]
+    PB.assert_same_plans(first, second, keys, dofs, Ws)
+    PB.assert_same_plans(first, replay, keys, dofs, Ws)
     checked, issues = PB.check_batch_paths(oracle_mod, robots, cons, probs, scenes, start, goal,
                                            first, 0.3)
     assert not issues, issues[:10]
@@ -96,8 +98,7 @@ def test_mixed_batch_paths_graph_and_tuning(torch_cuda, oracle_mod):
         tuned = ctx.autotune_batch(probs, s, g, prm, trial_rounds=5)
         again = to_np(ctx.plan_batch(probs, s, g, prm, tuning=tuned, edges=True))
     stream.synchronize()
-    for k in ("path_len", "path", "rounds", "waypoints", "work"):
-        assert np.array_equal(first[k], again[k]), k
+    PB.assert_same_plans(first, again, keys, dofs, Ws)
     ctx.close()
 
 

@@ -103,8 +103,7 @@ def test_config5_batch_full_size(torch_cuda, oracle_mod):
         ctx.batch_replay()
     stream.synchronize()
     replay = to_np(out)
-    for k in ("path_len", "path", "rounds", "waypoints"):
-        assert np.array_equal(direct[k], replay[k]), k
+    PB.assert_same_plans(direct, replay, dofs=[robots[pr[0]].dof for pr in probs])
     L = direct["path_len"]
     solved = np.nonzero(L > 0)[0]
     assert len(solved) > 0.3 * len(probs), len(solved)

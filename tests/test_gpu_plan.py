@@ -63,8 +63,7 @@ def test_plan_roll_pitch_paths_are_valid_and_deterministic(torch_cuda, oracle_mo
     prm = ctx.plan_params(range_=0.3, W=32, max_rounds=600, workers=8, seed=7)
     out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
     again = run_plan(torch_cuda, ctx, None, start, goal, prm)
-    for k in ("path_len", "path", "rounds", "waypoints"):
-        assert np.array_equal(out[k], again[k]), k
+    PB.assert_same_plans(out, again)
     L = out["path_len"]
     assert (L >= 0).all()
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)

@@ -200,10 +200,10 @@ def test_work_counters_match_outputs(torch_cuda, oracle_mod):
     st, it = (parity.to_np(out[k]).astype(np.int64) for k in ("status", "iters"))
     reached = int((st != 1).sum())
     nb = len(np.unique(rb.spheres[:, 0]))
-    n_obs = len(sc.sph) + len(sc.box) + len(sc.cap)
     assert 0 < cnt[0] <= (it * 31).sum()
     assert 32 * reached <= cnt[1] <= 2 * 32 * reached
-    n_chunks = (n_obs + 31) // 32
+    # chunk boxes: 8 obstacles of one kind each
+    n_chunks = sum(-(-len(x) // 8) for x in (sc.sph, sc.box, sc.cap))
     assert cnt[3:].sum() >= reached * nb * n_chunks
     assert cnt[2] >= 32 * reached * nb
     ctx.close()
