@@ -241,8 +241,8 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   auto nodes = [&](int t) { return P.nodes + (size_t)t * MN * 8; };
   auto parent = [&](int t) { return P.parent + (size_t)t * MN; };
   auto edges = [&](int t) { return P.edges + (size_t)t * MN * wd; };
-  float* wnode = P.pend + (size_t)warp * 8;              // node produced this round
-  float* wedge = P.pend_edges + (size_t)warp * 2 * wd;   // its motion, then the hop
+  // per-warp global scratch: the closing hop's motion is kept at wedge + wd
+  float* wedge = P.pend_edges + (size_t)warp * 2 * wd;
 
   if (warp == 0) {
     float q[kMaxDof];
@@ -312,11 +312,9 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         } else {
           accept = dist2(qe, qt, dof) < dist2(cur, qt, dof);
         }
-        if (accept) {
-          add = 1;
-          store_cfg(wnode, qe, dof);
-          store_edge<WPL>(wedge, q, W, dof);
-        }
+        // an accepted node stays in qe (shared) and its motion in q (registers) until its
+        // index in the tree is known after the barrier
+        add = accept ? 1 : 0;
       }
     }
     if (lane == 0) {
@@ -343,8 +341,8 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         if (sh->padd[w] && sh->ptree[w] == ta) ++off;
       dst = count_of(ta) + off;
       if (dst < a.max_nodes) {
-        copy_warp(nodes(ta) + (size_t)dst * 8, wnode, 8);
-        copy_warp(edges(ta) + (size_t)dst * wd, wedge, (int)wd);
+        if (lane < 8) nodes(ta)[(size_t)dst * 8 + lane] = qe[lane];
+        store_edge<WPL>(edges(ta) + (size_t)dst * wd, q, W, dof);
         if (lane == 0) parent(ta)[dst] = last;
       } else {
         dst = -1;
