@@ -128,8 +128,9 @@ int cprrtc_set_stream(cprrtc_ctx* ctx, void* stream);
 /* Message for the last error on this context ("" if none). Owned by the context. */
 const char* cprrtc_last_error(const cprrtc_ctx* ctx);
 
-/* Robot kinematic table and collision spheres (Sec. III: "each thread performs forward
- * kinematics (FK) and collision checking (CC)"). 1 <= dof <= 8, 1 <= n_spheres <= 256,
+/* Robot kinematic table and collision spheres (Sec. III: every waypoint of a motion is
+ * placed by the arm's kinematic chain and its spheres tested against the obstacles).
+ * 1 <= dof <= 8, 1 <= n_spheres <= 256,
  * sphere frames in [0, dof], ee = end-effector point in frame dof (host pointers).
  * Errors: E_INVALID_ARG, E_UNSUPPORTED (sizes beyond the maxima), E_CUDA, E_OOM. */
 int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,

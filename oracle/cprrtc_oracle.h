@@ -8,7 +8,8 @@
  * It follows the paper (Hu, Wang, Christensen, "cpRRTC: GPU-Parallel RRT-Connect for
  * Constrained Motion Planning") step by step, in double precision, one motion at a time:
  *   - Sec. III: straight-line interpolation of a motion segment between q_near and q_steer,
- *     projection, then forward kinematics (FK) and collision checking (CC) per waypoint.
+ *     projection, then, per waypoint, the sphere positions from the kinematic chain (FK)
+ *     and the sphere-obstacle tests (CC).
  *   - Sec. III-A, Algorithm 1 (ParallelProject): Jacobi-style projection of all waypoints
  *     at once, a task term J^+ E_task and a smoothing term J_sm E_sm, a shared prefix
  *     `prog` of accepted waypoints, success when the whole segment is accepted.
