@@ -207,3 +207,74 @@ def test_work_counters_match_outputs(torch_cuda, oracle_mod):
     assert cnt[3:].sum() >= reached * nb * n_chunks
     assert cnt[2] >= 32 * reached * nb
     ctx.close()
+
+
+def test_culling_layouts_and_degenerate_primitives(torch_cuda, oracle_mod):
+    """Collision parity over obstacle layouts that stress the culling: each kind alone,
+    partial chunks of 8 at every kind boundary, more than 32 chunks of one kind, and
+    degenerate primitives (zero-radius spheres, zero-extent boxes, zero-length capsules)."""
+    rb = S.make_arm7(1)
+    c = S.no_constraint()
+    q0 = S.uniform_configs(rb, 48, 9100)
+    q1 = S.nearby_configs(rb, q0, 0.3, 9101)
+    layouts = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (9, 1, 17), (8, 8, 8), (33, 0, 7),
+               (0, 257, 0), (300, 20, 1)]
+    for k, (a, b, cc) in enumerate(layouts):
+        sc = S.make_scene(9200 + k, a, b, cc, sph_r=(0.02, 0.08), box_side=(0.02, 0.2),
+                          cap_len=(0.05, 0.3), cap_r=(0.01, 0.05))
+        stats, _, _ = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32)
+        print((a, b, cc), stats)
+    # degenerate primitives in the arm's workspace
+    rng = np.random.default_rng(9300)
+    sph = np.zeros((40, 4))
+    sph[:, :3] = rng.uniform(S.CUBE_LO, S.CUBE_HI, (40, 3))
+    box = np.zeros((40, 15))
+    box[:, :3] = rng.uniform(S.CUBE_LO, S.CUBE_HI, (40, 3))
+    box[:, 6:] = np.eye(3).reshape(-1)
+    box[::2, 3:6] = rng.uniform(0.0, 0.1, (20, 3)) * (rng.random((20, 3)) < 0.5)
+    cap = np.zeros((40, 7))
+    cap[:, :3] = rng.uniform(S.CUBE_LO, S.CUBE_HI, (40, 3))
+    cap[:, 3:6] = cap[:, :3]
+    cap[:, 6] = rng.uniform(0.0, 0.05, 40)
+    sc = S.Scene(S.f32(sph), S.f32(box), S.f32(cap))
+    stats, out, _ = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32)
+    print("degenerate", stats)
+
+
+def test_candidate_list_overflow(torch_cuda, oracle_mod):
+    """Thousands of small spheres packed around each motion but clear of the arm: more
+    obstacles touch a motion's swept frame bounds than one candidate list holds (512), so
+    listing and checking alternate (seen in the chain counter: more than two chains per
+    waypoint), and the obstacle stream does not fit shared memory. Every motion is free by
+    construction; the verdicts match the oracle's."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rb = S.make_arm7(1)
+    c = S.no_constraint()
+    W = 32
+    q0 = S.uniform_configs(rb, 16, 9401)
+    q1 = S.nearby_configs(rb, q0, 0.3, 9402)
+    orc = oracle_mod.Oracle(rb, S.Scene(), c)
+    centres = np.concatenate([orc.sphere_centres(x) for a, b in zip(q0, q1)
+                              for x in oracle_mod.interpolate(a, b, W)])
+    rng = np.random.default_rng(9403)
+    r_obs, clear = 0.005, rb.spheres[:, 4].max() + 0.005 + 0.01
+    pts = centres[rng.integers(0, len(centres), 120_000)]
+    d = rng.normal(size=pts.shape)
+    pts = pts + d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(0.1, 0.35, (len(pts), 1))
+    near, _ = spatial.cKDTree(centres).query(pts)
+    keep = pts[near > clear]
+    sph = np.concatenate([keep, np.full((len(keep), 1), r_obs)], axis=1)
+    sc = S.Scene(S.f32(sph), np.zeros((0, 15)), np.zeros((0, 7)))
+    ctx = make_ctx(rb, sc, c)
+    ctx.work_counters(reset=True)
+    out = ctx.validate(torch_cuda.from_numpy(q0.astype(np.float32)).cuda(),
+                       torch_cuda.from_numpy(q1.astype(np.float32)).cuda(), W)
+    torch_cuda.cuda.synchronize()
+    chains = int(ctx.work_counters()[1])
+    ctx.close()
+    runs = parity.oracle_runs(oracle_mod.Oracle(rb, sc, c), c, q0, q1, W, n_threads=8)
+    stats, bad = parity.compare(out, runs)
+    assert not bad, (stats, bad[:10])
+    assert (parity.to_np(out["status"]) == 0).all()
+    assert chains > 2 * (W - 1) * len(q0), chains
+    print(len(keep), "obstacles", stats, chains)
