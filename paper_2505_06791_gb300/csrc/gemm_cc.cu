@@ -14,11 +14,11 @@
 // |s_tensor - s| from the unit roundoff of the precision and the coordinate ranges; folding
 // -E into alpha makes the contraction s - E. A pair with s_tensor - E >= 0 has s >= 0, i.e.
 // clearance >= g > 0: no collision, and no FP32 rounding can turn it into one. An epilogue
-// warp ORs the raw bits of its 64 accumulator columns: a clear sign bit clears all 64 pairs;
-// otherwise (rarely) the row is rechecked against those 64 obstacles with the same FP32
-// test as the
-// exact collision kernel, on sphere centres computed by the same FK arithmetic, so the
-// verdicts, and each motion's first colliding waypoint, are those of the exact kernel.
+// warp reads its 64 accumulator columns with tensor-memory loads that also return the
+// minimum of what they load: a positive minimum clears all 64 pairs; otherwise (rarely) the
+// row is rechecked against those 64 obstacles with the same FP32 test as the exact
+// collision kernel, on sphere centres computed by the same FK arithmetic, so the verdicts,
+// and each motion's first colliding waypoint, are those of the exact kernel.
 //
 // One persistent CTA per SM takes motions from a global counter (the FK group fetches them,
 // skipping motions that did not project, into a small ring every role reads in the same
@@ -38,8 +38,8 @@
 //               the operand layout, and the centre kept for the recheck.
 //   warps 4-19  epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and the
 //               64-column quarter (w - 4) / 4 of each N tile (both loads at once, so the
-//               accumulator is released before the tests), ORs the values' bits, and in the
-//               rare case of a set sign bit rechecks those 64 pairs exactly.
+//               accumulator is released before the tests), takes the loads' minima, and in
+//               the rare case of a minimum <= 0 rechecks those 64 pairs exactly.
 //   warp 20     producer of B' chunks; warp 21 allocates tensor memory and issues the MMAs.
 // Early termination: after each waypoint the epilogue publishes a verdict. Waypoint w of a
 // motion is issued only while waypoint w - 2 was collision-free, so after the first
@@ -158,16 +158,20 @@ __device__ __forceinline__ void mma_cc(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void commit_to(uint32_t b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
 }
-__device__ __forceinline__ void tld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+// Loads 32 accumulator columns of this thread's lane and returns their minimum (the load's
+// own min reduction); the loaded values themselves are not needed. Valid after tld_wait.
+__device__ __forceinline__ float tld32_min(uint32_t taddr) {
+  float r[32], m;
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"
+      : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]), "=f"(r[8]),
+        "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15]), "=f"(r[16]),
+        "=f"(r[17]), "=f"(r[18]), "=f"(r[19]), "=f"(r[20]), "=f"(r[21]), "=f"(r[22]), "=f"(r[23]), "=f"(r[24]),
+        "=f"(r[25]), "=f"(r[26]), "=f"(r[27]), "=f"(r[28]), "=f"(r[29]), "=f"(r[30]), "=f"(r[31]), "=f"(m)
       : "r"(taddr)
       : "memory");
+  return m;
 }
 __device__ __forceinline__ void tld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
           s_centre[buf * 128 + row] = make_float4(cx, cy, cz, l.w);
           const float ax = cx - ori.x, ay = cy - ori.y, az = cz - ori.z;
           const float rp = l.w + ori.w;
-          // alpha less the bound: a candidate pair is then simply s - E < 0 (a sign bit)
+          // alpha less the bound: a candidate pair is then simply s - E <= 0
           const float al = fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, -rp * rp))) - a.bound;
           const float m2[3] = {-2.f * ax, -2.f * ay, -2.f * az};
 #pragma unroll
@@ -489,17 +493,14 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
           }
           tca();
           const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)qc * 64;
-          uint32_t va[32], vb[32];
-          tld32_issue(base, va);
-          tld32_issue(base + 32, vb);
+          const float ma = tld32_min(base), mb = tld32_min(base + 32);
           tld_wait();
-          uint32_t any = 0u;  // sign bit set iff some s - E < 0 among this warp's 64 columns
-#pragma unroll
-          for (int i = 0; i < 32; ++i) any |= va[i] | vb[i];
+          // some s - E <= 0 among this warp's 64 columns (a NaN would also count)
+          const bool any = !(fminf(ma, mb) > 0.f);
           tcb();
           __syncwarp();
           if (lane == 0) mb_arrive(bar(kAccE + slot));
-          if ((any >> 31) && !drain && cen_p->w >= 0.f) {
+          if (any && !drain && cen_p->w >= 0.f) {
             // rare: recheck this row against the 64 obstacles exactly
             const float4 cen = *cen_p;
             const int j0 = t * 256 + qc * 64;
