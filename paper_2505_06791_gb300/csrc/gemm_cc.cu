@@ -79,6 +79,10 @@ constexpr int kOffAbortCc = kOffTmemCc + 4;
 constexpr int kOffRechk = kOffAbortCc + 4;  // unsigned long long
 constexpr int kOffRing8 = kOffRechk + 8;    // int [8] motion ring, int fetched, int done
 constexpr int kRingM = 8;
+// Work items are runs of kWpRun waypoints of one motion, handed out run-major (every
+// motion's first run, then every second run, ...), so the long collision-free motions
+// spread over the SMs instead of ending the launch on a few of them.
+constexpr int kWpRun = 16;
 constexpr int kSmemCc = kOffRing8 + (kRingM + 2) * 4;
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint64_t kDrainNs = 20000000ull;
@@ -257,14 +261,23 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     }
     return true;
   };
-  // the k-th motion of this CTA (-1: none left; -2: aborted)
+  // the k-th work item of this CTA (-1: none left; -2: aborted): motion item % n, waypoints
+  // [w0, w1) with w0 = (item / n) * kWpRun
   auto motion = [&](int k) -> int {
     if (!wait_count(s_fetched, k + 1)) return -2;
     return *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]);
   };
+  const int n_runs = (W + kWpRun - 1) / kWpRun;
+  auto run_of = [&](int item, int& m, int& w0, int& w1) {
+    const int j = item / a.n;
+    m = item - j * a.n;
+    w0 = j * kWpRun;
+    w1 = min(W, w0 + kWpRun);
+  };
   // verdict of global waypoint g: the epilogue stores g + 1 into s_hit[g % 2] when it collided
   auto verdict_hit = [&](uint32_t g) { return s_hit[g & 1] == (int)(g + 1); };
-  // per motion: issue(w) = w < W and (w < 2 or the motion is still active after verdict(w - 2))
+  // per item: issue(w) = w < w1 and (w - w0 < 2 or the item is still active after
+  // verdict(w - 2))
 
   if (warp == kProdWarp) {
     if (lane == 0) {
@@ -281,14 +294,16 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
       } else {
         uint32_t fill = 0, g = 0;
         for (int k = 0; ok; ++k) {
-          const int m = motion(k);
-          if (m == -2) ok = false;
-          if (m < 0) break;
+          const int item = motion(k);
+          if (item == -2) ok = false;
+          if (item < 0) break;
+          int m, w0, w1;
+          run_of(item, m, w0, w1);
           bool active = true;
-          for (int w = 0; ok && w < W; ++w, ++g) {
+          for (int w = w0; ok && w < w1; ++w, ++g) {
             if (g >= 2) {
               if (!mb_wait(bar(kVerdict + (g & 1)), ((g - 2) >> 1) & 1, s_abort)) { ok = false; break; }
-              if (w >= 2 && verdict_hit(g - 2)) active = false;
+              if (w - w0 >= 2 && verdict_hit(g - 2)) active = false;
             }
             if (!active) break;
             for (int c = 0; c < n_chunks; ++c, ++fill) {
@@ -316,14 +331,16 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
       bool ok = true, loaded = false;
       uint32_t g = 0, tcount = 0, use = 0;
       for (int k = 0; ok; ++k) {
-        const int m = motion(k);
-        if (m == -2) ok = false;
-        if (m < 0) break;
+        const int item = motion(k);
+        if (item == -2) ok = false;
+        if (item < 0) break;
+        int m, w0, w1;
+        run_of(item, m, w0, w1);
         bool active = true;
-        for (int w = 0; ok && w < W; ++w, ++g) {
+        for (int w = w0; ok && w < w1; ++w, ++g) {
           if (g >= 2) {
             if (!mb_wait(bar(kVerdict + (g & 1)), ((g - 2) >> 1) & 1, s_abort)) { ok = false; break; }
-            if (w >= 2 && verdict_hit(g - 2)) active = false;
+            if (w - w0 >= 2 && verdict_hit(g - 2)) active = false;
           }
           if (!active) break;
           if (!mb_wait(bar(kAFull + (g & 1)), (g >> 1) & 1, s_abort)) { ok = false; break; }
@@ -373,13 +390,23 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     uint32_t g = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
-      if (threadIdx.x == 0) {  // fetch the next projected motion into the ring
+      if (threadIdx.x == 0) {  // fetch the next work item of a projected motion into the ring
         int m = -1;
         if (wait_count(s_done, k - kRingM + 1)) {  // slot k % 8 no longer read
-          do {
-            m = atomicAdd(a.next, 1);
-          } while (m < a.n && a.status[m] != kValid);
-          if (m >= a.n) m = -1;
+          // skip motions that did not project, and runs after a collision already found
+          // (run-major order: the earlier runs of a motion were handed out before)
+          for (;;) {
+            const int item = atomicAdd(a.next, 1);
+            if (item >= a.n * n_runs) break;
+            int mm, w0, w1;
+            run_of(item, mm, w0, w1);
+            const int st = *reinterpret_cast<volatile const uint8_t*>(&a.status[mm]);
+            const unsigned ff = (unsigned)*reinterpret_cast<volatile const int*>(&a.first_fail[mm]);
+            if ((st == kValid || st == kCollision) && ff >= (unsigned)w0) {
+              m = item;
+              break;
+            }
+          }
         } else {
           m = -2;
         }
@@ -388,18 +415,20 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         *s_fetched = k + 1;
       }
       asm volatile("bar.sync 1, %0;" ::"r"(kFkWarps * 32) : "memory");
-      const int m = *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]);
-      if (m == -2) ok = false;
-      if (m < 0) break;
+      const int item = *reinterpret_cast<volatile int*>(&s_mring[k % kRingM]);
+      if (item == -2) ok = false;
+      if (item < 0) break;
+      int m, w0, w1;
+      run_of(item, m, w0, w1);
       bool active = true;
-      for (int w = 0; ok && w < W; ++w, ++g) {
+      for (int w = w0; ok && w < w1; ++w, ++g) {
         const int buf = g & 1;
         float* fr = s_frames + buf * 9 * 12;
         if (threadIdx.x == 0) {
           int ctl = 1;
           if (g >= 2) {  // buffer g % 2 is free once waypoint g - 2 has its verdict
             if (!mb_wait(bar(kVerdict + (g & 1)), ((g - 2) >> 1) & 1, s_abort)) ctl = -1;
-            else if (w >= 2 && verdict_hit(g - 2)) ctl = 0;
+            else if (w - w0 >= 2 && verdict_hit(g - 2)) ctl = 0;
           }
           if (ctl == 1) {  // the chain, with the exact kernel's arithmetic
             const float* q = a.q + ((size_t)m * W + w) * dof;
@@ -471,11 +500,13 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     uint32_t g = 0, tcount = 0;
     unsigned rechecks = 0;
     for (int k = 0; ok; ++k) {
-      const int m = motion(k);
-      if (m == -2) ok = false;
-      if (m < 0) break;
+      const int item = motion(k);
+      if (item == -2) ok = false;
+      if (item < 0) break;
+      int m, w0, w1;
+      run_of(item, m, w0, w1);
       int first_hit = -1;
-      for (int w = 0; ok && w < W; ++w, ++g) {
+      for (int w = w0; ok && w < w1; ++w, ++g) {
         const int buf = g & 1;
         const bool drain = first_hit >= 0;  // the one waypoint issued after the first hit
         // the FK warps' centres for this waypoint (a_full cannot move on before this verdict)
@@ -527,10 +558,12 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         if (s_hit[buf] == (int)(g + 1)) {
           first_hit = w;
           if (e == 0 && lane == 0) {
+            // runs of one motion may finish in any order: the smallest colliding waypoint
+            // wins (a projected motion enters with first_fail = -1, the largest unsigned)
             a.status[m] = (uint8_t)kCollision;
-            a.first_fail[m] = w;
+            atomicMin(reinterpret_cast<unsigned*>(&a.first_fail[m]), (unsigned)w);
           }
-          if (w + 1 >= W) {
+          if (w + 1 >= w1) {
             ++g;
             break;
           }
