@@ -297,7 +297,9 @@ typedef struct {
   double range;        /* steering step, L2 in joint space; default 0.3 */
   int W;               /* waypoints per motion, 2..64; default 32 */
   int max_rounds;      /* rounds per problem (>= 1); default 200 */
-  int workers;         /* extensions per round = warps per problem, 1..16; default 8 */
+  int workers;         /* extensions per round = warps per problem, 1..16 (fewer for
+                          W > 32, where the kernel's registers bound the CTA size: more is
+                          E_UNSUPPORTED); default 8 */
   int max_nodes;       /* capacity of each tree (>= 2); default 2048 */
   int max_connect;     /* greedy connect steps per extension (>= 0); default 32 */
   int max_path;        /* capacity of the path outputs, in nodes (>= 2); default 512 */

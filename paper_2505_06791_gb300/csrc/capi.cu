@@ -304,6 +304,16 @@ std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres)
   return idx;
 }
 
+// The planner kernel's registers bound its CTA size: with two waypoints per lane (W > 32)
+// fewer than the maximum 16 workers fit.
+int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char* who) {
+  const int mw = plan_max_workers(ctx->cs.type, pp->W);
+  if (pp->workers > mw)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": at most " + std::to_string(mw) +
+                                               " workers fit one CTA at W = " + std::to_string(pp->W));
+  return CPRRTC_OK;
+}
+
 float round_down(double x) {
   float f = (float)x;
   return (double)f > x ? std::nextafter(f, -INFINITY) : f;
@@ -1323,6 +1333,7 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   if (n == 0) return CPRRTC_OK;
   if (!start || !goal || !path_len || !path) return fail(ctx, CPRRTC_E_INVALID_ARG, "plan: null pointer");
   DeviceGuard g(ctx->device);
+  if (int rc = check_plan_workers(ctx, pp, "plan")) return rc;
   const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
   const size_t B = (size_t)pp->workers, MN = (size_t)pp->max_nodes;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -1506,6 +1517,7 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   if (!start || !goal || !path_len || !path)
     return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: null pointer");
   DeviceGuard g(ctx->device);
+  if (int rc = check_plan_workers(ctx, pp, "plan_static")) return rc;
   const void* arrays[] = {start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work};
   for (const void* a : arrays)
     if (a && !is_device_ptr(a))

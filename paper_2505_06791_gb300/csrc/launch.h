@@ -100,6 +100,9 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
                               cudaStream_t stream);
 
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
+// Most workers (warps per CTA) the planner kernel for this constraint type and W can launch
+// with (its registers per thread bound the CTA size); 0 if the query fails.
+int plan_max_workers(int cons_type, int W);
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,

@@ -619,6 +619,15 @@ static const void* plan_fn(int ct, int W) {
   }
 }
 
+int plan_max_workers(int cons_type, int W) {
+  cudaFuncAttributes attr;
+  if (cudaFuncGetAttributes(&attr, plan_fn(cons_type, W)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return attr.maxThreadsPerBlock / 32 < kMaxWorkers ? attr.maxThreadsPerBlock / 32 : kMaxWorkers;
+}
+
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage) {
   return SmemLayout(stage ? max_scene_f4 : 0, rb.n_spheres, W, workers, sizeof(PlanShared)).total;
 }

@@ -130,6 +130,11 @@ def test_plan_argument_errors(torch_cuda, oracle_mod):
         with pytest.raises(capi.CprrtcError) as e:
             ctx.plan(q, q, ctx.plan_params(**bad))
         assert e.value.code == capi.E_INVALID_ARG, bad
+    # W = 64 (two waypoints per lane) takes fewer than 16 workers: a clear refusal, not a
+    # failed launch
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.plan(q, q, ctx.plan_params(W=64, workers=16))
+    assert e.value.code == capi.E_UNSUPPORTED
     # start == goal in an empty scene, unconstrained: connects in the first round
     ctx.set_constraint(S.no_constraint())
     out = ctx.plan(q, q, ctx.plan_params(W=8, workers=2))
