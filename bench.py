@@ -105,6 +105,22 @@ def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def fp32_peak(ctx, sm_count: int, peaks: dict):
+    """(peak TFLOP/s, note) for the FP32-ALU rooflines: measured on this GPU by the library's
+    FMA-chain kernel (after the timed region), with the nominal unit-count figure beside it;
+    the nominal figure only if the measurement fails."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    nominal = fp32_peak_tflops(sm_count, mhz)
+    try:
+        measured = ctx.measure_fp32_peak()
+    except Exception as exc:  # the roofline's denominator only; the step is already timed
+        return nominal, (f"FP32 FMA pipe, nominal: {sm_count} SMs x 128 x 2 x {mhz:.0f} MHz "
+                         f"(measurement failed: {exc})")
+    return measured, (f"FP32 FMA measured on this GPU: scalar and packed FMA chains on every SM "
+                      f"(cprrtc_measure_fp32_peak), {measured:.1f} TFLOP/s; nominal {sm_count} "
+                      f"SMs x 128 x 2 x {mhz:.0f} MHz = {nominal:.1f}")
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -316,7 +332,7 @@ def run_plan(args, world, rank, local):
 
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    peak, peak_note = fp32_peak(ctx, sm_count, peaks)
     avg_kernel_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_kernel_s / 1e12
     solved = L > 0
@@ -351,9 +367,7 @@ def run_plan(args, world, rank, local):
                                          "cc_chains": float(counters[1]),
                                          "transforms": float(counters[2]),
                                          "tests_sph_box_cap": [float(x) for x in counters[3:6]]},
-                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
-                                  "counts; no measured FP32 peak)"},
+                     "peak_note": peak_note},
         "all_pairs_equivalent": {"flop_per_launch": nominal,
                                  "tflops": nominal / avg_kernel_s / 1e12,
                                  "note": "FLOPs a check of every robot sphere against every "
@@ -523,7 +537,7 @@ def run_batch(args, world, rank, local):
     e2e_s = time.perf_counter() - t0
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    peak, peak_note = fp32_peak(ctx, sm_count, peaks)
     avg_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_s / 1e12
     solved = L > 0
@@ -560,9 +574,7 @@ def run_batch(args, world, rank, local):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "plan_batch_kernel (6 classes, one graph)",
                      "flop_per_launch": flops, "avg_launch_ms": avg_s * 1e3,
-                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
-                                  "counts; no measured FP32 peak)"},
+                     "peak_note": peak_note},
         "gpu_launches": int(launches) * sum(1 for v in classes.values() if v),
         "clocks": clk,
     }
@@ -678,7 +690,7 @@ def run_validate(args, world, rank, local):
 
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = fp32_peak_tflops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    peak, peak_note = fp32_peak(ctx, sm_count, peaks)
     avg_kernel_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_kernel_s / 1e12
     line = {
@@ -698,9 +710,7 @@ def run_validate(args, world, rank, local):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "validate_kernel", "flop_per_launch": flops,
                      "avg_launch_ms": avg_kernel_s * 1e3,
-                     "peak_note": f"FP32 FMA pipe: {sm_count} SMs x 128 x 2 x "
-                                  f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (of nominal unit "
-                                  "counts; no measured FP32 peak)"},
+                     "peak_note": peak_note},
         "all_pairs_equivalent": {"flop_per_launch": nominal,
                                  "tflops": nominal / avg_kernel_s / 1e12},
         "gpu_launches": int(launches),

@@ -464,6 +464,13 @@ int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);
 
+/* Measurement helper with no counterpart in the paper: the FP32 FMA throughput of the
+ * context's GPU (TFLOP/s, the best of scalar and packed FP32x2 FMA chains on every SM, CUDA
+ * events on the context's stream), the denominator of the FP32 rooflines. Runs for a few
+ * milliseconds and synchronises the stream; *tflops is a host pointer.
+ * Errors: E_INVALID_ARG, E_CUDA, E_OOM. */
+int cprrtc_measure_fp32_peak(cprrtc_ctx* ctx, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -130,6 +130,7 @@ _SIGS = {
     "cprrtc_kernel_time": [C.c_void_p, C.c_char_p, C.POINTER(C.c_double),
                            C.POINTER(C.c_longlong)],
     "cprrtc_reset_timing": [C.c_void_p],
+    "cprrtc_measure_fp32_peak": [C.c_void_p, C.c_void_p],
 }
 
 
@@ -288,6 +289,12 @@ class Context:
         out = np.zeros(6, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
+
+    def measure_fp32_peak(self) -> float:
+        """FP32 FMA throughput of this context's GPU in TFLOP/s (measured on the device)."""
+        t = C.c_double()
+        self._check(self._L.cprrtc_measure_fp32_peak(self.h, C.byref(t)))
+        return t.value
 
     def reset_timing(self):
         self._check(self._L.cprrtc_reset_timing(self.h))

@@ -1416,6 +1416,14 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
   return st.end(ctx);
 }
 
+int cprrtc_measure_fp32_peak(cprrtc_ctx* ctx, double* tflops) {
+  if (!ctx || !tflops) return CPRRTC_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = measure_fp32_peak(ctx->dev, ctx->stream, tflops);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "measure_fp32_peak");
+  return CPRRTC_OK;
+}
+
 int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset) {
   if (!ctx || !out) return CPRRTC_E_INVALID_ARG;
   DeviceGuard g(ctx->device);

@@ -107,6 +107,8 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
                           cudaStream_t stream);
+// FP32 FMA throughput (TFLOP/s) measured with FMA chains on every SM (fp32_peak.cu).
+cudaError_t measure_fp32_peak(const DeviceInfo& dev, cudaStream_t stream, double* tflops);
 
 // ---- learned warm start (mlp.cu) ----
 constexpr int kMlpLayers = 4;

@@ -278,3 +278,17 @@ def test_candidate_list_overflow(torch_cuda, oracle_mod):
     assert (parity.to_np(out["status"]) == 0).all()
     assert chains > 2 * (W - 1) * len(q0), chains
     print(len(keep), "obstacles", stats, chains)
+
+
+def test_fp32_peak_measurement(torch_cuda):
+    """The FMA-chain measurement lands near the nominal FP32 rate (SMs x 128 x 2 x clock),
+    below it by no more than clock and issue losses, and not above it by more than the
+    clock's rounding."""
+    from paper_2505_06791_gb300.capi import Context
+    ctx = Context(0)
+    t = ctx.measure_fp32_peak()
+    sm = torch_cuda.cuda.get_device_properties(0).multi_processor_count
+    nominal = sm * 128 * 2 * 2.2e9 / 1e12  # above any SM clock of this GPU
+    assert 0.3 * nominal < t < 1.05 * nominal, (t, nominal)
+    print("fp32 peak", t, "TFLOP/s")
+    ctx.close()
