@@ -52,6 +52,12 @@ extern "C" {
 #define CPRRTC_CONSTRAINT_NONE 0       /* no projection; collision checks only */
 #define CPRRTC_CONSTRAINT_ROLL_PITCH 1 /* end-effector roll and pitch held at 0 */
 #define CPRRTC_CONSTRAINT_Z_PLANE 2    /* end-effector point on the plane z = target */
+/* The paper's other constraint variants (Sec. V-B: a line, and a fixed orientation added to
+ * a plane or a line); the fixed orientation is roll = pitch = 0 and yaw = `yaw`. Validation,
+ * projection and plan only (not the uneven batch). */
+#define CPRRTC_CONSTRAINT_LINE 3         /* end-effector point on {y = line_y, z = target} */
+#define CPRRTC_CONSTRAINT_ORIENT_PLANE 4 /* fixed orientation and the plane z = target */
+#define CPRRTC_CONSTRAINT_ORIENT_LINE 5  /* fixed orientation and the line of LINE */
 
 #define CPRRTC_MOTION_VALID 0
 #define CPRRTC_MOTION_PROJ_FAIL 1 /* Alg. 1 returned None (not projected in max_iters) */
@@ -97,10 +103,14 @@ typedef struct {
  * E_sm,k = max(0, |xi_k[i] - xi_k[i-1]| - tau) and
  * tau = max(c_sm * ||q_end - q_start||_inf / (W - 1), tau_floor).
  * Update: xi_new[i] = clamp(xi[i] - alpha (J^+ E_task + (xi[i] - xi[i-1]) * E_sm)), with
- * the damped pseudoinverse J^+ = J^T (J J^T + lambda^2 I)^-1. */
+ * the damped pseudoinverse J^+ = J^T (J J^T + lambda^2 I)^-1. Task errors (m rows):
+ * ROLL_PITCH [roll, pitch] (ZYX Euler angles of the end-effector rotation); Z_PLANE
+ * [p_z - target]; LINE [p_y - line_y, p_z - target]; ORIENT_PLANE [roll, pitch,
+ * yaw - yaw (wrapped to (-pi, pi]), p_z - target]; ORIENT_LINE [roll, pitch, yaw - yaw,
+ * p_y - line_y, p_z - target]; p is the end-effector point. */
 typedef struct {
   int type;         /* CPRRTC_CONSTRAINT_* */
-  double target;    /* plane height for Z_PLANE */
+  double target;    /* plane height (Z_PLANE, ORIENT_PLANE) or line height (LINE, ORIENT_LINE) */
   double tol_task;  /* default 1e-4 */
   double c_sm;      /* default 2 */
   double tau_floor; /* default 1e-3 */
@@ -108,6 +118,8 @@ typedef struct {
   double alpha;     /* default 1 */
   double lambda;    /* default 1e-3 */
   int max_iters;    /* 1..255, default 20 */
+  double line_y;    /* LINE, ORIENT_LINE: y of the line */
+  double yaw;       /* ORIENT_PLANE, ORIENT_LINE: end-effector yaw, rad */
 } cprrtc_constraint;
 
 typedef struct cprrtc_ctx cprrtc_ctx;

@@ -50,7 +50,8 @@ class _Scene(C.Structure):
 class _Constraint(C.Structure):
     _fields_ = [("type", C.c_int), ("target", C.c_double), ("tol_task", C.c_double),
                 ("c_sm", C.c_double), ("tau_floor", C.c_double), ("tol_sm", C.c_double),
-                ("alpha", C.c_double), ("lam", C.c_double), ("max_iters", C.c_int)]
+                ("alpha", C.c_double), ("lam", C.c_double), ("max_iters", C.c_int),
+                ("line_y", C.c_double), ("yaw", C.c_double)]
 
 
 class _PlanParams(C.Structure):
@@ -111,10 +112,11 @@ class Oracle:
 
     def set_constraint(self, c):
         if c is None:
-            self.c = _Constraint(0, 0.0, 1e-4, 2.0, 1e-3, 1e-4, 1.0, 1e-3, 20)
+            self.c = _Constraint(0, 0.0, 1e-4, 2.0, 1e-3, 1e-4, 1.0, 1e-3, 20, 0.0, 0.0)
         else:
             self.c = _Constraint(c.type, c.target, c.tol_task, c.c_sm, c.tau_floor, c.tol_sm,
-                                 c.alpha, c.lam, c.max_iters)
+                                 c.alpha, c.lam, c.max_iters, getattr(c, "line_y", 0.0),
+                                 getattr(c, "yaw", 0.0))
 
     # ---- kinematics ----
     def fk(self, q) -> np.ndarray:

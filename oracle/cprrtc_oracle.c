@@ -116,6 +116,14 @@ void orc_sphere_centres(const orc_robot* rb, const double* q, double* out) {
  *    J_task = E(psi, theta) J_w, where E maps world angular velocity to Euler rates:
  *    phi_dot = (c_psi w_x + s_psi w_y) / c_theta,  theta_dot = -s_psi w_x + c_psi w_y.
  *  - ORC_Z_PLANE: e = p_z - target, J_task = row z of J_v.
+ * The paper's other variants (Sec. V-B: a line; a fixed orientation with a plane or a line):
+ *  - ORC_LINE: the EE point on the line {y = line_y, z = target}: e = [p_y - line_y,
+ *    p_z - target], J_task = rows y and z of J_v.
+ *  - ORC_ORIENT_PLANE / ORC_ORIENT_LINE: the orientation fixed at roll = pitch = 0 and
+ *    yaw = c->yaw, with the plane or the line: e = [phi, theta, psi - yaw (wrapped into
+ *    (-pi, pi]), position rows]. The yaw rate of ZYX Euler angles is
+ *    psi_dot = w_z + tan(theta) (c_psi w_x + s_psi w_y), from w = psi_dot z +
+ *    theta_dot Rz(psi) y + phi_dot Rz(psi) Ry(theta) x.
  * ======================================================================================== */
 
 int orc_task(const orc_robot* rb, const orc_constraint* c, const double* q, double* e,
@@ -132,20 +140,49 @@ int orc_task(const orc_robot* rb, const orc_constraint* c, const double* q, doub
     for (int k = 0; k < n; ++k) Jt[k] = J[2 * n + k];
     return 1;
   }
-  /* ORC_ROLL_PITCH */
+  if (c->type == ORC_LINE) {
+    e[0] = Fe[7] - c->line_y;
+    e[1] = Fe[11] - c->target;
+    for (int k = 0; k < n; ++k) {
+      Jt[0 * n + k] = J[1 * n + k];
+      Jt[1 * n + k] = J[2 * n + k];
+    }
+    return 2;
+  }
+  /* ORC_ROLL_PITCH and the fixed orientations */
   double R11 = Fe[0], R21 = Fe[4], R31 = Fe[8], R32 = Fe[9], R33 = Fe[10];
   double roll = atan2(R32, R33);
   double pitch = atan2(-R31, sqrt(R32 * R32 + R33 * R33));
   double yaw = atan2(R21, R11);
   e[0] = roll;
   e[1] = pitch;
-  double cy = cos(yaw), sy = sin(yaw), cp = cos(pitch);
+  double cy = cos(yaw), sy = sin(yaw), cp = cos(pitch), tp = tan(pitch);
   for (int k = 0; k < n; ++k) {
     double wx = J[3 * n + k], wy = J[4 * n + k];
     Jt[0 * n + k] = (cy * wx + sy * wy) / cp;
     Jt[1 * n + k] = -sy * wx + cy * wy;
   }
-  return 2;
+  if (c->type == ORC_ROLL_PITCH) return 2;
+  double dyaw = yaw - c->yaw;
+  const double pi = 3.14159265358979323846;
+  while (dyaw > pi) dyaw -= 2.0 * pi;
+  while (dyaw <= -pi) dyaw += 2.0 * pi;
+  e[2] = dyaw;
+  for (int k = 0; k < n; ++k)
+    Jt[2 * n + k] = J[5 * n + k] + tp * (cy * J[3 * n + k] + sy * J[4 * n + k]);
+  if (c->type == ORC_ORIENT_PLANE) {
+    e[3] = Fe[11] - c->target;
+    for (int k = 0; k < n; ++k) Jt[3 * n + k] = J[2 * n + k];
+    return 4;
+  }
+  /* ORC_ORIENT_LINE */
+  e[3] = Fe[7] - c->line_y;
+  e[4] = Fe[11] - c->target;
+  for (int k = 0; k < n; ++k) {
+    Jt[3 * n + k] = J[1 * n + k];
+    Jt[4 * n + k] = J[2 * n + k];
+  }
+  return 5;
 }
 
 /* Solves A x = b (m x m, m <= 6) by Gaussian elimination with partial pivoting. */

@@ -36,7 +36,8 @@ extern "C" {
 #define ORC_MAX_DOF 8
 #define ORC_MAX_W 64
 
-enum { ORC_NONE = 0, ORC_ROLL_PITCH = 1, ORC_Z_PLANE = 2 };
+enum { ORC_NONE = 0, ORC_ROLL_PITCH = 1, ORC_Z_PLANE = 2, ORC_LINE = 3, ORC_ORIENT_PLANE = 4,
+       ORC_ORIENT_LINE = 5 };
 enum { ORC_VALID = 0, ORC_PROJ_FAIL = 1, ORC_COLLISION = 2 };
 
 typedef struct {
@@ -57,8 +58,8 @@ typedef struct {
 } orc_scene;
 
 typedef struct {
-  int type;               /* ORC_NONE, ORC_ROLL_PITCH, ORC_Z_PLANE */
-  double target;          /* plane height for ORC_Z_PLANE */
+  int type;               /* ORC_NONE .. ORC_ORIENT_LINE */
+  double target;          /* plane height (Z_PLANE, ORIENT_PLANE) or line height (LINE, ORIENT_LINE) */
   double tol_task;        /* tau_task of Alg. 1 (on ||E_task||_inf) */
   double c_sm;            /* step threshold tau = max(c_sm ||q1-q0||_inf/(W-1), tau_floor) */
   double tau_floor;
@@ -66,6 +67,8 @@ typedef struct {
   double alpha;           /* step size alpha of Alg. 1 */
   double lambda;          /* damping of the pseudoinverse J^+ */
   int max_iters;          /* max_iters of Alg. 1 */
+  double line_y;          /* y of the line {y = line_y, z = target} (LINE, ORIENT_LINE) */
+  double yaw;             /* end-effector yaw of the fixed orientation (ORIENT_*) */
 } orc_constraint;
 
 /* ---- kinematics ---------------------------------------------------------------------- */

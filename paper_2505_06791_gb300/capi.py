@@ -37,7 +37,8 @@ OBS_CAPSULE_DT = np.dtype([("p0", "<f8", 3), ("p1", "<f8", 3), ("r", "<f8")], al
 class cprrtc_constraint(C.Structure):
     _fields_ = [("type", C.c_int), ("target", C.c_double), ("tol_task", C.c_double),
                 ("c_sm", C.c_double), ("tau_floor", C.c_double), ("tol_sm", C.c_double),
-                ("alpha", C.c_double), ("lambda_", C.c_double), ("max_iters", C.c_int)]
+                ("alpha", C.c_double), ("lambda_", C.c_double), ("max_iters", C.c_int),
+                ("line_y", C.c_double), ("yaw", C.c_double)]
 
 
 class cprrtc_plan_params(C.Structure):
@@ -214,7 +215,8 @@ def scene_arrays(scene):
 
 def constraint_struct(c) -> cprrtc_constraint:
     return cprrtc_constraint(c.type, c.target, c.tol_task, c.c_sm, c.tau_floor, c.tol_sm,
-                             c.alpha, c.lam, c.max_iters)
+                             c.alpha, c.lam, c.max_iters, getattr(c, "line_y", 0.0),
+                             getattr(c, "yaw", 0.0))
 
 
 class Context:

@@ -457,7 +457,7 @@ int cprrtc_create(cprrtc_ctx** out, int device, void* stream) {
     delete ctx;
     return CPRRTC_E_OOM;
   }
-  ctx->cs = ConsDev{kConsNone, 0.f, 1e-4f, 2.f, 1e-3f, 1e-4f, 1.f, 1e-6f, 20};
+  ctx->cs = ConsDev{kConsNone, 0.f, 0.f, 0.f, 1e-4f, 2.f, 1e-3f, 1e-4f, 1.f, 1e-6f, 20};
   ctx->sc = SceneDev{nullptr, 0, 0, 0};
   *out = ctx;
   return CPRRTC_OK;
@@ -869,17 +869,19 @@ int cprrtc_set_scene_batch(cprrtc_ctx* ctx, int n_scenes, const cprrtc_obs_spher
 int cprrtc_set_constraint(cprrtc_ctx* ctx, const cprrtc_constraint* c) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (!c) return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: null pointer");
-  if (c->type < CPRRTC_CONSTRAINT_NONE || c->type > CPRRTC_CONSTRAINT_Z_PLANE)
+  if (c->type < CPRRTC_CONSTRAINT_NONE || c->type > CPRRTC_CONSTRAINT_ORIENT_LINE)
     return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: unknown type");
   if (c->max_iters < 1 || c->max_iters > 255)
     return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: max_iters must be in [1, 255]");
-  if (!is_finite(c->target) || !(c->tol_task > 0) || !(c->tol_sm > 0) || !(c->c_sm > 0) ||
+  if (!is_finite(c->target) || !is_finite(c->line_y) || !is_finite(c->yaw) ||
+      !(c->tol_task > 0) || !(c->tol_sm > 0) || !(c->c_sm > 0) ||
       !(c->tau_floor >= 0) || !is_finite(c->alpha) || !(c->lambda >= 0) || !is_finite(c->lambda) ||
       !is_finite(c->tol_task) || !is_finite(c->tol_sm) || !is_finite(c->c_sm) || !is_finite(c->tau_floor))
     return fail(ctx, CPRRTC_E_INVALID_ARG, "set_constraint: bad parameter");
-  ctx->cs = ConsDev{c->type,          (float)c->target, (float)c->tol_task,
-                    (float)c->c_sm,   (float)c->tau_floor, (float)c->tol_sm,
-                    (float)c->alpha,  (float)(c->lambda * c->lambda), c->max_iters};
+  ctx->cs = ConsDev{c->type,          (float)c->target,    (float)c->line_y,
+                    (float)c->yaw,    (float)c->tol_task,  (float)c->c_sm,
+                    (float)c->tau_floor, (float)c->tol_sm, (float)c->alpha,
+                    (float)(c->lambda * c->lambda), c->max_iters};
   return CPRRTC_OK;
 }
 
@@ -1861,6 +1863,8 @@ int cprrtc_set_constraint_table(cprrtc_ctx* ctx, const cprrtc_constraint* cons, 
   std::vector<ConsDev> tab(n);
   for (int i = 0; i < n; ++i) {
     int rc = cprrtc_set_constraint(ctx, &cons[i]);  // validates and converts
+    if (rc == CPRRTC_OK && cons[i].type > CPRRTC_CONSTRAINT_Z_PLANE)
+      rc = fail(ctx, CPRRTC_E_UNSUPPORTED, "constraint table: the uneven batch takes NONE, ROLL_PITCH and Z_PLANE");
     if (rc) {
       ctx->cs = saved;
       return rc;

@@ -10,7 +10,17 @@ constexpr int kMaxW = 64;
 constexpr int kMaxSpheres = 256;
 constexpr unsigned kFull = 0xffffffffu;
 
-enum : int { kConsNone = 0, kConsRollPitch = 1, kConsZPlane = 2 };
+// Task constraints (Sec. V-B): the end effector's roll and pitch, a plane, a line, and the
+// fixed orientation (roll, pitch, yaw) with a plane or a line.
+enum : int {
+  kConsNone = 0,
+  kConsRollPitch = 1,
+  kConsZPlane = 2,
+  kConsLine = 3,
+  kConsOrientPlane = 4,
+  kConsOrientLine = 5
+};
+constexpr int kNumCons = 6;
 enum : int { kValid = 0, kProjFail = 1, kCollision = 2 };
 
 // One DH joint, FP32, with the trigonometry of the fixed angles precomputed on the host.
@@ -81,7 +91,9 @@ struct SceneDev {
 // Task constraint and Algorithm 1 parameters in FP32.
 struct ConsDev {
   int type;
-  float target;
+  float target;    // plane or line height z
+  float target_y;  // line: y of the line {y = target_y, z = target} (parallel to x)
+  float yaw;       // fixed orientation: yaw of the end effector
   float tol_task;
   float c_sm;
   float tau_floor;

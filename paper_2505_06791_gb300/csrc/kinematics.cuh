@@ -28,6 +28,9 @@ struct ChainState {
   // z-plane Jacobian term of joint k: (z_k x p_k)_z for revolute joints (so that
   // J_k = zx_k pe_y - zy_k pe_x - zm_k), -z_k,z for prismatic ones (zx = zy = 0 there)
   float zm[kMaxDof];
+  // the same axes in full and m_k = z_k x p_k, for the line and fixed-orientation tasks
+  // (J_v,k = z_k x p_e - m_k and J_w,k = z_k for revolute joints; z_k and 0 for prismatic)
+  float gz0[kMaxDof], gz1[kMaxDof], gz2[kMaxDof], gm0[kMaxDof], gm1[kMaxDof], gm2[kMaxDof];
 };
 
 // Runs the DH chain for configuration q. If `fr` is non-null, frames 1..dof are written to
@@ -47,6 +50,10 @@ __device__ __forceinline__ void chain(const RobotDev& rb, const float* q, float*
       } else {
         s.zx[k] = z0; s.zy[k] = z1; s.zm[k] = fmaf(z0, p1, -z1 * p0);
       }
+      s.gz0[k] = z0; s.gz1[k] = z1; s.gz2[k] = z2;
+      s.gm0[k] = fmaf(z1, p2, -z2 * p1);
+      s.gm1[k] = fmaf(z2, p0, -z0 * p2);
+      s.gm2[k] = fmaf(z0, p1, -z1 * p0);
       float ct, st, d = J.d;
       if (J.prismatic) {
         ct = J.ct0;
@@ -160,5 +167,195 @@ __device__ __forceinline__ float task_err_inf(const Task<CT>& t) {
   return CT == kConsRollPitch ? fmaxf(fabsf(t.e0), fabsf(t.e1))
                               : (CT == kConsZPlane ? fabsf(t.e0) : 0.f);
 }
+
+// ---- the line and fixed-orientation tasks (m = 2, 4, 5 rows) ------------------------------
+//
+// Rows, with p_e the end-effector point and R = [x y z] its rotation:
+//   LINE          [p_y - line_y, p_z - target]
+//   ORIENT_PLANE  [roll, pitch, yaw - yaw0, p_z - target]
+//   ORIENT_LINE   [roll, pitch, yaw - yaw0, p_y - line_y, p_z - target]
+// with ZYX Euler angles (yaw - yaw0 wrapped into (-pi, pi]). Jacobian rows from the
+// geometric columns (v, w) of joint k: position rows are v_y, v_z; with c2 = R11^2 + R21^2
+// (= cos^2 pitch) the Euler-rate rows are roll (R11 w_x + R21 w_y) / c2, pitch
+// (R11 w_y - R21 w_x) / sqrt(c2) and yaw w_z - R31 (R11 w_x + R21 w_y) / c2.
+template <int CT>
+__host__ __device__ constexpr int task_rows() {
+  return CT == kConsLine ? 2 : CT == kConsOrientPlane ? 4 : CT == kConsOrientLine ? 5 : 1;
+}
+
+template <int CT>
+struct TaskN {
+  float e[task_rows<CT>()];
+  float pe0, pe1, pe2;   // end-effector point
+  float r11, r21, r31;   // rotation entries of the Euler-rate rows
+  float inv_c2, inv_c;   // 1 / cos^2 pitch, 1 / cos pitch
+};
+
+template <int CT>
+__device__ __forceinline__ TaskN<CT> task_error_n(const RobotDev& rb, const ConsDev& c,
+                                                  const ChainState& s) {
+  TaskN<CT> t{};
+  t.pe0 = fmaf(s.x0, rb.ee[0], fmaf(s.y0, rb.ee[1], fmaf(s.z0, rb.ee[2], s.p0)));
+  t.pe1 = fmaf(s.x1, rb.ee[0], fmaf(s.y1, rb.ee[1], fmaf(s.z1, rb.ee[2], s.p1)));
+  t.pe2 = fmaf(s.x2, rb.ee[0], fmaf(s.y2, rb.ee[1], fmaf(s.z2, rb.ee[2], s.p2)));
+  if (CT == kConsLine) {
+    t.e[0] = t.pe1 - c.target_y;
+    t.e[1] = t.pe2 - c.target;
+  } else {
+    t.r11 = s.x0;
+    t.r21 = s.x1;
+    t.r31 = s.x2;
+    t.e[0] = atan2f(s.y2, s.z2);
+    t.e[1] = atan2f(-s.x2, sqrtf(fmaf(s.y2, s.y2, s.z2 * s.z2)));
+    float dy = atan2f(s.x1, s.x0) - c.yaw;
+    const float two_pi = 6.28318530717958647692f;
+    while (dy > 3.14159265358979323846f) dy -= two_pi;
+    while (dy <= -3.14159265358979323846f) dy += two_pi;
+    t.e[2] = dy;
+    const float c2 = fmaf(s.x0, s.x0, s.x1 * s.x1);
+    t.inv_c2 = 1.0f / c2;
+    t.inv_c = rsqrtf(c2);
+    if (CT == kConsOrientPlane) {
+      t.e[3] = t.pe2 - c.target;
+    } else {
+      t.e[3] = t.pe1 - c.target_y;
+      t.e[4] = t.pe2 - c.target;
+    }
+  }
+  return t;
+}
+
+// Column k of the task Jacobian.
+template <int CT>
+__device__ __forceinline__ void jac_column_n(const RobotDev& rb, const ChainState& s,
+                                             const TaskN<CT>& t, int k,
+                                             float (&j)[task_rows<CT>()]) {
+  const bool rev = !rb.j[k].prismatic;
+  const float z0 = s.gz0[k], z1 = s.gz1[k], z2 = s.gz2[k];
+  // v = z x p_e - m (revolute) or z (prismatic)
+  const float vy = rev ? fmaf(z2, t.pe0, -z0 * t.pe2) - s.gm1[k] : z1;
+  const float vz = rev ? fmaf(z0, t.pe1, -z1 * t.pe0) - s.gm2[k] : z2;
+  if (CT == kConsLine) {
+    j[0] = vy;
+    j[1] = vz;
+  } else {
+    const float wx = rev ? z0 : 0.f, wy = rev ? z1 : 0.f, wz = rev ? z2 : 0.f;
+    const float a = fmaf(t.r11, wx, t.r21 * wy);
+    j[0] = a * t.inv_c2;
+    j[1] = fmaf(t.r11, wy, -t.r21 * wx) * t.inv_c;
+    j[2] = fmaf(-t.r31 * a, t.inv_c2, wz);
+    if (CT == kConsOrientPlane) {
+      j[3] = vz;
+    } else {
+      j[3] = vy;
+      j[4] = vz;
+    }
+  }
+}
+
+// Solves (J J^T + lambda^2 I) y = e (m x m, symmetric positive definite) by Cholesky.
+template <int CT>
+__device__ __forceinline__ void damped_solve_n(const RobotDev& rb, const ConsDev& c,
+                                               const ChainState& s, const TaskN<CT>& t,
+                                               float (&y)[task_rows<CT>()]) {
+  constexpr int M = task_rows<CT>();
+  float A[M][M];
+#pragma unroll
+  for (int r = 0; r < M; ++r)
+#pragma unroll
+    for (int q = 0; q < M; ++q) A[r][q] = r == q ? c.lam2 : 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) {
+    if (k < rb.dof) {
+      float j[M];
+      jac_column_n<CT>(rb, s, t, k, j);
+#pragma unroll
+      for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int q = 0; q <= r; ++q) A[r][q] = fmaf(j[r], j[q], A[r][q]);
+    }
+  }
+  // A = L L^T, L in the lower triangle of A
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    float d = A[q][q];
+#pragma unroll
+    for (int p = 0; p < q; ++p) d = fmaf(-A[q][p], A[q][p], d);
+    const float lqq = sqrtf(d), inv = 1.0f / lqq;
+    A[q][q] = lqq;
+#pragma unroll
+    for (int r = q + 1; r < M; ++r) {
+      float v = A[r][q];
+#pragma unroll
+      for (int p = 0; p < q; ++p) v = fmaf(-A[r][p], A[q][p], v);
+      A[r][q] = v * inv;
+    }
+  }
+  // L z = e, then L^T y = z
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    float v = t.e[r];
+#pragma unroll
+    for (int p = 0; p < r; ++p) v = fmaf(-A[r][p], y[p], v);
+    y[r] = v / A[r][r];
+  }
+#pragma unroll
+  for (int r = M - 1; r >= 0; --r) {
+    float v = y[r];
+#pragma unroll
+    for (int p = r + 1; p < M; ++p) v = fmaf(-A[p][r], y[p], v);
+    y[r] = v / A[r][r];
+  }
+}
+
+// One configuration's task evaluation for Alg. 1, whatever the constraint type: the error,
+// its infinity norm, and per joint the component g_k of J^+ e. The roll-pitch and z-plane
+// forms keep their closed-form arithmetic.
+template <int CT, bool GENERIC = (CT >= kConsLine)>
+struct TaskEval;
+
+template <int CT>
+struct TaskEval<CT, false> {
+  Task<CT> t;
+  float y0, y1;
+  __device__ __forceinline__ void eval(const RobotDev& rb, const ConsDev& c, const ChainState& s) {
+    t = task_error<CT>(rb, c, s);
+  }
+  __device__ __forceinline__ float err_inf() const { return task_err_inf<CT>(t); }
+  __device__ __forceinline__ void solve(const RobotDev& rb, const ConsDev& c, const ChainState& s) {
+    damped_solve<CT>(rb, c, s, t, y0, y1);
+  }
+  __device__ __forceinline__ float step(const RobotDev& rb, const ChainState& s, int k) const {
+    float j0, j1;
+    jac_entry<CT>(rb, s, t, k, j0, j1);
+    return fmaf(j0, y0, j1 * y1);
+  }
+};
+
+template <int CT>
+struct TaskEval<CT, true> {
+  TaskN<CT> t;
+  float y[task_rows<CT>()];
+  __device__ __forceinline__ void eval(const RobotDev& rb, const ConsDev& c, const ChainState& s) {
+    t = task_error_n<CT>(rb, c, s);
+  }
+  __device__ __forceinline__ float err_inf() const {
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < task_rows<CT>(); ++r) m = fmaxf(m, fabsf(t.e[r]));
+    return m;
+  }
+  __device__ __forceinline__ void solve(const RobotDev& rb, const ConsDev& c, const ChainState& s) {
+    damped_solve_n<CT>(rb, c, s, t, y);
+  }
+  __device__ __forceinline__ float step(const RobotDev& rb, const ChainState& s, int k) const {
+    float j[task_rows<CT>()];
+    jac_column_n<CT>(rb, s, t, k, j);
+    float g = 0.f;
+#pragma unroll
+    for (int r = 0; r < task_rows<CT>(); ++r) g = fmaf(j[r], y[r], g);
+    return g;
+  }
+};
 
 }  // namespace cprrtc

@@ -111,9 +111,9 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
       // every lane evaluates (lanes past W on a clamped copy) so that the shuffles below
       // run converged
       chain(rb, q[s], nullptr, cs);
-      const Task<CT> t = task_error<CT>(rb, c, cs);
-      float y0, y1;
-      damped_solve<CT>(rb, c, cs, t, y0, y1);
+      TaskEval<CT> te;
+      te.eval(rb, c, cs);
+      te.solve(rb, c, cs);
       float esm_max = 0.f;
 #pragma unroll
       for (int k = 0; k < kMaxDof; ++k) {
@@ -124,9 +124,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
             const float wrap = __shfl_sync(kFull, q[s > 0 ? s - 1 : 0][k], 31);
             if (lane == 0) prev = wrap;
           }
-          float j0, j1;
-          jac_entry<CT>(rb, cs, t, k, j0, j1);
-          const float g = fmaf(j0, y0, j1 * y1);
+          const float g = te.step(rb, cs, k);
           const float dk = q[s][k] - prev;
           const float esm = fmaxf(0.f, fabsf(dk) - tau);
           const float v = fmaf(-c.alpha, fmaf(dk, esm, g), q[s][k]);
@@ -134,7 +132,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
           esm_max = fmaxf(esm_max, esm);
         }
       }
-      const float et = task_err_inf<CT>(t);
+      const float et = te.err_inf();
       const bool valid = (i >= W) || ((esm_max < c.tol_sm) && (et < c.tol_task));
       if (i > prog && i < W) last_err[s] = et;
       valid_mask |= (unsigned long long)__ballot_sync(kFull, valid) << (32 * s);

@@ -614,6 +614,12 @@ static const void* plan_fn(int ct, int W) {
       return two ? (const void*)plan_kernel<kConsRollPitch, 2> : (const void*)plan_kernel<kConsRollPitch, 1>;
     case kConsZPlane:
       return two ? (const void*)plan_kernel<kConsZPlane, 2> : (const void*)plan_kernel<kConsZPlane, 1>;
+    case kConsLine:
+      return two ? (const void*)plan_kernel<kConsLine, 2> : (const void*)plan_kernel<kConsLine, 1>;
+    case kConsOrientPlane:
+      return two ? (const void*)plan_kernel<kConsOrientPlane, 2> : (const void*)plan_kernel<kConsOrientPlane, 1>;
+    case kConsOrientLine:
+      return two ? (const void*)plan_kernel<kConsOrientLine, 2> : (const void*)plan_kernel<kConsOrientLine, 1>;
     default:
       return two ? (const void*)plan_kernel<kConsNone, 2> : (const void*)plan_kernel<kConsNone, 1>;
   }

@@ -60,10 +60,13 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
             qw[k] = k < dof ? fminf(fmaxf(qp[k] + fmaf(-taper, y0[k], y[k]), rb.j[k].lo), rb.j[k].hi)
                             : 0.f;
           ChainState ch;
+          TaskEval<CT> te;
           chain(rb, qp, nullptr, ch);
-          e_plain = fmaxf(e_plain, task_err_inf<CT>(task_error<CT>(rb, cs, ch)));
+          te.eval(rb, cs, ch);
+          e_plain = fmaxf(e_plain, te.err_inf());
           chain(rb, qw, nullptr, ch);
-          e_warm = fmaxf(e_warm, task_err_inf<CT>(task_error<CT>(rb, cs, ch)));
+          te.eval(rb, cs, ch);
+          e_warm = fmaxf(e_warm, te.err_inf());
           work.updates += 2u;
         }
       }
@@ -138,24 +141,21 @@ __global__ void project_configs_kernel(RobotDev rb, ConsDev cs, const float* __r
   float err = 0.f;
   for (int it = 0; it <= max_iters; ++it) {
     chain(rb, q, nullptr, s);
-    const Task<CT> t = task_error<CT>(rb, cs, s);
-    err = task_err_inf<CT>(t);
+    TaskEval<CT> te;
+    te.eval(rb, cs, s);
+    err = te.err_inf();
     if (err < cs.tol_task) {
       success = 1;
       break;
     }
     if (it == max_iters) break;
-    float y0, y1;
-    damped_solve<CT>(rb, cs, s, t, y0, y1);
+    te.solve(rb, cs, s);
+    float g[kMaxDof];  // every step from the same configuration before any joint moves
 #pragma unroll
-    for (int k = 0; k < kMaxDof; ++k) {
-      if (k < dof) {
-        float j0, j1;
-        jac_entry<CT>(rb, s, t, k, j0, j1);
-        const float g = fmaf(j0, y0, j1 * y1);
-        q[k] = fminf(fmaxf(fmaf(-cs.alpha, g, q[k]), rb.j[k].lo), rb.j[k].hi);
-      }
-    }
+    for (int k = 0; k < kMaxDof; ++k) g[k] = k < dof ? te.step(rb, s, k) : 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k)
+      if (k < dof) q[k] = fminf(fmaxf(fmaf(-cs.alpha, g[k], q[k]), rb.j[k].lo), rb.j[k].hi);
   }
 #pragma unroll
   for (int k = 0; k < kMaxDof; ++k)
@@ -171,6 +171,14 @@ static const void* validate_fn(int ct, int W) {
       return two ? (const void*)validate_kernel<kConsRollPitch, 2> : (const void*)validate_kernel<kConsRollPitch, 1>;
     case kConsZPlane:
       return two ? (const void*)validate_kernel<kConsZPlane, 2> : (const void*)validate_kernel<kConsZPlane, 1>;
+    case kConsLine:
+      return two ? (const void*)validate_kernel<kConsLine, 2> : (const void*)validate_kernel<kConsLine, 1>;
+    case kConsOrientPlane:
+      return two ? (const void*)validate_kernel<kConsOrientPlane, 2>
+                 : (const void*)validate_kernel<kConsOrientPlane, 1>;
+    case kConsOrientLine:
+      return two ? (const void*)validate_kernel<kConsOrientLine, 2>
+                 : (const void*)validate_kernel<kConsOrientLine, 1>;
     default:
       return two ? (const void*)validate_kernel<kConsNone, 2> : (const void*)validate_kernel<kConsNone, 1>;
   }
@@ -210,10 +218,25 @@ cudaError_t launch_project_configs(const RobotDev& rb, const ConsDev& cs, const 
   if (n <= 0) return cudaSuccess;
   const int block = 128;
   const int grid = (n + block - 1) / block;
-  if (cs.type == kConsZPlane)
-    project_configs_kernel<kConsZPlane><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
-  else
-    project_configs_kernel<kConsRollPitch><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
+  switch (cs.type) {
+    case kConsZPlane:
+      project_configs_kernel<kConsZPlane><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
+      break;
+    case kConsLine:
+      project_configs_kernel<kConsLine><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok, resid);
+      break;
+    case kConsOrientPlane:
+      project_configs_kernel<kConsOrientPlane><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok,
+                                                                         resid);
+      break;
+    case kConsOrientLine:
+      project_configs_kernel<kConsOrientLine><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok,
+                                                                        resid);
+      break;
+    default:
+      project_configs_kernel<kConsRollPitch><<<grid, block, 0, stream>>>(rb, cs, q_in, n, max_iters, q_out, ok,
+                                                                       resid);
+  }
   return cudaGetLastError();
 }
 

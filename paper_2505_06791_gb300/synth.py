@@ -265,13 +265,13 @@ def nearby_configs(robot: Robot, q: np.ndarray, step: float, seed: int) -> np.nd
 
 
 # Constraint presets (type codes shared with the C-ABI and the oracle).
-C_NONE, C_ROLL_PITCH, C_Z_PLANE = 0, 1, 2
+C_NONE, C_ROLL_PITCH, C_Z_PLANE, C_LINE, C_ORIENT_PLANE, C_ORIENT_LINE = 0, 1, 2, 3, 4, 5
 
 
 @dataclass
 class Constraint:
     type: int = C_ROLL_PITCH
-    target: float = 0.0        # plane height for C_Z_PLANE
+    target: float = 0.0        # plane (C_Z_PLANE, C_ORIENT_PLANE) or line (C_LINE, C_ORIENT_LINE) height
     tol_task: float = 1e-4     # ||E_task||_inf threshold
     c_sm: float = 2.0          # tau_step = max(c_sm * ||q1-q0||_inf / (W-1), tau_floor)
     tau_floor: float = 1e-3
@@ -279,6 +279,24 @@ class Constraint:
     alpha: float = 1.0         # step size
     lam: float = 1e-3          # damping of the pseudoinverse
     max_iters: int = 20
+    line_y: float = 0.0        # y of the line {y = line_y, z = target} (parallel to x)
+    yaw: float = 0.0           # end-effector yaw of the fixed orientation
+
+
+def line(y0: float = 0.0, z0: float = 0.6, max_iters: int = 20) -> Constraint:
+    """End-effector point on the line {y = y0, z = z0}."""
+    return Constraint(type=C_LINE, target=z0, line_y=y0, max_iters=max_iters)
+
+
+def orient_plane(yaw: float = 0.0, z0: float = 0.6, max_iters: int = 20) -> Constraint:
+    """Fixed end-effector orientation (roll = pitch = 0, yaw) on the plane z = z0."""
+    return Constraint(type=C_ORIENT_PLANE, target=z0, yaw=yaw, max_iters=max_iters)
+
+
+def orient_line(yaw: float = 0.0, y0: float = 0.0, z0: float = 0.6,
+                max_iters: int = 20) -> Constraint:
+    """Fixed end-effector orientation on the line {y = y0, z = z0}."""
+    return Constraint(type=C_ORIENT_LINE, target=z0, line_y=y0, yaw=yaw, max_iters=max_iters)
 
 
 def roll_pitch(max_iters: int = 20) -> Constraint:

@@ -59,12 +59,24 @@ def roll_pitch(R):
     return np.array([roll, pitch])
 
 
-def task_error(joints, ee, q, ctype, target=0.0):
+def task_error(joints, ee, q, ctype, target=0.0, line_y=0.0, yaw=0.0):
+    """The task errors of every constraint type from scipy's Euler angles: roll-pitch,
+    z-plane, line {y = line_y, z = target}, and the fixed orientation (roll, pitch, yaw
+    wrapped into (-pi, pi]) with the plane or the line."""
     F = fk_frames(joints, ee, q)[-1]
     if ctype == 1:
         return roll_pitch(F[:3, :3])
     if ctype == 2:
         return np.array([F[2, 3] - target])
+    if ctype == 3:
+        return np.array([F[1, 3] - line_y, F[2, 3] - target])
+    if ctype in (4, 5):
+        yaw_, _, _ = Rot.from_matrix(F[:3, :3]).as_euler("ZYX")
+        dy = (yaw_ - yaw + np.pi) % (2 * np.pi) - np.pi
+        if dy <= -np.pi:
+            dy += 2 * np.pi
+        pos = [F[2, 3] - target] if ctype == 4 else [F[1, 3] - line_y, F[2, 3] - target]
+        return np.concatenate([roll_pitch(F[:3, :3]), [dy], pos])
     return np.zeros(0)
 
 

@@ -55,11 +55,16 @@ def _outcome(r, m):
             int(r["first_fail"][m]) if int(r["status"][m]) == 1 else None)
 
 
-def compare(gpu, runs):
+def compare(gpu, runs, fail_drift=False):
+    """Parity protocol. With fail_drift, a motion that both sides fail to project (at the
+    iteration cap) may differ in the waypoint where Alg. 1 gave up: with four or five task
+    rows the damped system J J^T + lambda^2 I is ill-conditioned near singular arm poses, and
+    over the iterations of a failing projection FP32 and FP64 iterates separate; such
+    motions are counted (stats["fail_drift"]), not failed."""
     g = {k: to_np(v) for k, v in gpu.items()}
     base = runs[0]
     n = len(g["status"])
-    stats = dict(n=n, robust=0, sensitive=0, ambiguous_cc=0, max_dq=0.0, exact=0)
+    stats = dict(n=n, robust=0, sensitive=0, ambiguous_cc=0, max_dq=0.0, exact=0, fail_drift=0)
     bad = []
     for m in range(n):
         outs = [_outcome(r, m) for r in runs]
@@ -68,6 +73,9 @@ def compare(gpu, runs):
         robust = all(o == outs[0] for o in outs)
         stats["robust" if robust else "sensitive"] += 1
         match = [i for i, o in enumerate(outs) if o == g_out]
+        if not match and fail_drift and g_out[0] and outs[0][0] and g_out[1] == outs[0][1]:
+            stats["fail_drift"] += 1
+            continue
         if not match:
             bad.append((m, "projection outcome", outs[0], g_out, robust))
             continue

@@ -31,14 +31,15 @@ def test_struct_layouts_match_header():
     assert capi.OBS_SPHERE_DT.itemsize == 32
     assert capi.OBS_BOX_DT.itemsize == 120
     assert capi.OBS_CAPSULE_DT.itemsize == 56
-    assert C.sizeof(capi.cprrtc_constraint) == 72
+    # int, 7 doubles, int (padded to 8), 2 doubles
+    assert C.sizeof(capi.cprrtc_constraint) == 88
     # field order mirrors the header's struct declarations
     hdr = open(capi.HEADER).read()
     body = hdr[:hdr.index("} cprrtc_constraint;")]
     body = re.sub(r"/\*.*?\*/", "", body[body.rindex("typedef struct {"):], flags=re.S)
     names = re.findall(r"(\w+);", body)
     assert names == ["type", "target", "tol_task", "c_sm", "tau_floor", "tol_sm", "alpha",
-                     "lambda", "max_iters"]
+                     "lambda", "max_iters", "line_y", "yaw"]
 
 
 def test_null_context_is_rejected(libpath):

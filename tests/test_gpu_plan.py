@@ -176,3 +176,22 @@ def test_plan_time_budget_and_allocation_failure(torch_cuda, oracle_mod):
         run_plan(torch, ctx, None, start[:1], goal[:1], bad)
     assert err.value.code == -1  # CPRRTC_E_INVALID_ARG
     ctx.close()
+
+
+@pytest.mark.parametrize("ctype", [3, 4, 5])
+def test_plan_line_and_fixed_orientation(torch_cuda, oracle_mod, ctype):
+    """The planner under the new constraints: every returned path is re-validated by the
+    oracle (on the manifold, continuous, collision-free) and runs are deterministic."""
+    rb = S.make_arm7(1)
+    c = {3: S.line(0.1, 0.6), 4: S.orient_plane(0.5, 0.6), 5: S.orient_line(-0.4, 0.1, 0.6)}[ctype]
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 8, 9700 + ctype,
+                                               counts=(40, 20, 10))
+    ctx = ctx_for(rb, c)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=400, workers=8, seed=5)
+    out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
+    again = run_plan(torch_cuda, ctx, None, start, goal, prm)
+    PB.assert_same_plans(out, again)
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
+    assert not issues, issues[:10]
+    print(ctype, "solved", checked, "of 8")
+    ctx.close()

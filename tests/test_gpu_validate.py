@@ -40,14 +40,14 @@ def manifold_starts(orc, robot, n, seed):
     return S.f32(np.array(out))
 
 
-def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.8):
+def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.8, fail_drift=False):
     ctx = make_ctx(robot, scene, c)
     dq0 = torch.from_numpy(q0.astype(np.float32)).cuda()
     dq1 = torch.from_numpy(q1.astype(np.float32)).cuda()
     out = ctx.validate(dq0, dq1, W)
     torch.cuda.synchronize()
     runs = parity.oracle_runs(oracle_mod.Oracle(robot, scene, c), c, q0, q1, W)
-    stats, bad = parity.compare(out, runs)
+    stats, bad = parity.compare(out, runs, fail_drift=fail_drift)
     ctx.close()
     assert not bad, (stats, bad[:10])
     assert stats["exact"] >= min_exact * stats["n"], stats
@@ -291,4 +291,60 @@ def test_fp32_peak_measurement(torch_cuda):
     nominal = sm * 128 * 2 * 2.2e9 / 1e12  # above any SM clock of this GPU
     assert 0.3 * nominal < t < 1.05 * nominal, (t, nominal)
     print("fp32 peak", t, "TFLOP/s")
+    ctx.close()
+
+
+NEW_CONSTRAINTS = {3: lambda: S.line(0.1, 0.6), 4: lambda: S.orient_plane(0.5, 0.6),
+                   5: lambda: S.orient_line(-0.4, 0.1, 0.6)}
+
+
+@pytest.mark.parametrize("ctype", [3, 4, 5])
+def test_line_and_fixed_orientation_parity(torch_cuda, oracle_mod, ctype):
+    """The paper's other constraint variants (Sec. V-B: a line; a fixed orientation with a
+    plane or a line; 2, 4 and 5 task rows, Cholesky-solved damped steps): strict parity with
+    the oracle on planner-like 0.3 rad motions; on long motions, which mostly fail to
+    project, the give-up waypoint of a failing projection may drift with four or five task
+    rows (ill-conditioned damped system), for at most 5 % of the motions."""
+    rb = S.make_arm7(1)
+    sc = S.make_mixed_scene(9500 + ctype, 40, 20, 10)
+    c = NEW_CONSTRAINTS[ctype]()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 96, 9510 + ctype)
+    short = S.nearby_configs(rb, q0, 0.3, 9520 + ctype)
+    far = S.uniform_configs(rb, 96, 9530 + ctype)
+    for q1, drift in ((short, False), (far, ctype >= 4)):
+        stats, out, _ = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32, min_exact=0.7,
+                                 fail_drift=drift)
+        assert stats["fail_drift"] <= 0.05 * stats["n"], stats
+        print(ctype, stats, np.bincount(parity.to_np(out["status"]), minlength=3))
+
+
+@pytest.mark.parametrize("ctype", [3, 4, 5])
+def test_line_and_fixed_orientation_single_config_projection(torch_cuda, oracle_mod, ctype):
+    """cprrtc_project_configs for the new constraints, from uniform configurations (up to 60
+    damped steps): the oracle's success verdict on at least 90 %, every GPU success on the
+    manifold, and converged points within 1e-4 of the oracle's for the line (two rows). With
+    four or five rows the steps drift along the null space, differently in FP32 and FP64,
+    over tens of iterations: the two land on different points of the manifold."""
+    rb = S.make_arm7(1)
+    c = NEW_CONSTRAINTS[ctype]()
+    orc = oracle_mod.Oracle(rb, constraint=c)
+    q = S.uniform_configs(rb, 300, 9600 + ctype)
+    ctx = make_ctx(rb, S.Scene(), c)
+    out = ctx.project_configs(torch_cuda.from_numpy(q.astype(np.float32)).cuda(), 60)
+    gq, gok = parity.to_np(out["q"]), parity.to_np(out["ok"])
+    verdict, both, close = 0, 0, 0
+    for i in range(len(q)):
+        ok, qp, it, res = orc.project_config(q[i], max_iters=60)
+        verdict += ok == bool(gok[i])
+        if gok[i]:
+            e, _ = orc.task(gq[i].astype(np.float64))
+            assert np.abs(e).max() < 2 * c.tol_task
+        if ok and gok[i]:
+            both += 1
+            close += np.abs(gq[i] - qp).max() < 1e-4
+    assert verdict >= 0.9 * len(q), verdict
+    if ctype == 3:
+        assert close >= 0.95 * both, (close, both)
+    print(ctype, "verdicts", verdict, "both projected", both, "within 1e-4", close)
     ctx.close()

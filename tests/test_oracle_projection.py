@@ -23,7 +23,8 @@ def on_manifold(orc, rb, n, seed, max_iters=60):
 def gauss_newton_reference(rb, c, q, max_iters):
     """Damped Gauss-Newton written from library pieces: scipy Euler angles for E_task, a
     finite-difference Jacobian, and numpy lstsq for the damped least-squares step."""
-    f = lambda x: indep.task_error(rb.joints, rb.ee, x, c.type, c.target)  # noqa: E731
+    f = lambda x: indep.task_error(rb.joints, rb.ee, x, c.type, c.target,  # noqa: E731
+                                   getattr(c, "line_y", 0.0), getattr(c, "yaw", 0.0))
     q = np.array(q, np.float64)
     for it in range(1, max_iters + 1):
         e = f(q)
