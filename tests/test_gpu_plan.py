@@ -181,17 +181,21 @@ def test_plan_time_budget_and_allocation_failure(torch_cuda, oracle_mod):
 @pytest.mark.parametrize("ctype", [3, 4, 5])
 def test_plan_line_and_fixed_orientation(torch_cuda, oracle_mod, ctype):
     """The planner under the new constraints: every returned path is re-validated by the
-    oracle (on the manifold, continuous, collision-free) and runs are deterministic."""
+    oracle (on the manifold, continuous, collision-free) and runs are deterministic. With
+    the orientation fixed only one or two joints' worth of freedom is left, so those
+    problems get sparser scenes and more rounds."""
     rb = S.make_arm7(1)
     c = {3: S.line(0.1, 0.6), 4: S.orient_plane(0.5, 0.6), 5: S.orient_line(-0.4, 0.1, 0.6)}[ctype]
     scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 8, 9700 + ctype,
-                                               counts=(40, 20, 10))
+                                               counts=(40, 20, 10) if ctype == 3 else (6, 3, 3))
     ctx = ctx_for(rb, c)
-    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=400, workers=8, seed=5)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=400 if ctype == 3 else 2000,
+                          workers=8, max_nodes=4096, seed=5)
     out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
     again = run_plan(torch_cuda, ctx, None, start, goal, prm)
     PB.assert_same_plans(out, again)
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
     assert not issues, issues[:10]
+    assert checked >= 1, "no path to check"
     print(ctype, "solved", checked, "of 8")
     ctx.close()
