@@ -719,6 +719,95 @@ def run_validate(args, world, rank, local):
     return line, (rb, sc, c, n, W, q0.cpu().numpy(), q1.cpu().numpy())
 
 
+# ---- early termination ablation over obstacle density -----------------------------------------
+
+EE_N, EE_W = 4096, 32
+
+
+def run_earlyexit(args, world, rank, local):
+    """The paper's early termination (Sec. IV) against checking every waypoint and candidate,
+    on planner-like motions (0.3 rad, roll-pitch) among 24 axis-aligned boxes cut into 1, 10
+    and 100 pieces (same occupied volume, 24 to 2400 primitives; the density scaling of
+    Sec. V-A). Outputs must be identical with and without early exit."""
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    rb, c = S.make_arm7(1), S.roll_pitch(20)
+    n, W = EE_N, EE_W
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_constraint(c)
+    rows = []
+    total_ms_on = 0.0
+    with torch.cuda.stream(stream):
+        q0 = manifold_starts_gpu(ctx, rb, n, 30_000 + 97 * rank)
+        q1 = torch.from_numpy(S.nearby_configs(rb, q0.cpu().numpy(), 0.3,
+                                               31_000 + 97 * rank).astype(np.float32)).to(dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        for split in (1, 10, 100):
+            sc = S.make_subdivided_boxes(40 + rank, 24, split)
+            ctx.set_obstacles(sc)
+            res = {}
+            for early in (True, False):
+                ctx.set_early_exit(early)
+                out = ctx.alloc_validate_outputs(n, W, q0)
+                for _ in range(args.warmup):
+                    ctx.validate(q0, q1, W, out=out)
+                stream.synchronize()
+                ctx.work_counters(reset=True)
+                starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+                ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+                barrier(world)
+                torch.cuda.synchronize()
+                for k in range(args.steps):
+                    flush.fill_(float(k))
+                    starts[k].record(stream)
+                    ctx.validate(q0, q1, W, out=out)
+                    ends[k].record(stream)
+                torch.cuda.synchronize()
+                barrier(world)
+                ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)), world)
+                cnt = ctx.work_counters() / max(args.steps, 1)
+                res[early] = dict(ms=ms / args.steps, tests=float(cnt[3:].sum()),
+                                  out={k: v.cpu().numpy() for k, v in out.items()})
+            ctx.set_early_exit(True)
+            same = all(np.array_equal(res[True]["out"][k], res[False]["out"][k])
+                       for k in ("status", "first_fail", "q"))
+            st = res[True]["out"]["status"]
+            if split == 100:
+                total_ms_on = res[True]["ms"] * args.steps
+            rows.append({"boxes": len(sc.box), "early_exit_ms": res[True]["ms"],
+                         "no_early_exit_ms": res[False]["ms"],
+                         "speedup": res[False]["ms"] / res[True]["ms"],
+                         "tests_early_exit": res[True]["tests"],
+                         "tests_no_early_exit": res[False]["tests"],
+                         "identical_outputs": bool(same),
+                         "collision_rate": float((st == 2).mean())})
+        clk = clocks.stop()
+    value = sum_over_ranks(n * W * args.steps, world) / (max_over_ranks(total_ms_on, world) / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_on / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "early-termination ablation: 24 boxes cut into 1/10/100",
+                   "motions": n, "W": W, "dof": rb.dof, "constraint": "roll-pitch",
+                   "motion": "0.3 rad from on-manifold starts",
+                   "value_from": "early exit on, 2400 boxes",
+                   "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "densities": rows,
+        "gpu_launches": int(args.steps * 6),
+        "clocks": clk,
+    }
+    return line, None
+
+
 # ---- config 3: collision checking in GEMM form ---------------------------------------------
 
 CC_N, CC_W = 4096, 64
@@ -1155,14 +1244,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="plan",
-                    choices=["plan", "validate", "batch", "warmstart", "gemmcc"])
+                    choices=["plan", "validate", "batch", "warmstart", "gemmcc", "earlyexit"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
                     help="warm-start training epochs (fewer for profiling runs)")
-    ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch",
+    ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch,earlyexit",
                     help="with the default planner workload on one GPU: the other configurations, "
                          "each run as its own process and reported under 'legs' ('none' to skip)")
     args = ap.parse_args()
@@ -1189,6 +1278,9 @@ def main():
     elif args.workload == "warmstart":
         line, inputs = run_warmstart(args, world, rank, local)
         baseline = cpu_baseline_validate
+    elif args.workload == "earlyexit":
+        line, inputs = run_earlyexit(args, world, rank, local)
+        baseline = None
     else:
         line, inputs = run_validate(args, world, rank, local)
         baseline = cpu_baseline_validate

@@ -476,6 +476,12 @@ int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);
 
+/* Ablation of the paper's early termination (Sec. IV: a collision found by one thread ends
+ * the motion's checks): with enabled = 0, cprrtc_validate and cprrtc_validate_ws check
+ * every waypoint against every candidate obstacle, with the same outputs; the default is 1.
+ * The planner always stops early. Errors: E_INVALID_ARG. */
+int cprrtc_set_early_exit(cprrtc_ctx* ctx, int enabled);
+
 /* Measurement helper with no counterpart in the paper: the FP32 FMA throughput of the
  * context's GPU (TFLOP/s, the best of scalar and packed FP32x2 FMA chains on every SM, CUDA
  * events on the context's stream), the denominator of the FP32 rooflines. Runs for a few

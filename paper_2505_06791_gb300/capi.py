@@ -132,6 +132,7 @@ _SIGS = {
                            C.POINTER(C.c_longlong)],
     "cprrtc_reset_timing": [C.c_void_p],
     "cprrtc_measure_fp32_peak": [C.c_void_p, C.c_void_p],
+    "cprrtc_set_early_exit": [C.c_void_p, C.c_int],
 }
 
 
@@ -291,6 +292,10 @@ class Context:
         out = np.zeros(6, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
+
+    def set_early_exit(self, enabled: bool):
+        """Ablation switch of the early termination of collision checking (default on)."""
+        self._check(self._L.cprrtc_set_early_exit(self.h, int(bool(enabled))))
 
     def measure_fp32_peak(self) -> float:
         """FP32 FMA throughput of this context's GPU in TFLOP/s (measured on the device)."""

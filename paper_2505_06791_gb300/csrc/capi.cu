@@ -78,6 +78,7 @@ struct cprrtc_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   // collision checking in GEMM form
   int cc_mode = CPRRTC_CC_EXACT;
+  int early_exit = 1;  // 0: collision checking skips nothing (ablation)
   double cc_guard = 0.005;
   std::vector<float4> host_sph;  // sphere obstacles as staged (FP32), image row order
   std::vector<float4> host_robot_sph;  // robot spheres {x, y, z, r} in their frames
@@ -901,6 +902,7 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
   a.n = n;
   a.W = W;
   a.cc_skip_first = 0;
+  a.no_early_exit = !ctx->early_exit;
   a.work_counters = ctx->d_work;
   Staging st;
   st.input(q_start, N * dof * sizeof(float), &a.q_start);
@@ -1291,6 +1293,7 @@ int cprrtc_validate_ws(cprrtc_ctx* ctx, const float* q_start, const float* q_end
   a.n = n;
   a.W = W;
   a.cc_skip_first = 0;
+  a.no_early_exit = !ctx->early_exit;
   a.work_counters = ctx->d_work;
   a.warm = ctx->d_warm;
   a.warm_error = mlp_error_flag(ctx->mlp);
@@ -1416,6 +1419,12 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
   cudaError_t e = launch_philox(key0, key1, d_in, n, d_out, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "philox launch");
   return st.end(ctx);
+}
+
+int cprrtc_set_early_exit(cprrtc_ctx* ctx, int enabled) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  ctx->early_exit = enabled ? 1 : 0;
+  return CPRRTC_OK;
 }
 
 int cprrtc_measure_fp32_peak(cprrtc_ctx* ctx, double* tflops) {

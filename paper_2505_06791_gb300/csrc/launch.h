@@ -36,6 +36,7 @@ struct ValidateArgs {
   uint8_t* warm_used;  // [n] 1 when the warm-started segment was accepted (may be null)
   const int* warm_error;  // nonzero: the corrections are not valid; plain Alg. 1 only
   int skip_cc;            // 1: projection only (collision checking is done elsewhere)
+  int no_early_exit;      // 1: collision checking evaluates every waypoint and candidate
   int stage_obs;  // set by the launcher
 };
 

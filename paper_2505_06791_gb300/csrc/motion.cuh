@@ -431,7 +431,8 @@ __device__ __forceinline__ unsigned swept_mask(const ObsView& v, const float4* s
 // q). Returns the smallest colliding waypoint, or -1. With `any_hit`, returns as soon as
 // some waypoint is known to collide (the index is then a colliding waypoint, not
 // necessarily the smallest): the paper's shared flag (Sec. IV), for callers that only need
-// the verdict.
+// the verdict. With early = false (an ablation) nothing is skipped: every waypoint is
+// tested against every candidate and the answer is the same.
 //
 // Exact culling in three levels (a miss at a level proves a miss of everything under it,
 // every radius padded by at least 1e-5 m, far above the FP32 error of the tests):
@@ -446,7 +447,7 @@ template <int WPL>
 __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev& sc,
                                               const float4* __restrict__ obs, const CcShared& S,
                                               const float (&q)[WPL][kMaxDof], int W, int i0,
-                                              bool any_hit, WorkCount& work) {
+                                              bool any_hit, WorkCount& work, bool early = true) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
@@ -600,7 +601,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
     bool any_act = false;
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {
-      act[s] = act[s] && lane + 32 * s < best;
+      act[s] = act[s] && (!early || lane + 32 * s < best);
       any_act |= act[s];
     }
     if (!__any_sync(kFull, any_act)) break;
@@ -637,7 +638,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
           bool any = false;
 #pragma unroll
           for (int s = 0; s < WPL; ++s) {
-            near[s] = act[s] && !hit[s] && hit_view(ov, bc[s][0], bc[s][1], bc[s][2], b.w);
+            near[s] = act[s] && (!early || !hit[s]) && hit_view(ov, bc[s][0], bc[s][1], bc[s][2], b.w);
             any |= near[s];
           }
           work.count_test(sc, o, n_act);
@@ -675,7 +676,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       const unsigned hb = __ballot_sync(kFull, hit[s]);
       if (hb) best = min(best, 32 * s + __ffs(hb) - 1);
     }
-    if (best != 0x7fffffff && (any_hit || best == i0)) break;
+    if (early && best != 0x7fffffff && (any_hit || best == i0)) break;
   }
   return best == 0x7fffffff ? -1 : best;
 }

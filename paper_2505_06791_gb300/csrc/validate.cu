@@ -98,7 +98,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     pr.iters += spent;
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid && !a.skip_cc) {
-      ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work);
+      ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work, !a.no_early_exit);
       if (ff >= 0) st = kCollision;
     }
     if (a.out_q) {

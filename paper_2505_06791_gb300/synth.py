@@ -212,6 +212,26 @@ def make_planning_scene(seed: int, n_sph: int = 100, n_box: int = 60, n_cap: int
     return Scene(f32(sph), f32(box), f32(cap))
 
 
+def make_subdivided_boxes(seed: int, n_boxes: int = 24, split: int = 1) -> Scene:
+    """Axis-aligned boxes with sides U[0.1, 0.4] m, centres uniform in the obstacle cube; each
+    box is cut into `split` equal boxes (split = 10: ten slabs along x; 100: a 10 x 10 grid
+    in x and y), so the occupied volume stays the same while the primitive count grows (the
+    density scaling of Sec. V-A)."""
+    rng = np.random.default_rng(seed)
+    nx, ny = {1: (1, 1), 10: (10, 1), 100: (10, 10)}[split]
+    rows = []
+    for _ in range(n_boxes):
+        c = rng.uniform(CUBE_LO, CUBE_HI)
+        h = rng.uniform(0.1, 0.4, 3) / 2
+        for i in range(nx):
+            for j in range(ny):
+                hx, hy = h[0] / nx, h[1] / ny
+                cx = c[0] - h[0] + (2 * i + 1) * hx
+                cy = c[1] - h[1] + (2 * j + 1) * hy
+                rows.append([cx, cy, c[2], hx, hy, h[2], 1, 0, 0, 0, 1, 0, 0, 0, 1])
+    return Scene(box=f32(np.array(rows)))
+
+
 def make_mixed_scene(seed: int, n_sph: int = 100, n_box: int = 60, n_cap: int = 40) -> Scene:
     """Mixed primitives: spheres r U[0.05,0.15], oriented boxes with sides U[0.05,0.3],
     capsules with length U[0.1,0.4] and radius U[0.02,0.08]."""

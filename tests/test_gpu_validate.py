@@ -348,3 +348,33 @@ def test_line_and_fixed_orientation_single_config_projection(torch_cuda, oracle_
         assert close >= 0.95 * both, (close, both)
     print(ctype, "verdicts", verdict, "both projected", both, "within 1e-4", close)
     ctx.close()
+
+
+def test_early_exit_ablation_gives_identical_outputs(torch_cuda, oracle_mod):
+    """With early termination switched off every waypoint meets every candidate obstacle:
+    more primitive tests, the same outputs (status, first colliding waypoint, waypoints), on
+    sparse and subdivided (dense) box scenes and on mixed primitives."""
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, constraint=c)
+    q0 = manifold_starts(orc, rb, 128, 9800)
+    q1 = S.nearby_configs(rb, q0, 0.3, 9801)
+    far = S.uniform_configs(rb, 128, 9802)
+    for sc in (S.make_subdivided_boxes(41, 24, 1), S.make_subdivided_boxes(41, 24, 100),
+               S.make_mixed_scene(9803)):
+        ctx = make_ctx(rb, sc, c)
+        for end in (q1, far):
+            d0 = torch_cuda.from_numpy(q0.astype(np.float32)).cuda()
+            d1 = torch_cuda.from_numpy(end.astype(np.float32)).cuda()
+            res = {}
+            for early in (True, False):
+                ctx.set_early_exit(early)
+                ctx.work_counters(reset=True)
+                out = {k: parity.to_np(v) for k, v in ctx.validate(d0, d1, 32).items()}
+                res[early] = (out, ctx.work_counters())
+            for k in ("status", "first_fail", "q", "iters"):
+                assert np.array_equal(res[True][0][k], res[False][0][k]), k
+            tests_on, tests_off = res[True][1][3:].sum(), res[False][1][3:].sum()
+            assert tests_off >= tests_on
+            if (res[True][0]["status"] == 2).any():
+                assert tests_off > tests_on
+        ctx.close()
