@@ -808,6 +808,94 @@ def run_earlyexit(args, world, rank, local):
     return line, None
 
 
+# ---- the paper's naive baseline: sequential projection inside the same planner -------------
+
+NAIVE_N = 304
+
+
+def run_naive(args, world, rank, local):
+    """cpRRTC-Naive against cpRRTC-Parallel (Sec. V): the planner of configuration 2 on 304
+    problems (one wave of 2 per SM), once with Alg. 1 and once with the sequential
+    projection; success, plan time and validated waypoints per second for each."""
+    import torch
+    from paper_2505_06791_gb300 import build
+    from paper_2505_06791_gb300.capi import Context
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rb, c = S.make_arm7(1), S.roll_pitch(20)
+    n = NAIVE_N
+    seed = 7 + 1000 * rank
+    scenes = config2_scenes(n, seed)
+    start, goal = gpu_start_goal(rb, c, scenes, seed, local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(local, stream.cuda_stream)
+    ctx.set_robot(rb)
+    ctx.set_constraint(c)
+    ctx.set_scene_batch(scenes)
+    prm = ctx.plan_params(seed=seed, **PLAN_PARAMS)
+    modes = {}
+    with torch.cuda.stream(stream):
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        for name, seq in (("parallel", False), ("naive", True)):
+            ctx.set_projection(seq)
+            out = ctx.alloc_plan_outputs(n, prm, start, edges=False)
+            for _ in range(args.warmup):
+                ctx.plan(start, goal, prm, out=out)
+            stream.synchronize()
+            starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+                ctx.plan(start, goal, prm, out=out)
+                ends[k].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms = max_over_ranks(sum(s_.elapsed_time(e) for s_, e in zip(starts, ends)), world)
+            L = out["path_len"].cpu().numpy()
+            pm = out["plan_ms"].cpu().numpy()
+            wp = int(out["waypoints"].cpu().numpy().sum())
+            work = out["work"].cpu().numpy()
+            solved = L > 0
+            modes[name] = {
+                "ms_per_step": ms / args.steps,
+                "value": sum_over_ranks(wp, world) * args.steps / (ms / 1e3),
+                "success_rate": float(solved.mean()),
+                "p50_plan_ms": float(np.median(pm[solved])) if solved.any() else None,
+                "mean_plan_ms_solved": float(pm[solved].mean()) if solved.any() else None,
+                "mean_rounds": float(out["rounds"].cpu().numpy().mean()),
+                "projection_updates_per_waypoint": float(work[:, 0].sum() / max(wp, 1)),
+            }
+        ctx.set_projection(False)
+        clk = clocks.stop()
+    par, nv = modes["parallel"], modes["naive"]
+    line = {
+        "metric": METRIC, "value": par["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": par["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "cpRRTC-Parallel vs cpRRTC-Naive projection, planner of config 2",
+                   "problems": n, "W": PLAN_PARAMS["W"], "range": PLAN_PARAMS["range_"],
+                   "max_rounds": PLAN_PARAMS["max_rounds"], "constraint": "roll-pitch",
+                   "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "modes": modes,
+        "parallel_vs_naive": {
+            "success_rate_delta": par["success_rate"] - nv["success_rate"],
+            "mean_solved_plan_ms_ratio": (nv["mean_plan_ms_solved"] / par["mean_plan_ms_solved"])
+            if par["mean_plan_ms_solved"] and nv["mean_plan_ms_solved"] else None,
+            "paper": "Parallel 1.1x faster, success +19 % (Sec. V, RTX 5090, MotionBenchMaker)"},
+        "gpu_launches": int(2 * args.steps),
+        "clocks": clk,
+    }
+    return line, None
+
+
 # ---- config 3: collision checking in GEMM form ---------------------------------------------
 
 CC_N, CC_W = 4096, 64
@@ -1244,14 +1332,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="plan",
-                    choices=["plan", "validate", "batch", "warmstart", "gemmcc", "earlyexit"])
+                    choices=["plan", "validate", "batch", "warmstart", "gemmcc", "earlyexit",
+                             "naive"])
     ap.add_argument("--problems", type=int, default=PLAN_N)
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
                     help="warm-start training epochs (fewer for profiling runs)")
-    ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch,earlyexit",
+    ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch,earlyexit,naive",
                     help="with the default planner workload on one GPU: the other configurations, "
                          "each run as its own process and reported under 'legs' ('none' to skip)")
     args = ap.parse_args()
@@ -1280,6 +1369,9 @@ def main():
         baseline = cpu_baseline_validate
     elif args.workload == "earlyexit":
         line, inputs = run_earlyexit(args, world, rank, local)
+        baseline = None
+    elif args.workload == "naive":
+        line, inputs = run_naive(args, world, rank, local)
         baseline = None
     else:
         line, inputs = run_validate(args, world, rank, local)

@@ -476,6 +476,19 @@ int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);
 
+/* The projection the validation and the planner use: CPRRTC_PROJECTION_PARALLEL (Alg. 1,
+ * the default) or CPRRTC_PROJECTION_SEQUENTIAL, the paper's naive baseline (cpRRTC-Naive,
+ * Sec. V, CBiRRT-style): waypoints 1..W-1 one after another, each by damped steps from its
+ * interpolated point moved by the previous waypoint's correction until ||E_task||_inf <
+ * tol_task (at most max_iters steps), failing at the first waypoint that does not converge
+ * or ends farther than tau + tol_sm from its predecessor; iters reports the total steps
+ * (capped at 255). It takes ROLL_PITCH or Z_PLANE, and W <= 32 for planning (else
+ * E_UNSUPPORTED); cprrtc_validate_ws and the uneven batch always use
+ * Alg. 1. Errors: E_INVALID_ARG. */
+#define CPRRTC_PROJECTION_PARALLEL 0
+#define CPRRTC_PROJECTION_SEQUENTIAL 1
+int cprrtc_set_projection(cprrtc_ctx* ctx, int mode);
+
 /* Ablation of the paper's early termination (Sec. IV: a collision found by one thread ends
  * the motion's checks): with enabled = 0, cprrtc_validate and cprrtc_validate_ws check
  * every waypoint against every candidate obstacle, with the same outputs; the default is 1.

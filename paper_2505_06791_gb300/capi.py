@@ -133,6 +133,7 @@ _SIGS = {
     "cprrtc_reset_timing": [C.c_void_p],
     "cprrtc_measure_fp32_peak": [C.c_void_p, C.c_void_p],
     "cprrtc_set_early_exit": [C.c_void_p, C.c_int],
+    "cprrtc_set_projection": [C.c_void_p, C.c_int],
 }
 
 
@@ -292,6 +293,10 @@ class Context:
         out = np.zeros(6, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
+
+    def set_projection(self, sequential: bool):
+        """Alg. 1 (default) or the naive baseline's sequential projection."""
+        self._check(self._L.cprrtc_set_projection(self.h, int(bool(sequential))))
 
     def set_early_exit(self, enabled: bool):
         """Ablation switch of the early termination of collision checking (default on)."""

@@ -79,6 +79,7 @@ struct cprrtc_ctx {
   // collision checking in GEMM form
   int cc_mode = CPRRTC_CC_EXACT;
   int early_exit = 1;  // 0: collision checking skips nothing (ablation)
+  int projection = CPRRTC_PROJECTION_PARALLEL;
   double cc_guard = 0.005;
   std::vector<float4> host_sph;  // sphere obstacles as staged (FP32), image row order
   std::vector<float4> host_robot_sph;  // robot spheres {x, y, z, r} in their frames
@@ -308,7 +309,11 @@ std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres)
 // The planner kernel's registers bound its CTA size: with two waypoints per lane (W > 32)
 // fewer than the maximum 16 workers fit.
 int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char* who) {
-  const int mw = plan_max_workers(ctx->cs.type, pp->W);
+  const bool seq = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
+  if (seq && (pp->W > 32 || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane)))
+    return fail(ctx, CPRRTC_E_UNSUPPORTED,
+                std::string(who) + ": the sequential projection plans with ROLL_PITCH or Z_PLANE and W <= 32");
+  const int mw = plan_max_workers(ctx->cs.type, pp->W, seq);
   if (pp->workers > mw)
     return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": at most " + std::to_string(mw) +
                                                " workers fit one CTA at W = " + std::to_string(pp->W));
@@ -903,6 +908,10 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
   a.W = W;
   a.cc_skip_first = 0;
   a.no_early_exit = !ctx->early_exit;
+  a.sequential = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
+  if (a.sequential && ctx->cs.type != kConsNone && ctx->cs.type != kConsRollPitch &&
+      ctx->cs.type != kConsZPlane)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the sequential projection takes ROLL_PITCH or Z_PLANE");
   a.work_counters = ctx->d_work;
   Staging st;
   st.input(q_start, N * dof * sizeof(float), &a.q_start);
@@ -1367,6 +1376,7 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   a.max_path = pp->max_path;
   a.seed = pp->seed;
   a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
+  a.sequential = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
   a.work_counters = ctx->d_work;
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
@@ -1419,6 +1429,14 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
   cudaError_t e = launch_philox(key0, key1, d_in, n, d_out, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "philox launch");
   return st.end(ctx);
+}
+
+int cprrtc_set_projection(cprrtc_ctx* ctx, int mode) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (mode != CPRRTC_PROJECTION_PARALLEL && mode != CPRRTC_PROJECTION_SEQUENTIAL)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_projection: unknown mode");
+  ctx->projection = mode;
+  return CPRRTC_OK;
 }
 
 int cprrtc_set_early_exit(cprrtc_ctx* ctx, int enabled) {
@@ -1571,6 +1589,7 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   a.max_path = pp->max_path;
   a.seed = pp->seed;
   a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
+  a.sequential = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;

@@ -37,6 +37,7 @@ struct ValidateArgs {
   const int* warm_error;  // nonzero: the corrections are not valid; plain Alg. 1 only
   int skip_cc;            // 1: projection only (collision checking is done elsewhere)
   int no_early_exit;      // 1: collision checking evaluates every waypoint and candidate
+  int sequential;         // 1: the naive baseline's sequential projection instead of Alg. 1
   int stage_obs;  // set by the launcher
 };
 
@@ -50,6 +51,7 @@ struct PlanArgs {
   int W, max_rounds, workers, max_nodes, max_connect, max_path;
   uint32_t seed;
   unsigned long long budget_ns;  // per-problem device-time budget (0: none)
+  int sequential;                // 1: the naive baseline's sequential projection
   const float4* scene_obs;  // scene batch: obstacle stream
   const int4* scenes;       // [n] {float4 offset, n_sph, n_box, n_cap}; null: shared scene
   int max_scene_f4;         // largest scene, float4 slots
@@ -103,7 +105,7 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
 // Most workers (warps per CTA) the planner kernel for this constraint type and W can launch
 // with (its registers per thread bound the CTA size); 0 if the query fails.
-int plan_max_workers(int cons_type, int W);
+int plan_max_workers(int cons_type, int W, bool sequential = false);
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,

@@ -172,6 +172,83 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
   return res;
 }
 
+// The sequential projection of the naive baseline (cpRRTC-Naive, Sec. V; CBiRRT-style):
+// waypoints 1..W-1 one after another, each by damped steps from its interpolated point moved
+// by the previous waypoint's correction, until ||E_task||_inf < tol_task (at most max_iters
+// steps). It fails at the first waypoint that does not converge or ends farther than
+// tau + tol_sm (in some joint) from its predecessor. Every lane takes the same steps (the
+// other waypoints wait, as in the baseline); lane i % 32 keeps waypoint i. iters is the
+// total number of steps.
+template <int CT, int WPL>
+__device__ __forceinline__ ProjResult project_sequential(const RobotDev& rb, const ConsDev& c,
+                                                         int max_iters, const float* q0,
+                                                         const float* q1,
+                                                         float (&q)[WPL][kMaxDof], int W,
+                                                         float tau) {
+  const int lane = threadIdx.x & 31;
+  const int dof = rb.dof;
+  ProjResult res{kValid, 0, -1, 0.f, 0};
+  if (CT == kConsNone) return res;
+  float prev_p[kMaxDof], prev_i[kMaxDof];  // previous waypoint: projected, interpolated
+#pragma unroll
+  for (int k = 0; k < kMaxDof; ++k) prev_p[k] = prev_i[k] = k < dof ? q0[k] : 0.f;
+  float resid = 0.f;
+  for (int i = 1; i < W; ++i) {
+    float qi[kMaxDof], x[kMaxDof];
+    interp(q0, q1, i, W, dof, qi);
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k)
+      x[k] = k < dof ? fminf(fmaxf(qi[k] + (prev_p[k] - prev_i[k]), rb.j[k].lo), rb.j[k].hi) : 0.f;
+    ChainState cs;
+    bool ok = false;
+    float err = 0.f;
+    int it = 0;
+    for (;; ++it) {
+      chain(rb, x, nullptr, cs);
+      TaskEval<CT> te;
+      te.eval(rb, c, cs);
+      err = te.err_inf();
+      if (err < c.tol_task) {
+        ok = true;
+        break;
+      }
+      if (it == max_iters) break;
+      te.solve(rb, c, cs);
+      float g[kMaxDof];
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k) g[k] = k < dof ? te.step(rb, cs, k) : 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) x[k] = fminf(fmaxf(fmaf(-c.alpha, g[k], x[k]), rb.j[k].lo), rb.j[k].hi);
+    }
+    res.iters += it;
+    res.updates += it;
+    float step = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k)
+      if (k < dof) step = fmaxf(step, fabsf(x[k] - prev_p[k]) - tau);
+#pragma unroll
+    for (int s = 0; s < WPL; ++s)
+      if (i == lane + 32 * s) {
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k) q[s][k] = x[k];
+      }
+    resid = fmaxf(resid, err);
+    if (!ok || step >= c.tol_sm) {
+      res.status = kProjFail;
+      res.first_fail = i;
+      break;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) {
+      prev_p[k] = x[k];
+      prev_i[k] = qi[k];
+    }
+  }
+  res.resid = resid;
+  return res;
+}
+
 // Shared-memory layout of the motion kernels, in bytes from the dynamic shared base:
 //   obstacles (staged only when they fit) | robot spheres (sorted by frame) | frame bounds |
 //   spheres per frame | first sphere of each frame | joints |

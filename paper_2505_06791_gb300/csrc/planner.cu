@@ -183,7 +183,7 @@ struct MotionWork {  // per warp (32-bit suffices for one launch)
 
 // Interpolate q0 -> q1, project (at most max_iters iterations), FK + CC from waypoint 1
 // stopping at the first collision found.
-template <int CT, int WPL>
+template <int CT, int WPL, bool SEQ = false>
 __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDev& sc,
                                                const ConsDev& cs, int max_iters, MotionWork& work,
                                                WorkCount& wc, const float4* obs,
@@ -194,7 +194,11 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 #pragma unroll
   for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
   const float tau = step_threshold(cs, q0, q1, W, rb.dof);
-  const ProjResult pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau);
+  ProjResult pr;
+  if constexpr (SEQ)
+    pr = project_sequential<CT, WPL>(rb, cs, max_iters, q0, q1, q, W, tau);
+  else
+    pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau);
   __syncwarp();
   work.proj += (unsigned)pr.updates;
   wc.updates += (unsigned)pr.updates;
@@ -219,7 +223,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 
 // The planner for one problem, run by the whole CTA (one warp per worker). Shared memory
 // (robot tables, obstacles, per-warp scratch) is staged by the caller.
-template <int CT, int WPL>
+template <int CT, int WPL, bool SEQ = false>
 __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
@@ -295,7 +299,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     }
     float q[WPL][kMaxDof];
     // the closing hop is checked as it stands: one Alg. 1 iteration
-    const int st = validate_motion<CT, WPL>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
+    const int st = validate_motion<CT, WPL, SEQ>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
                                             cur, q1, W, q);
     wp += W;
     int add = 0, conn = 0;
@@ -453,7 +457,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   }
 }
 
-template <int CT, int WPL>
+template <int CT, int WPL, bool SEQ = false>
 __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
                                              PlanArgs a) {
   const int p = blockIdx.x;
@@ -498,7 +502,7 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     P.estride = (int)wd;
   }
   __syncthreads();
-  plan_problem<CT, WPL>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
+  plan_problem<CT, WPL, SEQ>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
   wc.flush(a.work_counters);
 }
 
@@ -607,8 +611,14 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
   return cudaGetLastError();
 }
 
-static const void* plan_fn(int ct, int W) {
+static const void* plan_fn(int ct, int W, bool sequential = false) {
   const bool two = W > 32;
+  if (sequential) {  // the naive baseline's projection: roll-pitch and z-plane, W <= 32
+    if (two) return nullptr;
+    if (ct == kConsRollPitch) return (const void*)plan_kernel<kConsRollPitch, 1, true>;
+    if (ct == kConsZPlane) return (const void*)plan_kernel<kConsZPlane, 1, true>;
+    return nullptr;
+  }
   switch (ct) {
     case kConsRollPitch:
       return two ? (const void*)plan_kernel<kConsRollPitch, 2> : (const void*)plan_kernel<kConsRollPitch, 1>;
@@ -625,9 +635,11 @@ static const void* plan_fn(int ct, int W) {
   }
 }
 
-int plan_max_workers(int cons_type, int W) {
+int plan_max_workers(int cons_type, int W, bool sequential) {
   cudaFuncAttributes attr;
-  if (cudaFuncGetAttributes(&attr, plan_fn(cons_type, W)) != cudaSuccess) {
+  const void* fn = plan_fn(cons_type, W, sequential);
+  if (!fn) return 0;
+  if (cudaFuncGetAttributes(&attr, fn) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -645,7 +657,8 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
   a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
   if (!a.stage_obs) smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, false);
   if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-  const void* fn = plan_fn(cs.type, a.W);
+  const void* fn = plan_fn(cs.type, a.W, a.sequential != 0);
+  if (!fn) return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {const_cast<RobotDev*>(&rb), const_cast<SceneDev*>(&sc),

@@ -9,7 +9,7 @@ namespace cprrtc {
 // stream is staged there too when it fits (coalesced float4 copies), else read from
 // global memory through L1. The first colliding waypoint is exact (no early exit).
 // (No __launch_bounds__: with it, ptxas caps registers low enough to spill here.)
-template <int CT, int WPL>
+template <int CT, int WPL, bool SEQ = false>
 __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int n4 = sc.n_float4();
@@ -87,7 +87,10 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
               q[s][k] = fminf(fmaxf(q[s][k] + fmaf(-taper, y0[k], y[k]), rb.j[k].lo), rb.j[k].hi);
         }
       }
-      pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? a.refine_iters : cs.max_iters, q, W, tau);
+      if constexpr (SEQ)
+        pr = project_sequential<CT, WPL>(rb, cs, cs.max_iters, q0, q1, q, W, tau);
+      else
+        pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? a.refine_iters : cs.max_iters, q, W, tau);
       work.updates += (unsigned)pr.updates;
       if (pass == 0 && pr.status == kValid) {
         warm_ok = 1;
@@ -116,7 +119,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     if (lane == 0) {
       a.status[m] = (uint8_t)st;
       if (a.first_fail) a.first_fail[m] = ff;
-      if (a.iters) a.iters[m] = (uint8_t)pr.iters;
+      if (a.iters) a.iters[m] = (uint8_t)min(pr.iters, 255);
       if (a.resid) a.resid[m] = pr.resid;
       if (a.warm_used) a.warm_used[m] = (uint8_t)warm_ok;
     }
@@ -164,8 +167,17 @@ __global__ void project_configs_kernel(RobotDev rb, ConsDev cs, const float* __r
   if (resid) resid[m] = err;
 }
 
-static const void* validate_fn(int ct, int W) {
+static const void* validate_fn(int ct, int W, bool sequential) {
   const bool two = W > 32;
+  if (sequential) {  // the naive baseline's projection: roll-pitch and z-plane
+    if (ct == kConsRollPitch)
+      return two ? (const void*)validate_kernel<kConsRollPitch, 2, true>
+                 : (const void*)validate_kernel<kConsRollPitch, 1, true>;
+    if (ct == kConsZPlane)
+      return two ? (const void*)validate_kernel<kConsZPlane, 2, true>
+                 : (const void*)validate_kernel<kConsZPlane, 1, true>;
+    return nullptr;
+  }
   switch (ct) {
     case kConsRollPitch:
       return two ? (const void*)validate_kernel<kConsRollPitch, 2> : (const void*)validate_kernel<kConsRollPitch, 1>;
@@ -195,7 +207,8 @@ cudaError_t launch_validate(const RobotDev& rb, const SceneDev& sc, const ConsDe
   a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
   if (!a.stage_obs) smem = validate_smem_bytes(rb, sc, a.W, false);
   if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-  const void* fn = validate_fn(cs.type, a.W);
+  const void* fn = validate_fn(cs.type, a.W, a.sequential != 0 && cs.type != kConsNone);
+  if (!fn) return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

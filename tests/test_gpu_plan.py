@@ -199,3 +199,23 @@ def test_plan_line_and_fixed_orientation(torch_cuda, oracle_mod, ctype):
     assert checked >= 1, "no path to check"
     print(ctype, "solved", checked, "of 8")
     ctx.close()
+
+
+def test_plan_with_sequential_projection(torch_cuda, oracle_mod):
+    """The naive baseline's planner (sequential projection, Sec. V): paths re-validated by
+    the oracle; modes it does not support are refused."""
+    from paper_2505_06791_gb300.capi import CprrtcError, E_UNSUPPORTED
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 8, 9950, counts=(40, 20, 10))
+    ctx = ctx_for(rb, c)
+    ctx.set_projection(True)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=400, workers=8, seed=6)
+    out = run_plan(torch_cuda, ctx, scenes, start, goal, prm)
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
+    assert not issues, issues[:10]
+    assert checked >= 1
+    with pytest.raises(CprrtcError) as e:
+        run_plan(torch_cuda, ctx, None, start, goal, ctx.plan_params(W=64, seed=6))
+    assert e.value.code == E_UNSUPPORTED
+    print("sequential planner solved", checked, "of 8")
+    ctx.close()

@@ -378,3 +378,44 @@ def test_early_exit_ablation_gives_identical_outputs(torch_cuda, oracle_mod):
             if (res[True][0]["status"] == 2).any():
                 assert tests_off > tests_on
         ctx.close()
+
+
+def test_sequential_projection_parity(torch_cuda, oracle_mod):
+    """The naive baseline's sequential projection (cpRRTC-Naive, Sec. V) on the GPU against
+    the oracle's: the same verdict and failing waypoint, projected waypoints within 1e-4, the
+    same total number of damped steps, on short and long roll-pitch motions (at least 95 %:
+    FP32 and FP64 may take a threshold decision differently); collision verdicts of the
+    projected motions agree with the oracle's clearances."""
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    sc = S.make_mixed_scene(9900, 30, 10, 10)
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 96, 9901)
+    W = 32
+    for q1 in (S.nearby_configs(rb, q0, 0.3, 9902), S.uniform_configs(rb, 96, 9903)):
+        ctx = make_ctx(rb, sc, c)
+        ctx.set_projection(True)
+        out = {k: parity.to_np(v) for k, v in ctx.validate(
+            torch_cuda.from_numpy(q0.astype(np.float32)).cuda(),
+            torch_cuda.from_numpy(q1.astype(np.float32)).cuda(), W).items()}
+        ctx.close()
+        agree = 0
+        for m in range(len(q0)):
+            xi = oracle_mod.interpolate(S.f32(q0[m]), S.f32(q1[m]), W)
+            tau = oracle_mod.tau_step(c, S.f32(q0[m]), S.f32(q1[m]), W)
+            ok, xo, ff, tot = orc.project_motion_sequential(xi, tau)
+            g_ok = out["status"][m] != 1
+            same = ok == g_ok and int(out["iters"][m]) == min(tot, 255)
+            if same and not ok:
+                same = int(out["first_fail"][m]) == ff
+            if same and ok:
+                same = np.abs(out["q"][m].astype(np.float64) - xo).max() < 1e-4
+                if same:  # collision verdict on the GPU's own waypoints
+                    cl = np.array([orc.config_clearance(x) for x in out["q"][m]])
+                    hit = np.nonzero(cl < 0)[0]
+                    ref_ff = int(hit[0]) if len(hit) else -1
+                    if np.abs(cl).min() > 1e-5:
+                        assert int(out["first_fail"][m]) == ref_ff, (m, ref_ff, out["first_fail"][m])
+            agree += same
+        assert agree >= 0.95 * len(q0), agree
+        print("sequential agreement", agree, "of", len(q0),
+              np.bincount(out["status"], minlength=3))
