@@ -1116,7 +1116,27 @@ def run_warmstart(args, world, rank, local):
         clocks.start()
         ms_plain, kt_plain = timed(lambda: ctx.validate(q0, q1, W, out=out_p))
         ms_ws, kt_ws = timed(lambda: ctx.validate_ws(q0, q1, W, WS_REFINE, out=out_w))
+        # the planner's motions (steering range 0.3 rad, as in configurations 2 and 5):
+        # plain against warm start on the same starts
+        q1s = torch.from_numpy(S.nearby_configs(rb, q0.cpu().numpy(), 0.3,
+                                                61_000 + 97 * rank).astype(np.float32)).to(dev)
+        out_ps = ctx.alloc_validate_outputs(n, W, q0)
+        out_ws = ctx.alloc_validate_outputs(n, W, q0)
+        for _ in range(args.warmup):
+            ctx.validate(q0, q1s, W, out=out_ps)
+            ctx.validate_ws(q0, q1s, W, WS_REFINE, out=out_ws)
+        ms_ps, _ = timed(lambda: ctx.validate(q0, q1s, W, out=out_ps))
+        ms_wss, _ = timed(lambda: ctx.validate_ws(q0, q1s, W, WS_REFINE, out=out_ws))
         clk = clocks.stop()
+    Ps = {k: v.cpu().numpy() for k, v in out_ps.items()}
+    Ws_ = {k: v.cpu().numpy() for k, v in out_ws.items()}
+    short = {"motion": "0.3 rad from the same starts (planner steering range)",
+             "plain_ms_per_step": ms_ps / args.steps, "warm_start_ms_per_step": ms_wss / args.steps,
+             "plain_projected": int((Ps["status"] != 1).sum()),
+             "warm_start_projected": int((Ws_["status"] != 1).sum()),
+             "plain_mean_iters": float(Ps["iters"].astype(float).mean()),
+             "warm_start_mean_iters": float(Ws_["iters"].astype(float).mean()),
+             "warm_used": float(Ws_["warm"].astype(bool).mean())}
 
     P = {k: v.cpu().numpy() for k, v in out_p.items()}
     Wr = {k: v.cpu().numpy() for k, v in out_w.items()}
@@ -1175,6 +1195,7 @@ def run_warmstart(args, world, rank, local):
                        "lost": int((p_ok & ~w_ok).sum()),
                        "infer_ms_per_step": infer_avg_s * 1e3,
                        "validate_ms_per_step": vk_ms / max(vk_launches, 1)},
+        "planner_like_motions": short,
         "training": {"pairs": int(q_tr.shape[0]), "pair_generation_s": pairs_s,
                      "epochs": args.train_epochs, "batch": 1024, "lr": 1e-3, "train_s": train_s,
                      "samples_per_s": args.train_epochs * q_tr.shape[0] / train_s,

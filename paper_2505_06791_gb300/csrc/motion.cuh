@@ -605,6 +605,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
   const int n_chunks = sc.n_chunks();
   int cb = 0;          // next group of 32 chunks to screen
   unsigned near = 0u;  // chunks of the current group (base cb - 32) still to list
+  unsigned cfr = 0u;   // lane j: the frames whose swept bound chunk cb - 32 + j's box touches
   bool listed_all = false;
   while (!listed_all) {
     // ---- candidate list: obstacles touching a swept bound, with the frames they touch ----
@@ -617,19 +618,19 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
         }
         // lanes screen 32 chunks at once: chunk box against every swept frame bound
         const int ch = cb + lane;
-        bool hit_chunk = false;
+        cfr = 0u;
         if (ch < n_chunks) {
           const float4* cbx = obs + sc.chunk_off() + 2 * ch;
           const float4 lo = cbx[0], hi = cbx[1];
-          hit_chunk = frames_touched(S.sbnd, fmask, [&](float4 b) {
-                        const float e0 = fmaxf(fmaxf(lo.x - b.x, b.x - hi.x), 0.f);
-                        const float e1 = fmaxf(fmaxf(lo.y - b.y, b.y - hi.y), 0.f);
-                        const float e2 = fmaxf(fmaxf(lo.z - b.z, b.z - hi.z), 0.f);
-                        const float rr = b.w + 1e-5f;
-                        return fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < rr * rr;
-                      }) != 0u;
+          cfr = frames_touched(S.sbnd, fmask, [&](float4 b) {
+                  const float e0 = fmaxf(fmaxf(lo.x - b.x, b.x - hi.x), 0.f);
+                  const float e1 = fmaxf(fmaxf(lo.y - b.y, b.y - hi.y), 0.f);
+                  const float e2 = fmaxf(fmaxf(lo.z - b.z, b.z - hi.z), 0.f);
+                  const float rr = b.w + 1e-5f;
+                  return fmaf(e0, e0, fmaf(e1, e1, e2 * e2)) < rr * rr;
+                });
         }
-        near = __ballot_sync(kFull, hit_chunk);
+        near = __ballot_sync(kFull, cfr != 0u);
         work.p_box += (unsigned)(rb.bound_count * min(32, n_chunks - cb));
         cb += 32;
         continue;
@@ -654,14 +655,16 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
         m &= m - 1u;
       }
       near &= ~(kmask ^ m);  // the chunks taken
+      // an obstacle can only touch the swept bounds its chunk's box touches
+      const unsigned my_fr = __shfl_sync(kFull, cfr, my_c >= 0 ? my_c - base : 0);
       int o = -1;
       unsigned mask = 0u;
       if (my_c >= 0) o = k_o0 + (my_c - k_c0) * kChunk + lane % kChunk;
       const bool valid = o >= 0 && o < k_o1;
       int box_tests = 0;
-      if (valid) mask = swept_mask(load_obstacle(sc, obs, o), S.sbnd, fmask, box_tests);
-      {  // balls (spheres, and the balls containing boxes) or capsules against every bound
-        const unsigned tested = (unsigned)(__popc(__ballot_sync(kFull, valid)) * rb.bound_count);
+      if (valid) mask = swept_mask(load_obstacle(sc, obs, o), S.sbnd, my_fr, box_tests);
+      {  // balls (spheres, and the balls containing boxes) or capsules against those bounds
+        const unsigned tested = __reduce_add_sync(kFull, valid ? (unsigned)__popc(my_fr) : 0u);
         if (kind == 2)
           work.p_cap += tested;
         else
