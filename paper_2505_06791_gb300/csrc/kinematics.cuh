@@ -34,9 +34,10 @@ struct ChainState {
 };
 
 // Runs the DH chain for configuration q. If `fr` is non-null, frames 1..dof are written to
-// fr[(k-1)*12 ..] as {x, y, z, p}.
+// fr[(k-1)*12 ..] as {x, y, z, p}; if `wq` is non-null, each joint's {sin, cos} (revolute)
+// or {q, 0} (prismatic) to wq[k] (the collision check's per-waypoint cache).
 __device__ __forceinline__ void chain(const RobotDev& rb, const float* q, float* fr,
-                                      ChainState& s) {
+                                      ChainState& s, float2* wq = nullptr) {
   float x0 = 1.f, x1 = 0.f, x2 = 0.f;
   float y0 = 0.f, y1 = 1.f, y2 = 0.f;
   float z0 = 0.f, z1 = 0.f, z2 = 1.f;
@@ -59,8 +60,10 @@ __device__ __forceinline__ void chain(const RobotDev& rb, const float* q, float*
         ct = J.ct0;
         st = J.st0;
         d += q[k];
+        if (wq) wq[k] = make_float2(q[k], 0.f);
       } else {
         sincospif((J.theta0 + q[k]) * kInvPi, &st, &ct);
+        if (wq) wq[k] = make_float2(st, ct);
       }
       const float u0 = fmaf(x0, ct, y0 * st), u1 = fmaf(x1, ct, y1 * st), u2 = fmaf(x2, ct, y2 * st);
       const float v0 = fmaf(y0, ct, -x0 * st), v1 = fmaf(y1, ct, -x1 * st), v2 = fmaf(y2, ct, -x2 * st);

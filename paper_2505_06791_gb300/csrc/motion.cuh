@@ -87,10 +87,13 @@ struct WorkCount {
 // Alg. 1 on the warp's motion, constraint type CT, at most max_iters iterations.
 // q[WPL][kMaxDof] holds this lane's waypoints (the interpolated segment on entry, the
 // segment after the last iteration on exit). With CT = kConsNone nothing is done.
+// With `wq` (the warp's collision-check cache [W][9]), every evaluation also stores each
+// waypoint's joint {sin, cos}: after a success the cache holds those of the returned segment,
+// which the last iteration evaluated.
 template <int CT, int WPL>
 __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const ConsDev& c,
                                                    int max_iters, float (&q)[WPL][kMaxDof],
-                                                   int W, float tau) {
+                                                   int W, float tau, float2* wq = nullptr) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   ProjResult res{kValid, 0, -1, 0.f, 0};
@@ -110,7 +113,7 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
       const int i = lane + 32 * s;
       // every lane evaluates (lanes past W on a clamped copy) so that the shuffles below
       // run converged
-      chain(rb, q[s], nullptr, cs);
+      chain(rb, q[s], nullptr, cs, (wq && i < W) ? wq + i * 9 : nullptr);
       TaskEval<CT> te;
       te.eval(rb, c, cs);
       te.solve(rb, c, cs);
@@ -524,14 +527,16 @@ template <int WPL>
 __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev& sc,
                                               const float4* __restrict__ obs, const CcShared& S,
                                               const float (&q)[WPL][kMaxDof], int W, int i0,
-                                              bool any_hit, WorkCount& work, bool early = true) {
+                                              bool any_hit, WorkCount& work, bool early = true,
+                                              bool wq_ready = false) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
   // each waypoint's joint terms to shared memory once (the chains below walk frames in a
-  // runtime loop, once for the swept bounds and once per pass)
+  // runtime loop, once for the swept bounds and once per pass), unless the projection's last
+  // evaluation left them there (wq_ready)
 #pragma unroll
-  for (int s = 0; s < WPL; ++s) {
+  for (int s = 0; s < WPL && !wq_ready; ++s) {
     const int i = lane + 32 * s;
     if (i < W) {
 #pragma unroll

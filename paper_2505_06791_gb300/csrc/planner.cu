@@ -198,12 +198,12 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
   if constexpr (SEQ)
     pr = project_sequential<CT, WPL>(rb, cs, max_iters, q0, q1, q, W, tau);
   else
-    pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau);
+    pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau, S.wq);
   __syncwarp();
   work.proj += (unsigned)pr.updates;
   wc.updates += (unsigned)pr.updates;
   if (pr.status != kValid) return kProjFail;
-  const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc);
+  const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc, true, !SEQ && CT != kConsNone);
   __syncwarp();
   work.cc += (unsigned)(ff >= 0 ? ff : W - 1);
   return ff >= 0 ? kCollision : kValid;

@@ -90,7 +90,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
       if constexpr (SEQ)
         pr = project_sequential<CT, WPL>(rb, cs, cs.max_iters, q0, q1, q, W, tau);
       else
-        pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? a.refine_iters : cs.max_iters, q, W, tau);
+        pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? a.refine_iters : cs.max_iters, q, W, tau, S.wq);
       work.updates += (unsigned)pr.updates;
       if (pass == 0 && pr.status == kValid) {
         warm_ok = 1;
@@ -101,7 +101,8 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
     pr.iters += spent;
     int st = pr.status, ff = pr.first_fail;
     if (st == kValid && !a.skip_cc) {
-      ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work, !a.no_early_exit);
+      ff = collide_motion<WPL>(rb, sc, obs, S, q, W, a.cc_skip_first, false, work, !a.no_early_exit,
+                               !SEQ && CT != kConsNone);
       if (ff >= 0) st = kCollision;
     }
     if (a.out_q) {
