@@ -14,9 +14,9 @@
 // |s_tensor - s| from the unit roundoff of the precision and the coordinate ranges; folding
 // -E into alpha makes the contraction s - E. A pair with s_tensor - E >= 0 has s >= 0, i.e.
 // clearance >= g > 0: no collision, and no FP32 rounding can turn it into one. An epilogue
-// warp reads its 64 accumulator columns with tensor-memory loads that also return the
-// minimum of what they load: a positive minimum clears all 64 pairs; otherwise (rarely) the
-// row is rechecked against those 64 obstacles with the same FP32 test as the exact
+// warp reads its block of accumulator columns with tensor-memory loads that also return the
+// minimum of what they load: a positive minimum clears all its pairs; otherwise (rarely) the
+// row is rechecked against the block's obstacles with the same FP32 test as the exact
 // collision kernel, on sphere centres computed by the same FK arithmetic, so the verdicts,
 // and each motion's first colliding waypoint, are those of the exact kernel.
 //
@@ -32,15 +32,16 @@
 // chunks stay resident in shared memory (4096 obstacles in BF16); larger images stream
 // through a four-stage ring filled by bulk (TMA) copies.
 //
-// Warp roles (704 threads):
+// Warp roles (kCcThreads threads):
 //   warps 0-3   FK: the chain of the waypoint (one thread, Frame::advance from the base),
 //               then one thread per robot sphere: FP32 centre (Frame::world), the A' row in
 //               the operand layout, and the centre kept for the recheck.
-//   warps 4-19  epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31 and the
-//               64-column quarter (w - 4) / 4 of each N tile (both loads at once, so the
-//               accumulator is released before the tests), takes the loads' minima, and in
-//               the rare case of a minimum <= 0 rechecks those 64 pairs exactly.
-//   warp 20     producer of B' chunks; warp 21 allocates tensor memory and issues the MMAs.
+//   kEpiWarpsCc epilogue warps from warp 4: warp w reads accumulator lanes 32 (w % 4) .. + 31
+//               and column block (w - 4) / 4 (kEpiCols columns) of each N tile in pairs of
+//               32-column loads, releases the accumulator, takes the loads' minima, and in
+//               the rare case of a minimum <= 0 rechecks the block's pairs exactly.
+//   then        the producer of B' chunks, and a warp that allocates tensor memory and
+//               issues the MMAs.
 // Early termination: after each waypoint the epilogue publishes a verdict. Waypoint w of a
 // motion is issued only while waypoint w - 2 was collision-free, so after the first
 // colliding waypoint h exactly one more (h + 1, if it exists) is in flight and is drained.
@@ -57,10 +58,16 @@ namespace cprrtc {
 
 namespace {
 
-constexpr int kCcThreads = 704;
+#ifndef CPRRTC_CC_EPI_WARPS
+#define CPRRTC_CC_EPI_WARPS 16
+#endif
 constexpr int kFkWarps = 4;
-constexpr int kEpiFirst = 4, kEpiWarpsCc = 16;
-constexpr int kProdWarp = 20, kMmaWarpCc = 21;
+// epilogue warps: 4 lane quarters x (kEpiWarpsCc / 4) column blocks of kEpiCols columns
+constexpr int kEpiFirst = 4, kEpiWarpsCc = CPRRTC_CC_EPI_WARPS;
+constexpr int kEpiCols = 256 / (kEpiWarpsCc / 4);
+constexpr int kProdWarp = kEpiFirst + kEpiWarpsCc, kMmaWarpCc = kProdWarp + 1;
+constexpr int kCcThreads = 32 * (kMmaWarpCc + 1);
+static_assert(kEpiWarpsCc % 4 == 0 && kEpiCols % 64 == 0, "epilogue loads go in pairs of 32 columns");
 constexpr int kCcStages = 4;
 constexpr int kChunkBytes = 32768;
 constexpr int kATile = 128 * 128;  // one waypoint's A' (SW128, 128 rows x 128 B)
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     }
   } else if (warp >= kEpiFirst && warp < kEpiFirst + kEpiWarpsCc) {
     const int e = warp - kEpiFirst;
-    const int lq = warp & 3, qc = e >> 2;  // lane quarter, 64-column quarter of each tile
+    const int lq = warp & 3, qc = e >> 2;  // lane quarter, column block of each tile
     const int row = lq * 32 + lane;
     bool ok = true;
     uint32_t g = 0, tcount = 0;
@@ -514,8 +521,8 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
         // the FK warps' centre of this row is read only when a recheck needs it
         const float4* cen_p = s_centre + buf * 128 + row;
         bool hit = false;
-        // per N tile: this warp's 64 columns in two loads issued together; the accumulator
-        // is released as soon as they land, so the next tile's MMA overlaps the tests
+        // per N tile: this warp's columns, two loads at a time; the accumulator is released
+        // as soon as they land, so the next tile's MMA overlaps the tests
         for (int t = 0; ok && t < n_tiles; ++t) {
           const uint32_t tc = tcount + (uint32_t)t, slot = tc & 1;
           if (!__all_sync(0xffffffffu, mb_wait(bar(kAccF + slot), (tc >> 1) & 1, s_abort))) {
@@ -523,19 +530,24 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
             break;
           }
           tca();
-          const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)qc * 64;
-          const float ma = tld32_min(base), mb = tld32_min(base + 32);
-          tld_wait();
-          // some s - E <= 0 among this warp's 64 columns (a NaN would also count)
-          const bool any = !(fminf(ma, mb) > 0.f);
+          const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + slot * 256 + (uint32_t)qc * kEpiCols;
+          float mn = INFINITY;  // loads in pairs, each pair's minima read after its wait
+#pragma unroll
+          for (int u = 0; u < kEpiCols / 32; u += 2) {
+            const float ma = tld32_min(base + 32 * u), mb = tld32_min(base + 32 * u + 32);
+            tld_wait();
+            mn = fminf(mn, fminf(ma, mb));
+          }
+          // some s - E <= 0 among this warp's columns (a NaN would also count)
+          const bool any = !(mn > 0.f);
           tcb();
           __syncwarp();
           if (lane == 0) mb_arrive(bar(kAccE + slot));
           if (any && !drain && cen_p->w >= 0.f) {
-            // rare: recheck this row against the 64 obstacles exactly
+            // rare: recheck this row against the block's obstacles exactly
             const float4 cen = *cen_p;
-            const int j0 = t * 256 + qc * 64;
-            for (int i = 0; i < 64 && !hit; ++i) {
+            const int j0 = t * 256 + qc * kEpiCols;
+            for (int i = 0; i < kEpiCols && !hit; ++i) {
               if (j0 + i < a.n_obs) {
                 ++rechecks;
                 hit = hit_sphere(cen.x, cen.y, cen.z, cen.w, a.obs[j0 + i]);
