@@ -460,7 +460,8 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
 
 /* When enabled, the library records CUDA events around each launch of its kernels on the
  * context's stream. cprrtc_kernel_time returns the summed device time (ms) and the launch
- * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer", "gemm_cc")
+ * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer", "gemm_cc",
+ * "self_collide")
  * since the last reset,
  * synchronising on the events. */
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
@@ -475,6 +476,17 @@ int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
 int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);
+
+/* Self-collision, an addition for realistic arms (the paper's robots' own links are implied
+ * obstacles, Sec. V): frame_pairs [(dof+1)][(dof+1)] (host, row-major; entry (a, b) or
+ * (b, a) nonzero, a != b: the robot spheres of frames a and b are tested against each other,
+ * touching counts as free; pairs on one frame are never tested). After cprrtc_validate's
+ * collision check, motions that are valid or collide later get the first waypoint where
+ * such a pair overlaps (status COLLISION, first_fail that waypoint). n = (dof+1)^2, or 0
+ * (or frame_pairs NULL) to switch it off; set_robot switches it off. cprrtc_plan and
+ * cprrtc_plan_static refuse to run while it is on (E_UNSUPPORTED); cprrtc_validate_ws and
+ * the uneven batch do not test it. Errors: E_INVALID_ARG, E_NOT_CONFIGURED. */
+int cprrtc_set_self_collision(cprrtc_ctx* ctx, const uint8_t* frame_pairs, int n);
 
 /* The projection the validation and the planner use: CPRRTC_PROJECTION_PARALLEL (Alg. 1,
  * the default) or CPRRTC_PROJECTION_SEQUENTIAL, the paper's naive baseline (cpRRTC-Naive,

@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
 class _Robot(C.Structure):
     _fields_ = [("dof", C.c_int), ("joints", C.POINTER(C.c_double)),
                 ("ee", C.POINTER(C.c_double)), ("n_spheres", C.c_int),
-                ("spheres", C.POINTER(C.c_double))]
+                ("spheres", C.POINTER(C.c_double)), ("self_pairs", C.POINTER(C.c_ubyte))]
 
 
 class _Scene(C.Structure):
@@ -90,12 +90,21 @@ def _p(a):
 class Oracle:
     """Holds one robot, scene and constraint (numpy float64 copies) for oracle calls."""
 
-    def __init__(self, robot, scene=None, constraint=None):
+    def __init__(self, robot, scene=None, constraint=None, self_pairs=None):
+        """self_pairs: optional [(dof+1)][(dof+1)] 0/1 matrix of frame pairs whose spheres are
+        tested against each other (self-collision)."""
         self._keep = []
         j, ee, sp = _d(robot.joints), _d(robot.ee), _d(robot.spheres)
         self._keep += [j, ee, sp]
         self.dof = robot.dof
-        self.rb = _Robot(robot.dof, _p(j), _p(ee), len(sp), _p(sp))
+        if self_pairs is None:
+            sp_ptr = None
+        else:
+            pm = np.ascontiguousarray(np.asarray(self_pairs) != 0, np.uint8)
+            assert pm.shape == (robot.dof + 1, robot.dof + 1)
+            self._keep.append(pm)
+            sp_ptr = pm.ctypes.data_as(C.POINTER(C.c_ubyte))
+        self.rb = _Robot(robot.dof, _p(j), _p(ee), len(sp), _p(sp), sp_ptr)
         self.set_scene(scene)
         self.set_constraint(constraint)
 

@@ -413,7 +413,9 @@ double orc_clear_capsule(const double* p, double r, const double* cp) {
   return sqrt(dx * dx + dy * dy + dz * dz) - (r + cp[6]);
 }
 
-/* Min clearance of one configuration over every sphere x obstacle pair. */
+/* Min clearance of one configuration over every sphere x obstacle pair, and, when the robot
+ * names frame pairs for self-collision, over every pair of its spheres on such frames
+ * (distance of the centres minus both radii). */
 static double config_clearance(const orc_robot* rb, const orc_scene* sc, const double* q,
                                double* centres) {
   orc_sphere_centres(rb, q, centres);
@@ -424,6 +426,21 @@ static double config_clearance(const orc_robot* rb, const orc_scene* sc, const d
     for (int o = 0; o < sc->n_sph; ++o) best = fmin(best, orc_clear_sphere(p, r, sc->sph + 4 * o));
     for (int o = 0; o < sc->n_box; ++o) best = fmin(best, orc_clear_box(p, r, sc->box + 15 * o));
     for (int o = 0; o < sc->n_cap; ++o) best = fmin(best, orc_clear_capsule(p, r, sc->cap + 7 * o));
+  }
+  if (rb->self_pairs) {
+    const int nf = rb->dof + 1;
+    for (int s = 0; s < rb->n_spheres; ++s) {
+      const int fs = (int)rb->spheres[5 * s];
+      for (int t = s + 1; t < rb->n_spheres; ++t) {
+        const int ft = (int)rb->spheres[5 * t];
+        if (fs == ft || !rb->self_pairs[fs * nf + ft]) continue;
+        const double* a = centres + 3 * s;
+        const double* b = centres + 3 * t;
+        double d[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+        best = fmin(best, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) -
+                              (rb->spheres[5 * s + 4] + rb->spheres[5 * t + 4]));
+      }
+    }
   }
   return best;
 }

@@ -46,6 +46,9 @@ typedef struct {
   const double* ee;       /* [3] */
   int n_spheres;
   const double* spheres;  /* [n_spheres][5] */
+  /* self-collision: [(dof+1)][(dof+1)], nonzero at (a, b), a != b, when spheres of frames a
+   * and b are tested against each other; NULL: no self-collision test */
+  const unsigned char* self_pairs;
 } orc_robot;
 
 typedef struct {

@@ -134,6 +134,7 @@ _SIGS = {
     "cprrtc_measure_fp32_peak": [C.c_void_p, C.c_void_p],
     "cprrtc_set_early_exit": [C.c_void_p, C.c_int],
     "cprrtc_set_projection": [C.c_void_p, C.c_int],
+    "cprrtc_set_self_collision": [C.c_void_p, C.c_void_p, C.c_int],
 }
 
 
@@ -293,6 +294,14 @@ class Context:
         out = np.zeros(6, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
+
+    def set_self_collision(self, frame_pairs=None):
+        """Self-collision test of cprrtc_validate: frame_pairs [(dof+1)][(dof+1)] 0/1 (None: off)."""
+        if frame_pairs is None:
+            self._check(self._L.cprrtc_set_self_collision(self.h, None, 0))
+            return
+        pm = np.ascontiguousarray(np.asarray(frame_pairs) != 0, np.uint8)
+        self._check(self._L.cprrtc_set_self_collision(self.h, pm.ctypes.data, pm.size))
 
     def set_projection(self, sequential: bool):
         """Alg. 1 (default) or the naive baseline's sequential projection."""

@@ -79,6 +79,8 @@ struct cprrtc_ctx {
   // collision checking in GEMM form
   int cc_mode = CPRRTC_CC_EXACT;
   int early_exit = 1;  // 0: collision checking skips nothing (ablation)
+  bool self_on = false;                   // self-collision after cprrtc_validate
+  unsigned short self_rows[kMaxDof + 1] = {};
   int projection = CPRRTC_PROJECTION_PARALLEL;
   double cc_guard = 0.005;
   std::vector<float4> host_sph;  // sphere obstacles as staged (FP32), image row order
@@ -309,6 +311,8 @@ std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres)
 // The planner kernel's registers bound its CTA size: with two waypoints per lane (W > 32)
 // fewer than the maximum 16 workers fit.
 int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char* who) {
+  if (ctx->self_on)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": self-collision is checked by validate only");
   const bool seq = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
   if (seq && (pp->W > 32 || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane)))
     return fail(ctx, CPRRTC_E_UNSUPPORTED,
@@ -638,6 +642,7 @@ int cprrtc_set_robot(cprrtc_ctx* ctx, const cprrtc_joint* joints, int dof,
   rb.sphere_frame = ctx->d_sframe;
   ctx->rb = rb;
   ctx->has_robot = true;
+  ctx->self_on = false;  // frame pairs belong to a robot: set them again for a new one
   ctx->host_robot_sph = loc;
   if (ctx->cc_mode != CPRRTC_CC_EXACT) return build_cc_image(ctx);  // the bound depends on the robot
   return CPRRTC_OK;
@@ -924,14 +929,9 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
   int rc = st.begin(ctx);
   if (rc) return rc;
   const bool gemm = ctx->cc_mode != CPRRTC_CC_EXACT;
-  if (gemm) {
-    // projection only here; the GEMM-form check needs the projected waypoints and a
+  if (gemm || ctx->self_on) {
+    // the GEMM-form check and the self-collision pass need the projected waypoints and a
     // first-failure array even when the caller does not ask for them
-    if (ctx->sc.n_box || ctx->sc.n_cap)
-      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes sphere obstacles only");
-    if (ctx->rb.n_spheres > 128)
-      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes at most 128 robot spheres");
-    a.skip_cc = 1;
     if (!a.out_q) {
       const size_t need = N * W * dof * sizeof(float);
       if (need > ctx->cc_q_cap) {
@@ -939,7 +939,7 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
         ctx->d_cc_q = nullptr;
         ctx->cc_q_cap = 0;
         cudaError_t e = cudaMalloc(&ctx->d_cc_q, need);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form waypoint buffer");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: waypoint buffer");
         ctx->cc_q_cap = need;
       }
       a.out_q = ctx->d_cc_q;
@@ -951,11 +951,19 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
         ctx->d_cc_ff = nullptr;
         ctx->cc_ff_cap = 0;
         cudaError_t e = cudaMalloc(&ctx->d_cc_ff, need);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form buffer");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: first-failure buffer");
         ctx->cc_ff_cap = need;
       }
       a.first_fail = ctx->d_cc_ff;
     }
+  }
+  if (gemm) {
+    // projection only here
+    if (ctx->sc.n_box || ctx->sc.n_cap)
+      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes sphere obstacles only");
+    if (ctx->rb.n_spheres > 128)
+      return fail(ctx, CPRRTC_E_UNSUPPORTED, "validate: the GEMM-form check takes at most 128 robot spheres");
+    a.skip_cc = 1;
   }
   LaunchTimer tm(ctx, "validate");
   cudaError_t e = launch_validate(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
@@ -983,6 +991,20 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
     e = launch_gemm_cc(ctx->cc_mode == CPRRTC_CC_GEMM_TF32, ctx->rb, g, ctx->dev.sm_count, ctx->stream);
     tg.done();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form check launch");
+  }
+  if (ctx->self_on) {
+    SelfArgs sa{};
+    sa.q = a.out_q;
+    sa.n = n;
+    sa.W = W;
+    sa.i0 = a.cc_skip_first;
+    sa.status = a.status;
+    sa.first_fail = a.first_fail;
+    for (int f = 0; f <= kMaxDof; ++f) sa.rows[f] = ctx->self_rows[f];
+    LaunchTimer ts(ctx, "self_collide");
+    e = launch_self_collide(ctx->rb, sa, ctx->stream);
+    ts.done();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: self-collision launch");
   }
   rc = st.end(ctx);
   if (rc == CPRRTC_OK && gemm && st.any_host) {
@@ -1429,6 +1451,28 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
   cudaError_t e = launch_philox(key0, key1, d_in, n, d_out, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "philox launch");
   return st.end(ctx);
+}
+
+int cprrtc_set_self_collision(cprrtc_ctx* ctx, const uint8_t* frame_pairs, int n) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (n == 0 || !frame_pairs) {
+    ctx->self_on = false;
+    return CPRRTC_OK;
+  }
+  if (!ctx->has_robot) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "set_self_collision: set_robot first");
+  const int nf = ctx->rb.dof + 1;
+  if (n != nf * nf)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_self_collision: n must be (dof + 1)^2");
+  for (int f = 0; f <= kMaxDof; ++f) ctx->self_rows[f] = 0;
+  bool any = false;
+  for (int i = 0; i < nf; ++i)
+    for (int j = i + 1; j < nf; ++j)
+      if (frame_pairs[i * nf + j] || frame_pairs[j * nf + i]) {
+        ctx->self_rows[i] |= (unsigned short)(1u << j);
+        any = true;
+      }
+  ctx->self_on = any;
+  return CPRRTC_OK;
 }
 
 int cprrtc_set_projection(cprrtc_ctx* ctx, int mode) {

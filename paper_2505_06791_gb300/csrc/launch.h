@@ -110,6 +110,18 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
                           cudaStream_t stream);
+// Self-collision after validation (self_collide.cu): motions that are valid or collide
+// later get the first waypoint where spheres of two paired frames overlap.
+struct SelfArgs {
+  const float* q;        // [n][W][dof] the returned waypoints
+  int n, W, i0;          // waypoints i0..W-1 are checked
+  uint8_t* status;       // [n] updated in place
+  int* first_fail;       // [n] updated in place
+  unsigned short rows[kMaxDof + 1];  // bit b of rows[a] (a < b): test frames a and b
+};
+size_t self_collide_smem_bytes();
+cudaError_t launch_self_collide(const RobotDev& rb, const SelfArgs& a, cudaStream_t stream);
+
 // FP32 FMA throughput (TFLOP/s) measured with FMA chains on every SM (fp32_peak.cu).
 cudaError_t measure_fp32_peak(const DeviceInfo& dev, cudaStream_t stream, double* tflops);
 

@@ -353,3 +353,11 @@ def make_batch_mix(n: int, seed: int, max_obstacles: int = 5000):
         scenes.append(make_planning_scene(seed * 100_003 + p, ns, nb, nc, scale=scale))
         problems.append((r, c, p, W))
     return robots, constraints, problems, scenes
+
+
+def self_pairs_gap(robot: Robot, gap: int = 2) -> np.ndarray:
+    """Self-collision frame pairs: spheres of frames a and b are tested against each other
+    when |a - b| >= gap (adjacent links, which touch at their joint, are left out)."""
+    n = robot.dof + 1
+    a = np.arange(n)
+    return (np.abs(a[:, None] - a[None, :]) >= gap).astype(np.uint8)

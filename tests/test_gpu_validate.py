@@ -419,3 +419,42 @@ def test_sequential_projection_parity(torch_cuda, oracle_mod):
         assert agree >= 0.95 * len(q0), agree
         print("sequential agreement", agree, "of", len(q0),
               np.bincount(out["status"], minlength=3))
+
+
+@pytest.mark.parametrize("constrained", [False, True])
+def test_self_collision_parity(torch_cuda, oracle_mod, constrained):
+    """Self-collision (spheres of frames two or more apart) after the obstacle check: status
+    and first colliding waypoint under the parity protocol against the oracle, whose
+    clearance then includes the robot's own sphere pairs; switching it off restores the
+    plain outputs; the planner refuses to run with it."""
+    from paper_2505_06791_gb300.capi import CprrtcError, E_UNSUPPORTED
+    rb = S.make_arm7(1)
+    pairs = S.self_pairs_gap(rb, 2)
+    sc = S.make_mixed_scene(9990, 20, 10, 10)
+    c = S.roll_pitch() if constrained else S.no_constraint()
+    orc = oracle_mod.Oracle(rb, sc, c, self_pairs=pairs)
+    q0 = manifold_starts(oracle_mod.Oracle(rb, sc, c), rb, 128, 9991) if constrained \
+        else S.uniform_configs(rb, 128, 9991)
+    q1 = S.uniform_configs(rb, 128, 9992)
+    ctx = make_ctx(rb, sc, c)
+    d0 = torch_cuda.from_numpy(q0.astype(np.float32)).cuda()
+    d1 = torch_cuda.from_numpy(q1.astype(np.float32)).cuda()
+    plain = {k: parity.to_np(v) for k, v in ctx.validate(d0, d1, 32).items()}
+    ctx.set_self_collision(pairs)
+    out = ctx.validate(d0, d1, 32)
+    torch_cuda.cuda.synchronize()
+    runs = parity.oracle_runs(orc, c, q0, q1, 32)
+    stats, bad = parity.compare(out, runs)
+    assert not bad, (stats, bad[:10])
+    got = {k: parity.to_np(v) for k, v in out.items()}
+    changed = (got["status"] != plain["status"]) | (got["first_fail"] != plain["first_fail"])
+    assert changed.sum() >= 5, changed.sum()  # the folding arm hits itself
+    with pytest.raises(CprrtcError) as e:
+        ctx.plan(q0[:2], q1[:2], ctx.plan_params(use_scene_batch=False))
+    assert e.value.code == E_UNSUPPORTED
+    ctx.set_self_collision(None)
+    again = {k: parity.to_np(v) for k, v in ctx.validate(d0, d1, 32).items()}
+    for k in ("status", "first_fail", "q"):
+        assert np.array_equal(again[k], plain[k]), k
+    print(stats, "self-collision changed", int(changed.sum()), "motions")
+    ctx.close()
