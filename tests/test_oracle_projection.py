@@ -158,3 +158,38 @@ def test_sequential_projection_produces_continuous_segment(oracle_mod):
                 assert np.abs(indep.task_error(rb.joints, rb.ee, out[i], 1)).max() < c.tol_task
                 assert np.max(np.abs(out[i] - out[i - 1])) - tau < c.tol_sm
     assert n_ok >= 3
+
+
+def test_sequential_projection_composes_single_projections(oracle_mod):
+    """The naive baseline's projection is a chain of single-configuration projections:
+    waypoint i is the damped Gauss-Newton projection (the independent reference) of its
+    interpolated point moved by waypoint i-1's correction, its step count adds to the total,
+    and with W = 2 the whole motion is the projection of its end point."""
+    rb = S.make_arm7(1)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, constraint=c)
+    q0 = on_manifold(orc, rb, 6, 63)
+    q1 = S.nearby_configs(rb, q0, 0.3, 64)
+    checked = 0
+    for a, b in zip(q0, q1):
+        xi = oracle_mod.interpolate(a, b, 8)
+        tau = oracle_mod.tau_step(c, a, b, 8)
+        ok, out, ff, tot = orc.project_motion_sequential(xi, tau)
+        last = 8 if ok else ff + 1
+        steps = 0
+        for i in range(1, last):
+            start = np.clip(xi[i] + (out[i - 1] - xi[i - 1]), rb.lo, rb.hi)
+            pok, qp, it, _ = orc.project_config(start, max_iters=c.max_iters)
+            assert np.array_equal(qp, out[i]), i
+            ref_ok, ref_it, ref_q = gauss_newton_reference(rb, c, start, c.max_iters + 1)
+            if pok:
+                assert ref_ok and ref_it - 1 == it
+                assert np.abs(ref_q - qp).max() < 1e-6
+            steps += it
+        assert steps == tot
+        checked += 1
+        ok2, out2, ff2, tot2 = orc.project_motion_sequential(oracle_mod.interpolate(a, b, 2),
+                                                             oracle_mod.tau_step(c, a, b, 2))
+        pok, qp, it, _ = orc.project_config(np.asarray(b, np.float64), max_iters=c.max_iters)
+        assert np.array_equal(out2[1], qp) and tot2 == it
+    assert checked == 6
