@@ -15,6 +15,9 @@
  *     `prog` of accepted waypoints, success when the whole segment is accepted.
  *   - Sec. IV: CC reports the motion invalid at its first colliding waypoint.
  *   - Sec. III / Sec. II: RRT-Connect with greedy connect toward the other tree.
+ *   - Sec. V: the baseline's sequential (CBiRRT-style) projection, and the other task
+ *     constraints of Sec. V-B (a line; a fixed orientation with a plane or a line).
+ *   - Optional self-collision: robot sphere pairs on frames the caller names.
  *
  * Array conventions (all row-major, double):
  *   joints   [dof][7]  {type (0 revolute, 1 prismatic), d, a, alpha, theta0, lo, hi}
