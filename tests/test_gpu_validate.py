@@ -458,3 +458,17 @@ def test_self_collision_parity(torch_cuda, oracle_mod, constrained):
         assert np.array_equal(again[k], plain[k]), k
     print(stats, "self-collision changed", int(changed.sum()), "motions")
     ctx.close()
+
+
+@pytest.mark.parametrize("ctype", [3, 4, 5])
+def test_new_constraints_on_the_prismatic_arm(torch_cuda, oracle_mod, ctype):
+    """The generic task columns of a prismatic joint (linear velocity along its axis, no
+    angular part): parity on the 8-DOF arm's planner-like motions."""
+    rb = S.make_arm8(1)
+    c = NEW_CONSTRAINTS[ctype]()
+    sc = S.make_mixed_scene(9970 + ctype, 30, 10, 10)
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 64, 9975 + ctype)
+    q1 = S.nearby_configs(rb, q0, 0.3, 9980 + ctype)
+    stats, out, _ = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, 32, min_exact=0.7)
+    print(ctype, stats)

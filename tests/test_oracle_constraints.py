@@ -50,9 +50,13 @@ def test_yaw_error_is_wrapped(oracle_mod):
         assert abs(ea[2] - eb[2]) < 1e-12
 
 
+@pytest.mark.parametrize("arm", ["arm7", "arm8"])
 @pytest.mark.parametrize("ctype", [3, 4, 5])
-def test_task_jacobian_finite_differences(oracle_mod, ctype):
-    rb, c = S.make_arm7(1), CASES[ctype]()
+def test_task_jacobian_finite_differences(oracle_mod, ctype, arm):
+    """Task Jacobians against central differences, also on the 8-DOF arm whose prismatic
+    torso adds a column with linear velocity only."""
+    rb = S.make_arm7(1) if arm == "arm7" else S.make_arm8(1)
+    c = CASES[ctype]()
     orc = oracle_mod.Oracle(rb, constraint=c)
     checked = 0
     for qi in S.uniform_configs(rb, 30, 60 + ctype):
@@ -63,6 +67,7 @@ def test_task_jacobian_finite_differences(oracle_mod, ctype):
                     abs(e[1]) > 1.3:
                 continue
         Jfd = indep.fd_jacobian(lambda q: ref_error(rb, c, q), qi)
+        assert J.shape == (Jfd.shape[0], rb.dof)
         assert np.abs(J - Jfd).max() < 1e-7, np.abs(J - Jfd).max()
         checked += 1
     assert checked >= 8
