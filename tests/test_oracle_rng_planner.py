@@ -65,3 +65,40 @@ def test_planner_paths_are_valid(oracle_mod):
     again = orc.plan(s, g, range_=0.3, W=32, max_rounds=300, n_workers=8, seed=5, n_threads=3)
     assert np.array_equal(again["path_len"], out["path_len"])
     assert np.array_equal(again["path"], out["path"])
+
+
+def test_free_space_connect_is_a_straight_greedy_chain(oracle_mod):
+    """RRT-Connect in empty space without a constraint (Sec. II): the first extension adds
+    one node within `range` of its root, then CONNECT walks straight at the other root in
+    steps of exactly `range` (every step strictly closer, nothing rejects it) until it lands
+    on it, and the closing hop ends the problem. The round count is one per node of the
+    winning chain plus the hop, and the path is that chain with both roots."""
+    rb = S.make_arm7(1)
+    c = S.no_constraint()
+    orc = oracle_mod.Oracle(rb, S.Scene(), c)
+    s, g = S.uniform_configs(rb, 6, 91), S.uniform_configs(rb, 6, 92)
+    rng_ = 0.3
+    out = orc.plan(s, g, range_=rng_, W=16, max_rounds=100, n_workers=8, seed=3)
+    reach = 10 * c.tau_floor
+    for p in range(6):
+        L = int(out["path_len"][p])
+        assert L > 0
+        path = out["path"][p, :L]
+        assert np.array_equal(path[0], s[p].astype(np.float64))
+        assert np.array_equal(path[-1], g[p].astype(np.float64))
+        assert out["rounds"][p] == L - 1
+        # the node that landed on the other root duplicates it (within the hop reach)
+        gaps = np.abs(np.diff(path, axis=0)).max(axis=1)
+        hops = np.flatnonzero(gaps <= reach)
+        assert len(hops) == 1 and hops[0] in (0, L - 2)
+        chain = np.delete(path, hops[0] + (1 if hops[0] == 0 else 0), axis=0)
+        if hops[0] == 0:  # grown from the goal tree: walk it from the goal side
+            chain = chain[::-1]
+        steps = np.diff(chain, axis=0)
+        length = np.linalg.norm(steps, axis=1)
+        assert length[0] <= rng_ + 1e-9  # the extension toward the sample
+        walk, left = steps[1:], length[1:]
+        assert np.allclose(left[:-1], rng_, atol=1e-9) and left[-1] <= rng_ + 1e-9
+        # straight at the other root
+        u = (chain[-1] - chain[1]) / np.linalg.norm(chain[-1] - chain[1])
+        assert np.allclose(walk / left[:, None], u[None, :], atol=1e-9)
