@@ -193,3 +193,41 @@ def test_sequential_projection_composes_single_projections(oracle_mod):
         pok, qp, it, _ = orc.project_config(np.asarray(b, np.float64), max_iters=c.max_iters)
         assert np.array_equal(out2[1], qp) and tot2 == it
     assert checked == 6
+
+
+def test_first_iteration_combines_task_and_smoothing_terms(oracle_mod):
+    """One iteration of Alg. 1 on an uneven segment, the smoothing hinge active on some
+    joints and not on others: every waypoint after the accepted prefix moves by
+    -alpha (J^+ E_task + d * max(0, |d| - tau)) with d its difference to the previous
+    waypoint (the task step from the independent damped least squares), then clamped to the
+    limits; the prefix stays as it was."""
+    rb = S.make_arm7(1)
+    c = S.roll_pitch(max_iters=1)
+    orc = oracle_mod.Oracle(rb, constraint=c)
+    q0s = on_manifold(orc, rb, 6, 121)
+    rng = np.random.default_rng(122)
+    t = np.array([0.0, 0.05, 0.1, 0.4, 0.45, 0.7, 1.0])
+    tau = 0.03
+    active = inactive = 0
+    for q0 in q0s:
+        delta = rng.normal(size=rb.dof)
+        delta *= 0.6 / np.linalg.norm(delta)
+        xi = np.clip(q0[None, :] + t[:, None] * delta[None, :], rb.lo, rb.hi)
+        r = orc.project_motion(xi, tau=tau, trace=True)
+        assert not r["ok"] and r["iters"] == 1
+        prog = int(r["prog_trace"][0])
+        assert np.array_equal(r["xi"][: prog + 1], xi[: prog + 1])
+        assert r["first_fail"] == prog + 1
+        f = lambda x: indep.task_error(rb.joints, rb.ee, x, c.type)  # noqa: E731
+        for i in range(prog + 1, len(t)):
+            J = indep.fd_jacobian(f, xi[i], 1e-7)
+            A = np.vstack([J, c.lam * np.eye(rb.dof)])
+            b = np.concatenate([f(xi[i]), np.zeros(rb.dof)])
+            g_task = np.linalg.lstsq(A, b, rcond=None)[0]
+            d = xi[i] - xi[i - 1]
+            hinge = np.maximum(0.0, np.abs(d) - tau)
+            want = np.clip(xi[i] - c.alpha * (g_task + d * hinge), rb.lo, rb.hi)
+            assert np.abs(r["xi"][i] - want).max() < 1e-6, (i, r["xi"][i] - want)
+            active += int((hinge > 0).sum())
+            inactive += int((hinge == 0).sum())
+    assert active >= 20 and inactive >= 20
