@@ -131,10 +131,14 @@ typedef struct cprrtc_ctx cprrtc_ctx;
  * Errors: E_INVALID_ARG (out NULL, bad device), E_CUDA, E_OOM. */
 int cprrtc_create(cprrtc_ctx** out, int device, void* stream);
 
-/* Frees the context and every device buffer it owns. Accepts NULL. */
+/* Waits for the context's stream (the whole device when it runs on the legacy default
+ * stream), then frees the context and every device buffer it owns. Accepts NULL. Always
+ * returns CPRRTC_OK. */
 int cprrtc_destroy(cprrtc_ctx* ctx);
 
-/* Replaces the stream later calls run on. */
+/* Replaces the stream later calls run on (a cudaStream_t; NULL: the legacy default stream).
+ * Work already queued stays on the previous stream; order the two streams yourself if a
+ * later call reads its results. Errors: E_INVALID_ARG (null context). */
 int cprrtc_set_stream(cprrtc_ctx* ctx, void* stream);
 
 /* Message for the last error on this context ("" if none). Owned by the context. */
@@ -365,7 +369,10 @@ typedef struct {
  * Errors: as cprrtc_set_robot, E_UNSUPPORTED for n beyond the maximum. */
 int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n);
 
-/* Constraint table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_CONSTRAINTS). */
+/* Constraint table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_CONSTRAINTS; host
+ * array). Every entry is checked as cprrtc_set_constraint checks it; the context's own
+ * constraint is left as it was. Errors: E_INVALID_ARG (empty table, bad field),
+ * E_UNSUPPORTED (n beyond the maximum, a type other than NONE, ROLL_PITCH or Z_PLANE). */
 int cprrtc_set_constraint_table(cprrtc_ctx* ctx, const cprrtc_constraint* constraints, int n);
 
 /* One problem of a batch: indices into the robot table, the constraint table and the scene
@@ -405,7 +412,9 @@ int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, co
 /* Autotuner: for every class present in the batch, times short runs (trial_rounds rounds)
  * of each launch shape (obstacles staged or read through L1; 1 up to the fitting number of
  * CTAs per SM) and keeps the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
- * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. */
+ * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. The trial
+ * outputs go to library buffers; returns after the trials. Errors: as cprrtc_plan_batch,
+ * and E_INVALID_ARG for trial_rounds < 1. */
 int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
                           const float* start, const float* goal, const cprrtc_plan_params* params,
                           int trial_rounds, cprrtc_tuning* out);
@@ -413,7 +422,9 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
 /* Records one cprrtc_plan_batch into a CUDA graph held by the context (replacing any
  * previous one); cprrtc_batch_replay launches it on the context's stream. Every array must
  * be device memory; a replay reads the current contents of start and goal and overwrites
- * the outputs. The problems, tables and scene batch are the ones at capture time. */
+ * the outputs. The problems, tables and scene batch are the ones at capture time.
+ * Capture errors: as cprrtc_plan_batch, and E_INVALID_ARG for a host array. Replay errors:
+ * E_NOT_CONFIGURED (nothing captured), E_CUDA. */
 int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
                          const float* start, const float* goal, const cprrtc_plan_params* params,
                          const cprrtc_tuning* tuning, int32_t* path_len, float* path,
@@ -452,18 +463,22 @@ int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const float* goal, i
 /* ---- counter-based random numbers ---- */
 
 /* Philox4x32-10 (Salmon et al., SC'11) of n counters [n][4] under key {key0, key1}, on the
- * device: out [n][4]. The generator the planner samples with. */
+ * device: out [n][4]. The generator the planner samples with (the paper samples with a
+ * Halton sequence, Sec. V; a counter-based generator keeps every problem's samples
+ * independent of the launch). n = 0 does nothing. Errors: E_INVALID_ARG (n < 0, null
+ * array), E_CUDA, E_OOM. */
 int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t* counters,
                   int n, uint32_t* out);
 
 /* ---- timing ---- */
 
-/* When enabled, the library records CUDA events around each launch of its kernels on the
- * context's stream. cprrtc_kernel_time returns the summed device time (ms) and the launch
- * count of the kernel named `name` ("validate", "project", "plan", "mlp_infer", "gemm_cc",
- * "self_collide")
- * since the last reset,
- * synchronising on the events. */
+/* Measurement helpers with no counterpart in the paper. When enabled, the library records
+ * CUDA events around each launch of its kernels on the context's stream.
+ * cprrtc_kernel_time returns the summed device time (ms) and the launch count of the
+ * kernel named `name` ("validate", "project", "plan", "mlp_infer", "gemm_cc",
+ * "self_collide") since the last reset, waiting for the recorded events (a name never
+ * launched gives 0 and 0); cprrtc_reset_timing waits for them too and drops the sums.
+ * Errors: E_INVALID_ARG (null argument), E_CUDA (kernel_time). */
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
 
 /* Work the validate and plan kernels of this context evaluated since creation or the last
