@@ -126,3 +126,37 @@ def test_validate_first_collision_index_and_strict_contact(oracle_mod, offset, e
     assert out["status"][0] == 2
     assert out["first_fail"][0] == first
     assert abs(out["cc_margin"][0] - min(abs(v) for v in clear[: (first + 1 if first >= 0 else W)])) < 1e-12
+
+
+@pytest.mark.parametrize("ctype", [1, 2, 4])
+def test_segment_check_against_independent_pieces(oracle_mod, ctype):
+    """The segment judge used on warm-started segments and planner paths: its largest task
+    error (waypoints 1..W-1, independent forward kinematics and Euler angles), its largest
+    per-joint step excess over tau, and its smallest clearance (brute force over every
+    robot sphere, every obstacle sphere and every waypoint, waypoint 0 included)."""
+    rb = S.make_arm7(1)
+    c = {1: S.roll_pitch(), 2: S.z_plane(0.9), 4: S.orient_plane(0.5, 0.6)}[ctype]
+    sc = S.make_scene(300 + ctype, n_sph=30)
+    orc = oracle_mod.Oracle(rb, sc, c)
+    rng = np.random.default_rng(310 + ctype)
+    q0 = S.uniform_configs(rb, 5, 320 + ctype)
+    q1 = S.nearby_configs(rb, q0, 0.4, 330 + ctype)
+    for a, b in zip(q0, q1):
+        W = 9
+        xi = oracle_mod.interpolate(a, b, W) + rng.normal(scale=0.01, size=(W, rb.dof))
+        tau = 0.02
+        mt, ms, mc = orc.check_segment(xi, tau)
+        errs = []
+        for i in range(1, W):
+            e = indep.task_error(rb.joints, rb.ee, xi[i], c.type, c.target, c.line_y, c.yaw)
+            if ctype == 4:  # the yaw row up to its wrap at +-pi
+                e[2] = min(abs(e[2]), abs(abs(e[2]) - 2 * np.pi))
+            errs.append(np.abs(e).max())
+        assert abs(mt - max(errs)) < 1e-12
+        assert abs(ms - (np.abs(np.diff(xi, axis=0)) - tau).max()) < 1e-15
+        clear = np.inf
+        for q in xi:
+            C = indep.sphere_centres(rb.joints, rb.ee, rb.spheres, q)
+            D = np.sqrt(((C[:, None, :] - sc.sph[None, :, :3]) ** 2).sum(-1))
+            clear = min(clear, (D - rb.spheres[:, 4][:, None] - sc.sph[None, :, 3]).min())
+        assert abs(mc - clear) < 1e-12
