@@ -64,3 +64,18 @@ def test_oracle_is_not_imported_by_the_package():
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "cprrtc_oracle" not in text, f
+
+
+def test_oracle_shares_nothing_with_the_cuda_library():
+    """The oracle's sources include only the C library and its own header, and its Python
+    loader imports nothing from the package (not even the input generators)."""
+    root = os.path.join(os.path.dirname(os.path.dirname(capi.__file__)), "oracle")
+    for f in os.listdir(root):
+        if not f.endswith((".c", ".h", ".py")):
+            continue
+        text = open(os.path.join(root, f)).read()
+        for inc in re.findall(r'#include\s*[<"]([^>"]+)[>"]', text):
+            assert inc in ("cprrtc_oracle.h", "math.h", "pthread.h", "stdlib.h", "string.h",
+                           "stdint.h"), (f, inc)
+        assert "paper_2505_06791_gb300" not in text and "cprrtc.h" not in text, f
+        assert "csrc" not in text, f
