@@ -160,3 +160,60 @@ def test_segment_check_against_independent_pieces(oracle_mod, ctype):
             D = np.sqrt(((C[:, None, :] - sc.sph[None, :, :3]) ** 2).sum(-1))
             clear = min(clear, (D - rb.spheres[:, 4][:, None] - sc.sph[None, :, 3]).min())
         assert abs(mc - clear) < 1e-12
+
+
+@pytest.mark.parametrize("ctype", [0, 1])
+def test_validate_is_projection_then_first_collision(oracle_mod, ctype):
+    """The batched validation composes the two stages as Sec. III orders them: Alg. 1 on the
+    interpolated segment (its verdict, failing waypoint and iterations), then, for projected
+    segments, the smallest waypoint index whose robot spheres overlap an obstacle, found here
+    by brute force on independent forward kinematics (waypoint 0 included; with the planner's
+    flag it is skipped). Host threads change nothing."""
+    rb = S.make_arm7(1)
+    c = S.roll_pitch() if ctype == 1 else S.no_constraint()
+    sc = S.make_scene(400 + ctype, n_sph=40)
+    orc = oracle_mod.Oracle(rb, sc, c)
+    starts = []
+    for q in S.uniform_configs(rb, 200, 410 + ctype):
+        ok, qp, _, _ = orc.project_config(q, max_iters=60)
+        if ok or ctype == 0:
+            starts.append(qp if ok else q)
+        if len(starts) == 24:
+            break
+    q0 = S.f32(np.array(starts))
+    q1 = np.vstack([S.nearby_configs(rb, q0[:12], 0.3, 420 + ctype),
+                    S.uniform_configs(rb, 12, 430 + ctype)])
+    W = 16
+    out = orc.validate(q0, q1, W, n_threads=1)
+    par = orc.validate(q0, q1, W, n_threads=5)
+    for k in ("status", "first_fail", "iters", "q"):
+        assert np.array_equal(out[k], par[k]), k
+    skip = orc.validate(q0, q1, W, cc_skip_first=True)
+    seen = set()
+    for m in range(len(q0)):
+        xi = oracle_mod.interpolate(q0[m], q1[m], W)
+        if ctype == 1:
+            r = orc.project_motion(xi, oracle_mod.tau_step(c, q0[m], q1[m], W))
+            if not r["ok"]:
+                assert out["status"][m] == 1 and out["first_fail"][m] == r["first_fail"]
+                assert out["iters"][m] == r["iters"]
+                seen.add(1)
+                continue
+            xi = r["xi"]
+            assert out["iters"][m] == r["iters"]
+        assert np.abs(out["q"][m] - xi).max() == 0
+        first = -1
+        for i in range(W):
+            C = indep.sphere_centres(rb.joints, rb.ee, rb.spheres, xi[i])
+            D = np.sqrt(((C[:, None, :] - sc.sph[None, :, :3]) ** 2).sum(-1))
+            if (D - rb.spheres[:, 4][:, None] - sc.sph[None, :, 3]).min() < 0:
+                first = i
+                break
+        assert out["status"][m] == (2 if first >= 0 else 0)
+        assert out["first_fail"][m] == first
+        seen.add(out["status"][m])
+        if first == 0:  # the planner's form skips waypoint 0 (a tree node)
+            assert skip["first_fail"][m] != 0
+        else:
+            assert skip["first_fail"][m] == first and skip["status"][m] == out["status"][m]
+    assert 0 in seen and 2 in seen and (ctype == 0 or 1 in seen)
