@@ -177,7 +177,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # workloads
 
-def config1_workload(seed=1):
+def validation_workload(seed=1):
     """7-DOF arm (59 spheres), 16 obstacle spheres in the 1.2 m cube, 256 motions x 32
     waypoints between uniform configurations, roll/pitch constraint, <= 20 iterations."""
     rb = S.make_arm7(seed)
@@ -205,8 +205,8 @@ PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=1000, workers=8, max_nodes=2048,
                    max_connect=32, max_path=512)
 
 
-def config2_scenes(n, seed=2):
-    """Config 2: per-problem scenes of 200 mixed obstacles (100 spheres, 60 oriented boxes,
+def planner_scenes(n, seed=2):
+    """Full planner: per-problem scenes of 200 mixed obstacles (100 spheres, 60 oriented boxes,
     40 capsules) in a 3 x 3 x 1.8 m workspace around the arm, base keep-out 0.35 m."""
     return [S.make_planning_scene(2_000_000 + 10_007 * seed + p) for p in range(n)]
 
@@ -267,7 +267,7 @@ def run_plan(args, world, rank, local):
     n = args.problems
     # each rank plans its own seeded problems (weak scaling, no collective)
     seed = 2 + 1000 * rank
-    scenes = config2_scenes(n, seed)
+    scenes = planner_scenes(n, seed)
     start, goal = gpu_start_goal(rb, c, scenes, seed, local)
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream.cuda_stream)
@@ -336,14 +336,14 @@ def run_plan(args, world, rank, local):
     avg_kernel_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_kernel_s / 1e12
     solved = L > 0
-    per_round = profiled_traffic_per_unit("plan_kernel_config2.md",
+    per_round = profiled_traffic_per_unit("plan_kernel_planner_1000_problems.md",
                                           "traffic_per_problem_round_bytes")
     traffic = None if per_round is None else per_round * float(rounds.sum())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "config 2: RRT-Connect planner, plain form", "problems": n,
+        "config": {"workload": "full planner, plain form: RRT-Connect on a 7-DOF arm among 200 mixed obstacles per problem, roll-pitch", "problems": n,
                    "dof": rb.dof, "robot_spheres": len(rb.spheres),
                    "obstacles_per_problem": {"spheres": 100, "boxes": 60, "capsules": 40},
                    "constraint": "roll-pitch", "range": PLAN_PARAMS["range_"],
@@ -361,7 +361,7 @@ def run_plan(args, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "plan_kernel",
                      "traffic_note": "ncu DRAM bytes per problem-round of a 304-problem capture "
-                                     "(profiles/plan_kernel_config2.md) x problem-rounds",
+                                     "(profiles/plan_kernel_planner_1000_problems.md) x problem-rounds",
                      "flop_per_launch": flops, "avg_launch_ms": avg_kernel_s * 1e3,
                      "work_per_launch": {"alg1_updates": float(counters[0]),
                                          "cc_chains": float(counters[1]),
@@ -549,7 +549,7 @@ def run_batch(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "config 5: batched uneven serving mix, one CUDA-graph launch",
+        "config": {"workload": "batched uneven serving mix: mixed DOF, obstacle counts, constraints and W in one CUDA-graph launch",
                    "problems": len(probs), "dof": [6, 7, 8],
                    "obstacles_per_problem": "log-uniform [10, 5000], 50/30/20 spheres/boxes/"
                                             "capsules, sizes x min(1, (200/n)^(1/3))",
@@ -628,7 +628,7 @@ def run_validate(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    rb, sc, c, n, W = config1_workload()
+    rb, sc, c, n, W = validation_workload()
     ctx = Context(local, stream.cuda_stream)
     ctx.set_robot(rb)
     ctx.set_obstacles(sc)
@@ -697,7 +697,7 @@ def run_validate(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "config 1: batched constrained motion validation",
+        "config": {"workload": "plain batched constrained motion validation: 7-DOF arm, obstacle spheres in a 1.2 m cube, roll-pitch",
                    "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
                    "obstacles": {"spheres": len(sc.sph)}, "constraint": "roll-pitch",
                    "max_iters": c.max_iters, "l2": "flushed (256 MB write) between steps",
@@ -814,7 +814,7 @@ NAIVE_N = 304
 
 
 def run_naive(args, world, rank, local):
-    """cpRRTC-Naive against cpRRTC-Parallel (Sec. V): the planner of configuration 2 on 304
+    """cpRRTC-Naive against cpRRTC-Parallel (Sec. V): the full planner (7-DOF arm, 200 mixed obstacles per problem) on 304
     problems (one wave of 2 per SM), once with Alg. 1 and once with the sequential
     projection; success, plan time and validated waypoints per second for each."""
     import torch
@@ -826,7 +826,7 @@ def run_naive(args, world, rank, local):
     rb, c = S.make_arm7(1), S.roll_pitch(20)
     n = NAIVE_N
     seed = 7 + 1000 * rank
-    scenes = config2_scenes(n, seed)
+    scenes = planner_scenes(n, seed)
     start, goal = gpu_start_goal(rb, c, scenes, seed, local)
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(local, stream.cuda_stream)
@@ -879,7 +879,7 @@ def run_naive(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": par["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "cpRRTC-Parallel vs cpRRTC-Naive projection, planner of config 2",
+        "config": {"workload": "cpRRTC-Parallel vs cpRRTC-Naive projection inside the full planner (7-DOF arm, 200 mixed obstacles, roll-pitch)",
                    "problems": n, "W": PLAN_PARAMS["W"], "range": PLAN_PARAMS["range_"],
                    "max_rounds": PLAN_PARAMS["max_rounds"], "constraint": "roll-pitch",
                    "l2": "flushed (256 MB write) between steps",
@@ -896,12 +896,12 @@ def run_naive(args, world, rank, local):
     return line, None
 
 
-# ---- config 3: collision checking in GEMM form ---------------------------------------------
+# ---- obstacle-rich scene: collision checking in GEMM form ---------------------------------------------
 
 CC_N, CC_W = 4096, 64
 
 
-def config3_workload(seed=3):
+def point_cloud_workload(seed=3):
     """8-DOF arm (7-DOF arm on a 0..0.4 m prismatic torso, 120 spheres), 4096 obstacle
     spheres of radius 0.02 m on the surfaces of 12 random boxes, end effector on z = 0.9 m."""
     return S.make_arm8(1), S.make_box_surface_cloud(seed), S.z_plane(0.9)
@@ -917,7 +917,7 @@ def run_gemmcc(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    rb, sc, c = config3_workload()
+    rb, sc, c = point_cloud_workload()
     n, W = (CC_N if args.problems == PLAN_N else args.problems), CC_W
     ctx = Context(local, stream.cuda_stream)
     ctx.set_robot(rb)
@@ -988,14 +988,14 @@ def run_gemmcc(args, world, rank, local):
                                        else "BF16 measured (MEASURED_PEAKS.json bf16_tflops)"})
         summary[name] = entry
     best = max(("gemm_tf32", "gemm_bf16"), key=lambda k: summary[k]["value"])
-    gcc_tile_bytes = profiled_traffic_per_unit("gemm_cc_kernel_config3.md", "traffic_per_waypoint_tile_bytes")
+    gcc_tile_bytes = profiled_traffic_per_unit("gemm_cc_kernel_point_cloud_4096.md", "traffic_per_waypoint_tile_bytes")
     b = summary[best]
     line = {
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": f"{best[5:]} contraction, f32 recheck",
         "data": "synthetic",
-        "config": {"workload": "config 3: obstacle-rich scene, collision check in GEMM form",
+        "config": {"workload": "obstacle-rich scene, collision check in GEMM form: 8-DOF arm, point-cloud sphere obstacles, z-plane",
                    "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
                    "obstacles": {"spheres": len(sc.sph), "radius": 0.02},
                    "constraint": "z-plane 0.9 m", "guard_m": 0.005,
@@ -1008,7 +1008,7 @@ def run_gemmcc(args, world, rank, local):
                      "traffic": (None if gcc_tile_bytes is None or best != "gemm_bf16"
                                  else gcc_tile_bytes * tiles),
                      "traffic_note": "ncu DRAM bytes per waypoint tile of a 512-motion BF16 capture "
-                                     "(profiles/gemm_cc_kernel_config3.md) x waypoint tiles",
+                                     "(profiles/gemm_cc_kernel_point_cloud_4096.md) x waypoint tiles",
                      "kernel": "gemm_cc_kernel",
                      "flop_per_launch": tensor_flop, "avg_launch_ms": b["gemm_cc_kernel_ms"]},
         "gpu_launches": 2 * args.steps,
@@ -1017,7 +1017,7 @@ def run_gemmcc(args, world, rank, local):
     return line, (rb, sc, c, 64, W, q0[:64].cpu().numpy(), q1[:64].cpu().numpy())
 
 
-# ---- config 4: learned warm start -------------------------------------------------------
+# ---- learned warm start -------------------------------------------------------
 
 WS_MOTIONS = 16384
 WS_W = 32
@@ -1031,7 +1031,7 @@ def mlp_flops_per_row(dof: int, hidden: int = 256) -> int:
     return 2 * (dof * hidden + 2 * hidden * hidden + hidden * dof)
 
 
-def config4_workload(seed=4):
+def warm_start_workload(seed=4):
     """7-DOF arm (59 spheres), roll/pitch constraint, one config-2 scene (100 spheres, 60
     boxes, 40 capsules)."""
     rb = S.make_arm7(1)
@@ -1051,7 +1051,7 @@ def run_warmstart(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    rb, sc, c = config4_workload()
+    rb, sc, c = warm_start_workload()
     n, W = (WS_MOTIONS if args.problems == PLAN_N else args.problems), WS_W
     ctx = Context(local, stream.cuda_stream)
     ctx.set_robot(rb)
@@ -1116,7 +1116,7 @@ def run_warmstart(args, world, rank, local):
         clocks.start()
         ms_plain, kt_plain = timed(lambda: ctx.validate(q0, q1, W, out=out_p))
         ms_ws, kt_ws = timed(lambda: ctx.validate_ws(q0, q1, W, WS_REFINE, out=out_w))
-        # the planner's motions (steering range 0.3 rad, as in configurations 2 and 5):
+        # the planner's motions (steering range 0.3 rad, as in the full planner and the uneven batch):
         # plain against warm start on the same starts
         q1s = torch.from_numpy(S.nearby_configs(rb, q0.cpu().numpy(), 0.3,
                                                 61_000 + 97 * rank).astype(np.float32)).to(dev)
@@ -1162,7 +1162,7 @@ def run_warmstart(args, world, rank, local):
     infer_ms, infer_launches = kt_ws["mlp_infer"]
     infer_avg_s = infer_ms / 1e3 / max(infer_launches, 1)
     flops_infer = mlp_flops_per_row(rb.dof) * n * W
-    mlp_row_bytes = profiled_traffic_per_unit("mlp_fused_kernel_config4.md", "traffic_per_row_bytes")
+    mlp_row_bytes = profiled_traffic_per_unit("mlp_fused_kernel_warm_start_16384x32.md", "traffic_per_row_bytes")
     tensor_peak = float(peaks.get("bf16_tflops", 1900.0))
     achieved = flops_infer / infer_avg_s / 1e12
     vk_ms, vk_launches = kt_ws["validate"]
@@ -1171,7 +1171,7 @@ def run_warmstart(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_ws / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 projection",
         "data": "synthetic",
-        "config": {"workload": "config 4: learned warm start vs plain projection",
+        "config": {"workload": "learned warm start vs plain projection: 7-DOF arm among 200 mixed obstacles, roll-pitch",
                    "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
                    "obstacles": {"spheres": len(sc.sph), "boxes": len(sc.box),
                                  "capsules": len(sc.cap)},
@@ -1208,7 +1208,7 @@ def run_warmstart(args, world, rank, local):
                      "frac": achieved / tensor_peak,
                      "traffic": (None if mlp_row_bytes is None else mlp_row_bytes * n * W),
                      "traffic_note": "ncu DRAM bytes per row of a 131072-row capture "
-                                     "(profiles/mlp_fused_kernel_config4.md) x rows",
+                                     "(profiles/mlp_fused_kernel_warm_start_16384x32.md) x rows",
                      "kernel": "mlp_fused_kernel",
                      "flop_per_launch": flops_infer, "avg_launch_ms": infer_avg_s * 1e3,
                      "peak_note": "measured dense BF16 (MEASURED_PEAKS.json bf16_tflops, burst)"},
@@ -1253,7 +1253,7 @@ def reference_arm_plan(args, world, rank):
     seed = 2
     cores = os.cpu_count() or 1
     n = cores
-    scenes = config2_scenes(n, seed)
+    scenes = planner_scenes(n, seed)
     starts, goals = [], []
     for p, sc in enumerate(scenes):
         orc = oracle.Oracle(rb, sc, c)
@@ -1284,7 +1284,7 @@ def reference_arm_plan(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "config 2: RRT-Connect planner, plain form",
+            "config": {"workload": "full planner, plain form: RRT-Connect on a 7-DOF arm among 200 mixed obstacles per problem, roll-pitch",
                        "problems": n, "dof": rb.dof, "parallelism": "host threads"},
             "p50_plan_ms": float(np.percentile(ms_all, 50)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -1298,7 +1298,7 @@ def reference_arm(args, world, rank):
     if rank != 0:
         return None
     import oracle
-    rb, sc, c, n, W = config1_workload()
+    rb, sc, c, n, W = validation_workload()
     orc = oracle.Oracle(rb, sc, c)
     starts = []
     for q in S.uniform_configs(rb, 4 * n, 10_000):
@@ -1321,7 +1321,7 @@ def reference_arm(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "config 1: batched constrained motion validation",
+            "config": {"workload": "plain batched constrained motion validation: 7-DOF arm, obstacle spheres in a 1.2 m cube, roll-pitch",
                        "motions": n, "W": W, "dof": rb.dof, "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} passes over {n} motions x {W} waypoints"},

@@ -37,7 +37,7 @@ def to_np(d):
             if v is not None}
 
 
-def test_config2_planner_full_size(torch_cuda, oracle_mod):
+def test_full_planner_1000_problems_full_size(torch_cuda, oracle_mod):
     """1000 problems of 200 mixed obstacles, range 0.3, W = 32, 8 workers, 1000 rounds (the
     headline launch): deterministic; 40 sampled solved paths re-validated by the oracle."""
     from paper_2505_06791_gb300.capi import Context
@@ -74,7 +74,7 @@ def test_config2_planner_full_size(torch_cuda, oracle_mod):
     ctx.close()
 
 
-def test_config5_batch_full_size(torch_cuda, oracle_mod):
+def test_uneven_batch_512_problems_full_size(torch_cuda, oracle_mod):
     """512 problems, DOF 6/7/8, 10..5000 obstacles, three constraints, W 16/32/64, one graph
     replay: the replay equals a direct launch; 24 sampled solved paths re-validated."""
     from paper_2505_06791_gb300.capi import Context
@@ -120,7 +120,7 @@ def test_config5_batch_full_size(torch_cuda, oracle_mod):
     ctx.close()
 
 
-def test_config3_gemm_form_full_size(torch_cuda, oracle_mod):
+def test_gemm_form_4096_point_cloud_full_size(torch_cuda, oracle_mod):
     """4096 motions x 64 waypoints on the 4096-point cloud: TF32 and BF16 GEMM forms equal
     the exact check on every motion; the exact check is compared with the oracle on 24
     sampled motions (parity protocol)."""

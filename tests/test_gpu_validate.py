@@ -54,7 +54,7 @@ def run_case(torch, oracle_mod, robot, scene, c, q0, q1, W, min_exact=0.8, fail_
     return stats, out, runs[0]
 
 
-def test_config1_full_size_roll_pitch(torch_cuda, oracle_mod):
+def test_validation_256_motions_full_size_roll_pitch(torch_cuda, oracle_mod):
     """7-DOF arm, 59 spheres, 16 obstacle spheres, 256 motions x 32 waypoints, roll/pitch."""
     rb = S.make_arm7(1)
     sc = S.make_scene(1001, n_sph=16)

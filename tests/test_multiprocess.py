@@ -26,7 +26,7 @@ def _rank(rank, world, port, queue):
            "max": bench.max_over_ranks(1.5 + r, w), "sum": bench.sum_over_ranks(10 * (r + 1), w)}
     bench.barrier(w)
     # weak scaling: each rank's problems come from its own seed
-    scenes = bench.config2_scenes(2, 2 + 1000 * r)
+    scenes = bench.planner_scenes(2, 2 + 1000 * r)
     res["first_obstacle"] = [float(x) for x in scenes[0].sph[0]]
     res["reference_line"] = bench.reference_arm_plan(None, w, r) if r != 0 else "rank 0"
     dist.destroy_process_group()
