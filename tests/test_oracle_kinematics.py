@@ -147,3 +147,30 @@ def test_damped_step_against_numpy_pinv_and_lstsq(oracle_mod):
             b = np.concatenate([e, np.zeros(7)])
             ref = np.linalg.lstsq(A, b, rcond=None)[0]
             assert np.abs(g - ref).max() < 1e-12
+
+
+def test_damped_step_identities(oracle_mod):
+    """J J^+_lambda = I - lambda^2 (J J^T + lambda^2 I)^-1 (the damped pseudoinverse's
+    residual map) for every row count a constraint uses (1, 2, 4, 5), and on a rank-deficient
+    J (two equal rows) the damped step stays finite, lies in the row space of J and tends to
+    the minimum-norm least-squares step of numpy's SVD pseudoinverse as lambda -> 0."""
+    rng = np.random.default_rng(5)
+    for m in (1, 2, 4, 5):
+        J = rng.normal(size=(m, 7))
+        lam = 0.2
+        Ginv = np.linalg.inv(J @ J.T + lam ** 2 * np.eye(m))
+        for _ in range(4):
+            e = rng.normal(size=m)
+            g = oracle_mod.Oracle.damped_step(J, e, lam)
+            assert np.abs(J @ g - (e - lam ** 2 * Ginv @ e)).max() < 1e-12
+    J = rng.normal(size=(4, 7))
+    J[3] = J[1]
+    e = rng.normal(size=4)
+    P = np.linalg.pinv(J)
+    row_space = P @ J  # projector onto the row space
+    for lam in (1e-2, 1e-4):
+        g = oracle_mod.Oracle.damped_step(J, e, lam)
+        assert np.all(np.isfinite(g))
+        # J J^T + lambda^2 I has condition ~1/lambda^2 here: rounding grows with it
+        assert np.abs(row_space @ g - g).max() < 1e-14 / lam ** 2
+        assert np.abs(g - P @ e).max() < 50 * lam ** 2 * np.abs(P @ e).max() + 1e-9
