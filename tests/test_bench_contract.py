@@ -47,3 +47,33 @@ def test_native_arm_fails_loudly_without_a_gpu():
     p = run_bench("--steps", "1", "--warmup", "3", "--legs", "none")
     assert p.returncode != 0
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def test_roofline_accounting():
+    """The per-unit work bench.py divides by kernel time: one Alg. 1 waypoint update at
+    dof 7 = 558 FLOP (chain 48, roll-pitch task 8 and damped step 9 and update 10 per joint,
+    plus the fixed parts), sphere FK 18, 11 / 34 / 25 per sphere / box / capsule pair, the
+    warm-start network's 2 x (7x256 + 2x256x256 + 256x7) per row, and the nominal FP32 peak
+    152 SMs x 128 lanes x 2 x 2070 MHz."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.flops_waypoint_iter(7) == 558
+    assert bench.flops_cc_waypoint(1, 1, 0, 0) == 18 + 11
+    assert bench.flops_cc_waypoint(59, 100, 60, 40) == 59 * (18 + 100 * 11 + 60 * 34 + 40 * 25)
+    # outcomes: valid, projection failed, first collision at waypoint 3
+    f, cc = bench.algorithmic_flops(7, 32, 59, (16, 0, 0), [0, 1, 2], [-1, 5, 3], [2, 20, 1])
+    assert cc == 32 + 0 + 4
+    assert f == (2 + 20 + 1) * 31 * 558 + cc * bench.flops_cc_waypoint(59, 16, 0, 0)
+    ex = bench.executed_flops(7, [10, 3, 100, 7, 5, 2])
+    assert ex == 10 * 558 + 3 * 7 * 48 + 100 * 18 + 7 * 11 + 5 * 34 + 2 * 25
+    assert bench.mlp_flops_per_row(7) == 269312
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.548) < 1e-3
+    work = np.array([[100, 40], [0, 8]])
+    from paper_2505_06791_gb300 import synth as S
+    scenes = [S.make_scene(1, 16), S.make_scene(2, 4, 2, 1)]
+    want = 100 * 558 + 40 * bench.flops_cc_waypoint(59, 16, 0, 0) + \
+        8 * bench.flops_cc_waypoint(59, 4, 2, 1)
+    assert bench.plan_flops(7, scenes, 59, work) == want
