@@ -351,6 +351,10 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
 
 /* ---- batches of uneven planning problems ---- */
 
+/* An addition for serving: the paper plans one problem per run. Every problem of a batch
+ * is planned as cprrtc_plan plans it (Sec. III), with its own robot, constraint, scene
+ * and W; only the launch (persistent kernels, a CUDA graph, tuned shapes) differs. */
+
 /* One robot of a robot table (arguments of cprrtc_set_robot). */
 typedef struct {
   const cprrtc_joint* joints;
