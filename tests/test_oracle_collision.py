@@ -217,3 +217,24 @@ def test_validate_is_projection_then_first_collision(oracle_mod, ctype):
         else:
             assert skip["first_fail"][m] == first and skip["status"][m] == out["status"][m]
     assert 0 in seen and 2 in seen and (ctype == 0 or 1 in seen)
+
+
+def test_config_clearance_is_the_minimum_over_every_pair(oracle_mod):
+    """A configuration's clearance is the smallest clearance of any (robot sphere, obstacle)
+    pair over spheres, boxes and capsules: independent forward kinematics for the sphere
+    centres, and the per-primitive clearances pinned above."""
+    rb = S.make_arm7(1)
+    sc = S.make_scene(501, n_sph=6, n_box=5, n_cap=5)
+    orc = oracle_mod.Oracle(rb, sc)
+    O = oracle_mod.Oracle
+    for q in S.uniform_configs(rb, 6, 502):
+        C = indep.sphere_centres(rb.joints, rb.ee, rb.spheres, q)
+        best = np.inf
+        for c, r in zip(C, rb.spheres[:, 4]):
+            for o in sc.sph:
+                best = min(best, O.clear_sphere(c, r, o))
+            for b in sc.box:
+                best = min(best, O.clear_box(c, r, b))
+            for cp in sc.cap:
+                best = min(best, O.clear_capsule(c, r, cp))
+        assert abs(orc.config_clearance(q) - best) < 1e-12
