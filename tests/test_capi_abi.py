@@ -79,3 +79,44 @@ def test_oracle_shares_nothing_with_the_cuda_library():
                            "stdint.h"), (f, inc)
         assert "paper_2505_06791_gb300" not in text and "cprrtc.h" not in text, f
         assert "csrc" not in text, f
+
+
+def test_codes_agree_across_header_kernels_oracle_and_generators():
+    """The constraint, status and error codes are written down separately in the public
+    header, the kernels' device types, the oracle's header, the Python binding and the input
+    generators (the oracle shares no code with the library): they must agree."""
+    from paper_2505_06791_gb300 import synth as S
+
+    root = os.path.dirname(os.path.dirname(capi.__file__))
+    hdr = open(capi.HEADER).read()
+    dev = open(os.path.join(os.path.dirname(capi.__file__), "csrc", "device_types.cuh")).read()
+    orc = open(os.path.join(root, "oracle", "cprrtc_oracle.h")).read()
+
+    def define(name):
+        return int(re.search(r"#define\s+" + name + r"\s+\(?(-?\d+)\)?", hdr).group(1))
+
+    def enum(text, name):
+        return int(re.search(r"\b" + name + r"\s*=\s*(\d+)", text).group(1))
+
+    cons = [("NONE", "kConsNone", "ORC_NONE", S.C_NONE),
+            ("ROLL_PITCH", "kConsRollPitch", "ORC_ROLL_PITCH", S.C_ROLL_PITCH),
+            ("Z_PLANE", "kConsZPlane", "ORC_Z_PLANE", S.C_Z_PLANE),
+            ("LINE", "kConsLine", "ORC_LINE", S.C_LINE),
+            ("ORIENT_PLANE", "kConsOrientPlane", "ORC_ORIENT_PLANE", S.C_ORIENT_PLANE),
+            ("ORIENT_LINE", "kConsOrientLine", "ORC_ORIENT_LINE", S.C_ORIENT_LINE)]
+    for h, d, o, s in cons:
+        v = define("CPRRTC_CONSTRAINT_" + h)
+        assert v == enum(dev, d) == enum(orc, o) == s, h
+    status = [("VALID", "kValid", "ORC_VALID", capi.MOTION_VALID),
+              ("PROJ_FAIL", "kProjFail", "ORC_PROJ_FAIL", capi.MOTION_PROJ_FAIL),
+              ("COLLISION", "kCollision", "ORC_COLLISION", capi.MOTION_COLLISION)]
+    for h, d, o, p in status:
+        assert define("CPRRTC_MOTION_" + h) == enum(dev, d) == enum(orc, o) == p, h
+    for name in ("INVALID_ARG", "NOT_CONFIGURED", "CUDA", "OOM", "CAPACITY", "TIMEOUT",
+                 "UNSUPPORTED"):
+        assert define("CPRRTC_E_" + name) == getattr(capi, "E_" + name), name
+    assert define("CPRRTC_OK") == capi.OK == 0
+    assert define("CPRRTC_MAX_DOF") == int(re.search(r"kMaxDof = (\d+)", dev).group(1)) == \
+        int(re.search(r"ORC_MAX_DOF (\d+)", orc).group(1))
+    assert define("CPRRTC_MAX_W") == int(re.search(r"kMaxW = (\d+)", dev).group(1)) == \
+        int(re.search(r"ORC_MAX_W (\d+)", orc).group(1))
