@@ -1,7 +1,8 @@
 """ctypes loader for the FP64 CPU oracle (oracle/cprrtc_oracle.c).
 
 TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the benchmark's
-CPU-baseline leg, never by the library. It shares no code with the CUDA path.
+CPU legs (the cpu_baseline figure and the reference arm), never by the library. It shares
+no code with the CUDA path.
 """
 from __future__ import annotations
 
