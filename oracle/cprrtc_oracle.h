@@ -2,8 +2,9 @@
  * FP64 CPU oracle for cpRRTC constrained motion validation and planning.
  *
  * TEST INFRASTRUCTURE ONLY. This library exists to check the CUDA path: only the test
- * suite, the smoke check and the benchmark's CPU-baseline leg load it. It shares no code,
- * header or table with the CUDA library, and the CUDA library never calls it.
+ * suite, the smoke check and the benchmark's CPU legs (its cpu_baseline figure and its
+ * reference arm) load it. It shares no code, header or table with the CUDA library, and
+ * the CUDA library never calls it.
  *
  * It follows the paper (Hu, Wang, Christensen, "cpRRTC: GPU-Parallel RRT-Connect for
  * Constrained Motion Planning") step by step, in double precision, one motion at a time:
