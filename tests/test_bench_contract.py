@@ -77,3 +77,20 @@ def test_roofline_accounting():
     want = 100 * 558 + 40 * bench.flops_cc_waypoint(59, 16, 0, 0) + \
         8 * bench.flops_cc_waypoint(59, 4, 2, 1)
     assert bench.plan_flops(7, scenes, 59, work) == want
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched as the scaling run launches it (torchrun, 2 ranks; gloo here), only rank 0
+    runs the oracle and prints; the other rank exits 0 without work."""
+    env = dict(os.environ, CPRRTC_BENCH_GLOO="1")
+    p = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+                        "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
+                        "--master-port", "29563", "bench.py", "--impl", "reference",
+                        "--gpus", "2", "--workload", "validate", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300, env=env)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
