@@ -160,13 +160,15 @@ def test_sequential_projection_produces_continuous_segment(oracle_mod):
     assert n_ok >= 3
 
 
-def test_sequential_projection_composes_single_projections(oracle_mod):
+@pytest.mark.parametrize("ctype", [1, 2])
+def test_sequential_projection_composes_single_projections(oracle_mod, ctype):
     """The naive baseline's projection is a chain of single-configuration projections:
     waypoint i is the damped Gauss-Newton projection (the independent reference) of its
     interpolated point moved by waypoint i-1's correction, its step count adds to the total,
-    and with W = 2 the whole motion is the projection of its end point."""
+    and with W = 2 the whole motion is the projection of its end point. Both constraints
+    the GPU's sequential form takes (roll-pitch, z-plane)."""
     rb = S.make_arm7(1)
-    c = S.roll_pitch()
+    c = S.roll_pitch() if ctype == 1 else S.z_plane(0.6)
     orc = oracle_mod.Oracle(rb, constraint=c)
     q0 = on_manifold(orc, rb, 6, 63)
     q1 = S.nearby_configs(rb, q0, 0.3, 64)
