@@ -197,14 +197,16 @@ def test_sequential_projection_composes_single_projections(oracle_mod, ctype):
     assert checked == 6
 
 
-def test_first_iteration_combines_task_and_smoothing_terms(oracle_mod):
+@pytest.mark.parametrize("ctype", [1, 2, 5])
+def test_first_iteration_combines_task_and_smoothing_terms(oracle_mod, ctype):
     """One iteration of Alg. 1 on an uneven segment, the smoothing hinge active on some
     joints and not on others: every waypoint after the accepted prefix moves by
     -alpha (J^+ E_task + d * max(0, |d| - tau)) with d its difference to the previous
     waypoint (the task step from the independent damped least squares), then clamped to the
     limits; the prefix stays as it was."""
     rb = S.make_arm7(1)
-    c = S.roll_pitch(max_iters=1)
+    c = {1: S.roll_pitch(), 2: S.z_plane(0.6), 5: S.orient_line(-0.4, 0.1, 0.6)}[ctype]
+    c.max_iters = 1
     orc = oracle_mod.Oracle(rb, constraint=c)
     q0s = on_manifold(orc, rb, 6, 121)
     rng = np.random.default_rng(122)
@@ -220,7 +222,8 @@ def test_first_iteration_combines_task_and_smoothing_terms(oracle_mod):
         prog = int(r["prog_trace"][0])
         assert np.array_equal(r["xi"][: prog + 1], xi[: prog + 1])
         assert r["first_fail"] == prog + 1
-        f = lambda x: indep.task_error(rb.joints, rb.ee, x, c.type)  # noqa: E731
+        f = lambda x: indep.task_error(rb.joints, rb.ee, x, c.type, c.target,  # noqa: E731
+                                       c.line_y, c.yaw)
         for i in range(prog + 1, len(t)):
             J = indep.fd_jacobian(f, xi[i], 1e-7)
             A = np.vstack([J, c.lam * np.eye(rb.dof)])
