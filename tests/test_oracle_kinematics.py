@@ -174,3 +174,19 @@ def test_damped_step_identities(oracle_mod):
         # J J^T + lambda^2 I has condition ~1/lambda^2 here: rounding grows with it
         assert np.abs(row_space @ g - g).max() < 1e-14 / lam ** 2
         assert np.abs(g - P @ e).max() < 50 * lam ** 2 * np.abs(P @ e).max() + 1e-9
+
+
+def test_prismatic_torso_translates_the_arm(oracle_mod):
+    """The 8-DOF arm's first joint slides along the base z axis: changing only it by delta
+    moves every later frame by delta along world z and rotates none of them (the prismatic
+    form of the DH factor adds q to d)."""
+    rb = S.make_arm8(3)
+    orc = oracle_mod.Oracle(rb)
+    for qi in S.uniform_configs(rb, 5, 17):
+        q2 = qi.copy()
+        delta = 0.4 - qi[0] if qi[0] < 0.2 else -qi[0]
+        q2[0] = qi[0] + delta
+        F, G = orc.fk(qi), orc.fk(q2)
+        for k in range(1, len(F)):
+            assert np.abs(G[k][:3, :3] - F[k][:3, :3]).max() < 1e-14
+            assert np.abs(G[k][:3, 3] - F[k][:3, 3] - [0.0, 0.0, delta]).max() < 1e-14
