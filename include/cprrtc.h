@@ -17,7 +17,8 @@
  *  - Array pointers may be host or device memory (detected per pointer). If every array of
  *    a call is device memory the call is asynchronous on the context's stream; otherwise
  *    the library copies through its own device buffers and returns after the results are in
- *    host memory.
+ *    host memory. Device memory must belong to the context's GPU (managed memory is
+ *    accepted as it is); an array in another GPU's memory is E_INVALID_ARG.
  *  - The caller owns every buffer it passes. set_* calls copy their arguments into
  *    library-owned device memory, replacing the previous copy.
  *  - One context per host thread; contexts are independent.
@@ -237,6 +238,30 @@ int64_t cprrtc_mlp_param_count(int dof);
  * Requires set_robot. Errors: E_NOT_CONFIGURED, E_CUDA, E_OOM. */
 int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed);
 
+/* Limit of every bounded wait in the tensor-core kernels (the GEMM-form collision check and
+ * the warm-start network's fused inference), in seconds: 0 restores the default of 1 s;
+ * otherwise 1e-6 .. 10. A wait that reaches it makes the kernel give up: it raises its
+ * abort flag, lets its copies and MMAs in flight complete, frees its tensor memory and
+ * exits, and the call reports it: cprrtc_validate with a GEMM mode and cprrtc_mlp_infer
+ * return E_TIMEOUT when they are synchronous (some array in host memory; their outputs are
+ * then not valid), and cprrtc_validate_ws falls back to plain Alg. 1 for every motion. The
+ * next call starts afresh. The paper has no counterpart: this is a failure-detection
+ * setting, and a very short limit lets a test make the waits run out on an ordinary input.
+ * Errors: E_INVALID_ARG. */
+int cprrtc_set_wait_limit(cprrtc_ctx* ctx, double seconds);
+
+/* Arithmetic of the network's calls (cprrtc_mlp_grad, cprrtc_mlp_train, cprrtc_mlp_infer,
+ * cprrtc_validate_ws): CPRRTC_MLP_BF16 (the default; BF16 weights and activations, FP32
+ * accumulation, tensor-core inference) or CPRRTC_MLP_FP32, a checking mode with the FP32
+ * master weights and FP32 activations on FP32 FMA kernels (no BF16 rounding anywhere; the
+ * inference is the unfused forward pass). The checking mode separates the layers'
+ * arithmetic from BF16 rounding when the kernels are compared with an FP64 evaluation; it
+ * is not a production path. The setting persists across cprrtc_mlp_init.
+ * Errors: E_INVALID_ARG (unknown precision). */
+#define CPRRTC_MLP_BF16 0
+#define CPRRTC_MLP_FP32 1
+int cprrtc_mlp_set_precision(cprrtc_ctx* ctx, int precision);
+
 /* Sets / reads the parameters (host arrays of `count` = cprrtc_mlp_param_count(dof)
  * floats). Setting resets the Adam state. Errors: E_NOT_CONFIGURED (no network),
  * E_INVALID_ARG (count mismatch, null), E_CUDA. */
@@ -449,15 +474,22 @@ int cprrtc_batch_replay(cprrtc_ctx* ctx);
  * arguments.
  *  - It allocates nothing: the trees live in a file-scope device array of
  *    CPRRTC_STATIC_SCRATCH_BYTES instead of library-allocated memory. Inputs and outputs
- *    are the caller's and must all be device memory (host pointers: E_INVALID_ARG).
+ *    are the caller's and must all be device memory of the context's GPU (host pointers,
+ *    or another GPU's memory: E_INVALID_ARG).
  *  - Sizes beyond the array (n * 2 * max_nodes * (W * dof + 9) * 4 bytes plus
  *    n * workers * (2 * W * dof + 8) * 4 bytes, each part rounded up to 256 bytes) are
- *    rejected with E_CAPACITY.
- *  - The first call on a device looks up the array's device address (once per device);
- *    make that first call before any stream capture.
+ *    rejected with E_CAPACITY before anything is launched; the sizes are checked factor by
+ *    factor, so no product can wrap around and pass.
+ *  - The first call on a device looks up the array's device address (once per device and
+ *    CUDA context); make that first call before any stream capture. A device reset
+ *    (cudaDeviceReset, or a reset of the primary context) makes a new context, and the
+ *    next call after it looks the address up again.
  *  - Every call on a device shares the one array, whose contents persist between calls;
- *    calls that overlap on the GPU (other streams, other host threads) race on it.
- *  - Kernel timing (cprrtc_set_timing) does not cover this call.
+ *    calls that overlap on the GPU (other streams, other host threads) race on it. The
+ *    planner initialises every tree it reads, so a call never depends on an earlier
+ *    call's contents.
+ *  - Its work is added to cprrtc_work_counters like cprrtc_plan's. Kernel timing
+ *    (cprrtc_set_timing) does not cover this call.
  * Errors: as cprrtc_plan, plus E_CAPACITY. */
 int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                        const cprrtc_plan_params* params, int32_t* path_len, float* path,

@@ -23,6 +23,7 @@ OK = 0
 E_INVALID_ARG, E_NOT_CONFIGURED, E_CUDA, E_OOM, E_CAPACITY, E_TIMEOUT, E_UNSUPPORTED = \
     -1, -2, -3, -4, -5, -6, -7
 MOTION_VALID, MOTION_PROJ_FAIL, MOTION_COLLISION = 0, 1, 2
+MLP_BF16, MLP_FP32 = 0, 1
 MAX_DOF, MAX_W, MAX_SPHERES = 8, 64, 256
 
 JOINT_DT = np.dtype([("type", "<i4"), ("d", "<f8"), ("a", "<f8"), ("alpha", "<f8"),
@@ -115,6 +116,8 @@ _SIGS = {
     "cprrtc_cc_stats": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_int],
     "cprrtc_mlp_param_count": [C.c_int],
     "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
+    "cprrtc_mlp_set_precision": [C.c_void_p, C.c_int],
+    "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
@@ -382,6 +385,14 @@ class Context:
 
     def mlp_init(self, seed: int = 0):
         self._check(self._L.cprrtc_mlp_init(self.h, int(seed)))
+
+    def set_wait_limit(self, seconds: float):
+        """Limit of the tensor-core kernels' bounded waits (0: the default, 1 s)."""
+        self._check(self._L.cprrtc_set_wait_limit(self.h, float(seconds)))
+
+    def mlp_set_precision(self, fp32: bool):
+        """FP32 checking mode (True) or the BF16 tensor-core arithmetic (False)."""
+        self._check(self._L.cprrtc_mlp_set_precision(self.h, MLP_FP32 if fp32 else MLP_BF16))
 
     def mlp_set_params(self, params):
         p = np.ascontiguousarray(params, np.float32)

@@ -98,6 +98,8 @@ struct cprrtc_ctx {
   size_t cc_ff_cap = 0;
   // learned warm start
   MlpDev* mlp = nullptr;
+  bool mlp_fp32 = false;    // the network's FP32 checking mode
+  unsigned long long wait_ns = 0;  // bounded-wait limit of the tensor-core kernels (0: 1 s)
   float* d_warm = nullptr;  // corrections [n*W][16]
   size_t warm_cap = 0;      // bytes
   bool timing = false;
@@ -147,6 +149,23 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Where an array argument lives, seen from `device`: host memory (pageable or pinned),
+// device memory of `device` or managed memory (usable as it is), or device memory of
+// another GPU (rejected: the kernels would read or write peer memory nobody mapped).
+enum PtrWhere { kPtrHost = 0, kPtrHere = 1, kPtrOtherDevice = 2 };
+
+PtrWhere ptr_where(const void* p, int device) {
+  if (!p) return kPtrHost;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kPtrHost;
+  }
+  if (a.type == cudaMemoryTypeManaged) return kPtrHere;
+  if (a.type == cudaMemoryTypeDevice) return a.device == device ? kPtrHere : kPtrOtherDevice;
+  return kPtrHost;
+}
+
 cudaEvent_t take_event(cprrtc_ctx* ctx) {
   if (!ctx->events.empty()) {
     cudaEvent_t e = ctx->events.back();
@@ -191,10 +210,23 @@ struct Staging {
   std::vector<Item> items;
   size_t total = 0;
   bool any_host = false;
+  bool foreign = false;  // some array is device memory of another GPU
+  int device = -1;       // the context's device (current while a call runs)
+
+  // Classifies p against the current device: true if it is used as it is (null, empty,
+  // device memory of this GPU or managed memory); a foreign device pointer is recorded and
+  // makes begin() fail.
+  bool usable(const void* p, size_t bytes) {
+    if (!p || bytes == 0) return true;
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) device = -1;
+    const PtrWhere w = ptr_where(p, device);
+    if (w == kPtrOtherDevice) foreign = true;
+    return w != kPtrHost;
+  }
 
   template <class T>
   void input(const T* p, size_t bytes, const T** dev) {
-    if (!p || bytes == 0 || is_device_ptr(p)) {
+    if (usable(p, bytes)) {
       *dev = p;
       return;
     }
@@ -204,7 +236,7 @@ struct Staging {
   }
   template <class T>
   void output(T* p, size_t bytes, T** dev) {
-    if (!p || bytes == 0 || is_device_ptr(p)) {
+    if (usable(p, bytes)) {
       *dev = p;
       return;
     }
@@ -214,6 +246,9 @@ struct Staging {
   }
   // Allocates, assigns device pointers and uploads inputs.
   int begin(cprrtc_ctx* ctx) {
+    if (foreign)
+      return fail(ctx, CPRRTC_E_INVALID_ARG,
+                  "an array argument is device memory of another GPU than the context's");
     if (total > ctx->stage_cap) {
       const size_t cap = std::max(total, ctx->stage_cap * 2);
       if (ctx->d_stage) cudaFree(ctx->d_stage);
@@ -985,7 +1020,10 @@ int cprrtc_validate(cprrtc_ctx* ctx, const float* q_start, const float* q_end, i
     g.counters = ctx->d_cc_counters;
     g.error = ctx->d_cc_error;
     g.next = reinterpret_cast<int*>(ctx->d_cc_counters + 2);
+    g.wait_ns = ctx->wait_ns;
     e = cudaMemsetAsync(g.next, 0, sizeof(int), ctx->stream);
+    // a timeout of an earlier call must not be reported again
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_cc_error, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "validate: GEMM-form scheduling counter");
     LaunchTimer tg(ctx, "gemm_cc");
     e = launch_gemm_cc(ctx->cc_mode == CPRRTC_CC_GEMM_TF32, ctx->rb, g, ctx->dev.sm_count, ctx->stream);
@@ -1062,8 +1100,30 @@ int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed) {
     ctx->mlp = nullptr;
   }
   cudaError_t e = mlp_create(&ctx->mlp, ctx->rb.dof);
+  if (e == cudaSuccess) {
+    mlp_set_fp32(ctx->mlp, ctx->mlp_fp32);
+    mlp_set_wait_ns(ctx->mlp, ctx->wait_ns);
+  }
   if (e == cudaSuccess) e = mlp_init(ctx->mlp, seed, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_init");
+  return CPRRTC_OK;
+}
+
+int cprrtc_set_wait_limit(cprrtc_ctx* ctx, double seconds) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (!(seconds == 0.0 || (seconds >= 1e-6 && seconds <= 10.0)))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_wait_limit: 0 (default) or 1e-6 .. 10 seconds");
+  ctx->wait_ns = (unsigned long long)(seconds * 1e9);
+  if (ctx->mlp) mlp_set_wait_ns(ctx->mlp, ctx->wait_ns);
+  return CPRRTC_OK;
+}
+
+int cprrtc_mlp_set_precision(cprrtc_ctx* ctx, int precision) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (precision != CPRRTC_MLP_BF16 && precision != CPRRTC_MLP_FP32)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "mlp_set_precision: CPRRTC_MLP_BF16 or CPRRTC_MLP_FP32");
+  ctx->mlp_fp32 = precision == CPRRTC_MLP_FP32;
+  if (ctx->mlp) mlp_set_fp32(ctx->mlp, ctx->mlp_fp32);
   return CPRRTC_OK;
 }
 
@@ -1192,6 +1252,8 @@ int cprrtc_mlp_load(cprrtc_ctx* ctx, const char* path) {
     }
     cudaError_t e = mlp_create(&ctx->mlp, ctx->rb.dof);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_load");
+    mlp_set_fp32(ctx->mlp, ctx->mlp_fp32);
+    mlp_set_wait_ns(ctx->mlp, ctx->wait_ns);
   }
   std::vector<float> p(n), m(n), v(n);
   memcpy(p.data(), buf.data() + sizeof(h), n * 4);
@@ -1560,8 +1622,43 @@ static __device__ __align__(256) unsigned char g_plan_scratch[CPRRTC_STATIC_SCRA
 constexpr int kStaticMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticMaxDevices] = {};
+unsigned long long g_static_ctx[kStaticMaxDevices] = {};  // context id the address belongs to
+
+// Unique id of the current CUDA context (driver entry points looked up through the runtime,
+// so the library does not link the driver library). 0 when unavailable.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrentFn>(f1);
+      get_id = reinterpret_cast<GetIdFn>(f2);
+    } else {
+      cudaGetLastError();
+    }
+    looked_up = true;
+  }
+  void* c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of g_plan_scratch on `device` (which must be current); nullptr on error.
+// The address is looked up once per device and context: a device reset (cudaDeviceReset,
+// or a reset of the primary context) creates a new context, whose id no longer matches, and
+// the next call looks the address up again. Without the context id (an old driver) the
+// address is looked up on every call.
 void* static_scratch(int device, cudaError_t* err) {
   *err = cudaSuccess;
   if (device < 0 || device >= kStaticMaxDevices) {
@@ -1569,13 +1666,25 @@ void* static_scratch(int device, cudaError_t* err) {
     return nullptr;
   }
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[device]) {
+  const unsigned long long id = current_context_id();
+  if (!g_static_ptr[device] || id == 0 || id != g_static_ctx[device]) {
     void* p = nullptr;
     *err = cudaGetSymbolAddress(&p, g_plan_scratch);
-    if (*err != cudaSuccess) return nullptr;
+    if (*err != cudaSuccess) {
+      g_static_ptr[device] = nullptr;
+      return nullptr;
+    }
     g_static_ptr[device] = p;
+    g_static_ctx[device] = id;
   }
   return g_static_ptr[device];
+}
+
+// a * b into *out unless it exceeds `limit` (or overflows); false then.
+bool mul_within(size_t a, size_t b, size_t limit, size_t* out) {
+  if (a != 0 && b > limit / a) return false;
+  *out = a * b;
+  return *out <= limit;
 }
 
 }  // namespace
@@ -1601,21 +1710,37 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   if (int rc = check_plan_workers(ctx, pp, "plan_static")) return rc;
   const void* arrays[] = {start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work};
   for (const void* a : arrays)
-    if (a && !is_device_ptr(a))
-      return fail(ctx, CPRRTC_E_INVALID_ARG, "plan_static: every array must be device memory");
+    if (a && ptr_where(a, ctx->device) != kPtrHere)
+      return fail(ctx, CPRRTC_E_INVALID_ARG,
+                  "plan_static: every array must be device memory of the context's GPU");
   const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
   const size_t B = (size_t)pp->workers, MN = (size_t)pp->max_nodes;
+  // Every product is bounded by the array's size before it is formed, so that no size wraps
+  // around to a small value and passes the capacity check (the array is this call's only
+  // guard: no allocation can fail first).
+  const size_t cap = (size_t)CPRRTC_STATIC_SCRATCH_BYTES;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t b_nodes = al(N * 2 * MN * 8 * sizeof(float));
-  const size_t b_parent = al(N * 2 * MN * sizeof(int));
-  const size_t b_edges = al(N * 2 * MN * W * dof * sizeof(float));
-  const size_t b_pend = al(N * B * 8 * sizeof(float));
-  const size_t b_pedge = al(N * B * 2 * W * dof * sizeof(float));
-  const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
-  if (need > (size_t)CPRRTC_STATIC_SCRATCH_BYTES)
+  size_t trees = 0, per_node = 0, b_tree_part = 0, workers_n = 0, per_worker = 0, b_w = 0;
+  const bool fits = mul_within(N, 2 * MN, cap, &trees) &&         // tree nodes of all problems
+                    mul_within(W * dof + 9, sizeof(float), cap, &per_node) &&
+                    mul_within(trees, per_node, cap, &b_tree_part) &&
+                    mul_within(N, B, cap, &workers_n) &&
+                    mul_within(2 * W * dof + 8, sizeof(float), cap, &per_worker) &&
+                    mul_within(workers_n, per_worker, cap, &b_w);
+  size_t need = cap + 1;
+  size_t b_nodes = 0, b_parent = 0, b_edges = 0, b_pend = 0, b_pedge = 0;
+  if (fits) {
+    b_nodes = al(trees * 8 * sizeof(float));
+    b_parent = al(trees * sizeof(int));
+    b_edges = al(trees * W * dof * sizeof(float));
+    b_pend = al(workers_n * 8 * sizeof(float));
+    b_pedge = al(workers_n * 2 * W * dof * sizeof(float));
+    need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
+  }
+  if (need > cap)
     return fail(ctx, CPRRTC_E_CAPACITY,
-                "plan_static: needs " + std::to_string(need) + " bytes of scratch, the fixed array holds " +
-                    std::to_string((size_t)CPRRTC_STATIC_SCRATCH_BYTES) +
+                std::string("plan_static: needs ") + (fits ? std::to_string(need) : std::string("more")) +
+                    " bytes of scratch, the fixed array holds " + std::to_string(cap) +
                     " (reduce n, max_nodes, W or workers)");
   cudaError_t e;
   char* base = static_cast<char*>(static_scratch(ctx->device, &e));
@@ -1655,6 +1780,7 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   a.waypoints = reinterpret_cast<long long*>(waypoints);
   a.plan_ms = plan_ms;
   a.work = reinterpret_cast<long long*>(work);
+  a.work_counters = ctx->d_work;  // allocated with the context: nothing is allocated here
   e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "plan_static launch");
   return CPRRTC_OK;
@@ -2086,8 +2212,9 @@ int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
   DeviceGuard g(ctx->device);
   const void* arrays[] = {start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work};
   for (const void* ptr : arrays)
-    if (ptr && !is_device_ptr(ptr))
-      return fail(ctx, CPRRTC_E_INVALID_ARG, "batch capture: every array must be device memory");
+    if (ptr && ptr_where(ptr, ctx->device) != kPtrHere)
+      return fail(ctx, CPRRTC_E_INVALID_ARG,
+                  "batch capture: every array must be device memory of the context's GPU");
   BatchPlan bp;
   rc = prepare_batch(ctx, problems, n, bp);
   if (rc) return rc;

@@ -91,8 +91,10 @@ constexpr int kRingM = 8;
 // spread over the SMs instead of ending the launch on a few of them.
 constexpr int kWpRun = 16;
 constexpr int kSmemCc = kOffRing8 + (kRingM + 2) * 4;
-constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint64_t kWaitNs = 1000000000ull;  // default limit of a bounded wait: 1 s
 constexpr uint64_t kDrainNs = 20000000ull;
+// this launch's limit of a bounded wait (set by thread 0 before the first barrier)
+__shared__ uint64_t s_wait_ns;
 static_assert(kOffBarCc % 8 == 0 && kOffRechk % 8 == 0, "alignment");
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -128,7 +130,7 @@ __device__ bool mb_wait(uint32_t b, uint32_t parity, volatile int* abort_flag) {
     for (int i = 0; i < 32; ++i)
       if (mb_try(b, parity)) return true;
     if (*abort_flag) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > s_wait_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -238,6 +240,7 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
       s_hit[i] = 0;
     }
     *s_abort = 0;
+    s_wait_ns = a.wait_ns ? a.wait_ns : kWaitNs;
     *s_rechk = 0ull;
     *reinterpret_cast<volatile int*>(sm + kOffRing8 + kRingM * 4) = 0;
     *reinterpret_cast<volatile int*>(sm + kOffRing8 + kRingM * 4 + 4) = 0;
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, Gem
     const uint64_t t0 = gtime();
     while (*cnt < need) {
       if (*s_abort) return false;
-      if (gtime() - t0 > kWaitNs) {
+      if (gtime() - t0 > s_wait_ns) {
         *s_abort = 1;
         return false;
       }

@@ -135,6 +135,9 @@ size_t mlp_compact_count(int dof);
 cudaError_t mlp_create(MlpDev** out, int dof);
 void mlp_destroy(MlpDev* d);
 int mlp_dof(const MlpDev* d);
+void mlp_set_fp32(MlpDev* d, bool on);  // FP32 checking mode (no BF16 rounding)
+void mlp_set_wait_ns(MlpDev* d, unsigned long long ns);  // bounded-wait limit of inference
+bool mlp_fp32(const MlpDev* d);
 int mlp_step(const MlpDev* d);
 cudaError_t mlp_set_params(MlpDev* d, const float* host, cudaStream_t s);
 cudaError_t mlp_get_params(MlpDev* d, float* host, cudaStream_t s);
@@ -169,6 +172,7 @@ struct GemmCcArgs {
   unsigned long long* counters;  // [1] exact rechecks (may be null)
   int* error;
   int* next;  // motion counter for the CTAs' dynamic scheduling, zeroed before the launch
+  unsigned long long wait_ns;  // limit of every bounded wait (0: the default, 1 s)
 };
 size_t gemm_cc_smem_bytes();
 cudaError_t launch_gemm_cc(int tf32, const RobotDev& rb, const GemmCcArgs& a, int sm_count, cudaStream_t s);
@@ -187,6 +191,7 @@ struct FusedMlpArgs {
   const float* bias;     // [3][256] + [16] FP32
   float* out;            // [rows][16] corrections
   int* error;            // set to 1 when a wait timed out
+  unsigned long long wait_ns;  // limit of every bounded wait (0: the default, 1 s)
 };
 size_t mlp_fused_image_bytes();
 int mlp_fused_bias_floats();

@@ -9,6 +9,12 @@
 // 32 x 32), staged in shared memory as [row][k] with a padded pitch (conflict-free
 // fragment loads), transposed on the way in when needed. Epilogues fuse the bias, GELU,
 // GELU's derivative and split-K accumulation.
+//
+// FP32 checking mode: the same network, forward pass and gradient with FP32 weights and
+// activations (no rounding to BF16 anywhere) on a plain FP32 FMA GEMM with the same
+// epilogues. It separates the arithmetic of the layers from the BF16 rounding when the
+// kernels are compared with an FP64 evaluation; inference in this mode skips the fused
+// tensor-core kernel.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -44,20 +50,53 @@ enum : int {
   kEpiAtomic = 4,    // C (FP32) += acc  (split-K)
 };
 
-struct GemmArgs {
+// Operands of one GEMM; T is the element type of A, B and the activation output H (BF16, or
+// FP32 in the checking mode).
+template <class T>
+struct GemmArgsT {
   int M, N, K;
-  const __nv_bfloat16* A;
+  const T* A;
   int lda, transA;
-  const __nv_bfloat16* B;
+  const T* B;
   int ldb, transB;
   float* C;  // FP32 output / Z (ldc)
   int ldc;
-  __nv_bfloat16* H;  // BF16 output (ldh)
+  T* H;      // activation output (ldh)
   int ldh;
   const float* bias;
   const float* Z;  // pre-activation for the GELU backward (ldc)
   int k_split;     // K range per blockIdx.z
 };
+using GemmArgs = GemmArgsT<__nv_bfloat16>;
+using GemmArgsF = GemmArgsT<float>;
+
+template <class T>
+__device__ __forceinline__ T to_act(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_act<__nv_bfloat16>(float x) { return __float2bfloat16(x); }
+template <>
+__device__ __forceinline__ float to_act<float>(float x) { return x; }
+__device__ __forceinline__ float act_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float act_f(float x) { return x; }
+
+// The epilogue of one accumulated element (row gm, column gn), shared by both GEMMs.
+template <int EPI, class T>
+__device__ __forceinline__ void epilogue(const GemmArgsT<T>& g, int gm, int gn, float v) {
+  const size_t ci = (size_t)gm * g.ldc + gn;
+  if (EPI == kEpiStore) {
+    g.C[ci] = v;
+  } else if (EPI == kEpiAtomic) {
+    atomicAdd(&g.C[ci], v);
+  } else if (EPI == kEpiBias) {
+    g.C[ci] = v + g.bias[gn];
+  } else if (EPI == kEpiBiasGelu) {
+    const float z = v + g.bias[gn];
+    if (g.C) g.C[ci] = z;
+    g.H[(size_t)gm * g.ldh + gn] = to_act<T>(mlp_gelu(z));
+  } else {  // kEpiGeluBwd
+    g.H[(size_t)gm * g.ldh + gn] = to_act<T>(v * mlp_gelu_grad(g.Z[ci]));
+  }
+}
 
 template <int EPI>
 __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
@@ -143,36 +182,97 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
         const int gm = m0 + wm + 16 * i + gid + (r >> 1) * 8;
         const int gn = n0 + wn + 8 * j + 2 * tig + (r & 1);
         if (gm >= g.M || gn >= g.N) continue;
-        const float v = acc[i][j][r];
-        const size_t ci = (size_t)gm * g.ldc + gn;
-        if (EPI == kEpiStore) {
-          g.C[ci] = v;
-        } else if (EPI == kEpiAtomic) {
-          atomicAdd(&g.C[ci], v);
-        } else if (EPI == kEpiBias) {
-          g.C[ci] = v + g.bias[gn];
-        } else if (EPI == kEpiBiasGelu) {
-          const float z = v + g.bias[gn];
-          if (g.C) g.C[ci] = z;
-          g.H[(size_t)gm * g.ldh + gn] = __float2bfloat16(mlp_gelu(z));
-        } else {  // kEpiGeluBwd
-          g.H[(size_t)gm * g.ldh + gn] = __float2bfloat16(v * mlp_gelu_grad(g.Z[ci]));
-        }
+        epilogue<EPI>(g, gm, gn, acc[i][j][r]);
       }
+}
+
+// The FP32 checking mode's GEMM: 64 x 64 output tiles, K steps of 16, 256 threads with 4 x 4
+// outputs each; operands staged in shared memory as [k][row] (transposed on the way in
+// when needed); FP32 FMA accumulation in k order within a split.
+constexpr int kFK = 16;
+template <int EPI>
+__global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgsF g) {
+  __shared__ float As[kFK][kTM + 4];
+  __shared__ float Bs[kFK][kTN + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
+  const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += kFK) {
+    for (int e = tid; e < kTM * kFK; e += 256) {
+      int r, k;
+      if (g.transA) {  // source [K][M]
+        r = e % kTM;
+        k = e / kTM;
+      } else {         // source [M][K]
+        r = e / kFK;
+        k = e % kFK;
+      }
+      const int gm = m0 + r, gk = k0 + k;
+      float v = 0.f;
+      if (gm < g.M && gk < ke) v = g.transA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+      As[k][r] = v;
+    }
+    for (int e = tid; e < kTN * kFK; e += 256) {
+      int c, k;
+      if (g.transB) {  // source [N][K]
+        c = e / kFK;
+        k = e % kFK;
+      } else {         // source [K][N]
+        c = e % kTN;
+        k = e / kTN;
+      }
+      const int gn = n0 + c, gk = k0 + k;
+      float v = 0.f;
+      if (gn < g.N && gk < ke) v = g.transB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
+      Bs[k][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kFK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+      if (gm < g.M && gn < g.N) epilogue<EPI>(g, gm, gn, acc[i][j]);
+    }
+}
+
+// Grid of one GEMM: output tiles, and for the split-K epilogue enough splits of the
+// reduction to cover the GPU.
+template <class T>
+static dim3 gemm_grid(int epi, GemmArgsT<T>& g, int k_step) {
+  int splits = 1;
+  if (epi == kEpiAtomic) {
+    const int tiles = ((g.M + kTM - 1) / kTM) * ((g.N + kTN - 1) / kTN);
+    splits = std::max(1, std::min((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
+  }
+  g.k_split = ((g.K + splits - 1) / splits + k_step - 1) / k_step * k_step;
+  splits = (g.K + g.k_split - 1) / g.k_split;
+  return dim3((g.M + kTM - 1) / kTM, (g.N + kTN - 1) / kTN, splits);
 }
 
 cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
   GemmArgs g = g0;
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-  int splits = 1;
-  if (epi == kEpiAtomic) {
-    // split the reduction so that the grid covers the GPU
-    const int tiles = ((g.M + kTM - 1) / kTM) * ((g.N + kTN - 1) / kTN);
-    splits = std::max(1, std::min((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
-  }
-  g.k_split = ((g.K + splits - 1) / splits + kTK - 1) / kTK * kTK;
-  splits = (g.K + g.k_split - 1) / g.k_split;
-  dim3 grid((g.M + kTM - 1) / kTM, (g.N + kTN - 1) / kTN, splits);
+  const dim3 grid = gemm_grid(epi, g, kTK);
   switch (epi) {
     case kEpiStore: gemm_bf16_kernel<kEpiStore><<<grid, 128, 0, stream>>>(g); break;
     case kEpiBiasGelu: gemm_bf16_kernel<kEpiBiasGelu><<<grid, 128, 0, stream>>>(g); break;
@@ -183,20 +283,35 @@ cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_gemm(int epi, const GemmArgsF& g0, cudaStream_t stream) {
+  GemmArgsF g = g0;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  const dim3 grid = gemm_grid(epi, g, kFK);
+  switch (epi) {
+    case kEpiStore: gemm_f32_kernel<kEpiStore><<<grid, 256, 0, stream>>>(g); break;
+    case kEpiBiasGelu: gemm_f32_kernel<kEpiBiasGelu><<<grid, 256, 0, stream>>>(g); break;
+    case kEpiBias: gemm_f32_kernel<kEpiBias><<<grid, 256, 0, stream>>>(g); break;
+    case kEpiGeluBwd: gemm_f32_kernel<kEpiGeluBwd><<<grid, 256, 0, stream>>>(g); break;
+    default: gemm_f32_kernel<kEpiAtomic><<<grid, 256, 0, stream>>>(g); break;
+  }
+  return cudaGetLastError();
+}
+
 // ---- elementwise kernels ---------------------------------------------------------------
 
 // X[r][0..in) = q[r][k] / pi (k < dof), zero padding; rows of the input to layer 1.
-__global__ void mlp_input_kernel(const float* __restrict__ q, int ldq, int rows, int dof, int in,
-                                 __nv_bfloat16* X) {
+template <class T>
+__global__ void mlp_input_kernel(const float* __restrict__ q, int ldq, int rows, int dof, int in, T* X) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * in) return;
   const int r = i / in, k = i - r * in;
-  X[i] = __float2bfloat16(k < dof ? q[(size_t)r * ldq + k] * kMlpInvPi : 0.f);
+  X[i] = to_act<T>(k < dof ? q[(size_t)r * ldq + k] * kMlpInvPi : 0.f);
 }
 
 // Interpolated waypoints of each motion as MLP input rows (row m * W + i).
+template <class T>
 __global__ void mlp_interp_input_kernel(const float* __restrict__ q0, const float* __restrict__ q1,
-                                        int n, int W, int dof, int in, __nv_bfloat16* X) {
+                                        int n, int W, int dof, int in, T* X) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * W * in) return;
   const int r = i / in, k = i - r * in;
@@ -206,13 +321,13 @@ __global__ void mlp_interp_input_kernel(const float* __restrict__ q0, const floa
     const float a = q0[(size_t)m * dof + k], b = q1[(size_t)m * dof + k];
     v = fmaf((float)w / (float)(W - 1), b - a, a) * kMlpInvPi;
   }
-  X[i] = __float2bfloat16(v);
+  X[i] = to_act<T>(v);
 }
 
 // dY = (Y - T) / rows on the dof used outputs (zero on padding), and the loss 0.5 |Y-T|^2 / rows.
+template <class A>
 __global__ void mse_grad_kernel(const float* __restrict__ Y, int ldy, const float* __restrict__ T,
-                                int ldt, int rows, int dof, int out, __nv_bfloat16* dY,
-                                float* loss) {
+                                int ldt, int rows, int dof, int out, A* dY, float* loss) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.f;
   if (i < rows * out) {
@@ -222,18 +337,19 @@ __global__ void mse_grad_kernel(const float* __restrict__ Y, int ldy, const floa
       d = Y[(size_t)r * ldy + k] - T[(size_t)r * ldt + k];
       l = 0.5f * d * d / (float)rows;
     }
-    dY[i] = __float2bfloat16(d / (float)rows);
+    dY[i] = to_act<A>(d / (float)rows);
   }
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
   if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l);
 }
 
-// db[n] = sum_r D[r][n]  (D in BF16, [rows][ld])
-__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ D, int ld, int rows, int N, float* db) {
+// db[n] = sum_r D[r][n]  (D [rows][ld])
+template <class T>
+__global__ void bias_grad_kernel(const T* __restrict__ D, int ld, int rows, int N, float* db) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   float s = 0.f;
-  for (int r = blockIdx.y; r < rows; r += gridDim.y) s += __bfloat162float(D[(size_t)r * ld + n]);
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) s += act_f(D[(size_t)r * ld + n]);
   atomicAdd(&db[n], s);
 }
 
@@ -294,34 +410,37 @@ cudaError_t launch_accumulate(float* dst, const float* src, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_input(const float* q, int ldq, int rows, int dof, int in, __nv_bfloat16* X,
-                             cudaStream_t s) {
+template <class T>
+cudaError_t launch_mlp_input(const float* q, int ldq, int rows, int dof, int in, T* X, cudaStream_t s) {
   const int n = rows * in;
   if (n <= 0) return cudaSuccess;
-  mlp_input_kernel<<<(n + 255) / 256, 256, 0, s>>>(q, ldq, rows, dof, in, X);
+  mlp_input_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(q, ldq, rows, dof, in, X);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_interp_input(const float* q0, const float* q1, int n, int W, int dof, int in,
-                                    __nv_bfloat16* X, cudaStream_t s) {
+template <class T>
+cudaError_t launch_mlp_interp_input(const float* q0, const float* q1, int n, int W, int dof, int in, T* X,
+                                    cudaStream_t s) {
   const long long tot = (long long)n * W * in;
   if (tot <= 0) return cudaSuccess;
-  mlp_interp_input_kernel<<<(int)((tot + 255) / 256), 256, 0, s>>>(q0, q1, n, W, dof, in, X);
+  mlp_interp_input_kernel<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(q0, q1, n, W, dof, in, X);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mse_grad(const float* Y, int ldy, const float* T, int ldt, int rows, int dof, int out,
-                            __nv_bfloat16* dY, float* loss, cudaStream_t s) {
+template <class T>
+cudaError_t launch_mse_grad(const float* Y, int ldy, const float* Tg, int ldt, int rows, int dof, int out,
+                            T* dY, float* loss, cudaStream_t s) {
   const int n = rows * out;
   if (n <= 0) return cudaSuccess;
-  mse_grad_kernel<<<(n + 255) / 256, 256, 0, s>>>(Y, ldy, T, ldt, rows, dof, out, dY, loss);
+  mse_grad_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(Y, ldy, Tg, ldt, rows, dof, out, dY, loss);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bias_grad(const __nv_bfloat16* D, int ld, int rows, int N, float* db, cudaStream_t s) {
+template <class T>
+cudaError_t launch_bias_grad(const T* D, int ld, int rows, int N, float* db, cudaStream_t s) {
   if (rows <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + 127) / 128, std::min(rows, 256));
-  bias_grad_kernel<<<grid, 128, 0, s>>>(D, ld, rows, N, db);
+  bias_grad_kernel<T><<<grid, 128, 0, s>>>(D, ld, rows, N, db);
   return cudaGetLastError();
 }
 
@@ -377,6 +496,8 @@ struct MlpDev {
   int* err = nullptr;
   bool packed = false;
   int sm_count = 0;
+  bool fp32 = false;  // checking mode: FP32 weights and activations, unfused inference
+  unsigned long long wait_ns = 0;  // bounded-wait limit of the fused kernel (0: its default)
   // workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -438,6 +559,9 @@ void mlp_destroy(MlpDev* d) {
 }
 
 int mlp_dof(const MlpDev* d) { return d->dof; }
+void mlp_set_fp32(MlpDev* d, bool on) { d->fp32 = on; }
+void mlp_set_wait_ns(MlpDev* d, unsigned long long ns) { d->wait_ns = ns; }
+bool mlp_fp32(const MlpDev* d) { return d->fp32; }
 const int* mlp_error_flag(const MlpDev* d) { return d->err; }
 int mlp_step(const MlpDev* d) { return d->step; }
 
@@ -582,54 +706,67 @@ cudaError_t mlp_init(MlpDev* d, uint64_t seed, cudaStream_t s) {
   return mlp_set_params(d, p.data(), s);
 }
 
-// Workspace layout for `rows` rows: X (bf16 16) | H ping-pong (bf16 256 x 2) | Z x 3 (f32
-// 256, training only) | Y (f32 16) | dY (bf16 16) | dZ ping-pong (bf16 256 x 2) | loss (f32).
+// Workspace layout for `rows` rows: X (16) | H ping-pong (256 x 2) | Z x 3 (f32 256, training
+// only) | Y (f32 16) | dY (16) | dZ ping-pong (256 x 2) | loss (f32); X, H, dY and dZ in the
+// activation type T (BF16, or FP32 in the checking mode).
+template <class T>
 struct MlpWs {
-  __nv_bfloat16 *X, *H[2], *dY, *dZ[2];
+  T *X, *H[2], *dY, *dZ[2];
   float *Z[3], *Y, *loss;
 };
 
-static size_t ws_layout(char* base, int rows, bool train, MlpWs* w) {
+template <class T>
+static size_t ws_layout(char* base, int rows, bool train, MlpWs<T>* w) {
   size_t o = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + o : nullptr;
     o += (bytes + 255) & ~size_t(255);
     return p;
   };
-  const size_t R = (size_t)rows;
-  w->X = (__nv_bfloat16*)take(R * kMlpIO * 2);
-  w->H[0] = (__nv_bfloat16*)take(R * kMlpHidden * 2);
-  w->H[1] = (__nv_bfloat16*)take(R * kMlpHidden * 2);
+  const size_t R = (size_t)rows, e = sizeof(T);
+  w->X = (T*)take(R * kMlpIO * e);
+  w->H[0] = (T*)take(R * kMlpHidden * e);
+  w->H[1] = (T*)take(R * kMlpHidden * e);
   for (int i = 0; i < 3; ++i) w->Z[i] = train ? (float*)take(R * kMlpHidden * 4) : nullptr;
   w->Y = (float*)take(R * kMlpIO * 4);
-  w->dY = train ? (__nv_bfloat16*)take(R * kMlpIO * 2) : nullptr;
-  w->dZ[0] = train ? (__nv_bfloat16*)take(R * kMlpHidden * 2) : nullptr;
-  w->dZ[1] = train ? (__nv_bfloat16*)take(R * kMlpHidden * 2) : nullptr;
+  w->dY = train ? (T*)take(R * kMlpIO * e) : nullptr;
+  w->dZ[0] = train ? (T*)take(R * kMlpHidden * e) : nullptr;
+  w->dZ[1] = train ? (T*)take(R * kMlpHidden * e) : nullptr;
   w->loss = (float*)take(4);
   return o;
 }
 
-// Forward pass of rows of X already in w.X; Y (FP32 [rows][16]) = corrections. In training
-// mode the activations H_l (kept in a 3-deep set for the backward) and Z_l are stored.
-static cudaError_t forward(MlpDev* d, const MlpWs& w, int rows, __nv_bfloat16* Hkeep[3],
+// Layer l's weight [out][in] in the arithmetic's type: the BF16 copy, or the FP32 master.
+template <class T>
+static const T* weights_of(MlpDev* d, int l);
+template <>
+const __nv_bfloat16* weights_of<__nv_bfloat16>(MlpDev* d, int l) { return wb_of(d, l); }
+template <>
+const float* weights_of<float>(MlpDev* d, int l) { return d->p + w_off(l); }
+
+// Forward pass of rows of X already in w.X; Y (FP32 [rows][16], `y` or else w.Y) =
+// corrections. In training mode the activations H_l (kept in a 3-deep set for the backward)
+// and Z_l are stored.
+template <class T>
+static cudaError_t forward(MlpDev* d, const MlpWs<T>& w, int rows, T* Hkeep[3], float* y,
                            cudaStream_t s) {
-  const __nv_bfloat16* in = w.X;
+  const T* in = w.X;
   int ld_in = kMlpIO;
   for (int l = 0; l < kMlpLayers; ++l) {
-    GemmArgs g{};
+    GemmArgsT<T> g{};
     g.M = rows;
     g.N = kOut[l];
     g.K = kIn[l];
     g.A = in;
     g.lda = ld_in;
     g.transA = 0;
-    g.B = wb_of(d, l);  // [out][in] = [N][K]
+    g.B = weights_of<T>(d, l);  // [out][in] = [N][K]
     g.ldb = kIn[l];
     g.transB = 1;
     g.bias = d->p + w_off(l) + (size_t)kOut[l] * kIn[l];
     cudaError_t e;
     if (l < kMlpLayers - 1) {
-      __nv_bfloat16* out = Hkeep ? Hkeep[l] : w.H[l & 1];
+      T* out = Hkeep ? Hkeep[l] : w.H[l & 1];
       g.C = w.Z[0] && Hkeep ? w.Z[l] : nullptr;
       g.ldc = kMlpHidden;
       g.H = out;
@@ -638,7 +775,7 @@ static cudaError_t forward(MlpDev* d, const MlpWs& w, int rows, __nv_bfloat16* H
       in = out;
       ld_in = kMlpHidden;
     } else {
-      g.C = w.Y;
+      g.C = y ? y : w.Y;
       g.ldc = kMlpIO;
       e = launch_gemm(kEpiBias, g, s);
     }
@@ -665,12 +802,30 @@ static cudaError_t run_fused(MlpDev* d, FusedMlpArgs a, cudaStream_t s) {
   a.wpack = d->wpack;
   a.bias = d->bias_pad;
   a.error = d->err;
+  a.wait_ns = d->wait_ns;
   if (e == cudaSuccess) e = launch_mlp_fused(a, d->sm_count, s);
+  return e;
+}
+
+// The checking mode's inference: the unfused FP32 forward pass on rows of q (or of the
+// interpolated motions when q0 is set) into Y [rows][16].
+static cudaError_t infer_f32(MlpDev* d, const float* q, int ldq, const float* q0, const float* q1, int W,
+                             int rows, float* Y, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  MlpWs<float> w;
+  cudaError_t e = ensure_ws(d, ws_layout<float>(nullptr, rows, false, &w));
+  if (e != cudaSuccess) return e;
+  ws_layout<float>(d->ws, rows, false, &w);
+  e = q0 ? launch_mlp_interp_input<float>(q0, q1, rows / W, W, d->dof, kMlpIO, w.X, s)
+         : launch_mlp_input<float>(q, ldq, rows, d->dof, kMlpIO, w.X, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = forward<float>(d, w, rows, nullptr, Y, s);
   return e;
 }
 
 // Inference: corrections Y [rows][16] for rows of q ([rows][ldq], first dof used).
 cudaError_t mlp_infer(MlpDev* d, const float* q, int ldq, int rows, float* Y, cudaStream_t s) {
+  if (d->fp32) return infer_f32(d, q, ldq, nullptr, nullptr, 1, rows, Y, s);
   FusedMlpArgs a{};
   a.q = q;
   a.ldq = ldq;
@@ -682,6 +837,7 @@ cudaError_t mlp_infer(MlpDev* d, const float* q, int ldq, int rows, float* Y, cu
 // Inference on the interpolated waypoints of n motions (row m * W + i) into Y [n*W][16].
 cudaError_t mlp_infer_motions(MlpDev* d, const float* q0, const float* q1, int n, int W, float* Y,
                               cudaStream_t s) {
+  if (d->fp32) return infer_f32(d, nullptr, 0, q0, q1, W, n * W, Y, s);
   FusedMlpArgs a{};
   a.q0 = q0;
   a.q1 = q1;
@@ -693,36 +849,37 @@ cudaError_t mlp_infer_motions(MlpDev* d, const float* q0, const float* q1, int n
 
 // Loss 0.5 |MLP(q) - (t - q)|^2 averaged over rows and its gradient into d->g.
 // q, t: [rows][dof] device arrays. *loss_dev (device float) receives the loss.
+template <class T>
 static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int rows, cudaStream_t s,
-                                 MlpWs& w) {
-  const size_t need = ws_layout(nullptr, rows, true, &w) + (size_t)rows * kMlpIO * 4;
+                                 MlpWs<T>& w) {
+  const size_t need = ws_layout<T>(nullptr, rows, true, &w) + (size_t)rows * kMlpIO * 4;
   cudaError_t e = ensure_ws(d, need);
   if (e != cudaSuccess) return e;
-  const size_t used = ws_layout(d->ws, rows, true, &w);
+  const size_t used = ws_layout<T>(d->ws, rows, true, &w);
   float* target = reinterpret_cast<float*>(d->ws + used);  // t - q, [rows][16]
-  e = launch_mlp_input(q, d->dof, rows, d->dof, kMlpIO, w.X, s);
+  e = launch_mlp_input<T>(q, d->dof, rows, d->dof, kMlpIO, w.X, s);
   if (e != cudaSuccess) return e;
   e = launch_residual_target(q, t, rows, d->dof, target, s);
   if (e != cudaSuccess) return e;
-  __nv_bfloat16* H[3] = {w.H[0], w.H[1], w.dZ[1]};  // three stored activations
+  T* H[3] = {w.H[0], w.H[1], w.dZ[1]};  // three stored activations
   // a third activation buffer: reuse dZ[1] for H3 during the forward; the backward below
   // writes dZ only into buffers whose activation is no longer needed
-  e = forward(d, w, rows, H, s);
+  e = forward<T>(d, w, rows, H, nullptr, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(w.loss, 0, 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d->g, 0, mlp_param_count() * 4, s);
   if (e == cudaSuccess)
-    e = launch_mse_grad(w.Y, kMlpIO, target, kMlpIO, rows, d->dof, kMlpIO, w.dY, w.loss, s);
+    e = launch_mse_grad<T>(w.Y, kMlpIO, target, kMlpIO, rows, d->dof, kMlpIO, w.dY, w.loss, s);
   if (e != cudaSuccess) return e;
   // backward, layer 3 .. 0: D_l = dL/dZ_l (BF16), previous activation A_{l} = H[l-1] or X
-  const __nv_bfloat16* D = w.dY;
+  const T* D = w.dY;
   int ldD = kMlpIO;
-  __nv_bfloat16* dz_out[3] = {w.dZ[0], w.H[1], w.dZ[0]};  // dZ_2 -> dZ[0], dZ_1 -> H[1], dZ_0 -> dZ[0]
+  T* dz_out[3] = {w.dZ[0], w.H[1], w.dZ[0]};  // dZ_2 -> dZ[0], dZ_1 -> H[1], dZ_0 -> dZ[0]
   for (int l = kMlpLayers - 1; l >= 0; --l) {
-    const __nv_bfloat16* Aprev = l == 0 ? w.X : H[l - 1];
+    const T* Aprev = l == 0 ? w.X : H[l - 1];
     const int ldA = l == 0 ? kMlpIO : kMlpHidden;
     // weight gradient dW_l [out][in] = D^T Aprev  (split-K over rows, atomics)
-    GemmArgs gw{};
+    GemmArgsT<T> gw{};
     gw.M = kOut[l];
     gw.N = kIn[l];
     gw.K = rows;
@@ -735,18 +892,19 @@ static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int 
     gw.C = d->g + w_off(l);
     gw.ldc = kIn[l];
     e = launch_gemm(kEpiAtomic, gw, s);
-    if (e == cudaSuccess) e = launch_bias_grad(D, ldD, rows, kOut[l], d->g + w_off(l) + (size_t)kOut[l] * kIn[l], s);
+    if (e == cudaSuccess)
+      e = launch_bias_grad<T>(D, ldD, rows, kOut[l], d->g + w_off(l) + (size_t)kOut[l] * kIn[l], s);
     if (e != cudaSuccess) return e;
     if (l == 0) break;
     // dZ_{l-1} = (D W_l) * gelu'(Z_{l-1})
-    GemmArgs gd{};
+    GemmArgsT<T> gd{};
     gd.M = rows;
     gd.N = kIn[l];
     gd.K = kOut[l];
     gd.A = D;
     gd.lda = ldD;
     gd.transA = 0;
-    gd.B = wb_of(d, l);  // [out][in] = [K][N]
+    gd.B = weights_of<T>(d, l);  // [out][in] = [K][N]
     gd.ldb = kIn[l];
     gd.transB = 0;
     gd.Z = w.Z[l - 1];
@@ -763,9 +921,18 @@ static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int 
 
 cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float* grads_host,
                      float* loss_host, cudaStream_t s) {
-  MlpWs w;
-  cudaError_t e = loss_and_grad(d, q, t, rows, s, w);
-  if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, w.loss, 4, cudaMemcpyDeviceToHost, s);
+  float* loss_dev = nullptr;
+  cudaError_t e;
+  if (d->fp32) {
+    MlpWs<float> w;
+    e = loss_and_grad<float>(d, q, t, rows, s, w);
+    loss_dev = w.loss;
+  } else {
+    MlpWs<__nv_bfloat16> w;
+    e = loss_and_grad<__nv_bfloat16>(d, q, t, rows, s, w);
+    loss_dev = w.loss;
+  }
+  if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, loss_dev, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && grads_host) e = to_compact(d, d->g, grads_host, s);
   return e;
@@ -774,8 +941,17 @@ cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float*
 // One Adam step on the batch; the batch loss is added to *loss_dev (device) if given.
 cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, float lr,
                            float* loss_dev, cudaStream_t s) {
-  MlpWs w;
-  cudaError_t e = loss_and_grad(d, q, t, rows, s, w);
+  float* batch_loss = nullptr;
+  cudaError_t e;
+  if (d->fp32) {
+    MlpWs<float> w;
+    e = loss_and_grad<float>(d, q, t, rows, s, w);
+    batch_loss = w.loss;
+  } else {
+    MlpWs<__nv_bfloat16> w;
+    e = loss_and_grad<__nv_bfloat16>(d, q, t, rows, s, w);
+    batch_loss = w.loss;
+  }
   if (e != cudaSuccess) return e;
   d->step++;
   for (int l = 0; l < kMlpLayers; ++l) {
@@ -791,7 +967,7 @@ cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, 
     }
     if (e != cudaSuccess) return e;
   }
-  if (loss_dev) e = launch_accumulate(loss_dev, w.loss, s);
+  if (loss_dev) e = launch_accumulate(loss_dev, batch_loss, s);
   return e;
 }
 

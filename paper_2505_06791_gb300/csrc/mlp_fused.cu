@@ -62,15 +62,18 @@ constexpr int kOffRing = 2 * kActBytes;
 constexpr int kOffBias = kOffRing + kStages * kStageBytes;
 constexpr int kOffBar = kOffBias + kBiasFloats * 4;  // 8-byte aligned
 // barriers: w_full[stages] w_empty[stages] acc_full[2] acc_empty[2] (per tile of the pair)
-// act_full[2][4] (per tile and 64-column block)
+// act_full[2][4] (per tile and 64-column block) drain (the MMA issuer's last commit)
 constexpr int kBarWFull = 0, kBarWEmpty = kStages, kBarAccFull = 2 * kStages;
 constexpr int kBarAccEmpty = kBarAccFull + 2, kBarAct = kBarAccEmpty + 2;
-constexpr int kNumBars = kBarAct + 8;
+constexpr int kBarDrain = kBarAct + 8;
+constexpr int kNumBars = kBarDrain + 1;
 constexpr int kOffTmem = kOffBar + kNumBars * 8;
 constexpr int kOffAbort = kOffTmem + 4;
 constexpr int kSmemUsed = kOffAbort + 4;
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s: every wait here is microseconds
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // default 1 s: every wait here is microseconds
 constexpr uint64_t kDrainLimitNs = 20000000ull;
+// this launch's limit of a bounded wait (set by thread 0 before the first barrier)
+__shared__ uint64_t s_wait_limit_ns;
 
 static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
 
@@ -143,7 +146,7 @@ __device__ __forceinline__ uint64_t now_ns() {
 }
 
 // Waits for the phase of `parity` to complete. Gives up (false) when another role raised
-// the abort flag, or after kWaitLimitNs, raising it.
+// the abort flag, or after the launch's wait limit, raising it.
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = now_ns();
@@ -151,7 +154,7 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     for (int i = 0; i < 32; ++i)
       if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (now_ns() - t0 > kWaitLimitNs) {
+    if (now_ns() - t0 > s_wait_limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -253,7 +256,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(FusedMlpArg
       mbar_init(bar(kBarAccEmpty + u), kGroupWarps);
     }
     for (int b = 0; b < 8; ++b) mbar_init(bar(kBarAct + b), kGroupWarps);
+    mbar_init(bar(kBarDrain), 1);
     *s_abort = 0;
+    s_wait_limit_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -338,7 +343,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(FusedMlpArg
           }
         }
       }
-      if (last_u >= 0) mbar_drain(bar(kBarAccFull + last_u), (((layers >> (16 * last_u)) & 0xffffu) - 1) & 1);
+      // every MMA this thread issued has completed before tensor memory is freed, also when
+      // it gave up in the middle of a slab (MMAs issued but not yet committed elsewhere): a
+      // commit tracks all of the thread's earlier tcgen05 operations
+      (void)last_u;
+      umma_commit(bar(kBarDrain));
+      mbar_drain(bar(kBarDrain), 0);
     }
   } else {
     // epilogue warps: group u serves tile u of each pair

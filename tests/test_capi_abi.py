@@ -116,6 +116,8 @@ def test_codes_agree_across_header_kernels_oracle_and_generators():
                  "UNSUPPORTED"):
         assert define("CPRRTC_E_" + name) == getattr(capi, "E_" + name), name
     assert define("CPRRTC_OK") == capi.OK == 0
+    assert define("CPRRTC_MLP_BF16") == capi.MLP_BF16 == 0
+    assert define("CPRRTC_MLP_FP32") == capi.MLP_FP32 == 1
     assert define("CPRRTC_MAX_DOF") == int(re.search(r"kMaxDof = (\d+)", dev).group(1)) == \
         int(re.search(r"ORC_MAX_DOF (\d+)", orc).group(1))
     assert define("CPRRTC_MAX_W") == int(re.search(r"kMaxW = (\d+)", dev).group(1)) == \

@@ -135,3 +135,58 @@ def test_batch_projection_matches_single(oracle_mod):
         np.testing.assert_array_equal(out[k], q1)
         assert res[k] == r1
     assert ok.mean() > 0.5
+
+
+def _bound_case(seed, rows, out_scale=0.3):
+    rng = np.random.default_rng(seed)
+    dims = [(256, 7), (256, 256), (256, 256), (7, 256)]
+    parts = []
+    for l, (o, i) in enumerate(dims):
+        s = np.sqrt(2.0 / i) * (out_scale if l == 3 else 1.0)
+        parts += [rng.normal(0, s, o * i), rng.normal(0, 0.05, o)]
+    p = np.concatenate(parts).astype(np.float32).astype(np.float64)
+    rb = S.make_arm7(1)
+    q = S.uniform_configs(rb, rows, seed + 1).astype(np.float32)
+    t = (q + rng.normal(0, 0.3, q.shape)).astype(np.float32)
+    return p, q, t
+
+
+def test_bound_helper_evaluation_is_the_oracle(oracle_mod):
+    """The FP64 re-evaluation the GPU tests size their tolerances with (tests/mlp_bounds.py)
+    computes the oracle's network: same corrections, loss and gradient."""
+    from tests import mlp_bounds as MB
+    p, q, t = _bound_case(5, 97)
+    ev = MB.evaluate(p, q, t)
+    np.testing.assert_allclose(ev["y"], oracle_mod.mlp_forward(p, q.astype(np.float64), 7, 256),
+                               rtol=1e-12, atol=1e-14)
+    loss, g = oracle_mod.mlp_loss_grad(p, q, t, 7, 256)
+    assert abs(ev["loss"] - loss) <= 1e-12 * loss
+    np.testing.assert_allclose(ev["grad"], g, rtol=1e-10, atol=1e-16)
+
+
+def test_bf16_tolerances_hold_for_emulated_bf16_arithmetic():
+    """The per-element tolerances (C = 8 standard deviations of the probabilistic rounding
+    model) hold for a CPU emulation of the GPU's BF16 arithmetic (BF16 storage of inputs,
+    activations and back-propagated signals; FP32 sums), for every element of the
+    correction and of every gradient tensor; and they are tight enough to catch a wrong
+    element: each is a small fraction of the element's magnitude scale, and the emulated
+    errors reach a sizeable part of them (the model is neither loose nor optimistic)."""
+    from tests import mlp_bounds as MB
+    p, q, t = _bound_case(7, 301)
+    p16 = p.copy()
+    # the GPU works with BF16 weights (biases FP32); so does the evaluation it is compared to
+    for (ws, _, _) in layer_slices(7, 256):
+        p16[ws] = MB.bf16_round(p[ws])
+    ev = MB.evaluate(p16, q, t)
+    fs = MB.forward_sigma(ev, MB.U_BF16, acc_factor=2.0)
+    gs = MB.gradient_sigma(ev, fs, MB.U_BF16)
+    y_em, g_em = MB.emulate_bf16(p16, q, t)
+    ry = np.abs(y_em - ev["y"]) / fs["y"]
+    rg = np.abs(g_em - ev["grad"]) / gs
+    assert ry.max() < 8.0 and rg.max() < 8.0, (ry.max(), rg.max())
+    assert ry.max() > 1.0 and rg.max() > 1.0, (ry.max(), rg.max())
+    mag = MB.gradient_magnitude(ev)
+    used = mag > 0
+    assert np.max(8.0 * gs[used] / mag[used]) < 0.05
+    ymag = np.abs(ev["h"][2]) @ np.abs(ev["layers"][3][0]).T + np.abs(ev["layers"][3][1])
+    assert np.max(8.0 * fs["y"] / ymag) < 0.05
