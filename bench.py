@@ -177,6 +177,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # workloads
 
+VAL_SWEEP = (256, 4096, 65536)
+
+
 def validation_workload(seed=1):
     """7-DOF arm (59 spheres), 16 obstacle spheres in the 1.2 m cube, 256 motions x 32
     waypoints between uniform configurations, roll/pitch constraint, <= 20 iterations."""
@@ -350,12 +353,20 @@ def run_plan(args, world, rank, local):
                    "W": PLAN_PARAMS["W"], "max_rounds": PLAN_PARAMS["max_rounds"],
                    "workers_per_problem": PLAN_PARAMS["workers"],
                    "l2": "flushed (256 MB write) between steps",
+                   "recipe_departure": "obstacle centres in a 3 x 3 x 1.8 m workspace with a 0.35 m "
+                                       "keep-out around the base instead of the 1.2 m cube: with "
+                                       "200 obstacles the cube leaves no collision-free configuration",
                    "parallelism": f"replicas x{world}"},
         "p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
         "p95_plan_ms": float(np.percentile(ms[solved], 95)) if solved.any() else None,
         "p50_plan_ms_all": float(np.percentile(ms, 50)),
         "success_rate": float(solved.mean()),
         "waypoints_per_step": waypoints_step,
+        "evaluated_waypoints_per_s": sum_over_ranks(int(work[:, 1].sum()), world) * args.steps
+                                     / (total_ms / 1e3),
+        "evaluated_note": "waypoints of attempted motions that went through projection, FK and "
+                          "CC (motions that fail projection or collide early count only what "
+                          "was checked); `value` counts W per attempted motion",
         "mean_rounds": float(rounds.mean()),
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -672,6 +683,53 @@ def run_validate(args, world, rank, local):
     flops = executed_flops(rb.dof, counters)
     waypoints = n * W * args.steps * world
     value = waypoints / (total_ms / 1e3)
+    peaks = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, peak_note = fp32_peak(ctx, sm_count, peaks)
+
+    # throughput sweep of the same distribution at sizes that fill the GPU (256 motions are
+    # less than one wave of 152 SMs)
+    sweep = []
+    with torch.cuda.stream(stream):
+        for n_s in VAL_SWEEP:
+            a0 = manifold_starts_gpu(ctx, rb, n_s, 30_000 + 97 * rank)
+            a1 = torch.from_numpy(S.uniform_configs(rb, n_s, 40_000 + 97 * rank).astype(np.float32)).to(dev)
+            o_s = ctx.alloc_validate_outputs(n_s, W, a0)
+            for _ in range(args.warmup):
+                ctx.validate(a0, a1, W, out=o_s)
+            stream.synchronize()
+            ctx.set_timing(True)
+            ctx.reset_timing()
+            ctx.work_counters(reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.validate(a0, a1, W, out=o_s)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            ms_s = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), world)
+            k_ms, k_n = ctx.kernel_time("validate")
+            cnt = ctx.work_counters() / max(args.steps, 1)
+            ctx.set_timing(False)
+            st_s = o_s["status"].cpu().numpy()
+            ff_s = o_s["first_fail"].cpu().numpy()
+            it_s = o_s["iters"].cpu().numpy()
+            _, cc_s = algorithmic_flops(rb.dof, W, len(rb.spheres),
+                                        (len(sc.sph), len(sc.box), len(sc.cap)), st_s, ff_s, it_s)
+            k_s = k_ms / 1e3 / max(k_n, 1)
+            ach = executed_flops(rb.dof, cnt) / k_s / 1e12
+            sweep.append({"motions": n_s, "value": n_s * W * args.steps * world / (ms_s / 1e3),
+                          "ms_per_step": ms_s / args.steps,
+                          "evaluated_waypoints_per_s": cc_s * args.steps * world / (ms_s / 1e3),
+                          "validate_kernel_ms": k_s * 1e3, "achieved_tflops": ach,
+                          "frac": ach / peak, "mean_iters": float(it_s.mean()),
+                          "proj_fail": int((st_s == 1).sum()), "collision": int((st_s == 2).sum())})
+            del a0, a1, o_s
 
     # end to end through the C ABI with pinned host buffers
     h_q0 = q0.cpu().pin_memory()
@@ -688,9 +746,6 @@ def run_validate(args, world, rank, local):
     e2e = {"value": n * W * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
-    peaks = load_peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak, peak_note = fp32_peak(ctx, sm_count, peaks)
     avg_kernel_s = kms / 1e3 / max(launches, 1)
     achieved = flops / avg_kernel_s / 1e12
     line = {
@@ -705,6 +760,11 @@ def run_validate(args, world, rank, local):
         "outcomes": {"valid": int((st == 0).sum()), "proj_fail": int((st == 1).sum()),
                      "collision": int((st == 2).sum()), "mean_iters": float(it.mean()),
                      "cc_waypoints": cc_wp},
+        "evaluated_waypoints_per_s": cc_wp * args.steps * world / (total_ms / 1e3),
+        "evaluated_note": "waypoints that went through projection, FK and CC: all W of a valid "
+                          "motion, up to the first colliding one of a colliding motion, none of "
+                          "a motion that failed projection",
+        "sweep": sweep,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
@@ -907,9 +967,22 @@ def point_cloud_workload(seed=3):
     return S.make_arm8(1), S.make_box_surface_cloud(seed), S.z_plane(0.9)
 
 
+def near_ends(q0, rb, half_width, seed):
+    """Planner-like motion ends: each start moved by U[-w, w] per joint, clipped to the limits."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    d = (torch.rand(q0.shape, generator=g) * 2 - 1) * half_width
+    lo = torch.tensor(rb.lo, dtype=torch.float32)
+    hi = torch.tensor(rb.hi, dtype=torch.float32)
+    return torch.maximum(torch.minimum(q0.cpu() + d, hi), lo).to(q0.device).contiguous()
+
+
 def run_gemmcc(args, world, rank, local):
     """Validation of 4096 motions x 64 waypoints with the exact collision check and with the
-    GEMM form (TF32 and BF16 contraction + exact recheck); outputs compared across modes."""
+    GEMM form (TF32 and BF16 contraction + exact recheck); outputs compared across modes.
+    Two motion sets on the same scene: ends uniform in the joint limits (the configuration;
+    most motions fail the projection before any collision check), and planner-like ends
+    within 0.3 rad of the start (most motions reach the collision check)."""
     import torch
     from paper_2505_06791_gb300 import build
     from paper_2505_06791_gb300.capi import Context
@@ -925,13 +998,11 @@ def run_gemmcc(args, world, rank, local):
     ctx.set_constraint(c)
     peaks = load_peaks()
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-    modes = {}
-    with torch.cuda.stream(stream):
-        q0 = manifold_starts_gpu(ctx, rb, n, 70_000 + 97 * rank)
-        q1 = torch.from_numpy(S.uniform_configs(rb, n, 80_000 + 97 * rank).astype(np.float32)).to(dev)
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        clocks = ClockSampler(local)
-        clocks.start()
+    n_obs, n_rs = len(sc.sph), len(rb.spheres)
+    n_tiles = (n_obs + 255) // 256
+
+    def measure(q0, q1, flush):
+        modes = {}
         for name, mode in (("exact", 0), ("gemm_tf32", 1), ("gemm_bf16", 2)):
             ctx.set_cc_mode(mode, 0.005)
             out = ctx.alloc_validate_outputs(n, W, q0)
@@ -959,50 +1030,77 @@ def run_gemmcc(args, world, rank, local):
             bound, rechecks = ctx.cc_stats(reset=True)
             modes[name] = dict(ms=ms, kv=kv, kg=kg, bound=bound, rechecks=rechecks / max(args.steps, 1),
                                out={k: v.cpu().numpy() for k, v in out.items()})
-        clk = clocks.stop()
         ctx.set_cc_mode(0)
-    ex = modes["exact"]["out"]
-    st, ff = ex["status"], ex["first_fail"]
-    # waypoint tiles the GEMM form evaluates: every waypoint of a collision-free projected
-    # motion, and up to the first colliding waypoint + 1 of a colliding one
-    tiles = int(np.where(st == 0, W, np.where(st == 2, np.minimum(ff + 2, W), 0)).sum())
-    n_tiles = (len(sc.sph) + 255) // 256
-    tensor_flop = tiles * 128 * n_tiles * 256 * 2 * 16
-    wps = n * W * args.steps * world
-    summary = {}
-    for name, m in modes.items():
-        o = m["out"]
-        same = bool(np.array_equal(o["status"], st) and np.array_equal(o["first_fail"], ff)
-                    and np.array_equal(o["q"], ex["q"]))
-        entry = {"value": wps / (m["ms"] / 1e3), "ms_per_step": m["ms"] / args.steps,
-                 "validate_kernel_ms": m["kv"][0] / max(m["kv"][1], 1), "identical_to_exact": same}
-        if name != "exact":
-            g_ms = m["kg"][0] / max(m["kg"][1], 1)
-            peak = bf16_peak if name == "gemm_bf16" else bf16_peak / 2.0
-            entry.update({"gemm_cc_kernel_ms": g_ms, "error_bound_m2": m["bound"],
-                          "exact_rechecks_per_step": m["rechecks"],
-                          "tensor_tflops": tensor_flop / (g_ms / 1e3) / 1e12,
-                          "tensor_peak_tflops": peak,
-                          "peak_note": "BF16 measured (MEASURED_PEAKS.json bf16_tflops); TF32 = "
-                                       "BF16 x 0.5 (nominal dense ratio)" if name == "gemm_tf32"
-                                       else "BF16 measured (MEASURED_PEAKS.json bf16_tflops)"})
-        summary[name] = entry
+        ex = modes["exact"]["out"]
+        st, ff = ex["status"], ex["first_fail"]
+        # waypoint tiles the GEMM form evaluates: every waypoint of a collision-free projected
+        # motion, and up to the first colliding waypoint + 1 of a colliding one
+        tiles = int(np.where(st == 0, W, np.where(st == 2, np.minimum(ff + 2, W), 0)).sum())
+        # algorithmic work: 16 FLOP per (robot sphere, obstacle) pair of an evaluated
+        # waypoint (the distance as an 8-term augmented dot product, 2 x 8); the MMAs as
+        # issued (128 padded rows, 256-column tiles, K = 16 hi/lo-split terms) are counted
+        # separately
+        tensor_flop = tiles * n_rs * n_obs * 16
+        issued_flop = tiles * 128 * n_tiles * 256 * 2 * 16
+        wps = n * W * args.steps * world
+        summary = {}
+        for name, m in modes.items():
+            o = m["out"]
+            same = bool(np.array_equal(o["status"], st) and np.array_equal(o["first_fail"], ff)
+                        and np.array_equal(o["q"], ex["q"]))
+            entry = {"value": wps / (m["ms"] / 1e3), "ms_per_step": m["ms"] / args.steps,
+                     "evaluated_waypoints_per_s": tiles * args.steps * world / (m["ms"] / 1e3),
+                     "validate_kernel_ms": m["kv"][0] / max(m["kv"][1], 1), "identical_to_exact": same}
+            if name != "exact":
+                g_ms = m["kg"][0] / max(m["kg"][1], 1)
+                peak = bf16_peak if name == "gemm_bf16" else bf16_peak / 2.0
+                entry.update({"gemm_cc_kernel_ms": g_ms, "error_bound_m2": m["bound"],
+                              "exact_rechecks_per_step": m["rechecks"],
+                              "tensor_tflops": tensor_flop / (g_ms / 1e3) / 1e12,
+                              "issued_mma_tflops": issued_flop / (g_ms / 1e3) / 1e12,
+                              "tensor_peak_tflops": peak,
+                              "peak_note": "BF16 measured (MEASURED_PEAKS.json bf16_tflops); TF32 = "
+                                           "BF16 x 0.5 (nominal dense ratio)" if name == "gemm_tf32"
+                                           else "BF16 measured (MEASURED_PEAKS.json bf16_tflops)"})
+            summary[name] = entry
+        outcomes = {"valid": int((st == 0).sum()), "proj_fail": int((st == 1).sum()),
+                    "collision": int((st == 2).sum()), "gemm_waypoint_tiles": tiles}
+        return summary, outcomes, tensor_flop, issued_flop, tiles
+
+    with torch.cuda.stream(stream):
+        q0 = manifold_starts_gpu(ctx, rb, n, 70_000 + 97 * rank)
+        q1 = torch.from_numpy(S.uniform_configs(rb, n, 80_000 + 97 * rank).astype(np.float32)).to(dev)
+        q1n = near_ends(q0, rb, 0.3, 81_000 + 97 * rank)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        clocks = ClockSampler(local)
+        clocks.start()
+        summary, outcomes, tensor_flop, issued_flop, tiles = measure(q0, q1, flush)
+        near_summary, near_outcomes, near_flop, near_issued, near_tiles = measure(q0, q1n, flush)
+        clk = clocks.stop()
     best = max(("gemm_tf32", "gemm_bf16"), key=lambda k: summary[k]["value"])
     gcc_tile_bytes = profiled_traffic_per_unit("gemm_cc_kernel_point_cloud_4096.md", "traffic_per_waypoint_tile_bytes")
     b = summary[best]
+    nb = near_summary["gemm_bf16"]
     line = {
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": f"{best[5:]} contraction, f32 recheck",
         "data": "synthetic",
         "config": {"workload": "obstacle-rich scene, collision check in GEMM form: 8-DOF arm, point-cloud sphere obstacles, z-plane",
-                   "motions": n, "W": W, "dof": rb.dof, "robot_spheres": len(rb.spheres),
-                   "obstacles": {"spheres": len(sc.sph), "radius": 0.02},
-                   "constraint": "z-plane 0.9 m", "guard_m": 0.005,
+                   "motions": n, "W": W, "dof": rb.dof, "robot_spheres": n_rs,
+                   "obstacles": {"spheres": n_obs, "radius": 0.02},
+                   "constraint": "z-plane 0.9 m", "guard_m": 0.005, "motion_ends": "uniform in the joint limits",
                    "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas x{world}"},
         "modes": summary,
-        "outcomes": {"valid": int((st == 0).sum()), "proj_fail": int((st == 1).sum()),
-                     "collision": int((st == 2).sum()), "gemm_waypoint_tiles": tiles},
+        "outcomes": outcomes,
+        "planner_like": {"motion_ends": "start + U[-0.3, 0.3] rad per joint, clipped",
+                         "modes": near_summary, "outcomes": near_outcomes,
+                         "roofline_bf16": {"bound": "tensor", "achieved": nb["tensor_tflops"],
+                                           "peak": nb["tensor_peak_tflops"], "unit": "TFLOP/s",
+                                           "frac": nb["tensor_tflops"] / nb["tensor_peak_tflops"],
+                                           "flop_per_launch": near_flop,
+                                           "issued_mma_flop_per_launch": near_issued,
+                                           "avg_launch_ms": nb["gemm_cc_kernel_ms"]}},
         "roofline": {"bound": "tensor", "achieved": b["tensor_tflops"], "peak": b["tensor_peak_tflops"],
                      "unit": "TFLOP/s", "frac": b["tensor_tflops"] / b["tensor_peak_tflops"],
                      "traffic": (None if gcc_tile_bytes is None or best != "gemm_bf16"
@@ -1010,7 +1108,10 @@ def run_gemmcc(args, world, rank, local):
                      "traffic_note": "ncu DRAM bytes per waypoint tile of a 512-motion BF16 capture "
                                      "(profiles/gemm_cc_kernel_point_cloud_4096.md) x waypoint tiles",
                      "kernel": "gemm_cc_kernel",
-                     "flop_per_launch": tensor_flop, "avg_launch_ms": b["gemm_cc_kernel_ms"]},
+                     "flop_per_launch": tensor_flop,
+                     "flop_note": "16 FLOP per (robot sphere, obstacle) pair of each evaluated waypoint",
+                     "issued_mma_flop_per_launch": issued_flop,
+                     "avg_launch_ms": b["gemm_cc_kernel_ms"]},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
     }

@@ -82,16 +82,17 @@ def oracle_view(p32, wmask):
 
 def check_elementwise(got, want, sigma, what, extra=0.0):
     """Every element within C_SIGMA * sigma (+ extra); reports the worst element."""
-    tol = C_SIGMA * sigma + extra
+    got, want = np.ravel(got), np.ravel(want)
+    tol = np.ravel(C_SIGMA * np.asarray(sigma) + extra)
     ratio = np.abs(got - want) / np.maximum(tol, 1e-300)
     k = int(np.argmax(ratio))
-    assert ratio[k] <= 1.0, (what, k, float(got.ravel()[k]), float(want.ravel()[k]),
-                             float(tol.ravel()[k]))
+    assert ratio[k] <= 1.0, (what, k, float(got[k]), float(want[k]), float(tol[k]))
     return float(ratio.max())
 
 
 def check_rel_fp32(got, want, mag, what):
     """The FP32 mode's 1e-4 relative agreement (see REL_FP32)."""
+    got, want, mag = np.ravel(got), np.ravel(want), np.ravel(mag)
     d = np.abs(got - want)
     assert np.all(d <= REL_FP32 * mag + 1e-30), (what, float(np.max(d / np.maximum(mag, 1e-300))))
     mild = np.abs(want) >= 0.1 * mag
