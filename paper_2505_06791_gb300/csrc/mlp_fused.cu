@@ -301,7 +301,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(FusedMlpArg
       uint32_t use = 0;
       uint32_t layers = 0;  // layers issued per tile slot u, 16-bit field u
       uint32_t act_par = 0;            // bit 4u + b: parity of the next phase of block b of tile u
-      int last_u = -1;
       bool ok = true;
       for (int p = blockIdx.x; ok && p < pairs; p += gridDim.x) {
         const int nt = (2 * p + 1 < tiles) ? 2 : 1;
@@ -339,14 +338,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) mlp_fused_kernel(FusedMlpArg
             if (!ok) break;
             umma_commit(bar(kBarAccFull + u));
             layers += 1u << (16 * u);
-            last_u = u;
           }
         }
       }
       // every MMA this thread issued has completed before tensor memory is freed, also when
       // it gave up in the middle of a slab (MMAs issued but not yet committed elsewhere): a
       // commit tracks all of the thread's earlier tcgen05 operations
-      (void)last_u;
       umma_commit(bar(kBarDrain));
       mbar_drain(bar(kBarDrain), 0);
     }
