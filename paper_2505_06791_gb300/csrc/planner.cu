@@ -474,6 +474,9 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
 struct PoolWorker {
   int mode, ta, last, target, steps;  // chain state (plan_problem keeps it in registers)
   int add, conn;                      // outcome of this round's motion
+  // the worker's node appended by the last commit whose motion still waits in the worker's
+  // scratch (-1: none): the worker's next task moves it to the tree's edge array
+  int pdst, pta;
   unsigned wp, wproj, wcc;            // waypoints validated, Alg. 1 updates, CC waypoints
   float cfg[4][8];                    // current chain node, target, motion end, scratch
 };
@@ -522,6 +525,7 @@ __device__ void pool_load(const RobotDev& rb, const SceneDev& shared_scene, cons
   }
   if (a.stage_obs) {
     const int n4 = sc.n_float4();
+#pragma unroll 4
     for (int i = lane; i < n4; i += 32) s_obs[i] = sc.obs[i];
   }
   const size_t wd = (size_t)W * dof;
@@ -535,7 +539,7 @@ __device__ void pool_load(const RobotDev& rb, const SceneDev& shared_scene, cons
   for (int w = lane; w < B; w += 32) {
     PoolWorker& k = sl.w[w];
     k.mode = 0; k.ta = 0; k.last = 0; k.target = -1; k.steps = 0;
-    k.add = 0; k.conn = 0; k.wp = 0u; k.wproj = 0u; k.wcc = 0u;
+    k.add = 0; k.conn = 0; k.pdst = -1; k.pta = 0; k.wp = 0u; k.wproj = 0u; k.wcc = 0u;
   }
   if (lane == 0) {
     parent[0] = -1;
@@ -579,8 +583,11 @@ __device__ __forceinline__ void pool_task(const RobotDev& rb, const ConsDev& cs,
                                           const CcShared& S, WorkCount& wc) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof, W = a.W, MN = a.max_nodes;
-  const ProblemView& P = sl.pv;
-  const int p = P.p, r = sl.round;
+  // the slot's fields in registers: the collision walk reads the scene in its inner loops
+  const SceneDev sc = sl.sc;
+  const int p = sl.pv.p, r = sl.round;
+  float* const tree_nodes = sl.pv.nodes;
+  float* const wedge = sl.pv.pend_edges + (size_t)w * 2 * W * dof;
   const int cnt0 = sl.cnt[0], cnt1 = sl.cnt[1];
   auto count_of = [&](int t) { return t ? cnt1 : cnt0; };
   PoolWorker& k = sl.w[w];
@@ -591,7 +598,16 @@ __device__ __forceinline__ void pool_task(const RobotDev& rb, const ConsDev& cs,
   float* q1 = k.cfg[2];
   float* qe = k.cfg[3];
   const size_t wd = (size_t)W * dof;
-  auto nodes = [&](int t) { return P.nodes + (size_t)t * MN * 8; };
+  auto nodes = [&](int t) { return tree_nodes + (size_t)t * MN * 8; };
+  // the motion of this worker's node appended at the last commit: scratch -> tree, before
+  // this task overwrites the scratch
+  if (k.pdst >= 0) {
+    float* dst = sl.pv.edges + ((size_t)k.pta * MN + k.pdst) * wd;
+#pragma unroll 4
+    for (int i = lane; i < (int)wd; i += 32) dst[i] = wedge[i];
+    __syncwarp();
+    if (lane == 0) k.pdst = -1;
+  }
   if (mode == 0) {
     ta = (r + w) & 1;
     const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)w, 0u}, a.seed, 0u);
@@ -615,10 +631,9 @@ __device__ __forceinline__ void pool_task(const RobotDev& rb, const ConsDev& cs,
   float q[WPL][kMaxDof];
   MotionWork work{0u, 0u};
   // the closing hop is checked as it stands: one Alg. 1 iteration
-  const int st = validate_motion<CT, WPL, SEQ>(rb, sl.sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs,
+  const int st = validate_motion<CT, WPL, SEQ>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs,
                                                S, cur, q1, W, q);
   int add = 0, conn = 0;
-  float* wedge = P.pend_edges + (size_t)w * 2 * wd;
   if (st == kValid) {
     if (mode == 2) {
       conn = 1;
@@ -746,8 +761,9 @@ __device__ void pool_commit(const RobotDev& rb, const SceneDev& shared_scene, co
     pool_finish(rb, shared_scene, a, sl, true, r + 1, s_obs);
     return;
   }
-  const size_t wd = (size_t)W * dof;
   const float connect_radius = 10.f * cs.tau_floor;
+  float* const tree_nodes = P.nodes;
+  int* const tree_parent = P.parent;
   int n0 = sl.cnt[0], n1 = sl.cnt[1];  // running tree sizes: nodes go in worker order
   for (int w = 0; w < B; ++w) {
     PoolWorker& k = sl.w[w];
@@ -756,12 +772,16 @@ __device__ void pool_commit(const RobotDev& rb, const SceneDev& shared_scene, co
       const int t = k.ta;
       dst = t ? n1++ : n0++;
       if (dst < MN) {
-        float* nd = P.nodes + ((size_t)t * MN + dst) * 8;
+        // the node and its parent now; its motion stays in the worker's scratch until the
+        // worker's next task moves it (every worker has a task in every round, and a path is
+        // read only after a round in which all of them ran)
+        float* nd = tree_nodes + ((size_t)t * MN + dst) * 8;
         if (lane < 8) nd[lane] = k.cfg[3][lane];
-        const float* __restrict__ src = P.pend_edges + (size_t)w * 2 * wd;
-        float* __restrict__ e = P.edges + ((size_t)t * MN + dst) * wd;
-        for (int i = lane; i < (int)wd; i += 32) e[i] = src[i];
-        if (lane == 0) P.parent[(size_t)t * MN + dst] = k.last;
+        if (lane == 0) {
+          tree_parent[(size_t)t * MN + dst] = k.last;
+          k.pdst = dst;
+          k.pta = t;
+        }
       } else {
         dst = -1;
       }
@@ -816,7 +836,7 @@ __device__ void pool_commit(const RobotDev& rb, const SceneDev& shared_scene, co
   }
   // the round's appends and the chains before the next round's tasks can be claimed
   __syncwarp();
-  __threadfence();
+  __threadfence_block();
   if (lane == 0) atomicExch(&sl.next_task, 0);
   __syncwarp();
 }
@@ -964,7 +984,8 @@ __global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTabl
       for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = s_sc.obs[i];
     stage_robot(rb, smem, L);
     __syncthreads();
-    plan_problem<CT, WPL>(rb, s_sc, a.stage_obs ? s_obs : s_sc.obs, cs, a, sh->pv, S, sh, wc);
+    const SceneDev sc = s_sc;  // in registers: the collision walk reads it in its inner loops
+    plan_problem<CT, WPL>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc);
   }
   wc.flush(a.work_counters);
 }
