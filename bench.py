@@ -251,10 +251,6 @@ def gpu_start_goal(rb, c, scenes, seed, device):
     return torch.stack(starts).contiguous(), torch.stack(goals).contiguous()
 
 
-def waypoints_step_of(out):
-    return int(out["waypoints"].sum().item())
-
-
 def plan_flops(dof, scenes, n_spheres, work):
     work = np.asarray(work, dtype=np.float64)
     f_iter = flops_waypoint_iter(dof)
@@ -311,37 +307,12 @@ def run_plan(args, world, rank, local):
         counters = ctx.work_counters() / max(args.steps, 1)
         ctx.set_timing(False)
     total_ms = max_over_ranks(sum(step_ms), world)
-    shape = ctx.plan_schedule()
     L = out["path_len"].cpu().numpy()
     wp = out["waypoints"].cpu().numpy()
     ms = out["plan_ms"].cpu().numpy()
     work = out["work"].cpu().numpy()
     rounds = out["rounds"].cpu().numpy()
 
-    # the same problems with the round-barrier schedule (one problem per CTA, one warp per
-    # worker, every warp waits for the round's slowest motion): same results, its time beside
-    with torch.cuda.stream(stream):
-        ctx.set_plan_schedule(PLAN_PARAMS["workers"], 1)
-        out_rb = ctx.alloc_plan_outputs(n, prm, start, edges=False)
-        ctx.plan(start, goal, prm, out=out_rb)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        barrier(world)
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            ctx.plan(start, goal, prm, out=out_rb)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        rb_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), world)
-        same_rb = all(bool(torch.equal(out[k], out_rb[k])) for k in ("path_len", "rounds", "waypoints", "work"))
-        ctx.set_plan_schedule(0, 0)
-    round_barrier = {"ms_per_step": rb_ms / args.steps,
-                     "value": sum_over_ranks(waypoints_step_of(out_rb), world) * args.steps / (rb_ms / 1e3),
-                     "identical_results": same_rb,
-                     "shape": {"warps_per_cta": PLAN_PARAMS["workers"], "problems_per_cta": 1}}
     waypoints_step = int(wp.sum())
     value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     nominal = plan_flops(rb.dof, scenes, len(rb.spheres), work)
@@ -398,10 +369,6 @@ def run_plan(args, world, rank, local):
                           "CC (motions that fail projection or collide early count only what "
                           "was checked); `value` counts W per attempted motion",
         "mean_rounds": float(rounds.mean()),
-        "schedule": {"warps_per_cta": shape[0], "problems_per_cta": shape[1], "ctas": shape[2],
-                     "note": "pooled: a CTA holds several problems and any warp takes any held "
-                             "problem's next motion; the round's last finisher commits it"},
-        "round_barrier_schedule": round_barrier,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "plan_kernel",

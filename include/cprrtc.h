@@ -338,7 +338,9 @@ typedef struct {
   double range;        /* steering step, L2 in joint space; default 0.3 */
   int W;               /* waypoints per motion, 2..64; default 32 */
   int max_rounds;      /* rounds per problem (>= 1); default 200 */
-  int workers;         /* extensions per round, 1..16; default 8 */
+  int workers;         /* extensions per round = warps per problem, 1..16 (fewer for
+                          W > 32, where the kernel's registers bound the CTA size: more is
+                          E_UNSUPPORTED); default 8 */
   int max_nodes;       /* capacity of each tree (>= 2); default 2048 */
   int max_connect;     /* greedy connect steps per extension (>= 0); default 32 */
   int max_path;        /* capacity of the path outputs, in nodes (>= 2); default 512 */
@@ -360,37 +362,17 @@ typedef struct {
  *              nodes j and j+1, waypoint 0 at node j (rows of path and path_edges
  *              beyond path_len are not written);
  *   rounds     [n] rounds run; waypoints [n] waypoints validated (W per motion checked);
- *   plan_ms    [n] device time from the problem's start to its end, ms;
+ *   plan_ms    [n] device time of the problem's CTA, ms;
  *   work       [n][2] work evaluated: Alg. 1 waypoint updates (iterations x (W-1) summed
  *              over motions) and waypoints collision-checked (early exit included).
  * The library keeps the trees in its own device memory (about
  * n * 2 * max_nodes * (W * dof + 9) * 4 bytes). Requires set_robot, and set_obstacles or
- * set_scene_batch (n_scenes = n).
- * Execution: a persistent kernel whose CTAs each hold several problems at once and whose
- * warps take any held problem's next unvalidated motion; the warp that finishes a round's
- * last motion commits that round (see cprrtc_set_plan_schedule). Results do not depend on
- * the schedule. Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_UNSUPPORTED, E_CUDA, E_OOM,
- * E_TIMEOUT (synchronous calls: a warp waited more than 1 s for work; outputs invalid). */
+ * set_scene_batch (n_scenes = n). Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_UNSUPPORTED,
+ * E_CUDA, E_OOM. */
 int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 const cprrtc_plan_params* params, int32_t* path_len, float* path,
                 float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
                 int64_t* work);
-
-/* Schedule of cprrtc_plan and cprrtc_plan_static (not in the paper, which runs one thread
- * block per extension, Sec. IV): each CTA has `warps_per_cta` warps (0: the most the kernel's
- * registers allow, at most 16) and holds `problems_per_cta` problems at once (0: automatic,
- * 3, or fewer when fewer problems than that fill the GPU; a given count is reduced only when
- * the problems' staged obstacles do not fit in shared memory). A round's motions are tasks
- * that any warp of the CTA may take, so a warp whose motion ended early validates another
- * held problem's motion instead of idling until the round's slowest motion ends. With
- * warps_per_cta = workers and problems_per_cta = 1 each problem has its own CTA and its warps
- * wait for the round's last motion, the round-barrier schedule. Results (paths, rounds,
- * waypoints, work) are the same for every schedule; only plan_ms changes.
- * Errors: E_INVALID_ARG (warps outside 0..16, problems outside 0..8). */
-int cprrtc_set_plan_schedule(cprrtc_ctx* ctx, int warps_per_cta, int problems_per_cta);
-/* Shape of the last planner launch: warps per CTA, problems held per CTA, CTAs (zeros before
- * any). Errors: E_INVALID_ARG (null argument). */
-int cprrtc_plan_schedule(cprrtc_ctx* ctx, int* warps_per_cta, int* problems_per_cta, int* ctas);
 
 /* ---- batches of uneven planning problems ---- */
 

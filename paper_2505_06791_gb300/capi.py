@@ -118,8 +118,6 @@ _SIGS = {
     "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
     "cprrtc_mlp_set_precision": [C.c_void_p, C.c_int],
     "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
-    "cprrtc_set_plan_schedule": [C.c_void_p, C.c_int, C.c_int],
-    "cprrtc_plan_schedule": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
@@ -387,18 +385,6 @@ class Context:
 
     def mlp_init(self, seed: int = 0):
         self._check(self._L.cprrtc_mlp_init(self.h, int(seed)))
-
-    def set_plan_schedule(self, warps_per_cta: int = 0, problems_per_cta: int = 0):
-        """Planner CTA shape: warps and problems held at once (0: the defaults)."""
-        self._check(self._L.cprrtc_set_plan_schedule(self.h, int(warps_per_cta),
-                                                     int(problems_per_cta)))
-
-    def plan_schedule(self):
-        """(warps per CTA, problems per CTA, CTAs) of the last planner launch."""
-        v = np.zeros(3, np.int32)
-        self._check(self._L.cprrtc_plan_schedule(self.h, v[0:].ctypes.data, v[1:].ctypes.data,
-                                                 v[2:].ctypes.data))
-        return tuple(int(x) for x in v)
 
     def set_wait_limit(self, seconds: float):
         """Limit of the tensor-core kernels' bounded waits (0: the default, 1 s)."""

@@ -100,9 +100,6 @@ struct cprrtc_ctx {
   MlpDev* mlp = nullptr;
   bool mlp_fp32 = false;    // the network's FP32 checking mode
   unsigned long long wait_ns = 0;  // bounded-wait limit of the tensor-core kernels (0: 1 s)
-  int plan_warps = 0;              // planner CTA: warps (0: the most, up to 16)
-  int plan_slots = 0;              // planner CTA: problems held at once (0: the default)
-  PlanShape last_plan_shape{};     // shape of the last planner launch
   float* d_warm = nullptr;  // corrections [n*W][16]
   size_t warm_cap = 0;      // bytes
   bool timing = false;
@@ -346,8 +343,8 @@ std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres)
   return idx;
 }
 
-// Planner configurations the kernels do not cover. Workers are tasks of a pool, not warps,
-// so any worker count up to kMaxWorkers runs whatever the kernel's registers allow per CTA.
+// The planner kernel's registers bound its CTA size: with two waypoints per lane (W > 32)
+// fewer than the maximum 16 workers fit.
 int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char* who) {
   if (ctx->self_on)
     return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": self-collision is checked by validate only");
@@ -355,35 +352,10 @@ int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char
   if (seq && (pp->W > 32 || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane)))
     return fail(ctx, CPRRTC_E_UNSUPPORTED,
                 std::string(who) + ": the sequential projection plans with ROLL_PITCH or Z_PLANE and W <= 32");
-  if (plan_max_warps(ctx->cs.type, pp->W, seq) < 1)
-    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": no planner kernel for this configuration");
-  return CPRRTC_OK;
-}
-
-// Launches the planner on `a` (trees and outputs set) with the context's schedule: the planner's
-// queue counter and error word live after the work counters.
-int run_planner(cprrtc_ctx* ctx, PlanArgs& a, const char* who) {
-  a.queue = reinterpret_cast<unsigned*>(ctx->d_work + kWorkCounters);
-  a.error = reinterpret_cast<int*>(ctx->d_work + kWorkCounters + 1);
-  const PlanShape shape = plan_shape(ctx->rb, ctx->cs, a, ctx->dev, ctx->plan_warps, ctx->plan_slots);
-  if (shape.grid < 1)
-    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": the planner kernel does not fit an SM");
-  cudaError_t e = cudaMemsetAsync(a.error, 0, sizeof(int), ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, who);
-  LaunchTimer tm(ctx, "plan");
-  e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, shape, ctx->stream);
-  tm.done();
-  if (e != cudaSuccess) return cuda_fail(ctx, e, who);
-  ctx->last_plan_shape = shape;
-  return CPRRTC_OK;
-}
-
-// After a synchronous planner call: a wait for work that ran out of time (E_TIMEOUT).
-int planner_status(cprrtc_ctx* ctx, const char* who) {
-  int flag = 0;
-  cudaError_t e = cudaMemcpy(&flag, ctx->d_work + kWorkCounters + 1, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, who);
-  if (flag) return fail(ctx, CPRRTC_E_TIMEOUT, std::string(who) + ": a wait of the planner timed out");
+  const int mw = plan_max_workers(ctx->cs.type, pp->W, seq);
+  if (pp->workers > mw)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": at most " + std::to_string(mw) +
+                                               " workers fit one CTA at W = " + std::to_string(pp->W));
   return CPRRTC_OK;
 }
 
@@ -523,10 +495,8 @@ int cprrtc_create(cprrtc_ctx** out, int device, void* stream) {
     return CPRRTC_E_CUDA;
   }
   ctx->dev.smem_optin = (size_t)smem;
-  // the work counters, then the planner's queue counter and error word (kept with them so
-  // that planning without allocation has them too)
-  if (cudaMalloc(&ctx->d_work, (kWorkCounters + 2) * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(ctx->d_work, 0, (kWorkCounters + 2) * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->d_work, kWorkCounters * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->d_work, 0, kWorkCounters * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(ctx->d_work);
     delete ctx;
@@ -1139,23 +1109,6 @@ int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed) {
   return CPRRTC_OK;
 }
 
-int cprrtc_set_plan_schedule(cprrtc_ctx* ctx, int warps_per_cta, int problems_per_cta) {
-  if (!ctx) return CPRRTC_E_INVALID_ARG;
-  if (warps_per_cta < 0 || warps_per_cta > kMaxWorkers || problems_per_cta < 0 || problems_per_cta > 8)
-    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_plan_schedule: warps 0..16, problems 0..8");
-  ctx->plan_warps = warps_per_cta;
-  ctx->plan_slots = problems_per_cta;
-  return CPRRTC_OK;
-}
-
-int cprrtc_plan_schedule(cprrtc_ctx* ctx, int* warps_per_cta, int* problems_per_cta, int* ctas) {
-  if (!ctx || !warps_per_cta || !problems_per_cta || !ctas) return CPRRTC_E_INVALID_ARG;
-  *warps_per_cta = ctx->last_plan_shape.warps;
-  *problems_per_cta = ctx->last_plan_shape.slots;
-  *ctas = ctx->last_plan_shape.grid;
-  return CPRRTC_OK;
-}
-
 int cprrtc_set_wait_limit(cprrtc_ctx* ctx, double seconds) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (!(seconds == 0.0 || (seconds >= 1e-6 && seconds <= 10.0)))
@@ -1536,11 +1489,11 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   st.output(reinterpret_cast<long long*>(work), N * 2 * sizeof(int64_t), &a.work);
   int rc = st.begin(ctx);
   if (rc) return rc;
-  rc = run_planner(ctx, a, "plan");
-  if (rc) return rc;
-  rc = st.end(ctx);
-  if (rc == CPRRTC_OK && st.any_host) rc = planner_status(ctx, "plan");
-  return rc;
+  LaunchTimer tm(ctx, "plan");
+  cudaError_t e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  tm.done();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
+  return st.end(ctx);
 }
 
 int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t* counters, int n,
@@ -1828,7 +1781,9 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   a.plan_ms = plan_ms;
   a.work = reinterpret_cast<long long*>(work);
   a.work_counters = ctx->d_work;  // allocated with the context: nothing is allocated here
-  return run_planner(ctx, a, "plan_static launch");
+  e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "plan_static launch");
+  return CPRRTC_OK;
 }
 
 

@@ -69,17 +69,6 @@ struct PlanArgs {
   long long* work;          // [n][2] Alg. 1 waypoint updates, collision-checked waypoints
   unsigned long long* work_counters;  // [6] executed-work totals (may be null)
   int stage_obs;            // set by the launcher
-  unsigned* queue;          // next problem of the planner's queue (zeroed by the launcher)
-  int* error;               // set to 1 when a wait for work exceeded its limit (may be null)
-};
-
-// Launch shape of the planner kernel (plan_shape); grid 0 when it cannot launch.
-struct PlanShape {
-  int warps;   // warps per CTA
-  int slots;   // problems a CTA holds at once
-  int grid;    // CTAs (persistent)
-  size_t smem;
-  bool stage;  // obstacles staged in shared memory
 };
 
 // Persistent batch of uneven planning problems (one launch).
@@ -113,16 +102,12 @@ int plan_batch_occupancy(int cls, int workers, size_t smem);
 cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
                               cudaStream_t stream);
 
-size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int warps, int slots, bool stage);
-// Most warps per CTA of the planner kernel for this constraint type and W (its registers per
-// thread bound the CTA size); 0 if there is no such kernel or the query fails.
-int plan_max_warps(int cons_type, int W, bool sequential = false);
-// Shape of a planner launch: `warps` per CTA (0: the most, up to 16) and `max_slots` problems
-// per CTA (0: automatic, at most 3).
-PlanShape plan_shape(const RobotDev& rb, const ConsDev& cs, const PlanArgs& a, const DeviceInfo& dev,
-                     int warps, int max_slots);
+size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
+// Most workers (warps per CTA) the planner kernel for this constraint type and W can launch
+// with (its registers per thread bound the CTA size); 0 if the query fails.
+int plan_max_workers(int cons_type, int W, bool sequential = false);
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
-                        const PlanShape& shape, cudaStream_t stream);
+                        const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
                           cudaStream_t stream);
 // Self-collision after validation (self_collide.cu): motions that are valid or collide

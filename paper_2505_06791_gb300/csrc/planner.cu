@@ -457,64 +457,13 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   }
 }
 
-// ---- pooled scheduling: many problems per CTA, no round barrier ---------------------------
-//
-// The round-synchronous search of plan_problem with the round barrier replaced by a task pool.
-// A persistent CTA of NW warps holds up to P problems (slots); a round of a slot is its B
-// tasks, one motion per worker. A warp claims any slot's next unclaimed task, validates that
-// motion and records the worker's outcome in shared memory (an accepted motion's waypoints go
-// to the worker's global scratch); the warp that finishes a round's last task commits the
-// round exactly as plan_problem does after its barrier (the lowest connecting worker wins,
-// accepted nodes are appended in worker order, chains advance) and opens the next round, or,
-// when the problem is done, writes its outputs and loads the next problem from a global
-// queue. A warp whose motion finished early takes another slot's motion instead of waiting for
-// the slowest motion of its round, and each problem's samples, trees and outputs are those of
-// plan_problem.
-
-struct PoolWorker {
-  int mode, ta, last, target, steps;  // chain state (plan_problem keeps it in registers)
-  int add, conn;                      // outcome of this round's motion
-  // the worker's node appended by the last commit whose motion still waits in the worker's
-  // scratch (-1: none): the worker's next task moves it to the tree's edge array
-  int pdst, pta;
-  unsigned wp, wproj, wcc;            // waypoints validated, Alg. 1 updates, CC waypoints
-  float cfg[4][8];                    // current chain node, target, motion end, scratch
-};
-
-struct PoolSlot {
-  ProblemView pv;
-  SceneDev sc;
-  long long t_start;
-  int active;     // 1 while the slot holds a problem; 0 once the queue had none left for it
-  int round;
-  int cnt[2];     // tree sizes when the round began
-  int next_task;  // tasks of the round claimed so far (>= workers: none to claim)
-  int done;       // tasks of the round finished
-  PoolWorker w[kMaxWorkers];
-};
-
-struct PoolShared {
-  int abort;  // a wait for work exceeded its limit: every warp stops
-};
-
-constexpr unsigned long long kPoolIdleNs = 1000000000ull;  // longest wait for a task: 1 s
-
-__device__ __forceinline__ int vload(const int& x) { return *reinterpret_cast<const volatile int*>(&x); }
-
-// Loads the next problem of the global queue into slot `sl` (one warp). With none left the slot
-// is retired (active = 0).
-__device__ void pool_load(const RobotDev& rb, const SceneDev& shared_scene, const PlanArgs& a,
-                          PoolSlot& sl, float4* s_obs) {
-  const int lane = threadIdx.x & 31;
-  const int dof = rb.dof, W = a.W, B = a.workers;
-  int p = 0;
-  if (lane == 0) p = (int)atomicAdd(a.queue, 1u);
-  p = __shfl_sync(kFull, p, 0);
-  if (p >= a.n) {
-    if (lane == 0) *reinterpret_cast<volatile int*>(&sl.active) = 0;
-    __syncwarp();
-    return;
-  }
+template <int CT, int WPL, bool SEQ = false>
+__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
+                                             PlanArgs a) {
+  const int p = blockIdx.x;
+  if (p >= a.n) return;
+  const int warp = threadIdx.x >> 5;
+  const int B = a.workers, dof = rb.dof, W = a.W;
   SceneDev sc = shared_scene;
   if (a.scenes) {
     const int4 d = a.scenes[p];
@@ -523,34 +472,27 @@ __device__ void pool_load(const RobotDev& rb, const SceneDev& shared_scene, cons
     sc.n_box = d.z;
     sc.n_cap = d.w;
   }
-  if (a.stage_obs) {
-    const int n4 = sc.n_float4();
-#pragma unroll 4
-    for (int i = lane; i < n4; i += 32) s_obs[i] = sc.obs[i];
-  }
+  extern __shared__ __align__(16) char smem[];
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, W, B, sizeof(PlanShared));
+  const int n4 = sc.n_float4();
+  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
+  if (a.stage_obs)
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
+  stage_robot(rb, smem, L);
+  const float4* obs = a.stage_obs ? s_obs : sc.obs;
+  const CcShared S = cc_shared(smem, L, warp);
+  PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
   const size_t wd = (size_t)W * dof;
-  const size_t tree0 = (size_t)p * 2 * a.max_nodes;
-  float* nodes = a.nodes + tree0 * 8;
-  int* parent = a.parent + tree0;
-  if (lane < 8) {
-    nodes[lane] = lane < dof ? a.start[(size_t)p * dof + lane] : 0.f;
-    nodes[(size_t)a.max_nodes * 8 + lane] = lane < dof ? a.goal[(size_t)p * dof + lane] : 0.f;
-  }
-  for (int w = lane; w < B; w += 32) {
-    PoolWorker& k = sl.w[w];
-    k.mode = 0; k.ta = 0; k.last = 0; k.target = -1; k.steps = 0;
-    k.add = 0; k.conn = 0; k.pdst = -1; k.pta = 0; k.wp = 0u; k.wproj = 0u; k.wcc = 0u;
-  }
-  if (lane == 0) {
-    parent[0] = -1;
-    parent[a.max_nodes] = -1;
-    ProblemView& P = sl.pv;
+  const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
+  if (threadIdx.x == 0) {
+    ProblemView& P = sh->pv;
     P.p = p;
     P.start = a.start + (size_t)p * dof;
     P.goal = a.goal + (size_t)p * dof;
     P.W = W;
-    P.nodes = nodes;
-    P.parent = parent;
+    P.nodes = a.nodes + tree0 * 8;
+    P.parent = a.parent + tree0;
     P.edges = a.edges + tree0 * wd;
     P.pend = a.pend + (size_t)p * B * 8;
     P.pend_edges = a.pend_edges + (size_t)p * B * 2 * wd;
@@ -558,368 +500,9 @@ __device__ void pool_load(const RobotDev& rb, const SceneDev& shared_scene, cons
     P.path_edges = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
     P.ostride = dof;
     P.estride = (int)wd;
-    sl.sc = sc;
-    sl.round = 0;
-    sl.cnt[0] = 1;
-    sl.cnt[1] = 1;
-    sl.done = 0;
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    sl.t_start = t;
-    sl.active = 1;
   }
-  // the slot's state, trees and staged obstacles before any warp can claim a task
-  __syncwarp();
-  __threadfence_block();
-  if (lane == 0) atomicExch(&sl.next_task, 0);
-  __syncwarp();
-}
-
-// One task: worker w's motion of the slot's current round (plan_problem's loop body up to its
-// barrier, with the chain state in shared memory).
-template <int CT, int WPL, bool SEQ>
-__device__ __forceinline__ void pool_task(const RobotDev& rb, const ConsDev& cs, const PlanArgs& a,
-                                          PoolSlot& sl, int w, const float4* obs,
-                                          const CcShared& S, WorkCount& wc) {
-  const int lane = threadIdx.x & 31;
-  const int dof = rb.dof, W = a.W, MN = a.max_nodes;
-  // the slot's fields in registers: the collision walk reads the scene in its inner loops
-  const SceneDev sc = sl.sc;
-  const int p = sl.pv.p, r = sl.round;
-  float* const tree_nodes = sl.pv.nodes;
-  float* const wedge = sl.pv.pend_edges + (size_t)w * 2 * W * dof;
-  const int cnt0 = sl.cnt[0], cnt1 = sl.cnt[1];
-  auto count_of = [&](int t) { return t ? cnt1 : cnt0; };
-  PoolWorker& k = sl.w[w];
-  const int mode = k.mode;
-  int ta = k.ta, last = k.last, target = k.target;
-  float* cur = k.cfg[0];
-  float* qt = k.cfg[1];
-  float* q1 = k.cfg[2];
-  float* qe = k.cfg[3];
-  const size_t wd = (size_t)W * dof;
-  auto nodes = [&](int t) { return tree_nodes + (size_t)t * MN * 8; };
-  // the motion of this worker's node appended at the last commit: scratch -> tree, before
-  // this task overwrites the scratch
-  if (k.pdst >= 0) {
-    float* dst = sl.pv.edges + ((size_t)k.pta * MN + k.pdst) * wd;
-#pragma unroll 4
-    for (int i = lane; i < (int)wd; i += 32) dst[i] = wedge[i];
-    __syncwarp();
-    if (lane == 0) k.pdst = -1;
-  }
-  if (mode == 0) {
-    ta = (r + w) & 1;
-    const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)w, 0u}, a.seed, 0u);
-    const U32x4 u1 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)w, 1u}, a.seed, 0u);
-    const uint32_t w8[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-    float v = 0.f;
-#pragma unroll
-    for (int j = 0; j < kMaxDof; ++j)  // lane j takes word j (no dynamic register index)
-      if (j == lane && j < dof) v = fmaf(u24(w8[j]), rb.j[j].hi - rb.j[j].lo, rb.j[j].lo);
-    __syncwarp();
-    if (lane < 8) qe[lane] = v;  // the sample, in the scratch slot
-    __syncwarp();
-    last = nearest_warp(nodes(ta), count_of(ta), qe, dof);
-    copy_cfg(cur, nodes(ta) + (size_t)last * 8, dof);
-    steer(cur, qe, a.range, dof, q1);
-  } else if (mode == 1) {
-    steer(cur, qt, a.range, dof, q1);
-  } else {
-    copy_cfg(q1, qt, dof);
-  }
-  float q[WPL][kMaxDof];
-  MotionWork work{0u, 0u};
-  // the closing hop is checked as it stands: one Alg. 1 iteration
-  const int st = validate_motion<CT, WPL, SEQ>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs,
-                                               S, cur, q1, W, q);
-  int add = 0, conn = 0;
-  if (st == kValid) {
-    if (mode == 2) {
-      conn = 1;
-      store_edge<WPL>(wedge + wd, q, W, dof);
-    } else {
-      last_waypoint<WPL>(q, W, dof, qe);
-      bool accept = true;
-      if (mode == 0) {
-        target = nearest_warp(nodes(ta ^ 1), count_of(ta ^ 1), qe, dof);
-        copy_cfg(qt, nodes(ta ^ 1) + (size_t)target * 8, dof);
-      } else {
-        accept = dist2(qe, qt, dof) < dist2(cur, qt, dof);
-      }
-      add = accept ? 1 : 0;
-      // the node's index is known once the round is committed: its motion waits here
-      if (add) store_edge<WPL>(wedge, q, W, dof);
-    }
-  }
-  if (lane == 0) {
-    k.add = add;
-    k.conn = conn;
-    k.ta = ta;
-    k.last = last;
-    k.target = target;
-    k.wp += (unsigned)W;
-    k.wproj += work.proj;
-    k.wcc += work.cc;
-  }
-  __syncwarp();
-}
-
-// Path of a connected problem (plan_problem's output step): root_a .. last, the closing hop,
-// target .. root_b, reversed when tree a is the goal tree.
-__device__ void pool_path(const PlanArgs& a, const PoolSlot& sl, const PoolWorker& k, int win, int W,
-                          int dof) {
-  const int lane = threadIdx.x & 31;
-  const ProblemView& P = sl.pv;
-  const int MN = a.max_nodes;
-  const size_t wd = (size_t)W * dof;
-  const int ta = k.ta, tb = ta ^ 1, last = k.last, target = k.target;
-  auto nodes = [&](int t) { return P.nodes + (size_t)t * MN * 8; };
-  auto parent = [&](int t) { return P.parent + (size_t)t * MN; };
-  auto edges = [&](int t) { return P.edges + (size_t)t * MN * wd; };
-  const float* hop = P.pend_edges + (size_t)win * 2 * wd + wd;
-  int len_a = 0, len_b = 0;
-  for (int v = last; v >= 0; v = parent(ta)[v]) ++len_a;
-  for (int v = target; v >= 0; v = parent(tb)[v]) ++len_b;
-  const int total = len_a + len_b;
-  const bool flip = ta == 1;
-  const int os = P.ostride;
-  const size_t we = (size_t)P.estride;
-  float* path = P.path;
-  float* pe = P.path_edges;
-  if (total <= a.max_path) {
-    int pos = len_a - 1;
-    for (int v = last; v >= 0; v = parent(ta)[v], --pos) {
-      const int np = flip ? total - 1 - pos : pos;
-      copy_warp(path + (size_t)np * os, nodes(ta) + (size_t)v * 8, os);
-      if (pe && parent(ta)[v] >= 0) {
-        const int e = flip ? total - 1 - pos : pos - 1;
-        copy_edge(pe + (size_t)e * we, edges(ta) + (size_t)v * wd, W, dof, os, flip);
-      }
-    }
-    if (pe) {
-      const int e = flip ? total - 1 - len_a : len_a - 1;
-      copy_edge(pe + (size_t)e * we, hop, W, dof, os, flip);
-    }
-    pos = len_a;
-    for (int v = target; v >= 0; v = parent(tb)[v], ++pos) {
-      const int np = flip ? total - 1 - pos : pos;
-      copy_warp(path + (size_t)np * os, nodes(tb) + (size_t)v * 8, os);
-      if (pe && parent(tb)[v] >= 0) {
-        const int e = flip ? total - 2 - pos : pos;
-        copy_edge(pe + (size_t)e * we, edges(tb) + (size_t)v * wd, W, dof, os, !flip);
-      }
-    }
-  }
-  if (lane == 0) a.path_len[P.p] = total <= a.max_path ? total : -total;
-}
-
-// Outputs of a finished problem, then the slot's next problem.
-__device__ void pool_finish(const RobotDev& rb, const SceneDev& shared_scene, const PlanArgs& a,
-                            PoolSlot& sl, bool solved, int rounds_used, float4* s_obs) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) {
-    const int p = sl.pv.p;
-    if (!solved) a.path_len[p] = 0;
-    long long total_wp = 0, tp = 0, tc = 0;
-    for (int w = 0; w < a.workers; ++w) {
-      total_wp += sl.w[w].wp;
-      tp += sl.w[w].wproj;
-      tc += sl.w[w].wcc;
-    }
-    if (a.rounds) a.rounds[p] = rounds_used;
-    if (a.waypoints) a.waypoints[p] = total_wp;
-    if (a.work) {
-      a.work[2 * p] = tp;
-      a.work[2 * p + 1] = tc;
-    }
-    long long t_end;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sl.t_start) * 1e-6);
-  }
-  __syncwarp();
-  pool_load(rb, shared_scene, a, sl, s_obs);
-}
-
-// Commit of a slot's round by the warp that finished its last task (plan_problem's steps
-// after its barrier).
-__device__ void pool_commit(const RobotDev& rb, const SceneDev& shared_scene, const ConsDev& cs,
-                            const PlanArgs& a, PoolSlot& sl, float4* s_obs) {
-  const int lane = threadIdx.x & 31;
-  const int B = a.workers, W = a.W, dof = rb.dof, MN = a.max_nodes;
-  __threadfence_block();  // every worker's outcome, node and motion of the round
-  const ProblemView& P = sl.pv;
-  const int r = sl.round;
-  int win = -1;
-  for (int w = 0; w < B; ++w)
-    if (sl.w[w].conn) {
-      win = w;
-      break;
-    }
-  if (win >= 0) {
-    pool_path(a, sl, sl.w[win], win, W, dof);
-    pool_finish(rb, shared_scene, a, sl, true, r + 1, s_obs);
-    return;
-  }
-  const float connect_radius = 10.f * cs.tau_floor;
-  float* const tree_nodes = P.nodes;
-  int* const tree_parent = P.parent;
-  int n0 = sl.cnt[0], n1 = sl.cnt[1];  // running tree sizes: nodes go in worker order
-  for (int w = 0; w < B; ++w) {
-    PoolWorker& k = sl.w[w];
-    int dst = -1;
-    if (k.add) {
-      const int t = k.ta;
-      dst = t ? n1++ : n0++;
-      if (dst < MN) {
-        // the node and its parent now; its motion stays in the worker's scratch until the
-        // worker's next task moves it (every worker has a task in every round, and a path is
-        // read only after a round in which all of them ran)
-        float* nd = tree_nodes + ((size_t)t * MN + dst) * 8;
-        if (lane < 8) nd[lane] = k.cfg[3][lane];
-        if (lane == 0) {
-          tree_parent[(size_t)t * MN + dst] = k.last;
-          k.pdst = dst;
-          k.pta = t;
-        }
-      } else {
-        dst = -1;
-      }
-    }
-    // the chain's next motion (warp-uniform)
-    int mode = 0, steps = k.steps;
-    if (dst >= 0) {
-      float gap = 0.f;
-#pragma unroll
-      for (int j = 0; j < kMaxDof; ++j)
-        if (j < dof) gap = fmaxf(gap, fabsf(k.cfg[3][j] - k.cfg[1][j]));
-      if (gap <= connect_radius) {
-        mode = 2;
-      } else if (steps < a.max_connect) {
-        mode = 1;
-        ++steps;
-      } else {
-        mode = 0;
-        steps = 0;
-      }
-    } else {
-      steps = 0;
-    }
-    __syncwarp();
-    if (dst >= 0 && lane < 8) k.cfg[0][lane] = k.cfg[3][lane];
-    if (lane == 0) {
-      if (dst >= 0) k.last = dst;
-      k.mode = mode;
-      k.steps = steps;
-    }
-    __syncwarp();
-  }
-  int stop = r + 1 >= a.max_rounds;
-  if (a.budget_ns && lane == 0) {  // one clock reading, the warp follows it
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if ((unsigned long long)(t - sl.t_start) > a.budget_ns) stop = 1;
-  }
-  stop = __shfl_sync(kFull, stop, 0);
-  if (lane == 0) {
-    sl.cnt[0] = min(n0, MN);
-    sl.cnt[1] = min(n1, MN);
-  }
-  __syncwarp();
-  if (stop) {
-    pool_finish(rb, shared_scene, a, sl, false, r + 1, s_obs);
-    return;
-  }
-  if (lane == 0) {
-    sl.round = r + 1;
-    sl.done = 0;
-  }
-  // the round's appends and the chains before the next round's tasks can be claimed
-  __syncwarp();
-  __threadfence_block();
-  if (lane == 0) atomicExch(&sl.next_task, 0);
-  __syncwarp();
-}
-
-template <int CT, int WPL, bool SEQ = false>
-__global__ void CPRRTC_PLAN_REGS plan_pool_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
-                                                  PlanArgs a, int P) {
-  extern __shared__ __align__(16) char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int NW = blockDim.x >> 5, B = a.workers;
-  const int mf4 = a.max_scene_f4;
-  const SmemLayout L(a.stage_obs ? P * mf4 : 0, rb.n_spheres, a.W, NW,
-                     (size_t)P * sizeof(PoolSlot) + sizeof(PoolShared));
-  float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
-  PoolSlot* slots = reinterpret_cast<PoolSlot*>(smem + L.extra);
-  PoolShared* ps = reinterpret_cast<PoolShared*>(smem + L.extra + (size_t)P * sizeof(PoolSlot));
-  stage_robot(rb, smem, L);
-  if (threadIdx.x == 0) ps->abort = 0;
-  for (int s = warp; s < P; s += NW) pool_load(rb, shared_scene, a, slots[s], s_obs + (size_t)s * mf4);
   __syncthreads();
-  const CcShared S = cc_shared(smem, L, warp);
-  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
-  unsigned long long idle_since = 0ull;
-  for (;;) {
-    // lane 0 reads the shared state and claims a task; the warp follows its decision (the
-    // lanes must not read flags that may change between their reads)
-    int sg = -1, wg = -1, stop = 0;
-    if (lane == 0) {
-      if (*reinterpret_cast<volatile int*>(&ps->abort)) {
-        stop = 1;
-      } else {
-        bool any_active = false;
-        for (int i = 0; i < P && sg < 0; ++i) {
-          const int s = (warp + i) % P;
-          PoolSlot& sl = slots[s];
-          if (!vload(sl.active)) continue;
-          any_active = true;
-          if (vload(sl.next_task) < B) {
-            const int t = atomicAdd(&sl.next_task, 1);
-            if (t < B) {
-              sg = s;
-              wg = t;
-            }
-          }
-        }
-        if (sg < 0) {
-          if (!any_active) {
-            stop = 1;  // every slot retired: the queue is empty
-          } else {
-            // every open round's motions are taken: wait (bounded) for a commit
-            unsigned long long now;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-            if (idle_since == 0ull) {
-              idle_since = now;
-            } else if (now - idle_since > kPoolIdleNs) {
-              *reinterpret_cast<volatile int*>(&ps->abort) = 1;
-              if (a.error) atomicExch(a.error, 1);
-              stop = 1;
-            }
-          }
-        } else {
-          idle_since = 0ull;
-        }
-      }
-    }
-    stop = __shfl_sync(kFull, stop, 0);
-    if (stop) break;
-    sg = __shfl_sync(kFull, sg, 0);
-    wg = __shfl_sync(kFull, wg, 0);
-    if (sg < 0) {
-      __nanosleep(256);
-      continue;
-    }
-    __threadfence_block();  // the slot's round state as its last commit left it
-    PoolSlot& sl = slots[sg];
-    const float4* obs = a.stage_obs ? s_obs + (size_t)sg * mf4 : sl.sc.obs;
-    pool_task<CT, WPL, SEQ>(rb, cs, a, sl, wg, obs, S, wc);
-    __threadfence_block();  // this task's outcome before it is counted
-    int d = 0;
-    if (lane == 0) d = atomicAdd(&sl.done, 1);
-    d = __shfl_sync(kFull, d, 0);
-    if (d == B - 1) pool_commit(rb, shared_scene, cs, a, sl, s_obs + (size_t)sg * mf4);
-  }
+  plan_problem<CT, WPL, SEQ>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
   wc.flush(a.work_counters);
 }
 
@@ -1033,29 +616,27 @@ static const void* plan_fn(int ct, int W, bool sequential = false) {
   const bool two = W > 32;
   if (sequential) {  // the naive baseline's projection: roll-pitch and z-plane, W <= 32
     if (two) return nullptr;
-    if (ct == kConsRollPitch) return (const void*)plan_pool_kernel<kConsRollPitch, 1, true>;
-    if (ct == kConsZPlane) return (const void*)plan_pool_kernel<kConsZPlane, 1, true>;
+    if (ct == kConsRollPitch) return (const void*)plan_kernel<kConsRollPitch, 1, true>;
+    if (ct == kConsZPlane) return (const void*)plan_kernel<kConsZPlane, 1, true>;
     return nullptr;
   }
   switch (ct) {
     case kConsRollPitch:
-      return two ? (const void*)plan_pool_kernel<kConsRollPitch, 2> : (const void*)plan_pool_kernel<kConsRollPitch, 1>;
+      return two ? (const void*)plan_kernel<kConsRollPitch, 2> : (const void*)plan_kernel<kConsRollPitch, 1>;
     case kConsZPlane:
-      return two ? (const void*)plan_pool_kernel<kConsZPlane, 2> : (const void*)plan_pool_kernel<kConsZPlane, 1>;
+      return two ? (const void*)plan_kernel<kConsZPlane, 2> : (const void*)plan_kernel<kConsZPlane, 1>;
     case kConsLine:
-      return two ? (const void*)plan_pool_kernel<kConsLine, 2> : (const void*)plan_pool_kernel<kConsLine, 1>;
+      return two ? (const void*)plan_kernel<kConsLine, 2> : (const void*)plan_kernel<kConsLine, 1>;
     case kConsOrientPlane:
-      return two ? (const void*)plan_pool_kernel<kConsOrientPlane, 2> : (const void*)plan_pool_kernel<kConsOrientPlane, 1>;
+      return two ? (const void*)plan_kernel<kConsOrientPlane, 2> : (const void*)plan_kernel<kConsOrientPlane, 1>;
     case kConsOrientLine:
-      return two ? (const void*)plan_pool_kernel<kConsOrientLine, 2> : (const void*)plan_pool_kernel<kConsOrientLine, 1>;
+      return two ? (const void*)plan_kernel<kConsOrientLine, 2> : (const void*)plan_kernel<kConsOrientLine, 1>;
     default:
-      return two ? (const void*)plan_pool_kernel<kConsNone, 2> : (const void*)plan_pool_kernel<kConsNone, 1>;
+      return two ? (const void*)plan_kernel<kConsNone, 2> : (const void*)plan_kernel<kConsNone, 1>;
   }
 }
 
-// Warps a CTA of the planner kernel can have for this constraint type and W (its registers
-// per thread bound it), at most kMaxWorkers; 0 if the kernel does not exist or the query fails.
-int plan_max_warps(int cons_type, int W, bool sequential) {
+int plan_max_workers(int cons_type, int W, bool sequential) {
   cudaFuncAttributes attr;
   const void* fn = plan_fn(cons_type, W, sequential);
   if (!fn) return 0;
@@ -1066,74 +647,24 @@ int plan_max_warps(int cons_type, int W, bool sequential) {
   return attr.maxThreadsPerBlock / 32 < kMaxWorkers ? attr.maxThreadsPerBlock / 32 : kMaxWorkers;
 }
 
-size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int warps, int slots, bool stage) {
-  return SmemLayout(stage ? slots * max_scene_f4 : 0, rb.n_spheres, W, warps,
-                    (size_t)slots * sizeof(PoolSlot) + sizeof(PoolShared))
-      .total;
-}
-
-// Shape of a planner launch: warps per CTA, problem slots per CTA, CTAs. With max_slots = 0,
-// up to 3 problems share a CTA, fewer (down to one) when fewer problems than that fill the GPU,
-// so that small launches spread over the SMs; otherwise max_slots problems share a CTA (fewer
-// only when their staged obstacles do not fit in shared memory).
-PlanShape plan_shape(const RobotDev& rb, const ConsDev& cs, const PlanArgs& a, const DeviceInfo& dev,
-                     int warps, int max_slots) {
-  PlanShape sh{};
-  const void* fn = plan_fn(cs.type, a.W, a.sequential != 0);
-  if (!fn || a.n <= 0) return sh;
-  const int mw = plan_max_warps(cs.type, a.W, a.sequential != 0);
-  if (mw < 1) return sh;
-  int nw = warps > 0 ? warps : kMaxWorkers;
-  nw = nw < mw ? nw : mw;
-  int slots = max_slots > 0 ? max_slots : 3;
-  for (;; --slots) {
-    // obstacles staged per slot when they fit, else read from global memory
-    size_t smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, nw, slots, true);
-    bool stage = smem <= dev.smem_optin;
-    if (!stage) smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, nw, slots, false);
-    if (smem <= dev.smem_optin || slots == 1) {
-      sh.smem = smem;
-      sh.stage = stage && smem <= dev.smem_optin;
-      break;
-    }
-  }
-  if (sh.smem > dev.smem_optin) return PlanShape{};
-  int per_sm = 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * nw, sh.smem) != cudaSuccess || per_sm < 1) {
-    cudaGetLastError();
-    return PlanShape{};
-  }
-  const int resident = per_sm * dev.sm_count;
-  if (max_slots > 0) {
-    sh.slots = slots;  // as asked (fewer only if shared memory forced it)
-  } else {
-    // slots per CTA: enough to hold every problem at once when possible, at most `slots`
-    const int need = (a.n + resident - 1) / resident;
-    sh.slots = need < slots ? need : slots;
-    if (sh.slots < 1) sh.slots = 1;
-  }
-  const int ctas = (a.n + sh.slots - 1) / sh.slots;
-  sh.grid = ctas < resident ? ctas : resident;
-  sh.warps = nw;
-  sh.smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, nw, sh.slots, sh.stage);
-  return sh;
+size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage) {
+  return SmemLayout(stage ? max_scene_f4 : 0, rb.n_spheres, W, workers, sizeof(PlanShared)).total;
 }
 
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
-                        const PlanShape& shape, cudaStream_t stream) {
+                        const DeviceInfo& dev, cudaStream_t stream) {
   if (a.n <= 0) return cudaSuccess;
+  size_t smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, true);
+  a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
+  if (!a.stage_obs) smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, false);
+  if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
   const void* fn = plan_fn(cs.type, a.W, a.sequential != 0);
-  if (!fn || shape.grid < 1) return cudaErrorNotSupported;
-  a.stage_obs = shape.stage ? 1 : 0;
-  cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned), stream);
+  if (!fn) return cudaErrorNotSupported;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
-  if (e != cudaSuccess) return e;
-  int slots = shape.slots;
   void* args[] = {const_cast<RobotDev*>(&rb), const_cast<SceneDev*>(&sc),
-                  const_cast<ConsDev*>(&cs), &a, &slots};
-  e = cudaLaunchKernel(fn, dim3(shape.grid), dim3(32 * shape.warps), args, shape.smem, stream);
+                  const_cast<ConsDev*>(&cs), &a};
+  e = cudaLaunchKernel(fn, dim3(a.n), dim3(32 * a.workers), args, smem, stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
