@@ -70,7 +70,7 @@ def executed_flops(dof: int, counters) -> float:
     """FLOPs of the work the kernels evaluated (cprrtc_work_counters): Alg. 1 waypoint
     updates, DH chains of the collision check, points moved to world coordinates, and
     ball-vs-primitive tests by primitive."""
-    upd, chains, tf, ps, pb, pc = [float(x) for x in counters]
+    upd, chains, tf, ps, pb, pc = [float(x) for x in counters[:6]]
     return (upd * flops_waypoint_iter(dof) + chains * dof * F_CHAIN_JOINT + tf * F_SPHERE_FK
             + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
 
@@ -316,6 +316,51 @@ def run_plan(args, world, rank, local):
     waypoints_step = int(wp.sum())
     value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     nominal = plan_flops(rb.dof, scenes, len(rb.spheres), work)
+
+    # the learned form on the same problems: the network trained first (untimed), every extend
+    # motion warm-started by it, plain Alg. 1 as judge and fallback
+    learned = None
+    if args.learned:
+        with torch.cuda.stream(stream):
+            tr = train_warm_network(ctx, rb, 40 + 1000 * rank, dev, args.train_epochs, stream)
+            ctx.set_plan_warm_start(WS_REFINE)
+            out_w = ctx.alloc_plan_outputs(n, prm, start, edges=False)
+            for _ in range(max(1, args.warmup)):
+                ctx.plan(start, goal, prm, out=out_w)
+            ctx.work_counters(reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.plan(start, goal, prm, out=out_w)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            w_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), world)
+            wcnt = ctx.work_counters() / max(args.steps, 1)
+            ctx.set_plan_warm_start(0)
+        Lw = out_w["path_len"].cpu().numpy()
+        msw = out_w["plan_ms"].cpu().numpy()
+        sw = Lw > 0
+        learned = {
+            "ms_per_step": w_ms / args.steps,
+            "value": sum_over_ranks(int(out_w["waypoints"].sum().item()), world) * args.steps / (w_ms / 1e3),
+            "p50_plan_ms": float(np.percentile(msw[sw], 50)) if sw.any() else None,
+            "p95_plan_ms": float(np.percentile(msw[sw], 95)) if sw.any() else None,
+            "success_rate": float(sw.mean()),
+            "mean_rounds": float(out_w["rounds"].cpu().numpy().mean()),
+            "extend_motions_warm_started_per_step": float(wcnt[6]),
+            "warm_segments_accepted_per_step": float(wcnt[7]),
+            "network": {"train_pairs": WS_TRAIN, "epochs": args.train_epochs, "refine_iters": WS_REFINE,
+                        "pairs_from": "cprrtc_project_configs (the tests train on oracle pairs)",
+                        "held_out_loss": [float(tr["held0"]), float(tr["held1"])],
+                        "zero_prediction_loss": tr["zero_loss"], "train_s": tr["train_s"]},
+            "note": "extend motions warm-started by the network's correction of their end, spread "
+                    "along the motion; Alg. 1 judges and falls back; connect steps unchanged",
+        }
     flops = executed_flops(rb.dof, counters)
 
     # end to end through the C ABI with pinned host buffers
@@ -362,6 +407,11 @@ def run_plan(args, world, rank, local):
         "p95_plan_ms": float(np.percentile(ms[solved], 95)) if solved.any() else None,
         "p50_plan_ms_all": float(np.percentile(ms, 50)),
         "success_rate": float(solved.mean()),
+        "learned_vs_plain": {"plain": {"p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
+                                       "p95_plan_ms": float(np.percentile(ms[solved], 95)) if solved.any() else None,
+                                       "success_rate": float(solved.mean()),
+                                       "ms_per_step": total_ms / args.steps},
+                             "learned": learned},
         "waypoints_per_step": waypoints_step,
         "evaluated_waypoints_per_s": sum_over_ranks(int(work[:, 1].sum()), world) * args.steps
                                      / (total_ms / 1e3),
@@ -533,7 +583,7 @@ def run_batch(args, world, rank, local):
     value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     # executed FLOPs: dof differs per problem; weight Alg. 1 updates by the mean dof
     mean_dof = float(np.mean([robots[r].dof for r, _, _, _ in probs]))
-    upd, chains, tf, ps, pb, pc = [float(x) for x in counters]
+    upd, chains, tf, ps, pb, pc = [float(x) for x in counters[:6]]
     flops = (upd * flops_waypoint_iter(round(mean_dof)) + chains * mean_dof * F_CHAIN_JOINT
              + tf * F_SPHERE_FK + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
     # end to end through the C ABI with pinned host buffers
@@ -1128,6 +1178,37 @@ WS_EPOCHS = 10
 WS_REFINE = 5
 
 
+def train_warm_network(ctx, rb, seed, dev, epochs, stream):
+    """The warm-start network of the context's robot and constraint, trained (untimed) on 2^20
+    (uniform configuration -> its projection) pairs from cprrtc_project_configs; held-out
+    loss before and after on 16384 more pairs."""
+    import torch
+    t0 = time.perf_counter()
+    qs, ts, k = [], [], 0
+    while sum(len(x) for x in qs) < WS_TRAIN + 16384:
+        q = torch.from_numpy(S.uniform_configs(rb, 1 << 19, seed * 7919 + k).astype(np.float32)).to(dev)
+        r = ctx.project_configs(q, 60)
+        ok = r["ok"].bool()
+        qs.append(q[ok])
+        ts.append(r["q"][ok])
+        k += 1
+    q_all, t_all = torch.cat(qs), torch.cat(ts)
+    q_tr, t_tr = q_all[:WS_TRAIN].contiguous(), t_all[:WS_TRAIN].contiguous()
+    q_ho = q_all[WS_TRAIN:WS_TRAIN + 16384].contiguous()
+    t_ho = t_all[WS_TRAIN:WS_TRAIN + 16384].contiguous()
+    stream.synchronize()
+    pairs_s = time.perf_counter() - t0
+    ctx.mlp_init(seed)
+    held0, _ = ctx.mlp_grad(q_ho, t_ho)
+    t0 = time.perf_counter()
+    losses = ctx.mlp_train(q_tr, t_tr, batch=1024, epochs=epochs, lr=1e-3, seed=seed)
+    train_s = time.perf_counter() - t0
+    held1, _ = ctx.mlp_grad(q_ho, t_ho)
+    zero_loss = float(0.5 * ((t_ho - q_ho) ** 2).sum(1).mean())
+    return dict(pairs_s=pairs_s, train_s=train_s, losses=losses, held0=held0, held1=held1,
+                zero_loss=zero_loss)
+
+
 def mlp_flops_per_row(dof: int, hidden: int = 256) -> int:
     """Multiply-adds of the warm-start network per row, x 2."""
     return 2 * (dof * hidden + 2 * hidden * hidden + hidden * dof)
@@ -1161,29 +1242,9 @@ def run_warmstart(args, world, rank, local):
     ctx.set_constraint(c)
     seed = 40 + 1000 * rank
     with torch.cuda.stream(stream):
-        # training pairs
-        t0 = time.perf_counter()
-        qs, ts, k = [], [], 0
-        while sum(len(x) for x in qs) < WS_TRAIN + 16384:
-            q = torch.from_numpy(S.uniform_configs(rb, 1 << 19, seed * 7919 + k)
-                                 .astype(np.float32)).to(dev)
-            r = ctx.project_configs(q, 60)
-            ok = r["ok"].bool()
-            qs.append(q[ok])
-            ts.append(r["q"][ok])
-            k += 1
-        q_all, t_all = torch.cat(qs), torch.cat(ts)
-        q_tr, t_tr = q_all[:WS_TRAIN].contiguous(), t_all[:WS_TRAIN].contiguous()
-        q_ho, t_ho = q_all[WS_TRAIN:WS_TRAIN + 16384].contiguous(), t_all[WS_TRAIN:WS_TRAIN + 16384].contiguous()
-        stream.synchronize()
-        pairs_s = time.perf_counter() - t0
-        ctx.mlp_init(seed)
-        held0, _ = ctx.mlp_grad(q_ho, t_ho)
-        t0 = time.perf_counter()
-        losses = ctx.mlp_train(q_tr, t_tr, batch=1024, epochs=args.train_epochs, lr=1e-3, seed=seed)
-        train_s = time.perf_counter() - t0
-        held1, _ = ctx.mlp_grad(q_ho, t_ho)
-        zero_loss = float(0.5 * ((t_ho - q_ho) ** 2).sum(1).mean())
+        tr = train_warm_network(ctx, rb, seed, dev, args.train_epochs, stream)
+        pairs_s, train_s, losses = tr["pairs_s"], tr["train_s"], tr["losses"]
+        held0, held1, zero_loss = tr["held0"], tr["held1"], tr["zero_loss"]
 
         q0 = manifold_starts_gpu(ctx, rb, n, 50_000 + 97 * rank)
         q1 = torch.from_numpy(S.uniform_configs(rb, n, 60_000 + 97 * rank).astype(np.float32)).to(dev)
@@ -1461,6 +1522,8 @@ def main():
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--learned", type=int, default=1,
+                    help="planner workload: also time the learned form (trains the network first)")
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
                     help="warm-start training epochs (fewer for profiling runs)")
     ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch,earlyexit,naive",

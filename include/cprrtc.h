@@ -374,6 +374,23 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
                 int64_t* work);
 
+/* The planner's learned form (not in the paper; the warm start of cprrtc_validate_ws inside
+ * RRT-Connect): with refine_iters in 1..20, cprrtc_plan and cprrtc_plan_static warm-start every
+ * extend motion (the first motion of a chain, toward a sample). The network's correction
+ * f(q1) of the motion's end q1 moves waypoint i by (i / (W-1)) f(q1), clamped to the joint
+ * limits: cprrtc_validate_ws's correction f(xi_i) - (1 - i/(W-1)) f(xi_0) with f taken linear
+ * along the motion, where the start term cancels (one network evaluation per motion instead
+ * of W). The corrected segment is tried only if its largest ||E_task||_inf over waypoints
+ * 1..W-1 is below the interpolation's, for refine_iters Alg. 1 iterations; if they do not
+ * accept the whole segment, plain Alg. 1 runs from the interpolation with max_iters, so Alg. 1
+ * stays the judge of every motion. Connect steps and closing hops are planned as without it.
+ * The network is the context's (cprrtc_mlp_init / cprrtc_mlp_load for the robot's dof, BF16
+ * weights); each warp evaluates its motion's row itself. Constraints ROLL_PITCH and Z_PLANE
+ * with the parallel projection; planning otherwise returns E_UNSUPPORTED, and without a
+ * network for the robot E_NOT_CONFIGURED. 0 turns it off (the default).
+ * Errors: E_INVALID_ARG (refine_iters outside 0..20). */
+int cprrtc_set_plan_warm_start(cprrtc_ctx* ctx, int refine_iters);
+
 /* ---- batches of uneven planning problems ---- */
 
 /* An addition for serving: the paper plans one problem per run. Every problem of a batch
@@ -518,12 +535,15 @@ int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t*
 int cprrtc_set_timing(cprrtc_ctx* ctx, int enabled);
 
 /* Work the validate and plan kernels of this context evaluated since creation or the last
- * reset, for throughput accounting (out has 6 entries): out[0] Alg. 1 waypoint updates (per
- * iteration, the waypoints after prog), out[1] DH chains evaluated by collision checking
- * (per checked waypoint and pass), out[2] points moved to world coordinates (frame bounding
- * spheres and robot spheres), out[3..5] ball-vs-primitive tests against spheres, boxes and
- * capsules (swept bounds, frame bounds and robot spheres together). Synchronises the
- * context's stream; reset = 1 zeroes them. */
+ * reset, for throughput accounting (out has 8 entries): out[0] Alg. 1 waypoint updates (per
+ * iteration, the waypoints after prog; with a warm start also the two task-error evaluations
+ * per waypoint that decide whether to use it), out[1] DH chains evaluated by collision
+ * checking (per checked waypoint and pass), out[2] points moved to world coordinates (frame
+ * bounding spheres and robot spheres), out[3..5] ball-vs-primitive tests against spheres,
+ * boxes and capsules (swept bounds, frame bounds and robot spheres together), out[6] extend
+ * motions of the planner's learned form that evaluated the network, out[7] those whose
+ * warm-started segment was accepted. Synchronises the context's stream; reset = 1 zeroes
+ * them. */
 int cprrtc_work_counters(cprrtc_ctx* ctx, int64_t* out, int reset);
 int cprrtc_kernel_time(cprrtc_ctx* ctx, const char* name, double* ms, long long* launches);
 int cprrtc_reset_timing(cprrtc_ctx* ctx);

@@ -118,6 +118,7 @@ _SIGS = {
     "cprrtc_mlp_init": [C.c_void_p, C.c_uint64],
     "cprrtc_mlp_set_precision": [C.c_void_p, C.c_int],
     "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
+    "cprrtc_set_plan_warm_start": [C.c_void_p, C.c_int],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
@@ -293,8 +294,8 @@ class Context:
 
     def work_counters(self, reset: bool = False) -> np.ndarray:
         """[Alg. 1 updates, collision-check chains, world transforms, sphere tests, box tests,
-        capsule tests] since the last reset."""
-        out = np.zeros(6, np.int64)
+        capsule tests, warm-started extend motions tried, accepted] since the last reset."""
+        out = np.zeros(8, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
 
@@ -385,6 +386,10 @@ class Context:
 
     def mlp_init(self, seed: int = 0):
         self._check(self._L.cprrtc_mlp_init(self.h, int(seed)))
+
+    def set_plan_warm_start(self, refine_iters: int):
+        """Planner's learned form: extend motions warm-started by the network (0: off)."""
+        self._check(self._L.cprrtc_set_plan_warm_start(self.h, int(refine_iters)))
 
     def set_wait_limit(self, seconds: float):
         """Limit of the tensor-core kernels' bounded waits (0: the default, 1 s)."""

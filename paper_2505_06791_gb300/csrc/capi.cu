@@ -100,6 +100,7 @@ struct cprrtc_ctx {
   MlpDev* mlp = nullptr;
   bool mlp_fp32 = false;    // the network's FP32 checking mode
   unsigned long long wait_ns = 0;  // bounded-wait limit of the tensor-core kernels (0: 1 s)
+  int plan_warm = 0;               // planner's learned form: refine iterations (0: off)
   float* d_warm = nullptr;  // corrections [n*W][16]
   size_t warm_cap = 0;      // bytes
   bool timing = false;
@@ -352,7 +353,16 @@ int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char
   if (seq && (pp->W > 32 || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane)))
     return fail(ctx, CPRRTC_E_UNSUPPORTED,
                 std::string(who) + ": the sequential projection plans with ROLL_PITCH or Z_PLANE and W <= 32");
-  const int mw = plan_max_workers(ctx->cs.type, pp->W, seq);
+  const bool warm = ctx->plan_warm > 0;
+  if (warm) {
+    if (seq || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane))
+      return fail(ctx, CPRRTC_E_UNSUPPORTED,
+                  std::string(who) + ": the learned form plans with ROLL_PITCH or Z_PLANE and the parallel projection");
+    if (!ctx->mlp || mlp_dof(ctx->mlp) != ctx->rb.dof)
+      return fail(ctx, CPRRTC_E_NOT_CONFIGURED,
+                  std::string(who) + ": the learned form needs a network for the robot (mlp_init or mlp_load)");
+  }
+  const int mw = plan_max_workers(ctx->cs.type, pp->W, seq, warm);
   if (pp->workers > mw)
     return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": at most " + std::to_string(mw) +
                                                " workers fit one CTA at W = " + std::to_string(pp->W));
@@ -1109,6 +1119,14 @@ int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed) {
   return CPRRTC_OK;
 }
 
+int cprrtc_set_plan_warm_start(cprrtc_ctx* ctx, int refine_iters) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (refine_iters < 0 || refine_iters > 20)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_plan_warm_start: refine_iters 0..20");
+  ctx->plan_warm = refine_iters;
+  return CPRRTC_OK;
+}
+
 int cprrtc_set_wait_limit(cprrtc_ctx* ctx, double seconds) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (!(seconds == 0.0 || (seconds >= 1e-6 && seconds <= 10.0)))
@@ -1462,6 +1480,10 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
   a.sequential = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
   a.work_counters = ctx->d_work;
+  if (ctx->plan_warm > 0) {
+    a.net = mlp_view(ctx->mlp);
+    a.warm_refine = ctx->plan_warm;
+  }
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;
@@ -1759,6 +1781,10 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
   a.seed = pp->seed;
   a.budget_ns = pp->time_budget_ms > 0.0 ? (unsigned long long)(pp->time_budget_ms * 1e6) : 0ull;
   a.sequential = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
+  if (ctx->plan_warm > 0) {
+    a.net = mlp_view(ctx->mlp);
+    a.warm_refine = ctx->plan_warm;
+  }
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;

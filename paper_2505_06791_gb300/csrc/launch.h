@@ -9,7 +9,9 @@
 namespace cprrtc {
 
 constexpr int kValidateWarps = 4;  // warps (motions in flight) per CTA
-constexpr int kWorkCounters = 6;   // updates, chains, transforms, sphere / box / capsule tests
+// updates, chains, transforms, sphere / box / capsule tests, warm-started motions tried and
+// accepted (the planner's learned form)
+constexpr int kWorkCounters = 8;
 
 struct DeviceInfo {
   int sm_count;
@@ -43,6 +45,15 @@ struct ValidateArgs {
 
 constexpr int kMaxWorkers = 16;  // warps per planning problem
 
+// The warm-start network as the planner's kernels read it: BF16 transposes [in][out] of
+// layers 0..2 (input widths 16, 256, 256; outputs 256), layer 3 as [16][256], FP32 biases.
+struct MlpView {
+  const void* wt[3];
+  const void* w3;
+  const float* b[4];
+  int dof;
+};
+
 struct PlanArgs {
   const float* start;
   const float* goal;
@@ -67,8 +78,12 @@ struct PlanArgs {
   long long* waypoints;
   float* plan_ms;
   long long* work;          // [n][2] Alg. 1 waypoint updates, collision-checked waypoints
-  unsigned long long* work_counters;  // [6] executed-work totals (may be null)
+  unsigned long long* work_counters;  // executed-work totals (may be null)
   int stage_obs;            // set by the launcher
+  // learned warm start of extend motions (warm_refine > 0): the network and the Alg. 1
+  // iterations the corrected segment gets before plain Alg. 1 takes over
+  MlpView net;
+  int warm_refine;
 };
 
 // Persistent batch of uneven planning problems (one launch).
@@ -105,7 +120,7 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
 size_t plan_smem_bytes(const RobotDev& rb, int max_scene_f4, int W, int workers, bool stage);
 // Most workers (warps per CTA) the planner kernel for this constraint type and W can launch
 // with (its registers per thread bound the CTA size); 0 if the query fails.
-int plan_max_workers(int cons_type, int W, bool sequential = false);
+int plan_max_workers(int cons_type, int W, bool sequential = false, bool warm = false);
 cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs, PlanArgs a,
                         const DeviceInfo& dev, cudaStream_t stream);
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, const uint32_t* ctr, int n, uint32_t* out,
@@ -136,6 +151,7 @@ cudaError_t mlp_create(MlpDev** out, int dof);
 void mlp_destroy(MlpDev* d);
 int mlp_dof(const MlpDev* d);
 void mlp_set_fp32(MlpDev* d, bool on);  // FP32 checking mode (no BF16 rounding)
+MlpView mlp_view(MlpDev* d);             // the BF16 network for the planner's kernels
 void mlp_set_wait_ns(MlpDev* d, unsigned long long ns);  // bounded-wait limit of inference
 bool mlp_fp32(const MlpDev* d);
 int mlp_step(const MlpDev* d);

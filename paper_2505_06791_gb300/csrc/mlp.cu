@@ -490,6 +490,9 @@ struct MlpDev {
   float* v = nullptr;
   float* g = nullptr;   // gradients
   __nv_bfloat16* wb = nullptr;  // BF16 weights [out][in] per layer (biases stay FP32)
+  // BF16 transposes [in][out] of layers 0..2, for the planner's per-warp evaluation (a warp's
+  // lanes read consecutive outputs of one input)
+  __nv_bfloat16* wbt = nullptr;
   // fused inference: packed weight image, padded biases, timeout flag
   uint8_t* wpack = nullptr;
   float* bias_pad = nullptr;
@@ -525,6 +528,7 @@ cudaError_t mlp_create(MlpDev** out, int dof) {
   if (e == cudaSuccess) e = cudaMalloc(&d->v, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d->g, n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d->wb, nw * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&d->wbt, (nw - (size_t)kOut[3] * kIn[3]) * 2);
   if (e == cudaSuccess) e = cudaMemset(d->p, 0, n * 4);
   if (e == cudaSuccess) e = cudaMemset(d->m, 0, n * 4);
   if (e == cudaSuccess) e = cudaMemset(d->v, 0, n * 4);
@@ -551,6 +555,7 @@ void mlp_destroy(MlpDev* d) {
   cudaFree(d->v);
   cudaFree(d->g);
   cudaFree(d->wb);
+  cudaFree(d->wbt);
   cudaFree(d->ws);
   cudaFree(d->wpack);
   cudaFree(d->bias_pad);
@@ -560,10 +565,17 @@ void mlp_destroy(MlpDev* d) {
 
 int mlp_dof(const MlpDev* d) { return d->dof; }
 void mlp_set_fp32(MlpDev* d, bool on) { d->fp32 = on; }
+
 void mlp_set_wait_ns(MlpDev* d, unsigned long long ns) { d->wait_ns = ns; }
 bool mlp_fp32(const MlpDev* d) { return d->fp32; }
 const int* mlp_error_flag(const MlpDev* d) { return d->err; }
 int mlp_step(const MlpDev* d) { return d->step; }
+
+static __nv_bfloat16* wbt_of(MlpDev* d, int l) {  // layers 0..2
+  size_t o = 0;
+  for (int i = 0; i < l; ++i) o += (size_t)kOut[i] * kIn[i];
+  return d->wbt + o;
+}
 
 static __nv_bfloat16* wb_of(MlpDev* d, int l) {
   size_t o = 0;
@@ -571,11 +583,21 @@ static __nv_bfloat16* wb_of(MlpDev* d, int l) {
   return d->wb + o;
 }
 
+MlpView mlp_view(MlpDev* d) {
+  MlpView v{};
+  for (int l = 0; l < kMlpLayers - 1; ++l) v.wt[l] = wbt_of(d, l);
+  v.w3 = wb_of(d, kMlpLayers - 1);
+  for (int l = 0; l < kMlpLayers; ++l) v.b[l] = d->p + w_off(l) + (size_t)kOut[l] * kIn[l];
+  v.dof = d->dof;
+  return v;
+}
+
 // Refreshes the BF16 weight copies from the FP32 master parameters.
 static cudaError_t refresh_bf16(MlpDev* d, cudaStream_t s) {
   d->packed = false;
   for (int l = 0; l < kMlpLayers; ++l) {
-    cudaError_t e = launch_to_bf16(d->p + w_off(l), kOut[l], kIn[l], wb_of(d, l), nullptr, s);
+    cudaError_t e = launch_to_bf16(d->p + w_off(l), kOut[l], kIn[l], wb_of(d, l),
+                                   l < kMlpLayers - 1 ? wbt_of(d, l) : nullptr, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -959,7 +981,8 @@ cudaError_t mlp_train_step(MlpDev* d, const float* q, const float* t, int rows, 
     const int cols_used = l == 0 ? d->dof : kIn[l];
     const size_t o = w_off(l);
     e = launch_adam(d->p + o, d->m + o, d->v + o, d->g + o, kOut[l], kIn[l], rows_used, cols_used, lr,
-                    0.9f, 0.999f, 1e-8f, d->step, wb_of(d, l), nullptr, s);
+                    0.9f, 0.999f, 1e-8f, d->step, wb_of(d, l),
+                    l < kMlpLayers - 1 ? wbt_of(d, l) : nullptr, s);
     if (e == cudaSuccess) {
       const size_t ob = o + (size_t)kOut[l] * kIn[l];
       e = launch_adam(d->p + ob, d->m + ob, d->v + ob, d->g + ob, 1, kOut[l], 1, rows_used, lr, 0.9f,

@@ -52,6 +52,7 @@ struct WorkCount {
   unsigned chains;      // DH chains evaluated for collision checking
   unsigned transforms;  // points moved to world coordinates (frame bounds, robot spheres)
   unsigned p_sph, p_box, p_cap;  // ball-vs-primitive tests by primitive
+  unsigned warm_tried, warm_used; // planner's learned form: extend motions warm-started, accepted
   __device__ __forceinline__ void add_type(const SceneDev& sc, int o, unsigned n) {
     if (o < sc.n_sph)
       p_sph += n;
@@ -81,6 +82,8 @@ struct WorkCount {
     atomicAdd(dst + 3, (unsigned long long)p_sph);
     atomicAdd(dst + 4, (unsigned long long)p_box);
     atomicAdd(dst + 5, (unsigned long long)p_cap);
+    if (warm_tried) atomicAdd(dst + 6, (unsigned long long)warm_tried);
+    if (warm_used) atomicAdd(dst + 7, (unsigned long long)warm_used);
   }
 };
 

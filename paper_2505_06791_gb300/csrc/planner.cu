@@ -19,6 +19,7 @@
 #include "launch.h"
 #include "motion.cuh"
 #include "philox.cuh"
+#include "warm_net.cuh"
 
 namespace cprrtc {
 
@@ -183,25 +184,84 @@ struct MotionWork {  // per warp (32-bit suffices for one launch)
 
 // Interpolate q0 -> q1, project (at most max_iters iterations), FK + CC from waypoint 1
 // stopping at the first collision found.
-template <int CT, int WPL, bool SEQ = false>
+//
+// Learned form (WARM, `net` set: extend motions): the network's correction f(q1) of the motion's
+// end is spread along the segment, waypoint i moving by (i / (W-1)) f(q1) (clamped to the
+// limits). This is the warm start of cprrtc_validate_ws, f(xi_i) - (1 - t_i) f(xi_0), with f
+// taken linear along the short motion between f(xi_0) and f(q1): the start term cancels, so one
+// network row per motion. The corrected segment is used only if its largest ||E_task||_inf over
+// waypoints 1..W-1 is below the interpolation's, and only for warm_refine Alg. 1 iterations;
+// otherwise, or if they do not accept the whole segment, plain Alg. 1 runs from the
+// interpolation with max_iters, as without the network.
+template <int CT, int WPL, bool SEQ = false, bool WARM = false>
 __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDev& sc,
                                                const ConsDev& cs, int max_iters, MotionWork& work,
                                                WorkCount& wc, const float4* obs,
                                                const CcShared& S, const float* q0,
                                                const float* q1, int W,
-                                               float (&q)[WPL][kMaxDof]) {
+                                               float (&q)[WPL][kMaxDof],
+                                               const MlpView* net = nullptr, int warm_refine = 0,
+                                               float* fcorr = nullptr) {
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < WPL; ++s) interp(q0, q1, min(lane + 32 * s, W - 1), W, rb.dof, q[s]);
-  const float tau = step_threshold(cs, q0, q1, W, rb.dof);
+  const int dof = rb.dof;
+  const float tau = step_threshold(cs, q0, q1, W, dof);
   ProjResult pr;
-  if constexpr (SEQ)
-    pr = project_sequential<CT, WPL>(rb, cs, max_iters, q0, q1, q, W, tau);
-  else
-    pr = project_warp<CT, WPL>(rb, cs, max_iters, q, W, tau, S.wq);
-  __syncwarp();
-  work.proj += (unsigned)pr.updates;
-  wc.updates += (unsigned)pr.updates;
+  int first_pass = 1;
+  if constexpr (WARM && !SEQ && CT != kConsNone) {
+    if (net) {
+      net_correction_warp(*net, q1, dof, reinterpret_cast<float*>(S.cand), fcorr);
+      float e_warm = 0.f, e_plain = 0.f;
+#pragma unroll
+      for (int s = 0; s < WPL; ++s) {
+        const int i = lane + 32 * s;
+        if (i >= 1 && i < W) {
+          float qp[kMaxDof], qw[kMaxDof];
+          interp(q0, q1, i, W, dof, qp);
+          const float t = (float)i / (float)(W - 1);
+#pragma unroll
+          for (int k = 0; k < kMaxDof; ++k)
+            qw[k] = k < dof ? fminf(fmaxf(fmaf(t, fcorr[k], qp[k]), rb.j[k].lo), rb.j[k].hi) : 0.f;
+          ChainState ch;
+          TaskEval<CT> te;
+          chain(rb, qp, nullptr, ch);
+          te.eval(rb, cs, ch);
+          e_plain = fmaxf(e_plain, te.err_inf());
+          chain(rb, qw, nullptr, ch);
+          te.eval(rb, cs, ch);
+          e_warm = fmaxf(e_warm, te.err_inf());
+        }
+      }
+      const unsigned gate = 2u * (unsigned)(W - 1);
+      work.proj += gate;
+      wc.updates += gate;
+      wc.warm_tried += 1u;
+      first_pass = warp_max(e_warm) < warp_max(e_plain) ? 0 : 1;
+    }
+  }
+  for (int pass = first_pass; pass < 2; ++pass) {
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+      const int i = min(lane + 32 * s, W - 1);
+      interp(q0, q1, i, W, dof, q[s]);
+      if (WARM && pass == 0 && i > 0) {
+        const float t = (float)i / (float)(W - 1);
+#pragma unroll
+        for (int k = 0; k < kMaxDof; ++k)
+          if (k < dof) q[s][k] = fminf(fmaxf(fmaf(t, fcorr[k], q[s][k]), rb.j[k].lo), rb.j[k].hi);
+      }
+    }
+    if constexpr (SEQ)
+      pr = project_sequential<CT, WPL>(rb, cs, max_iters, q0, q1, q, W, tau);
+    else
+      pr = project_warp<CT, WPL>(rb, cs, pass == 0 ? warm_refine : max_iters, q, W, tau, S.wq);
+    __syncwarp();
+    work.proj += (unsigned)pr.updates;
+    wc.updates += (unsigned)pr.updates;
+    if (pass == 0 && pr.status == kValid) {
+      wc.warm_used += 1u;
+      break;
+    }
+  }
   if (pr.status != kValid) return kProjFail;
   const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc, true, !SEQ && CT != kConsNone);
   __syncwarp();
@@ -223,7 +283,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 
 // The planner for one problem, run by the whole CTA (one warp per worker). Shared memory
 // (robot tables, obstacles, per-warp scratch) is staged by the caller.
-template <int CT, int WPL, bool SEQ = false>
+template <int CT, int WPL, bool SEQ = false, bool WARM = false>
 __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
@@ -299,8 +359,12 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     }
     float q[WPL][kMaxDof];
     // the closing hop is checked as it stands: one Alg. 1 iteration
-    const int st = validate_motion<CT, WPL, SEQ>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
-                                            cur, q1, W, q);
+    // the learned form warm-starts extend motions only: connect steps and the closing hop
+    // head for a node on the manifold
+    const int st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
+                                                       obs, S, cur, q1, W, q,
+                                                       WARM && mode == 0 ? &a.net : nullptr,
+                                                       a.warm_refine, qe);
     wp += W;
     int add = 0, conn = 0;
     if (st == kValid) {
@@ -457,9 +521,9 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   }
 }
 
-template <int CT, int WPL, bool SEQ = false>
-__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
-                                             PlanArgs a) {
+template <int CT, int WPL, bool SEQ, bool WARM>
+__device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const SceneDev& shared_scene,
+                                                 const ConsDev& cs, const PlanArgs& a) {
   const int p = blockIdx.x;
   if (p >= a.n) return;
   const int warp = threadIdx.x >> 5;
@@ -482,7 +546,7 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
   const float4* obs = a.stage_obs ? s_obs : sc.obs;
   const CcShared S = cc_shared(smem, L, warp);
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
-  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
+  WorkCount wc{};
   const size_t wd = (size_t)W * dof;
   const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
   if (threadIdx.x == 0) {
@@ -502,8 +566,22 @@ __global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene,
     P.estride = (int)wd;
   }
   __syncthreads();
-  plan_problem<CT, WPL, SEQ>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
+  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
   wc.flush(a.work_counters);
+}
+
+template <int CT, int WPL, bool SEQ = false>
+__global__ void CPRRTC_PLAN_REGS plan_kernel(RobotDev rb, SceneDev shared_scene, ConsDev cs,
+                                             PlanArgs a) {
+  plan_kernel_body<CT, WPL, SEQ, false>(rb, shared_scene, cs, a);
+}
+
+// The learned form, held to two CTAs of 8 warps per SM (the network's evaluation otherwise
+// takes registers that halve the warps an SM holds).
+template <int CT, int WPL>
+__global__ void __launch_bounds__(256, 2) plan_warm_kernel(RobotDev rb, SceneDev shared_scene,
+                                                           ConsDev cs, PlanArgs a) {
+  plan_kernel_body<CT, WPL, false, true>(rb, shared_scene, cs, a);
 }
 
 // ---- persistent batch of uneven problems --------------------------------------------------
@@ -526,7 +604,7 @@ __global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTabl
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
   const CcShared S = cc_shared(smem, L, warp);
   float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
-  WorkCount wc{0u, 0u, 0u, 0u, 0u, 0u};
+  WorkCount wc{};
   const size_t MN = (size_t)a.max_nodes, ew = (size_t)b.max_W * 8;  // edge floats (max)
   const size_t slot = blockIdx.x;
   for (;;) {
@@ -612,8 +690,17 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
   return cudaGetLastError();
 }
 
-static const void* plan_fn(int ct, int W, bool sequential = false) {
+static const void* plan_fn(int ct, int W, bool sequential = false, bool warm = false) {
   const bool two = W > 32;
+  if (warm) {  // the learned form: roll-pitch and z-plane
+    if (ct == kConsRollPitch)
+      return two ? (const void*)plan_warm_kernel<kConsRollPitch, 2>
+                 : (const void*)plan_warm_kernel<kConsRollPitch, 1>;
+    if (ct == kConsZPlane)
+      return two ? (const void*)plan_warm_kernel<kConsZPlane, 2>
+                 : (const void*)plan_warm_kernel<kConsZPlane, 1>;
+    return nullptr;
+  }
   if (sequential) {  // the naive baseline's projection: roll-pitch and z-plane, W <= 32
     if (two) return nullptr;
     if (ct == kConsRollPitch) return (const void*)plan_kernel<kConsRollPitch, 1, true>;
@@ -636,9 +723,9 @@ static const void* plan_fn(int ct, int W, bool sequential = false) {
   }
 }
 
-int plan_max_workers(int cons_type, int W, bool sequential) {
+int plan_max_workers(int cons_type, int W, bool sequential, bool warm) {
   cudaFuncAttributes attr;
-  const void* fn = plan_fn(cons_type, W, sequential);
+  const void* fn = plan_fn(cons_type, W, sequential, warm);
   if (!fn) return 0;
   if (cudaFuncGetAttributes(&attr, fn) != cudaSuccess) {
     cudaGetLastError();
@@ -658,7 +745,7 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
   a.stage_obs = smem <= dev.smem_optin ? 1 : 0;
   if (!a.stage_obs) smem = plan_smem_bytes(rb, a.max_scene_f4, a.W, a.workers, false);
   if (smem > dev.smem_optin) return cudaErrorInvalidConfiguration;
-  const void* fn = plan_fn(cs.type, a.W, a.sequential != 0);
+  const void* fn = plan_fn(cs.type, a.W, a.sequential != 0, a.warm_refine > 0);
   if (!fn) return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -23,7 +23,7 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int dof = rb.dof, W = a.W;
   const CcShared S = cc_shared(smem, L, warp);
-  WorkCount work{0u, 0u, 0u, 0u, 0u, 0u};
+  WorkCount work{};
 
   for (int m = blockIdx.x * kValidateWarps + warp; m < a.n; m += gridDim.x * kValidateWarps) {
     float q0[kMaxDof], q1[kMaxDof];

@@ -219,3 +219,51 @@ def test_plan_with_sequential_projection(torch_cuda, oracle_mod):
     assert e.value.code == E_UNSUPPORTED
     print("sequential planner solved", checked, "of 8")
     ctx.close()
+
+
+def test_plan_learned_form_paths_are_valid(torch_cuda, oracle_mod):
+    """The planner's learned form (extend motions warm-started by the network, trained here on
+    oracle projections; plain Alg. 1 as judge and fallback): every returned path is
+    re-validated by the oracle, runs are deterministic, the network was evaluated on extend
+    motions and some warm-started segments were accepted; and it refuses to run without a
+    network for the robot."""
+    from paper_2505_06791_gb300 import capi
+    torch = torch_cuda
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, 12, 1900)
+    ctx = ctx_for(rb, c)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=500, workers=8, seed=13)
+    ctx.set_plan_warm_start(5)
+    ctx.set_scene_batch(scenes)
+    with pytest.raises(capi.CprrtcError) as e:   # no network yet
+        run_plan(torch, ctx, None, start, goal, prm)
+    assert e.value.code == capi.E_NOT_CONFIGURED
+    orc = oracle_mod.Oracle(rb, None, c)
+    q = S.uniform_configs(rb, 40000, 1901).astype(np.float32)
+    ok, qp, _ = orc.project_configs(q, 60, n_threads=os.cpu_count() or 4)
+    ctx.mlp_init(3)
+    ctx.mlp_train(torch.from_numpy(q[ok]).cuda(), torch.from_numpy(qp[ok].astype(np.float32)).cuda(),
+                  batch=512, epochs=15, lr=1e-3, seed=4)
+    ctx.work_counters(reset=True)
+    out = run_plan(torch, ctx, None, start, goal, prm)
+    cnt = ctx.work_counters(reset=True)
+    again = run_plan(torch, ctx, None, start, goal, prm)
+    PB.assert_same_plans(out, again, keys=("path_len", "path", "path_edges", "rounds", "waypoints", "work"))
+    assert cnt[6] > 0 and 0 < cnt[7] <= cnt[6], cnt
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
+    assert not issues, issues[:10]
+    assert checked == int((out["path_len"] > 0).sum()) >= 1
+    ctx.set_plan_warm_start(0)
+    plain = run_plan(torch, ctx, None, start, goal, prm)
+    print("learned solved", checked, "plain solved", int((plain["path_len"] > 0).sum()),
+          "warm tried", int(cnt[6]), "accepted", int(cnt[7]))
+    # the learned form is for roll-pitch and z-plane with the parallel projection
+    ctx.set_plan_warm_start(5)
+    ctx.set_constraint(S.no_constraint())
+    with pytest.raises(capi.CprrtcError) as e:
+        run_plan(torch, ctx, None, start, goal, prm)
+    assert e.value.code == capi.E_UNSUPPORTED
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.set_plan_warm_start(21)
+    assert e.value.code == capi.E_INVALID_ARG
+    ctx.close()
