@@ -414,6 +414,11 @@ typedef struct {
 /* Robot table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_ROBOTS; host pointers).
  * Errors: as cprrtc_set_robot, E_UNSUPPORTED for n beyond the maximum. */
 int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n);
+/* Self-collision frame pairs of robot `robot` of the table, as cprrtc_set_self_collision's
+ * frame_pairs for that robot's dof (n = (dof+1)^2; 0 or NULL: none): the uneven batch checks
+ * every motion of that robot's problems against them. cprrtc_set_robot_table clears every
+ * robot's pairs. Errors: E_INVALID_ARG (no such robot, wrong n). */
+int cprrtc_set_table_self_collision(cprrtc_ctx* ctx, int robot, const uint8_t* frame_pairs, int n);
 
 /* Constraint table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_CONSTRAINTS; host
  * array). Every entry is checked as cprrtc_set_constraint checks it; the context's own
@@ -553,10 +558,13 @@ int cprrtc_reset_timing(cprrtc_ctx* ctx);
  * (b, a) nonzero, a != b: the robot spheres of frames a and b are tested against each other,
  * touching counts as free; pairs on one frame are never tested). After cprrtc_validate's
  * collision check, motions that are valid or collide later get the first waypoint where
- * such a pair overlaps (status COLLISION, first_fail that waypoint). n = (dof+1)^2, or 0
- * (or frame_pairs NULL) to switch it off; set_robot switches it off. cprrtc_plan and
- * cprrtc_plan_static refuse to run while it is on (E_UNSUPPORTED); cprrtc_validate_ws and
- * the uneven batch do not test it. Errors: E_INVALID_ARG, E_NOT_CONFIGURED. */
+ * such a pair overlaps (status COLLISION, first_fail that waypoint). cprrtc_plan and
+ * cprrtc_plan_static check every motion they validate in the same way (waypoints 1..W-1,
+ * after its obstacles): a motion whose robot meets itself is not valid, so no returned path
+ * self-collides. n = (dof+1)^2, or 0 (or frame_pairs NULL) to switch it off; set_robot
+ * switches it off. cprrtc_validate_ws does not test it; the uneven batch takes each table
+ * robot's pairs from cprrtc_set_table_self_collision. Errors: E_INVALID_ARG,
+ * E_NOT_CONFIGURED. */
 int cprrtc_set_self_collision(cprrtc_ctx* ctx, const uint8_t* frame_pairs, int n);
 
 /* The projection the validation and the planner use: CPRRTC_PROJECTION_PARALLEL (Alg. 1,

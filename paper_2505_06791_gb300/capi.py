@@ -119,6 +119,7 @@ _SIGS = {
     "cprrtc_mlp_set_precision": [C.c_void_p, C.c_int],
     "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
     "cprrtc_set_plan_warm_start": [C.c_void_p, C.c_int],
+    "cprrtc_set_table_self_collision": [C.c_void_p, C.c_int, C.c_void_p, C.c_int],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
@@ -299,8 +300,17 @@ class Context:
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
 
+    def set_table_self_collision(self, robot: int, frame_pairs=None):
+        """Self-collision frame pairs of a robot of the batch's robot table (None: none)."""
+        if frame_pairs is None:
+            self._check(self._L.cprrtc_set_table_self_collision(self.h, int(robot), None, 0))
+            return
+        pm = np.ascontiguousarray(np.asarray(frame_pairs) != 0, np.uint8)
+        self._check(self._L.cprrtc_set_table_self_collision(self.h, int(robot), pm.ctypes.data, pm.size))
+
     def set_self_collision(self, frame_pairs=None):
-        """Self-collision test of cprrtc_validate: frame_pairs [(dof+1)][(dof+1)] 0/1 (None: off)."""
+        """Self-collision test of cprrtc_validate and the planner: frame_pairs
+        [(dof+1)][(dof+1)] 0/1 (None: off)."""
         if frame_pairs is None:
             self._check(self._L.cprrtc_set_self_collision(self.h, None, 0))
             return

@@ -64,6 +64,7 @@ struct cprrtc_ctx {
   unsigned long long* d_work = nullptr;
   // batch tables
   std::vector<RobotDev> tab_robots;
+  std::vector<SelfMask> tab_self;  // each table robot's self-collision frame pairs
   float4* d_tab_sph = nullptr;
   size_t tab_sph_cap = 0;
   int* d_tab_frm = nullptr;
@@ -347,8 +348,6 @@ std::vector<int> morton_order(const std::vector<std::array<double, 3>>& centres)
 // The planner kernel's registers bound its CTA size: with two waypoints per lane (W > 32)
 // fewer than the maximum 16 workers fit.
 int check_plan_workers(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, const char* who) {
-  if (ctx->self_on)
-    return fail(ctx, CPRRTC_E_UNSUPPORTED, std::string(who) + ": self-collision is checked by validate only");
   const bool seq = ctx->projection == CPRRTC_PROJECTION_SEQUENTIAL;
   if (seq && (pp->W > 32 || (ctx->cs.type != kConsRollPitch && ctx->cs.type != kConsZPlane)))
     return fail(ctx, CPRRTC_E_UNSUPPORTED,
@@ -1484,6 +1483,8 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
     a.net = mlp_view(ctx->mlp);
     a.warm_refine = ctx->plan_warm;
   }
+  a.self_on = ctx->self_on ? 1 : 0;
+  for (int f = 0; f <= kMaxDof; ++f) a.self_rows[f] = ctx->self_rows[f];
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;
@@ -1785,6 +1786,8 @@ extern "C" int cprrtc_plan_static(cprrtc_ctx* ctx, const float* start, const flo
     a.net = mlp_view(ctx->mlp);
     a.warm_refine = ctx->plan_warm;
   }
+  a.self_on = ctx->self_on ? 1 : 0;
+  for (int f = 0; f <= kMaxDof; ++f) a.self_rows[f] = ctx->self_rows[f];
   if (pp->use_scene_batch) {
     a.scene_obs = ctx->d_batch_obs;
     a.scenes = ctx->d_batch_tab;
@@ -1963,6 +1966,7 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
   }
   BatchTables T{};
   for (size_t i = 0; i < ctx->tab_robots.size(); ++i) T.robots[i] = ctx->tab_robots[i];
+  for (size_t i = 0; i < ctx->tab_self.size() && i < (size_t)kBatchMaxRobots; ++i) T.self[i] = ctx->tab_self[i];
   for (size_t i = 0; i < ctx->tab_cons.size(); ++i) T.cons[i] = ctx->tab_cons[i];
   if (!ctx->ev_fork) {
     if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
@@ -2075,6 +2079,34 @@ int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int
     tab[i].sphere_frame = ctx->d_tab_frm + off[i];
   }
   ctx->tab_robots = tab;
+  ctx->tab_self.assign(n, SelfMask{});  // frame pairs belong to the robots: set them again
+  return CPRRTC_OK;
+}
+
+// Frame pairs of an (n_frames x n_frames) 0/1 matrix as row masks (bit b of rows[a], a < b).
+static bool self_mask_of(const uint8_t* frame_pairs, int nf, SelfMask& m) {
+  m = SelfMask{};
+  for (int i = 0; i < nf; ++i)
+    for (int j = i + 1; j < nf; ++j)
+      if (frame_pairs[i * nf + j] || frame_pairs[j * nf + i]) {
+        m.rows[i] |= (unsigned short)(1u << j);
+        m.on = 1;
+      }
+  return m.on != 0;
+}
+
+int cprrtc_set_table_self_collision(cprrtc_ctx* ctx, int robot, const uint8_t* frame_pairs, int n) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (robot < 0 || robot >= (int)ctx->tab_robots.size())
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_table_self_collision: no such robot in the table");
+  if (n == 0 || !frame_pairs) {
+    ctx->tab_self[robot] = SelfMask{};
+    return CPRRTC_OK;
+  }
+  const int nf = ctx->tab_robots[robot].dof + 1;
+  if (n != nf * nf)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_table_self_collision: n must be (dof + 1)^2");
+  self_mask_of(frame_pairs, nf, ctx->tab_self[robot]);
   return CPRRTC_OK;
 }
 

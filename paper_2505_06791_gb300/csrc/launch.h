@@ -8,6 +8,13 @@
 
 namespace cprrtc {
 
+// Frame pairs whose spheres are tested against each other (self-collision): bit b of rows[a]
+// for a < b; `on` = 0 when none.
+struct SelfMask {
+  unsigned short rows[kMaxDof + 1];
+  int on;
+};
+
 constexpr int kValidateWarps = 4;  // warps (motions in flight) per CTA
 // updates, chains, transforms, sphere / box / capsule tests, warm-started motions tried and
 // accepted (the planner's learned form)
@@ -84,6 +91,9 @@ struct PlanArgs {
   // iterations the corrected segment gets before plain Alg. 1 takes over
   MlpView net;
   int warm_refine;
+  // self-collision of the robot: bit b of self_rows[a] (a < b) pairs frames a and b
+  unsigned short self_rows[kMaxDof + 1];
+  int self_on;
 };
 
 // Persistent batch of uneven planning problems (one launch).
@@ -93,6 +103,7 @@ constexpr int kBatchMaxCons = 8;
 struct BatchTables {
   RobotDev robots[kBatchMaxRobots];
   ConsDev cons[kBatchMaxCons];
+  SelfMask self[kBatchMaxRobots];  // each robot's self-collision frame pairs
 };
 
 struct BatchArgs {

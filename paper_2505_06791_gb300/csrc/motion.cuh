@@ -15,6 +15,7 @@
 #pragma once
 #include "collide.cuh"
 #include "kinematics.cuh"
+#include "launch.h"
 
 namespace cprrtc {
 
@@ -442,6 +443,70 @@ struct Frame {
     cz = fmaf(x2, lx, fmaf(y2, ly, fmaf(z2, lz, p2)));
   }
 };
+
+// Spheres of frames fa < fb of one waypoint (joint terms wq[0..dof), the collision check's
+// cache) against each other: true if two of them overlap (touching is free).
+static __device__ __noinline__ bool self_pair_spheres(const JointDev* jnt, const float4* sph,
+                                                      const int* foff, const float2* wq, int fa,
+                                                      int fb) {
+  Frame F, A;
+  F.identity();
+  A.identity();
+#pragma unroll 1
+  for (int f = 1; f <= fb; ++f) {
+    F.advance_cached(jnt[f - 1], wq[f - 1]);
+    if (f == fa) A = F;
+  }
+#pragma unroll 1
+  for (int sa = foff[fa]; sa < foff[fa + 1]; ++sa) {
+    const float4 la = sph[sa];
+    float ax, ay, az;
+    A.world(la.x, la.y, la.z, ax, ay, az);
+#pragma unroll 1
+    for (int sb = foff[fb]; sb < foff[fb + 1]; ++sb) {
+      const float4 lb = sph[sb];
+      float bx, by, bz;
+      F.world(lb.x, lb.y, lb.z, bx, by, bz);
+      const float dx = ax - bx, dy = ay - by, dz = az - bz, r = la.w + lb.w;
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r * r) return true;
+    }
+  }
+  return false;
+}
+
+// Self-collision of one waypoint: each paired frames' bounding spheres (padded) first, the
+// spheres only where those overlap. The predicates of the self-collision kernel of
+// cprrtc_validate (self_collide.cu). Out of line, with runtime loops and the frame centres
+// in a small per-thread array, so that the callers' register allocation does not grow.
+static __device__ __noinline__ bool self_hit_waypoint(int dof, const JointDev* jnt, const float4* bnd,
+                                                      const float4* sph, const int* foff,
+                                                      const float2* wq, SelfMask m) {
+  float4 c[kMaxDof + 1];  // frame bounding spheres in world coordinates {centre, radius}
+  Frame F;
+  F.identity();
+#pragma unroll 1
+  for (int f = 0; f <= dof; ++f) {
+    if (f > 0) F.advance_cached(jnt[f - 1], wq[f - 1]);
+    const float4 b = bnd[f];
+    float x, y, z;
+    F.world(b.x, b.y, b.z, x, y, z);
+    c[f] = make_float4(x, y, z, b.w);
+  }
+#pragma unroll 1
+  for (int fa = 0; fa < dof; ++fa) {
+    const unsigned rows = m.rows[fa];
+    if (!rows || c[fa].w < 0.f) continue;
+#pragma unroll 1
+    for (int fb = fa + 1; fb <= dof; ++fb) {
+      if (!((rows >> fb) & 1u) || c[fb].w < 0.f) continue;
+      const float dx = c[fa].x - c[fb].x, dy = c[fa].y - c[fb].y, dz = c[fa].z - c[fb].z;
+      const float rr = c[fa].w + c[fb].w;
+      if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= rr * rr) continue;
+      if (self_pair_spheres(jnt, sph, foff, wq, fa, fb)) return true;
+    }
+  }
+  return false;
+}
 
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll

@@ -201,7 +201,7 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
                                                const float* q1, int W,
                                                float (&q)[WPL][kMaxDof],
                                                const MlpView* net = nullptr, int warm_refine = 0,
-                                               float* fcorr = nullptr) {
+                                               float* fcorr = nullptr, const SelfMask* self = nullptr) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const float tau = step_threshold(cs, q0, q1, W, dof);
@@ -263,9 +263,21 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
     }
   }
   if (pr.status != kValid) return kProjFail;
-  const int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc, true, !SEQ && CT != kConsNone);
+  int ff = collide_motion<WPL>(rb, sc, obs, S, q, W, 1, true, wc, true, !SEQ && CT != kConsNone);
   __syncwarp();
   work.cc += (unsigned)(ff >= 0 ? ff : W - 1);
+  if (ff < 0 && self && self->on) {
+    // the robot against itself on waypoints 1..W-1 (joint terms in the collision cache)
+    bool h = false;
+#pragma unroll
+    for (int s = 0; s < WPL; ++s) {
+      const int i = lane + 32 * s;
+      if (i >= 1 && i < W && !h)
+        h = self_hit_waypoint(rb.dof, S.jnt, S.bnd, S.sph, S.foff, S.wq + i * 9, *self);
+    }
+    wc.chains += (unsigned)(W - 1);
+    if (__any_sync(kFull, h)) ff = 1;
+  }
   return ff >= 0 ? kCollision : kValid;
 }
 
@@ -288,7 +300,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
                                              const CcShared& S, PlanShared* sh,
-                                             WorkCount& wc) {
+                                             WorkCount& wc, const SelfMask& self) {
   const int p = P.p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int B = blockDim.x >> 5, dof = rb.dof, W = P.W;
@@ -364,7 +376,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     const int st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
                                                        obs, S, cur, q1, W, q,
                                                        WARM && mode == 0 ? &a.net : nullptr,
-                                                       a.warm_refine, qe);
+                                                       a.warm_refine, qe, &self);
     wp += W;
     int add = 0, conn = 0;
     if (st == kValid) {
@@ -566,7 +578,11 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
     P.estride = (int)wd;
   }
   __syncthreads();
-  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc);
+  SelfMask self;
+#pragma unroll
+  for (int f = 0; f <= kMaxDof; ++f) self.rows[f] = a.self_on ? a.self_rows[f] : (unsigned short)0;
+  self.on = a.self_on;
+  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self);
   wc.flush(a.work_counters);
 }
 
@@ -646,7 +662,8 @@ __global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTabl
     stage_robot(rb, smem, L);
     __syncthreads();
     const SceneDev sc = s_sc;  // in registers: the collision walk reads it in its inner loops
-    plan_problem<CT, WPL>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc);
+    const SelfMask self = T.self[s_robot];
+    plan_problem<CT, WPL>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc, self);
   }
   wc.flush(a.work_counters);
 }

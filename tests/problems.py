@@ -7,13 +7,13 @@ from paper_2505_06791_gb300 import synth as S
 
 
 def planning_problems(oracle_mod, robot, constraint, n, seed, counts=(100, 60, 40),
-                      clearance=1e-3):
+                      clearance=1e-3, self_pairs=None):
     scenes, starts, goals = [], [], []
     p = 0
     attempt = 0
     while p < n:
         sc = S.make_planning_scene(seed + 7919 * attempt + p, *counts)
-        orc = oracle_mod.Oracle(robot, sc, constraint)
+        orc = oracle_mod.Oracle(robot, sc, constraint, self_pairs=self_pairs)
         found = []
         for q in S.uniform_configs(robot, 60, seed + 104729 * attempt + p):
             if constraint.type != 0:
@@ -35,8 +35,9 @@ def planning_problems(oracle_mod, robot, constraint, n, seed, counts=(100, 60, 4
 
 
 def check_paths(oracle_mod, robot, constraint, scenes, start, goal, out, W, range_,
-                problems=None, slack=2e-6, contact=1e-5):
-    """Re-validates every returned path with the oracle; returns (#checked, list of issues)."""
+                problems=None, slack=2e-6, contact=1e-5, self_pairs=None):
+    """Re-validates every returned path with the oracle (with `self_pairs`, the robot's named
+    frame pairs count as obstacles too); returns (#checked, list of issues)."""
     to_np = lambda x: x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)  # noqa
     L = to_np(out["path_len"])
     path = to_np(out["path"])
@@ -48,7 +49,7 @@ def check_paths(oracle_mod, robot, constraint, scenes, start, goal, out, W, rang
         if n <= 0:
             continue
         checked += 1
-        orc = oracle_mod.Oracle(robot, scenes[p], constraint)
+        orc = oracle_mod.Oracle(robot, scenes[p], constraint, self_pairs=self_pairs)
         P = path[p, :n].astype(np.float64)
         if not (np.array_equal(path[p, 0], start[p].astype(np.float32)) and
                 np.array_equal(path[p, n - 1], goal[p].astype(np.float32))):

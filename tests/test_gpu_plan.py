@@ -267,3 +267,45 @@ def test_plan_learned_form_paths_are_valid(torch_cuda, oracle_mod):
         ctx.set_plan_warm_start(21)
     assert e.value.code == capi.E_INVALID_ARG
     ctx.close()
+
+
+def test_plan_with_self_collision(torch_cuda, oracle_mod):
+    """Self-collision inside the planners: with frame pairs two or more apart named, every
+    path cprrtc_plan returns is free of the robot's own spheres too (oracle re-validation
+    with the same pairs), and so is every path of the uneven batch whose table robot has the
+    pairs; the batch of one robot plans exactly as cprrtc_plan."""
+    torch = torch_cuda
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    pairs = S.self_pairs_gap(rb, 2)
+    n = 10
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, n, 2100, counts=(40, 20, 10),
+                                               self_pairs=pairs)
+    ctx = ctx_for(rb, c)
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=400, workers=8, seed=17)
+    ctx.set_self_collision(pairs)
+    out = run_plan(torch, ctx, scenes, start, goal, prm)
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3,
+                                     self_pairs=pairs)
+    assert not issues, issues[:10]
+    assert checked >= 1
+    # without the pairs the same problems may give paths through the robot itself
+    ctx.set_self_collision(None)
+    plain = run_plan(torch, ctx, None, start, goal, prm)
+    _, plain_issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, plain, 32, 0.3,
+                                     self_pairs=pairs)
+    print("self-aware solved", checked, "plain paths crossing the robot",
+          len({i[0] for i in plain_issues}))
+    # the uneven batch with the table robot's pairs: the same plans
+    ctx.set_robot_table([rb])
+    ctx.set_constraint_table([c])
+    ctx.set_table_self_collision(0, pairs)
+    s8 = torch.zeros((n, 8), device="cuda")
+    g8 = torch.zeros((n, 8), device="cuda")
+    s8[:, :7] = torch.from_numpy(start.astype(np.float32)).cuda()
+    g8[:, :7] = torch.from_numpy(goal.astype(np.float32)).cuda()
+    ob = ctx.plan_batch([(0, 0, p, 32) for p in range(n)], s8, g8, prm, edges=True)
+    torch.cuda.synchronize()
+    ob = {k: (v.cpu().numpy() if v is not None else None) for k, v in ob.items()}
+    for k in ("path_len", "rounds", "waypoints", "work"):
+        assert np.array_equal(ob[k], out[k]), k
+    ctx.close()
