@@ -742,7 +742,7 @@ def run_validate(args, world, rank, local):
     # less than one wave of 152 SMs)
     sweep = []
     with torch.cuda.stream(stream):
-        for n_s in VAL_SWEEP:
+        for n_s in [int(x) for x in args.sweep.split(",") if x]:
             a0 = manifold_starts_gpu(ctx, rb, n_s, 30_000 + 97 * rank)
             a1 = torch.from_numpy(S.uniform_configs(rb, n_s, 40_000 + 97 * rank).astype(np.float32)).to(dev)
             o_s = ctx.alloc_validate_outputs(n_s, W, a0)
@@ -1522,6 +1522,8 @@ def main():
     ap.add_argument("--max-rounds", type=int, default=None,
                     help="override the planner's round cap (small profiling runs)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--sweep", default=",".join(str(x) for x in VAL_SWEEP),
+                    help="validation workload: motion counts of the throughput sweep")
     ap.add_argument("--learned", type=int, default=1,
                     help="planner workload: also time the learned form (trains the network first)")
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
@@ -1532,6 +1534,7 @@ def main():
     args = ap.parse_args()
     if args.max_rounds is not None:
         PLAN_PARAMS["max_rounds"] = args.max_rounds
+        BATCH_PARAMS["max_rounds"] = args.max_rounds
     world, rank, local = init_dist()
     if args.impl == "reference":
         fn = reference_arm_plan if args.workload == "plan" else reference_arm

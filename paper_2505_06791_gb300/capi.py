@@ -169,6 +169,18 @@ def lib():
     return _lib
 
 
+def _need(x, dtype, what="array"):
+    """x (numpy array or torch tensor, or None) must hold `dtype` elements ('float32', 'int32',
+    'uint8', 'int64'): the library reads the bytes as that type, so a float64 array would be
+    misread, not converted."""
+    if x is None:
+        return x
+    name = str(x.dtype).replace("torch.", "")
+    if name != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {name}")
+    return x
+
+
 def _ptr(x):
     """Address of a numpy array or torch tensor (None -> NULL)."""
     if x is None:
@@ -602,8 +614,18 @@ class Context:
 
 # ---- functions under the C names (pointer marshalling only) ----
 
+def _plan_io(start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work):
+    for x, t, w in ((start, "float32", "start"), (goal, "float32", "goal"),
+                    (path_len, "int32", "path_len"), (path, "float32", "path"),
+                    (path_edges, "float32", "path_edges"), (rounds, "int32", "rounds"),
+                    (waypoints, "int64", "waypoints"), (plan_ms, "float32", "plan_ms"),
+                    (work, "int64", "work")):
+        _need(x, t, w)
+
+
 def cprrtc_plan(h, start, goal, n, params, path_len, path, path_edges, rounds, waypoints,
                 plan_ms, work):
+    _plan_io(start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work)
     return lib().cprrtc_plan(h, _ptr(start), _ptr(goal), n, C.byref(params), _ptr(path_len),
                              _ptr(path), _ptr(path_edges), _ptr(rounds), _ptr(waypoints),
                              _ptr(plan_ms), _ptr(work))
@@ -611,6 +633,7 @@ def cprrtc_plan(h, start, goal, n, params, path_len, path, path_edges, rounds, w
 
 def cprrtc_plan_static(h, start, goal, n, params, path_len, path, path_edges, rounds,
                        waypoints, plan_ms, work):
+    _plan_io(start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work)
     return lib().cprrtc_plan_static(h, _ptr(start), _ptr(goal), n, C.byref(params),
                                     _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
                                     _ptr(waypoints), _ptr(plan_ms), _ptr(work))
@@ -618,6 +641,7 @@ def cprrtc_plan_static(h, start, goal, n, params, path_len, path, path_edges, ro
 
 def cprrtc_plan_batch(h, problems, n, start, goal, params, tuning, path_len, path, path_edges,
                       rounds, waypoints, plan_ms, work):
+    _plan_io(start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work)
     return lib().cprrtc_plan_batch(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
                                    C.byref(params), C.addressof(tuning) if tuning else None,
                                    _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
@@ -625,6 +649,8 @@ def cprrtc_plan_batch(h, problems, n, start, goal, params, tuning, path_len, pat
 
 
 def cprrtc_autotune_batch(h, problems, n, start, goal, params, trial_rounds, out):
+    _need(start, "float32", "start")
+    _need(goal, "float32", "goal")
     return lib().cprrtc_autotune_batch(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
                                        C.byref(params), trial_rounds,
                                        C.addressof(out) if out is not None else None)
@@ -632,6 +658,7 @@ def cprrtc_autotune_batch(h, problems, n, start, goal, params, trial_rounds, out
 
 def cprrtc_batch_capture(h, problems, n, start, goal, params, tuning, path_len, path, path_edges,
                          rounds, waypoints, plan_ms, work):
+    _plan_io(start, goal, path_len, path, path_edges, rounds, waypoints, plan_ms, work)
     return lib().cprrtc_batch_capture(h, C.addressof(problems), n, _ptr(start), _ptr(goal),
                                       C.byref(params), C.addressof(tuning) if tuning else None,
                                       _ptr(path_len), _ptr(path), _ptr(path_edges), _ptr(rounds),
@@ -646,32 +673,51 @@ def cprrtc_philox(h, key0, key1, counters, n, out):
     return lib().cprrtc_philox(h, key0, key1, _ptr(counters), n, _ptr(out))
 
 
+def _validate_io(q_start, q_end, out_q, status, first_fail, iters, resid, warm_used=None):
+    for x, t, w in ((q_start, "float32", "q_start"), (q_end, "float32", "q_end"),
+                    (out_q, "float32", "out_q"), (status, "uint8", "status"),
+                    (first_fail, "int32", "first_fail"), (iters, "uint8", "iters"),
+                    (resid, "float32", "resid"), (warm_used, "uint8", "warm_used")):
+        _need(x, t, w)
+
+
 def cprrtc_validate(h, q_start, q_end, n, W, out_q, status, first_fail, iters, resid):
+    _validate_io(q_start, q_end, out_q, status, first_fail, iters, resid)
     return lib().cprrtc_validate(h, _ptr(q_start), _ptr(q_end), n, W, _ptr(out_q),
                                  _ptr(status), _ptr(first_fail), _ptr(iters), _ptr(resid))
 
 
 def cprrtc_validate_ws(h, q_start, q_end, n, W, refine_iters, out_q, status, first_fail, iters,
                        resid, warm_used):
+    _validate_io(q_start, q_end, out_q, status, first_fail, iters, resid, warm_used)
     return lib().cprrtc_validate_ws(h, _ptr(q_start), _ptr(q_end), n, W, refine_iters,
                                     _ptr(out_q), _ptr(status), _ptr(first_fail), _ptr(iters),
                                     _ptr(resid), _ptr(warm_used))
 
 
 def cprrtc_mlp_grad(h, q, t, rows, grads, loss):
+    for x, w in ((q, "q"), (t, "t"), (grads, "grads"), (loss, "loss")):
+        _need(x, "float32", w)
     return lib().cprrtc_mlp_grad(h, _ptr(q), _ptr(t), rows, _ptr(grads), _ptr(loss))
 
 
 def cprrtc_mlp_train(h, q, t, n, batch, epochs, lr, seed, loss_per_epoch):
+    for x, w in ((q, "q"), (t, "t"), (loss_per_epoch, "loss_per_epoch")):
+        _need(x, "float32", w)
     return lib().cprrtc_mlp_train(h, _ptr(q), _ptr(t), n, batch, epochs, lr, seed,
                                   _ptr(loss_per_epoch))
 
 
 def cprrtc_mlp_infer(h, q, rows, q_out):
+    _need(q, "float32", "q")
+    _need(q_out, "float32", "q_out")
     return lib().cprrtc_mlp_infer(h, _ptr(q), rows, _ptr(q_out))
 
 
 def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
+    for x, t, w in ((q_in, "float32", "q_in"), (q_out, "float32", "q_out"), (ok, "uint8", "ok"),
+                    (resid, "float32", "resid")):
+        _need(x, t, w)
     return lib().cprrtc_project_configs(h, _ptr(q_in), n, max_iters, _ptr(q_out), _ptr(ok),
                                         _ptr(resid))
 

@@ -88,7 +88,10 @@ __device__ __forceinline__ int nearest_warp(const float* __restrict__ nodes, int
   // smallest distance, then the smallest index holding it (distances are >= 0, so their
   // bit patterns order like the values)
   const int kb = __reduce_min_sync(kFull, __float_as_int(best));
-  return __reduce_min_sync(kFull, __float_as_int(best) == kb ? bi : 0x7fffffff);
+  const int r = __reduce_min_sync(kFull, __float_as_int(best) == kb ? bi : 0x7fffffff);
+  // no finite distance (configurations out of any sensible range, or NaN): node 0, so that
+  // the index always lies in the tree
+  return r < count ? r : 0;
 }
 
 // dst[0..7] = src[0..dof) padded with zeros (lanes 0..7), then the warp synchronises.
