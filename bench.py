@@ -1359,9 +1359,9 @@ def run_warmstart(args, world, rank, local):
                        "infer_ms_per_step": infer_avg_s * 1e3,
                        "validate_ms_per_step": vk_ms / max(vk_launches, 1)},
         "planner_like_motions": short,
-        "training": {"pairs": int(q_tr.shape[0]), "pair_generation_s": pairs_s,
+        "training": {"pairs": WS_TRAIN, "pair_generation_s": pairs_s,
                      "epochs": args.train_epochs, "batch": 1024, "lr": 1e-3, "train_s": train_s,
-                     "samples_per_s": args.train_epochs * q_tr.shape[0] / train_s,
+                     "samples_per_s": args.train_epochs * WS_TRAIN / train_s,
                      "loss_first_last_epoch": [float(losses[0]), float(losses[-1])],
                      "heldout_loss_init_trained": [held0, held1],
                      "heldout_zero_prediction_loss": zero_loss,
