@@ -67,6 +67,7 @@ constexpr int kEpiFirst = 4, kEpiWarpsCc = CPRRTC_CC_EPI_WARPS;
 constexpr int kEpiCols = 256 / (kEpiWarpsCc / 4);
 constexpr int kProdWarp = kEpiFirst + kEpiWarpsCc, kMmaWarpCc = kProdWarp + 1;
 constexpr int kCcThreads = 32 * (kMmaWarpCc + 1);
+static_assert(kCcThreads * 88 <= 65536, "the register cap of gemm_cc_kernel must fit one CTA per SM");
 static_assert(kEpiWarpsCc % 4 == 0 && kEpiCols % 64 == 0, "epilogue loads go in pairs of 32 columns");
 constexpr int kCcStages = 4;
 constexpr int kChunkBytes = 32768;
@@ -207,7 +208,9 @@ __device__ __forceinline__ void put(uint8_t* tile, int row, int col, float v) {
 }
 
 template <int TF32>
-__global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, GemmCcArgs a) {
+// 88 registers: the most a CTA of kCcThreads (704) threads can hold in 8-register steps
+// (88 x 704 <= 65536); the compiler's own choice for one such CTA per SM was 80 with spills.
+__global__ void __maxnreg__(88) gemm_cc_kernel(RobotDev rb, GemmCcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = saddr(sm);

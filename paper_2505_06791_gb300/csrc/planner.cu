@@ -373,9 +373,9 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       copy_cfg(q1, qt, dof);
     }
     float q[WPL][kMaxDof];
-    // the closing hop is checked as it stands: one Alg. 1 iteration
-    // the learned form warm-starts extend motions only: connect steps and the closing hop
-    // head for a node on the manifold
+    // the closing hop is checked as it stands (one Alg. 1 iteration); the learned form
+    // warm-starts extend motions only: connect steps and the closing hop head for a node on
+    // the manifold
     const int st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
                                                        obs, S, cur, q1, W, q,
                                                        WARM && mode == 0 ? &a.net : nullptr,

@@ -8,9 +8,9 @@ namespace cprrtc {
 // Robot tables and each warp's collision scratch live in shared memory; the obstacle
 // stream is staged there too when it fits (coalesced float4 copies), else read from
 // global memory through L1. The first colliding waypoint is exact (no early exit).
-// (No __launch_bounds__: with it, ptxas caps registers low enough to spill here.)
-template <int CT, int WPL, bool SEQ = false>
-__global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
+template <int CT, int WPL, bool SEQ>
+__device__ __forceinline__ void validate_body(const RobotDev& rb, const SceneDev& sc, const ConsDev& cs,
+                                              const ValidateArgs& a) {
   extern __shared__ __align__(16) char smem[];
   const int n4 = sc.n_float4();
   const SmemLayout L(a.stage_obs ? n4 : 0, rb.n_spheres, a.W, kValidateWarps, 0);
@@ -129,6 +129,21 @@ __global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateAr
   work.flush(a.work_counters);
 }
 
+// Most instantiations get the compiler's register choice (a cap of 128 spills them). The
+// roll-pitch kernel with one waypoint per lane (the batched validation of configuration 1)
+// fits 128 registers without spilling, so it is held to four 4-warp CTAs per SM instead of
+// the three its 150 registers allow: more warps to hide its dependent-instruction latency.
+template <int CT, int WPL, bool SEQ = false>
+__global__ void validate_kernel(RobotDev rb, SceneDev sc, ConsDev cs, ValidateArgs a) {
+  validate_body<CT, WPL, SEQ>(rb, sc, cs, a);
+}
+
+template <int CT>
+__global__ void __launch_bounds__(kValidateWarps * 32, 4) validate_kernel_4(RobotDev rb, SceneDev sc,
+                                                                             ConsDev cs, ValidateArgs a) {
+  validate_body<CT, 1, false>(rb, sc, cs, a);
+}
+
 // One thread per configuration: damped steps until ||E_task||_inf < tol_task.
 template <int CT>
 __global__ void project_configs_kernel(RobotDev rb, ConsDev cs, const float* __restrict__ q_in,
@@ -181,7 +196,7 @@ static const void* validate_fn(int ct, int W, bool sequential) {
   }
   switch (ct) {
     case kConsRollPitch:
-      return two ? (const void*)validate_kernel<kConsRollPitch, 2> : (const void*)validate_kernel<kConsRollPitch, 1>;
+      return two ? (const void*)validate_kernel<kConsRollPitch, 2> : (const void*)validate_kernel_4<kConsRollPitch>;
     case kConsZPlane:
       return two ? (const void*)validate_kernel<kConsZPlane, 2> : (const void*)validate_kernel<kConsZPlane, 1>;
     case kConsLine:
