@@ -119,12 +119,11 @@ int fail(cprrtc_ctx* ctx, int code, const std::string& msg) {
 
 int cuda_fail(cprrtc_ctx* ctx, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-  if (e == cudaErrorMemoryAllocation) {
-    // A failed allocation is not sticky; clear it so that the next launch check of this
-    // thread does not report it again.
-    cudaGetLastError();
-    return fail(ctx, CPRRTC_E_OOM, m);
-  }
+  // a failed launch (resources, configuration) leaves the runtime's last-error state set; a
+  // later call's launch check would report it again, so it is consumed here (sticky errors,
+  // which end the context, are not cleared by this)
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, CPRRTC_E_OOM, m);
   return fail(ctx, CPRRTC_E_CUDA, m);
 }
 

@@ -67,7 +67,6 @@ constexpr int kEpiFirst = 4, kEpiWarpsCc = CPRRTC_CC_EPI_WARPS;
 constexpr int kEpiCols = 256 / (kEpiWarpsCc / 4);
 constexpr int kProdWarp = kEpiFirst + kEpiWarpsCc, kMmaWarpCc = kProdWarp + 1;
 constexpr int kCcThreads = 32 * (kMmaWarpCc + 1);
-static_assert(kCcThreads * 88 <= 65536, "the register cap of gemm_cc_kernel must fit one CTA per SM");
 static_assert(kEpiWarpsCc % 4 == 0 && kEpiCols % 64 == 0, "epilogue loads go in pairs of 32 columns");
 constexpr int kCcStages = 4;
 constexpr int kChunkBytes = 32768;
@@ -208,9 +207,10 @@ __device__ __forceinline__ void put(uint8_t* tile, int row, int col, float v) {
 }
 
 template <int TF32>
-// 88 registers: the most a CTA of kCcThreads (704) threads can hold in 8-register steps
-// (88 x 704 <= 65536); the compiler's own choice for one such CTA per SM was 80 with spills.
-__global__ void __maxnreg__(88) gemm_cc_kernel(RobotDev rb, GemmCcArgs a) {
+// 80 registers (the compiler's choice, with a small spill): an SM splits its registers between
+// four sub-partitions of 16,384 each, and the 22 warps of a CTA put six warps on two of them,
+// so 6 x 32 x R <= 16,384 bounds R at 85, i.e. 80 in 8-register steps (88 fails to launch).
+__global__ void __launch_bounds__(kCcThreads, 1) gemm_cc_kernel(RobotDev rb, GemmCcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sb = saddr(sm);
