@@ -414,6 +414,17 @@ typedef struct {
 /* Robot table for cprrtc_plan_batch (1 <= n <= CPRRTC_BATCH_MAX_ROBOTS; host pointers).
  * Errors: as cprrtc_set_robot, E_UNSUPPORTED for n beyond the maximum. */
 int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n);
+/* The uneven batch's learned form (not in the paper): a copy of the context's current network
+ * (cprrtc_mlp_init / cprrtc_mlp_train / cprrtc_mlp_load, trained for the table robot's dof
+ * and that constraint) for the problems of table robot `robot` and table constraint
+ * `constraint` (ROLL_PITCH or Z_PLANE). With cprrtc_set_plan_warm_start on, cprrtc_plan_batch,
+ * cprrtc_autotune_batch and cprrtc_batch_capture warm-start the extend motions of those
+ * problems as cprrtc_plan does; problems of a pair without a network plan as without it.
+ * Adopting again for a pair replaces its copy; cprrtc_set_robot_table and
+ * cprrtc_set_constraint_table drop every copy. Errors: E_INVALID_ARG (no such robot or
+ * constraint), E_UNSUPPORTED (another constraint type), E_NOT_CONFIGURED (no network, or one
+ * of another dof), E_CUDA, E_OOM. */
+int cprrtc_batch_adopt_network(cprrtc_ctx* ctx, int robot, int constraint);
 /* Self-collision frame pairs of robot `robot` of the table, as cprrtc_set_self_collision's
  * frame_pairs for that robot's dof (n = (dof+1)^2; 0 or NULL: none): the uneven batch checks
  * every motion of that robot's problems against them. cprrtc_set_robot_table clears every

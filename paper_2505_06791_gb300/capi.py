@@ -120,6 +120,7 @@ _SIGS = {
     "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
     "cprrtc_set_plan_warm_start": [C.c_void_p, C.c_int],
     "cprrtc_set_table_self_collision": [C.c_void_p, C.c_int, C.c_void_p, C.c_int],
+    "cprrtc_batch_adopt_network": [C.c_void_p, C.c_int, C.c_int],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_get_params": [C.c_void_p, C.c_void_p, C.c_int64],
     "cprrtc_mlp_save": [C.c_void_p, C.c_char_p],
@@ -311,6 +312,10 @@ class Context:
         out = np.zeros(8, np.int64)
         self._check(self._L.cprrtc_work_counters(self.h, out.ctypes.data, int(reset)))
         return out
+
+    def batch_adopt_network(self, robot: int, constraint: int):
+        """The context's network for the uneven batch's problems of (robot, constraint)."""
+        self._check(self._L.cprrtc_batch_adopt_network(self.h, int(robot), int(constraint)))
 
     def set_table_self_collision(self, robot: int, frame_pairs=None):
         """Self-collision frame pairs of a robot of the batch's robot table (None: none)."""

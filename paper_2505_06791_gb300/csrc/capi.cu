@@ -65,6 +65,10 @@ struct cprrtc_ctx {
   // batch tables
   std::vector<RobotDev> tab_robots;
   std::vector<SelfMask> tab_self;  // each table robot's self-collision frame pairs
+  // the uneven batch's learned form: a copy of a trained network per (table robot,
+  // constraint) pair, [robot * kBatchMaxCons + constraint] (buffer null: none)
+  void* batch_net_buf[kBatchMaxRobots * kBatchMaxCons] = {};
+  MlpView batch_net[kBatchMaxRobots * kBatchMaxCons] = {};
   float4* d_tab_sph = nullptr;
   size_t tab_sph_cap = 0;
   int* d_tab_frm = nullptr;
@@ -530,6 +534,7 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
   cudaFree(ctx->d_plan);
   cudaFree(ctx->d_work);
   cudaFree(ctx->d_tab_sph);
+  for (void* b : ctx->batch_net_buf) cudaFree(b);
   cudaFree(ctx->d_tab_frm);
   mlp_destroy(ctx->mlp);
   cudaFree(ctx->d_warm);
@@ -1905,7 +1910,7 @@ ClassLaunch class_launch(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuni
     L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, false);
   }
   if (L.smem > ctx->dev.smem_optin) return L;
-  const int occ = plan_batch_occupancy(c, L.workers, L.smem);
+  const int occ = plan_batch_occupancy(c, L.workers, L.smem, ctx->plan_warm > 0);
   if (occ < 1) return L;
   const int per_sm = t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
   L.grid = std::min(nc, per_sm * ctx->dev.sm_count);
@@ -1966,6 +1971,9 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
   BatchTables T{};
   for (size_t i = 0; i < ctx->tab_robots.size(); ++i) T.robots[i] = ctx->tab_robots[i];
   for (size_t i = 0; i < ctx->tab_self.size() && i < (size_t)kBatchMaxRobots; ++i) T.self[i] = ctx->tab_self[i];
+  if (ctx->plan_warm > 0)
+    for (int r = 0; r < kBatchMaxRobots; ++r)
+      for (int c = 0; c < kBatchMaxCons; ++c) T.nets[r][c] = ctx->batch_net[r * kBatchMaxCons + c];
   for (size_t i = 0; i < ctx->tab_cons.size(); ++i) T.cons[i] = ctx->tab_cons[i];
   if (!ctx->ev_fork) {
     if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
@@ -2021,6 +2029,7 @@ PlanArgs batch_base(cprrtc_ctx* ctx, const cprrtc_plan_params* pp, int n) {
   a.scene_obs = ctx->d_batch_obs;
   a.scenes = ctx->d_batch_tab;
   a.work_counters = ctx->d_work;
+  a.warm_refine = ctx->plan_warm;
   return a;
 }
 
@@ -2051,6 +2060,11 @@ void stage_batch_io(Staging& st, PlanArgs& a, size_t N, int max_path, int max_W,
 
 extern "C" {
 
+// Drops the uneven batch's networks (their buffers are kept for reuse).
+static void clear_batch_nets(cprrtc_ctx* ctx) {
+  for (auto& v : ctx->batch_net) v = MlpView{};
+}
+
 int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int n) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (!robots || n < 1) return fail(ctx, CPRRTC_E_INVALID_ARG, "robot table: empty");
@@ -2079,6 +2093,7 @@ int cprrtc_set_robot_table(cprrtc_ctx* ctx, const cprrtc_robot_desc* robots, int
   }
   ctx->tab_robots = tab;
   ctx->tab_self.assign(n, SelfMask{});  // frame pairs belong to the robots: set them again
+  clear_batch_nets(ctx);                // so do the networks
   return CPRRTC_OK;
 }
 
@@ -2128,6 +2143,57 @@ int cprrtc_set_constraint_table(cprrtc_ctx* ctx, const cprrtc_constraint* cons, 
   }
   ctx->cs = saved;
   ctx->tab_cons = tab;
+  clear_batch_nets(ctx);  // networks belong to (robot, constraint) pairs of the tables
+  return CPRRTC_OK;
+}
+
+int cprrtc_batch_adopt_network(cprrtc_ctx* ctx, int robot, int constraint) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (robot < 0 || robot >= (int)ctx->tab_robots.size() || constraint < 0 ||
+      constraint >= (int)ctx->tab_cons.size())
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "batch_adopt_network: no such robot or constraint in the tables");
+  const int ct = ctx->tab_cons[constraint].type;
+  if (ct != kConsRollPitch && ct != kConsZPlane)
+    return fail(ctx, CPRRTC_E_UNSUPPORTED, "batch_adopt_network: the learned form plans with ROLL_PITCH or Z_PLANE");
+  if (!ctx->mlp || mlp_dof(ctx->mlp) != ctx->tab_robots[robot].dof)
+    return fail(ctx, CPRRTC_E_NOT_CONFIGURED,
+                "batch_adopt_network: the context's network must be for the table robot's dof");
+  DeviceGuard g(ctx->device);
+  const MlpView src = mlp_view(ctx->mlp);
+  // one buffer: layer 0..2 transposes (BF16 [16][256], [256][256] x 2), layer 3 (BF16 [16][256]),
+  // biases (FP32 3 x 256 + 16)
+  const size_t b0 = 16 * 256 * 2, b1 = 256 * 256 * 2, b3 = 16 * 256 * 2, bb = (3 * 256 + 16) * 4;
+  const size_t total = b0 + 2 * b1 + b3 + bb;
+  const int slot = robot * kBatchMaxCons + constraint;
+  char* buf = static_cast<char*>(ctx->batch_net_buf[slot]);
+  cudaError_t e = cudaSuccess;
+  if (!buf) {
+    e = cudaMalloc(reinterpret_cast<void**>(&buf), total);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch_adopt_network: allocation");
+    ctx->batch_net_buf[slot] = buf;
+  }
+  MlpView v{};
+  v.wt[0] = buf;
+  v.wt[1] = buf + b0;
+  v.wt[2] = buf + b0 + b1;
+  v.w3 = buf + b0 + 2 * b1;
+  float* bias = reinterpret_cast<float*>(buf + b0 + 2 * b1 + b3);
+  v.b[0] = bias;
+  v.b[1] = bias + 256;
+  v.b[2] = bias + 512;
+  v.b[3] = bias + 768;
+  v.dof = src.dof;
+  const void* from[4] = {src.wt[0], src.wt[1], src.wt[2], src.w3};
+  const void* to[4] = {v.wt[0], v.wt[1], v.wt[2], v.w3};
+  const size_t bytes[4] = {b0, b1, b1, b3};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(const_cast<void*>(to[i]), from[i], bytes[i], cudaMemcpyDeviceToDevice, ctx->stream);
+  for (int l = 0; l < 4 && e == cudaSuccess; ++l)
+    e = cudaMemcpyAsync(const_cast<float*>(v.b[l]), src.b[l], (l < 3 ? 256 : src.dof) * sizeof(float),
+                        cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch_adopt_network: copy");
+  ctx->batch_net[slot] = v;
   return CPRRTC_OK;
 }
 
@@ -2222,7 +2288,7 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
       t.ctas_per_sm[c] = 0;
       const ClassLaunch full = class_launch(ctx, bp, t, pp->workers, c);
       if (!full.on || full.stage != stage) continue;  // staging did not fit: tried as L1
-      const int occ = plan_batch_occupancy(c, full.workers, full.smem);
+      const int occ = plan_batch_occupancy(c, full.workers, full.smem, ctx->plan_warm > 0);
       for (int ctas = 1; ctas <= std::min(occ, 4) && !rc; ++ctas) {
         t.ctas_per_sm[c] = ctas;
         cudaEventRecord(e0, ctx->stream);

@@ -104,6 +104,8 @@ struct BatchTables {
   RobotDev robots[kBatchMaxRobots];
   ConsDev cons[kBatchMaxCons];
   SelfMask self[kBatchMaxRobots];  // each robot's self-collision frame pairs
+  // the learned form's network of each (robot, constraint) pair (dof 0: none)
+  MlpView nets[kBatchMaxRobots][kBatchMaxCons];
 };
 
 struct BatchArgs {
@@ -124,7 +126,7 @@ struct BatchArgs {
 // Problem classes: 2 * constraint type + (W > 32).
 constexpr int kBatchClasses = 6;
 size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage);
-int plan_batch_occupancy(int cls, int workers, size_t smem);
+int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm = false);
 cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
                               cudaStream_t stream);
 

@@ -303,7 +303,8 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
                                              const CcShared& S, PlanShared* sh,
-                                             WorkCount& wc, const SelfMask& self) {
+                                             WorkCount& wc, const SelfMask& self,
+                                             const MlpView* net = nullptr) {
   const int p = P.p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int B = blockDim.x >> 5, dof = rb.dof, W = P.W;
@@ -378,7 +379,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     // the manifold
     const int st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
                                                        obs, S, cur, q1, W, q,
-                                                       WARM && mode == 0 ? &a.net : nullptr,
+                                                       WARM && mode == 0 ? net : nullptr,
                                                        a.warm_refine, qe, &self);
     wp += W;
     int add = 0, conn = 0;
@@ -585,7 +586,7 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
 #pragma unroll
   for (int f = 0; f <= kMaxDof; ++f) self.rows[f] = a.self_on ? a.self_rows[f] : (unsigned short)0;
   self.on = a.self_on;
-  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self);
+  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self, WARM ? &a.net : nullptr);
   wc.flush(a.work_counters);
 }
 
@@ -611,8 +612,10 @@ __global__ void __launch_bounds__(256, 2) plan_warm_kernel(RobotDev rb, SceneDev
 // order (longest expected first). Each problem names its robot, constraint, scene and W; the
 // CTA stages that robot and scene into shared memory and runs plan_problem. Trees live in a
 // per-CTA scratch slot reused across problems.
-template <int CT, int WPL>
-__global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTables T) {
+// With WARM (the learned form), problems whose robot and constraint have a network in the
+// table warm-start their extend motions with it; the others plan as without it.
+template <int CT, int WPL, bool WARM>
+__device__ __forceinline__ void plan_batch_body(const BatchArgs& b, const BatchTables& T) {
   extern __shared__ __align__(16) char smem[];
   __shared__ SceneDev s_sc;
   __shared__ int s_t, s_robot, s_cons;
@@ -666,12 +669,35 @@ __global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTabl
     __syncthreads();
     const SceneDev sc = s_sc;  // in registers: the collision walk reads it in its inner loops
     const SelfMask self = T.self[s_robot];
-    plan_problem<CT, WPL>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc, self);
+    const MlpView* net = WARM && T.nets[s_robot][s_cons].dof ? &T.nets[s_robot][s_cons] : nullptr;
+    plan_problem<CT, WPL, false, WARM>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc,
+                                       self, net);
   }
   wc.flush(a.work_counters);
 }
 
-static const void* plan_batch_fn(int cls) {
+template <int CT, int WPL>
+__global__ void plan_batch_kernel(BatchArgs b, const __grid_constant__ BatchTables T) {
+  plan_batch_body<CT, WPL, false>(b, T);
+}
+
+// The learned form of a class, held to two CTAs of 8 warps per SM like plan_warm_kernel.
+template <int CT, int WPL>
+__global__ void __launch_bounds__(256, 2) plan_batch_warm_kernel(BatchArgs b,
+                                                                 const __grid_constant__ BatchTables T) {
+  plan_batch_body<CT, WPL, true>(b, T);
+}
+
+static const void* plan_batch_fn(int cls, bool warm = false) {
+  if (warm) {  // the learned form of the roll-pitch and z-plane classes
+    switch (cls) {
+      case 2: return (const void*)plan_batch_warm_kernel<kConsRollPitch, 1>;
+      case 3: return (const void*)plan_batch_warm_kernel<kConsRollPitch, 2>;
+      case 4: return (const void*)plan_batch_warm_kernel<kConsZPlane, 1>;
+      case 5: return (const void*)plan_batch_warm_kernel<kConsZPlane, 2>;
+      default: break;
+    }
+  }
   switch (cls) {
     case 0: return (const void*)plan_batch_kernel<kConsNone, 1>;
     case 1: return (const void*)plan_batch_kernel<kConsNone, 2>;
@@ -686,8 +712,8 @@ size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers
   return SmemLayout(stage ? max_scene_f4 : 0, max_S, max_W, workers, sizeof(PlanShared)).total;
 }
 
-int plan_batch_occupancy(int cls, int workers, size_t smem) {
-  const void* fn = plan_batch_fn(cls);
+int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm) {
+  const void* fn = plan_batch_fn(cls, warm);
   int per_sm = 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * workers, smem) != cudaSuccess) {
@@ -701,7 +727,7 @@ cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int gr
                               cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
-  const void* fn = plan_batch_fn(cls);
+  const void* fn = plan_batch_fn(cls, b.a.warm_refine > 0);
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&b, const_cast<BatchTables*>(&T)};

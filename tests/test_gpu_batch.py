@@ -123,3 +123,60 @@ def test_batch_argument_errors(torch_cuda):
     out = ctx.plan_batch([(0, 0, 0, 16)], q, q, prm)
     assert out["path_len"][0] >= 2      # start == goal, empty scene, no constraint
     ctx.close()
+
+
+def test_batch_learned_form_equals_plan(torch_cuda, oracle_mod):
+    """The uneven batch's learned form: with the context's network (trained here on oracle
+    projections) adopted for its (robot, constraint) pair, a batch of one robot plans exactly
+    as cprrtc_plan's learned form; its paths are re-validated by the oracle; a pair without a
+    network plans as without the learned form; adopting for another dof is refused."""
+    import os
+    from paper_2505_06791_gb300.capi import Context, CprrtcError, E_NOT_CONFIGURED
+    torch = torch_cuda
+    rb, c = S.make_arm7(1), S.roll_pitch()
+    n = 8
+    scenes, start, goal = PB.planning_problems(oracle_mod, rb, c, n, 2300)
+    ctx = Context(0)
+    ctx.set_robot(rb)
+    ctx.set_constraint(c)
+    ctx.set_scene_batch(scenes)
+    orc = oracle_mod.Oracle(rb, None, c)
+    q = S.uniform_configs(rb, 30000, 2301).astype(np.float32)
+    ok, qp, _ = orc.project_configs(q, 60, n_threads=os.cpu_count() or 4)
+    ctx.mlp_init(5)
+    ctx.mlp_train(torch.from_numpy(q[ok]).cuda(), torch.from_numpy(qp[ok].astype(np.float32)).cuda(),
+                  batch=512, epochs=10, lr=1e-3, seed=6)
+    ctx.set_robot_table([rb, S.make_arm6(1)])
+    ctx.set_constraint_table([c])
+    with pytest.raises(CprrtcError) as e:   # the network is for 7 joints, robot 1 has 6
+        ctx.batch_adopt_network(1, 0)
+    assert e.value.code == E_NOT_CONFIGURED
+    prm = ctx.plan_params(range_=0.3, W=32, max_rounds=300, workers=8, seed=19)
+    s = torch.from_numpy(start.astype(np.float32)).cuda()
+    g = torch.from_numpy(goal.astype(np.float32)).cuda()
+    s8 = torch.zeros((n, 8), device="cuda")
+    g8 = torch.zeros((n, 8), device="cuda")
+    s8[:, :7] = s
+    g8[:, :7] = g
+    probs = [(0, 0, p, 32) for p in range(n)]
+    ctx.set_plan_warm_start(5)
+    plain_batch = to_np(ctx.plan_batch(probs, s8, g8, prm, edges=True))  # no network adopted yet
+    ctx.batch_adopt_network(0, 0)
+    ctx.work_counters(reset=True)
+    learned_batch = to_np(ctx.plan_batch(probs, s8, g8, prm, edges=True))
+    cnt = ctx.work_counters(reset=True)
+    learned_plan = to_np(ctx.plan(s, g, prm))
+    torch.cuda.synchronize()
+    assert cnt[6] > 0 and cnt[7] > 0, cnt
+    for k in ("path_len", "rounds", "waypoints", "work"):
+        assert np.array_equal(learned_batch[k], learned_plan[k]), k
+    ctx.set_plan_warm_start(0)
+    plain_plan = to_np(ctx.plan(s, g, prm))
+    for k in ("path_len", "rounds", "waypoints", "work"):
+        assert np.array_equal(plain_batch[k], plain_plan[k]), k
+    out = {"path_len": learned_batch["path_len"], "path": learned_batch["path"][:, :, :7],
+           "path_edges": learned_batch["path_edges"][:, :, :32, :7]}
+    checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
+    assert not issues, issues[:10]
+    assert checked >= 1
+    ctx.close()
