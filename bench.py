@@ -607,6 +607,68 @@ def run_batch(args, world, rank, local):
     for (r, c, sc, W) in probs:
         key = f"{['none', 'roll-pitch', 'z-plane'][c]}/W{W}"
         classes[key] = classes.get(key, 0) + 1
+    rounds_b = out["rounds"].cpu().numpy()
+    # what ends the replay: the problems that run longest (usually to the round cap)
+    slow = np.argsort(-ms)[:5]
+    critical = {"slowest_problem_ms": float(ms.max()), "step_ms": total_ms / args.steps,
+                "slowest": [{"class": f"{['none', 'roll-pitch', 'z-plane'][probs[p][1]]}/W{probs[p][3]}",
+                             "dof": int(robots[probs[p][0]].dof),
+                             "obstacles": int(len(scenes[probs[p][2]].sph) + len(scenes[probs[p][2]].box)
+                                              + len(scenes[probs[p][2]].cap)),
+                             "rounds": int(rounds_b[p]), "solved": bool(L[p] > 0),
+                             "plan_ms": float(ms[p])} for p in slow],
+                "note": "the replay lasts as long as its slowest problem's rounds: the step is "
+                        "bound by that critical path, and the SMs idle as the other problems end"}
+    learned = None
+    if args.learned:
+        with torch.cuda.stream(stream):
+            pairs = sorted({(r, c) for (r, c, sc_, W_) in probs if cons[c].type in (1, 2)})
+            t0 = time.perf_counter()
+            for (r, c) in pairs:   # one network per (robot, constraint), trained untimed
+                ctx.set_robot(robots[r])
+                ctx.set_constraint(cons[c])
+                train_warm_network(ctx, robots[r], 40 + 17 * r + 5 * c + 1000 * rank, dev,
+                                   args.train_epochs, stream)
+                ctx.batch_adopt_network(r, c)
+            train_total_s = time.perf_counter() - t0
+            ctx.set_plan_warm_start(WS_REFINE)
+            out_w = ctx.alloc_batch_outputs(len(probs), prm, max_W, start)
+            ctx.batch_capture(probs, start, goal, prm, out_w, tuning=tuning)
+            for _ in range(args.warmup):
+                ctx.batch_replay()
+            ctx.work_counters(reset=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.batch_replay()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            w_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), world)
+            wcnt = ctx.work_counters() / max(args.steps, 1)
+            ctx.set_plan_warm_start(0)
+        Lw = out_w["path_len"].cpu().numpy()
+        msw = out_w["plan_ms"].cpu().numpy()
+        sw = Lw > 0
+        learned = {
+            "ms_per_step": w_ms / args.steps,
+            "value": sum_over_ranks(int(out_w["waypoints"].sum().item()), world) * args.steps / (w_ms / 1e3),
+            "p50_plan_ms": float(np.percentile(msw[sw], 50)) if sw.any() else None,
+            "p99_plan_ms": float(np.percentile(msw[sw], 99)) if sw.any() else None,
+            "success_rate": float(sw.mean()),
+            "extend_motions_warm_started_per_step": float(wcnt[6]),
+            "warm_segments_accepted_per_step": float(wcnt[7]),
+            "networks": [{"robot_dof": int(robots[r].dof),
+                          "constraint": ["none", "roll-pitch", "z-plane"][cons[c].type]} for r, c in pairs],
+            "training_s": train_total_s,
+            "note": "one network per (robot, constraint) pair, trained on 2^20 pairs from "
+                    "cprrtc_project_configs; extend motions of those problems warm-started, "
+                    "plain Alg. 1 as judge and fallback; unconstrained problems unchanged",
+        }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -625,6 +687,12 @@ def run_batch(args, world, rank, local):
         "p50_plan_ms_all": float(np.percentile(ms, 50)),
         "p99_plan_ms_all": float(np.percentile(ms, 99)),
         "success_rate": float(solved.mean()),
+        "learned_vs_plain": {"plain": {"p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
+                                       "p99_plan_ms": float(np.percentile(ms[solved], 99)) if solved.any() else None,
+                                       "success_rate": float(solved.mean()),
+                                       "ms_per_step": total_ms / args.steps},
+                             "learned": learned},
+        "critical_path": critical,
         "waypoints_per_step": waypoints_step,
         "classes": classes,
         "tuning": tuning.as_dict(), "autotune_s": tune_s,
