@@ -586,6 +586,30 @@ def run_batch(args, world, rank, local):
     upd, chains, tf, ps, pb, pc = [float(x) for x in counters[:6]]
     flops = (upd * flops_waypoint_iter(round(mean_dof)) + chains * mean_dof * F_CHAIN_JOINT
              + tf * F_SPHERE_FK + ps * F_PAIR_SPHERE + pb * F_PAIR_BOX + pc * F_PAIR_CAPSULE)
+    # the autotuned launch shapes against the library's fixed default (as many CTAs as fit,
+    # obstacles staged when they fit, one warp per motion): same graph form, inputs and flush
+    from paper_2505_06791_gb300.capi import default_tuning
+    with torch.cuda.stream(stream):
+        out_d = ctx.alloc_batch_outputs(len(probs), prm, max_W, start)
+        ctx.batch_capture(probs, start, goal, prm, out_d, tuning=default_tuning())
+        ctx.batch_replay()
+        ev_d = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev_d[k][0].record(stream)
+            ctx.batch_replay()
+            ev_d[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    d_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev_d), world) / args.steps
+    same_d = all(np.array_equal(out_d[k].cpu().numpy(), out[k].cpu().numpy())
+                 for k in ("path_len", "rounds", "waypoints"))
+    vs_default = {"default_ms_per_step": d_ms, "autotuned_ms_per_step": total_ms / args.steps,
+                  "speedup": d_ms / (total_ms / args.steps), "identical_results": same_d}
+    del out_d
     # end to end through the C ABI with pinned host buffers
     h_start = start.cpu().pin_memory()
     h_goal = goal.cpu().pin_memory()
@@ -695,7 +719,7 @@ def run_batch(args, world, rank, local):
         "critical_path": critical,
         "waypoints_per_step": waypoints_step,
         "classes": classes,
-        "tuning": tuning.as_dict(), "autotune_s": tune_s,
+        "tuning": tuning.as_dict(), "autotune_s": tune_s, "autotuned_vs_default": vs_default,
         "e2e": {"value": waypoints_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * len(probs) * 8 * 4,
                 "d2h_bytes_per_step": sum(v.numel() * v.element_size()

@@ -446,12 +446,20 @@ typedef struct {
   int W;
 } cprrtc_problem;
 
-/* Launch shape of each problem class: CTAs per SM (0: as many as fit) and whether the class
- * stages its obstacles into shared memory (else they are read through L1). Neither changes
- * any result: a problem's search depends only on its own inputs and the plan parameters. */
+/* Launch shape of each problem class (class = 2 * constraint type + (W > 32)): CTAs per SM
+ * (0: as many as fit), whether the class stages its obstacles into shared memory (else they
+ * are read through L1), and warps per motion: 1, or 2 for a class of 33..64 waypoints (each
+ * worker's motion held by a warp pair, one waypoint per lane: Alg. 1 runs in step on both
+ * warps, each checks its own waypoints for collisions; plain form only, at most 8 workers;
+ * elsewhere, 0 or any other value means 1). None of them changes any result: a problem's
+ * search depends only on its own inputs and the plan parameters. Only the executed-work
+ * counts differ with warp pairs (cprrtc_work_counters, the `work` output): a pair's halves
+ * stop their collision walks when either finds a collision, so their collision work
+ * depends on timing. */
 typedef struct {
   int ctas_per_sm[CPRRTC_BATCH_CLASSES];
   int stage_obstacles[CPRRTC_BATCH_CLASSES];
+  int warps_per_motion[CPRRTC_BATCH_CLASSES];
 } cprrtc_tuning;
 
 /* Plans n problems of mixed robots, constraints, scenes and W in one go: every problem class
@@ -461,7 +469,8 @@ typedef struct {
  * index p in the Philox counter). problems: host array. start, goal: [n][8] (first dof
  * entries used). params: range, max_rounds, workers, max_nodes, max_connect, max_path and
  * seed are used; W and use_scene_batch are ignored. tuning: NULL uses the last
- * cprrtc_autotune_batch result (as many CTAs as fit, staging when it fits, if none). Outputs as cprrtc_plan with configurations padded to 8 floats: path
+ * cprrtc_autotune_batch result (as many CTAs as fit, staging when it fits, one warp per
+ * motion, if none). Outputs as cprrtc_plan with configurations padded to 8 floats: path
  * [n][max_path][8], path_edges [n][max_path-1][Wmax][8] (Wmax = largest W of the batch; NULL
  * allowed). Errors: E_NOT_CONFIGURED (tables or scene batch missing), E_INVALID_ARG (bad
  * index, W, parameter), E_CUDA, E_OOM. */
@@ -473,7 +482,8 @@ int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, co
 
 /* Autotuner: for every class present in the batch, times short runs (trial_rounds rounds)
  * of each launch shape (obstacles staged or read through L1; 1 up to the fitting number of
- * CTAs per SM) and keeps the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
+ * CTAs per SM; one warp or a warp pair per motion where the class allows pairs) and keeps
+ * the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
  * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. The trial
  * outputs go to library buffers; returns after the trials. Errors: as cprrtc_plan_batch,
  * and E_INVALID_ARG for trial_rounds < 1. */

@@ -1886,14 +1886,24 @@ cprrtc_tuning default_tuning() {
   for (int c = 0; c < kBatchClasses; ++c) {
     t.ctas_per_sm[c] = 0;
     t.stage_obstacles[c] = 1;
+    t.warps_per_motion[c] = 1;
   }
   return t;
+}
+
+// Warps per worker class c can run with: 2 only where asked, for a class of 33..64
+// waypoints, in the plain form, with at most 8 workers (16 warps).
+int class_warps_per_motion(cprrtc_ctx* ctx, const cprrtc_tuning& t, int workers, int c) {
+  return (t.warps_per_motion[c] == 2 && plan_batch_has_pairs(c) && ctx->plan_warm <= 0 &&
+          2 * workers <= kMaxWorkers)
+             ? 2
+             : 1;
 }
 
 // Shared memory and grid of class c under tuning t (stage falls back to L1 if it does not fit).
 struct ClassLaunch {
   bool on = false;
-  int workers = 8, grid = 0, stage = 0;
+  int workers = 8, grid = 0, stage = 0, K = 1;
   size_t smem = 0;
 };
 
@@ -1903,14 +1913,15 @@ ClassLaunch class_launch(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuni
   const int nc = bp.off[c + 1] - bp.off[c];
   if (nc == 0) return L;
   L.workers = workers;
+  L.K = class_warps_per_motion(ctx, t, workers, c);
   L.stage = t.stage_obstacles[c] ? 1 : 0;
-  L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, L.stage);
+  L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, L.stage, L.K);
   if (L.smem > ctx->dev.smem_optin) {
     L.stage = 0;
-    L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, false);
+    L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, false, L.K);
   }
   if (L.smem > ctx->dev.smem_optin) return L;
-  const int occ = plan_batch_occupancy(c, L.workers, L.smem, ctx->plan_warm > 0);
+  const int occ = plan_batch_occupancy(c, L.workers, L.smem, ctx->plan_warm > 0, L.K);
   if (occ < 1) return L;
   const int per_sm = t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
   L.grid = std::min(nc, per_sm * ctx->dev.sm_count);
@@ -2006,7 +2017,7 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
     b.pend = b.edges + G * 2 * MN * ew;
     b.pend_edges = b.pend + G * B * 8;
     if ((e = cudaStreamWaitEvent(ctx->side[c], ctx->ev_fork, 0)) != cudaSuccess ||
-        (e = launch_plan_batch(c, b, T, L[c].grid, L[c].smem, ctx->side[c])) != cudaSuccess ||
+        (e = launch_plan_batch(c, b, T, L[c].grid, L[c].smem, L[c].K, ctx->side[c])) != cudaSuccess ||
         (e = cudaEventRecord(ctx->ev_join[c], ctx->side[c])) != cudaSuccess ||
         (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join[c], 0)) != cudaSuccess)
       return cuda_fail(ctx, e, "batch launch");
@@ -2282,13 +2293,17 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
   for (int c = 0; c < kBatchClasses && !rc; ++c) {
     if (bp.off[c + 1] == bp.off[c]) continue;
     double best_rate = -1.0;
-    for (int stage = 1; stage >= 0 && !rc; --stage) {
+    // shapes: one warp per worker with obstacles staged / through L1, then warp pairs
+    for (int shape = 0; shape < 4 && !rc; ++shape) {
+      const int K = 1 + shape / 2, stage = 1 - shape % 2;
       cprrtc_tuning t = best;
+      t.warps_per_motion[c] = K;
+      if (class_warps_per_motion(ctx, t, pp->workers, c) != K) continue;  // no pairs here
       t.stage_obstacles[c] = stage;
       t.ctas_per_sm[c] = 0;
       const ClassLaunch full = class_launch(ctx, bp, t, pp->workers, c);
       if (!full.on || full.stage != stage) continue;  // staging did not fit: tried as L1
-      const int occ = plan_batch_occupancy(c, full.workers, full.smem, ctx->plan_warm > 0);
+      const int occ = plan_batch_occupancy(c, full.workers, full.smem, ctx->plan_warm > 0, K);
       for (int ctas = 1; ctas <= std::min(occ, 4) && !rc; ++ctas) {
         t.ctas_per_sm[c] = ctas;
         cudaEventRecord(e0, ctx->stream);
@@ -2309,6 +2324,7 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
           best_rate = rate;
           best.stage_obstacles[c] = stage;
           best.ctas_per_sm[c] = ctas;
+          best.warps_per_motion[c] = K;
         }
       }
     }

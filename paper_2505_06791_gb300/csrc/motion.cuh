@@ -179,6 +179,118 @@ __device__ __forceinline__ ProjResult project_warp(const RobotDev& rb, const Con
   return res;
 }
 
+// ---- one motion on two warps (33 <= W <= 64) ----------------------------------------------
+//
+// Warp h of the pair holds waypoints 32 h + lane, one per lane. The two warps run Alg. 1 in
+// step: each iteration they publish their `valid` ballots (and warp 0 its candidate update of
+// waypoint 31, the predecessor of warp 1's first waypoint) to this exchange area, meet at a
+// named barrier of 64 threads and both advance `prog` over the same 64-bit mask. Slots are
+// double-buffered by iteration parity, so one barrier per iteration suffices: a slot is
+// written again two iterations later, after the reader has passed the barrier in between.
+// The collision check then splits the same way (each warp its own waypoints); `hit` holds
+// the generation of the last motion in which either warp found a collision.
+struct SplitX {
+  unsigned ballot[2][2];     // [parity][warp]
+  float qn31[2][kMaxDof];    // [parity] warp 0's candidate update of waypoint 31
+  float p31[kMaxDof];        // waypoint 31 as it stands (kept by warp 1's lane 0 alone)
+  float qend[kMaxDof];       // the projected motion's last waypoint (held by warp 1)
+  float resid[2];            // [warp] largest last-evaluated ||E_task||_inf over its waypoints
+  int hit;                   // generation of the last motion found colliding
+  int pad;
+};
+
+__device__ __forceinline__ void pair_barrier(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Alg. 1 on the motion q0 -> q1 held by a warp pair, this warp being half h (0 or 1): q[0]
+// is this lane's waypoint min(32 h + lane, W - 1) on entry, as project_warp<CT, 1> would
+// hold it; results (status, iterations, prog, updates, resid) are those of the one-warp
+// form with WPL = 2 on the same motion, identical in both warps. Every call made by one warp
+// of the pair must be made by the other (the barriers pair them up).
+template <int CT>
+__device__ __forceinline__ ProjResult project_pair(const RobotDev& rb, const ConsDev& c,
+                                                   int max_iters, float (&q)[1][kMaxDof], int W,
+                                                   float tau, float2* wq, int h, SplitX* x,
+                                                   int bar, const float* q0, const float* q1) {
+  const int lane = threadIdx.x & 31;
+  const int dof = rb.dof;
+  const int i = 32 * h + lane;
+  ProjResult res{kValid, 0, -1, 0.f, 0};
+  ChainState cs;
+  if (CT == kConsNone) return res;
+  const unsigned long long in_range = (W >= 64) ? ~0ull : ((1ull << W) - 1ull);
+  if (h == 1 && lane == 0) interp(q0, q1, 31, W, dof, x->p31);
+  float last_err = 0.f;
+  int prog = 0;
+  for (int it = 1; it <= max_iters; ++it) {
+    const int par = it & 1;
+    float qn[kMaxDof];
+    chain(rb, q[0], nullptr, cs, (wq && i < W) ? wq + i * 9 : nullptr);
+    TaskEval<CT> te;
+    te.eval(rb, c, cs);
+    te.solve(rb, c, cs);
+    float esm_max = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) {
+      if (k < dof) {
+        float prev = __shfl_up_sync(kFull, q[0][k], 1);
+        if (h == 1 && lane == 0) prev = x->p31[k];
+        const float g = te.step(rb, cs, k);
+        const float dk = q[0][k] - prev;
+        const float esm = fmaxf(0.f, fabsf(dk) - tau);
+        const float v = fmaf(-c.alpha, fmaf(dk, esm, g), q[0][k]);
+        qn[k] = fminf(fmaxf(v, rb.j[k].lo), rb.j[k].hi);
+        esm_max = fmaxf(esm_max, esm);
+      }
+    }
+    const float et = te.err_inf();
+    const bool valid = (i >= W) || ((esm_max < c.tol_sm) && (et < c.tol_task));
+    if (i > prog && i < W) last_err = et;
+    const unsigned b = __ballot_sync(kFull, valid);
+    if (lane == 0) x->ballot[par][h] = b;
+    if (h == 0 && lane == 31) {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) x->qn31[par][k] = qn[k];
+    }
+    pair_barrier(bar);
+    const unsigned long long valid_mask =
+        (unsigned long long)x->ballot[par][0] | ((unsigned long long)x->ballot[par][1] << 32);
+    res.updates += W - 1 - prog;
+    const unsigned long long after = in_range & ~((2ull << prog) - 1ull);  // (prog, W)
+    const unsigned long long invalid = after & ~valid_mask;
+    if (invalid == 0ull) {
+      prog = W - 1;
+      res.iters = it;
+      break;
+    }
+    prog = __ffsll((long long)invalid) - 2;
+    if (i > prog && i < W) {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) q[0][k] = qn[k];
+    }
+    if (h == 1 && lane == 0 && prog < 31) {
+#pragma unroll
+      for (int k = 0; k < kMaxDof; ++k)
+        if (k < dof) x->p31[k] = x->qn31[par][k];
+    }
+  }
+  float m = i >= 1 ? last_err : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+  if (lane == 0) x->resid[h] = m;
+  pair_barrier(bar);
+  res.resid = fmaxf(x->resid[0], x->resid[1]);
+  if (prog != W - 1) {
+    res.status = kProjFail;
+    res.iters = max_iters;
+    res.first_fail = prog + 1;
+  }
+  return res;
+}
+
 // The sequential projection of the naive baseline (cpRRTC-Naive, Sec. V; CBiRRT-style):
 // waypoints 1..W-1 one after another, each by damped steps from its interpolated point moved
 // by the previous waypoint's correction, until ||E_task||_inf < tol_task (at most max_iters
@@ -591,21 +703,35 @@ __device__ __forceinline__ unsigned swept_mask(const ObsView& v, const float4* s
 //  2. per waypoint (lane), frame by frame along the chain: the frame's bounding sphere
 //     against each listed obstacle of that frame;
 //  3. the frame's robot spheres, for lanes whose bound touched the obstacle.
-template <int WPL>
+//
+// With PAIR (a motion held by a warp pair, see SplitX), lane l holds waypoint wbase + l, the
+// walk covers this warp's waypoints only, any_hit is assumed, and the warp gives up as soon
+// as x->hit shows that the other warp found a collision in this motion (generation gen):
+// the pair's verdict is the flag, the count it returns covers this warp's part.
+template <int WPL, bool PAIR = false>
 __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev& sc,
                                               const float4* __restrict__ obs, const CcShared& S,
                                               const float (&q)[WPL][kMaxDof], int W, int i0,
                                               bool any_hit, WorkCount& work, bool early = true,
-                                              bool wq_ready = false) {
+                                              bool wq_ready = false, int wbase = 0,
+                                              const SplitX* x = nullptr, int gen = 0) {
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
+  // the other warp of a pair has found a collision in this motion (warp-uniform)
+  auto other_hit = [&]() {
+    if constexpr (PAIR) {
+      return __any_sync(kFull, *reinterpret_cast<const volatile int*>(&x->hit) == gen);
+    } else {
+      return false;
+    }
+  };
   // each waypoint's joint terms to shared memory once (the chains below walk frames in a
   // runtime loop, once for the swept bounds and once per pass), unless the projection's last
   // evaluation left them there (wq_ready)
 #pragma unroll
   for (int s = 0; s < WPL && !wq_ready; ++s) {
-    const int i = lane + 32 * s;
+    const int i = wbase + lane + 32 * s;
     if (i < W) {
 #pragma unroll
       for (int k = 0; k < kMaxDof; ++k) {
@@ -623,10 +749,10 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
   int n_act = 0;
 #pragma unroll
   for (int s = 0; s < WPL; ++s) {
-    const int i = lane + 32 * s;
+    const int i = wbase + lane + 32 * s;
     act[s] = i >= i0 && i < W;
   }
-  n_act = max(0, W - i0);
+  n_act = max(0, min(W, wbase + 32 * WPL) - max(i0, wbase));
   if (n_act == 0 || n_obs == 0) return -1;
 
   // ---- level 1: swept frame bounds over the segment ----
@@ -639,7 +765,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       if (f > 0) {
         const JointDev J = S.jnt[f - 1];
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(wbase + lane + 32 * s, W - 1) * 9 + f - 1]);
       }
       const float4 b = S.bnd[f];
       if (b.w < 0.f) continue;  // no spheres on this frame (warp-uniform)
@@ -673,6 +799,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
     work.transforms += (unsigned)(n_act * (dof + 1));
     __syncwarp();
   }
+  if (other_hit()) return -1;
 
   int best = 0x7fffffff;  // smallest colliding waypoint found so far
   const int n_chunks = sc.n_chunks();
@@ -689,6 +816,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
           listed_all = true;
           break;
         }
+        if (other_hit()) return -1;
         // lanes screen 32 chunks at once: chunk box against every swept frame bound
         const int ch = cb + lane;
         cfr = 0u;
@@ -754,7 +882,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
     bool any_act = false;
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {
-      act[s] = act[s] && (!early || lane + 32 * s < best);
+      act[s] = act[s] && (!early || wbase + lane + 32 * s < best);
       any_act |= act[s];
     }
     if (!__any_sync(kFull, any_act)) break;
@@ -769,7 +897,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       if (f > 0) {
         const JointDev J = S.jnt[f - 1];
 #pragma unroll
-        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(lane + 32 * s, W - 1) * 9 + f - 1]);
+        for (int s = 0; s < WPL; ++s) F[s].advance_cached(J, S.wq[min(wbase + lane + 32 * s, W - 1) * 9 + f - 1]);
       }
       const float4 b = S.bnd[f];
       if (b.w < 0.f) continue;
@@ -819,6 +947,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
 #pragma unroll
         for (int s = 0; s < WPL; ++s) h |= hit[s];
         if (__any_sync(kFull, h)) break;
+        if (other_hit()) return -1;
       }
     }
     work.chains += n_act;
@@ -827,7 +956,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
 #pragma unroll
     for (int s = 0; s < WPL; ++s) {
       const unsigned hb = __ballot_sync(kFull, hit[s]);
-      if (hb) best = min(best, 32 * s + __ffs(hb) - 1);
+      if (hb) best = min(best, wbase + 32 * s + __ffs(hb) - 1);
     }
     if (early && best != 0x7fffffff && (any_hit || best == i0)) break;
   }

@@ -139,13 +139,15 @@ __device__ __forceinline__ void last_waypoint(const float (&q)[WPL][kMaxDof], in
   __syncwarp();
 }
 
+// The lanes' waypoints wbase + lane + 32 s (< W) to dst[W][dof] (each warp of a pair writes
+// its half).
 template <int WPL>
 __device__ __forceinline__ void store_edge(float* dst, const float (&q)[WPL][kMaxDof], int W,
-                                           int dof) {
+                                           int dof, int wbase = 0) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int s = 0; s < WPL; ++s) {
-    const int i = lane + 32 * s;
+    const int i = wbase + lane + 32 * s;
     if (i < W) {
 #pragma unroll
       for (int k = 0; k < kMaxDof; ++k)
@@ -284,6 +286,54 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
   return ff >= 0 ? kCollision : kValid;
 }
 
+// validate_motion for a motion of 33..64 waypoints held by a warp pair (see SplitX), this warp
+// being half h: the same verdict as validate_motion<CT, 2> on the motion (Alg. 1 in step over
+// the exchange area, each warp checking its own waypoints, the collision verdict through
+// x->hit with generation gen), returned identically in both warps, and with a valid motion
+// its last waypoint in x->qend. Work counts: Alg. 1 updates by half 0, collision work by each
+// half for its part. No learned form, no sequential projection.
+template <int CT>
+__device__ __forceinline__ int validate_motion_pair(const RobotDev& rb, const SceneDev& sc,
+                                                    const ConsDev& cs, int max_iters,
+                                                    MotionWork& work, WorkCount& wc,
+                                                    const float4* obs, const CcShared& S,
+                                                    const float* q0, const float* q1, int W,
+                                                    float (&q)[1][kMaxDof], const SelfMask* self,
+                                                    int h, SplitX* x, int bar, int gen) {
+  const int lane = threadIdx.x & 31;
+  const int dof = rb.dof;
+  const int i = 32 * h + lane;
+  const float tau = step_threshold(cs, q0, q1, W, dof);
+  interp(q0, q1, min(i, W - 1), W, dof, q[0]);
+  const ProjResult pr = project_pair<CT>(rb, cs, max_iters, q, W, tau, S.wq, h, x, bar, q0, q1);
+  __syncwarp();
+  if (h == 0) {
+    work.proj += (unsigned)pr.updates;
+    wc.updates += (unsigned)pr.updates;
+  }
+  if (pr.status != kValid) return kProjFail;  // both halves, from the same exchange
+  if (i == W - 1) {
+#pragma unroll
+    for (int k = 0; k < kMaxDof; ++k) x->qend[k] = k < dof ? q[0][k] : 0.f;
+  }
+  const int lo = max(1, 32 * h), hi = min(W, 32 * h + 32);  // this half's waypoints
+  int ff = collide_motion<1, true>(rb, sc, obs, S, q, W, 1, true, wc, true, CT != kConsNone,
+                                   32 * h, x, gen);
+  __syncwarp();
+  work.cc += (unsigned)(ff >= 0 ? ff - lo + 1 : hi - lo);
+  bool hit = ff >= 0;
+  if (!hit && self && self->on &&
+      !__any_sync(kFull, *reinterpret_cast<volatile int*>(&x->hit) == gen)) {
+    const bool hs = i >= 1 && i < W &&
+                    self_hit_waypoint(rb.dof, S.jnt, S.bnd, S.sph, S.foff, S.wq + i * 9, *self);
+    wc.chains += (unsigned)(hi - lo);
+    hit = __any_sync(kFull, hs);
+  }
+  if (hit && lane == 0) x->hit = gen;
+  pair_barrier(bar);
+  return x->hit == gen ? kCollision : kValid;
+}
+
 // Register cap of the planner kernel (0: the compiler's choice). Fewer registers let more
 // 8-warp CTAs share an SM at the price of some spills.
 #ifndef CPRRTC_PLAN_MAXNREG
@@ -296,24 +346,31 @@ __device__ __forceinline__ int validate_motion(const RobotDev& rb, const SceneDe
 #endif
 
 
-// The planner for one problem, run by the whole CTA (one warp per worker). Shared memory
-// (robot tables, obstacles, per-warp scratch) is staged by the caller.
-template <int CT, int WPL, bool SEQ = false, bool WARM = false>
+// The planner for one problem, run by the whole CTA (one warp per worker, or with K = 2 a warp
+// pair per worker: motions of 33..64 waypoints split by waypoints, see SplitX; the pair's
+// exchange areas xs[worker]). Shared memory (robot tables, obstacles, per-warp scratch) is
+// staged by the caller. Both warps of a pair follow the same chain (identical copies of its
+// state, computed from identical inputs); the pair's half 0 writes the worker's shared flags,
+// tree nodes and path, each half its own waypoints of a motion's edge.
+template <int CT, int WPL, bool SEQ = false, bool WARM = false, int K = 1>
 __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
                                              const CcShared& S, PlanShared* sh,
                                              WorkCount& wc, const SelfMask& self,
-                                             const MlpView* net = nullptr) {
+                                             const MlpView* net = nullptr, SplitX* xs = nullptr) {
+  static_assert(K == 1 || (K == 2 && WPL == 1 && !SEQ && !WARM), "warp pairs: plain Alg. 1, one waypoint per lane");
   const int p = P.p;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int B = blockDim.x >> 5, dof = rb.dof, W = P.W;
+  const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;  // physical warp
+  const int warp = pw / K, h = pw % K;                        // worker, half of its pair
+  const int NW = blockDim.x >> 5, B = NW / K, dof = rb.dof, W = P.W;
   if (threadIdx.x == 0) {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     sh->t_start = t;
     sh->stop = 0;
   }
+  if (K > 1 && threadIdx.x < B) xs[threadIdx.x].hit = 0;
 
   const size_t wd = (size_t)W * dof;
   const int MN = a.max_nodes;
@@ -321,10 +378,10 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   auto nodes = [&](int t) { return P.nodes + (size_t)t * MN * 8; };
   auto parent = [&](int t) { return P.parent + (size_t)t * MN; };
   auto edges = [&](int t) { return P.edges + (size_t)t * MN * wd; };
-  // per-warp global scratch: the closing hop's motion is kept at wedge + wd
+  // per-worker global scratch: the closing hop's motion is kept at wedge + wd
   float* wedge = P.pend_edges + (size_t)warp * 2 * wd;
 
-  if (warp == 0) {
+  if (pw == 0) {
     float q[kMaxDof];
     load_cfg(P.start, dof, q);
     store_cfg(nodes(0), q, dof);
@@ -348,10 +405,10 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   int rounds_used = 0, win = -1;
   // chain state (warp-uniform): 0 extend, 1 connect, 2 closing hop
   int mode = 0, ta = 0, last = 0, target = -1, steps = 0;
-  float* cur = sh->cfg[warp][0];
-  float* qt = sh->cfg[warp][1];
-  float* q1 = sh->cfg[warp][2];
-  float* qe = sh->cfg[warp][3];
+  float* cur = sh->cfg[pw][0];
+  float* qt = sh->cfg[pw][1];
+  float* q1 = sh->cfg[pw][2];
+  float* qe = sh->cfg[pw][3];
   for (int r = 0; r < a.max_rounds; ++r) {
     if (mode == 0) {
       ta = (r + warp) & 1;
@@ -377,18 +434,30 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     // the closing hop is checked as it stands (one Alg. 1 iteration); the learned form
     // warm-starts extend motions only: connect steps and the closing hop head for a node on
     // the manifold
-    const int st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
-                                                       obs, S, cur, q1, W, q,
-                                                       WARM && mode == 0 ? net : nullptr,
-                                                       a.warm_refine, qe, &self);
+    int st;
+    if constexpr (K == 1) {
+      st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
+                                               obs, S, cur, q1, W, q,
+                                               WARM && mode == 0 ? net : nullptr,
+                                               a.warm_refine, qe, &self);
+    } else {
+      st = validate_motion_pair<CT>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
+                                    cur, q1, W, q, &self, h, xs + warp, 1 + warp, r + 1);
+    }
     wp += W;
     int add = 0, conn = 0;
     if (st == kValid) {
       if (mode == 2) {
         conn = 1;
-        store_edge<WPL>(wedge + wd, q, W, dof);
+        store_edge<WPL>(wedge + wd, q, W, dof, 32 * h);
       } else {
-        last_waypoint<WPL>(q, W, dof, qe);
+        if constexpr (K == 1) {
+          last_waypoint<WPL>(q, W, dof, qe);
+        } else {
+          __syncwarp();  // the pair barrier made x->qend visible
+          if (lane < 8) qe[lane] = xs[warp].qend[lane];
+          __syncwarp();
+        }
         bool accept = true;
         if (mode == 0) {
           target = nearest_warp(nodes(ta ^ 1), count_of(ta ^ 1), qe, dof);
@@ -401,7 +470,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         add = accept ? 1 : 0;
       }
     }
-    if (lane == 0) {
+    if (lane == 0 && h == 0) {
       sh->padd[warp] = add;
       sh->ptree[warp] = ta;
       sh->pparent[warp] = last;
@@ -425,9 +494,9 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
         if (sh->padd[w] && sh->ptree[w] == ta) ++off;
       dst = count_of(ta) + off;
       if (dst < a.max_nodes) {
-        if (lane < 8) nodes(ta)[(size_t)dst * 8 + lane] = qe[lane];
-        store_edge<WPL>(edges(ta) + (size_t)dst * wd, q, W, dof);
-        if (lane == 0) parent(ta)[dst] = last;
+        if (lane < 8 && h == 0) nodes(ta)[(size_t)dst * 8 + lane] = qe[lane];
+        store_edge<WPL>(edges(ta) + (size_t)dst * wd, q, W, dof, 32 * h);
+        if (lane == 0 && h == 0) parent(ta)[dst] = last;
       } else {
         dst = -1;
       }
@@ -471,13 +540,13 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       steps = 0;
     }
   }
-  if (lane == 0) {
-    sh->wp[warp] = wp;
-    sh->wproj[warp] = work.proj;
-    sh->wcc[warp] = work.cc;
+  if (lane == 0) {  // per physical warp: a pair's half 1 adds its collision work only
+    sh->wp[pw] = h == 0 ? wp : 0;
+    sh->wproj[pw] = work.proj;
+    sh->wcc[pw] = work.cc;
   }
 
-  if (win >= 0 && warp == win) {
+  if (win >= 0 && warp == win && h == 0) {
     // path: root_a .. last, closing hop, target .. root_b; reversed when tree a is the
     // goal tree
     const int tb = ta ^ 1;
@@ -520,7 +589,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   if (threadIdx.x == 0) {
     if (win < 0) a.path_len[p] = 0;
     long long total_wp = 0, tp = 0, tc = 0;
-    for (int w = 0; w < B; ++w) {
+    for (int w = 0; w < NW; ++w) {
       total_wp += sh->wp[w];
       tp += sh->wproj[w];
       tc += sh->wcc[w];
@@ -614,16 +683,23 @@ __global__ void __launch_bounds__(256, 2) plan_warm_kernel(RobotDev rb, SceneDev
 // per-CTA scratch slot reused across problems.
 // With WARM (the learned form), problems whose robot and constraint have a network in the
 // table warm-start their extend motions with it; the others plan as without it.
-template <int CT, int WPL, bool WARM>
+// Bytes after the per-warp areas: the planner's shared state, and with warp pairs their
+// exchange areas (one per worker).
+__host__ __device__ constexpr size_t plan_extra_bytes(int K) {
+  return ((sizeof(PlanShared) + 15) & ~size_t(15)) + (K > 1 ? sizeof(SplitX) * kMaxWorkers / 2 : 0);
+}
+
+template <int CT, int WPL, bool WARM, int K = 1>
 __device__ __forceinline__ void plan_batch_body(const BatchArgs& b, const BatchTables& T) {
   extern __shared__ __align__(16) char smem[];
   __shared__ SceneDev s_sc;
   __shared__ int s_t, s_robot, s_cons;
   const PlanArgs& a = b.a;
-  const int B = blockDim.x >> 5;
+  const int NW = blockDim.x >> 5, B = NW / K;  // warps, workers
   const int warp = threadIdx.x >> 5;
-  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, b.max_S, b.max_W, B, sizeof(PlanShared));
+  const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, b.max_S, b.max_W, NW, plan_extra_bytes(K));
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
+  SplitX* xs = K > 1 ? reinterpret_cast<SplitX*>(smem + L.extra + plan_extra_bytes(1)) : nullptr;
   const CcShared S = cc_shared(smem, L, warp);
   float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
   WorkCount wc{};
@@ -670,8 +746,8 @@ __device__ __forceinline__ void plan_batch_body(const BatchArgs& b, const BatchT
     const SceneDev sc = s_sc;  // in registers: the collision walk reads it in its inner loops
     const SelfMask self = T.self[s_robot];
     const MlpView* net = WARM && T.nets[s_robot][s_cons].dof ? &T.nets[s_robot][s_cons] : nullptr;
-    plan_problem<CT, WPL, false, WARM>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh, wc,
-                                       self, net);
+    plan_problem<CT, WPL, false, WARM, K>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh,
+                                          wc, self, net, xs);
   }
   wc.flush(a.work_counters);
 }
@@ -688,7 +764,23 @@ __global__ void __launch_bounds__(256, 2) plan_batch_warm_kernel(BatchArgs b,
   plan_batch_body<CT, WPL, true>(b, T);
 }
 
-static const void* plan_batch_fn(int cls, bool warm = false) {
+// A class of 33..64-waypoint problems with a warp pair per worker (one waypoint per lane):
+// up to 16 warps, held to the 128 registers that let them share one SM.
+template <int CT>
+__global__ void __launch_bounds__(512, 1) plan_batch_pair_kernel(BatchArgs b,
+                                                                 const __grid_constant__ BatchTables T) {
+  plan_batch_body<CT, 1, false, 2>(b, T);
+}
+
+static const void* plan_batch_fn(int cls, bool warm = false, int K = 1) {
+  if (K == 2) {  // warp pairs: the classes of 33..64 waypoints, plain form
+    switch (cls) {
+      case 1: return (const void*)plan_batch_pair_kernel<kConsNone>;
+      case 3: return (const void*)plan_batch_pair_kernel<kConsRollPitch>;
+      case 5: return (const void*)plan_batch_pair_kernel<kConsZPlane>;
+      default: return nullptr;
+    }
+  }
   if (warm) {  // the learned form of the roll-pitch and z-plane classes
     switch (cls) {
       case 2: return (const void*)plan_batch_warm_kernel<kConsRollPitch, 1>;
@@ -708,15 +800,18 @@ static const void* plan_batch_fn(int cls, bool warm = false) {
   }
 }
 
-size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage) {
-  return SmemLayout(stage ? max_scene_f4 : 0, max_S, max_W, workers, sizeof(PlanShared)).total;
+size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage, int K) {
+  return SmemLayout(stage ? max_scene_f4 : 0, max_S, max_W, workers * K, plan_extra_bytes(K)).total;
 }
 
-int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm) {
-  const void* fn = plan_batch_fn(cls, warm);
+bool plan_batch_has_pairs(int cls) { return plan_batch_fn(cls, false, 2) != nullptr; }
+
+int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm, int K) {
+  const void* fn = plan_batch_fn(cls, warm, K);
   int per_sm = 0;
+  if (!fn) return 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * workers, smem) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * workers * K, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -724,14 +819,15 @@ int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm) {
 }
 
 cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
-                              cudaStream_t stream) {
+                              int K, cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
-  const void* fn = plan_batch_fn(cls, b.a.warm_refine > 0);
+  const void* fn = plan_batch_fn(cls, b.a.warm_refine > 0, K);
+  if (!fn) return cudaErrorNotSupported;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {&b, const_cast<BatchTables*>(&T)};
-  e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * b.a.workers), args, smem, stream);
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * b.a.workers * K), args, smem, stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
