@@ -526,6 +526,27 @@ def gpu_batch_start_goal(robots, cons, problems, scenes, seed, device):
     return start, goal
 
 
+def batch_timeline(span, sm_count: int):
+    """Problems in flight over one batch run, from each problem's start and end on the GPU's
+    global timer (cprrtc_batch_spans)."""
+    ran = span[:, 1] > 0
+    s0, e0 = span[ran, 0].astype(np.float64), span[ran, 1].astype(np.float64)
+    t0, t1 = s0.min(), e0.max()
+    T = t1 - t0
+    ts = t0 + T * np.linspace(0.0, 1.0, 401)
+    inflight = np.array([int(((s0 <= t) & (e0 > t)).sum()) for t in ts])
+    full = np.nonzero(inflight >= sm_count)[0]
+    last_full = ts[full[-1]] if len(full) else t0
+    return {"run_ms": float(T) / 1e6,
+            "problem_ms_sum": float((e0 - s0).sum()) / 1e6,
+            "mean_in_flight": float((e0 - s0).sum() / T),
+            "in_flight_at_pct": {str(q): int(inflight[int(q * 4)]) for q in (0, 10, 25, 50, 75, 90, 99)},
+            "last_problem_started_at_ms": float(s0.max() - t0) / 1e6,
+            "tail_ms_with_fewer_in_flight_than_sms": float(t1 - last_full) / 1e6,
+            "note": "problems in flight at fractions of the run; after the last start the queues "
+                    "are empty and the run ends with its slowest problems"}
+
+
 def run_batch(args, world, rank, local):
     import torch
     from paper_2505_06791_gb300 import build
@@ -572,6 +593,7 @@ def run_batch(args, world, rank, local):
         barrier(world)
         clk = clocks.stop()
         step_ms = [s_.elapsed_time(e) for s_, e in zip(starts, ends)]
+        spans = ctx.batch_spans(len(probs))  # the last timed replay
         kms, launches = ctx.kernel_time("plan_batch")
         counters = ctx.work_counters() / max(args.steps, 1)
         ctx.set_timing(False)
@@ -641,6 +663,7 @@ def run_batch(args, world, rank, local):
                                               + len(scenes[probs[p][2]].cap)),
                              "rounds": int(rounds_b[p]), "solved": bool(L[p] > 0),
                              "plan_ms": float(ms[p])} for p in slow],
+                "timeline": batch_timeline(spans, torch.cuda.get_device_properties(dev).multi_processor_count),
                 "note": "the replay lasts as long as its slowest problem's rounds: the step is "
                         "bound by that critical path, and the SMs idle as the other problems end"}
     learned = None

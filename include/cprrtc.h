@@ -504,6 +504,17 @@ int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
                          int64_t* work);
 int cprrtc_batch_replay(cprrtc_ctx* ctx);
 
+/* When each problem of the last batch run on this context (cprrtc_plan_batch, a
+ * cprrtc_batch_replay, or the autotuner's last trial) started and ended, in nanoseconds of
+ * the GPU's global timer (the %globaltimer register read by the problem's CTA as it takes the
+ * problem and as it writes its results): span[2p] and span[2p + 1], a host array of 2n
+ * entries, n being that batch's problem count. Problems that did not run in it (an autotuner
+ * trial runs one class) read 0 and 0. A measurement aid: the spans show how many problems
+ * are in flight over the run, and so whether the run ends with the SMs idle behind its
+ * slowest problems. Synchronises the context's stream. Errors: E_NOT_CONFIGURED (no batch has
+ * run), E_INVALID_ARG (n other than that count, span NULL or not host memory), E_CUDA. */
+int cprrtc_batch_spans(cprrtc_ctx* ctx, int64_t* span, int n);
+
 /* ---- planning without allocation ---- */
 
 /* Size of the library's fixed device scratch for cprrtc_plan_static: 16 MiB, held by every

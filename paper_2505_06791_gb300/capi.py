@@ -125,6 +125,7 @@ _SIGS = {
                              C.POINTER(cprrtc_plan_params), C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "cprrtc_batch_replay": [C.c_void_p],
+    "cprrtc_batch_spans": [C.c_void_p, C.c_void_p, C.c_int],
     "cprrtc_philox": [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int, C.c_void_p],
     "cprrtc_set_cc_mode": [C.c_void_p, C.c_int, C.c_double],
     "cprrtc_cc_stats": [C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_int],
@@ -609,6 +610,13 @@ class Context:
     def batch_replay(self):
         self._check(cprrtc_batch_replay(self.h))
 
+    def batch_spans(self, n: int):
+        """[n][2] int64: each problem's start and end (GPU global-timer ns) in the last batch
+        run on this context."""
+        span = np.zeros((n, 2), np.int64)
+        self._check(cprrtc_batch_spans(self.h, span, n))
+        return span
+
     def philox(self, key0, key1, counters):
         c = np.ascontiguousarray(counters, dtype=np.uint32)
         out = np.empty_like(c)
@@ -688,6 +696,11 @@ def cprrtc_batch_replay(h):
     return lib().cprrtc_batch_replay(h)
 
 
+def cprrtc_batch_spans(h, span, n):
+    _need(span, "int64", "span")
+    return lib().cprrtc_batch_spans(h, _ptr(span), n)
+
+
 def cprrtc_philox(h, key0, key1, counters, n, out):
     return lib().cprrtc_philox(h, key0, key1, _ptr(counters), n, _ptr(out))
 
@@ -744,5 +757,5 @@ def cprrtc_project_configs(h, q_in, n, max_iters, q_out, ok, resid):
 __all__ = ["Context", "CprrtcError", "lib", "header_symbols", "synth", "cprrtc_validate",
            "cprrtc_project_configs", "cprrtc_plan", "cprrtc_plan_static", "cprrtc_philox",
            "cprrtc_plan_batch", "cprrtc_autotune_batch", "cprrtc_batch_capture",
-           "cprrtc_batch_replay", "cprrtc_validate_ws", "cprrtc_mlp_grad", "cprrtc_mlp_train",
+           "cprrtc_batch_replay", "cprrtc_batch_spans", "cprrtc_validate_ws", "cprrtc_mlp_grad", "cprrtc_mlp_train",
            "cprrtc_mlp_infer"]

@@ -26,6 +26,9 @@ struct BatchRes {
   unsigned* d_counters = nullptr;
   char* d_scratch = nullptr;
   size_t scratch_cap = 0;
+  long long* d_span = nullptr;  // [n][2] each problem's start and end on the global timer
+  size_t span_cap = 0;
+  int n = 0;                    // problems of the batch these buffers last served
 };
 
 struct TimingRec {
@@ -77,6 +80,7 @@ struct cprrtc_ctx {
   cprrtc_tuning tuned{};
   bool has_tuned = false;
   BatchRes batch_res, graph_res;
+  const BatchRes* last_batch = nullptr;  // the buffers of the last batch run (for its spans)
   cudaStream_t side[kBatchClasses] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[kBatchClasses] = {};
@@ -548,6 +552,7 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
     cudaFree(r->d_order);
     cudaFree(r->d_counters);
     cudaFree(r->d_scratch);
+    cudaFree(r->d_span);
   }
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   for (int c = 0; c < kBatchClasses; ++c) {
@@ -1968,7 +1973,13 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "batch counters");
     }
     if (!rc) rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, scratch_off[kBatchClasses]);
+    if (!rc) rc = ensure(ctx, &res.d_span, &res.span_cap, 2 * (size_t)bp.n);
+    if (!rc && bp.n > 0) {
+      cudaError_t e = cudaMemsetAsync(res.d_span, 0, 2 * (size_t)bp.n * sizeof(long long), ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "batch spans");
+    }
     if (rc) return rc;
+    res.n = bp.n;
     if (!bp.probs.empty()) {
       cudaError_t e = cudaMemcpyAsync(res.d_probs, bp.probs.data(), bp.probs.size() * sizeof(int4),
                                       cudaMemcpyHostToDevice, ctx->stream);
@@ -2000,6 +2011,7 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
     if (!L[c].on) continue;
     BatchArgs b{};
     b.a = base;
+    b.a.span = res.d_span;
     b.a.stage_obs = L[c].stage;
     b.a.max_scene_f4 = bp.max_f4[c];
     b.problems = res.d_probs;
@@ -2232,6 +2244,7 @@ int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, co
   rc = run_batch(ctx, bp, ctx->batch_res, a, t, (1u << kBatchClasses) - 1u, false);
   tm.done();
   if (rc) return rc;
+  ctx->last_batch = &ctx->batch_res;
   return st.end(ctx);
 }
 
@@ -2309,6 +2322,7 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
         cudaEventRecord(e0, ctx->stream);
         rc = run_batch(ctx, bp, ctx->batch_res, a, t, 1u << c, false);
         if (rc) break;
+        ctx->last_batch = &ctx->batch_res;
         cudaEventRecord(e1, ctx->stream);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
           rc = cuda_fail(ctx, e, "autotune trial");
@@ -2410,6 +2424,22 @@ int cprrtc_batch_replay(cprrtc_ctx* ctx) {
   cudaError_t e = cudaGraphLaunch(ctx->graph_exec, ctx->stream);
   tm.done();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch replay");
+  ctx->last_batch = &ctx->graph_res;
+  return CPRRTC_OK;
+}
+
+int cprrtc_batch_spans(cprrtc_ctx* ctx, int64_t* span, int n) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  const BatchRes* r = ctx->last_batch;
+  if (!r || !r->d_span) return fail(ctx, CPRRTC_E_NOT_CONFIGURED, "batch spans: no batch has run");
+  if (!span || n != r->n) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch spans: n must be the last batch's problem count");
+  if (ptr_where(span, ctx->device) != kPtrHost)
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "batch spans: span must be host memory");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaMemcpyAsync(span, r->d_span, 2 * (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch spans");
   return CPRRTC_OK;
 }
 

@@ -84,6 +84,7 @@ struct PlanArgs {
   int32_t* rounds;
   long long* waypoints;
   float* plan_ms;
+  long long* span;          // [n][2] global-timer ns at each problem's start and end (may be null)
   long long* work;          // [n][2] Alg. 1 waypoint updates, collision-checked waypoints
   unsigned long long* work_counters;  // executed-work totals (may be null)
   int stage_obs;            // set by the launcher

@@ -603,6 +603,10 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     long long t_end;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
     if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sh->t_start) * 1e-6);
+    if (a.span) {
+      a.span[2 * p] = sh->t_start;
+      a.span[2 * p + 1] = t_end;
+    }
   }
 }
 

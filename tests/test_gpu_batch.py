@@ -79,12 +79,24 @@ def test_mixed_batch_paths_graph_and_tuning(torch_cuda, oracle_mod):
         g = torch.from_numpy(goal.astype(np.float32)).cuda()
         first = to_np(ctx.plan_batch(probs, s, g, prm, edges=True))
         second = to_np(ctx.plan_batch(probs, s, g, prm, edges=True))
+        span_direct = ctx.batch_spans(len(probs))
         out = ctx.alloc_batch_outputs(len(probs), prm, max_W, s, edges=True)
         ctx.batch_capture(probs, s, g, prm, out)
         ctx.batch_replay()
         ctx.batch_replay()
+        span_replay = ctx.batch_spans(len(probs))
     stream.synchronize()
     replay = to_np(out)
+    # each problem's span on the global timer is the time its plan_ms reports, for the last
+    # direct run and for the last replay
+    for sp, res in ((span_direct, second), (span_replay, replay)):
+        assert (sp[:, 0] > 0).all() and (sp[:, 1] >= sp[:, 0]).all()
+        np.testing.assert_allclose((sp[:, 1] - sp[:, 0]) / 1e6, res["plan_ms"], rtol=1e-5, atol=1e-5)
+    assert not np.array_equal(span_direct, span_replay)
+    from paper_2505_06791_gb300.capi import CprrtcError, E_INVALID_ARG
+    with pytest.raises(CprrtcError) as e:
+        ctx.batch_spans(len(probs) + 1)
+    assert e.value.code == E_INVALID_ARG
     keys = ("path_len", "path", "path_edges", "rounds", "waypoints", "work")
     dofs = [robots[pr[0]].dof for pr in probs]
     Ws = [pr[3] for pr in probs]
@@ -153,6 +165,9 @@ def test_batch_argument_errors(torch_cuda):
     q = np.zeros((1, 8), np.float32)
     with pytest.raises(capi.CprrtcError) as e:
         ctx.plan_batch([(0, 0, 0, 32)], q, q, prm)
+    assert e.value.code == capi.E_NOT_CONFIGURED
+    with pytest.raises(capi.CprrtcError) as e:
+        ctx.batch_spans(1)  # no batch has run
     assert e.value.code == capi.E_NOT_CONFIGURED
     ctx.set_robot_table([S.make_arm7(1)])
     ctx.set_constraint_table([S.no_constraint()])
