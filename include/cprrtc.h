@@ -448,14 +448,15 @@ typedef struct {
 
 /* Launch shape of each problem class (class = 2 * constraint type + (W > 32)): CTAs per SM
  * (0: as many as fit), whether the class stages its obstacles into shared memory (else they
- * are read through L1), and warps per motion: 1, or 2 for a class of 33..64 waypoints (each
- * worker's motion held by a warp pair, one waypoint per lane: Alg. 1 runs in step on both
- * warps, each checks its own waypoints for collisions; plain form only, at most 8 workers;
- * elsewhere, 0 or any other value means 1). None of them changes any result: a problem's
- * search depends only on its own inputs and the plan parameters. Only the executed-work
- * counts differ with warp pairs (cprrtc_work_counters, the `work` output): a pair's halves
- * stop their collision walks when either finds a collision, so their collision work
- * depends on timing. */
+ * are read through L1), and warps per motion: 1, or 2 (each worker's motion held by a warp
+ * pair; plain form only, at most 8 workers; any other value means 1). A pair splits a motion
+ * of 33..64 waypoints by waypoints (one per lane: Alg. 1 runs in step on both warps, each
+ * checks its own waypoints for collisions) and a motion of up to 32 waypoints by obstacles
+ * (both warps run Alg. 1 on the whole motion, each checks half of the obstacle chunks).
+ * None of them changes any result: a problem's search depends only on its own inputs and
+ * the plan parameters. Only the executed-work counts differ with warp pairs
+ * (cprrtc_work_counters, the `work` output): a pair's halves stop their collision walks
+ * when either finds a collision, so their collision work depends on timing. */
 typedef struct {
   int ctas_per_sm[CPRRTC_BATCH_CLASSES];
   int stage_obstacles[CPRRTC_BATCH_CLASSES];
@@ -482,7 +483,7 @@ int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, co
 
 /* Autotuner: for every class present in the batch, times short runs (trial_rounds rounds)
  * of each launch shape (obstacles staged or read through L1; 1 up to the fitting number of
- * CTAs per SM; one warp or a warp pair per motion where the class allows pairs) and keeps
+ * CTAs per SM; one warp or a warp pair per motion, the latter not in the learned form) and keeps
  * the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
  * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. The trial
  * outputs go to library buffers; returns after the trials. Errors: as cprrtc_plan_batch,

@@ -1837,6 +1837,8 @@ struct BatchPlan {
   int off[kBatchClasses + 1] = {};   // class c: order[off[c] .. off[c + 1])
   int max_W[kBatchClasses] = {}, max_S[kBatchClasses] = {}, max_f4[kBatchClasses] = {};
   int max_W_all = 0;
+  double work[kBatchClasses] = {};  // estimated cost of the class's problems (see prepare_batch)
+  double work_all = 0.0;
 };
 
 int prepare_batch(cprrtc_ctx* ctx, const cprrtc_problem* probs, int n, BatchPlan& bp) {
@@ -1869,6 +1871,8 @@ int prepare_batch(cprrtc_ctx* ctx, const cprrtc_problem* probs, int n, BatchPlan
     // expected cost for longest-first ordering: waypoints x (obstacles + robot spheres)
     const double cost = (double)q.W * (n_obs + r.n_spheres) * (ct != kConsNone ? 2.0 : 1.0);
     cls[c].push_back({cost, p});
+    bp.work[c] += cost;
+    bp.work_all += cost;
     bp.max_W[c] = std::max(bp.max_W[c], q.W);
     bp.max_S[c] = std::max(bp.max_S[c], r.n_spheres);
     bp.max_f4[c] = std::max(bp.max_f4[c], f4);
@@ -1896,19 +1900,17 @@ cprrtc_tuning default_tuning() {
   return t;
 }
 
-// Warps per worker class c can run with: 2 only where asked, for a class of 33..64
-// waypoints, in the plain form, with at most 8 workers (16 warps).
+// Warps per worker class c runs with: 2 only where asked, in the plain form, with at most 8
+// workers (16 warps).
 int class_warps_per_motion(cprrtc_ctx* ctx, const cprrtc_tuning& t, int workers, int c) {
-  return (t.warps_per_motion[c] == 2 && plan_batch_has_pairs(c) && ctx->plan_warm <= 0 &&
-          2 * workers <= kMaxWorkers)
-             ? 2
-             : 1;
+  (void)c;
+  return (t.warps_per_motion[c] == 2 && ctx->plan_warm <= 0 && 2 * workers <= kMaxWorkers) ? 2 : 1;
 }
 
 // Shared memory and grid of class c under tuning t (stage falls back to L1 if it does not fit).
 struct ClassLaunch {
   bool on = false;
-  int workers = 8, grid = 0, stage = 0, K = 1;
+  int workers = 8, grid = 0, stage = 0, K = 1, per_sm = 0;
   size_t smem = 0;
 };
 
@@ -1929,7 +1931,14 @@ ClassLaunch class_launch(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuni
   const int occ = plan_batch_occupancy(c, L.workers, L.smem, ctx->plan_warm > 0, L.K);
   if (occ < 1) return L;
   const int per_sm = t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
-  L.grid = std::min(nc, per_sm * ctx->dev.sm_count);
+  L.per_sm = per_sm;
+  // The classes run concurrently, so each gets the share of the SMs that its estimated work
+  // is of the batch's: every class's CTAs are resident from the start and begin with their
+  // longest problems (a class given every SM would hold them until its queue is empty, and
+  // the classes launched after it would start their longest problems late).
+  const double share = bp.work_all > 0.0 ? bp.work[c] / bp.work_all : 1.0;
+  const int sms = std::max(1, (int)std::floor(share * ctx->dev.sm_count));
+  L.grid = std::min(nc, per_sm * sms);
   L.on = L.grid > 0;
   return L;
 }
@@ -2007,7 +2016,16 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
   }
   cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch fork");
-  for (int c = 0; c < kBatchClasses; ++c) {
+  // Launch order: classes whose CTAs take a whole SM first, then by estimated work. The block
+  // scheduler spreads a grid's CTAs over the SMs; CTAs that hold half an SM, placed first,
+  // would leave no whole SM free for the others until they finish.
+  int order[kBatchClasses];
+  for (int c = 0; c < kBatchClasses; ++c) order[c] = c;
+  std::stable_sort(order, order + kBatchClasses, [&](int x, int y) {
+    if (L[x].per_sm != L[y].per_sm) return L[x].per_sm < L[y].per_sm;
+    return bp.work[x] > bp.work[y];
+  });
+  for (int c : order) {
     if (!L[c].on) continue;
     BatchArgs b{};
     b.a = base;
@@ -2311,7 +2329,7 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
       const int K = 1 + shape / 2, stage = 1 - shape % 2;
       cprrtc_tuning t = best;
       t.warps_per_motion[c] = K;
-      if (class_warps_per_motion(ctx, t, pp->workers, c) != K) continue;  // no pairs here
+      if (class_warps_per_motion(ctx, t, pp->workers, c) != K) continue;  // no pairs: learned form
       t.stage_obstacles[c] = stage;
       t.ctas_per_sm[c] = 0;
       const ClassLaunch full = class_launch(ctx, bp, t, pp->workers, c);

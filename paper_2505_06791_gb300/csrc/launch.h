@@ -124,12 +124,11 @@ struct BatchArgs {
   float* pend_edges;         // per CTA slot: [workers][2][max_W * 8]
 };
 
-// Problem classes: 2 * constraint type + (W > 32). K = warps per worker: 1, or 2 (a warp
-// pair per motion, one waypoint per lane) for the classes of 33..64 waypoints in the plain
-// form (plan_batch_has_pairs).
+// Problem classes: 2 * constraint type + (W > 32). K = warps per worker: 1, or 2 in the
+// plain form (a warp pair per motion, split by waypoints in the classes of 33..64 waypoints,
+// by obstacles in the others).
 constexpr int kBatchClasses = 6;
 size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage, int K = 1);
-bool plan_batch_has_pairs(int cls);
 int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm = false, int K = 1);
 cudaError_t launch_plan_batch(int cls, BatchArgs b, const BatchTables& T, int grid, size_t smem,
                               int K, cudaStream_t stream);

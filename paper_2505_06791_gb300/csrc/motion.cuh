@@ -704,23 +704,27 @@ __device__ __forceinline__ unsigned swept_mask(const ObsView& v, const float4* s
 //     against each listed obstacle of that frame;
 //  3. the frame's robot spheres, for lanes whose bound touched the obstacle.
 //
-// With PAIR (a motion held by a warp pair, see SplitX), lane l holds waypoint wbase + l, the
-// walk covers this warp's waypoints only, any_hit is assumed, and the warp gives up as soon
-// as x->hit shows that the other warp found a collision in this motion (generation gen):
-// the pair's verdict is the flag, the count it returns covers this warp's part.
-template <int WPL, bool PAIR = false>
+// A motion shared by a warp pair (see SplitX) is split either by waypoints (PAIR: lane l
+// holds waypoint wbase + l and the walk covers this warp's waypoints) or by obstacles
+// (NSPLIT = 2: both warps hold every waypoint, and warp kw lists and walks only the chunks
+// c with c mod NSPLIT = kw, its swept bounds being the same as the other's). Either way
+// any_hit is assumed, and the warp gives up as soon as x->hit shows that the other warp
+// found a collision in this motion (generation gen): the pair's verdict is the flag, and the
+// count returned covers this warp's part.
+template <int WPL, bool PAIR = false, int NSPLIT = 1>
 __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev& sc,
                                               const float4* __restrict__ obs, const CcShared& S,
                                               const float (&q)[WPL][kMaxDof], int W, int i0,
                                               bool any_hit, WorkCount& work, bool early = true,
                                               bool wq_ready = false, int wbase = 0,
-                                              const SplitX* x = nullptr, int gen = 0) {
+                                              const SplitX* x = nullptr, int gen = 0, int kw = 0) {
+  constexpr bool kShared = PAIR || NSPLIT > 1;
   const int lane = threadIdx.x & 31;
   const int dof = rb.dof;
   const int n_obs = sc.n_sph + sc.n_box + sc.n_cap;
   // the other warp of a pair has found a collision in this motion (warp-uniform)
   auto other_hit = [&]() {
-    if constexpr (PAIR) {
+    if constexpr (kShared) {
       return __any_sync(kFull, *reinterpret_cast<const volatile int*>(&x->hit) == gen);
     } else {
       return false;
@@ -795,32 +799,38 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       const float rad = sqrtf(warp_max_exact(r2)) * 1.000001f + b.w + 1e-5f;
       if (lane == 0) S.sbnd[f] = make_float4(m0, m1, m2, rad);
     }
-    work.chains += n_act;
-    work.transforms += (unsigned)(n_act * (dof + 1));
+    if (NSPLIT == 1 || kw == 0) {  // both warps of an obstacle split sweep the same bounds
+      work.chains += n_act;
+      work.transforms += (unsigned)(n_act * (dof + 1));
+    }
     __syncwarp();
   }
   if (other_hit()) return -1;
 
   int best = 0x7fffffff;  // smallest colliding waypoint found so far
   const int n_chunks = sc.n_chunks();
-  int cb = 0;          // next group of 32 chunks to screen
-  unsigned near = 0u;  // chunks of the current group (base cb - 32) still to list
-  unsigned cfr = 0u;   // lane j: the frames whose swept bound chunk cb - 32 + j's box touches
+  // this warp's chunks as slots: slot t is chunk t * NSPLIT + kw (every chunk when NSPLIT = 1)
+  auto chunk_of = [&](int t) { return NSPLIT == 1 ? t : t * NSPLIT + kw; };
+  auto slots_below = [&](int c) { return NSPLIT == 1 ? c : (c - kw + NSPLIT - 1) / NSPLIT; };
+  const int n_slots = slots_below(n_chunks);
+  int cb = 0;          // next group of 32 slots to screen
+  unsigned near = 0u;  // slots of the current group (base cb - 32) still to list
+  unsigned cfr = 0u;   // lane j: the frames whose swept bound slot cb - 32 + j's chunk box touches
   bool listed_all = false;
   while (!listed_all) {
     // ---- candidate list: obstacles touching a swept bound, with the frames they touch ----
     int n_cand = 0;
     while (n_cand + 32 <= kCandMax) {
       if (!near) {
-        if (cb >= n_chunks) {
+        if (cb >= n_slots) {
           listed_all = true;
           break;
         }
         if (other_hit()) return -1;
         // lanes screen 32 chunks at once: chunk box against every swept frame bound
-        const int ch = cb + lane;
+        const int ch = chunk_of(cb + lane);
         cfr = 0u;
-        if (ch < n_chunks) {
+        if (cb + lane < n_slots) {
           const float4* cbx = obs + sc.chunk_off() + 2 * ch;
           const float4 lo = cbx[0], hi = cbx[1];
           cfr = frames_touched(S.sbnd, fmask, [&](float4 b) {
@@ -832,20 +842,20 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
                 });
         }
         near = __ballot_sync(kFull, cfr != 0u);
-        work.p_box += (unsigned)(rb.bound_count * min(32, n_chunks - cb));
+        work.p_box += (unsigned)(rb.bound_count * min(32, n_slots - cb));
         cb += 32;
         continue;
       }
       // up to 32 / kChunk touched chunks of one kind, kChunk lanes each (one code path)
-      const int base = cb - 32;  // chunk of bit 0 of `near`
-      const int kind = sc.chunk_kind(base + __ffs(near) - 1);
+      const int base = cb - 32;  // slot of bit 0 of `near`
+      const int kind = sc.chunk_kind(chunk_of(base + __ffs(near) - 1));
       const int cs = sc.chunks_sph(), cbx = sc.chunks_box();
       const int k_c1 = kind == 0 ? cs : kind == 1 ? cs + cbx : n_chunks;  // kind's chunk end
       const int k_o0 = kind == 0 ? 0 : kind == 1 ? sc.n_sph : sc.n_sph + sc.n_box;
       const int k_o1 = kind == 0 ? sc.n_sph : kind == 1 ? sc.n_sph + sc.n_box : n_obs;
       const int k_c0 = kind == 0 ? 0 : kind == 1 ? cs : cs + cbx;
-      // bits of `near` for chunks of this kind (chunk end relative to base, at most 32)
-      const int rel_end = k_c1 - base;
+      // bits of `near` for chunks of this kind (slot end relative to base, at most 32)
+      const int rel_end = slots_below(k_c1) - base;
       const unsigned kmask = near & (rel_end >= 32 ? kFull : (1u << rel_end) - 1u);
       unsigned m = kmask;
       int my_c = -1;
@@ -860,7 +870,7 @@ __device__ __forceinline__ int collide_motion(const RobotDev& rb, const SceneDev
       const unsigned my_fr = __shfl_sync(kFull, cfr, my_c >= 0 ? my_c - base : 0);
       int o = -1;
       unsigned mask = 0u;
-      if (my_c >= 0) o = k_o0 + (my_c - k_c0) * kChunk + lane % kChunk;
+      if (my_c >= 0) o = k_o0 + (chunk_of(my_c) - k_c0) * kChunk + lane % kChunk;
       const bool valid = o >= 0 && o < k_o1;
       int box_tests = 0;
       if (valid) mask = swept_mask(load_obstacle(sc, obs, o), S.sbnd, my_fr, box_tests);

@@ -334,6 +334,52 @@ __device__ __forceinline__ int validate_motion_pair(const RobotDev& rb, const Sc
   return x->hit == gen ? kCollision : kValid;
 }
 
+// validate_motion for a motion of at most 32 waypoints held by a warp pair split by obstacles,
+// this warp being half h: both warps run Alg. 1 on the whole motion (the same instructions on
+// the same inputs, so the same segment), each checks the chunks c with c mod 2 = h, and the
+// verdict goes through x->hit as in validate_motion_pair; it is that of
+// validate_motion<CT, 1>. Self-collision is checked by half 0 alone. Work counts: Alg. 1
+// updates and swept bounds by half 0, the listing and chain walks by each half for its part.
+template <int CT>
+__device__ __forceinline__ int validate_motion_osplit(const RobotDev& rb, const SceneDev& sc,
+                                                      const ConsDev& cs, int max_iters,
+                                                      MotionWork& work, WorkCount& wc,
+                                                      const float4* obs, const CcShared& S,
+                                                      const float* q0, const float* q1, int W,
+                                                      float (&q)[1][kMaxDof], const SelfMask* self,
+                                                      int h, SplitX* x, int bar, int gen) {
+  const int lane = threadIdx.x & 31;
+  const int dof = rb.dof;
+  const float tau = step_threshold(cs, q0, q1, W, dof);
+  interp(q0, q1, min(lane, W - 1), W, dof, q[0]);
+  const ProjResult pr = project_warp<CT, 1>(rb, cs, max_iters, q, W, tau, S.wq);
+  __syncwarp();
+  if (h == 0) {
+    work.proj += (unsigned)pr.updates;
+    wc.updates += (unsigned)pr.updates;
+  }
+  if (pr.status != kValid) return kProjFail;  // both halves: the same projection
+  int ff = collide_motion<1, false, 2>(rb, sc, obs, S, q, W, 1, true, wc, true, CT != kConsNone,
+                                       0, x, gen, h);
+  __syncwarp();
+  work.cc += (unsigned)(ff >= 0 ? ff : W - 1);
+  bool hit = ff >= 0;
+  if (h == 0 && !hit && self && self->on &&
+      !__any_sync(kFull, *reinterpret_cast<volatile int*>(&x->hit) == gen)) {
+    const bool hs = lane >= 1 && lane < W &&
+                    self_hit_waypoint(rb.dof, S.jnt, S.bnd, S.sph, S.foff, S.wq + lane * 9, *self);
+    wc.chains += (unsigned)(W - 1);
+    hit = __any_sync(kFull, hs);
+  }
+  if (hit && lane == 0) x->hit = gen;
+  pair_barrier(bar);
+  return x->hit == gen ? kCollision : kValid;
+}
+
+// How the warps of a worker share its motions: one warp (kSplitNone), or a pair split by
+// waypoints (W = 33..64) or by obstacles (W <= 32).
+enum : int { kSplitNone = 0, kSplitWaypoints = 1, kSplitObstacles = 2 };
+
 // Register cap of the planner kernel (0: the compiler's choice). Fewer registers let more
 // 8-warp CTAs share an SM at the price of some spills.
 #ifndef CPRRTC_PLAN_MAXNREG
@@ -346,20 +392,22 @@ __device__ __forceinline__ int validate_motion_pair(const RobotDev& rb, const Sc
 #endif
 
 
-// The planner for one problem, run by the whole CTA (one warp per worker, or with K = 2 a warp
-// pair per worker: motions of 33..64 waypoints split by waypoints, see SplitX; the pair's
+// The planner for one problem, run by the whole CTA (one warp per worker, or with SPLIT a warp
+// pair per worker, its motions split by waypoints or by obstacles, see SplitX; the pairs'
 // exchange areas xs[worker]). Shared memory (robot tables, obstacles, per-warp scratch) is
 // staged by the caller. Both warps of a pair follow the same chain (identical copies of its
 // state, computed from identical inputs); the pair's half 0 writes the worker's shared flags,
-// tree nodes and path, each half its own waypoints of a motion's edge.
-template <int CT, int WPL, bool SEQ = false, bool WARM = false, int K = 1>
+// tree nodes and path, and a motion's edge is written by the warps holding its waypoints
+// (each its half when split by waypoints, half 0 when split by obstacles).
+template <int CT, int WPL, bool SEQ = false, bool WARM = false, int SPLIT = kSplitNone>
 __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
                                              const CcShared& S, PlanShared* sh,
                                              WorkCount& wc, const SelfMask& self,
                                              const MlpView* net = nullptr, SplitX* xs = nullptr) {
-  static_assert(K == 1 || (K == 2 && WPL == 1 && !SEQ && !WARM), "warp pairs: plain Alg. 1, one waypoint per lane");
+  static_assert(SPLIT == kSplitNone || (WPL == 1 && !SEQ && !WARM), "warp pairs: plain Alg. 1, one waypoint per lane");
+  constexpr int K = SPLIT == kSplitNone ? 1 : 2;
   const int p = P.p;
   const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;  // physical warp
   const int warp = pw / K, h = pw % K;                        // worker, half of its pair
@@ -435,23 +483,32 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     // warm-starts extend motions only: connect steps and the closing hop head for a node on
     // the manifold
     int st;
-    if constexpr (K == 1) {
-      st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc,
-                                               obs, S, cur, q1, W, q,
+    const int iters = mode == 2 ? 1 : cs.max_iters;
+    if constexpr (SPLIT == kSplitNone) {
+      st = validate_motion<CT, WPL, SEQ, WARM>(rb, sc, cs, iters, work, wc, obs, S, cur, q1, W, q,
                                                WARM && mode == 0 ? net : nullptr,
                                                a.warm_refine, qe, &self);
+    } else if constexpr (SPLIT == kSplitWaypoints) {
+      st = validate_motion_pair<CT>(rb, sc, cs, iters, work, wc, obs, S, cur, q1, W, q, &self, h,
+                                    xs + warp, 1 + warp, r + 1);
     } else {
-      st = validate_motion_pair<CT>(rb, sc, cs, mode == 2 ? 1 : cs.max_iters, work, wc, obs, S,
-                                    cur, q1, W, q, &self, h, xs + warp, 1 + warp, r + 1);
+      st = validate_motion_osplit<CT>(rb, sc, cs, iters, work, wc, obs, S, cur, q1, W, q, &self, h,
+                                      xs + warp, 1 + warp, r + 1);
     }
+    // this warp's part of an edge: its waypoints (every waypoint, or none for half 1 of an
+    // obstacle split)
+    auto store_mine = [&](float* dst) {
+      if (SPLIT != kSplitObstacles || h == 0)
+        store_edge<WPL>(dst, q, W, dof, SPLIT == kSplitWaypoints ? 32 * h : 0);
+    };
     wp += W;
     int add = 0, conn = 0;
     if (st == kValid) {
       if (mode == 2) {
         conn = 1;
-        store_edge<WPL>(wedge + wd, q, W, dof, 32 * h);
+        store_mine(wedge + wd);
       } else {
-        if constexpr (K == 1) {
+        if constexpr (SPLIT != kSplitWaypoints) {
           last_waypoint<WPL>(q, W, dof, qe);
         } else {
           __syncwarp();  // the pair barrier made x->qend visible
@@ -495,7 +552,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       dst = count_of(ta) + off;
       if (dst < a.max_nodes) {
         if (lane < 8 && h == 0) nodes(ta)[(size_t)dst * 8 + lane] = qe[lane];
-        store_edge<WPL>(edges(ta) + (size_t)dst * wd, q, W, dof, 32 * h);
+        store_mine(edges(ta) + (size_t)dst * wd);
         if (lane == 0 && h == 0) parent(ta)[dst] = last;
       } else {
         dst = -1;
@@ -693,8 +750,9 @@ __host__ __device__ constexpr size_t plan_extra_bytes(int K) {
   return ((sizeof(PlanShared) + 15) & ~size_t(15)) + (K > 1 ? sizeof(SplitX) * kMaxWorkers / 2 : 0);
 }
 
-template <int CT, int WPL, bool WARM, int K = 1>
+template <int CT, int WPL, bool WARM, int SPLIT = kSplitNone>
 __device__ __forceinline__ void plan_batch_body(const BatchArgs& b, const BatchTables& T) {
+  constexpr int K = SPLIT == kSplitNone ? 1 : 2;
   extern __shared__ __align__(16) char smem[];
   __shared__ SceneDev s_sc;
   __shared__ int s_t, s_robot, s_cons;
@@ -750,8 +808,8 @@ __device__ __forceinline__ void plan_batch_body(const BatchArgs& b, const BatchT
     const SceneDev sc = s_sc;  // in registers: the collision walk reads it in its inner loops
     const SelfMask self = T.self[s_robot];
     const MlpView* net = WARM && T.nets[s_robot][s_cons].dof ? &T.nets[s_robot][s_cons] : nullptr;
-    plan_problem<CT, WPL, false, WARM, K>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S, sh,
-                                          wc, self, net, xs);
+    plan_problem<CT, WPL, false, WARM, SPLIT>(rb, sc, a.stage_obs ? s_obs : sc.obs, cs, a, sh->pv, S,
+                                              sh, wc, self, net, xs);
   }
   wc.flush(a.work_counters);
 }
@@ -768,21 +826,24 @@ __global__ void __launch_bounds__(256, 2) plan_batch_warm_kernel(BatchArgs b,
   plan_batch_body<CT, WPL, true>(b, T);
 }
 
-// A class of 33..64-waypoint problems with a warp pair per worker (one waypoint per lane):
-// up to 16 warps, held to the 128 registers that let them share one SM.
-template <int CT>
+// A class with a warp pair per worker, split by waypoints (33..64 waypoints, one per lane) or
+// by obstacles (up to 32 waypoints): up to 16 warps, held to the 128 registers that let them
+// share one SM.
+template <int CT, int SPLIT>
 __global__ void __launch_bounds__(512, 1) plan_batch_pair_kernel(BatchArgs b,
                                                                  const __grid_constant__ BatchTables T) {
-  plan_batch_body<CT, 1, false, 2>(b, T);
+  plan_batch_body<CT, 1, false, SPLIT>(b, T);
 }
 
 static const void* plan_batch_fn(int cls, bool warm = false, int K = 1) {
-  if (K == 2) {  // warp pairs: the classes of 33..64 waypoints, plain form
+  if (K == 2) {  // warp pairs, plain form
     switch (cls) {
-      case 1: return (const void*)plan_batch_pair_kernel<kConsNone>;
-      case 3: return (const void*)plan_batch_pair_kernel<kConsRollPitch>;
-      case 5: return (const void*)plan_batch_pair_kernel<kConsZPlane>;
-      default: return nullptr;
+      case 0: return (const void*)plan_batch_pair_kernel<kConsNone, kSplitObstacles>;
+      case 1: return (const void*)plan_batch_pair_kernel<kConsNone, kSplitWaypoints>;
+      case 2: return (const void*)plan_batch_pair_kernel<kConsRollPitch, kSplitObstacles>;
+      case 3: return (const void*)plan_batch_pair_kernel<kConsRollPitch, kSplitWaypoints>;
+      case 4: return (const void*)plan_batch_pair_kernel<kConsZPlane, kSplitObstacles>;
+      default: return (const void*)plan_batch_pair_kernel<kConsZPlane, kSplitWaypoints>;
     }
   }
   if (warm) {  // the learned form of the roll-pitch and z-plane classes
@@ -807,8 +868,6 @@ static const void* plan_batch_fn(int cls, bool warm = false, int K = 1) {
 size_t plan_batch_smem_bytes(int max_scene_f4, int max_S, int max_W, int workers, bool stage, int K) {
   return SmemLayout(stage ? max_scene_f4 : 0, max_S, max_W, workers * K, plan_extra_bytes(K)).total;
 }
-
-bool plan_batch_has_pairs(int cls) { return plan_batch_fn(cls, false, 2) != nullptr; }
 
 int plan_batch_occupancy(int cls, int workers, size_t smem, bool warm, int K) {
   const void* fn = plan_batch_fn(cls, warm, K);

@@ -117,11 +117,13 @@ def test_mixed_batch_paths_graph_and_tuning(torch_cuda, oracle_mod):
 
 
 def test_warp_pairs_plan_as_one_warp(torch_cuda, oracle_mod):
-    """Problems of 33..64 waypoints planned with a warp pair per worker (one waypoint per
-    lane, Alg. 1 in step over both warps, each checking its own waypoints) give the paths,
-    edges, rounds and waypoints of the one-warp kernels, with W = 33 (a pair whose second
-    warp holds one waypoint), 47 and 64, every constraint, self-collision pairs on one robot,
-    and the default tuning; the paths pass the oracle's re-validation."""
+    """Every class planned with a warp pair per worker gives the paths, edges, rounds and
+    waypoints of the one-warp kernels: problems of 33..64 waypoints split by waypoints (one
+    per lane, Alg. 1 in step over both warps, each checking its own waypoints), with W = 33
+    (a pair whose second warp holds one waypoint), 47 and 64; problems of 16 and 32 waypoints
+    split by obstacles (both warps project, each checks half of the obstacle chunks). Every
+    constraint, self-collision pairs on one robot; the long problems' paths pass the oracle's
+    re-validation."""
     from paper_2505_06791_gb300.capi import Context, default_tuning as _tuning
     torch = torch_cuda
     robots, cons, probs, scenes = S.make_batch_mix(30, 4242, max_obstacles=1500)
