@@ -1903,7 +1903,6 @@ cprrtc_tuning default_tuning() {
 // Warps per worker class c runs with: 2 only where asked, in the plain form, with at most 8
 // workers (16 warps).
 int class_warps_per_motion(cprrtc_ctx* ctx, const cprrtc_tuning& t, int workers, int c) {
-  (void)c;
   return (t.warps_per_motion[c] == 2 && ctx->plan_warm <= 0 && 2 * workers <= kMaxWorkers) ? 2 : 1;
 }
 
