@@ -727,6 +727,11 @@ def run_batch(args, world, rank, local):
                    "constraints": ["none", "roll-pitch", "z-plane"], "W": [16, 32, 64],
                    "max_rounds": BATCH_PARAMS["max_rounds"],
                    "workers_per_problem": BATCH_PARAMS["workers"],
+                   "recipe_departure": "obstacle sizes shrink by (200/n)^(1/3) above 200 obstacles "
+                                       "(the mix names counts, not sizes; full-size primitives at "
+                                       "thousands per scene leave few collision-free starts); one "
+                                       "CUDA graph of six concurrent class kernels (constraint type "
+                                       "x W class) instead of a single persistent kernel",
                    "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "p50_plan_ms": float(np.percentile(ms[solved], 50)) if solved.any() else None,
@@ -1455,6 +1460,10 @@ def run_warmstart(args, world, rank, local):
                                  "capsules": len(sc.cap)},
                    "constraint": "roll-pitch", "refine_iters": WS_REFINE,
                    "max_iters": c.max_iters, "l2": "flushed (256 MB write) between steps",
+                   "recipe_departure": "the 2^20 training pairs are projections by the library's "
+                                       "cprrtc_project_configs, not the oracle's (the bench runs "
+                                       "the oracle only in its CPU-baseline leg; the tests train "
+                                       "on oracle pairs)",
                    "parallelism": f"replicas x{world}"},
         "plain": {"value": value_plain, "ms_per_step": ms_plain / args.steps,
                   "projected": int(p_ok.sum()), "success_rate": float(p_ok.mean()),
