@@ -447,10 +447,14 @@ typedef struct {
 } cprrtc_problem;
 
 /* Launch shape of each problem class (class = 2 * constraint type + (W > 32)): CTAs per SM
- * (0: as many as fit), whether the class stages its obstacles into shared memory (else they
- * are read through L1), and warps per motion: 1, or 2 (each worker's motion held by a warp
- * pair; plain form only, at most 8 workers; any other value means 1). A pair splits a motion
- * of 33..64 waypoints by waypoints (one per lane: Alg. 1 runs in step on both warps, each
+ * of its one-warp part (0: as many as fit), whether the class stages its obstacles into
+ * shared memory (else they are read through L1), warps per motion, and pair_problems.
+ * Warps per motion is 1, or 2 for the whole class on warp pairs (each worker's motion held
+ * by two warps; plain form only, at most 8 workers; any other value means 1). With 1,
+ * pair_problems (0 or more) of the class's problems, its heaviest by the batch's cost
+ * estimate, are planned on warp pairs all the same, and the rest with one warp per motion:
+ * the heaviest problems end the batch, and pairs shorten them. A pair splits a motion of
+ * 33..64 waypoints by waypoints (one per lane: Alg. 1 runs in step on both warps, each
  * checks its own waypoints for collisions) and a motion of up to 32 waypoints by obstacles
  * (both warps run Alg. 1 on the whole motion, each checks half of the obstacle chunks).
  * None of them changes any result: a problem's search depends only on its own inputs and
@@ -461,6 +465,7 @@ typedef struct {
   int ctas_per_sm[CPRRTC_BATCH_CLASSES];
   int stage_obstacles[CPRRTC_BATCH_CLASSES];
   int warps_per_motion[CPRRTC_BATCH_CLASSES];
+  int pair_problems[CPRRTC_BATCH_CLASSES];
 } cprrtc_tuning;
 
 /* Plans n problems of mixed robots, constraints, scenes and W in one go: every problem class
@@ -483,7 +488,8 @@ int cprrtc_plan_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n, co
 
 /* Autotuner: for every class present in the batch, times short runs (trial_rounds rounds)
  * of each launch shape (obstacles staged or read through L1; 1 up to the fitting number of
- * CTAs per SM; one warp or a warp pair per motion, the latter not in the learned form) and keeps
+ * CTAs per SM; one warp per motion with none, 4 or 16 of the class's heaviest problems on warp
+ * pairs, or warp pairs for the whole class; no pairs in the learned form) and keeps
  * the shape with the most waypoints validated per second. The result is written to *out (may be NULL) and becomes the default of later
  * batch calls on this context. start, goal: device or host, as cprrtc_plan_batch. The trial
  * outputs go to library buffers; returns after the trials. Errors: as cprrtc_plan_batch,

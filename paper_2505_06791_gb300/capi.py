@@ -64,23 +64,27 @@ BATCH_CLASSES = 6
 class cprrtc_tuning(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int * BATCH_CLASSES),
                 ("stage_obstacles", C.c_int * BATCH_CLASSES),
-                ("warps_per_motion", C.c_int * BATCH_CLASSES)]
+                ("warps_per_motion", C.c_int * BATCH_CLASSES),
+                ("pair_problems", C.c_int * BATCH_CLASSES)]
 
     def as_dict(self):
         return {"ctas_per_sm": list(self.ctas_per_sm),
                 "stage_obstacles": list(self.stage_obstacles),
-                "warps_per_motion": list(self.warps_per_motion)}
+                "warps_per_motion": list(self.warps_per_motion),
+                "pair_problems": list(self.pair_problems)}
 
 
-def default_tuning(warps_per_motion: int = 1) -> "cprrtc_tuning":
+def default_tuning(warps_per_motion: int = 1, pair_problems: int = 0) -> "cprrtc_tuning":
     """The library's launch shapes when no tuning is given or tuned: as many CTAs per SM as
-    fit, obstacles staged when they fit, `warps_per_motion` warps per motion (1; 2 takes
-    warp pairs where a class allows them)."""
+    fit, obstacles staged when they fit, `warps_per_motion` warps per motion (1; 2: every
+    class on warp pairs) and `pair_problems` of each class's heaviest problems on warp pairs
+    (0)."""
     t = cprrtc_tuning()
     for c in range(BATCH_CLASSES):
         t.ctas_per_sm[c] = 0
         t.stage_obstacles[c] = 1
         t.warps_per_motion[c] = warps_per_motion
+        t.pair_problems[c] = pair_problems
     return t
 
 

@@ -81,9 +81,9 @@ struct cprrtc_ctx {
   bool has_tuned = false;
   BatchRes batch_res, graph_res;
   const BatchRes* last_batch = nullptr;  // the buffers of the last batch run (for its spans)
-  cudaStream_t side[kBatchClasses] = {};
+  cudaStream_t side[2 * kBatchClasses] = {};  // one per batch part (two per class)
   cudaEvent_t ev_fork = nullptr;
-  cudaEvent_t ev_join[kBatchClasses] = {};
+  cudaEvent_t ev_join[2 * kBatchClasses] = {};
   cudaGraphExec_t graph_exec = nullptr;
   // collision checking in GEMM form
   int cc_mode = CPRRTC_CC_EXACT;
@@ -555,7 +555,7 @@ int cprrtc_destroy(cprrtc_ctx* ctx) {
     cudaFree(r->d_span);
   }
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
-  for (int c = 0; c < kBatchClasses; ++c) {
+  for (int c = 0; c < 2 * kBatchClasses; ++c) {
     if (ctx->side[c]) cudaStreamDestroy(ctx->side[c]);
     if (ctx->ev_join[c]) cudaEventDestroy(ctx->ev_join[c]);
   }
@@ -1834,6 +1834,7 @@ struct BatchPlan {
   int n = 0;
   std::vector<int4> probs;
   std::vector<int> order;            // per class, concatenated
+  std::vector<double> cost;          // estimated cost of order[i] (see prepare_batch)
   int off[kBatchClasses + 1] = {};   // class c: order[off[c] .. off[c + 1])
   int max_W[kBatchClasses] = {}, max_S[kBatchClasses] = {}, max_f4[kBatchClasses] = {};
   int max_W_all = 0;
@@ -1884,7 +1885,10 @@ int prepare_batch(cprrtc_ctx* ctx, const cprrtc_problem* probs, int n, BatchPlan
                        return a.first > b.first;
                      });
     bp.off[c] = (int)bp.order.size();
-    for (auto& e : cls[c]) bp.order.push_back(e.second);
+    for (auto& e : cls[c]) {
+      bp.order.push_back(e.second);
+      bp.cost.push_back(e.first);
+    }
   }
   bp.off[kBatchClasses] = (int)bp.order.size();
   return CPRRTC_OK;
@@ -1896,50 +1900,88 @@ cprrtc_tuning default_tuning() {
     t.ctas_per_sm[c] = 0;
     t.stage_obstacles[c] = 1;
     t.warps_per_motion[c] = 1;
+    t.pair_problems[c] = 0;
   }
   return t;
 }
 
-// Warps per worker class c runs with: 2 only where asked, in the plain form, with at most 8
-// workers (16 warps).
-int class_warps_per_motion(cprrtc_ctx* ctx, const cprrtc_tuning& t, int workers, int c) {
-  return (t.warps_per_motion[c] == 2 && ctx->plan_warm <= 0 && 2 * workers <= kMaxWorkers) ? 2 : 1;
+// Whether class c may run warp pairs: plain form, at most 8 workers (16 warps).
+bool pairs_allowed(cprrtc_ctx* ctx, int workers) {
+  return ctx->plan_warm <= 0 && 2 * workers <= kMaxWorkers;
 }
 
-// Shared memory and grid of class c under tuning t (stage falls back to L1 if it does not fit).
-struct ClassLaunch {
+// One launch of a batch: part 0 of class c plans its first n problems in longest-first
+// order with warp pairs (the whole class with warps_per_motion = 2, else its pair_problems
+// heaviest), part 1 the others with one warp per motion. Each part has its own queue
+// counter, side stream and scratch slots.
+constexpr int kBatchParts = 2 * kBatchClasses;
+struct PartLaunch {
   bool on = false;
+  int cls = 0, first = 0, n = 0;  // problems order[off[cls] + first .. + n)
   int workers = 8, grid = 0, stage = 0, K = 1, per_sm = 0;
-  size_t smem = 0;
+  size_t smem = 0, slot_bytes = 0;
+  double work = 0.0;
 };
 
-ClassLaunch class_launch(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuning& t, int workers,
-                         int c) {
-  ClassLaunch L;
-  const int nc = bp.off[c + 1] - bp.off[c];
-  if (nc == 0) return L;
-  L.workers = workers;
-  L.K = class_warps_per_motion(ctx, t, workers, c);
-  L.stage = t.stage_obstacles[c] ? 1 : 0;
-  L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, L.stage, L.K);
-  if (L.smem > ctx->dev.smem_optin) {
-    L.stage = 0;
-    L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], L.workers, false, L.K);
+// Plans the parts of the classes in cls_mask under tuning t. A part that cannot be launched
+// (shared memory or registers beyond an SM) is E_UNSUPPORTED.
+int batch_parts(cprrtc_ctx* ctx, const BatchPlan& bp, const cprrtc_tuning& t, int workers,
+                size_t max_nodes, unsigned cls_mask, PartLaunch (&P)[kBatchParts]) {
+  for (auto& q : P) q = PartLaunch{};
+  for (int c = 0; c < kBatchClasses; ++c) {
+    const int nc = bp.off[c + 1] - bp.off[c];
+    if (!((cls_mask >> c) & 1u) || nc == 0) continue;
+    const bool pairs = pairs_allowed(ctx, workers);
+    const int n_pair = !pairs ? 0 : t.warps_per_motion[c] == 2 ? nc : std::max(0, std::min(nc, t.pair_problems[c]));
+    for (int part = 0; part < 2; ++part) {
+      PartLaunch& L = P[2 * c + part];
+      L.cls = c;
+      L.first = part == 0 ? 0 : n_pair;
+      L.n = part == 0 ? n_pair : nc - n_pair;
+      if (L.n == 0) continue;
+      for (int i = L.first; i < L.first + L.n; ++i) L.work += bp.cost[bp.off[c] + i];
+      L.workers = workers;
+      L.K = part == 0 ? 2 : 1;
+      L.stage = t.stage_obstacles[c] ? 1 : 0;
+      L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], workers, L.stage, L.K);
+      if (L.smem > ctx->dev.smem_optin) {
+        L.stage = 0;
+        L.smem = plan_batch_smem_bytes(bp.max_f4[c], bp.max_S[c], bp.max_W[c], workers, false, L.K);
+      }
+      const int occ = L.smem > ctx->dev.smem_optin
+                          ? 0
+                          : plan_batch_occupancy(c, workers, L.smem, ctx->plan_warm > 0, L.K);
+      if (occ < 1)
+        return fail(ctx, CPRRTC_E_UNSUPPORTED, "batch: class " + std::to_string(c) + " does not fit an SM");
+      L.per_sm = part == 1 && t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
+      const size_t ew = (size_t)bp.max_W[c] * 8;
+      L.slot_bytes = 2 * max_nodes * 8 * 4 + 2 * max_nodes * 4 + 2 * max_nodes * ew * 4 +
+                     (size_t)workers * 8 * 4 + (size_t)workers * 2 * ew * 4;
+    }
   }
-  if (L.smem > ctx->dev.smem_optin) return L;
-  const int occ = plan_batch_occupancy(c, L.workers, L.smem, ctx->plan_warm > 0, L.K);
-  if (occ < 1) return L;
-  const int per_sm = t.ctas_per_sm[c] > 0 ? std::min(t.ctas_per_sm[c], occ) : occ;
-  L.per_sm = per_sm;
-  // The classes run concurrently, so each gets the share of the SMs that its estimated work
-  // is of the batch's: every class's CTAs are resident from the start and begin with their
-  // longest problems (a class given every SM would hold them until its queue is empty, and
-  // the classes launched after it would start their longest problems late).
-  const double share = bp.work_all > 0.0 ? bp.work[c] / bp.work_all : 1.0;
-  const int sms = std::max(1, (int)std::floor(share * ctx->dev.sm_count));
-  L.grid = std::min(nc, per_sm * sms);
-  L.on = L.grid > 0;
-  return L;
+  // The parts run concurrently, so each gets the share of the SMs that its estimated work is
+  // of the batch's: every part's CTAs are resident from the start and begin with their
+  // longest problems (a part given every SM would hold them until its queue is empty, and
+  // the parts launched after it would start their longest problems late).
+  for (auto& L : P) {
+    if (L.n == 0) continue;
+    const double share = bp.work_all > 0.0 ? L.work / bp.work_all : 1.0;
+    const int sms = std::max(1, (int)std::floor(share * ctx->dev.sm_count));
+    L.grid = std::min(L.n, L.per_sm * sms);
+    L.on = L.grid > 0;
+  }
+  return CPRRTC_OK;
+}
+
+// Scratch of the parts, each part's slots 256-byte aligned, in part order.
+size_t parts_scratch(const PartLaunch (&P)[kBatchParts], size_t (*off)[kBatchParts + 1] = nullptr) {
+  size_t total = 0;
+  for (int i = 0; i < kBatchParts; ++i) {
+    if (off) (*off)[i] = total;
+    if (P[i].on) total += (P[i].slot_bytes * P[i].grid + 255) & ~size_t(255);
+  }
+  if (off) (*off)[kBatchParts] = total;
+  return total;
 }
 
 template <class T>
@@ -1954,33 +1996,24 @@ int ensure(cprrtc_ctx* ctx, T** p, size_t* cap, size_t count) {
   return CPRRTC_OK;
 }
 
-// Uploads the problems and orders, sizes the per-CTA scratch and launches the classes in
-// cls_mask concurrently on side streams joined back into the context's stream.
+// Uploads the problems and orders, sizes the per-CTA scratch and launches the parts of the
+// classes in cls_mask concurrently on side streams joined back into the context's stream.
 int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base,
               const cprrtc_tuning& t, unsigned cls_mask, bool capturing) {
-  ClassLaunch L[kBatchClasses];
-  size_t scratch_off[kBatchClasses + 1] = {};
+  PartLaunch P[kBatchParts];
   const size_t MN = (size_t)base.max_nodes;
-  for (int c = 0; c < kBatchClasses; ++c) {
-    scratch_off[c + 1] = scratch_off[c];
-    if (!((cls_mask >> c) & 1u)) continue;
-    L[c] = class_launch(ctx, bp, t, base.workers, c);
-    if (bp.off[c + 1] > bp.off[c] && !L[c].on)
-      return fail(ctx, CPRRTC_E_UNSUPPORTED, "batch: class " + std::to_string(c) + " does not fit an SM");
-    if (!L[c].on) continue;
-    const size_t ew = (size_t)bp.max_W[c] * 8;
-    const size_t slot = 2 * MN * 8 * 4 + 2 * MN * 4 + 2 * MN * ew * 4 +
-                        (size_t)L[c].workers * 8 * 4 + (size_t)L[c].workers * 2 * ew * 4;
-    scratch_off[c + 1] = scratch_off[c] + ((slot * L[c].grid + 255) & ~size_t(255));
-  }
+  int rc = batch_parts(ctx, bp, t, base.workers, MN, cls_mask, P);
+  if (rc) return rc;
+  size_t scratch_off[kBatchParts + 1];
+  parts_scratch(P, &scratch_off);
   if (!capturing) {
-    int rc = ensure(ctx, &res.d_probs, &res.probs_cap, bp.probs.size());
+    rc = ensure(ctx, &res.d_probs, &res.probs_cap, bp.probs.size());
     if (!rc) rc = ensure(ctx, &res.d_order, &res.order_cap, bp.order.size());
     if (!rc && !res.d_counters) {
-      cudaError_t e = cudaMalloc(&res.d_counters, kBatchClasses * sizeof(unsigned));
+      cudaError_t e = cudaMalloc(&res.d_counters, kBatchParts * sizeof(unsigned));
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "batch counters");
     }
-    if (!rc) rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, scratch_off[kBatchClasses]);
+    if (!rc) rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, scratch_off[kBatchParts]);
     if (!rc) rc = ensure(ctx, &res.d_span, &res.span_cap, 2 * (size_t)bp.n);
     if (!rc && bp.n > 0) {
       cudaError_t e = cudaMemsetAsync(res.d_span, 0, 2 * (size_t)bp.n * sizeof(long long), ctx->stream);
@@ -2008,47 +2041,49 @@ int run_batch(cprrtc_ctx* ctx, const BatchPlan& bp, BatchRes& res, PlanArgs base
   if (!ctx->ev_fork) {
     if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
       return cuda_fail(ctx, cudaGetLastError(), "batch events");
-    for (int c = 0; c < kBatchClasses; ++c)
-      if (cudaStreamCreateWithFlags(&ctx->side[c], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ctx->ev_join[c], cudaEventDisableTiming) != cudaSuccess)
+    for (int i = 0; i < kBatchParts; ++i)
+      if (cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
         return cuda_fail(ctx, cudaGetLastError(), "batch streams");
   }
   cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch fork");
-  // Launch order: classes whose CTAs take a whole SM first, then by estimated work. The block
+  // Launch order: parts whose CTAs take a whole SM first, then by estimated work. The block
   // scheduler spreads a grid's CTAs over the SMs; CTAs that hold half an SM, placed first,
   // would leave no whole SM free for the others until they finish.
-  int order[kBatchClasses];
-  for (int c = 0; c < kBatchClasses; ++c) order[c] = c;
-  std::stable_sort(order, order + kBatchClasses, [&](int x, int y) {
-    if (L[x].per_sm != L[y].per_sm) return L[x].per_sm < L[y].per_sm;
-    return bp.work[x] > bp.work[y];
+  int order[kBatchParts];
+  for (int i = 0; i < kBatchParts; ++i) order[i] = i;
+  std::stable_sort(order, order + kBatchParts, [&](int x, int y) {
+    if (P[x].per_sm != P[y].per_sm) return P[x].per_sm < P[y].per_sm;
+    return P[x].work > P[y].work;
   });
-  for (int c : order) {
-    if (!L[c].on) continue;
+  for (int i : order) {
+    const PartLaunch& L = P[i];
+    if (!L.on) continue;
+    const int c = L.cls;
     BatchArgs b{};
     b.a = base;
     b.a.span = res.d_span;
-    b.a.stage_obs = L[c].stage;
+    b.a.stage_obs = L.stage;
     b.a.max_scene_f4 = bp.max_f4[c];
     b.problems = res.d_probs;
-    b.order = res.d_order + bp.off[c];
-    b.n_class = bp.off[c + 1] - bp.off[c];
-    b.counter = res.d_counters + c;
+    b.order = res.d_order + bp.off[c] + L.first;
+    b.n_class = L.n;
+    b.counter = res.d_counters + i;
     b.max_S = bp.max_S[c];
     b.max_W = bp.max_W[c];
     b.out_max_W = bp.max_W_all;
-    const size_t ew = (size_t)bp.max_W[c] * 8, B = (size_t)L[c].workers, G = (size_t)L[c].grid;
-    char* base_p = res.d_scratch + scratch_off[c];
+    const size_t ew = (size_t)bp.max_W[c] * 8, B = (size_t)L.workers, G = (size_t)L.grid;
+    char* base_p = res.d_scratch + scratch_off[i];
     b.nodes = reinterpret_cast<float*>(base_p);
     b.parent = reinterpret_cast<int*>(b.nodes + G * 2 * MN * 8);
     b.edges = reinterpret_cast<float*>(b.parent + G * 2 * MN);
     b.pend = b.edges + G * 2 * MN * ew;
     b.pend_edges = b.pend + G * B * 8;
-    if ((e = cudaStreamWaitEvent(ctx->side[c], ctx->ev_fork, 0)) != cudaSuccess ||
-        (e = launch_plan_batch(c, b, T, L[c].grid, L[c].smem, L[c].K, ctx->side[c])) != cudaSuccess ||
-        (e = cudaEventRecord(ctx->ev_join[c], ctx->side[c])) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join[c], 0)) != cudaSuccess)
+    if ((e = cudaStreamWaitEvent(ctx->side[i], ctx->ev_fork, 0)) != cudaSuccess ||
+        (e = launch_plan_batch(c, b, T, L.grid, L.smem, L.K, ctx->side[i])) != cudaSuccess ||
+        (e = cudaEventRecord(ctx->ev_join[i], ctx->side[i])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0)) != cudaSuccess)
       return cuda_fail(ctx, e, "batch launch");
   }
   return CPRRTC_OK;
@@ -2323,19 +2358,27 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
   for (int c = 0; c < kBatchClasses && !rc; ++c) {
     if (bp.off[c + 1] == bp.off[c]) continue;
     double best_rate = -1.0;
-    // shapes: one warp per worker with obstacles staged / through L1, then warp pairs
-    for (int shape = 0; shape < 4 && !rc; ++shape) {
-      const int K = 1 + shape / 2, stage = 1 - shape % 2;
+    const int nc = bp.off[c + 1] - bp.off[c];
+    // shapes: one warp per worker with none, 4 or 16 of the class's heaviest problems on warp
+    // pairs, or the whole class on warp pairs (pairs = -1); obstacles staged or through L1;
+    // CTAs per SM of the one-warp part
+    const int pair_shapes[] = {0, 4, 16, -1};
+    for (int si = 0; si < 4 * 2 && !rc; ++si) {
+      const int pairs = pair_shapes[si / 2], stage = 1 - si % 2;
+      if (pairs != 0 && !pairs_allowed(ctx, pp->workers)) continue;
+      if (pairs > 0 && pairs >= nc) continue;  // the whole class: the pairs = -1 shape
       cprrtc_tuning t = best;
-      t.warps_per_motion[c] = K;
-      if (class_warps_per_motion(ctx, t, pp->workers, c) != K) continue;  // no pairs: learned form
+      t.warps_per_motion[c] = pairs < 0 ? 2 : 1;
+      t.pair_problems[c] = pairs < 0 ? 0 : pairs;
       t.stage_obstacles[c] = stage;
       t.ctas_per_sm[c] = 0;
-      const ClassLaunch full = class_launch(ctx, bp, t, pp->workers, c);
-      if (!full.on || full.stage != stage) continue;  // staging did not fit: tried as L1
-      const int occ = plan_batch_occupancy(c, full.workers, full.smem, ctx->plan_warm > 0, K);
-      for (int ctas = 1; ctas <= std::min(occ, 4) && !rc; ++ctas) {
-        t.ctas_per_sm[c] = ctas;
+      PartLaunch P[kBatchParts];
+      if (batch_parts(ctx, bp, t, pp->workers, (size_t)pp->max_nodes, 1u << c, P)) continue;  // does not fit
+      const PartLaunch &P0 = P[2 * c], &P1 = P[2 * c + 1];
+      if ((P0.n && P0.stage != stage) || (P1.n && P1.stage != stage)) continue;  // staging did not fit: tried as L1
+      const int max_ctas = P1.n ? std::min(P1.per_sm, 4) : 1;
+      for (int ctas = 1; ctas <= max_ctas && !rc; ++ctas) {
+        t.ctas_per_sm[c] = P1.n ? ctas : 0;
         cudaEventRecord(e0, ctx->stream);
         rc = run_batch(ctx, bp, ctx->batch_res, a, t, 1u << c, false);
         if (rc) break;
@@ -2354,8 +2397,9 @@ int cprrtc_autotune_batch(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n
         if (rate > best_rate) {
           best_rate = rate;
           best.stage_obstacles[c] = stage;
-          best.ctas_per_sm[c] = ctas;
-          best.warps_per_motion[c] = K;
+          best.ctas_per_sm[c] = t.ctas_per_sm[c];
+          best.warps_per_motion[c] = t.warps_per_motion[c];
+          best.pair_problems[c] = t.pair_problems[c];
         }
       }
     }
@@ -2402,18 +2446,10 @@ int cprrtc_batch_capture(cprrtc_ctx* ctx, const cprrtc_problem* problems, int n,
   if (rc) return rc;
   BatchRes& res = ctx->graph_res;
   {
-    // scratch for every class (run_batch with an empty mask sized nothing)
-    size_t need = 0;
-    const size_t MN = (size_t)pp->max_nodes;
-    for (int c = 0; c < kBatchClasses; ++c) {
-      const ClassLaunch L = class_launch(ctx, bp, t, pp->workers, c);
-      if (!L.on) continue;
-      const size_t ew = (size_t)bp.max_W[c] * 8;
-      const size_t slot = 2 * MN * 8 * 4 + 2 * MN * 4 + 2 * MN * ew * 4 +
-                          (size_t)L.workers * 8 * 4 + (size_t)L.workers * 2 * ew * 4;
-      need += (slot * L.grid + 255) & ~size_t(255);
-    }
-    rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, need);
+    // scratch for every part (run_batch with an empty mask sized nothing)
+    PartLaunch P[kBatchParts];
+    rc = batch_parts(ctx, bp, t, pp->workers, (size_t)pp->max_nodes, (1u << kBatchClasses) - 1u, P);
+    if (!rc) rc = ensure(ctx, &res.d_scratch, &res.scratch_cap, parts_scratch(P));
     if (rc) return rc;
   }
   if (!ctx->stream) return fail(ctx, CPRRTC_E_INVALID_ARG, "batch capture: needs a non-default stream");

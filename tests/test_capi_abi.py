@@ -40,8 +40,8 @@ def test_struct_layouts_match_header():
     names = re.findall(r"(\w+);", body)
     assert names == ["type", "target", "tol_task", "c_sm", "tau_floor", "tol_sm", "alpha",
                      "lambda", "max_iters", "line_y", "yaw"]
-    # launch shapes of the uneven batch: three int arrays, one entry per problem class
-    assert C.sizeof(capi.cprrtc_tuning) == 3 * capi.BATCH_CLASSES * 4
+    # launch shapes of the uneven batch: four int arrays, one entry per problem class
+    assert C.sizeof(capi.cprrtc_tuning) == 4 * capi.BATCH_CLASSES * 4
     body = hdr[:hdr.index("} cprrtc_tuning;")]
     body = re.sub(r"/\*.*?\*/", "", body[body.rindex("typedef struct {"):], flags=re.S)
     names = re.findall(r"int (\w+)\[CPRRTC_BATCH_CLASSES\];", body)

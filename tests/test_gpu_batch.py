@@ -121,7 +121,8 @@ def test_warp_pairs_plan_as_one_warp(torch_cuda, oracle_mod):
     waypoints of the one-warp kernels: problems of 33..64 waypoints split by waypoints (one
     per lane, Alg. 1 in step over both warps, each checking its own waypoints), with W = 33
     (a pair whose second warp holds one waypoint), 47 and 64; problems of 16 and 32 waypoints
-    split by obstacles (both warps project, each checks half of the obstacle chunks). Every
+    split by obstacles (both warps project, each checks half of the obstacle chunks); and
+    each class's two heaviest problems on pairs while the rest keep one warp. Every
     constraint, self-collision pairs on one robot; the long problems' paths pass the oracle's
     re-validation."""
     from paper_2505_06791_gb300.capi import Context, default_tuning as _tuning
@@ -147,9 +148,12 @@ def test_warp_pairs_plan_as_one_warp(torch_cuda, oracle_mod):
         one = to_np(ctx.plan_batch(probs, s, g, prm, tuning=_tuning(1), edges=True))
         pair = to_np(ctx.plan_batch(probs, s, g, prm, tuning=_tuning(2), edges=True))
         pair2 = to_np(ctx.plan_batch(probs, s, g, prm, tuning=_tuning(2), edges=True))
+        # each class's 2 heaviest problems on warp pairs, the others on one warp
+        mixed = to_np(ctx.plan_batch(probs, s, g, prm, tuning=_tuning(1, 2), edges=True))
     stream.synchronize()
     PB.assert_same_plans(one, pair, keys, dofs, Ws)
     PB.assert_same_plans(one, pair2, keys, dofs, Ws)
+    PB.assert_same_plans(one, mixed, keys, dofs, Ws)
     assert np.array_equal(one["work"][:, 0], pair["work"][:, 0])  # Alg. 1 updates
     long_solved = [p for p, (*_, W) in enumerate(probs) if W > 32 and one["path_len"][p] > 0]
     assert len(long_solved) >= 2, long_solved
