@@ -231,10 +231,14 @@ def test_batch_learned_form_equals_plan(torch_cuda, oracle_mod):
     learned_batch = to_np(ctx.plan_batch(probs, s8, g8, prm, edges=True))
     cnt = ctx.work_counters(reset=True)
     learned_plan = to_np(ctx.plan(s, g, prm))
+    # warp pairs asked for in the tuning: the learned form has none and keeps one warp
+    from paper_2505_06791_gb300.capi import default_tuning
+    learned_paired = to_np(ctx.plan_batch(probs, s8, g8, prm, tuning=default_tuning(2, 4), edges=True))
     torch.cuda.synchronize()
     assert cnt[6] > 0 and cnt[7] > 0, cnt
     for k in ("path_len", "rounds", "waypoints", "work"):
         assert np.array_equal(learned_batch[k], learned_plan[k]), k
+        assert np.array_equal(learned_paired[k], learned_batch[k]), k
     ctx.set_plan_warm_start(0)
     plain_plan = to_np(ctx.plan(s, g, prm))
     for k in ("path_len", "rounds", "waypoints", "work"):
