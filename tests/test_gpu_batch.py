@@ -249,3 +249,39 @@ def test_batch_learned_form_equals_plan(torch_cuda, oracle_mod):
     assert not issues, issues[:10]
     assert checked >= 1
     ctx.close()
+
+
+def test_batch_parts_edge_cases(torch_cuda, oracle_mod):
+    """Launch shapes at their edges plan as the default: warp pairs asked for with 12
+    workers (no room for pairs: one warp per motion, on problems of up to 32 waypoints, the
+    ones 12 warps fit), more heavy problems on pairs than a class holds (the whole class on
+    pairs), one heavy problem per class, and pairs on a batch of one class."""
+    from paper_2505_06791_gb300.capi import Context, default_tuning
+    torch = torch_cuda
+    robots, cons, probs, scenes = S.make_batch_mix(16, 9191, max_obstacles=300)
+    start, goal = PB.batch_start_goal(oracle_mod, robots, cons, probs, scenes, 23)
+    ctx = Context(0)
+    ctx.set_robot_table(robots)
+    ctx.set_constraint_table(cons)
+    ctx.set_scene_batch(scenes)
+    keys = ("path_len", "path", "rounds", "waypoints")
+    s = torch.from_numpy(start.astype(np.float32)).cuda()
+    g = torch.from_numpy(goal.astype(np.float32)).cuda()
+
+    def run(sel, workers, tuning):
+        prm = ctx.plan_params(range_=0.3, max_rounds=150, workers=workers, seed=4, max_path=200)
+        return to_np(ctx.plan_batch([probs[i] for i in sel], s[sel], g[sel], prm, tuning=tuning))
+
+    short = [i for i, p in enumerate(probs) if p[3] <= 32]
+    cls0 = [i for i, p in enumerate(probs)
+            if (cons[p[1]].type, p[3] > 32) == (cons[probs[0][1]].type, probs[0][3] > 32)]
+    assert len(short) >= 4 and len(cls0) >= 2
+    for sel, workers in ((short, 12), (list(range(len(probs))), 8), (cls0, 8)):
+        dofs = [robots[probs[i][0]].dof for i in sel]
+        ref = run(sel, workers, default_tuning())
+        for t in (default_tuning(2), default_tuning(1, 1000), default_tuning(1, 1)):
+            got = run(sel, workers, t)
+            PB.assert_same_plans(ref, got, keys, dofs)
+            if workers == 12:  # one warp per motion throughout: the work counts agree too
+                assert np.array_equal(ref["work"], got["work"])
+    ctx.close()
