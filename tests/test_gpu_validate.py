@@ -108,6 +108,35 @@ def test_z_plane_eight_dof_long_segments(torch_cuda, oracle_mod):
     print(stats)
 
 
+@pytest.mark.parametrize("W", [40, 64])
+def test_roll_pitch_long_segments(torch_cuda, oracle_mod, W):
+    """Roll–pitch motions of 40 and 64 waypoints (two per lane) among mixed obstacles match
+    the oracle under the parity protocol, with first colliding waypoints on both sides of
+    32, and turning early exit off changes nothing."""
+    rb = S.make_arm7(1)
+    sc = S.make_mixed_scene(4101, 40, 20, 12)
+    c = S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    q0 = manifold_starts(orc, rb, 96, 4102)
+    q1 = np.concatenate([S.nearby_configs(rb, q0[:64], 0.6, 4103), S.uniform_configs(rb, 32, 4104)])
+    stats, out, o = run_case(torch_cuda, oracle_mod, rb, sc, c, q0, q1, W)
+    st = parity.to_np(out["status"])
+    ff = parity.to_np(out["first_fail"])
+    assert (st == 2).sum() >= 10 and (st == 0).sum() >= 5, np.bincount(st, minlength=3)
+    # collisions in both of a lane's waypoint slots
+    hit = ff[st == 2]
+    assert (hit < 32).any() and (hit >= 32).any(), hit
+    ctx = make_ctx(rb, sc, c)
+    dq0 = torch_cuda.from_numpy(q0.astype(np.float32)).cuda()
+    dq1 = torch_cuda.from_numpy(q1.astype(np.float32)).cuda()
+    a = {k: parity.to_np(v).copy() for k, v in ctx.validate(dq0, dq1, W).items()}
+    ctx.set_early_exit(False)
+    b = {k: parity.to_np(v).copy() for k, v in ctx.validate(dq0, dq1, W).items()}
+    ctx.close()
+    for k in ("status", "first_fail", "iters", "q"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_six_dof_arm_and_tiny_robot(torch_cuda, oracle_mod):
     rb = S.make_arm6(4)
     sc = S.make_mixed_scene(5001, 10, 5, 5)
