@@ -1058,7 +1058,7 @@ static void* plan_worker(void* arg) {
     }
     int rounds = 0;
     long long wp = 0;
-    jb->path_len[p] = plan_one(jb->env, s, g, (uint32_t)p, jb->max_path,
+    jb->path_len[p] = plan_one(jb->env, s, g, jb->env->pp->first_problem + (uint32_t)p, jb->max_path,
                                jb->path + (size_t)p * jb->max_path * n, &rounds, &wp);
     if (jb->rounds) jb->rounds[p] = rounds;
     if (jb->waypoints) jb->waypoints[p] = wp;

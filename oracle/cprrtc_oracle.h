@@ -170,6 +170,7 @@ typedef struct {
   int max_nodes;          /* per tree */
   int max_connect;        /* greedy connect steps per extension */
   uint32_t seed;
+  uint32_t first_problem; /* problem p of a call draws with Philox problem index first_problem + p */
 } orc_plan_params;
 
 /* Plans each problem; path_len[p] = nodes in the path (0 on failure), path[p][max_path][dof],

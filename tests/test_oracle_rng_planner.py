@@ -65,6 +65,17 @@ def test_planner_paths_are_valid(oracle_mod):
     again = orc.plan(s, g, range_=0.3, W=32, max_rounds=300, n_workers=8, seed=5, n_threads=3)
     assert np.array_equal(again["path_len"], out["path_len"])
     assert np.array_equal(again["path"], out["path"])
+    # problem p alone, drawing with its batch index (R19), is problem p of the batch; with
+    # index 0 instead it is another search
+    for p in range(3):
+        alone = orc.plan(s[p:p + 1], g[p:p + 1], range_=0.3, W=32, max_rounds=300, n_workers=8,
+                         seed=5, first_problem=p)
+        for k in ("path_len", "rounds", "waypoints"):
+            assert alone[k][0] == out[k][p], (p, k)
+        assert np.array_equal(alone["path"][0], out["path"][p])
+    moved = orc.plan(s[1:2], g[1:2], range_=0.3, W=32, max_rounds=300, n_workers=8, seed=5)
+    assert not (moved["rounds"][0] == out["rounds"][1] and
+                np.array_equal(moved["path"][0], out["path"][1]))
 
 
 def test_free_space_connect_is_a_straight_greedy_chain(oracle_mod):
