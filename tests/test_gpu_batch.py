@@ -285,3 +285,47 @@ def test_batch_parts_edge_cases(torch_cuda, oracle_mod):
             if workers == 12:  # one warp per motion throughout: the work counts agree too
                 assert np.array_equal(ref["work"], got["work"])
     ctx.close()
+
+
+def test_mixed_batch_follows_the_oracle_planner(torch_cuda, oracle_mod):
+    """Every problem of a mixed batch (6/7/8 DOF, three constraints, W 16/32/64, up to 400
+    obstacles) runs the search of the oracle's planner with its own robot, constraint, scene,
+    W and batch index: the same rounds, path length and waypoints and nodes within 1e-4 on
+    most problems; a problem may part where an FP32 decision differs from FP64."""
+    import concurrent.futures as cf
+    import os
+    from paper_2505_06791_gb300.capi import Context
+    torch = torch_cuda
+    robots, cons, probs, scenes = S.make_batch_mix(18, 5151, max_obstacles=400)
+    start, goal = PB.batch_start_goal(oracle_mod, robots, cons, probs, scenes, 53)
+    ctx = Context(0)
+    ctx.set_robot_table(robots)
+    ctx.set_constraint_table(cons)
+    ctx.set_scene_batch(scenes)
+    prm = ctx.plan_params(range_=0.3, max_rounds=150, workers=8, max_nodes=2048, max_connect=32,
+                          seed=29, max_path=300)
+    s = torch.from_numpy(start.astype(np.float32)).cuda()
+    g = torch.from_numpy(goal.astype(np.float32)).cuda()
+    out = to_np(ctx.plan_batch(probs, s, g, prm))
+    ctx.close()
+
+    def oracle_plan(p):
+        r, c, sc, W = probs[p]
+        dof = robots[r].dof
+        return oracle_mod.Oracle(robots[r], scenes[sc], cons[c]).plan(
+            start[p:p + 1, :dof], goal[p:p + 1, :dof], range_=0.3, W=W, max_rounds=150, n_workers=8,
+            max_nodes=2048, max_connect=32, seed=29, max_path=300, first_problem=p)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        ref = list(ex.map(oracle_plan, range(len(probs))))
+    same = 0
+    for p, r in enumerate(ref):
+        L, dof = int(out["path_len"][p]), robots[probs[p][0]].dof
+        if L != int(r["path_len"][0]) or int(out["rounds"][p]) != int(r["rounds"][0]):
+            continue
+        same += 1
+        assert int(out["waypoints"][p]) == int(r["waypoints"][0]), p
+        if L > 0:
+            assert np.abs(out["path"][p, :L, :dof] - r["path"][0, :L]).max() < 1e-4, p
+    print("same search", same, "of", len(probs))
+    assert same >= len(probs) - 3, same
