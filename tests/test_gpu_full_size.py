@@ -39,7 +39,8 @@ def to_np(d):
 
 def test_full_planner_1000_problems_full_size(torch_cuda, oracle_mod):
     """1000 problems of 200 mixed obstacles, range 0.3, W = 32, 8 workers, 1000 rounds (the
-    headline launch): deterministic; 40 sampled solved paths re-validated by the oracle."""
+    headline launch): deterministic; 40 sampled solved paths re-validated by the oracle; 16
+    sampled problems run the oracle planner's search."""
     from paper_2505_06791_gb300.capi import Context
     torch = torch_cuda
     rb, c = S.make_arm7(1), S.roll_pitch(20)
@@ -71,6 +72,27 @@ def test_full_planner_1000_problems_full_size(torch_cuda, oracle_mod):
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3,
                                      problems=sorted(int(p) for p in sample))
     assert checked == 40 and not issues, issues[:10]
+    # the oracle's planner on 16 sampled problems, each alone with its batch index: the same
+    # search (rounds, path length, waypoints, nodes within 1e-4) unless an FP32 decision went
+    # the other way than in FP64 over the up to 8000 motions of its 1000 rounds
+    pick = sorted(int(p) for p in np.random.default_rng(6).choice(n, 16, replace=False))
+
+    def oracle_plan(p):
+        return oracle_mod.Oracle(rb, scenes[p], c).plan(
+            start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=1000, n_workers=8,
+            max_nodes=2048, max_connect=32, seed=11, first_problem=p)
+
+    same = 0
+    for p, r in zip(pick, pool_map(oracle_plan, pick)):
+        Lp = int(L[p])
+        if Lp != int(r["path_len"][0]) or int(out["rounds"][p]) != int(r["rounds"][0]):
+            continue
+        same += 1
+        assert int(out["waypoints"][p]) == int(r["waypoints"][0]), p
+        if Lp > 0:
+            assert np.abs(out["path"][p, :Lp] - r["path"][0, :Lp]).max() < 1e-4, p
+    print("same search as the oracle planner:", same, "of", len(pick))
+    assert same >= 13, same  # measured 16 of 16
     ctx.close()
 
 
