@@ -329,6 +329,20 @@ def test_plan_with_self_collision(torch_cuda, oracle_mod):
                                      self_pairs=pairs)
     assert not issues, issues[:10]
     assert checked >= 1
+    # and the oracle's planner with the same pairs runs the same search (R30)
+    import concurrent.futures as cf
+
+    def oracle_plan(p):
+        return oracle_mod.Oracle(rb, scenes[p], c, self_pairs=pairs).plan(
+            start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=400, n_workers=8,
+            max_nodes=2048, max_connect=32, seed=17, first_problem=p)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        ref = list(ex.map(oracle_plan, range(n)))
+    same = sum(int(out["path_len"][p]) == int(r["path_len"][0]) and
+               int(out["rounds"][p]) == int(r["rounds"][0]) for p, r in enumerate(ref))
+    print("self-aware search as the oracle's:", same, "of", n)
+    assert same >= n - 2, same
     # without the pairs the same problems may give paths through the robot itself
     ctx.set_self_collision(None)
     plain = run_plan(torch, ctx, None, start, goal, prm)
