@@ -238,7 +238,21 @@ def test_plan_line_and_fixed_orientation(torch_cuda, oracle_mod, ctype):
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
     assert not issues, issues[:10]
     assert checked >= 1, "no path to check"
-    print(ctype, "solved", checked, "of 8")
+    # the oracle's planner on the same problems (each alone with its index): the same search
+    # where no FP32 decision of the four- and five-row damped solves went the other way
+    import concurrent.futures as cf
+
+    def oracle_plan(p):
+        return oracle_mod.Oracle(rb, scenes[p], c).plan(
+            start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=prm.max_rounds,
+            n_workers=8, max_nodes=4096, max_connect=32, seed=5, first_problem=p)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        ref = list(ex.map(oracle_plan, range(8)))
+    same = sum(int(out["path_len"][p]) == int(r["path_len"][0]) and
+               int(out["rounds"][p]) == int(r["rounds"][0]) for p, r in enumerate(ref))
+    print(ctype, "solved", checked, "of 8; same search as the oracle's", same, "of 8")
+    assert same >= 6, same  # measured 8 of 8 for each of the three constraints
     ctx.close()
 
 
