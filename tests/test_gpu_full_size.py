@@ -185,3 +185,45 @@ def test_gemm_form_4096_point_cloud_full_size(torch_cuda, oracle_mod):
     stats, bad = parity.compare(sub, runs)
     assert not bad, (stats, bad[:5])
     ctx.close()
+
+
+def test_validation_65536_motions_full_size(torch_cuda, oracle_mod):
+    """The configuration-1 distribution at the throughput sweep's largest size, 65536
+    motions x 32 waypoints (roll-pitch, 16 obstacle spheres), where every warp of the
+    persistent validation kernel takes motion after motion: 200 sampled motions (projection
+    failures, collisions and valid ones) match the oracle under the parity protocol, and the
+    outcome counts are those of a run with the motions in reverse order (no state carried
+    from one motion to the next)."""
+    from paper_2505_06791_gb300.capi import Context
+    torch = torch_cuda
+    rb, sc, c = S.make_arm7(1), S.make_scene(1001, n_sph=16), S.roll_pitch()
+    orc = oracle_mod.Oracle(rb, sc, c)
+    n = 65536
+    q0 = []
+    k = 0
+    while len(q0) < n:
+        q = S.uniform_configs(rb, 32768, 90_000 + k).astype(np.float32)
+        ok, qp, _ = orc.project_configs(q, 60, n_threads=THREADS)
+        q0.extend(qp[ok])
+        k += 1
+    q0 = S.f32(np.array(q0[:n])).astype(np.float32)
+    q1 = S.uniform_configs(rb, n, 91_000).astype(np.float32)
+    ctx = Context(0)
+    ctx.set_robot(rb)
+    ctx.set_obstacles(sc)
+    ctx.set_constraint(c)
+    d0, d1 = torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()
+    out = to_np(ctx.validate(d0, d1, 32))
+    rev = to_np(ctx.validate(d0.flip(0).contiguous(), d1.flip(0).contiguous(), 32))
+    torch.cuda.synchronize()
+    ctx.close()
+    for key in ("status", "first_fail", "iters", "q"):
+        np.testing.assert_array_equal(rev[key][::-1], out[key], err_msg=key)
+    st = out["status"]
+    rng = np.random.default_rng(12)
+    pick = np.concatenate([rng.choice(np.nonzero(st == v)[0], m, replace=False)
+                           for v, m in ((0, min(40, int((st == 0).sum()))), (1, 80), (2, 80))])
+    runs = parity.oracle_runs(orc, c, q0[pick], q1[pick], 32, n_threads=THREADS)
+    stats, bad = parity.compare({k_: v[pick] for k_, v in out.items()}, runs)
+    assert not bad, (stats, bad[:5])
+    assert stats["exact"] >= 0.8 * stats["n"], stats
