@@ -58,7 +58,7 @@ class _Constraint(C.Structure):
 class _PlanParams(C.Structure):
     _fields_ = [("range", C.c_double), ("W", C.c_int), ("max_rounds", C.c_int),
                 ("n_workers", C.c_int), ("max_nodes", C.c_int), ("max_connect", C.c_int),
-                ("seed", C.c_uint32), ("first_problem", C.c_uint32)]
+                ("seed", C.c_uint32), ("first_problem", C.c_uint32), ("sequential", C.c_int)]
 
 
 def lib():
@@ -258,14 +258,16 @@ class Oracle:
     # ---- planner ----
     def plan(self, start, goal, range_=0.3, W=32, max_rounds=200, n_workers=8,
              max_nodes=4096, max_connect=64, seed=1, max_path=512, n_threads=1,
-             first_problem=0):
+             first_problem=0, sequential=False):
         """Plans each problem; problem p draws its samples with Philox problem index
-        first_problem + p (R19), so one problem of a batch can be planned alone."""
+        first_problem + p (R19), so one problem of a batch can be planned alone. With
+        sequential, motions are projected by the naive baseline's sequential projection
+        (R27) instead of Alg. 1."""
         s = np.ascontiguousarray(start, dtype=np.float32)
         g = np.ascontiguousarray(goal, dtype=np.float32)
         n = s.shape[0]
         pp = _PlanParams(range_, W, max_rounds, n_workers, max_nodes, max_connect, seed,
-                         first_problem)
+                         first_problem, int(bool(sequential)))
         path_len = np.zeros(n, dtype=np.int32)
         path = np.zeros((n, max_path, self.dof))
         rounds = np.zeros(n, dtype=np.int32)

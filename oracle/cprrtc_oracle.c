@@ -473,7 +473,8 @@ typedef struct {
 
 static motion_result validate_one(const orc_robot* rb, const orc_scene* sc,
                                   const orc_constraint* c, const double* q0, const double* q1,
-                                  int W, int cc_skip_first, double* xi, double* centres) {
+                                  int W, int cc_skip_first, double* xi, double* centres,
+                                  int sequential) {
   const int n = rb->dof;
   motion_result res = {ORC_VALID, -1, 0, 0.0, INFINITY, INFINITY};
   double xi_init[ORC_MAX_W * ORC_MAX_DOF];
@@ -485,8 +486,10 @@ static motion_result validate_one(const orc_robot* rb, const orc_scene* sc,
     memcpy(xi, xi_init, sizeof(double) * W * n);
   } else {
     double tau = step_threshold(c, q0, q1, n, W);
-    int ok = orc_project_motion(rb, c, xi_init, W, tau, xi, &res.iters, &res.first_fail,
-                                &res.resid, &res.proj_margin, NULL);
+    int ok = sequential
+                 ? orc_project_motion_sequential(rb, c, xi_init, W, tau, xi, &res.first_fail, &res.iters)
+                 : orc_project_motion(rb, c, xi_init, W, tau, xi, &res.iters, &res.first_fail,
+                                      &res.resid, &res.proj_margin, NULL);
     if (!ok) {
       res.status = ORC_PROJ_FAIL;
       return res;
@@ -531,7 +534,7 @@ static void* validate_worker(void* arg) {
       q1[k] = (double)jb->q_end[m * n + k];
     }
     motion_result r = validate_one(jb->rb, jb->sc, jb->c, q0, q1, W, jb->cc_skip_first, xi,
-                                   centres);
+                                   centres, 0);
     if (jb->out_q) memcpy(jb->out_q + (size_t)m * W * n, xi, sizeof(double) * W * n);
     if (jb->status) jb->status[m] = r.status;
     if (jb->first_fail) jb->first_fail[m] = r.first_fail;
@@ -885,7 +888,7 @@ static int motion_ok(const plan_env* env, const orc_constraint* c, const double*
                      const double* q1, double* q_end, double* xi, double* centres,
                      long long* wp) {
   int n = env->rb->dof, W = env->pp->W;
-  motion_result r = validate_one(env->rb, env->sc, c, q0, q1, W, 1, xi, centres);
+  motion_result r = validate_one(env->rb, env->sc, c, q0, q1, W, 1, xi, centres, env->pp->sequential);
   *wp += W;
   if (r.status != ORC_VALID) return 0;
   memcpy(q_end, xi + (W - 1) * n, sizeof(double) * n);

@@ -171,6 +171,8 @@ typedef struct {
   int max_connect;        /* greedy connect steps per extension */
   uint32_t seed;
   uint32_t first_problem; /* problem p of a call draws with Philox problem index first_problem + p */
+  int sequential;         /* 1: motions projected by orc_project_motion_sequential (the naive
+                             baseline, R27) instead of Alg. 1 */
 } orc_plan_params;
 
 /* Plans each problem; path_len[p] = nodes in the path (0 on failure), path[p][max_path][dof],

@@ -269,6 +269,20 @@ def test_plan_with_sequential_projection(torch_cuda, oracle_mod):
     checked, issues = PB.check_paths(oracle_mod, rb, c, scenes, start, goal, out, 32, 0.3)
     assert not issues, issues[:10]
     assert checked >= 1
+    # the oracle's planner with the same sequential projection runs the same search
+    import concurrent.futures as cf
+
+    def oracle_plan(p):
+        return oracle_mod.Oracle(rb, scenes[p], c).plan(
+            start[p:p + 1], goal[p:p + 1], range_=0.3, W=32, max_rounds=400, n_workers=8,
+            max_nodes=2048, max_connect=32, seed=6, first_problem=p, sequential=True)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        ref = list(ex.map(oracle_plan, range(8)))
+    same = sum(int(out["path_len"][p]) == int(r["path_len"][0]) and
+               int(out["rounds"][p]) == int(r["rounds"][0]) for p, r in enumerate(ref))
+    print("sequential search as the oracle's:", same, "of 8")
+    assert same >= 6, same  # measured 8 of 8
     with pytest.raises(CprrtcError) as e:
         run_plan(torch_cuda, ctx, None, start, goal, ctx.plan_params(W=64, seed=6))
     assert e.value.code == E_UNSUPPORTED

@@ -73,6 +73,21 @@ def test_planner_paths_are_valid(oracle_mod):
         for k in ("path_len", "rounds", "waypoints"):
             assert alone[k][0] == out[k][p], (p, k)
         assert np.array_equal(alone["path"][0], out["path"][p])
+    # the naive baseline's planner: every motion projected waypoint by waypoint (R27); its
+    # path nodes are valid too (on the manifold, collision-free, one steering range apart)
+    seq = orc.plan(s, g, range_=0.3, W=32, max_rounds=300, n_workers=8, seed=5, sequential=True)
+    assert (seq["path_len"] > 0).sum() >= 2
+    for p in range(3):
+        L = seq["path_len"][p]
+        if L <= 0:
+            continue
+        path = seq["path"][p, :L]
+        assert np.abs(path[0] - s[p]).max() < 1e-12 and np.abs(path[-1] - g[p]).max() < 1e-12
+        for q in path:
+            assert np.abs(indep.task_error(rb.joints, rb.ee, q, 1)).max() < c.tol_task
+            assert orc.config_clearance(q) > 0
+        steps = np.linalg.norm(np.diff(path, axis=0), axis=1)
+        assert steps.max() <= 0.3 + 1e-3
     moved = orc.plan(s[1:2], g[1:2], range_=0.3, W=32, max_rounds=300, n_workers=8, seed=5)
     assert not (moved["rounds"][0] == out["rounds"][1] and
                 np.array_equal(moved["path"][0], out["path"][1]))
