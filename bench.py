@@ -206,6 +206,8 @@ def manifold_starts_gpu(ctx, rb, n, seed):
 PLAN_N = 1000
 PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=1000, workers=8, max_nodes=2048,
                    max_connect=32, max_path=512)
+# the planner's time-sliced schedule (cprrtc_set_plan_slicing): first slice, later slices (rounds)
+PLAN_SLICING = (200, 50)
 
 
 def planner_scenes(n, seed=2):
@@ -277,6 +279,7 @@ def run_plan(args, world, rank, local):
     ctx.set_robot(rb)
     ctx.set_constraint(c)
     ctx.set_scene_batch(scenes)
+    ctx.set_plan_slicing(*PLAN_SLICING)
     prm = ctx.plan_params(seed=seed, **PLAN_PARAMS)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -316,6 +319,44 @@ def run_plan(args, world, rank, local):
     waypoints_step = int(wp.sum())
     value = sum_over_ranks(waypoints_step, world) * args.steps / (total_ms / 1e3)
     nominal = plan_flops(rb.dof, scenes, len(rb.spheres), work)
+
+    # the same problems on one CTA per problem, each planned in one stretch (the schedule
+    # without time slicing), timed alike: same search, so the same outputs
+    schedule = None
+    if args.schedule_ab:
+        with torch.cuda.stream(stream):
+            ctx.set_plan_slicing(0)
+            out_f = ctx.alloc_plan_outputs(n, prm, start, edges=False)
+            ctx.plan(start, goal, prm, out=out_f)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier(world)
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.plan(start, goal, prm, out=out_f)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+            f_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev), world)
+            ctx.set_plan_slicing(*PLAN_SLICING)
+        same = all(np.array_equal(out_f[k].cpu().numpy(), out[k].cpu().numpy())
+                   for k in ("path_len", "rounds", "waypoints", "work"))
+        msf = out_f["plan_ms"].cpu().numpy()
+        sf = out_f["path_len"].cpu().numpy() > 0
+        schedule = {
+            "time_sliced": {"first_slice_rounds": PLAN_SLICING[0], "slice_rounds": PLAN_SLICING[1],
+                            "ms_per_step": total_ms / args.steps},
+            "one_cta_per_problem": {"ms_per_step": f_ms / args.steps,
+                                    "p50_plan_ms": float(np.percentile(msf[sf], 50)) if sf.any() else None,
+                                    "p95_plan_ms": float(np.percentile(msf[sf], 95)) if sf.any() else None},
+            "speedup": f_ms / total_ms,
+            "same_outputs": bool(same),
+            "note": "persistent CTAs; an unsolved problem goes back to the queue's tail between "
+                    "slices while others wait, so the long problems share the GPU to the end; "
+                    "plan_ms is the device time of a problem's slices",
+        }
 
     # the learned form on the same problems: the network trained first (untimed), every extend
     # motion warm-started by it, plain Alg. 1 as judge and fallback
@@ -398,6 +439,8 @@ def run_plan(args, world, rank, local):
                    "constraint": "roll-pitch", "range": PLAN_PARAMS["range_"],
                    "W": PLAN_PARAMS["W"], "max_rounds": PLAN_PARAMS["max_rounds"],
                    "workers_per_problem": PLAN_PARAMS["workers"],
+                   "schedule": f"time-sliced persistent CTAs (first slice {PLAN_SLICING[0]} rounds, "
+                               f"then {PLAN_SLICING[1]})",
                    "l2": "flushed (256 MB write) between steps",
                    "recipe_departure": "obstacle centres in a 3 x 3 x 1.8 m workspace with a 0.35 m "
                                        "keep-out around the base instead of the 1.2 m cube: with "
@@ -419,6 +462,7 @@ def run_plan(args, world, rank, local):
                           "CC (motions that fail projection or collide early count only what "
                           "was checked); `value` counts W per attempted motion",
         "mean_rounds": float(rounds.mean()),
+        "schedule": schedule,
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "plan_kernel",
@@ -1650,6 +1694,8 @@ def main():
                     help="validation workload: motion counts of the throughput sweep")
     ap.add_argument("--learned", type=int, default=1,
                     help="planner workload: also time the learned form (trains the network first)")
+    ap.add_argument("--schedule-ab", type=int, default=1,
+                    help="planner workload: also time one CTA per problem without time slicing")
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
                     help="warm-start training epochs (fewer for profiling runs)")
     ap.add_argument("--legs", default="validate,gemmcc,warmstart,batch,earlyexit,naive",

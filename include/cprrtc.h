@@ -362,13 +362,15 @@ typedef struct {
  *              nodes j and j+1, waypoint 0 at node j (rows of path and path_edges
  *              beyond path_len are not written);
  *   rounds     [n] rounds run; waypoints [n] waypoints validated (W per motion checked);
- *   plan_ms    [n] device time of the problem's CTA, ms;
+ *   plan_ms    [n] device time the problem was planned, ms (the sum of its slices under
+ *              the time-sliced schedule, see cprrtc_set_plan_slicing);
  *   work       [n][2] work evaluated: Alg. 1 waypoint updates (iterations x (W-1) summed
  *              over motions) and waypoints collision-checked (early exit included).
  * The library keeps the trees in its own device memory (about
  * n * 2 * max_nodes * (W * dof + 9) * 4 bytes). Requires set_robot, and set_obstacles or
  * set_scene_batch (n_scenes = n). Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_UNSUPPORTED,
- * E_CUDA, E_OOM. */
+ * E_CUDA, E_OOM, and E_TIMEOUT (some array in host memory, time-sliced schedule) if a wait
+ * of the schedule's queue ran out (outputs then not valid). */
 int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 const cprrtc_plan_params* params, int32_t* path_len, float* path,
                 float* path_edges, int32_t* rounds, int64_t* waypoints, float* plan_ms,
@@ -390,6 +392,21 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
  * network for the robot E_NOT_CONFIGURED. 0 turns it off (the default).
  * Errors: E_INVALID_ARG (refine_iters outside 0..20). */
 int cprrtc_set_plan_warm_start(cprrtc_ctx* ctx, int refine_iters);
+
+/* Schedule of cprrtc_plan's problems on the GPU (not in the paper, which plans one problem per
+ * run; the search and every output but plan_ms's timing are the same for every setting).
+ * With first_slice > 0 (the default: first_slice 200, slice 50) the planner runs as many
+ * persistent CTAs as fit the GPU at once; a CTA takes a problem from a queue and runs its
+ * first first_slice rounds, later ones slice rounds at a time. Between slices an unsolved
+ * problem goes back to the queue's tail while other problems wait for a CTA, and stays with
+ * its CTA otherwise (its state between slices, about 1.6 KB, lives in the library's device
+ * memory beside the trees). Problems that solve within their first slice plan in one stretch;
+ * the long ones share the GPU round-robin, so a large batch no longer ends with the long
+ * problems that happened to start last. first_slice = 0: one CTA per problem, each planned
+ * in one stretch (cprrtc_plan_static always plans so). The queue's one wait (for another
+ * CTA's store of a handed-over problem, a few instructions) gives up after 1 s.
+ * Errors: E_INVALID_ARG (first_slice < 0, or slice < 1 with first_slice > 0). */
+int cprrtc_set_plan_slicing(cprrtc_ctx* ctx, int first_slice, int slice);
 
 /* ---- batches of uneven planning problems ---- */
 

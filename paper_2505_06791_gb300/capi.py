@@ -138,6 +138,7 @@ _SIGS = {
     "cprrtc_mlp_set_precision": [C.c_void_p, C.c_int],
     "cprrtc_set_wait_limit": [C.c_void_p, C.c_double],
     "cprrtc_set_plan_warm_start": [C.c_void_p, C.c_int],
+    "cprrtc_set_plan_slicing": [C.c_void_p, C.c_int, C.c_int],
     "cprrtc_set_table_self_collision": [C.c_void_p, C.c_int, C.c_void_p, C.c_int],
     "cprrtc_batch_adopt_network": [C.c_void_p, C.c_int, C.c_int],
     "cprrtc_mlp_set_params": [C.c_void_p, C.c_void_p, C.c_int64],
@@ -436,6 +437,10 @@ class Context:
     def set_plan_warm_start(self, refine_iters: int):
         """Planner's learned form: extend motions warm-started by the network (0: off)."""
         self._check(self._L.cprrtc_set_plan_warm_start(self.h, int(refine_iters)))
+
+    def set_plan_slicing(self, first_slice: int, slice_rounds: int = 50):
+        """cprrtc_set_plan_slicing: first_slice 0 plans each problem on one CTA in one stretch."""
+        self._check(self._L.cprrtc_set_plan_slicing(self.h, int(first_slice), int(slice_rounds)))
 
     def set_wait_limit(self, seconds: float):
         """Limit of the tensor-core kernels' bounded waits (0: the default, 1 s)."""

@@ -110,6 +110,8 @@ struct cprrtc_ctx {
   bool mlp_fp32 = false;    // the network's FP32 checking mode
   unsigned long long wait_ns = 0;  // bounded-wait limit of the tensor-core kernels (0: 1 s)
   int plan_warm = 0;               // planner's learned form: refine iterations (0: off)
+  int plan_first_slice = 200;      // planner's time-sliced schedule (0: one CTA per problem)
+  int plan_slice = 50;
   float* d_warm = nullptr;  // corrections [n*W][16]
   size_t warm_cap = 0;      // bytes
   bool timing = false;
@@ -1135,6 +1137,15 @@ int cprrtc_set_plan_warm_start(cprrtc_ctx* ctx, int refine_iters) {
   return CPRRTC_OK;
 }
 
+int cprrtc_set_plan_slicing(cprrtc_ctx* ctx, int first_slice, int slice) {
+  if (!ctx) return CPRRTC_E_INVALID_ARG;
+  if (first_slice < 0 || (first_slice > 0 && slice < 1))
+    return fail(ctx, CPRRTC_E_INVALID_ARG, "set_plan_slicing: first_slice >= 0, slice >= 1");
+  ctx->plan_first_slice = first_slice;
+  ctx->plan_slice = first_slice > 0 ? slice : 0;
+  return CPRRTC_OK;
+}
+
 int cprrtc_set_wait_limit(cprrtc_ctx* ctx, double seconds) {
   if (!ctx) return CPRRTC_E_INVALID_ARG;
   if (!(seconds == 0.0 || (seconds >= 1e-6 && seconds <= 10.0)))
@@ -1466,7 +1477,11 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   const size_t b_edges = al(N * 2 * MN * W * dof * sizeof(float));
   const size_t b_pend = al(N * B * 8 * sizeof(float));
   const size_t b_pedge = al(N * B * 2 * W * dof * sizeof(float));
-  const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge;
+  const bool sliced = ctx->plan_first_slice > 0;
+  const size_t b_state = sliced ? al(N * sizeof(PlanState)) : 0;
+  const size_t b_queue = sliced ? al(plan_queue_bytes(n)) : 0;
+  const size_t b_status = sliced ? 256 : 0;
+  const size_t need = b_nodes + b_parent + b_edges + b_pend + b_pedge + b_state + b_queue + b_status;
   if (need > ctx->plan_cap) {
     if (ctx->d_plan) cudaFree(ctx->d_plan);
     ctx->d_plan = nullptr;
@@ -1509,6 +1524,16 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   a.edges = reinterpret_cast<float*>(base + b_nodes + b_parent);
   a.pend = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges);
   a.pend_edges = reinterpret_cast<float*>(base + b_nodes + b_parent + b_edges + b_pend);
+  if (sliced) {
+    char* sb = base + b_nodes + b_parent + b_edges + b_pend + b_pedge;
+    a.state = reinterpret_cast<PlanState*>(sb);
+    a.queue = reinterpret_cast<PlanQueue*>(sb + b_state);
+    a.status = reinterpret_cast<int*>(sb + b_state + b_queue);
+    a.first_slice = ctx->plan_first_slice;
+    a.slice = ctx->plan_slice;
+    cudaError_t e = cudaMemsetAsync(a.status, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan: status");
+  }
   Staging st;
   st.input(start, N * dof * sizeof(float), &a.start);
   st.input(goal, N * dof * sizeof(float), &a.goal);
@@ -1525,7 +1550,14 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   cudaError_t e = launch_plan(ctx->rb, ctx->sc, ctx->cs, a, ctx->dev, ctx->stream);
   tm.done();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "plan launch");
-  return st.end(ctx);
+  rc = st.end(ctx);
+  if (rc == CPRRTC_OK && sliced && st.any_host) {
+    int flag = 0;
+    e = cudaMemcpy(&flag, a.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plan status");
+    if (flag) return fail(ctx, CPRRTC_E_TIMEOUT, "plan: a wait of the time-sliced queue timed out");
+  }
+  return rc;
 }
 
 int cprrtc_philox(cprrtc_ctx* ctx, uint32_t key0, uint32_t key1, const uint32_t* counters, int n,

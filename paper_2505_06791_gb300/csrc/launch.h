@@ -95,7 +95,44 @@ struct PlanArgs {
   // self-collision of the robot: bit b of self_rows[a] (a < b) pairs frames a and b
   unsigned short self_rows[kMaxDof + 1];
   int self_on;
+  // Time-sliced schedule (queue set): persistent CTAs take problems from the queue; a
+  // problem runs first_slice rounds, then slice rounds at a time, going back to the queue's
+  // tail between slices while other problems wait. Null queue: one CTA per problem.
+  struct PlanQueue* queue;
+  struct PlanState* state;  // [n] each problem between slices
+  int first_slice, slice;
+  int* status;                 // set to 1 when a wait of the queue timed out (may be null)
+  unsigned long long wait_ns;  // limit of the queue's bounded wait (0: 1 s)
 };
+
+// A problem between two slices: its next round, tree sizes, each worker's chain and the work
+// counted so far.
+struct PlanState {
+  int r_next;
+  int cnt[2];
+  int pad;
+  long long t_first;    // global timer at the start of its first slice
+  long long active_ns;  // device time of its slices so far
+  int mode[kMaxWorkers], ta[kMaxWorkers], last[kMaxWorkers], target[kMaxWorkers],
+      steps[kMaxWorkers];
+  unsigned wp[kMaxWorkers], proj[kMaxWorkers], cc[kMaxWorkers];
+  float cur[kMaxWorkers][8], qt[kMaxWorkers][8];
+};
+
+// Queue of the time-sliced schedule (a bounded ring of n slots). Ticket t < n is problem t's
+// first slice; ticket t >= n takes the problem pushed as number u = t - n, in slot s = u % n
+// of lap L = u / n: its pusher waits for seq[s] = 2 L (the slot's previous occupant taken),
+// stores ring[s] and sets 2 L + 1; the taker waits for 2 L + 1, reads ring[s] and sets
+// 2 L + 2. Both waits are short (a ticket is taken only while a problem waits for it, so the
+// other side is a running CTA a few instructions away) and bounded. The whole queue (header,
+// seq [n] 64-bit, ring [n] int) is zeroed before each launch; head and tail are 64-bit, as a
+// launch may hand problems over more than 2^32 times.
+struct PlanQueue {
+  unsigned long long head, tail;
+};
+inline size_t plan_queue_bytes(int n) {
+  return sizeof(PlanQueue) + (sizeof(long long) + sizeof(int)) * (size_t)n;
+}
 
 // Persistent batch of uneven planning problems (one launch).
 // Robot and constraint tables of a batch, passed by value (kernel parameter space).

@@ -51,7 +51,8 @@ struct PlanShared {
   long long wp[kMaxWorkers];   // waypoints validated by each warp
   long long wproj[kMaxWorkers];
   long long wcc[kMaxWorkers];
-  long long t_start;           // globaltimer at the problem's start
+  long long t_start;           // globaltimer at the start of the problem (of its slice)
+  long long t_prior;           // device time of the problem's earlier slices
   int stop;                    // 1 once the problem's time budget is spent
   // each warp's configurations, identical across its lanes: kept here instead of in every
   // lane's registers: [0] current chain node, [1] target, [2] motion end, [3] scratch
@@ -63,8 +64,10 @@ __device__ __forceinline__ void load_cfg(const float* src, int dof, float* q) {
   for (int k = 0; k < kMaxDof; ++k) q[k] = k < dof ? src[k] : 0.f;
 }
 
-// Nearest of nodes[0, count) (stride 8 floats) to q in L2; lowest index on ties.
-__device__ __forceinline__ int nearest_warp(const float* __restrict__ nodes, int count,
+// Nearest of nodes[0, count) (stride 8 floats) to q in L2; lowest index on ties. The nodes
+// are written during the launch (by this CTA, or by another one in an earlier slice), so the
+// pointer is not marked read-only.
+__device__ __forceinline__ int nearest_warp(const float* nodes, int count,
                                             const float* q, int dof) {
   const int lane = threadIdx.x & 31;
   float best = INFINITY;
@@ -399,16 +402,26 @@ enum : int { kSplitNone = 0, kSplitWaypoints = 1, kSplitObstacles = 2 };
 // state, computed from identical inputs); the pair's half 0 writes the worker's shared flags,
 // tree nodes and path, and a motion's edge is written by the warps holding its waypoints
 // (each its half when split by waypoints, half 0 when split by obstacles).
+//
+// Slices (ps set, one warp per worker): the call runs rounds [r_begin, r_end) of the problem
+// (r_begin > 0 resumes from the state in *ps). It returns false, with the problem's state saved
+// back to *ps, if rounds remain after r_end; otherwise it writes the problem's outputs and
+// returns true. The rounds are those of one uninterrupted call: the state holds everything a
+// round reads besides the trees in global memory, and the Philox counter names the round.
 template <int CT, int WPL, bool SEQ = false, bool WARM = false, int SPLIT = kSplitNone>
-__device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev& sc,
+__device__ __forceinline__ bool plan_problem(const RobotDev& rb, const SceneDev& sc,
                                              const float4* obs, const ConsDev& cs,
                                              const PlanArgs& a, const ProblemView& P,
                                              const CcShared& S, PlanShared* sh,
                                              WorkCount& wc, const SelfMask& self,
-                                             const MlpView* net = nullptr, SplitX* xs = nullptr) {
+                                             const MlpView* net = nullptr, SplitX* xs = nullptr,
+                                             int r_begin = 0, int r_end = 0x7fffffff,
+                                             bool sliced = false) {
   static_assert(SPLIT == kSplitNone || (WPL == 1 && !SEQ && !WARM), "warp pairs: plain Alg. 1, one waypoint per lane");
   constexpr int K = SPLIT == kSplitNone ? 1 : 2;
   const int p = P.p;
+  PlanState* const ps = SPLIT == kSplitNone && sliced ? a.state + p : nullptr;
+  const bool resume = ps && r_begin > 0;
   const int pw = threadIdx.x >> 5, lane = threadIdx.x & 31;  // physical warp
   const int warp = pw / K, h = pw % K;                        // worker, half of its pair
   const int NW = blockDim.x >> 5, B = NW / K, dof = rb.dof, W = P.W;
@@ -416,6 +429,7 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     sh->t_start = t;
+    sh->t_prior = resume ? ps->active_ns : 0;
     sh->stop = 0;
   }
   if (K > 1 && threadIdx.x < B) xs[threadIdx.x].hit = 0;
@@ -429,7 +443,12 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   // per-worker global scratch: the closing hop's motion is kept at wedge + wd
   float* wedge = P.pend_edges + (size_t)warp * 2 * wd;
 
-  if (pw == 0) {
+  if (resume) {
+    if (threadIdx.x == 0) {
+      sh->count0[0] = ps->cnt[0];
+      sh->count0[1] = ps->cnt[1];
+    }
+  } else if (pw == 0) {
     float q[kMaxDof];
     load_cfg(P.start, dof, q);
     store_cfg(nodes(0), q, dof);
@@ -457,7 +476,25 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
   float* qt = sh->cfg[pw][1];
   float* q1 = sh->cfg[pw][2];
   float* qe = sh->cfg[pw][3];
-  for (int r = 0; r < a.max_rounds; ++r) {
+  if (resume) {  // the chain as the last slice left it
+    mode = ps->mode[warp];
+    ta = ps->ta[warp];
+    last = ps->last[warp];
+    target = ps->target[warp];
+    steps = ps->steps[warp];
+    wp = ps->wp[warp];
+    work.proj = ps->proj[warp];
+    work.cc = ps->cc[warp];
+    rounds_used = r_begin;
+    __syncwarp();
+    if (lane < 8) {
+      cur[lane] = ps->cur[warp][lane];
+      qt[lane] = ps->qt[warp][lane];
+    }
+    __syncwarp();
+  }
+  const int r_stop = min(r_end, a.max_rounds);
+  for (int r = resume ? r_begin : 0; r < r_stop; ++r) {
     if (mode == 0) {
       ta = (r + warp) & 1;
       const U32x4 u0 = philox4x32_10(U32x4{(uint32_t)p, (uint32_t)r, (uint32_t)warp, 0u}, a.seed, 0u);
@@ -565,11 +602,12 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       cnt0 = min(cnt0 + n_add0, a.max_nodes);
       cnt1 = min(cnt1 + n_add1, a.max_nodes);
     }
-    // optional time budget: decided by one thread, seen by all after the barrier
+    // optional time budget: decided by one thread, seen by all after the barrier (earlier
+    // slices' device time included)
     if (a.budget_ns && threadIdx.x == 0) {
       long long t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      if ((unsigned long long)(t - sh->t_start) > a.budget_ns) sh->stop = 1;
+      if ((unsigned long long)(t - sh->t_start + (ps ? sh->t_prior : 0)) > a.budget_ns) sh->stop = 1;
     }
     // the appended nodes are visible to every warp's next nearest-neighbour scan, and the
     // flags may be overwritten
@@ -596,6 +634,34 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
       mode = 0;
       steps = 0;
     }
+  }
+  if (SPLIT == kSplitNone && ps && win < 0 && !sh->stop && rounds_used < a.max_rounds) {
+    // rounds remain: save the chain for the next slice (tree appends are in global memory)
+    if (lane == 0) {
+      ps->mode[warp] = mode;
+      ps->ta[warp] = ta;
+      ps->last[warp] = last;
+      ps->target[warp] = target;
+      ps->steps[warp] = steps;
+      ps->wp[warp] = wp;
+      ps->proj[warp] = work.proj;
+      ps->cc[warp] = work.cc;
+    }
+    if (lane < 8) {
+      ps->cur[warp][lane] = cur[lane];
+      ps->qt[warp][lane] = qt[lane];
+    }
+    if (threadIdx.x == 0) {
+      ps->r_next = rounds_used;
+      ps->cnt[0] = cnt0;
+      ps->cnt[1] = cnt1;
+      long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (!resume) ps->t_first = sh->t_start;
+      ps->active_ns = sh->t_prior + (t - sh->t_start);
+    }
+    __syncthreads();
+    return false;
   }
   if (lane == 0) {  // per physical warp: a pair's half 1 adds its collision work only
     sh->wp[pw] = h == 0 ? wp : 0;
@@ -659,64 +725,210 @@ __device__ __forceinline__ void plan_problem(const RobotDev& rb, const SceneDev&
     }
     long long t_end;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sh->t_start) * 1e-6);
+    // plan time: the device time of the problem's slices (one slice without a queue)
+    const long long prior = ps ? sh->t_prior : 0;
+    if (a.plan_ms) a.plan_ms[p] = (float)((double)(t_end - sh->t_start + prior) * 1e-6);
     if (a.span) {
-      a.span[2 * p] = sh->t_start;
+      a.span[2 * p] = resume ? ps->t_first : sh->t_start;
       a.span[2 * p + 1] = t_end;
     }
   }
+  return true;
 }
 
+// ---- the time-sliced schedule's queue (see PlanQueue) ---------------------------------------
+
+__device__ __forceinline__ long long ld_acquire(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(long long* p, long long v) {
+  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Thread 0: waits until seq[slot] = want (bounded; false and status set on timeout).
+__device__ bool queue_wait(const long long* seq, unsigned long long slot, long long want,
+                           unsigned long long wait_ns, int* status) {
+  const unsigned long long limit = wait_ns ? wait_ns : 1000000000ull;
+  long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (ld_acquire(seq + slot) != want) {
+    long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if ((unsigned long long)(t1 - t0) > limit) {
+      if (status) atomicExch(status, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Thread 0: the next problem, or -1 when no problem waits (the CTA then ends: every problem
+// left is held by a running CTA, which keeps it). *fresh is set when the problem has not
+// started. A ticket is taken only while a problem waits for it, so no pushed problem is ever
+// left without a taker, and the ticket's retries are bounded too.
+__device__ int queue_pop(PlanQueue* q, int n, unsigned long long wait_ns, int* status,
+                         bool* fresh) {
+  const unsigned long long un = (unsigned long long)n;
+  unsigned long long t = 0;
+  bool got = false;
+  for (int tries = 0; tries < (1 << 22) && !got; ++tries) {
+    const unsigned long long h = ld_volatile(&q->head);
+    const unsigned long long tl = ld_volatile(&q->tail);
+    if (h >= un && h - un >= tl) return -1;
+    if (atomicCAS(&q->head, h, h + 1ull) == h) {
+      t = h;
+      got = true;
+    }
+  }
+  if (!got) {
+    if (status) atomicExch(status, 1);
+    return -1;
+  }
+  *fresh = t < un;
+  if (t < un) return (int)t;
+  long long* seq = reinterpret_cast<long long*>(q + 1);
+  const int* ring = reinterpret_cast<const int*>(seq + n);
+  const unsigned long long u = t - un, slot = u % un, lap = u / un;
+  if (!queue_wait(seq, slot, (long long)(2 * lap + 1), wait_ns, status)) return -1;
+  const int p = ring[slot];
+  st_release(seq + slot, (long long)(2 * lap + 2));  // the slot is free for the next lap
+  return p;
+}
+
+// Thread 0, after a barrier that follows every write of the problem's slice: problem p to
+// the queue's tail. False (status set) if the slot did not come free in time; the caller then
+// keeps the problem.
+__device__ bool queue_push(PlanQueue* q, int n, int p, unsigned long long wait_ns, int* status) {
+  long long* seq = reinterpret_cast<long long*>(q + 1);
+  int* ring = reinterpret_cast<int*>(seq + n);
+  __threadfence();
+  const unsigned long long un = (unsigned long long)n;
+  const unsigned long long u = atomicAdd(&q->tail, 1ull), slot = u % un, lap = u / un;
+  if (!queue_wait(seq, slot, (long long)(2 * lap), wait_ns, status)) return false;
+  ring[slot] = p;
+  st_release(seq + slot, (long long)(2 * lap + 1));
+  return true;
+}
+
+// Thread 0: a problem waits in the queue (one not started, or one pushed and not taken).
+__device__ __forceinline__ bool queue_waiting(PlanQueue* q, int n) {
+  const unsigned long long un = (unsigned long long)n;
+  const unsigned long long h = ld_volatile(&q->head);
+  const unsigned long long tl = ld_volatile(&q->tail);
+  return h < un || tl > h - un;
+}
+
+// One CTA per problem (no queue), or persistent CTAs on the time-sliced queue: a CTA takes a
+// problem, runs its next slice, and either keeps it (nothing waits), hands it to the queue's
+// tail (other problems wait), or takes the next one once it is done. Problems that end within
+// their first slice plan in one stretch; the ones that run long share the SMs round-robin, so
+// the job no longer ends with the long problems that happened to start last.
 template <int CT, int WPL, bool SEQ, bool WARM>
 __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const SceneDev& shared_scene,
                                                  const ConsDev& cs, const PlanArgs& a) {
-  const int p = blockIdx.x;
-  if (p >= a.n) return;
+  const bool queued = a.queue != nullptr;
+  if (!queued && (int)blockIdx.x >= a.n) return;
+  __shared__ int s_p, s_r0, s_held, s_staged;
   const int warp = threadIdx.x >> 5;
   const int B = a.workers, dof = rb.dof, W = a.W;
-  SceneDev sc = shared_scene;
-  if (a.scenes) {
-    const int4 d = a.scenes[p];
-    sc.obs = a.scene_obs + d.x;
-    sc.n_sph = d.y;
-    sc.n_box = d.z;
-    sc.n_cap = d.w;
-  }
   extern __shared__ __align__(16) char smem[];
   const SmemLayout L(a.stage_obs ? a.max_scene_f4 : 0, rb.n_spheres, W, B, sizeof(PlanShared));
-  const int n4 = sc.n_float4();
   float4* s_obs = reinterpret_cast<float4*>(smem + L.obs);
-  if (a.stage_obs)
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
   stage_robot(rb, smem, L);
-  const float4* obs = a.stage_obs ? s_obs : sc.obs;
   const CcShared S = cc_shared(smem, L, warp);
   PlanShared* sh = reinterpret_cast<PlanShared*>(smem + L.extra);
   WorkCount wc{};
   const size_t wd = (size_t)W * dof;
-  const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
-  if (threadIdx.x == 0) {
-    ProblemView& P = sh->pv;
-    P.p = p;
-    P.start = a.start + (size_t)p * dof;
-    P.goal = a.goal + (size_t)p * dof;
-    P.W = W;
-    P.nodes = a.nodes + tree0 * 8;
-    P.parent = a.parent + tree0;
-    P.edges = a.edges + tree0 * wd;
-    P.pend = a.pend + (size_t)p * B * 8;
-    P.pend_edges = a.pend_edges + (size_t)p * B * 2 * wd;
-    P.path = a.path + (size_t)p * a.max_path * dof;
-    P.path_edges = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
-    P.ostride = dof;
-    P.estride = (int)wd;
-  }
-  __syncthreads();
   SelfMask self;
 #pragma unroll
   for (int f = 0; f <= kMaxDof; ++f) self.rows[f] = a.self_on ? a.self_rows[f] : (unsigned short)0;
   self.on = a.self_on;
-  plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self, WARM ? &a.net : nullptr);
+  // s_held: the problem this CTA keeps for its next slice (-1: none; -2: the CTA's one problem
+  // without a queue is done); s_staged: the problem whose scene is in shared memory
+  if (threadIdx.x == 0) {
+    s_held = -1;
+    s_staged = -1;
+  }
+  for (;;) {
+    __syncthreads();  // shared memory is free for the next slice
+    if (threadIdx.x == 0) {
+      int p = -1, r0 = 0;
+      const int held = s_held;
+      if (!queued) {
+        p = held == -1 ? (int)blockIdx.x : -1;
+        s_held = -2;
+      } else if (held >= 0) {
+        p = held;
+        r0 = a.state[p].r_next;
+      } else {
+        bool fresh = true;
+        p = queue_pop(a.queue, a.n, a.wait_ns, a.status, &fresh);
+        if (p >= 0 && !fresh) r0 = a.state[p].r_next;
+      }
+      s_p = p;
+      s_r0 = r0;
+    }
+    __syncthreads();
+    const int p = s_p, r0 = s_r0;
+    if (p < 0) break;
+    SceneDev sc = shared_scene;
+    if (a.scenes) {
+      const int4 d = a.scenes[p];
+      sc.obs = a.scene_obs + d.x;
+      sc.n_sph = d.y;
+      sc.n_box = d.z;
+      sc.n_cap = d.w;
+    }
+    if (a.stage_obs && (s_staged < 0 || (a.scenes && s_staged != p))) {
+      const int n4 = sc.n_float4();
+      for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
+    }
+    const float4* obs = a.stage_obs ? s_obs : sc.obs;
+    const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
+    if (threadIdx.x == 0) {
+      s_staged = p;
+      ProblemView& P = sh->pv;
+      P.p = p;
+      P.start = a.start + (size_t)p * dof;
+      P.goal = a.goal + (size_t)p * dof;
+      P.W = W;
+      P.nodes = a.nodes + tree0 * 8;
+      P.parent = a.parent + tree0;
+      P.edges = a.edges + tree0 * wd;
+      P.pend = a.pend + (size_t)p * B * 8;
+      P.pend_edges = a.pend_edges + (size_t)p * B * 2 * wd;
+      P.path = a.path + (size_t)p * a.max_path * dof;
+      P.path_edges = a.path_edges ? a.path_edges + (size_t)p * (a.max_path - 1) * wd : nullptr;
+      P.ostride = dof;
+      P.estride = (int)wd;
+    }
+    __syncthreads();
+    int r1 = a.max_rounds;
+    if (queued) {
+      const int sl = r0 == 0 ? a.first_slice : a.slice;
+      r1 = sl >= a.max_rounds - r0 ? a.max_rounds : r0 + sl;
+    }
+    const bool done = plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self,
+                                                       WARM ? &a.net : nullptr, nullptr, r0, r1,
+                                                       queued);
+    if (queued && threadIdx.x == 0) {
+      if (done) {
+        s_held = -1;
+      } else if (queue_waiting(a.queue, a.n) && queue_push(a.queue, a.n, p, a.wait_ns, a.status)) {
+        s_held = -1;
+      } else {
+        s_held = p;
+      }
+    }
+  }
   wc.flush(a.work_counters);
 }
 
@@ -954,9 +1166,19 @@ cudaError_t launch_plan(const RobotDev& rb, const SceneDev& sc, const ConsDev& c
   if (!fn) return cudaErrorNotSupported;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  int grid = a.n;
+  if (a.queue) {  // persistent CTAs: as many as fit the GPU at once, at most one per problem
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * a.workers, smem);
+    if (e != cudaSuccess) return e;
+    const long long slots = (long long)(per_sm > 0 ? per_sm : 1) * dev.sm_count;
+    grid = slots < a.n ? (int)slots : a.n;
+    e = cudaMemsetAsync(a.queue, 0, plan_queue_bytes(a.n), stream);
+    if (e != cudaSuccess) return e;
+  }
   void* args[] = {const_cast<RobotDev*>(&rb), const_cast<SceneDev*>(&sc),
                   const_cast<ConsDev*>(&cs), &a};
-  e = cudaLaunchKernel(fn, dim3(a.n), dim3(32 * a.workers), args, smem, stream);
+  e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * a.workers), args, smem, stream);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
