@@ -1678,6 +1678,7 @@ def run_legs(args):
 
 
 def main():
+    global PLAN_SLICING
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -1694,6 +1695,9 @@ def main():
                     help="validation workload: motion counts of the throughput sweep")
     ap.add_argument("--learned", type=int, default=1,
                     help="planner workload: also time the learned form (trains the network first)")
+    ap.add_argument("--slicing", default=None,
+                    help="planner's time-sliced schedule 'first,slice' in rounds (0,0: one CTA "
+                         "per problem); default %d,%d" % PLAN_SLICING)
     ap.add_argument("--schedule-ab", type=int, default=1,
                     help="planner workload: also time one CTA per problem without time slicing")
     ap.add_argument("--train-epochs", type=int, default=WS_EPOCHS,
@@ -1702,6 +1706,8 @@ def main():
                     help="with the default planner workload on one GPU: the other configurations, "
                          "each run as its own process and reported under 'legs' ('none' to skip)")
     args = ap.parse_args()
+    if args.slicing is not None:
+        PLAN_SLICING = tuple(int(x) for x in args.slicing.split(","))
     if args.max_rounds is not None:
         PLAN_PARAMS["max_rounds"] = args.max_rounds
         BATCH_PARAMS["max_rounds"] = args.max_rounds
