@@ -1317,6 +1317,8 @@ int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, f
   int rc = st.begin(ctx);
   if (rc) return rc;
   cudaError_t e = mlp_grad(ctx->mlp, dq, dt, rows, grads, loss, ctx->stream);
+  if (e == cudaErrorTimeout)
+    return fail(ctx, CPRRTC_E_TIMEOUT, "mlp_grad: a wait of a tensor-core GEMM timed out");
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_grad");
   return st.end(ctx);
 }
@@ -1341,6 +1343,8 @@ int cprrtc_mlp_train(cprrtc_ctx* ctx, const float* q, const float* t, int n, int
   LaunchTimer tm(ctx, "mlp_train");
   cudaError_t e = mlp_train(ctx->mlp, dq, dt, n, batch, epochs, lr, seed, loss_per_epoch, ctx->stream);
   tm.done();
+  if (e == cudaErrorTimeout)
+    return fail(ctx, CPRRTC_E_TIMEOUT, "mlp_train: a wait of a tensor-core GEMM timed out");
   if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_train");
   return st.end(ctx);
 }

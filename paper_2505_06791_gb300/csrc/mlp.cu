@@ -3,12 +3,16 @@
 // by the kernels below (forward, backward, optimiser), and evaluated in batches to give
 // Alg. 1 a starting segment closer to the manifold.
 //
-// GEMM: C[M,N] = A'[M,K] B'[K,N] in BF16 x BF16 -> FP32 with mma.sync m16n8k16. A' is A
-// ([M][K], or [K][M] when transposed) and B' is B ([K][N], or [N][K] when transposed), all
-// row-major with given leading dimensions. Tiles of 64 x 64 x 32 per CTA (4 warps, each
-// 32 x 32), staged in shared memory as [row][k] with a padded pitch (conflict-free
-// fragment loads), transposed on the way in when needed. Epilogues fuse the bias, GELU,
-// GELU's derivative and split-K accumulation.
+// GEMM: C[M,N] = A'[M,K] B'[K,N] in BF16 x BF16 -> FP32 on the 5th-generation tensor cores
+// (tcgen05.mma, kind::f16, accumulator in tensor memory). A' is A ([M][K], or [K][M] when
+// transposed) and B' is B ([K][N], or [N][K] when transposed), all row-major with given
+// leading dimensions. A CTA computes a 128 x BN output tile (BN = 32, or 16 for the 16-wide
+// input and output layers): its 8 warps stage K chunks of 64 of both operands into shared
+// memory in the 128-byte-swizzled K-major layout (transposed on the way in when needed, zero
+// past the matrix), two chunks in flight, while one thread issues the chunk's MMAs (K = 16
+// each) and commits them to the chunk's mbarrier. The epilogue reads the accumulator with
+// tensor-memory loads (warp w: lanes 32 (w % 4) .., 16-column groups of parity w / 4) and
+// fuses the bias, GELU, GELU's derivative or split-K accumulation.
 //
 // FP32 checking mode: the same network, forward pass and gradient with FP32 weights and
 // activations (no rounding to BF16 anywhere) on a plain FP32 FMA GEMM with the same
@@ -18,26 +22,21 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
 #include "launch.h"
 #include "mlp_common.cuh"
+#include "tcgen05.cuh"
 
 namespace cprrtc {
 
 namespace {
 
-constexpr int kTM = 64, kTN = 64, kTK = 32;
-constexpr int kPitch = kTK + 8;  // bf16 per staged row (20 words: conflict-free fragments)
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+constexpr int kTM = 64, kTN = 64;  // output tile of the FP32 checking mode's GEMM
+constexpr int kTcM = 128, kTcK = 64, kTcThreads = 256;
+constexpr uint64_t kTcWaitNs = 1000000000ull, kTcDrainNs = 20000000ull;
 
 }  // namespace
 
@@ -66,6 +65,9 @@ struct GemmArgsT {
   const float* bias;
   const float* Z;  // pre-activation for the GELU backward (ldc)
   int k_split;     // K range per blockIdx.z
+  int* error;      // set to 1 when a bounded wait of the tensor-core GEMM ran out (may be null)
+  unsigned long long wait_ns;  // limit of its bounded waits (0: 1 s)
+  int vec_a, vec_b;  // set by the launcher: K-contiguous operand with 16-byte aligned rows
 };
 using GemmArgs = GemmArgsT<__nv_bfloat16>;
 using GemmArgsF = GemmArgsT<float>;
@@ -98,92 +100,168 @@ __device__ __forceinline__ void epilogue(const GemmArgsT<T>& g, int gm, int gn, 
   }
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[kTM][kPitch];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kPitch];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
-  const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+// Shared memory of gemm_tc_kernel: two stages of (A' 128 x 64, B' up to 64 x 64) BF16
+// chunks, then two mbarriers (the chunk's MMAs done), the tensor-memory address and the
+// abort flag; 1024-byte alignment slack for the swizzled operands.
+constexpr int kTcStageA = kTcM * 128, kTcStage = kTcStageA + 64 * 128;
+constexpr int kTcOffBar = 2 * kTcStage;
+constexpr size_t kTcSmem = kTcOffBar + 32 + 1024;
+
+// One operand of a K chunk: rows r0.. (R rows, 128 or BN) x K [k0, k0 + 64) of a source
+// that is K-contiguous ([rows][K], `kmajor`) or row-contiguous ([K][rows]) with leading
+// dimension ld and `nrows` valid rows, staged into `dst` (swizzled), zero past the matrix and
+// past ke. Every thread first loads its share into registers (all loads in flight), then
+// stores it. A K-contiguous source with 16-byte aligned rows moves 8 elements at a time.
+template <int R_MAX>
+__device__ __forceinline__ void stage_operand(const __nv_bfloat16* __restrict__ src, int ld, bool kmajor,
+                                              bool vec, int r0, int nrows, int R, int k0, int ke,
+                                              uint8_t* dst) {
   const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = kb; k0 < ke; k0 += kTK) {
-    // stage A' rows m0.. and B' columns n0.. as [row][k]; 64 x 32 each, 16 per thread
-    for (int e = tid; e < kTM * kTK; e += 128) {
-      int r, k;
-      if (g.transA) {  // source [K][M]: consecutive threads walk m
-        r = e % kTM;
-        k = e / kTM;
-      } else {         // source [M][K]: consecutive threads walk k
-        r = e / kTK;
-        k = e % kTK;
+  if (kmajor && vec) {  // 16-byte pieces: piece p = row p / 8, k 8 (p % 8) .. + 7
+    constexpr int kPer = (R_MAX * kTcK / 8 + kTcThreads - 1) / kTcThreads;
+    uint4 v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int p = threadIdx.x + i * kTcThreads, r = p >> 3, k = (p & 7) * 8;
+      const int gr = r0 + r, gk = k0 + k;
+      v[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (r < R && gr < nrows) {
+        if (gk + 8 <= ke) {
+          v[i] = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
+        } else {
+          uint32_t w[4];  // the piece's elements before ke, packed two per word (low first)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const unsigned short lo = gk + 2 * j < ke ? __bfloat16_as_ushort(src[(size_t)gr * ld + gk + 2 * j]) : 0;
+            const unsigned short hi = gk + 2 * j + 1 < ke ? __bfloat16_as_ushort(src[(size_t)gr * ld + gk + 2 * j + 1]) : 0;
+            w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
+          }
+          v[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
       }
-      const int gm = m0 + r, gk = k0 + k;
-      __nv_bfloat16 v = zero;
-      if (gm < g.M && gk < ke)
-        v = g.transA ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
-      As[r][k] = v;
     }
-    for (int e = tid; e < kTN * kTK; e += 128) {
-      int c, k;
-      if (g.transB) {  // source [N][K]
-        c = e / kTK;
-        k = e % kTK;
-      } else {         // source [K][N]
-        c = e % kTN;
-        k = e / kTN;
-      }
-      const int gn = n0 + c, gk = k0 + k;
-      __nv_bfloat16 v = zero;
-      if (gn < g.N && gk < ke)
-        v = g.transB ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
-      Bs[c][k] = v;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int p = threadIdx.x + i * kTcThreads, r = p >> 3, k = (p & 7) * 8;
+      if (r < R) *reinterpret_cast<uint4*>(dst + tc::sw128(r, k, R)) = v[i];
     }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + gid;
-        a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tig]);
-        a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tig]);
-        a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 8 + 2 * tig]);
-        a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 8 + 2 * tig]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + 8 * j + gid;
-        b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * tig]);
-        b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 8 + 2 * tig]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-    }
-    __syncthreads();
+    return;
   }
-  // epilogue: acc[i][j] holds rows wm+16i+gid (+8), columns wn+8j+2tig (+1)
+  constexpr int kPer = (R_MAX * kTcK + kTcThreads - 1) / kTcThreads;
+  __nv_bfloat16 v[kPer];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < kPer; ++i) {
+    const int e = threadIdx.x + i * kTcThreads;
+    // K-contiguous: consecutive threads walk k; row-contiguous: consecutive threads walk rows
+    const int r = kmajor ? e / kTcK : e % R, k = kmajor ? e % kTcK : e / R;
+    const int gr = r0 + r, gk = k0 + k;
+    v[i] = zero;
+    if (e < R * kTcK && gr < nrows && gk < ke)
+      v[i] = kmajor ? src[(size_t)gr * ld + gk] : src[(size_t)gk * ld + gr];
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+  for (int i = 0; i < kPer; ++i) {
+    const int e = threadIdx.x + i * kTcThreads;
+    const int r = kmajor ? e / kTcK : e % R, k = kmajor ? e % kTcK : e / R;
+    if (e < R * kTcK) *reinterpret_cast<__nv_bfloat16*>(dst + tc::sw128(r, k, R)) = v[i];
+  }
+}
+
+// Stages K chunk [k0, k0 + 64) of the tile's A' rows m0.. (128) and B' rows n0.. (BN, the
+// output columns) into sa / sb.
+__device__ __forceinline__ void stage_tc(const GemmArgs& g, int m0, int n0, int BN, int k0, int ke,
+                                         uint8_t* sa, uint8_t* sb) {
+  stage_operand<kTcM>(g.A, g.lda, !g.transA, g.vec_a, m0, g.M, kTcM, k0, ke, sa);
+  stage_operand<64>(g.B, g.ldb, g.transB != 0, g.vec_b, n0, g.N, BN, k0, ke, sb);
+}
+
+// One 128 x BN output tile (BN 16 or 32) over the K range of split blockIdx.z. Every wait is
+// bounded; on expiry the CTA raises its abort flag, skips the rest, waits (bounded) for the
+// MMAs it issued, frees tensor memory, exits and sets *g.error.
+template <int EPI>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(GemmArgs g, int BN) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sbase = tc::smem_addr(smem);
+  auto bar = [&](int i) { return sbase + kTcOffBar + 8u * (uint32_t)i; };
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + kTcOffBar + 16);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kTcOffBar + 20);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * BN;
+  const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
+  const int nchunks = (ke - kb + kTcK - 1) / kTcK;
+  const uint32_t cols = BN <= 32 ? 32u : 64u;  // tensor-memory columns (a power of 2, >= 32)
+  const uint64_t limit = g.wait_ns ? g.wait_ns : kTcWaitNs;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar(0), 1);
+    tc::mbar_init(bar(1), 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_addr(s_tmem)),
+                 "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::tc_before();
+  __syncthreads();
+  tc::tc_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t idesc = tc::mma_idesc(kTcM, BN);
+  int issued = 0;  // thread 0: chunks whose MMAs were committed
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c & 1;
+    // stage s was read by the MMAs of chunk c - 2 (phase (c - 2) / 2 of its barrier)
+    if (c >= 2) tc::mbar_wait_for(bar(s), ((c - 2) >> 1) & 1, s_abort, limit);
+    __syncthreads();
+    if (*s_abort) break;
+    const int k0 = kb + c * kTcK;
+    stage_tc(g, m0, n0, BN, k0, ke, smem + s * kTcStage, smem + s * kTcStage + kTcStageA);
+    tc::fence_async_smem();  // the staged operands are visible to the tensor cores
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::tc_after();
+      const int steps = (min(kTcK, ke - k0) + 15) / 16;
+      const uint32_t a_addr = sbase + (uint32_t)(s * kTcStage), b_addr = a_addr + kTcStageA;
+      for (int kk = 0; kk < steps; ++kk)
+        tc::umma_bf16(tmem, tc::sw128_desc(a_addr + 32u * kk), tc::sw128_desc(b_addr + 32u * kk), idesc,
+                      (c > 0 || kk > 0) ? 1u : 0u);
+      tc::umma_commit(bar(s));
+      issued = c + 1;
+    }
+  }
+  // the accumulator is complete once the last chunk's MMAs are
+  if (!*s_abort) tc::mbar_wait_for(bar((nchunks - 1) & 1), ((nchunks - 1) >> 1) & 1, s_abort, limit);
+  tc::tc_after();
+  __syncthreads();
+  if (!*s_abort) {
+    const int q = warp & 3, h = warp >> 2;  // lane quarter, column-group parity
+    const int gm = m0 + 32 * q + lane;
+    for (int j = h; 16 * j < BN; j += 2) {
+      uint32_t v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * j), v);
+      tc::tmem_wait_ld();
+      if (gm < g.M) {
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int gm = m0 + wm + 16 * i + gid + (r >> 1) * 8;
-        const int gn = n0 + wn + 8 * j + 2 * tig + (r & 1);
-        if (gm >= g.M || gn >= g.N) continue;
-        epilogue<EPI>(g, gm, gn, acc[i][j][r]);
+        for (int i = 0; i < 16; ++i) {
+          const int gn = n0 + 16 * j + i;
+          if (gn < g.N) epilogue<EPI>(g, gm, gn, __uint_as_float(v[i]));
+        }
       }
+    }
+  } else if (threadIdx.x == 0) {  // no MMA may still be running when tensor memory is freed
+    for (int c = issued > 2 ? issued - 2 : 0; c < issued; ++c)
+      tc::mbar_drain_for(bar(c & 1), (c >> 1) & 1, kTcDrainNs);
+  }
+  tc::tc_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::tc_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+  }
+  if (threadIdx.x == 0 && *s_abort && g.error) atomicExch(g.error, 1);
 }
 
 // The FP32 checking mode's GEMM: 64 x 64 output tiles, K steps of 16, 256 threads with 4 x 4
@@ -255,38 +333,59 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmArgsF g) {
     }
 }
 
-// Grid of one GEMM: output tiles, and for the split-K epilogue enough splits of the
-// reduction to cover the GPU.
+// Grid of one GEMM: output tiles of tm x tn, and for the split-K epilogue enough splits of
+// the reduction to cover the GPU (each a multiple of k_step).
 template <class T>
-static dim3 gemm_grid(int epi, GemmArgsT<T>& g, int k_step) {
+static dim3 gemm_grid(int epi, GemmArgsT<T>& g, int tm, int tn, int k_step, int k_min = 256) {
   int splits = 1;
-  if (epi == kEpiAtomic) {
-    const int tiles = ((g.M + kTM - 1) / kTM) * ((g.N + kTN - 1) / kTN);
-    splits = std::max(1, std::min((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
+  if (epi == kEpiAtomic) {  // splits of at least k_min
+    const int tiles = ((g.M + tm - 1) / tm) * ((g.N + tn - 1) / tn);
+    splits = std::max(1, std::min((g.K + k_min - 1) / k_min, (4 * 152 + tiles - 1) / tiles));
   }
   g.k_split = ((g.K + splits - 1) / splits + k_step - 1) / k_step * k_step;
   splits = (g.K + g.k_split - 1) / g.k_split;
-  return dim3((g.M + kTM - 1) / kTM, (g.N + kTN - 1) / kTN, splits);
+  return dim3((g.M + tm - 1) / tm, (g.N + tn - 1) / tn, splits);
+}
+
+template <int EPI>
+static cudaError_t launch_tc(const GemmArgs& g, dim3 grid, int BN, cudaStream_t stream) {
+  // the kernel's shared memory is above the 48 KB default: set once per device
+  static std::atomic<unsigned long long> set_on{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(set_on.load() & bit)) {
+    e = cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    set_on.fetch_or(bit);
+  }
+  gemm_tc_kernel<EPI><<<grid, kTcThreads, kTcSmem, stream>>>(g, BN);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
   GemmArgs g = g0;
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-  const dim3 grid = gemm_grid(epi, g, kTK);
+  // narrow tiles and short splits: these GEMMs are small, so more CTAs finish sooner
+  const int BN = g.N <= 16 ? 16 : 32;
+  const dim3 grid = gemm_grid(epi, g, kTcM, BN, kTcK, 2 * kTcK);
+  auto rows16 = [](const void* p, int ld) { return ((uintptr_t)p & 15) == 0 && ld % 8 == 0; };
+  g.vec_a = !g.transA && rows16(g.A, g.lda);
+  g.vec_b = g.transB && rows16(g.B, g.ldb);
   switch (epi) {
-    case kEpiStore: gemm_bf16_kernel<kEpiStore><<<grid, 128, 0, stream>>>(g); break;
-    case kEpiBiasGelu: gemm_bf16_kernel<kEpiBiasGelu><<<grid, 128, 0, stream>>>(g); break;
-    case kEpiBias: gemm_bf16_kernel<kEpiBias><<<grid, 128, 0, stream>>>(g); break;
-    case kEpiGeluBwd: gemm_bf16_kernel<kEpiGeluBwd><<<grid, 128, 0, stream>>>(g); break;
-    default: gemm_bf16_kernel<kEpiAtomic><<<grid, 128, 0, stream>>>(g); break;
+    case kEpiStore: return launch_tc<kEpiStore>(g, grid, BN, stream);
+    case kEpiBiasGelu: return launch_tc<kEpiBiasGelu>(g, grid, BN, stream);
+    case kEpiBias: return launch_tc<kEpiBias>(g, grid, BN, stream);
+    case kEpiGeluBwd: return launch_tc<kEpiGeluBwd>(g, grid, BN, stream);
+    default: return launch_tc<kEpiAtomic>(g, grid, BN, stream);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(int epi, const GemmArgsF& g0, cudaStream_t stream) {
   GemmArgsF g = g0;
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-  const dim3 grid = gemm_grid(epi, g, kFK);
+  const dim3 grid = gemm_grid(epi, g, kTM, kTN, kFK);
   switch (epi) {
     case kEpiStore: gemm_f32_kernel<kEpiStore><<<grid, 256, 0, stream>>>(g); break;
     case kEpiBiasGelu: gemm_f32_kernel<kEpiBiasGelu><<<grid, 256, 0, stream>>>(g); break;
@@ -776,6 +875,8 @@ static cudaError_t forward(MlpDev* d, const MlpWs<T>& w, int rows, T* Hkeep[3], 
   int ld_in = kMlpIO;
   for (int l = 0; l < kMlpLayers; ++l) {
     GemmArgsT<T> g{};
+    g.error = d->err;
+    g.wait_ns = d->wait_ns;
     g.M = rows;
     g.N = kOut[l];
     g.K = kIn[l];
@@ -902,6 +1003,8 @@ static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int 
     const int ldA = l == 0 ? kMlpIO : kMlpHidden;
     // weight gradient dW_l [out][in] = D^T Aprev  (split-K over rows, atomics)
     GemmArgsT<T> gw{};
+    gw.error = d->err;
+    gw.wait_ns = d->wait_ns;
     gw.M = kOut[l];
     gw.N = kIn[l];
     gw.K = rows;
@@ -920,6 +1023,8 @@ static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int 
     if (l == 0) break;
     // dZ_{l-1} = (D W_l) * gelu'(Z_{l-1})
     GemmArgsT<T> gd{};
+    gd.error = d->err;
+    gd.wait_ns = d->wait_ns;
     gd.M = rows;
     gd.N = kIn[l];
     gd.K = kOut[l];
@@ -941,10 +1046,18 @@ static cudaError_t loss_and_grad(MlpDev* d, const float* q, const float* t, int 
   return cudaSuccess;
 }
 
+// After the stream synchronised: cudaErrorTimeout when a tensor-core GEMM gave up a wait.
+static cudaError_t gemm_status(MlpDev* d) {
+  int flag = 0;
+  const cudaError_t e = cudaMemcpy(&flag, d->err, sizeof(int), cudaMemcpyDeviceToHost);
+  return e != cudaSuccess ? e : flag ? cudaErrorTimeout : cudaSuccess;
+}
+
 cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float* grads_host,
                      float* loss_host, cudaStream_t s) {
   float* loss_dev = nullptr;
-  cudaError_t e;
+  cudaError_t e = cudaMemsetAsync(d->err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
   if (d->fp32) {
     MlpWs<float> w;
     e = loss_and_grad<float>(d, q, t, rows, s, w);
@@ -956,6 +1069,7 @@ cudaError_t mlp_grad(MlpDev* d, const float* q, const float* t, int rows, float*
   }
   if (e == cudaSuccess && loss_host) e = cudaMemcpyAsync(loss_host, loss_dev, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = gemm_status(d);
   if (e == cudaSuccess && grads_host) e = to_compact(d, d->g, grads_host, s);
   return e;
 }
@@ -1019,6 +1133,7 @@ cudaError_t mlp_train(MlpDev* d, const float* q, const float* t, int n, int batc
   if (e == cudaSuccess) e = cudaMalloc(&tb, (size_t)batch * dof * 4);
   if (e == cudaSuccess) e = cudaMalloc(&loss, (size_t)std::max(epochs, 1) * 4);
   if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, (size_t)std::max(epochs, 1) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d->err, 0, sizeof(int), s);
   std::vector<int> perm(n);
   for (int i = 0; i < n; ++i) perm[i] = i;
   uint64_t st = seed ^ 0xD1B54A32D192ED03ull;
@@ -1047,6 +1162,7 @@ cudaError_t mlp_train(MlpDev* d, const float* q, const float* t, int n, int batc
     for (int ep = 0; ep < epochs; ++ep) loss_host[ep] = l[ep] / nb;
   }
   cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = gemm_status(d);
   cudaFree(idx);
   cudaFree(qb);
   cudaFree(tb);

@@ -97,3 +97,4 @@ def test_fused_inference_wait_limit_expires_then_recovers(torch_cuda, oracle_mod
     # the same context, default limit: the inference is back and unchanged
     np.testing.assert_array_equal(np.array(ctx.mlp_infer(q), copy=True), ref)
     ctx.close()
+
