@@ -67,7 +67,7 @@ struct GemmArgsT {
   int k_split;     // K range per blockIdx.z
   int* error;      // set to 1 when a bounded wait of the tensor-core GEMM ran out (may be null)
   unsigned long long wait_ns;  // limit of its bounded waits (0: 1 s)
-  int vec_a, vec_b;  // set by the launcher: K-contiguous operand with 16-byte aligned rows
+  int vec_a, vec_b;  // set by the launcher: the operand's rows are 16-byte aligned
 };
 using GemmArgs = GemmArgsT<__nv_bfloat16>;
 using GemmArgsF = GemmArgsT<float>;
@@ -107,79 +107,105 @@ constexpr int kTcStageA = kTcM * 128, kTcStage = kTcStageA + 64 * 128;
 constexpr int kTcOffBar = 2 * kTcStage;
 constexpr size_t kTcSmem = kTcOffBar + 32 + 1024;
 
-// One operand of a K chunk: rows r0.. (R rows, 128 or BN) x K [k0, k0 + 64) of a source
-// that is K-contiguous ([rows][K], `kmajor`) or row-contiguous ([K][rows]) with leading
-// dimension ld and `nrows` valid rows, staged into `dst` (swizzled), zero past the matrix and
-// past ke. Every thread first loads its share into registers (all loads in flight), then
-// stores it. A K-contiguous source with 16-byte aligned rows moves 8 elements at a time.
-template <int R_MAX>
-__device__ __forceinline__ void stage_operand(const __nv_bfloat16* __restrict__ src, int ld, bool kmajor,
-                                              bool vec, int r0, int nrows, int R, int k0, int ke,
-                                              uint8_t* dst) {
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  if (kmajor && vec) {  // 16-byte pieces: piece p = row p / 8, k 8 (p % 8) .. + 7
-    constexpr int kPer = (R_MAX * kTcK / 8 + kTcThreads - 1) / kTcThreads;
+// One operand of a K chunk: rows r0.. (R rows: 128, or BN) x K [k0, k0 + 64) of a source that
+// is K-contiguous ([rows][K], KMAJOR) or row-contiguous ([K][rows]) with leading dimension ld
+// and `nrows` valid rows, staged into `dst` (swizzled), zero past the matrix and past ke.
+// With `vec` (16-byte aligned source rows) a thread moves 8 elements at a time: 8 consecutive
+// k of one row (K-contiguous), or 8 consecutive rows of one k (row-contiguous, written to 8
+// rows of the tile). Every thread loads its share into registers first (all loads in flight)
+// and then stores it.
+__device__ __forceinline__ unsigned short bits_or_zero(const __nv_bfloat16* p, bool ok) {
+  return ok ? __bfloat16_as_ushort(*p) : (unsigned short)0;
+}
+
+template <int R, bool KMAJOR>
+__device__ __forceinline__ void stage_operand(const __nv_bfloat16* __restrict__ src, int ld, bool vec,
+                                              int r0, int nrows, int k0, int ke, uint8_t* dst) {
+  if (vec) {
+    constexpr int kPieces = R * kTcK / 8, kPer = (kPieces + kTcThreads - 1) / kTcThreads;
     uint4 v[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const int p = threadIdx.x + i * kTcThreads, r = p >> 3, k = (p & 7) * 8;
+      const int p = threadIdx.x + i * kTcThreads;
+      // K-contiguous: row p / 8, k 8 (p % 8) ..; row-contiguous: k p / (R / 8), rows 8 (p % (R / 8)) ..
+      const int r = KMAJOR ? p >> 3 : 8 * (p % (R / 8)), k = KMAJOR ? 8 * (p & 7) : p / (R / 8);
       const int gr = r0 + r, gk = k0 + k;
       v[i] = make_uint4(0u, 0u, 0u, 0u);
-      if (r < R && gr < nrows) {
-        if (gk + 8 <= ke) {
-          v[i] = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
-        } else {
-          uint32_t w[4];  // the piece's elements before ke, packed two per word (low first)
+      if (p >= kPieces) continue;
+      if (KMAJOR ? (gr < nrows && gk + 8 <= ke) : (gk < ke && gr + 8 <= nrows)) {
+        v[i] = *reinterpret_cast<const uint4*>(KMAJOR ? src + (size_t)gr * ld + gk : src + (size_t)gk * ld + gr);
+      } else if (KMAJOR ? gr < nrows : gk < ke) {  // a ragged piece, element by element
+        uint32_t w[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const unsigned short lo = gk + 2 * j < ke ? __bfloat16_as_ushort(src[(size_t)gr * ld + gk + 2 * j]) : 0;
-            const unsigned short hi = gk + 2 * j + 1 < ke ? __bfloat16_as_ushort(src[(size_t)gr * ld + gk + 2 * j + 1]) : 0;
-            w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
-          }
-          v[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int j = 0; j < 4; ++j) {
+          const int j0 = 2 * j, j1 = 2 * j + 1;
+          const unsigned short lo = KMAJOR ? bits_or_zero(src + (size_t)gr * ld + gk + j0, gk + j0 < ke)
+                                           : bits_or_zero(src + (size_t)gk * ld + gr + j0, gr + j0 < nrows);
+          const unsigned short hi = KMAJOR ? bits_or_zero(src + (size_t)gr * ld + gk + j1, gk + j1 < ke)
+                                           : bits_or_zero(src + (size_t)gk * ld + gr + j1, gr + j1 < nrows);
+          w[j] = (uint32_t)lo | ((uint32_t)hi << 16);
         }
+        v[i] = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-      const int p = threadIdx.x + i * kTcThreads, r = p >> 3, k = (p & 7) * 8;
-      if (r < R) *reinterpret_cast<uint4*>(dst + tc::sw128(r, k, R)) = v[i];
+      const int p = threadIdx.x + i * kTcThreads;
+      if (p >= kPieces) continue;
+      if (KMAJOR) {
+        *reinterpret_cast<uint4*>(dst + tc::sw128(p >> 3, 8 * (p & 7), R)) = v[i];
+      } else {
+        const int r = 8 * (p % (R / 8)), k = p / (R / 8);
+        const uint32_t w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<unsigned short*>(dst + tc::sw128(r + j, k, R)) =
+              (unsigned short)(w[j >> 1] >> (16 * (j & 1)));
+      }
     }
     return;
   }
-  constexpr int kPer = (R_MAX * kTcK + kTcThreads - 1) / kTcThreads;
+  constexpr int kPer = R * kTcK / kTcThreads;
+  static_assert(R * kTcK % kTcThreads == 0, "whole elements per thread");
   __nv_bfloat16 v[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int e = threadIdx.x + i * kTcThreads;
     // K-contiguous: consecutive threads walk k; row-contiguous: consecutive threads walk rows
-    const int r = kmajor ? e / kTcK : e % R, k = kmajor ? e % kTcK : e / R;
+    const int r = KMAJOR ? e / kTcK : e % R, k = KMAJOR ? e % kTcK : e / R;
     const int gr = r0 + r, gk = k0 + k;
-    v[i] = zero;
-    if (e < R * kTcK && gr < nrows && gk < ke)
-      v[i] = kmajor ? src[(size_t)gr * ld + gk] : src[(size_t)gk * ld + gr];
+    v[i] = __float2bfloat16(0.f);
+    if (gr < nrows && gk < ke) v[i] = KMAJOR ? src[(size_t)gr * ld + gk] : src[(size_t)gk * ld + gr];
   }
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int e = threadIdx.x + i * kTcThreads;
-    const int r = kmajor ? e / kTcK : e % R, k = kmajor ? e % kTcK : e / R;
-    if (e < R * kTcK) *reinterpret_cast<__nv_bfloat16*>(dst + tc::sw128(r, k, R)) = v[i];
+    const int r = KMAJOR ? e / kTcK : e % R, k = KMAJOR ? e % kTcK : e / R;
+    *reinterpret_cast<__nv_bfloat16*>(dst + tc::sw128(r, k, R)) = v[i];
   }
 }
 
 // Stages K chunk [k0, k0 + 64) of the tile's A' rows m0.. (128) and B' rows n0.. (BN, the
 // output columns) into sa / sb.
-__device__ __forceinline__ void stage_tc(const GemmArgs& g, int m0, int n0, int BN, int k0, int ke,
+template <int BN>
+__device__ __forceinline__ void stage_tc(const GemmArgs& g, int m0, int n0, int k0, int ke,
                                          uint8_t* sa, uint8_t* sb) {
-  stage_operand<kTcM>(g.A, g.lda, !g.transA, g.vec_a, m0, g.M, kTcM, k0, ke, sa);
-  stage_operand<64>(g.B, g.ldb, g.transB != 0, g.vec_b, n0, g.N, BN, k0, ke, sb);
+  if (g.transA)
+    stage_operand<kTcM, false>(g.A, g.lda, g.vec_a, m0, g.M, k0, ke, sa);
+  else
+    stage_operand<kTcM, true>(g.A, g.lda, g.vec_a, m0, g.M, k0, ke, sa);
+  if (g.transB)
+    stage_operand<BN, true>(g.B, g.ldb, g.vec_b, n0, g.N, k0, ke, sb);
+  else
+    stage_operand<BN, false>(g.B, g.ldb, g.vec_b, n0, g.N, k0, ke, sb);
 }
 
 // One 128 x BN output tile (BN 16 or 32) over the K range of split blockIdx.z. Every wait is
 // bounded; on expiry the CTA raises its abort flag, skips the rest, waits (bounded) for the
 // MMAs it issued, frees tensor memory, exits and sets *g.error.
-template <int EPI>
-__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(GemmArgs g, int BN) {
+template <int EPI, int BN>
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(GemmArgs g) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 64, "MMA N of an M = 128 tile");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sbase = tc::smem_addr(smem);
@@ -190,7 +216,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(GemmArgs g, int 
   const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * BN;
   const int kb = blockIdx.z * g.k_split, ke = min(g.K, kb + g.k_split);
   const int nchunks = (ke - kb + kTcK - 1) / kTcK;
-  const uint32_t cols = BN <= 32 ? 32u : 64u;  // tensor-memory columns (a power of 2, >= 32)
+  constexpr uint32_t cols = BN <= 32 ? 32u : 64u;  // tensor-memory columns (a power of 2, >= 32)
   const uint64_t limit = g.wait_ns ? g.wait_ns : kTcWaitNs;
   if (threadIdx.x == 0) {
     tc::mbar_init(bar(0), 1);
@@ -217,7 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(GemmArgs g, int 
     __syncthreads();
     if (*s_abort) break;
     const int k0 = kb + c * kTcK;
-    stage_tc(g, m0, n0, BN, k0, ke, smem + s * kTcStage, smem + s * kTcStage + kTcStageA);
+    stage_tc<BN>(g, m0, n0, k0, ke, smem + s * kTcStage, smem + s * kTcStage + kTcStageA);
     tc::fence_async_smem();  // the staged operands are visible to the tensor cores
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -347,8 +373,8 @@ static dim3 gemm_grid(int epi, GemmArgsT<T>& g, int tm, int tn, int k_step, int 
   return dim3((g.M + tm - 1) / tm, (g.N + tn - 1) / tn, splits);
 }
 
-template <int EPI>
-static cudaError_t launch_tc(const GemmArgs& g, dim3 grid, int BN, cudaStream_t stream) {
+template <int EPI, int BN>
+static cudaError_t launch_tc(const GemmArgs& g, dim3 grid, cudaStream_t stream) {
   // the kernel's shared memory is above the 48 KB default: set once per device
   static std::atomic<unsigned long long> set_on{0};
   int dev = 0;
@@ -356,12 +382,17 @@ static cudaError_t launch_tc(const GemmArgs& g, dim3 grid, int BN, cudaStream_t 
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(set_on.load() & bit)) {
-    e = cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    e = cudaFuncSetAttribute(gemm_tc_kernel<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e != cudaSuccess) return e;
     set_on.fetch_or(bit);
   }
-  gemm_tc_kernel<EPI><<<grid, kTcThreads, kTcSmem, stream>>>(g, BN);
+  gemm_tc_kernel<EPI, BN><<<grid, kTcThreads, kTcSmem, stream>>>(g);
   return cudaGetLastError();
+}
+
+template <int EPI>
+static cudaError_t launch_tc_n(const GemmArgs& g, dim3 grid, int BN, cudaStream_t stream) {
+  return BN == 16 ? launch_tc<EPI, 16>(g, grid, stream) : launch_tc<EPI, 32>(g, grid, stream);
 }
 
 cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
@@ -371,14 +402,14 @@ cudaError_t launch_gemm(int epi, const GemmArgs& g0, cudaStream_t stream) {
   const int BN = g.N <= 16 ? 16 : 32;
   const dim3 grid = gemm_grid(epi, g, kTcM, BN, kTcK, 2 * kTcK);
   auto rows16 = [](const void* p, int ld) { return ((uintptr_t)p & 15) == 0 && ld % 8 == 0; };
-  g.vec_a = !g.transA && rows16(g.A, g.lda);
-  g.vec_b = g.transB && rows16(g.B, g.ldb);
+  g.vec_a = rows16(g.A, g.lda);
+  g.vec_b = rows16(g.B, g.ldb);
   switch (epi) {
-    case kEpiStore: return launch_tc<kEpiStore>(g, grid, BN, stream);
-    case kEpiBiasGelu: return launch_tc<kEpiBiasGelu>(g, grid, BN, stream);
-    case kEpiBias: return launch_tc<kEpiBias>(g, grid, BN, stream);
-    case kEpiGeluBwd: return launch_tc<kEpiGeluBwd>(g, grid, BN, stream);
-    default: return launch_tc<kEpiAtomic>(g, grid, BN, stream);
+    case kEpiStore: return launch_tc_n<kEpiStore>(g, grid, BN, stream);
+    case kEpiBiasGelu: return launch_tc_n<kEpiBiasGelu>(g, grid, BN, stream);
+    case kEpiBias: return launch_tc_n<kEpiBias>(g, grid, BN, stream);
+    case kEpiGeluBwd: return launch_tc_n<kEpiGeluBwd>(g, grid, BN, stream);
+    default: return launch_tc_n<kEpiAtomic>(g, grid, BN, stream);
   }
 }
 

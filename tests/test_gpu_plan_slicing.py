@@ -115,3 +115,41 @@ def test_slicing_arguments(torch_cuda):
         assert err.value.code == -1  # CPRRTC_E_INVALID_ARG
     ctx.set_plan_slicing(0, 0)  # one CTA per problem: slice ignored
     ctx.close()
+
+
+@pytest.mark.parametrize("form", ["sequential", "w64_z_plane", "self_collision", "learned"])
+def test_sliced_schedule_in_every_planner_form(torch_cuda, oracle_mod, form):
+    """The other instantiations of the planner kernel under hand-overs: the naive baseline's
+    sequential projection, two waypoints per lane (W = 64, 8-DOF, z-plane, 4 workers), the
+    robot's self-collision pairs, and the learned form (a network warm-starting extend
+    motions): 400 problems (more than the GPU holds at once) in slices of 3 then 2 rounds plan
+    exactly as one CTA per problem."""
+    if form == "w64_z_plane":
+        rb, c, W, workers = S.make_arm8(3), S.z_plane(0.9), 64, 4
+    else:
+        rb, c, W, workers = S.make_arm7(1), S.roll_pitch(), 32, 8
+    pairs = S.self_pairs_gap(rb, 2) if form == "self_collision" else None
+    base_sc, base_s, base_g = PB.planning_problems(oracle_mod, rb, c, 20, 5300,
+                                                   counts=(30, 15, 10), self_pairs=pairs)
+    reps = 20
+    tile = lambda x: np.ascontiguousarray(np.tile(x, (reps, 1)), dtype=np.float32)  # noqa: E731
+    scenes, start, goal = base_sc * reps, tile(base_s), tile(base_g)
+    ctx = ctx_for(rb, c)
+    ctx.set_scene_batch(scenes)
+    if form == "sequential":
+        ctx.set_projection(True)
+    if pairs is not None:
+        ctx.set_self_collision(pairs)
+    if form == "learned":
+        ctx.mlp_init(3)
+        ctx.set_plan_warm_start(5)
+    prm = ctx.plan_params(range_=0.3, W=W, max_rounds=40, workers=workers, seed=21,
+                          use_scene_batch=True, max_path=600)
+    ctx.set_plan_slicing(0)
+    ref = run(torch_cuda, ctx, start, goal, prm)
+    ctx.set_plan_slicing(3, 2)
+    out = run(torch_cuda, ctx, start, goal, prm)
+    PB.assert_same_plans(ref, out, keys=KEYS)
+    print(form, "problems past their first slice:", int((ref["rounds"] > 3).sum()))
+    assert (ref["rounds"] > 3).sum() > 304  # more than the GPU holds at once: hand-overs
+    ctx.close()
