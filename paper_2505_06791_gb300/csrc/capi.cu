@@ -1456,6 +1456,10 @@ int cprrtc_validate_ws(cprrtc_ctx* ctx, const float* q_start, const float* q_end
   return st.end(ctx);
 }
 
+namespace {
+bool mul_within(size_t a, size_t b, size_t limit, size_t* out);  // a * b <= limit, no wrap-around
+}  // namespace
+
 int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
                 const cprrtc_plan_params* pp, int32_t* path_len, float* path, float* path_edges,
                 int32_t* rounds, int64_t* waypoints, float* plan_ms, int64_t* work) {
@@ -1475,6 +1479,14 @@ int cprrtc_plan(cprrtc_ctx* ctx, const float* start, const float* goal, int n,
   if (int rc = check_plan_workers(ctx, pp, "plan")) return rc;
   const size_t dof = ctx->rb.dof, N = (size_t)n, W = (size_t)pp->W;
   const size_t B = (size_t)pp->workers, MN = (size_t)pp->max_nodes;
+  {  // every product below stays far from wrapping around 2^64 (larger requests cannot be met)
+    const size_t lim = (size_t)1 << 56;
+    size_t trees = 0, tree_bytes = 0, worker_bytes = 0;
+    if (!mul_within(N, 2 * MN, lim, &trees) ||
+        !mul_within(trees, (W * dof + 9) * sizeof(float), lim, &tree_bytes) ||
+        !mul_within(N, B * (2 * W * dof + 8) * sizeof(float), lim, &worker_bytes))
+      return fail(ctx, CPRRTC_E_OOM, "plan: the trees of n problems of max_nodes exceed any device memory");
+  }
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t b_nodes = al(N * 2 * MN * 8 * sizeof(float));
   const size_t b_parent = al(N * 2 * MN * sizeof(int));

@@ -392,3 +392,28 @@ def test_plan_with_self_collision(torch_cuda, oracle_mod):
     for k in ("path_len", "rounds", "waypoints", "work"):
         assert np.array_equal(ob[k], out[k]), k
     ctx.close()
+
+
+def test_plan_rejects_tree_sizes_whose_byte_count_would_wrap(torch_cuda):
+    """n * 2 * max_nodes * W * dof * 4 = 2^22 * 2^31 * 64 * 8 * 4 = 2^64 wraps to 0 in 64-bit
+    arithmetic: cprrtc_plan must still see that the trees cannot be allocated (E_OOM) and
+    launch nothing, whatever the schedule."""
+    from paper_2505_06791_gb300 import capi
+    torch = torch_cuda
+    ctx = ctx_for(S.make_arm8(1), S.z_plane())
+    ctx.set_obstacles(S.make_scene(3, n_sph=4))
+    s = torch.zeros((4, 8), dtype=torch.float32, device="cuda")
+    path_len = torch.zeros(4, dtype=torch.int32, device="cuda")
+    path = torch.zeros((4, 4, 8), dtype=torch.float32, device="cuda")
+    for first in (200, 0):
+        ctx.set_plan_slicing(first)
+        for n, max_nodes, workers in ((1 << 22, 1 << 30, 8), (1 << 30, 1 << 30, 8),
+                                      (2_000_000_000, 1 << 20, 1)):
+            prm = ctx.plan_params(range_=0.3, W=64, max_rounds=1, workers=workers,
+                                  max_nodes=max_nodes, max_path=4, seed=1, use_scene_batch=False)
+            rc = capi.cprrtc_plan(ctx.h, s, s, n, prm, path_len, path, None, None, None, None,
+                                  None)
+            assert rc == capi.E_OOM, (n, max_nodes, rc)
+    torch.cuda.synchronize()
+    assert int(path_len.abs().sum()) == 0  # nothing ran
+    ctx.close()
