@@ -836,7 +836,7 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
                                                  const ConsDev& cs, const PlanArgs& a) {
   const bool queued = a.queue != nullptr;
   if (!queued && (int)blockIdx.x >= a.n) return;
-  __shared__ int s_p, s_r0, s_held, s_staged;
+  __shared__ int s_p, s_r0, s_held, s_staged, s_restage;
   const int warp = threadIdx.x >> 5;
   const int B = a.workers, dof = rb.dof, W = a.W;
   extern __shared__ __align__(16) char smem[];
@@ -875,6 +875,9 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
       }
       s_p = p;
       s_r0 = r0;
+      // decided here, before the barrier, so that no thread reads s_staged while it changes
+      s_restage = p >= 0 && (s_staged < 0 || (a.scenes && s_staged != p));
+      if (p >= 0) s_staged = p;
     }
     __syncthreads();
     const int p = s_p, r0 = s_r0;
@@ -887,14 +890,13 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
       sc.n_box = d.z;
       sc.n_cap = d.w;
     }
-    if (a.stage_obs && (s_staged < 0 || (a.scenes && s_staged != p))) {
+    if (a.stage_obs && s_restage) {
       const int n4 = sc.n_float4();
       for (int i = threadIdx.x; i < n4; i += blockDim.x) s_obs[i] = sc.obs[i];
     }
     const float4* obs = a.stage_obs ? s_obs : sc.obs;
     const size_t tree0 = (size_t)p * 2 * a.max_nodes;  // first node slot of this problem
     if (threadIdx.x == 0) {
-      s_staged = p;
       ProblemView& P = sh->pv;
       P.p = p;
       P.start = a.start + (size_t)p * dof;
