@@ -347,15 +347,18 @@ def run_plan(args, world, rank, local):
         sf = out_f["path_len"].cpu().numpy() > 0
         schedule = {
             "time_sliced": {"first_slice_rounds": PLAN_SLICING[0], "slice_rounds": PLAN_SLICING[1],
-                            "ms_per_step": total_ms / args.steps},
+                            "ms_per_step": total_ms / args.steps,
+                            "mean_problems_in_flight": float(ms.sum()) / (total_ms / args.steps)},
             "one_cta_per_problem": {"ms_per_step": f_ms / args.steps,
+                                    "mean_problems_in_flight": float(msf.sum()) / (f_ms / args.steps),
                                     "p50_plan_ms": float(np.percentile(msf[sf], 50)) if sf.any() else None,
                                     "p95_plan_ms": float(np.percentile(msf[sf], 95)) if sf.any() else None},
             "speedup": f_ms / total_ms,
             "same_outputs": bool(same),
             "note": "persistent CTAs; an unsolved problem goes back to the queue's tail between "
                     "slices while others wait, so the long problems share the GPU to the end; "
-                    "plan_ms is the device time of a problem's slices",
+                    "plan_ms is the device time of a problem's slices; problems in flight = the "
+                    "sum of plan_ms over the step (the GPU holds 2 per SM at once)",
         }
 
     # the learned form on the same problems: the network trained first (untimed), every extend
