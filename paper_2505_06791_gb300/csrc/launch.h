@@ -129,6 +129,9 @@ struct PlanState {
 // launch may hand problems over more than 2^32 times.
 struct PlanQueue {
   unsigned long long head, tail;
+  // device time and rounds of every slice that ended with rounds left: the launch's mean
+  // round time, against which a problem's own decides whether it goes back to the queue
+  unsigned long long sum_ns, sum_rounds;
 };
 inline size_t plan_queue_bytes(int n) {
   return sizeof(PlanQueue) + (sizeof(long long) + sizeof(int)) * (size_t)n;

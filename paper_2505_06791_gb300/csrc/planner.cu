@@ -826,6 +826,25 @@ __device__ __forceinline__ bool queue_waiting(PlanQueue* q, int n) {
   return h < un || tl > h - un;
 }
 
+// Mean round time of a problem, relative to the launch's, above which it keeps its CTA.
+constexpr double kKeepFactor = 1.1;
+
+// Thread 0, after a slice of problem p (rounds r0 .. its next round; `prior`: its device time
+// before the slice) that left rounds: p's next holder, -1 when p went back to the queue. A problem whose
+// rounds take longer than the launch's mean by kKeepFactor keeps its CTA: the job ends with
+// the problems of most remaining time, and round-robin would stretch those most. The others
+// go back to the queue's tail while problems wait. Out of line, so that the planner's
+// register allocation does not carry it.
+__device__ __noinline__ int after_slice(const PlanArgs& a, int p, int r0, long long prior) {
+  const PlanState& ps = a.state[p];
+  const unsigned long long sum_ns = atomicAdd(&a.queue->sum_ns, (unsigned long long)(ps.active_ns - prior));
+  const unsigned long long sum_r = atomicAdd(&a.queue->sum_rounds, (unsigned long long)(ps.r_next - r0));
+  const bool slow = sum_r > 0 && (double)ps.active_ns * (double)sum_r >=
+                                     kKeepFactor * (double)sum_ns * (double)ps.r_next;
+  if (!slow && queue_waiting(a.queue, a.n) && queue_push(a.queue, a.n, p, a.wait_ns, a.status)) return -1;
+  return p;
+}
+
 // One CTA per problem (no queue), or persistent CTAs on the time-sliced queue: a CTA takes a
 // problem, runs its next slice, and either keeps it (nothing waits), hands it to the queue's
 // tail (other problems wait), or takes the next one once it is done. Problems that end within
@@ -921,15 +940,7 @@ __device__ __forceinline__ void plan_kernel_body(const RobotDev& rb, const Scene
     const bool done = plan_problem<CT, WPL, SEQ, WARM>(rb, sc, obs, cs, a, sh->pv, S, sh, wc, self,
                                                        WARM ? &a.net : nullptr, nullptr, r0, r1,
                                                        queued);
-    if (queued && threadIdx.x == 0) {
-      if (done) {
-        s_held = -1;
-      } else if (queue_waiting(a.queue, a.n) && queue_push(a.queue, a.n, p, a.wait_ns, a.status)) {
-        s_held = -1;
-      } else {
-        s_held = p;
-      }
-    }
+    if (queued && threadIdx.x == 0) s_held = done ? -1 : after_slice(a, p, s_r0, sh->t_prior);
   }
   wc.flush(a.work_counters);
 }
