@@ -207,7 +207,7 @@ PLAN_N = 1000
 PLAN_PARAMS = dict(range_=0.3, W=32, max_rounds=1000, workers=8, max_nodes=2048,
                    max_connect=32, max_path=512)
 # the planner's time-sliced schedule (cprrtc_set_plan_slicing): first slice, later slices (rounds)
-PLAN_SLICING = (200, 50)
+PLAN_SLICING = (100, 50)
 
 
 def planner_scenes(n, seed=2):

@@ -395,14 +395,15 @@ int cprrtc_set_plan_warm_start(cprrtc_ctx* ctx, int refine_iters);
 
 /* Schedule of cprrtc_plan's problems on the GPU (not in the paper, which plans one problem per
  * run; the search and every output but plan_ms's timing are the same for every setting).
- * With first_slice > 0 (the default: first_slice 200, slice 50) the planner runs as many
+ * With first_slice > 0 (the default: first_slice 100, slice 50) the planner runs as many
  * persistent CTAs as fit the GPU at once; a CTA takes a problem from a queue and runs its
  * first first_slice rounds, later ones slice rounds at a time. Between slices an unsolved
- * problem goes back to the queue's tail while other problems wait for a CTA, and stays with
+ * problem goes back to the queue's tail while other problems wait for a CTA, unless its
+ * rounds have taken more than 1.1 times the launch's mean round time so far, and stays with
  * its CTA otherwise (its state between slices, about 1.6 KB, lives in the library's device
  * memory beside the trees). Problems that solve within their first slice plan in one stretch;
- * the long ones share the GPU round-robin, so a large batch no longer ends with the long
- * problems that happened to start last. first_slice = 0: one CTA per problem, each planned
+ * the long ones share the GPU round-robin, the slowest keeping their CTAs, so a large batch
+ * no longer ends with the long problems that happened to start last. first_slice = 0: one CTA per problem, each planned
  * in one stretch (cprrtc_plan_static always plans so). The queue's one wait (for another
  * CTA's store of a handed-over problem, a few instructions) gives up after 1 s.
  * Errors: E_INVALID_ARG (first_slice < 0, or slice < 1 with first_slice > 0). */

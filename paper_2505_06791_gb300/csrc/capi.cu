@@ -110,7 +110,7 @@ struct cprrtc_ctx {
   bool mlp_fp32 = false;    // the network's FP32 checking mode
   unsigned long long wait_ns = 0;  // bounded-wait limit of the tensor-core kernels (0: 1 s)
   int plan_warm = 0;               // planner's learned form: refine iterations (0: off)
-  int plan_first_slice = 200;      // planner's time-sliced schedule (0: one CTA per problem)
+  int plan_first_slice = 100;      // planner's time-sliced schedule (0: one CTA per problem)
   int plan_slice = 50;
   float* d_warm = nullptr;  // corrections [n*W][16]
   size_t warm_cap = 0;      // bytes
