@@ -238,13 +238,14 @@ int64_t cprrtc_mlp_param_count(int dof);
  * Requires set_robot. Errors: E_NOT_CONFIGURED, E_CUDA, E_OOM. */
 int cprrtc_mlp_init(cprrtc_ctx* ctx, uint64_t seed);
 
-/* Limit of every bounded wait in the tensor-core kernels (the GEMM-form collision check and
- * the warm-start network's fused inference), in seconds: 0 restores the default of 1 s;
- * otherwise 1e-6 .. 10. A wait that reaches it makes the kernel give up: it raises its
- * abort flag, lets its copies and MMAs in flight complete, frees its tensor memory and
- * exits, and the call reports it: cprrtc_validate with a GEMM mode and cprrtc_mlp_infer
- * return E_TIMEOUT when they are synchronous (some array in host memory; their outputs are
- * then not valid), and cprrtc_validate_ws falls back to plain Alg. 1 for every motion. The
+/* Limit of every bounded wait in the tensor-core kernels (the GEMM-form collision check, the
+ * warm-start network's fused inference and its training GEMMs), in seconds: 0 restores the
+ * default of 1 s; otherwise 1e-6 .. 10. A wait that reaches it makes the kernel give up: it
+ * raises its abort flag, lets its copies and MMAs in flight complete, frees its tensor
+ * memory and exits, and the call reports it: cprrtc_validate with a GEMM mode and
+ * cprrtc_mlp_infer return E_TIMEOUT when they are synchronous (some array in host memory;
+ * their outputs are then not valid), cprrtc_mlp_grad and cprrtc_mlp_train return
+ * E_TIMEOUT, and cprrtc_validate_ws falls back to plain Alg. 1 for every motion. The
  * next call starts afresh. The paper has no counterpart: this is a failure-detection
  * setting, and a very short limit lets a test make the waits run out on an ordinary input.
  * Errors: E_INVALID_ARG. */
@@ -281,8 +282,11 @@ int cprrtc_mlp_load(cprrtc_ctx* ctx, const char* path);
 /* Loss L = (1 / rows) sum_r 0.5 |f(q_r) - (t_r - q_r)|^2 over rows pairs (q [rows][dof],
  * t [rows][dof]: q's projection) and its gradient with respect to every parameter
  * (grads: host array of cprrtc_mlp_param_count(dof) floats, compact layout; loss: host,
- * 1 float; either may be NULL). Does not change the parameters. Synchronous.
- * Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_CUDA, E_OOM. */
+ * 1 float; either may be NULL). Does not change the parameters. Synchronous. The GEMMs run
+ * on the tensor cores (BF16, FP32 accumulation; FP32 FMAs in the checking mode), every wait
+ * bounded by cprrtc_set_wait_limit's limit.
+ * Errors: E_NOT_CONFIGURED, E_INVALID_ARG, E_CUDA, E_OOM, E_TIMEOUT (a wait ran out; the
+ * outputs are then not valid). */
 int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, float* grads,
                     float* loss);
 
@@ -290,7 +294,8 @@ int cprrtc_mlp_grad(cprrtc_ctx* ctx, const float* q, const float* t, int rows, f
  * 0.999, eps 1e-8, learning rate lr) over floor(n / batch) batches in an order drawn per
  * epoch from `seed`. loss_per_epoch [epochs] (host, may be NULL) receives each epoch's mean
  * batch loss. Synchronous. Errors: E_NOT_CONFIGURED, E_INVALID_ARG (n < batch, batch < 1,
- * epochs < 0, lr not finite), E_CUDA, E_OOM. */
+ * epochs < 0, lr not finite), E_CUDA, E_OOM, E_TIMEOUT (a wait of the tensor-core GEMMs ran
+ * out; the parameters are then not valid). */
 int cprrtc_mlp_train(cprrtc_ctx* ctx, const float* q, const float* t, int n, int batch,
                      int epochs, float lr, uint64_t seed, float* loss_per_epoch);
 
